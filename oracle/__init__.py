@@ -1,0 +1,185 @@
+"""CPU oracle (test infrastructure only).
+
+A plain, slow CPU implementation of brushed multivariate volume rendering and
+linked parallel-coordinates histograms (arXiv 2207.12011, Sections 2.1-2.2):
+FP64 for every continuous quantity, FP32 with individually rounded IEEE
+operations for every integer decision (sample count, shell test, interpolation
+cell, brush test on the FP32 trilinear value, brick activity), written in C
+(`oracle.c`) and driven from here with ctypes.
+
+Only the test suite, the smoke check and the CPU-baseline leg of the
+benchmark may import this package. It shares no code with the CUDA library.
+
+Parity unpinned: appearance against the paper's figures (figures and data
+set absent). Every other function is pinned by the CPU tests in
+tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_DIR = os.path.join(_HERE, "lib")
+_LIB_PATH = os.path.join(_LIB_DIR, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+BRICK = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (no FP contraction, so FP32 steps round one by one)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i32, u32, f32 = ctypes.c_int, ctypes.c_uint32, ctypes.c_float
+            lib.oracle_brick_minmax.argtypes = [P, i32, i32, P, P]
+            lib.oracle_classify.argtypes = [P, P, i32, i32, f32, f32, P, P, u32, P, P]
+            lib.oracle_lod_mean.argtypes = [P, i32, i32, P]
+            lib.oracle_shell_bounds.argtypes = [i32, f32, f32, P, P]
+            lib.oracle_histogram.argtypes = [P, i32, i32, f32, f32, P, P, u32, i32,
+                                             P, i32, i32, P, P, P]
+            lib.oracle_render.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
+                                          P, P, u32, P, i32, f32, f32, P, i32, P,
+                                          ctypes.c_int64, P, P, i32]
+            lib.oracle_render.restype = i32
+            lib.oracle_num_threads.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _vol(vol) -> np.ndarray:
+    """Stored field values as float32 [V][n][n][n] (FP16 converts exactly)."""
+    if hasattr(vol, "detach"):
+        vol = vol.detach().cpu().float().numpy()
+    vol = _f32(vol)
+    assert vol.ndim == 4 and vol.shape[1] == vol.shape[2] == vol.shape[3], vol.shape
+    return vol
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def brick_minmax(vol):
+    """Per-brick, per-variable min and max over the 9^3 apron vertices -> (bmin, bmax) [nb,nb,nb,V]."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    nb = (n + BRICK - 1) // BRICK
+    mn = np.empty((nb, nb, nb, V), np.float32)
+    mx = np.empty((nb, nb, nb, V), np.float32)
+    _load().oracle_brick_minmax(_ptr(v), n, V, _ptr(mn), _ptr(mx))
+    return mn, mx
+
+
+def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask):
+    """Active and skippable brick flags (uint8 [nb,nb,nb]) from brick min/max and a brush."""
+    bmin, bmax = _f32(bmin), _f32(bmax)
+    V = bmin.shape[-1]
+    nb = bmin.shape[0]
+    lo, hi = _f32(lo), _f32(hi)
+    act = np.empty((nb, nb, nb), np.uint8)
+    skp = np.empty((nb, nb, nb), np.uint8)
+    _load().oracle_classify(_ptr(bmin), _ptr(bmax), n, V, np.float32(r_in), np.float32(r_out),
+                            _ptr(lo), _ptr(hi), int(active_mask) & 0xFFFFFFFF, _ptr(act), _ptr(skp))
+    return act, skp
+
+
+def lod_mean(vol) -> np.ndarray:
+    """One coarser level: the FP32 2x2x2 mean -> float32 [V][m][m][m], m = (n+1)//2."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    m = (n + 1) // 2
+    out = np.empty((V, m, m, m), np.float32)
+    _load().oracle_lod_mean(_ptr(v), n, V, _ptr(out))
+    return out
+
+
+def shell_bounds(n, r_in, r_out):
+    a = np.zeros(1, np.int64)
+    b = np.zeros(1, np.int64)
+    _load().oracle_shell_bounds(n, np.float32(r_in), np.float32(r_out), _ptr(a), _ptr(b))
+    return int(a[0]), int(b[0])
+
+
+def histogram(vol, r_in, r_out, lo, hi, active_mask, axis_order, edges, use_brush=True):
+    """Adjacent-axis PC histograms -> (uint32 [naxes-1, bins, bins], counted cells)."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    edges = _f32(edges)
+    naxes, bins = edges.shape[0], edges.shape[1] - 1
+    order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32))
+    assert order.shape[0] == naxes
+    out = np.zeros((naxes - 1, bins, bins), np.uint32)
+    cells = np.zeros(1, np.uint64)
+    _load().oracle_histogram(_ptr(v), n, V, np.float32(r_in), np.float32(r_out),
+                             _ptr(_f32(lo)), _ptr(_f32(hi)), int(active_mask) & 0xFFFFFFFF,
+                             int(bool(use_brush)), _ptr(order), naxes, bins, _ptr(edges),
+                             _ptr(out), _ptr(cells))
+    return out, int(cells[0])
+
+
+def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
+           tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0):
+    """Render (or render a subset of pixels) -> (rgba float64 [npix,4], counts uint32 [npix,2]).
+
+    counts[:, 0] = lattice samples marched (entry to termination),
+    counts[:, 1] = samples kept (in shell and in brush).
+    With pixels=None the result is reshaped to [h, w, 4] / [h, w, 2].
+    """
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    cam = _f32(cam)
+    assert cam.shape == (10,)
+    tf = _f32(tf_rgbs)
+    assert tf.shape == (256, 4)
+    bg = np.ascontiguousarray(np.asarray(bg, dtype=np.float64))
+    if pixels is None:
+        npix = w * h
+        pix_ptr = None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+        npix = pix.shape[0]
+        pix_ptr = _ptr(pix)
+    out = np.zeros((npix, 4), np.float64)
+    cnt = np.zeros((npix, 2), np.uint32)
+    rc = _load().oracle_render(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(cam),
+                               int(w), int(h), np.float32(dt), _ptr(_f32(lo)), _ptr(_f32(hi)),
+                               int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
+                               np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
+                               pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_render: invalid arguments")
+    if pixels is None:
+        return out.reshape(h, w, 4), cnt.reshape(h, w, 2)
+    return out, cnt

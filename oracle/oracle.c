@@ -1,0 +1,489 @@
+/*
+ * CPU oracle for brushed multivariate volume rendering and linked
+ * parallel-coordinates histograms (arXiv 2207.12011, Section 2.2 "Rendering"
+ * and Section 2.1 "Data Preprocessing").
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call this file;
+ * only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark load it. It shares no code, header or constant with the CUDA
+ * library.
+ *
+ * What it computes, plainly and slowly:
+ *   - brick min/max per variable over each 8^3 brick plus its +1 apron;
+ *   - brush classification of bricks (shell intersection and brush box);
+ *   - the 2x2x2 mean used for the coarser levels of detail (Section 2.1);
+ *   - front-to-back emission-absorption ray marching where a sample is
+ *     discarded when any restricted variable lies outside its brush bounds
+ *     (Section 2.2), colour from a 1D transfer function, early termination;
+ *   - adjacent-axis parallel-coordinates density histograms of the in-shell,
+ *     in-brush cells (Section 2.1 PC data, Fig. 2).
+ *
+ * Precision. Every continuous quantity (ray geometry for the colour value,
+ * transfer-function lookup, opacity, compositing) is FP64. Every quantity that
+ * DECIDES an integer -- how many lattice samples a ray has, whether a sample
+ * is in the shell, which cell it interpolates from, whether its FP32
+ * trilinear value passes the brush, which bricks are active -- is computed in
+ * FP32 with individually rounded IEEE operations (fmaf, +, -, *, /, sqrtf) in
+ * one fixed order, because the method interpolates in software FP32 and an
+ * integer decision must be taken in the precision of the method on both sides.
+ * Build with -ffp-contract=off so the compiler fuses nothing on its own.
+ *
+ * Parity of the appearance against the paper's figures is unpinned: the
+ * figures and the data set are absent.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define BRICK 8
+
+/* ------------------------------------------------------------------ */
+/* Volume access: vol[v][z][y][x] float32 (stored values, exact).       */
+/* ------------------------------------------------------------------ */
+static inline float val(const float *vol, int n, int v, int x, int y, int z) {
+    return vol[(((size_t)v * n + z) * n + y) * n + x];
+}
+
+/* ------------------------------------------------------------------ */
+/* Brick min/max: for brick (bx,by,bz) and variable v, the min and max  */
+/* of the stored values at vertices 8b .. min(8b+8, n-1) on each axis.  */
+/* A sample whose lower interpolation corner lies in the brick reads    */
+/* only these vertices. NaN values are ignored (fmin/fmax).             */
+/* Output layout: [bz][by][bx][v].                                      */
+/* ------------------------------------------------------------------ */
+void oracle_brick_minmax(const float *vol, int n, int nvars, float *out_min, float *out_max) {
+    int nb = (n + BRICK - 1) / BRICK;
+    for (int bz = 0; bz < nb; bz++)
+        for (int by = 0; by < nb; by++)
+            for (int bx = 0; bx < nb; bx++)
+                for (int v = 0; v < nvars; v++) {
+                    double mn = NAN, mx = NAN;
+                    int x1 = bx * BRICK + BRICK; if (x1 > n - 1) x1 = n - 1;
+                    int y1 = by * BRICK + BRICK; if (y1 > n - 1) y1 = n - 1;
+                    int z1 = bz * BRICK + BRICK; if (z1 > n - 1) z1 = n - 1;
+                    for (int z = bz * BRICK; z <= z1; z++)
+                        for (int y = by * BRICK; y <= y1; y++)
+                            for (int x = bx * BRICK; x <= x1; x++) {
+                                double a = val(vol, n, v, x, y, z);
+                                mn = fmin(mn, a);
+                                mx = fmax(mx, a);
+                            }
+                    size_t o = (((size_t)bz * nb + by) * nb + bx) * nvars + v;
+                    out_min[o] = (float)mn;
+                    out_max[o] = (float)mx;
+                }
+}
+
+/* ------------------------------------------------------------------ */
+/* Brush classification of bricks (FP32 decisions).                     */
+/*                                                                      */
+/* A brick is active when (1) the world box its samples can occupy,     */
+/* widened by 2^-10, meets the shell r_in <= |p| <= r_out, and (2) for   */
+/* every restricted variable v, max_v + d >= lo_v and min_v - d <= hi_v, */
+/* d = max(|min_v|, |max_v|) * 2^-20 + 2^-120. The widening d covers     */
+/* the rounding of the FP32 trilinear interpolation (at most about      */
+/* 10 * 2^-24 * max|corner|), so no sample that passes the brush can    */
+/* lie in an inactive brick. A brick is skippable when it and all its   */
+/* existing 26 neighbours are inactive.                                 */
+/* Output: active[b], skippable[b] as bytes 0/1, b = (bz*nb+by)*nb+bx.  */
+/* ------------------------------------------------------------------ */
+static void brick_box_axis(int b, int nb, int n, float *lo, float *hi) {
+    float sc = 2.0f / (float)n;
+    float l = fmaf((float)(b * BRICK) + 0.5f, sc, -1.0f) - 0x1p-10f;
+    float h = fmaf((float)(b * BRICK + BRICK) + 0.5f, sc, -1.0f) + 0x1p-10f;
+    if (b == 0) l = -2.0f;
+    if (b == nb - 1) h = 2.0f;
+    *lo = l;
+    *hi = h;
+}
+
+void oracle_classify(const float *bmin, const float *bmax, int n, int nvars,
+                     float r_in, float r_out, const float *lo, const float *hi,
+                     uint32_t active_mask, uint8_t *active, uint8_t *skippable) {
+    int nb = (n + BRICK - 1) / BRICK;
+    float rin2 = r_in * r_in, rout2 = r_out * r_out;
+    for (int bz = 0; bz < nb; bz++)
+        for (int by = 0; by < nb; by++)
+            for (int bx = 0; bx < nb; bx++) {
+                int bc[3] = {bx, by, bz};
+                float nearc[3], farc[3];
+                for (int a = 0; a < 3; a++) {
+                    float l, h;
+                    brick_box_axis(bc[a], nb, n, &l, &h);
+                    nearc[a] = (l > 0.0f) ? l : ((h < 0.0f) ? -h : 0.0f);
+                    farc[a] = fmaxf(fabsf(l), fabsf(h));
+                }
+                float near2 = fmaf(nearc[2], nearc[2], fmaf(nearc[1], nearc[1], nearc[0] * nearc[0]));
+                float far2 = fmaf(farc[2], farc[2], fmaf(farc[1], farc[1], farc[0] * farc[0]));
+                int act = (near2 <= rout2) && (far2 >= rin2);
+                size_t b = ((size_t)bz * nb + by) * nb + bx;
+                for (int v = 0; v < nvars && act; v++) {
+                    if (!((active_mask >> v) & 1u)) continue;
+                    float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
+                    float m = fmaxf(fabsf(mn), fabsf(mx));
+                    float d = fmaf(m, 0x1p-20f, 0x1p-120f);
+                    float up = mx + d, dn = mn - d;
+                    if (!(up >= lo[v] && dn <= hi[v])) act = 0;
+                }
+                active[b] = (uint8_t)act;
+            }
+    for (int bz = 0; bz < nb; bz++)
+        for (int by = 0; by < nb; by++)
+            for (int bx = 0; bx < nb; bx++) {
+                int s = 1;
+                for (int dz = -1; dz <= 1; dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int dx = -1; dx <= 1; dx++) {
+                            int x = bx + dx, y = by + dy, z = bz + dz;
+                            if (x < 0 || y < 0 || z < 0 || x >= nb || y >= nb || z >= nb) continue;
+                            if (active[((size_t)z * nb + y) * nb + x]) s = 0;
+                        }
+                skippable[((size_t)bz * nb + by) * nb + bx] = (uint8_t)s;
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* Level of detail (Section 2.1: each coarser level holds 1/8 of the    */
+/* cells). Coarse cell (i,j,k) = mean of fine cells (2i+a, 2j+b, 2k+c), */
+/* a,b,c in {0,1}, fine indices clamped to n-1; summed in FP32 as       */
+/* ((c000+c100)+(c010+c110)) + ((c001+c101)+(c011+c111)), times 1/8.    */
+/* Output: [v][m][m][m] float32, m = (n+1)/2.                           */
+/* ------------------------------------------------------------------ */
+void oracle_lod_mean(const float *vol, int n, int nvars, float *out) {
+    int m = (n + 1) / 2;
+    for (int v = 0; v < nvars; v++)
+        for (int k = 0; k < m; k++)
+            for (int j = 0; j < m; j++)
+                for (int i = 0; i < m; i++) {
+                    int x0 = 2 * i, y0 = 2 * j, z0 = 2 * k;
+                    int x1 = x0 + 1 < n ? x0 + 1 : n - 1;
+                    int y1 = y0 + 1 < n ? y0 + 1 : n - 1;
+                    int z1 = z0 + 1 < n ? z0 + 1 : n - 1;
+                    float s0 = (val(vol, n, v, x0, y0, z0) + val(vol, n, v, x1, y0, z0)) +
+                               (val(vol, n, v, x0, y1, z0) + val(vol, n, v, x1, y1, z0));
+                    float s1 = (val(vol, n, v, x0, y0, z1) + val(vol, n, v, x1, y0, z1)) +
+                               (val(vol, n, v, x0, y1, z1) + val(vol, n, v, x1, y1, z1));
+                    out[(((size_t)v * m + k) * m + j) * m + i] = (s0 + s1) * 0.125f;
+                }
+}
+
+/* ------------------------------------------------------------------ */
+/* Parallel-coordinates histograms.                                     */
+/*                                                                      */
+/* Cell (x,y,z) of an n^3 grid has centre p = (2i+1-n)/n per axis. It  */
+/* is in the shell iff S_in <= s <= S_out with the integer              */
+/* s = sum (2i+1-n)^2, S_in = ceil((r_in n)^2), S_out = floor((r_out n)^2)*/
+/* (both evaluated in double). It is in the brush iff lo_v <= v <= hi_v */
+/* for every restricted v (NaN fails). Its bin on an axis is the number */
+/* of interior edges e_1..e_{bins-1} that are <= the value. For each     */
+/* adjacent axis pair p: H[p][bin_p][bin_{p+1}] += 1.                    */
+/* ------------------------------------------------------------------ */
+void oracle_shell_bounds(int n, float r_in, float r_out, int64_t *s_in, int64_t *s_out) {
+    double a = (double)r_in * (double)n, b = (double)r_out * (double)n;
+    *s_in = (int64_t)ceil(a * a);
+    *s_out = (int64_t)floor(b * b);
+}
+
+static int bin_of(float v, const float *edges, int bins) {
+    int c = 0;
+    for (int k = 1; k < bins; k++)
+        if (v >= edges[k]) c++;
+    return c;
+}
+
+void oracle_histogram(const float *vol, int n, int nvars, float r_in, float r_out,
+                      const float *lo, const float *hi, uint32_t active_mask, int use_brush,
+                      const int *axis_order, int naxes, int bins, const float *edges,
+                      uint32_t *out /* (naxes-1)*bins*bins */, uint64_t *out_cells) {
+    int64_t s_in, s_out;
+    oracle_shell_bounds(n, r_in, r_out, &s_in, &s_out);
+    memset(out, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins);
+    uint64_t cells = 0;
+    int *b = (int *)malloc(sizeof(int) * naxes);
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                int64_t dx = 2 * x + 1 - n, dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
+                int64_t s = dx * dx + dy * dy + dz * dz;
+                if (s < s_in || s > s_out) continue;
+                int keep = 1;
+                if (use_brush)
+                    for (int v = 0; v < nvars; v++) {
+                        if (!((active_mask >> v) & 1u)) continue;
+                        float a = val(vol, n, v, x, y, z);
+                        if (!(a >= lo[v] && a <= hi[v])) { keep = 0; break; }
+                    }
+                if (!keep) continue;
+                cells++;
+                for (int a = 0; a < naxes; a++)
+                    b[a] = bin_of(val(vol, n, axis_order[a], x, y, z), edges + (size_t)a * (bins + 1), bins);
+                for (int p = 0; p + 1 < naxes; p++)
+                    out[((size_t)p * bins + b[p]) * bins + b[p + 1]] += 1u;
+            }
+    free(b);
+    if (out_cells) *out_cells = cells;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ray marching (Section 2.2).                                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const float *vol;
+    int n, nvars;
+    float r_in, r_out;
+    const float *cam;       /* eye[3], target[3], up[3], tan_half_vfov */
+    int w, h;
+    float dt;
+    const float *lo, *hi;
+    uint32_t active_mask;
+    const float *tf;        /* 256 x (r,g,b,sigma) */
+    int color_var;
+    float tf_lo, tf_hi;
+    const double *bg;       /* premultiplied background rgba */
+    int ert;
+    const int64_t *pixels;  /* NULL: all pixels in row-major order */
+    int64_t npix;
+    double *out;            /* npix x 4 */
+    uint32_t *counts;       /* npix x 2: marched lattice samples, kept samples (may be NULL) */
+    int64_t next;           /* shared work counter */
+    pthread_mutex_t lock;
+} render_job;
+
+/* FP32 decision geometry of the ray through pixel (px, py). */
+typedef struct { float o[3], d[3], t0, t1; int hit; } ray32;
+
+static void cross_f32(const float a[3], const float b[3], float c[3]) {
+    c[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
+    c[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
+    c[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
+}
+
+static float dot_f32(const float a[3], const float b[3]) {
+    return fmaf(a[2], b[2], fmaf(a[1], b[1], a[0] * b[0]));
+}
+
+static void normalize_f32(float a[3]) {
+    float l = sqrtf(dot_f32(a, a));
+    a[0] = a[0] / l; a[1] = a[1] / l; a[2] = a[2] / l;
+}
+
+static ray32 make_ray32(const render_job *J, int px, int py) {
+    ray32 r;
+    const float *c = J->cam;
+    float F[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
+    normalize_f32(F);
+    float R[3], U[3];
+    cross_f32(F, c + 6, R);
+    normalize_f32(R);
+    cross_f32(R, F, U);
+    float th = c[9];
+    float aspect = (float)J->w / (float)J->h;
+    float sxs = th * aspect;
+    float qx = (float)(2 * px + 1) / (float)J->w;
+    float qy = (float)(2 * py + 1) / (float)J->h;
+    float sx = (qx - 1.0f) * sxs;
+    float sy = (1.0f - qy) * th;
+    float d[3];
+    for (int a = 0; a < 3; a++) d[a] = fmaf(sy, U[a], fmaf(sx, R[a], F[a]));
+    normalize_f32(d);
+    for (int a = 0; a < 3; a++) { r.o[a] = c[a]; r.d[a] = d[a]; }
+    /* Sphere entry/exit through the closest point to the centre. */
+    float b = dot_f32(r.o, r.d);
+    float hv[3];
+    for (int a = 0; a < 3; a++) hv[a] = fmaf(-b, r.d[a], r.o[a]);
+    float h2 = dot_f32(hv, hv);
+    float disc = J->r_out * J->r_out - h2;
+    r.hit = disc > 0.0f;
+    if (r.hit) {
+        float sq = sqrtf(disc);
+        r.t0 = fmaxf(-b - sq, 0.0f);
+        r.t1 = -b + sq;
+    } else {
+        r.t0 = r.t1 = 0.0f;
+    }
+    return r;
+}
+
+/* FP64 geometry of the same ray, for the colour value. */
+typedef struct { double o[3], d[3], t0; } ray64;
+
+static ray64 make_ray64(const render_job *J, int px, int py) {
+    ray64 r;
+    const float *c = J->cam;
+    double F[3] = {(double)c[3] - c[0], (double)c[4] - c[1], (double)c[5] - c[2]};
+    double l = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+    for (int a = 0; a < 3; a++) F[a] /= l;
+    double up[3] = {c[6], c[7], c[8]};
+    double R[3] = {F[1] * up[2] - F[2] * up[1], F[2] * up[0] - F[0] * up[2], F[0] * up[1] - F[1] * up[0]};
+    l = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    for (int a = 0; a < 3; a++) R[a] /= l;
+    double U[3] = {R[1] * F[2] - R[2] * F[1], R[2] * F[0] - R[0] * F[2], R[0] * F[1] - R[1] * F[0]};
+    double th = c[9];
+    double sx = ((2.0 * px + 1.0) / J->w - 1.0) * th * ((double)J->w / J->h);
+    double sy = (1.0 - (2.0 * py + 1.0) / J->h) * th;
+    double d[3];
+    for (int a = 0; a < 3; a++) d[a] = F[a] + sx * R[a] + sy * U[a];
+    l = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int a = 0; a < 3; a++) { r.o[a] = c[a]; r.d[a] = d[a] / l; }
+    double b = r.o[0] * r.d[0] + r.o[1] * r.d[1] + r.o[2] * r.d[2];
+    double cc = r.o[0] * r.o[0] + r.o[1] * r.o[1] + r.o[2] * r.o[2] - (double)J->r_out * J->r_out;
+    double disc = b * b - cc;
+    r.t0 = disc > 0 ? fmax(-b - sqrt(disc), 0.0) : 0.0;
+    return r;
+}
+
+/* FP32 trilinear interpolation of variable v at FP32 grid coordinates.   */
+/* Lerps along x, then y, then z; each lerp is fmaf(f, b - a, a).          */
+static inline float lerp32(float a, float b, float f) { return fmaf(f, b - a, a); }
+
+static void grid_coord32(float p, int n, int *i0, float *f) {
+    float hn = 0.5f * (float)n;
+    float u = fmaf(p, hn, hn - 0.5f);
+    u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
+    int i = (int)floorf(u);
+    if (i > n - 2) i = n - 2;
+    *i0 = i;
+    *f = u - (float)i;
+}
+
+static float interp32(const render_job *J, int v, const int i[3], const float f[3]) {
+    const float *vol = J->vol;
+    int n = J->n;
+    float c[2][2][2];
+    for (int dz = 0; dz < 2; dz++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dx = 0; dx < 2; dx++) c[dx][dy][dz] = val(vol, n, v, i[0] + dx, i[1] + dy, i[2] + dz);
+    float c00 = lerp32(c[0][0][0], c[1][0][0], f[0]);
+    float c10 = lerp32(c[0][1][0], c[1][1][0], f[0]);
+    float c01 = lerp32(c[0][0][1], c[1][0][1], f[0]);
+    float c11 = lerp32(c[0][1][1], c[1][1][1], f[0]);
+    float c0 = lerp32(c00, c10, f[1]);
+    float c1 = lerp32(c01, c11, f[1]);
+    return lerp32(c0, c1, f[2]);
+}
+
+/* FP64 trilinear interpolation at an FP64 world position (same clamping). */
+static double interp64(const render_job *J, int v, const double p[3]) {
+    int n = J->n, i[3];
+    double f[3];
+    for (int a = 0; a < 3; a++) {
+        double u = (p[a] + 1.0) * 0.5 * n - 0.5;
+        if (u < 0) u = 0;
+        if (u > n - 1) u = n - 1;
+        int k = (int)floor(u);
+        if (k > n - 2) k = n - 2;
+        i[a] = k;
+        f[a] = u - k;
+    }
+    double s = 0.0;
+    for (int dz = 0; dz < 2; dz++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dx = 0; dx < 2; dx++) {
+                double w = (dx ? f[0] : 1 - f[0]) * (dy ? f[1] : 1 - f[1]) * (dz ? f[2] : 1 - f[2]);
+                s += w * val(J->vol, n, v, i[0] + dx, i[1] + dy, i[2] + dz);
+            }
+    return s;
+}
+
+static void render_pixel(const render_job *J, int px, int py, double *out, uint32_t *cnt) {
+    ray32 r = make_ray32(J, px, py);
+    ray64 q = make_ray64(J, px, py);
+    double C[3] = {0, 0, 0}, A = 0.0;
+    uint32_t marched = 0, kept = 0;
+    const double thr = 1.0 - ldexp(1.0, -12);
+    float rin2 = J->r_in * J->r_in, rout2 = J->r_out * J->r_out;
+    if (r.hit) {
+        for (int k = 0;; k++) {
+            float t = fmaf((float)k + 0.5f, J->dt, r.t0);
+            if (!(t < r.t1)) break;
+            marched++;
+            float p[3];
+            for (int a = 0; a < 3; a++) p[a] = fmaf(t, r.d[a], r.o[a]);
+            float r2 = dot_f32(p, p);
+            if (!(r2 >= rin2 && r2 <= rout2)) continue;
+            int i0[3];
+            float f[3];
+            for (int a = 0; a < 3; a++) grid_coord32(p[a], J->n, &i0[a], &f[a]);
+            int keep = 1;
+            for (int v = 0; v < J->nvars && keep; v++) {
+                if (!((J->active_mask >> v) & 1u)) continue;
+                float s = interp32(J, v, i0, f);
+                if (!(s >= J->lo[v] && s <= J->hi[v])) keep = 0;
+            }
+            if (!keep) continue;
+            kept++;
+            /* Colour: FP64 value at the FP64 sample position. */
+            double tk = q.t0 + ((double)k + 0.5) * (double)J->dt;
+            double p64[3];
+            for (int a = 0; a < 3; a++) p64[a] = q.o[a] + tk * q.d[a];
+            double vc = interp64(J, J->color_var, p64);
+            double s = (vc - J->tf_lo) / ((double)J->tf_hi - J->tf_lo) * 255.0;
+            if (s < 0) s = 0;
+            if (s > 255) s = 255;
+            int j = (int)floor(s);
+            if (j > 254) j = 254;
+            double w = s - j;
+            double e[4];
+            for (int c = 0; c < 4; c++) e[c] = J->tf[j * 4 + c] * (1.0 - w) + J->tf[(j + 1) * 4 + c] * w;
+            double alpha = 1.0 - exp(-e[3] * (double)J->dt);
+            double tr = 1.0 - A;
+            for (int c = 0; c < 3; c++) C[c] += tr * alpha * e[c];
+            A += tr * alpha;
+            if (J->ert && A >= thr) break;
+        }
+    }
+    out[0] = C[0] + (1.0 - A) * J->bg[0];
+    out[1] = C[1] + (1.0 - A) * J->bg[1];
+    out[2] = C[2] + (1.0 - A) * J->bg[2];
+    out[3] = A + (1.0 - A) * J->bg[3];
+    if (cnt) { cnt[0] = marched; cnt[1] = kept; }
+}
+
+static void *render_worker(void *arg) {
+    render_job *J = (render_job *)arg;
+    const int64_t chunk = 64;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int64_t s = J->next;
+        J->next += chunk;
+        pthread_mutex_unlock(&J->lock);
+        if (s >= J->npix) break;
+        int64_t e = s + chunk < J->npix ? s + chunk : J->npix;
+        for (int64_t i = s; i < e; i++) {
+            int64_t pix = J->pixels ? J->pixels[i] : i;
+            int px = (int)(pix % J->w), py = (int)(pix / J->w);
+            render_pixel(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL);
+        }
+    }
+    return NULL;
+}
+
+int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
+                  const float *cam, int w, int h, float dt,
+                  const float *lo, const float *hi, uint32_t active_mask,
+                  const float *tf, int color_var, float tf_lo, float tf_hi,
+                  const double *bg, int ert, const int64_t *pixels, int64_t npix,
+                  double *out, uint32_t *counts, int nthreads) {
+    if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
+    render_job J;
+    J.vol = vol; J.n = n; J.nvars = nvars; J.r_in = r_in; J.r_out = r_out;
+    J.cam = cam; J.w = w; J.h = h; J.dt = dt; J.lo = lo; J.hi = hi;
+    J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
+    J.tf_lo = tf_lo; J.tf_hi = tf_hi; J.bg = bg; J.ert = ert;
+    J.pixels = pixels; J.npix = pixels ? npix : (int64_t)w * h;
+    J.out = out; J.counts = counts; J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, render_worker, &J);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return 0;
+}
+
+int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }

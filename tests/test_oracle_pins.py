@@ -1,0 +1,562 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test ties one oracle function to a closed form, an invariant, a value
+worked out by hand, a brute-force count with library routines, or exact
+rational arithmetic, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in the oracle fails at least one of them. CPU only.
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2207_12011_gb300 import synth
+
+R_IN, R_OUT = 0.547, 1.0
+ALL_IN = (np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32))
+
+
+# ----------------------------------------------------------------------------
+# helpers (geometry in FP64, written from the pinhole-camera definition)
+# ----------------------------------------------------------------------------
+def pixel_rays64(cam: synth.Camera, w: int, h: int):
+    eye = np.array(cam.eye, np.float64)
+    F = np.array(cam.target, np.float64) - eye
+    F /= np.linalg.norm(F)
+    R = np.cross(F, np.array(cam.up, np.float64))
+    R /= np.linalg.norm(R)
+    U = np.cross(R, F)
+    th = float(cam.tan_half_vfov)
+    xs = ((2 * np.arange(w) + 1) / w - 1) * th * (w / h)
+    ys = (1 - (2 * np.arange(h) + 1) / h) * th
+    d = F[None, None, :] + xs[None, :, None] * R[None, None, :] + ys[:, None, None] * U[None, None, :]
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    return eye, d
+
+
+def shell_chord(eye, d, r_in=R_IN, r_out=R_OUT):
+    """Length of the ray inside r_in <= |p| <= r_out (camera outside r_out)."""
+    b2 = np.sum(np.cross(d, eye[None, None, :]) ** 2, axis=-1)   # squared impact parameter
+    outer = 2 * np.sqrt(np.clip(r_out ** 2 - b2, 0, None))
+    inner = 2 * np.sqrt(np.clip(r_in ** 2 - b2, 0, None))
+    return outer - inner, np.sqrt(b2)
+
+
+def const_volume(n, value=0.5, nvars=6):
+    return np.full((nvars, n, n, n), value, np.float32)
+
+
+def tf_const(rgb=(1.0, 0.5, 0.25), sigma=2.0):
+    return synth.constant_tf(rgb, sigma)
+
+
+# ----------------------------------------------------------------------------
+# (a) constant density shell: discrete and continuum closed forms
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [32, 64])
+def test_constant_shell_closed_form(n):
+    sigma, rgb = 2.0, (1.0, 0.5, 0.25)
+    tf = tf_const(rgb, sigma)
+    cam = synth.orbit_camera(30, 20, 3.0)
+    w = h = 48
+    dt = 1.0 / n
+    vol = const_volume(n)
+    img, cnt = oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, h, dt, *ALL_IN, 0,
+                             tf.rgbs, 0, 0.0, 1.0, ert=False)
+    kept = cnt[..., 1].astype(np.float64)
+    # discrete: A = 1 - exp(-sigma dt n_kept), C = c * A (premultiplied)
+    A_disc = 1 - np.exp(-sigma * dt * kept)
+    assert np.max(np.abs(img[..., 3] - A_disc)) < 1e-12
+    for c in range(3):
+        assert np.max(np.abs(img[..., c] - rgb[c] * A_disc)) < 1e-12
+    # the kept count is the number of lattice points in the shell: count it in FP64
+    eye, d = pixel_rays64(cam, w, h)
+    b = np.sum(eye[None, None, :] * d, axis=-1)
+    disc = R_OUT ** 2 - (np.sum(eye ** 2) - b * b)
+    n64 = np.zeros((h, w), np.int64)
+    for y in range(h):
+        for x in range(w):
+            if disc[y, x] <= 0:
+                continue
+            t0, t1 = -b[y, x] - math.sqrt(disc[y, x]), -b[y, x] + math.sqrt(disc[y, x])
+            ks = np.arange(int((t1 - t0) / dt) + 2)
+            tk = t0 + (ks + 0.5) * dt
+            tk = tk[tk < t1]
+            p = eye[None, :] + tk[:, None] * d[y, x][None, :]
+            r2 = np.sum(p * p, axis=1)
+            n64[y, x] = np.count_nonzero((r2 >= R_IN ** 2) & (r2 <= R_OUT ** 2))
+    diff = np.abs(n64 - cnt[..., 1].astype(np.int64))
+    assert diff.max() <= 1
+    assert np.count_nonzero(diff) <= max(2, int(0.003 * w * h))
+    # continuum: c (1 - exp(-sigma L)) within c sigma 4 dt (non-grazing rays)
+    L, bimp = shell_chord(eye, d)
+    A_cont = 1 - np.exp(-sigma * L)
+    ok = bimp < 0.97
+    assert np.max(np.abs(img[..., 3] - A_cont)[ok]) <= sigma * 4 * dt
+
+
+def test_constant_shell_converges_linearly():
+    sigma = 3.0
+    tf = tf_const((1, 1, 1), sigma)
+    cam = synth.orbit_camera(10, -15, 2.8)
+    w = h = 32
+    eye, d = pixel_rays64(cam, w, h)
+    L, bimp = shell_chord(eye, d)
+    ok = bimp < 0.95
+    errs = []
+    for n in (16, 32, 64, 128):
+        img, _ = oracle.render(const_volume(n), R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n,
+                               *ALL_IN, 0, tf.rgbs, 0, 0.0, 1.0, ert=False)
+        errs.append(np.mean(np.abs(img[..., 3] - (1 - np.exp(-sigma * L)))[ok]))
+    # error shrinks as dt halves (first order in dt)
+    assert errs[1] < errs[0] and errs[2] < errs[1] and errs[3] < errs[2]
+    assert errs[3] < 0.3 * errs[0]
+
+
+# ----------------------------------------------------------------------------
+# hand-worked 4^3 example
+# ----------------------------------------------------------------------------
+def _tiny_volume():
+    n = 4
+    vol = np.zeros((2, n, n, n), np.float32)
+    for z in range(n):
+        vol[0, z] = z          # var 0 = z index
+    vol[1] = 0.5               # var 1 constant (colour variable)
+    return vol
+
+
+def _tiny_tf():
+    t = np.zeros((256, 4), np.float32)
+    t[:, 0] = 1.0
+    t[:, 3] = np.arange(256, dtype=np.float32) / 255.0 * 8.0
+    # the colour value 0.5 on [0, 1] falls half way between entries 127 and 128
+    t[127] = (1.0, 0.0, 0.0, 3.5)
+    t[128] = (0.5, 1.0, 0.0, 4.5)
+    return t
+
+
+@pytest.mark.parametrize("lo,hi,kept,alpha", [
+    # centre ray of a camera at (0,0,3): samples at z = +-0.875, +-0.625 are in the shell and
+    # read var0 = 3.0, 2.75 (front) and 0.25, 0.0 (back); colour var = 0.5 -> TF position
+    # 127.5 -> (r, g, b, sigma) = (0.75, 0.5, 0, 4); alpha per kept sample = 1 - e^-1 and
+    # k kept samples give A = 1 - e^-k, premultiplied colour = (0.75 A, 0.5 A, 0).
+    (0.5, 2.9, 1, 0.6321205588285577),
+    (0.1, 3.0, 3, 0.950212931632136),
+    (-1.0, 5.0, 4, 0.9816843611112658),
+    (3.5, 9.0, 0, 0.0),
+])
+def test_hand_worked_center_ray(lo, hi, kept, alpha):
+    vol = _tiny_volume()
+    cam = synth.Camera((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.41421357)
+    lo_a = np.array([lo, -np.inf], np.float32)
+    hi_a = np.array([hi, np.inf], np.float32)
+    for w in (1, 3):
+        img, cnt = oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, w, 0.25, lo_a, hi_a, 1,
+                                 _tiny_tf(), 1, 0.0, 1.0, ert=False)
+        c = w // 2
+        assert cnt[c, c, 0] == 8          # t in (2, 4), dt = 0.25
+        assert cnt[c, c, 1] == kept
+        assert img[c, c, 3] == pytest.approx(alpha, abs=1e-12)
+        assert img[c, c, 0] == pytest.approx(0.75 * alpha, abs=1e-12)
+        assert img[c, c, 1] == pytest.approx(0.5 * alpha, abs=1e-12)
+        assert img[c, c, 2] == 0.0
+
+
+def test_background_is_composited_under():
+    vol = _tiny_volume()
+    cam = synth.Camera((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.41421357)
+    bg = (0.1, 0.2, 0.3, 0.5)
+    img, _ = oracle.render(vol, R_IN, R_OUT, cam.as_array(), 1, 1, 0.25,
+                           np.array([0.5, -np.inf], np.float32), np.array([2.9, np.inf], np.float32),
+                           1, _tiny_tf(), 1, 0.0, 1.0, bg=bg, ert=False)
+    a = 0.6321205588285577
+    assert img[0, 0, 0] == pytest.approx(0.75 * a + (1 - a) * 0.1, abs=1e-12)
+    assert img[0, 0, 1] == pytest.approx(0.5 * a + (1 - a) * 0.2, abs=1e-12)
+    assert img[0, 0, 3] == pytest.approx(a + (1 - a) * 0.5, abs=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# (b) (c) (d): brush invariants on synthetic shell data
+# ----------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def shell32():
+    vol = synth.make_shell_volume(32)
+    return vol.numpy()
+
+
+def _render(vol, brush_lo, brush_hi, mask, ert=True, w=40, h=32, tf=None, bg=(0, 0, 0, 0)):
+    n = vol.shape[1]
+    if tf is None:
+        tf = synth.make_tf(torch.from_numpy(vol), "T_anom")
+    cam = synth.orbit_camera(30, 20, 3.0)
+    return oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush_lo, brush_hi,
+                         mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, bg=bg, ert=ert)
+
+
+def test_all_excluding_brush_gives_background(shell32):
+    lo = np.full(6, -np.inf, np.float32)
+    hi = np.full(6, np.inf, np.float32)
+    lo[0], hi[0] = 1.0, 0.0                      # lo > hi: empty brush
+    bg = (0.25, 0.5, 0.125, 0.75)
+    img, cnt = _render(shell32, lo, hi, 1, bg=bg)
+    assert np.all(cnt[..., 1] == 0)
+    assert np.all(img == np.array(bg)[None, None, :])
+    bmin, bmax = oracle.brick_minmax(shell32)
+    act, skp = oracle.classify(bmin, bmax, 32, R_IN, R_OUT, lo, hi, 1)
+    assert act.sum() == 0 and skp.all()
+
+
+def test_all_including_brush_equals_unbrushed(shell32):
+    img0, cnt0 = _render(shell32, *ALL_IN, 0)
+    img1, cnt1 = _render(shell32, *ALL_IN, 0b111111)
+    assert np.array_equal(img0, img1) and np.array_equal(cnt0, cnt1)
+    assert cnt0[..., 1].sum() > 0
+
+
+def test_narrowing_brush_never_raises_opacity(shell32):
+    rng = np.random.default_rng(5)
+    vol_t = torch.from_numpy(shell32)
+    for trial in range(4):
+        base = synth.brush_from_quantiles(vol_t, synth.jittered_spec("c3", 100 + trial, 0.05))
+        narrow = base.copy()
+        for v in range(6):
+            if (base.active_mask >> v) & 1:
+                lo, hi = float(base.lo[v]), float(base.hi[v])
+                span = (hi - lo) if np.isfinite(hi - lo) else 1.0
+                narrow.lo[v] = np.float32(lo + rng.uniform(0, 0.2) * abs(span)) if np.isfinite(lo) else lo
+                narrow.hi[v] = np.float32(hi - rng.uniform(0, 0.2) * abs(span)) if np.isfinite(hi) else hi
+        wide_img, wide_cnt = _render(shell32, base.lo, base.hi, base.active_mask, ert=False)
+        nar_img, nar_cnt = _render(shell32, narrow.lo, narrow.hi, narrow.active_mask, ert=False)
+        assert np.all(nar_img[..., 3] <= wide_img[..., 3])          # exact without ERT
+        assert np.all(nar_cnt[..., 1] <= wide_cnt[..., 1])
+        wi, _ = _render(shell32, base.lo, base.hi, base.active_mask, ert=True)
+        ni, _ = _render(shell32, narrow.lo, narrow.hi, narrow.active_mask, ert=True)
+        assert np.all(ni[..., 3] <= wi[..., 3] + 2.0 ** -12 + 1e-6)
+
+
+def test_ert_changes_result_by_at_most_threshold(shell32):
+    tf = synth.make_tf(torch.from_numpy(shell32), "T_anom", sigma_max=400.0)   # opaque, so ERT fires
+    on, c_on = _render(shell32, *ALL_IN, 0, ert=True, tf=tf)
+    off, c_off = _render(shell32, *ALL_IN, 0, ert=False, tf=tf)
+    assert np.max(np.abs(on - off)) <= 2.0 ** -12 + 1e-12
+    fired = c_on[..., 0] < c_off[..., 0]
+    assert fired.sum() > 0
+    assert np.all(on[..., 3][fired] >= 1 - 2.0 ** -12)
+
+
+# ----------------------------------------------------------------------------
+# trilinear interpolation: affine fields are reproduced; slab brush -> analytic chord
+# ----------------------------------------------------------------------------
+def test_slab_brush_on_affine_field_matches_chord():
+    n = 64
+    c = (np.arange(n) + 0.5) * 2 / n - 1
+    vol = np.zeros((2, n, n, n), np.float32)
+    vol[0] = c[None, None, :]                 # var 0 = x coordinate of the cell centre
+    vol[1] = 0.5
+    x0, x1 = -0.3, 0.45
+    sigma = 2.5
+    tf = tf_const((1, 1, 1), sigma)
+    cam = synth.orbit_camera(70, 25, 3.0)
+    w = h = 40
+    img, cnt = oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n,
+                             np.array([x0, -np.inf], np.float32), np.array([x1, np.inf], np.float32),
+                             1, tf.rgbs, 1, 0.0, 1.0, ert=False)
+    eye, d = pixel_rays64(cam, w, h)
+    # analytic length of the ray inside shell AND slab x0 <= x <= x1
+    L = np.zeros((h, w))
+    for y in range(h):
+        for x in range(w):
+            dd = d[y, x]
+            b = eye @ dd
+            disc = 1 - (eye @ eye - b * b)
+            if disc <= 0:
+                continue
+            ta, tb = -b - math.sqrt(disc), -b + math.sqrt(disc)
+            tx = sorted([(x0 - eye[0]) / dd[0], (x1 - eye[0]) / dd[0]])
+            segs = [(max(ta, tx[0]), min(tb, tx[1]))]
+            di = R_IN ** 2 - (eye @ eye - b * b)
+            if di > 0:
+                ca, cb = -b - math.sqrt(di), -b + math.sqrt(di)
+                s0, s1 = segs[0]
+                segs = [(s0, min(s1, ca)), (max(s0, cb), s1)]
+            L[y, x] = sum(max(0.0, s1 - s0) for s0, s1 in segs)
+    A = 1 - np.exp(-sigma * L)
+    _, bimp = shell_chord(eye, d)
+    ok = bimp < 0.95
+    assert np.max(np.abs(img[..., 3] - A)[ok]) <= sigma * 6.0 / n
+    assert np.mean(np.abs(img[..., 3] - A)[ok]) <= sigma * 1.0 / n
+
+
+# ----------------------------------------------------------------------------
+# camera / geometry: cubic symmetry of the cell-centred grid
+# ----------------------------------------------------------------------------
+def test_radial_field_is_symmetric_under_quarter_turns():
+    n = 48
+    c = (np.arange(n) + 0.5) * 2 / n - 1
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z).astype(np.float32)
+    vol = np.stack([r, r])
+    t = np.zeros((256, 4), np.float32)
+    s = np.arange(256) / 255.0
+    t[:, 0] = s
+    t[:, 1] = 1 - s
+    t[:, 2] = 0.5
+    t[:, 3] = 30.0 * np.sin(np.pi * s) ** 4          # zero at both shell boundaries
+    imgs = []
+    for az in (0, 90, 180, 270):
+        cam = synth.orbit_camera(az, 30, 3.0)
+        img, _ = oracle.render(vol, R_IN, R_OUT, cam.as_array(), 32, 32, 1.0 / n, *ALL_IN, 0,
+                               t, 1, R_IN, R_OUT, ert=True)
+        imgs.append(img)
+    for img in imgs[1:]:
+        assert np.max(np.abs(img - imgs[0])) < 2e-3
+        assert np.mean(np.abs(img - imgs[0])) < 1e-5
+
+
+# ----------------------------------------------------------------------------
+# (e) histograms
+# ----------------------------------------------------------------------------
+def _cells_in_shell_exact(n, r_in, r_out):
+    """In-shell cell mask by exact rational comparison of |p|^2 with r^2."""
+    ri = Fraction(float(np.float32(r_in)))
+    ro = Fraction(float(np.float32(r_out)))
+    k = 2 * np.arange(n) + 1 - n
+    s = (k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    lo = ri * ri * n * n
+    hi = ro * ro * n * n
+    ins = np.zeros(s.shape, bool)
+    for val in np.unique(s):
+        ins[s == val] = (Fraction(int(val)) >= lo) and (Fraction(int(val)) <= hi)
+    return ins
+
+
+@pytest.mark.parametrize("n", [8, 16, 33, 64])
+def test_shell_bounds_match_exact_rational(n):
+    s_in, s_out = oracle.shell_bounds(n, R_IN, R_OUT)
+    k = 2 * np.arange(n) + 1 - n
+    s = (k[:, None, None] ** 2 + k[None, :, None] ** 2 + k[None, None, :] ** 2)
+    ins = (s >= s_in) & (s <= s_out)
+    assert np.array_equal(ins, _cells_in_shell_exact(n, R_IN, R_OUT))
+
+
+def _numpy_hist(vol, lo, hi, mask, order, edges, use_brush=True):
+    n = vol.shape[1]
+    ins = _cells_in_shell_exact(n, R_IN, R_OUT)
+    keep = ins.copy()
+    if use_brush:
+        for v in range(vol.shape[0]):
+            if (mask >> v) & 1:
+                keep &= (vol[v] >= lo[v]) & (vol[v] <= hi[v])
+    bins = edges.shape[1] - 1
+    b = [np.searchsorted(edges[a, 1:bins], vol[order[a]][keep], side="right") for a in range(len(order))]
+    H = np.zeros((len(order) - 1, bins, bins), np.int64)
+    for p in range(len(order) - 1):
+        np.add.at(H[p], (b[p], b[p + 1]), 1)
+    return H, int(keep.sum())
+
+
+@pytest.mark.parametrize("n,brush", [(8, "c1"), (16, "c2"), (16, "c3"), (24, None)])
+def test_histogram_matches_brute_force(n, brush):
+    vol_t = synth.make_shell_volume(n, seed=11)
+    vol = vol_t.numpy()
+    order = (0, 3, 1, 2, 5, 4)
+    edges = synth.make_edges(vol_t, order, bins=256)
+    if brush is None:
+        lo, hi, mask, use = *ALL_IN, 0, False
+    else:
+        b = synth.make_brush(vol_t, brush)
+        lo, hi, mask, use = b.lo, b.hi, b.active_mask, True
+    H, cells = oracle.histogram(vol, R_IN, R_OUT, lo, hi, mask, order, edges, use_brush=use)
+    Hn, cn = _numpy_hist(vol, lo, hi, mask, order, edges, use)
+    assert cells == cn
+    assert np.array_equal(H.astype(np.int64), Hn)
+    # totals equal the in-brush cell count; shared-axis marginals agree exactly
+    assert all(int(H[p].sum()) == cells for p in range(H.shape[0]))
+    for p in range(1, H.shape[0]):
+        assert np.array_equal(H[p].sum(axis=1), H[p - 1].sum(axis=0))
+
+
+def test_histogram_edge_values_and_clamping():
+    n = 8
+    vol = np.zeros((2, n, n, n), np.float32)
+    ins = _cells_in_shell_exact(n, R_IN, R_OUT)
+    edges = np.array([np.linspace(0, 4, 5, dtype=np.float32)] * 2)   # 4 bins: [0,1,2,3,4]
+    vals = np.array([-5.0, 0.0, 0.999, 1.0, 2.5, 3.0, 4.0, 99.0, np.nan], np.float32)
+    expect = [0, 0, 0, 1, 2, 3, 3, 3, 0]                # v >= e_k counted over interior edges
+    idx = np.argwhere(ins)
+    assert len(idx) >= len(vals)
+    for j, v in enumerate(vals):
+        z, y, x = idx[j]
+        vol[0, z, y, x] = v
+        vol[1, z, y, x] = v
+    H, cells = oracle.histogram(vol, R_IN, R_OUT, *ALL_IN, 0, (0, 1), edges, use_brush=False)
+    diag = np.zeros(4, np.int64)
+    for e in expect:
+        diag[e] += 1
+    diag[0] += int(ins.sum()) - len(vals)                # the remaining in-shell cells hold 0.0
+    assert np.array_equal(np.diag(H[0]).astype(np.int64), diag)
+    assert int(H[0].sum()) == int(ins.sum()) == cells
+
+
+# ----------------------------------------------------------------------------
+# bricks: min/max by brute force, classification on fields with a known layout
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [16, 20, 32])
+def test_brick_minmax_brute_force(n):
+    vol = synth.make_shell_volume(n, seed=3).numpy()
+    vol[2, 3, 5, 7] = np.nan                              # NaN values are ignored
+    mn, mx = oracle.brick_minmax(vol)
+    nb = (n + 7) // 8
+    for bz in range(nb):
+        for by in range(nb):
+            for bx in range(nb):
+                sl = vol[:, bz * 8:min(bz * 8 + 9, n), by * 8:min(by * 8 + 9, n), bx * 8:min(bx * 8 + 9, n)]
+                assert np.array_equal(mn[bz, by, bx], np.nanmin(sl.reshape(vol.shape[0], -1), axis=1))
+                assert np.array_equal(mx[bz, by, bx], np.nanmax(sl.reshape(vol.shape[0], -1), axis=1))
+
+
+def test_classify_affine_field_slabs():
+    n = 32
+    vol = np.zeros((1, n, n, n), np.float32)
+    vol[0] = np.arange(n, dtype=np.float32)[None, None, :]   # value = x index
+    mn, mx = oracle.brick_minmax(vol)
+    assert np.array_equal(mn[0, 0, :, 0], [0, 8, 16, 24]) and np.array_equal(mx[0, 0, :, 0], [8, 16, 24, 31])
+    nob = np.ones(1, np.float32)
+    # shell only (no restricted variable)
+    act0, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, -np.inf * nob, np.inf * nob, 0)
+    for lo, hi, cols in [(10.5, 12.0, {1}), (16.0, 16.0, {1, 2}), (8.0000005, 15.9, {0, 1}), (8.00002, 15.9, {1}),
+                         (31.5, 40.0, set()), (-3.0, -0.5, set()), (-3.0, 0.0, {0})]:
+        # brick 0 holds values 0..8: within the margin 8 * 2^-20 of lo = 8.0000005 it stays active
+        act, skp = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([lo]), np.float32([hi]), 1)
+        want = act0.copy()
+        for bx in range(4):
+            if bx not in cols:
+                want[:, :, bx] = 0
+        assert np.array_equal(act, want), (lo, hi)
+        # skippable: inactive and every existing neighbour inactive
+        pad = np.pad(act, 1)
+        nbr = np.zeros_like(act)
+        for dz in range(3):
+            for dy in range(3):
+                for dx in range(3):
+                    nbr |= pad[dz:dz + 4, dy:dy + 4, dx:dx + 4]
+        assert np.array_equal(skp, (nbr == 0).astype(np.uint8))
+
+
+def test_classify_shell_bracket():
+    for n in (32, 64):
+        nb = n // 8
+        vol = np.zeros((1, n, n, n), np.float32)
+        mn, mx = oracle.brick_minmax(vol)
+        act, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([-1]), np.float32([1]), 0)
+        ins = _cells_in_shell_exact(n, R_IN, R_OUT)
+        # necessary: every brick holding an in-shell cell centre is active
+        holds = ins.reshape(nb, 8, nb, 8, nb, 8).any(axis=(1, 3, 5))
+        assert np.all(act[holds] == 1)
+        # sufficient: a brick whose sample box lies clearly outside the shell is inactive
+        c = lambda b: ((8 * b + 0.5) * 2 / n - 1, (8 * b + 8.5) * 2 / n - 1)
+        for bz in range(nb):
+            for by in range(nb):
+                for bx in range(nb):
+                    boxes = [c(b) for b in (bx, by, bz)]
+                    boxes = [(-2 if b == 0 else l, 2 if b == nb - 1 else h)
+                             for (l, h), b in zip(boxes, (bx, by, bz))]
+                    near = math.sqrt(sum(0 if l <= 0 <= h else min(abs(l), abs(h)) ** 2 for l, h in boxes))
+                    far = math.sqrt(sum(max(abs(l), abs(h)) ** 2 for l, h in boxes))
+                    if near > R_OUT + 0.01 or far < R_IN - 0.01:
+                        assert act[bz, by, bx] == 0
+
+
+# ----------------------------------------------------------------------------
+# the classification margin covers FP32 trilinear rounding (exact rationals)
+# ----------------------------------------------------------------------------
+def _round_f32(x: Fraction) -> float:
+    """Round a rational to the nearest float32, ties to even (IEEE 754)."""
+    if x == 0:
+        return 0.0
+    sign = -1.0 if x < 0 else 1.0
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    while Fraction(2) ** e > a:
+        e -= 1
+    while Fraction(2) ** (e + 1) <= a:
+        e += 1
+    e = max(e, -126)
+    q = Fraction(2) ** (e - 23)
+    m = a / q
+    fl = m.numerator // m.denominator
+    rem = m - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
+        fl += 1
+    return sign * float(fl * q)
+
+
+def _lerp_exact(a, b, f):
+    a, b, f = Fraction(float(a)), Fraction(float(b)), Fraction(float(f))
+    d = _round_f32(b - a)
+    return _round_f32(f * Fraction(d) + a)
+
+
+def test_brush_margin_covers_fp32_trilinear_rounding():
+    rng = np.random.default_rng(2207)
+    worst = 0.0
+    for case in range(600):
+        kind = case % 4
+        if kind == 0:
+            c = rng.uniform(-1, 1, 8)
+        elif kind == 1:
+            c = rng.choice([-1, 1], 8) * 10.0 ** rng.uniform(-8, 2, 8)
+        elif kind == 2:
+            c = 1.0 + rng.uniform(-1e-6, 1e-6, 8)
+        else:
+            c = rng.uniform(-1, 1, 8) * 1e-38
+        c = c.astype(np.float32)
+        f = rng.uniform(0, 1, 3).astype(np.float32)
+        if case % 7 == 0:
+            f = np.float32(rng.choice([0.0, 1.0], 3))
+        cc = c.reshape(2, 2, 2)   # [dz][dy][dx]
+        x00 = _lerp_exact(cc[0, 0, 0], cc[0, 0, 1], f[0])
+        x10 = _lerp_exact(cc[0, 1, 0], cc[0, 1, 1], f[0])
+        x01 = _lerp_exact(cc[1, 0, 0], cc[1, 0, 1], f[0])
+        x11 = _lerp_exact(cc[1, 1, 0], cc[1, 1, 1], f[0])
+        y0 = _lerp_exact(x00, x10, f[1])
+        y1 = _lerp_exact(x01, x11, f[1])
+        v = _lerp_exact(y0, y1, f[2])
+        mn, mx = np.float32(c.min()), np.float32(c.max())
+        m = max(abs(float(mn)), abs(float(mx)))
+        d = _round_f32(Fraction(float(m)) * Fraction(2) ** -20 + Fraction(2) ** -120)
+        up = np.float32(mx) + np.float32(d)
+        dn = np.float32(mn) - np.float32(d)
+        assert dn <= v <= up
+        if m > 0:
+            worst = max(worst, (v - float(mx)) / m, (float(mn) - v) / m)
+    assert worst < 2.0 ** -20
+
+
+# ----------------------------------------------------------------------------
+# level of detail
+# ----------------------------------------------------------------------------
+def test_lod_mean_brute_force():
+    rng = np.random.default_rng(1)
+    vol = rng.integers(-50, 50, size=(3, 8, 8, 8)).astype(np.float32)   # integer sums are exact
+    got = oracle.lod_mean(vol)
+    want = vol.reshape(3, 4, 2, 4, 2, 4, 2).astype(np.float64).mean(axis=(2, 4, 6))
+    assert np.array_equal(got.astype(np.float64), want)
+    vol = rng.uniform(-1, 1, size=(2, 16, 16, 16)).astype(np.float32)
+    got = oracle.lod_mean(vol)
+    want = vol.reshape(2, 8, 2, 8, 2, 8, 2).astype(np.float64).mean(axis=(2, 4, 6))
+    assert np.max(np.abs(got - want)) < 4e-7
+    # odd size: the last coarse cell repeats the clamped fine index
+    vol = rng.integers(0, 9, size=(1, 5, 5, 5)).astype(np.float32)
+    got = oracle.lod_mean(vol)
+    assert got.shape == (1, 3, 3, 3)
+    pad = np.concatenate([vol, vol[:, -1:]], axis=1)
+    pad = np.concatenate([pad, pad[:, :, -1:]], axis=2)
+    pad = np.concatenate([pad, pad[:, :, :, -1:]], axis=3)
+    want = pad.reshape(1, 3, 2, 3, 2, 3, 2).astype(np.float64).mean(axis=(2, 4, 6))
+    assert np.array_equal(got.astype(np.float64), want)
