@@ -1,0 +1,243 @@
+/*
+ * raypc.h -- C ABI of the GB300 (sm_103a) library for brushed multivariate
+ * direct volume rendering with linked parallel-coordinates histograms
+ * (Fritsch et al., "RayPC: Interactive Ray Tracing Meets Parallel
+ * Coordinates", arXiv 2207.12011).
+ *
+ * The method (Section 2, "Approach"; Section 2.2, "Rendering"): rays are
+ * marched front to back through a multi-variable volume; at every sample all
+ * variables restricted in the parallel-coordinates plot are queried, and the
+ * sample is discarded when any of them lies outside its bounds (brushing
+ * and linking). Kept samples are coloured by a 1D transfer function and
+ * composited. The restrictions do not modify the data, so no acceleration
+ * structure is rebuilt when they change: per-brick min/max are built once
+ * and a brush edit only re-classifies bricks. The parallel-coordinates plot
+ * (Section 2.1, Fig. 2) is fed by adjacent-axis density histograms of the
+ * selected cells.
+ *
+ * Conventions used by every entry point:
+ *   - A volume is a cubic grid of n^3 cells with nvars (1..8) variables,
+ *     cell-centred over the world cube [-1,1]^3: value index i sits at
+ *     p = -1 + (i + 1/2) * 2/n. The spherical shell r_in <= |p| <= r_out is
+ *     the domain; everything outside it is empty.
+ *   - Caller buffers are plain pointers. "_dev" buffers are device memory of
+ *     the context's GPU; other pointers are host memory. The library copies
+ *     what it keeps (volume data, brush, transfer function); it never keeps
+ *     a pointer to a caller buffer after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *     enqueued asynchronously on it; errors found by the device surface at
+ *     the caller's next synchronisation. Host arguments are consumed before
+ *     the call returns.
+ *   - Every function returns RAYPC_OK (0) or an error code and never aborts
+ *     the process. raypc_last_error() gives a message for the calling thread.
+ *   - A context is bound to one device. Calls on one context are serialised
+ *     by an internal lock; the library sets and restores the current device.
+ */
+#ifndef RAYPC_H
+#define RAYPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int raypc_status;
+#define RAYPC_OK 0
+#define RAYPC_ERR_INVALID_ARG 1   /* bad pointer, size, id or value            */
+#define RAYPC_ERR_OOM 2           /* device allocation failed or over budget   */
+#define RAYPC_ERR_CUDA 3          /* a CUDA runtime call failed                */
+#define RAYPC_ERR_TIMEOUT 4       /* a bounded wait gave up                    */
+#define RAYPC_ERR_BUSY 5          /* resource in use                           */
+#define RAYPC_ERR_NOT_FOUND 6     /* unknown volume / level / request          */
+#define RAYPC_ERR_UNSUPPORTED 7   /* valid but not implemented (e.g. non-cubic) */
+
+/* Element types of volume data. */
+#define RAYPC_F32 0
+#define RAYPC_F16 1               /* IEEE binary16; FP32 -> FP16 rounds to nearest even */
+
+#define RAYPC_MAX_VARS 8
+#define RAYPC_BRICK 8             /* brick edge in cells                       */
+#define RAYPC_MAX_LOD 2           /* coarser levels beyond the full level 0    */
+#define RAYPC_TF_ENTRIES 256
+
+/* Indices into the optional device statistics array of raypc_render
+ * (RAYPC_NSTATS unsigned 64-bit counters that the kernel ADDS to). */
+#define RAYPC_STAT_MARCHED 0      /* lattice samples from entry to termination  */
+#define RAYPC_STAT_EVALUATED 1    /* samples whose field values were fetched    */
+#define RAYPC_STAT_KEPT 2         /* samples in shell and in brush (composited) */
+#define RAYPC_STAT_SKIPPED 3      /* lattice samples jumped by brick skipping   */
+#define RAYPC_STAT_RAYS 4         /* rays that hit the outer sphere             */
+#define RAYPC_STAT_ERT 5          /* rays ended by early ray termination        */
+#define RAYPC_NSTATS 8
+
+typedef struct raypc_ctx raypc_ctx;
+
+/* Pinhole camera. The view direction is normalize(target - eye); right =
+ * normalize(cross(view, up)); true up = cross(right, view). Pixel (x, y),
+ * y = 0 at the top row, looks along view + sx*right + sy*trueup with
+ * sx = ((2x+1)/w - 1) * tan_half_vfov * w/h and sy = (1 - (2y+1)/h) *
+ * tan_half_vfov (pixel centres). tan_half_vfov = tan(vertical fov / 2). */
+typedef struct raypc_camera {
+    float eye[3];
+    float target[3];
+    float up[3];
+    float tan_half_vfov;
+} raypc_camera;
+
+/* Options of one render. Zero-initialised = defaults except `ert`, which the
+ * caller sets explicitly. */
+typedef struct raypc_render_opts {
+    float step;          /* world distance between lattice samples; <= 0: half a
+                            voxel of the rendered level, i.e. 1/n_level         */
+    int ert;             /* nonzero: stop a ray once its opacity A >= 1 - 2^-12 */
+    int no_skip;         /* nonzero: disable brick-level empty-space skipping   */
+    float bg[4];         /* premultiplied background RGBA composited under     */
+    uint32_t *counts_dev;/* optional [h][w][2] uint32: per pixel, lattice
+                            samples marched and samples kept (debug/testing)    */
+} raypc_render_opts;
+
+/* ---------------------------------------------------------------------- */
+/* Errors and contexts                                                    */
+/* ---------------------------------------------------------------------- */
+
+/* Message of the last failing call on this thread ("" if none). The string
+ * is owned by the library and valid until the thread's next call. */
+const char *raypc_last_error(void);
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes caps the device
+ * memory the context may hold for volumes, levels and bricks (0 = no cap);
+ * a load that would exceed it fails with RAYPC_ERR_OOM and changes nothing. */
+raypc_status raypc_create(raypc_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Free every volume and the context. NULL is accepted. */
+raypc_status raypc_destroy(raypc_ctx *ctx);
+
+/* Bytes of device memory the context currently holds. */
+raypc_status raypc_memory_used(raypc_ctx *ctx, size_t *out_bytes);
+
+/* ---------------------------------------------------------------------- */
+/* Volumes (Section 2.1: data preprocessing)                              */
+/* ---------------------------------------------------------------------- */
+
+/* Copy a volume into the library. `src` holds nvars planes of nz*ny*nx values
+ * of type src_dtype, x fastest: src[((v*nz + z)*ny + y)*nx + x]; it is device
+ * memory if src_is_device, else host memory. The stored copy has element type
+ * store_dtype (FP16 storage rounds to nearest even; FP16 -> FP32 is exact)
+ * in the library's interleaved layout. Only cubic grids (nx == ny == nz >= 2)
+ * are supported (RAYPC_ERR_UNSUPPORTED otherwise). 0 <= r_in < r_out.
+ * Writes the new volume id to *out_vol. Allocates; the stored copy lives
+ * until raypc_free_volume or raypc_destroy. */
+raypc_status raypc_load_volume(raypc_ctx *ctx, const void *src, int src_is_device,
+                               int src_dtype, int store_dtype, int nx, int ny, int nz,
+                               int nvars, float r_in, float r_out, void *stream,
+                               int *out_vol);
+
+raypc_status raypc_free_volume(raypc_ctx *ctx, int vol);
+
+/* Level of detail (Section 2.1: an octree-like pyramid with coarser levels of
+ * 1/8 of the cells each) and brick min/max (Section 2.2: acceleration data
+ * that a brush change does not rebuild). Builds n_lod (0..RAYPC_MAX_LOD)
+ * coarser levels -- coarse cell = FP32 mean of its 2x2x2 fine cells, fine
+ * indices clamped at the edge, summed as ((c000+c100)+(c010+c110)) +
+ * ((c001+c101)+(c011+c111)) then times 1/8, stored in the volume's dtype --
+ * and, for every level, per 8^3 brick and variable, the min and max of the
+ * stored values at the brick's vertices 8b..min(8b+8, n-1) (NaN ignored).
+ * brick_dim must be RAYPC_BRICK. Calling it again rebuilds. */
+raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lod,
+                                void *stream);
+
+/* Set the brush box (Section 2: "upper and lower bounds for each variable";
+ * Section 2.2: a sample whose restricted values violate them is discarded).
+ * lo, hi: host arrays of nvars floats; variable v is restricted iff bit v of
+ * active_mask is set; a sample or cell passes iff lo[v] <= value <= hi[v]
+ * for every restricted v (inclusive; NaN values fail; lo > hi is a legal
+ * empty brush; infinite bounds are open sides; NaN bounds are rejected).
+ * Re-classifies the bricks of every built level on `stream`: a brick is
+ * active iff its sample box (widened by 2^-10) meets the shell and, for every
+ * restricted v, max_v + d >= lo[v] and min_v - d <= hi[v] with
+ * d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
+ * rounding); skippable iff it and its 26 neighbours are inactive. Requires
+ * raypc_build_bricks. */
+raypc_status raypc_set_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
+                             uint32_t active_mask, void *stream);
+
+/* Set the 1D transfer function (Section 3 and Fig. 4: colour by one chosen
+ * variable). rgbs: host array of 256 x (r, g, b, sigma); sigma is the
+ * extinction per world unit. The colour variable's value v maps to the
+ * position s = clamp((v - v_lo) / (v_hi - v_lo) * 255, 0, 255) and the entry
+ * is interpolated linearly between floor(s) and floor(s)+1. v_lo < v_hi. */
+raypc_status raypc_set_tf(raypc_ctx *ctx, int vol, const float *rgbs, int color_var,
+                          float v_lo, float v_hi, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Rendering (Section 2.2)                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Render level `lod` of a volume into out_rgba_dev ([h][w][4] float32,
+ * premultiplied RGBA, 16-byte aligned, caller-owned). Per pixel the ray enters
+ * the sphere r_out at t0 (or starts at the eye when inside) and leaves at t1;
+ * lattice samples sit at t_k = t0 + (k + 1/2) * step for t_k < t1. A sample is
+ * kept iff r_in^2 <= |p|^2 <= r_out^2 and every restricted variable's FP32
+ * trilinear value (clamped cell-centred interpolation, lerps along x, then y,
+ * then z, each as fma(f, b - a, a)) lies in the brush. Kept samples take
+ * (r, g, b, sigma) from the transfer function, alpha = 1 - exp(-sigma * step),
+ * and composite front to back: C += (1 - A) alpha rgb, A += (1 - A) alpha.
+ * The integer decisions use correctly rounded FP32 operations in one fixed
+ * order, so they do not depend on skipping, tiling or launch shape. Brick
+ * skipping never changes the image. Requires set_brush and set_tf.
+ * stats_dev: optional RAYPC_NSTATS uint64 device counters the kernel adds to.
+ * opts may be NULL only if the defaults with ert = 1 are wanted. */
+raypc_status raypc_render(raypc_ctx *ctx, int vol, int lod, const raypc_camera *cam,
+                          int w, int h, const raypc_render_opts *opts,
+                          float *out_rgba_dev, unsigned long long *stats_dev, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Parallel-coordinates histograms (Section 2.1 PC data; Fig. 2)            */
+/* ---------------------------------------------------------------------- */
+
+/* Density histograms of adjacent parallel-coordinates axes. axis_order: host
+ * array of naxes (2..8) variable indices; edges: host array of naxes rows of
+ * bins+1 floats (non-decreasing, no NaN); bins in 2..1024. A cell counts iff
+ * its centre is in the shell -- S_in <= sum_a (2 i_a + 1 - n)^2 <= S_out with
+ * S_in = ceil((r_in n)^2), S_out = floor((r_out n)^2) in double -- and, when
+ * use_brush is nonzero, its stored values pass the brush. Its bin on axis a is
+ * the number of interior edges e_1..e_{bins-1} of row a that are <= its value.
+ * out_counts_dev ([naxes-1][bins][bins] uint32, caller-owned) is zeroed and
+ * filled: H[p][bin_p][bin_{p+1}] counts cells. Counts are exact integers. */
+raypc_status raypc_pc_histogram(raypc_ctx *ctx, int vol, int lod, const int *axis_order,
+                                int naxes, int bins, const float *edges, int use_brush,
+                                uint32_t *out_counts_dev, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Inspection (testing and tools)                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Geometry of a level: cube edge n, variables, storage dtype and bricks per axis. */
+raypc_status raypc_volume_info(raypc_ctx *ctx, int vol, int lod, int *out_n, int *out_nvars,
+                               int *out_dtype, int *out_bricks_per_axis);
+
+/* Copy a level back in the planar layout of raypc_load_volume and in the
+ * storage dtype: out_dev holds nvars * n^3 elements. */
+raypc_status raypc_export_volume(raypc_ctx *ctx, int vol, int lod, void *out_dev, void *stream);
+
+/* Copy a level's brick min/max: two [nb][nb][nb][nvars] float32 device arrays
+ * (brick (bx,by,bz) at index (bz*nb + by)*nb + bx). */
+raypc_status raypc_get_bricks(raypc_ctx *ctx, int vol, int lod, float *out_min_dev,
+                              float *out_max_dev, void *stream);
+
+/* Copy a level's classification under the current brush. active_bits_dev and
+ * skippable_bits_dev receive ceil(nb^3 / 32) uint32 words (bit b%32 of word
+ * b/32 for brick b); active_list_dev (optional, nb^3 uint32) receives the ids
+ * of the active bricks in increasing order and n_active_dev (optional, one
+ * uint32) their number. */
+raypc_status raypc_get_skip_list(raypc_ctx *ctx, int vol, int lod, uint32_t *active_bits_dev,
+                                 uint32_t *skippable_bits_dev, uint32_t *active_list_dev,
+                                 uint32_t *n_active_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAYPC_H */

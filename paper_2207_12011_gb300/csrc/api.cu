@@ -1,0 +1,562 @@
+// Host runtime behind the C ABI declared in include/raypc.h: contexts,
+// resident volumes with their levels of detail, brick min/max and brush
+// classification, transfer functions, and the render / histogram entry
+// points. Every entry point validates its arguments, enqueues its work on
+// the caller's stream and reports failures as status codes with a
+// thread-local message; nothing aborts the process.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/raypc.h"
+#include "common.cuh"
+
+using namespace raypc;
+
+namespace {
+
+thread_local std::string g_err;
+
+raypc_status fail(raypc_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+raypc_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(RAYPC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(RAYPC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return;
+        ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct Level {
+    int n = 0, nb = 0;
+    void* data = nullptr;
+    size_t data_bytes = 0;
+    float* bmin = nullptr;
+    float* bmax = nullptr;
+    uint32_t* active = nullptr;
+    uint32_t* skippable = nullptr;
+    uint32_t* list = nullptr;
+    uint32_t* n_active = nullptr;
+    unsigned* pass_count = nullptr;
+    bool bricks = false;
+    bool classified = false;
+    size_t nbricks() const { return (size_t)nb * nb * nb; }
+    size_t nwords() const { return (nbricks() + 31) / 32; }
+};
+
+struct Volume {
+    int nvars = 0, vp = 0, dtype = 0;
+    float r_in = 0.f, r_out = 1.f;
+    int nlev = 0;             // built levels (1 + coarser)
+    Level lv[1 + RAYPC_MAX_LOD];
+    bool brush_set = false;
+    BrushArgs brush{};
+    float4* tf = nullptr;
+    bool tf_set = false;
+    int color_var = 0;
+    float tf_lo = 0.f, tf_hi = 1.f;
+    size_t bytes = 0;
+};
+
+size_t elem_size(int dtype) { return dtype == RAYPC_F16 ? 2 : 4; }
+
+}  // namespace
+
+struct raypc_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    std::mutex mu;
+    std::map<int, Volume*> vols;
+    int next_id = 1;
+
+    // Device allocation charged against the budget.
+    raypc_status alloc(void** p, size_t bytes, size_t* charged) {
+        if (budget && used + bytes > budget)
+            return fail(RAYPC_ERR_OOM, "HBM budget exceeded: %zu used + %zu requested > %zu", used, bytes, budget);
+        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        used += bytes;
+        *charged += bytes;
+        return RAYPC_OK;
+    }
+};
+
+namespace {
+
+void free_level(Level& L) {
+    void* ptrs[] = {L.data, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    L = Level{};
+}
+
+void free_bricks(Level& L) {
+    void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    L.bmin = L.bmax = nullptr;
+    L.active = L.skippable = L.list = L.n_active = nullptr;
+    L.pass_count = nullptr;
+    L.bricks = L.classified = false;
+}
+
+void free_volume(raypc_ctx* ctx, Volume* V) {
+    for (auto& L : V->lv) free_level(L);
+    if (V->tf) cudaFree(V->tf);
+    ctx->used -= V->bytes < ctx->used ? V->bytes : ctx->used;
+    delete V;
+}
+
+raypc_status get_volume(raypc_ctx* ctx, int vol, Volume** out) {
+    auto it = ctx->vols.find(vol);
+    if (it == ctx->vols.end()) return fail(RAYPC_ERR_NOT_FOUND, "unknown volume id %d", vol);
+    *out = it->second;
+    return RAYPC_OK;
+}
+
+raypc_status get_level(Volume* V, int lod, Level** out) {
+    if (lod < 0 || lod >= V->nlev) return fail(RAYPC_ERR_NOT_FOUND, "level %d not built (have %d)", lod, V->nlev);
+    *out = &V->lv[lod];
+    return RAYPC_OK;
+}
+
+raypc_status classify_level(Volume* V, Level& L, cudaStream_t s) {
+    CK(launch_classify(L.bmin, L.bmax, L.n, V->nvars, V->r_in, V->r_out, V->brush, L.active,
+                       L.skippable, L.list, L.n_active, L.pass_count, s),
+       "classify kernels");
+    L.classified = true;
+    return RAYPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* raypc_last_error(void) { return g_err.c_str(); }
+
+raypc_status raypc_create(raypc_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return fail(RAYPC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(RAYPC_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
+    raypc_ctx* c = new raypc_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    g_err.clear();
+    return RAYPC_OK;
+}
+
+raypc_status raypc_destroy(raypc_ctx* ctx) {
+    if (!ctx) return RAYPC_OK;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard g(ctx->device);
+        for (auto& kv : ctx->vols) free_volume(ctx, kv.second);
+        ctx->vols.clear();
+    }
+    delete ctx;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_memory_used(raypc_ctx* ctx, size_t* out_bytes) {
+    if (!ctx || !out_bytes) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    *out_bytes = ctx->used;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_device, int src_dtype,
+                               int store_dtype, int nx, int ny, int nz, int nvars, float r_in,
+                               float r_out, void* stream, int* out_vol) {
+    if (!ctx || !src || !out_vol) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if ((src_dtype != RAYPC_F32 && src_dtype != RAYPC_F16) || (store_dtype != RAYPC_F32 && store_dtype != RAYPC_F16))
+        return fail(RAYPC_ERR_INVALID_ARG, "dtype must be RAYPC_F32 or RAYPC_F16");
+    if (nvars < 1 || nvars > RAYPC_MAX_VARS) return fail(RAYPC_ERR_INVALID_ARG, "nvars %d not in 1..%d", nvars, RAYPC_MAX_VARS);
+    if (nx < 2 || ny < 2 || nz < 2) return fail(RAYPC_ERR_INVALID_ARG, "grid must be at least 2 cells per axis");
+    if (nx != ny || ny != nz) return fail(RAYPC_ERR_UNSUPPORTED, "only cubic grids are supported (%d x %d x %d)", nx, ny, nz);
+    if (nx > 8192) return fail(RAYPC_ERR_UNSUPPORTED, "grid edge %d > 8192", nx);
+    if (!(r_in >= 0.f) || !(r_out > r_in) || !isfinite(r_out))
+        return fail(RAYPC_ERR_INVALID_ARG, "need 0 <= r_in < r_out (got %g, %g)", r_in, r_out);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return fail(RAYPC_ERR_CUDA, "cannot select device %d", ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = nx;
+    const size_t nvox = (size_t)n * n * n;
+    Volume* V = new Volume();
+    V->nvars = nvars;
+    V->dtype = store_dtype;
+    V->vp = (store_dtype == RAYPC_F16) ? 8 : (nvars <= 4 ? 4 : 8);
+    V->r_in = r_in;
+    V->r_out = r_out;
+    Level& L = V->lv[0];
+    L.n = n;
+    L.nb = (n + RAYPC_BRICK - 1) / RAYPC_BRICK;
+    L.data_bytes = nvox * V->vp * elem_size(store_dtype);
+    raypc_status st = ctx->alloc(&L.data, L.data_bytes, &V->bytes);
+    if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
+    const void* dsrc = src;
+    void* staging = nullptr;
+    size_t src_bytes = nvox * nvars * elem_size(src_dtype);
+    cudaError_t e;
+    if (!src_is_device) {
+        e = cudaMallocAsync(&staging, src_bytes, s);
+        if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "staging allocation"); }
+        e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { cudaFreeAsync(staging, s); free_volume(ctx, V); return cuda_fail(e, "host to device copy"); }
+        dsrc = staging;
+    }
+    e = launch_ingest(dsrc, src_dtype, L.data, store_dtype, V->vp, n, nvars, s);
+    if (staging) cudaFreeAsync(staging, s);
+    if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "ingest kernel"); }
+    if (!src_is_device) {
+        // the caller's host buffer may be pageable: finish before returning
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "ingest"); }
+    }
+    V->nlev = 1;
+    int id = ctx->next_id++;
+    ctx->vols[id] = V;
+    *out_vol = id;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_free_volume(raypc_ctx* ctx, int vol) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    ctx->vols.erase(vol);
+    cudaDeviceSynchronize();
+    free_volume(ctx, V);
+    return RAYPC_OK;
+}
+
+raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lod, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    if (brick_dim != RAYPC_BRICK) return fail(RAYPC_ERR_UNSUPPORTED, "brick_dim must be %d", RAYPC_BRICK);
+    if (n_lod < 0 || n_lod > RAYPC_MAX_LOD) return fail(RAYPC_ERR_INVALID_ARG, "n_lod %d not in 0..%d", n_lod, RAYPC_MAX_LOD);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // coarser levels
+    for (int l = 1; l <= n_lod; ++l) {
+        Level& P = V->lv[l - 1];
+        Level& L = V->lv[l];
+        int m = (P.n + 1) / 2;
+        if (m < 2) return fail(RAYPC_ERR_INVALID_ARG, "level %d would have fewer than 2 cells per axis", l);
+        if (!L.data) {
+            L.n = m;
+            L.nb = (m + RAYPC_BRICK - 1) / RAYPC_BRICK;
+            L.data_bytes = (size_t)m * m * m * V->vp * elem_size(V->dtype);
+            st = ctx->alloc(&L.data, L.data_bytes, &V->bytes);
+            if (st) return st;
+        }
+        CK(launch_lod(P.data, P.n, L.data, V->dtype, V->vp, V->nvars, s), "LOD kernel");
+    }
+    V->nlev = 1 + n_lod > V->nlev ? 1 + n_lod : V->nlev;
+    for (int l = 0; l <= n_lod; ++l) {
+        Level& L = V->lv[l];
+        if (!L.bmin) {
+            size_t nbk = L.nbricks();
+            size_t mm = nbk * V->nvars * sizeof(float);
+            size_t words = L.nwords() * sizeof(uint32_t);
+            if ((st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.bmax, mm, &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.active, words, &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.skippable, words, &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.list, nbk * sizeof(uint32_t), &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.n_active, sizeof(uint32_t), &V->bytes)) ||
+                (st = ctx->alloc((void**)&L.pass_count, sizeof(unsigned) * kMaxVars, &V->bytes))) {
+                free_bricks(L);
+                return st;
+            }
+        }
+        CK(launch_brick_minmax(L.data, V->dtype, V->vp, L.n, V->nvars, L.bmin, L.bmax, s), "brick min/max kernel");
+        L.bricks = true;
+        L.classified = false;
+        if (V->brush_set && (st = classify_level(V, L, s))) return st;
+    }
+    return RAYPC_OK;
+}
+
+raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const float* hi,
+                             uint32_t active_mask, void* stream) {
+    if (!ctx || !lo || !hi) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    if (active_mask >> V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "active_mask 0x%x names variables >= nvars %d", active_mask, V->nvars);
+    BrushArgs b{};
+    for (int v = 0; v < kMaxVars; ++v) { b.lo[v] = -INFINITY; b.hi[v] = INFINITY; }
+    for (int v = 0; v < V->nvars; ++v) {
+        if (isnan(lo[v]) || isnan(hi[v])) return fail(RAYPC_ERR_INVALID_ARG, "NaN brush bound for variable %d", v);
+        b.lo[v] = lo[v];
+        b.hi[v] = hi[v];
+    }
+    b.mask = active_mask;
+    if (!V->lv[0].bricks) return fail(RAYPC_ERR_INVALID_ARG, "raypc_build_bricks must run before raypc_set_brush");
+    V->brush = b;
+    V->brush_set = true;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int l = 0; l < V->nlev; ++l)
+        if (V->lv[l].bricks && (st = classify_level(V, V->lv[l], s))) return st;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_var, float v_lo,
+                          float v_hi, void* stream) {
+    if (!ctx || !rgbs) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (!(v_lo < v_hi) || !isfinite(v_lo) || !isfinite(v_hi)) return fail(RAYPC_ERR_INVALID_ARG, "need finite v_lo < v_hi");
+    for (int i = 0; i < 4 * RAYPC_TF_ENTRIES; ++i)
+        if (!isfinite(rgbs[i])) return fail(RAYPC_ERR_INVALID_ARG, "non-finite transfer function entry %d", i);
+    for (int i = 0; i < RAYPC_TF_ENTRIES; ++i)
+        if (rgbs[4 * i + 3] < 0.f) return fail(RAYPC_ERR_INVALID_ARG, "negative extinction at entry %d", i);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    if (color_var < 0 || color_var >= V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "color_var %d out of range", color_var);
+    if (!V->tf) {
+        size_t dummy = 0;
+        if ((st = ctx->alloc((void**)&V->tf, sizeof(float4) * RAYPC_TF_ENTRIES, &dummy))) return st;
+        V->bytes += dummy;
+    }
+    // pageable host source: cudaMemcpyAsync stages it before returning
+    CK(cudaMemcpyAsync(V->tf, rgbs, sizeof(float4) * RAYPC_TF_ENTRIES, cudaMemcpyHostToDevice, (cudaStream_t)stream),
+       "transfer function upload");
+    V->color_var = color_var;
+    V->tf_lo = v_lo;
+    V->tf_hi = v_hi;
+    V->tf_set = true;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* cam, int w, int h,
+                          const raypc_render_opts* opts, float* out_rgba_dev,
+                          unsigned long long* stats_dev, void* stream) {
+    if (!ctx || !cam || !out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (w < 1 || h < 1 || w > 32768 || h > 32768) return fail(RAYPC_ERR_INVALID_ARG, "image size %d x %d out of range", w, h);
+    if (((uintptr_t)out_rgba_dev) & 15u) return fail(RAYPC_ERR_INVALID_ARG, "out_rgba_dev must be 16-byte aligned");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(cam->eye[i]) || !isfinite(cam->target[i]) || !isfinite(cam->up[i]))
+            return fail(RAYPC_ERR_INVALID_ARG, "non-finite camera");
+    if (!(cam->tan_half_vfov > 0.f) || !isfinite(cam->tan_half_vfov)) return fail(RAYPC_ERR_INVALID_ARG, "tan_half_vfov must be > 0");
+    {
+        float fx = cam->target[0] - cam->eye[0], fy = cam->target[1] - cam->eye[1], fz = cam->target[2] - cam->eye[2];
+        if (fx == 0.f && fy == 0.f && fz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "eye == target");
+        float cx = fy * cam->up[2] - fz * cam->up[1], cy = fz * cam->up[0] - fx * cam->up[2], cz = fx * cam->up[1] - fy * cam->up[0];
+        if (cx == 0.f && cy == 0.f && cz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "up is parallel to the view direction");
+    }
+    raypc_render_opts o{};
+    o.ert = 1;
+    if (opts) o = *opts;
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(o.bg[i])) return fail(RAYPC_ERR_INVALID_ARG, "non-finite background");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (!L->bricks || !L->classified) return fail(RAYPC_ERR_INVALID_ARG, "build_bricks and set_brush must run before render");
+    if (!V->tf_set) return fail(RAYPC_ERR_INVALID_ARG, "set_tf must run before render");
+    float dt = o.step > 0.f ? o.step : 1.0f / (float)L->n;
+    if (!isfinite(dt) || dt < 2.0f * V->r_out / 4194304.0f)
+        return fail(RAYPC_ERR_INVALID_ARG, "step %g too small (at most 2^21 samples per chord)", dt);
+    RenderArgs a{};
+    a.lv.data = L->data;
+    a.lv.n = L->n;
+    a.lv.nb = L->nb;
+    a.lv.bmin = L->bmin;
+    a.lv.bmax = L->bmax;
+    a.lv.active = L->active;
+    a.lv.skippable = L->skippable;
+    a.nvars = V->nvars;
+    a.brush = V->brush;
+    a.pass_count = L->pass_count;
+    for (int i = 0; i < 3; ++i) { a.eye[i] = cam->eye[i]; a.target[i] = cam->target[i]; a.up[i] = cam->up[i]; }
+    a.tan_half = cam->tan_half_vfov;
+    a.w = w;
+    a.h = h;
+    a.dt = dt;
+    a.rin2 = V->r_in * V->r_in;
+    a.rout2 = V->r_out * V->r_out;
+    a.tf = V->tf;
+    a.color_var = V->color_var;
+    a.tf_lo = V->tf_lo;
+    a.tf_scale = 255.0f / (V->tf_hi - V->tf_lo);
+    for (int i = 0; i < 4; ++i) a.bg[i] = o.bg[i];
+    a.ert = o.ert ? 1 : 0;
+    a.skip = o.no_skip ? 0 : 1;
+    a.out = reinterpret_cast<float4*>(out_rgba_dev);
+    a.counts = o.counts_dev;
+    a.stats = stats_dev;
+    CK(launch_render(a, V->dtype, V->vp, (cudaStream_t)stream), "render kernel");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axis_order, int naxes,
+                                int bins, const float* edges, int use_brush, uint32_t* out_counts_dev,
+                                void* stream) {
+    if (!ctx || !axis_order || !edges || !out_counts_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (naxes < 2 || naxes > RAYPC_MAX_VARS) return fail(RAYPC_ERR_INVALID_ARG, "naxes %d not in 2..%d", naxes, RAYPC_MAX_VARS);
+    if (bins < 2 || bins > 1024) return fail(RAYPC_ERR_INVALID_ARG, "bins %d not in 2..1024", bins);
+    for (int a = 0; a < naxes; ++a)
+        for (int k = 0; k <= bins; ++k) {
+            float e = edges[(size_t)a * (bins + 1) + k];
+            if (isnan(e)) return fail(RAYPC_ERR_INVALID_ARG, "NaN edge (axis %d, edge %d)", a, k);
+            if (k && e < edges[(size_t)a * (bins + 1) + k - 1]) return fail(RAYPC_ERR_INVALID_ARG, "edges of axis %d decrease at %d", a, k);
+        }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    for (int a = 0; a < naxes; ++a)
+        if (axis_order[a] < 0 || axis_order[a] >= V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d", a, axis_order[a]);
+    if (use_brush && !V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "use_brush needs raypc_set_brush");
+    cudaStream_t s = (cudaStream_t)stream;
+    HistArgs h{};
+    h.data = L->data;
+    h.n = L->n;
+    h.nvars = V->nvars;
+    h.brush = V->brush;
+    h.use_brush = use_brush ? 1 : 0;
+    h.naxes = naxes;
+    h.bins = bins;
+    for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? axis_order[a] : 0;
+    double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
+    h.s_in = (int64_t)ceil(ri * ri);
+    h.s_out = (int64_t)floor(ro * ro);
+    // edges: a small device copy owned by this call (freed in stream order)
+    size_t eb = sizeof(float) * naxes * (bins + 1);
+    float* dedges = nullptr;
+    CK(cudaMallocAsync((void**)&dedges, eb, s), "edge buffer");
+    cudaError_t e = cudaMemcpyAsync(dedges, edges, eb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out_counts_dev, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
+    if (e == cudaSuccess) {
+        h.edges = dedges;
+        h.out = out_counts_dev;
+        e = launch_histogram(h, V->dtype, V->vp, s);
+    }
+    cudaFreeAsync(dedges, s);
+    if (e != cudaSuccess) return cuda_fail(e, "histogram");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_volume_info(raypc_ctx* ctx, int vol, int lod, int* out_n, int* out_nvars,
+                               int* out_dtype, int* out_bricks_per_axis) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (out_n) *out_n = L->n;
+    if (out_nvars) *out_nvars = V->nvars;
+    if (out_dtype) *out_dtype = V->dtype;
+    if (out_bricks_per_axis) *out_bricks_per_axis = L->nb;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_export_volume(raypc_ctx* ctx, int vol, int lod, void* out_dev, void* stream) {
+    if (!ctx || !out_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    CK(launch_export(L->data, V->dtype, V->vp, out_dev, L->n, V->nvars, (cudaStream_t)stream), "export kernel");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_get_bricks(raypc_ctx* ctx, int vol, int lod, float* out_min_dev, float* out_max_dev,
+                              void* stream) {
+    if (!ctx || !out_min_dev || !out_max_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d not built", lod);
+    size_t bytes = L->nbricks() * V->nvars * sizeof(float);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out_min_dev, L->bmin, bytes, cudaMemcpyDeviceToDevice, s), "copy brick min");
+    CK(cudaMemcpyAsync(out_max_dev, L->bmax, bytes, cudaMemcpyDeviceToDevice, s), "copy brick max");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_get_skip_list(raypc_ctx* ctx, int vol, int lod, uint32_t* active_bits_dev,
+                                 uint32_t* skippable_bits_dev, uint32_t* active_list_dev,
+                                 uint32_t* n_active_dev, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (!L->classified) return fail(RAYPC_ERR_INVALID_ARG, "level %d not classified (set_brush)", lod);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t wb = L->nwords() * sizeof(uint32_t);
+    if (active_bits_dev) CK(cudaMemcpyAsync(active_bits_dev, L->active, wb, cudaMemcpyDeviceToDevice, s), "copy active bits");
+    if (skippable_bits_dev) CK(cudaMemcpyAsync(skippable_bits_dev, L->skippable, wb, cudaMemcpyDeviceToDevice, s), "copy skippable bits");
+    if (active_list_dev) CK(cudaMemcpyAsync(active_list_dev, L->list, L->nbricks() * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active list");
+    if (n_active_dev) CK(cudaMemcpyAsync(n_active_dev, L->n_active, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active count");
+    return RAYPC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Adjacent-axis parallel-coordinates density histograms (Section 2.1 PC data,
+// Fig. 2): for every in-shell (and, optionally, in-brush) cell and every pair
+// of adjacent axes (a, a+1), H[a][bin_a][bin_{a+1}] += 1.
+//
+// HBM-bound scan. A warp walks one x-row of cells at a time (lanes over x), so
+// the interleaved vertex loads are fully coalesced; rows whose cells all lie
+// outside the shell are skipped without touching memory. The in-shell test is
+// integer-exact. Bins come from a binary search over the FP32 edges held in
+// shared memory (comparisons only, so exact). Increments are aggregated per
+// warp with __match_any_sync on the (bin_a, bin_{a+1}) key: one atomicAdd per
+// distinct key per warp and pair.
+#include "common.cuh"
+
+namespace raypc {
+
+namespace {
+
+constexpr int kHistThreads = 256;
+
+// Number of interior edges e_1..e_{bins-1} that are <= v (edges non-decreasing;
+// NaN compares false everywhere and lands in bin 0).
+__device__ __forceinline__ int bin_of(const float* e, int bins, float v) {
+    int lo = 0, hi = bins - 1;   // answer in [0, bins-1]
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (v >= e[mid]) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int DT, int VP>
+__global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
+    extern __shared__ float s_edges[];
+    const int ne = A.naxes * (A.bins + 1);
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) s_edges[i] = A.edges[i];
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int n = A.n;
+    const long long rows = (long long)n * n;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int bins = A.bins;
+
+    for (long long r = gwarp; r < rows; r += nwarps) {
+        const int y = (int)(r % n), z = (int)(r / n);
+        const long long dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
+        const long long syz = dy * dy + dz * dz;
+        if (syz > A.s_out) continue;                       // whole row outside the outer sphere
+        const size_t row_base = (size_t)r * n;
+        for (int x0 = 0; x0 < n; x0 += 32) {
+            const int x = x0 + lane;
+            bool keep = false;
+            int bn[kMaxVars];
+            if (x < n) {
+                const long long dx = 2 * x + 1 - n;
+                const long long s = dx * dx + syz;
+                if (s >= A.s_in && s <= A.s_out) {
+                    const Vertex<DT, VP> vx = Vertex<DT, VP>::load(A.data, row_base + x);
+                    float val[kMaxVars];
+                    val[0] = vx.template get<0>();
+                    val[1] = vx.template get<1>();
+                    val[2] = vx.template get<2>();
+                    val[3] = vx.template get<3>();
+                    if (VP > 4) {
+                        val[4] = vx.template get<(VP > 4 ? 4 : 0)>();
+                        val[5] = vx.template get<(VP > 4 ? 5 : 0)>();
+                        val[6] = vx.template get<(VP > 4 ? 6 : 0)>();
+                        val[7] = vx.template get<(VP > 4 ? 7 : 0)>();
+                    } else {
+                        val[4] = val[5] = val[6] = val[7] = 0.0f;
+                    }
+                    keep = true;
+                    if (A.use_brush) {
+#pragma unroll
+                        for (int v = 0; v < kMaxVars; ++v)
+                            if ((A.brush.mask >> v) & 1u)
+                                keep = keep && (val[v] >= A.brush.lo[v]) && (val[v] <= A.brush.hi[v]);
+                    }
+                    if (keep) {
+#pragma unroll
+                        for (int a = 0; a < kMaxVars; ++a) {
+                            if (a < A.naxes) {
+                                float va = val[0];
+#pragma unroll
+                                for (int v = 1; v < kMaxVars; ++v)
+                                    if (A.axis[a] == v) va = val[v];
+                                bn[a] = bin_of(s_edges + a * (bins + 1), bins, va);
+                            }
+                        }
+                    }
+                }
+            }
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            if (km == 0u) continue;
+            if (keep) {
+#pragma unroll
+                for (int p = 0; p + 1 < kMaxVars; ++p) {
+                    if (p + 1 < A.naxes) {
+                        const unsigned key = (unsigned)bn[p] * (unsigned)bins + (unsigned)bn[p + 1];
+                        const unsigned peers = __match_any_sync(km, key);
+                        if (lane == __ffs(peers) - 1)
+                            atomicAdd(A.out + (size_t)p * bins * bins + key, (unsigned)__popc(peers));
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int DT, int VP>
+cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long rows = (long long)a.n * a.n;
+    long long want_blocks = (rows + (kHistThreads / 32) - 1) / (kHistThreads / 32);
+    int blocks = (int)(want_blocks < (long long)sms * 8 ? want_blocks : (long long)sms * 8);
+    if (blocks < 1) blocks = 1;
+    size_t smem = sizeof(float) * a.naxes * (a.bins + 1);
+    k_hist<DT, VP><<<blocks, kHistThreads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_histogram(const HistArgs& a, int dtype, int vp, cudaStream_t stream) {
+    if (dtype == kF16) return launch_t<kF16, 8>(a, stream);
+    if (vp == 4) return launch_t<kF32, 4>(a, stream);
+    return launch_t<kF32, 8>(a, stream);
+}
+
+}  // namespace raypc

@@ -1,0 +1,277 @@
+// Brushed emission-absorption ray marching (Section 2.2 of the paper).
+//
+// One thread per ray; a warp covers an 8x4 pixel tile so that neighbouring
+// rays fetch neighbouring vertices, and a 128-thread block covers 16x8
+// pixels. Per lattice sample: position, interpolation cell and brick
+// (exactly rounded FP32), brick activity bit (samples in inactive bricks
+// cannot pass the brush or the shell test), shell test, then the restricted
+// variables in increasing order of how many bricks pass them alone (most
+// selective first; the order cannot change the result), each as an FP32
+// trilinear interpolation of the corner vertices, with exit on the first
+// failure. Kept samples are coloured by the transfer function (from shared
+// memory) and composited front to back with early ray termination.
+//
+// Empty-space skipping: when a sample falls in a skippable brick (inactive
+// with all 26 neighbours inactive), the ray jumps to one lattice point before
+// the one at which it leaves the brick; every jumped sample lies in that brick
+// or, after FP32 rounding, in one of its inactive neighbours, so skipping
+// changes no decision. The lattice itself (t_k = t0 + (k + 1/2) dt) is never
+// shifted.
+#include "common.cuh"
+
+namespace raypc {
+
+namespace {
+
+constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+
+__device__ __forceinline__ void normalize_rn(float& x, float& y, float& z) {
+    float l = __fsqrt_rn(dot3_rn(x, y, z, x, y, z));
+    x = __fdiv_rn(x, l);
+    y = __fdiv_rn(y, l);
+    z = __fdiv_rn(z, l);
+}
+
+__device__ __forceinline__ void cross_rn(float ax, float ay, float az, float bx, float by, float bz,
+                                         float& cx, float& cy, float& cz) {
+    cx = __fmaf_rn(ay, bz, -__fmul_rn(az, by));
+    cy = __fmaf_rn(az, bx, -__fmul_rn(ax, bz));
+    cz = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t* bits, uint32_t id) {
+    return (__ldg(bits + (id >> 5)) >> (id & 31)) & 1u;
+}
+
+template <int DT, int VP, int V>
+__device__ __forceinline__ float interp_var(const Vertex<DT, VP> (&c)[8], float fx, float fy, float fz) {
+    // corner index = dx + 2 dy + 4 dz
+    return trilerp_rn(c[0].template get<V>(), c[1].template get<V>(), c[2].template get<V>(),
+                      c[3].template get<V>(), c[4].template get<V>(), c[5].template get<V>(),
+                      c[6].template get<V>(), c[7].template get<V>(), fx, fy, fz);
+}
+
+// Interpolate variable v (warp-uniform value) with compile-time register
+// selection: the switch is a uniform branch, no dynamic register indexing.
+template <int DT, int VP>
+__device__ __forceinline__ float interp_dyn(int v, const Vertex<DT, VP> (&c)[8], float fx, float fy, float fz) {
+    switch (v) {
+        case 0: return interp_var<DT, VP, 0>(c, fx, fy, fz);
+        case 1: return interp_var<DT, VP, 1>(c, fx, fy, fz);
+        case 2: return interp_var<DT, VP, 2>(c, fx, fy, fz);
+        case 3: return interp_var<DT, VP, 3>(c, fx, fy, fz);
+        case 4: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 4 : 0)>(c, fx, fy, fz); break;
+        case 5: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 5 : 0)>(c, fx, fy, fz); break;
+        case 6: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 6 : 0)>(c, fx, fy, fz); break;
+        case 7: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 7 : 0)>(c, fx, fy, fz); break;
+        default: break;
+    }
+    return 0.0f;
+}
+
+template <int DT, int VP>
+__global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
+    __shared__ float4 s_tf[kTF];
+    __shared__ int s_order[kMaxVars];
+    __shared__ int s_nact;
+    __shared__ float s_lo[kMaxVars], s_hi[kMaxVars];
+    for (int i = threadIdx.x; i < kTF; i += kThreads) s_tf[i] = A.tf[i];
+    if (threadIdx.x == 0) {
+        // restricted variables, most selective (fewest passing bricks) first
+        int cnt = 0;
+        unsigned pc[kMaxVars];
+        for (int v = 0; v < A.nvars; ++v) {
+            if (!((A.brush.mask >> v) & 1u)) continue;
+            unsigned c = A.pass_count ? A.pass_count[v] : 0u;
+            int j = cnt++;
+            while (j > 0 && pc[j - 1] > c) { pc[j] = pc[j - 1]; s_order[j] = s_order[j - 1]; --j; }
+            pc[j] = c;
+            s_order[j] = v;
+        }
+        s_nact = cnt;
+    }
+    if (threadIdx.x < kMaxVars) {
+        s_lo[threadIdx.x] = A.brush.lo[threadIdx.x];
+        s_hi[threadIdx.x] = A.brush.hi[threadIdx.x];
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    const bool inside = px < A.w && py < A.h;
+
+    unsigned marched = 0, kept = 0, evald = 0, skipped = 0, hit = 0, ert_hit = 0;
+    float Cr = 0.f, Cg = 0.f, Cb = 0.f, Aa = 0.f;
+
+    if (inside) {
+        // Camera basis and pixel direction (exactly rounded, fixed order).
+        float Fx = __fsub_rn(A.target[0], A.eye[0]);
+        float Fy = __fsub_rn(A.target[1], A.eye[1]);
+        float Fz = __fsub_rn(A.target[2], A.eye[2]);
+        normalize_rn(Fx, Fy, Fz);
+        float Rx, Ry, Rz, Ux, Uy, Uz;
+        cross_rn(Fx, Fy, Fz, A.up[0], A.up[1], A.up[2], Rx, Ry, Rz);
+        normalize_rn(Rx, Ry, Rz);
+        cross_rn(Rx, Ry, Rz, Fx, Fy, Fz, Ux, Uy, Uz);
+        const float aspect = __fdiv_rn((float)A.w, (float)A.h);
+        const float sxs = __fmul_rn(A.tan_half, aspect);
+        const float qx = __fdiv_rn((float)(2 * px + 1), (float)A.w);
+        const float qy = __fdiv_rn((float)(2 * py + 1), (float)A.h);
+        const float sx = __fmul_rn(__fsub_rn(qx, 1.0f), sxs);
+        const float sy = __fmul_rn(__fsub_rn(1.0f, qy), A.tan_half);
+        float dx = __fmaf_rn(sy, Ux, __fmaf_rn(sx, Rx, Fx));
+        float dy = __fmaf_rn(sy, Uy, __fmaf_rn(sx, Ry, Fy));
+        float dz = __fmaf_rn(sy, Uz, __fmaf_rn(sx, Rz, Fz));
+        normalize_rn(dx, dy, dz);
+        const float ox = A.eye[0], oy = A.eye[1], oz = A.eye[2];
+        // Outer-sphere interval through the point closest to the centre.
+        const float b = dot3_rn(ox, oy, oz, dx, dy, dz);
+        const float hx = __fmaf_rn(-b, dx, ox), hy = __fmaf_rn(-b, dy, oy), hz = __fmaf_rn(-b, dz, oz);
+        const float disc = __fsub_rn(A.rout2, dot3_rn(hx, hy, hz, hx, hy, hz));
+        if (disc > 0.0f) {
+            hit = 1;
+            const float sq = __fsqrt_rn(disc);
+            const float t0 = fmaxf(__fsub_rn(-b, sq), 0.0f);
+            const float t1 = __fadd_rn(-b, sq);
+            const int n = A.lv.n, nb = A.lv.nb;
+            const float hn = 0.5f * (float)n, off = hn - 0.5f;
+            const float dt = A.dt;
+            const size_t sy_ = (size_t)n, sz_ = (size_t)n * n;
+            const int nact = s_nact;
+            int k = 0;
+            for (;;) {
+                float t = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, t0);
+                if (!(t < t1)) break;
+                const float pxw = __fmaf_rn(t, dx, ox), pyw = __fmaf_rn(t, dy, oy), pzw = __fmaf_rn(t, dz, oz);
+                int ix, iy, iz;
+                float fx, fy, fz;
+                grid_coord_rn(pxw, n, hn, off, ix, fx);
+                grid_coord_rn(pyw, n, hn, off, iy, fy);
+                grid_coord_rn(pzw, n, hn, off, iz, fz);
+                const int bx = ix >> 3, by = iy >> 3, bz = iz >> 3;
+                const uint32_t bid = ((uint32_t)bz * nb + by) * nb + bx;
+                if (!bit_of(A.lv.active, bid)) {
+                    if (A.skip && bit_of(A.lv.skippable, bid)) {
+                        // exit time from the brick's sample region (any conservative value works)
+                        float te = __int_as_float(0x7f800000);
+                        const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz};
+                        const int bb[3] = {bx, by, bz};
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            if (dd[a] > 0.0f && bb[a] < nb - 1) {
+                                float pl = ((float)(kBrick * (bb[a] + 1)) + 0.5f) / hn - 1.0f;
+                                te = fminf(te, (pl - oo[a]) / dd[a]);
+                            } else if (dd[a] < 0.0f && bb[a] > 0) {
+                                float pl = ((float)(kBrick * bb[a]) + 0.5f) / hn - 1.0f;
+                                te = fminf(te, (pl - oo[a]) / dd[a]);
+                            }
+                        }
+                        float kk = (te - t0) / dt - 0.5f;
+                        kk = fminf(kk, 1.0e9f);
+                        int kn = (kk > (float)k) ? (int)ceilf(kk) - 1 : k + 1;
+                        kn = max(kn, k + 1);
+                        float tn = __fmaf_rn(__fadd_rn((float)kn, 0.5f), dt, t0);
+                        if (!(tn < t1)) {
+                            // jumped past the end: find the exact lattice end in (k, kn]
+                            int lo = k + 1, hi = kn;   // first index with t >= t1 lies in [lo, hi]
+                            while (lo < hi) {
+                                int mid = lo + ((hi - lo) >> 1);
+                                float tm = __fmaf_rn(__fadd_rn((float)mid, 0.5f), dt, t0);
+                                if (tm < t1) lo = mid + 1; else hi = mid;
+                            }
+                            kn = lo;
+                        }
+                        skipped += (unsigned)(kn - k - 1);
+                        k = kn;
+                        continue;
+                    }
+                    ++k;
+                    continue;
+                }
+                const float r2 = dot3_rn(pxw, pyw, pzw, pxw, pyw, pzw);
+                if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
+                // fetch the 8 corner vertices (all variables at once)
+                const size_t base = ((size_t)iz * n + iy) * n + ix;
+                Vertex<DT, VP> c[8];
+                c[0] = Vertex<DT, VP>::load(A.lv.data, base);
+                c[1] = Vertex<DT, VP>::load(A.lv.data, base + 1);
+                c[2] = Vertex<DT, VP>::load(A.lv.data, base + sy_);
+                c[3] = Vertex<DT, VP>::load(A.lv.data, base + sy_ + 1);
+                c[4] = Vertex<DT, VP>::load(A.lv.data, base + sz_);
+                c[5] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + 1);
+                c[6] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + sy_);
+                c[7] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + sy_ + 1);
+                ++evald;
+                bool pass = true;
+                float vc = 0.0f;
+                bool have_c = false;
+                for (int j = 0; j < nact; ++j) {
+                    const int v = s_order[j];
+                    const float s = interp_dyn<DT, VP>(v, c, fx, fy, fz);
+                    if (!(s >= s_lo[v] && s <= s_hi[v])) { pass = false; break; }
+                    if (v == A.color_var) { vc = s; have_c = true; }
+                }
+                if (!pass) { ++k; continue; }
+                if (!have_c) vc = interp_dyn<DT, VP>(A.color_var, c, fx, fy, fz);
+                ++kept;
+                // transfer function (continuous; no rounding contract needed)
+                float sp = (vc - A.tf_lo) * A.tf_scale;
+                sp = fminf(fmaxf(sp, 0.0f), 255.0f);
+                const int jj = min((int)sp, kTF - 2);
+                const float w = sp - (float)jj;
+                const float4 e0 = s_tf[jj], e1 = s_tf[jj + 1];
+                const float er = fmaf(w, e1.x - e0.x, e0.x);
+                const float eg = fmaf(w, e1.y - e0.y, e0.y);
+                const float eb = fmaf(w, e1.z - e0.z, e0.z);
+                const float es = fmaf(w, e1.w - e0.w, e0.w);
+                const float alpha = 1.0f - __expf(-es * dt);
+                const float ta = (1.0f - Aa) * alpha;
+                Cr = fmaf(ta, er, Cr);
+                Cg = fmaf(ta, eg, Cg);
+                Cb = fmaf(ta, eb, Cb);
+                Aa += ta;
+                if (A.ert && Aa >= kErtThreshold) { ert_hit = 1; ++k; break; }
+                ++k;
+            }
+            marched = (unsigned)k;
+        }
+        const float tr = 1.0f - Aa;
+        float4 o;
+        o.x = fmaf(tr, A.bg[0], Cr);
+        o.y = fmaf(tr, A.bg[1], Cg);
+        o.z = fmaf(tr, A.bg[2], Cb);
+        o.w = fmaf(tr, A.bg[3], Aa);
+        const size_t pix = (size_t)py * A.w + px;
+        A.out[pix] = o;
+        if (A.counts) {
+            A.counts[2 * pix] = marched;
+            A.counts[2 * pix + 1] = kept;
+        }
+    }
+    if (A.stats) {
+        unsigned vals[6] = {marched, evald, kept, skipped, hit, ert_hit};
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            unsigned r = __reduce_add_sync(0xffffffffu, vals[s]);
+            if (lane == 0 && r) atomicAdd(A.stats + s, (unsigned long long)r);
+        }
+    }
+}
+
+template <int DT, int VP>
+cudaError_t launch_t(const RenderArgs& a, cudaStream_t stream) {
+    dim3 grid((a.w + kTileW - 1) / kTileW, (a.h + kTileH - 1) / kTileH);
+    k_render<DT, VP><<<grid, kThreads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render(const RenderArgs& a, int dtype, int vp, cudaStream_t stream) {
+    if (dtype == kF16) return launch_t<kF16, 8>(a, stream);
+    if (vp == 4) return launch_t<kF32, 4>(a, stream);
+    return launch_t<kF32, 8>(a, stream);
+}
+
+}  // namespace raypc

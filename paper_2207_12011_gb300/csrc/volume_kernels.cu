@@ -1,0 +1,314 @@
+// Volume preparation kernels: ingest/relayout, export, level-of-detail mean,
+// brick min/max and brush classification of bricks.
+//
+// Section 2.1 of the paper prepares the data once (levels of detail, derived
+// variables); Section 2.2 relies on that preparation not depending on the
+// restrictions, so a brush edit only re-runs the (cheap) classification.
+#include "common.cuh"
+
+namespace raypc {
+
+namespace {
+
+__device__ __forceinline__ float load_src(const void* src, int dtype, size_t i) {
+    if (dtype == kF16) return __half2float(reinterpret_cast<const __half*>(src)[i]);
+    return reinterpret_cast<const float*>(src)[i];
+}
+
+__device__ __forceinline__ float load_slot(const void* data, int dtype, int vp, size_t vtx, int v) {
+    if (dtype == kF16) return __half2float(reinterpret_cast<const __half*>(data)[vtx * vp + v]);
+    return reinterpret_cast<const float*>(data)[vtx * vp + v];
+}
+
+__device__ __forceinline__ void store_slot(void* data, int dtype, int vp, size_t vtx, int v, float x) {
+    if (dtype == kF16)
+        reinterpret_cast<__half*>(data)[vtx * vp + v] = __float2half_rn(x);
+    else
+        reinterpret_cast<float*>(data)[vtx * vp + v] = x;
+}
+
+// One thread per vertex: gather the nvars planar values, write one interleaved
+// vertex (VP slots, padding zero). Planar reads and vertex writes are both
+// coalesced along x.
+__global__ void k_ingest(const void* __restrict__ src, int src_dtype, void* __restrict__ dst,
+                         int dst_dtype, int vp, int nvars, size_t nvox) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvox) return;
+    float v[kMaxVars];
+#pragma unroll
+    for (int k = 0; k < kMaxVars; ++k) v[k] = (k < nvars) ? load_src(src, src_dtype, (size_t)k * nvox + i) : 0.0f;
+    if (dst_dtype == kF16) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t lo = __half_as_ushort(__float2half_rn(v[2 * k]));
+            uint32_t hi = __half_as_ushort(__float2half_rn(v[2 * k + 1]));
+            w[k] = lo | (hi << 16);
+        }
+        reinterpret_cast<uint4*>(dst)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    } else if (vp == 4) {
+        reinterpret_cast<float4*>(dst)[i] = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        float4* d = reinterpret_cast<float4*>(dst) + 2 * i;
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+__global__ void k_export(const void* __restrict__ src, int dtype, int vp, void* __restrict__ dst,
+                         int nvars, size_t nvox) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nvox) return;
+    for (int k = 0; k < nvars; ++k) {
+        if (dtype == kF16)
+            reinterpret_cast<__half*>(dst)[(size_t)k * nvox + i] = reinterpret_cast<const __half*>(src)[i * vp + k];
+        else
+            reinterpret_cast<float*>(dst)[(size_t)k * nvox + i] = reinterpret_cast<const float*>(src)[i * vp + k];
+    }
+}
+
+// Coarse cell = FP32 mean of its 2x2x2 fine cells (fine indices clamped):
+// ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
+__global__ void k_lod(const void* __restrict__ src, int n, void* __restrict__ dst, int dtype,
+                      int vp, int nvars) {
+    int m = (n + 1) / 2;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)m * m * m;
+    if (i >= total) return;
+    int x = (int)(i % m), y = (int)((i / m) % m), z = (int)(i / ((size_t)m * m));
+    int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
+    int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1), z1 = min(z0 + 1, n - 1);
+    auto vid = [&](int a, int b, int c) { return ((size_t)c * n + b) * n + a; };
+    size_t v000 = vid(x0, y0, z0), v100 = vid(x1, y0, z0), v010 = vid(x0, y1, z0), v110 = vid(x1, y1, z0);
+    size_t v001 = vid(x0, y0, z1), v101 = vid(x1, y0, z1), v011 = vid(x0, y1, z1), v111 = vid(x1, y1, z1);
+    for (int k = 0; k < vp; ++k) {
+        float r = 0.0f;
+        if (k < nvars) {
+            float s0 = __fadd_rn(__fadd_rn(load_slot(src, dtype, vp, v000, k), load_slot(src, dtype, vp, v100, k)),
+                                 __fadd_rn(load_slot(src, dtype, vp, v010, k), load_slot(src, dtype, vp, v110, k)));
+            float s1 = __fadd_rn(__fadd_rn(load_slot(src, dtype, vp, v001, k), load_slot(src, dtype, vp, v101, k)),
+                                 __fadd_rn(load_slot(src, dtype, vp, v011, k), load_slot(src, dtype, vp, v111, k)));
+            r = __fmul_rn(__fadd_rn(s0, s1), 0.125f);
+        }
+        store_slot(dst, dtype, vp, i, k, r);
+    }
+}
+
+// One warp per brick: the 32 lanes stride over the brick's (up to) 9^3
+// vertices, keep running NaN-ignoring min/max per variable, then reduce.
+__global__ void k_brick_minmax(const void* __restrict__ data, int dtype, int vp, int n, int nvars,
+                               float* __restrict__ bmin, float* __restrict__ bmax) {
+    int nb = (n + kBrick - 1) / kBrick;
+    size_t nbricks = (size_t)nb * nb * nb;
+    size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= nbricks) return;
+    int bx = (int)(warp % nb), by = (int)((warp / nb) % nb), bz = (int)(warp / ((size_t)nb * nb));
+    int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+    int ex = min(x0 + kBrick, n - 1) - x0 + 1;
+    int ey = min(y0 + kBrick, n - 1) - y0 + 1;
+    int ez = min(z0 + kBrick, n - 1) - z0 + 1;
+    int cnt = ex * ey * ez;
+    float mn[kMaxVars], mx[kMaxVars];
+#pragma unroll
+    for (int k = 0; k < kMaxVars; ++k) { mn[k] = __int_as_float(0x7fffffff); mx[k] = mn[k]; }
+    for (int j = lane; j < cnt; j += 32) {
+        int dx = j % ex, dy = (j / ex) % ey, dz = j / (ex * ey);
+        size_t vtx = ((size_t)(z0 + dz) * n + (y0 + dy)) * n + (x0 + dx);
+#pragma unroll
+        for (int k = 0; k < kMaxVars; ++k) {
+            if (k < nvars) {
+                float a = load_slot(data, dtype, vp, vtx, k);
+                mn[k] = fminf(mn[k], a);
+                mx[k] = fmaxf(mx[k], a);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxVars; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
+            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+        }
+    }
+    if (lane < nvars) {
+        float a = mn[0], b = mx[0];
+#pragma unroll
+        for (int k = 1; k < kMaxVars; ++k)
+            if (lane == k) { a = mn[k]; b = mx[k]; }
+        bmin[warp * nvars + lane] = a;
+        bmax[warp * nvars + lane] = b;
+    }
+}
+
+// World box that the samples assigned to brick b (lower interpolation index in
+// [8b, 8b+8)) can occupy along one axis, widened by 2^-10; the first and
+// last bricks also own the clamped border.
+__device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, float& lo, float& hi) {
+    lo = __fsub_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
+    hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick + kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
+    if (b == 0) lo = -2.0f;
+    if (b == nb - 1) hi = 2.0f;
+}
+
+// One thread per brick: shell test of the widened box and brush test with the
+// rounding margin d = max(|min|, |max|) * 2^-20 + 2^-120. Writes the active
+// bitmask (one ballot word per warp) and counts, per restricted variable, the
+// in-shell bricks that pass that variable alone (a selectivity hint).
+__global__ void k_classify(const float* __restrict__ bmin, const float* __restrict__ bmax, int n,
+                           int nvars, float sc, float rin2, float rout2, BrushArgs brush,
+                           uint32_t* __restrict__ active, unsigned* __restrict__ pass_count) {
+    int nb = (n + kBrick - 1) / kBrick;
+    size_t nbricks = (size_t)nb * nb * nb;
+    size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    bool valid = b < nbricks;
+    bool act = false;
+    unsigned pass_bits = 0;
+    if (valid) {
+        int c[3] = {(int)(b % nb), (int)((b / nb) % nb), (int)(b / ((size_t)nb * nb))};
+        float nearc[3], farc[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float lo, hi;
+            brick_box_axis(c[a], nb, sc, lo, hi);
+            nearc[a] = (lo > 0.0f) ? lo : ((hi < 0.0f) ? -hi : 0.0f);
+            farc[a] = fmaxf(fabsf(lo), fabsf(hi));
+        }
+        float near2 = dot3_rn(nearc[0], nearc[1], nearc[2], nearc[0], nearc[1], nearc[2]);
+        float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
+        act = (near2 <= rout2) && (far2 >= rin2);
+        if (act) {
+            bool all = true;
+            for (int v = 0; v < nvars; ++v) {
+                if (!((brush.mask >> v) & 1u)) continue;
+                float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
+                float m = fmaxf(fabsf(mn), fabsf(mx));
+                float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                bool ok = (__fadd_rn(mx, d) >= brush.lo[v]) && (__fsub_rn(mn, d) <= brush.hi[v]);
+                if (ok) pass_bits |= 1u << v;
+                all = all && ok;
+            }
+            act = all;
+        }
+    }
+    unsigned word = __ballot_sync(0xffffffffu, act);
+    if (lane == 0 && (b >> 5) < (nbricks + 31) / 32) active[b >> 5] = word;
+    for (int v = 0; v < nvars; ++v) {
+        unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
+        if (lane == 0 && cnt) atomicAdd(&pass_count[v], cnt);
+    }
+}
+
+// Skippable = this brick and its existing 26 neighbours are inactive.
+__global__ void k_skippable(const uint32_t* __restrict__ active, int nb, uint32_t* __restrict__ skippable) {
+    size_t nbricks = (size_t)nb * nb * nb;
+    size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    bool s = false;
+    if (b < nbricks) {
+        int x = (int)(b % nb), y = (int)((b / nb) % nb), z = (int)(b / ((size_t)nb * nb));
+        s = true;
+        for (int dz = -1; dz <= 1 && s; ++dz)
+            for (int dy = -1; dy <= 1 && s; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = x + dx, yy = y + dy, zz = z + dz;
+                    if (xx < 0 || yy < 0 || zz < 0 || xx >= nb || yy >= nb || zz >= nb) continue;
+                    size_t id = ((size_t)zz * nb + yy) * nb + xx;
+                    if ((active[id >> 5] >> (id & 31)) & 1u) { s = false; break; }
+                }
+    }
+    unsigned word = __ballot_sync(0xffffffffu, s);
+    if (lane == 0 && (b >> 5) < (nbricks + 31) / 32) skippable[b >> 5] = word;
+}
+
+// Ordered compaction of the active brick ids: one block of 1024 threads, each
+// owning a contiguous run of bitmask words; block-wide exclusive scan of the
+// per-thread popcounts gives every thread its output offset.
+__global__ void __launch_bounds__(1024) k_compact(const uint32_t* __restrict__ active, size_t nwords,
+                                                  size_t nbricks, uint32_t* __restrict__ list,
+                                                  uint32_t* __restrict__ n_active) {
+    __shared__ unsigned s_sum[1024];
+    size_t per = (nwords + blockDim.x - 1) / blockDim.x;
+    size_t w0 = threadIdx.x * per, w1 = min(nwords, w0 + per);
+    unsigned cnt = 0;
+    for (size_t w = w0; w < w1; ++w) cnt += __popc(active[w]);
+    s_sum[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        unsigned add = threadIdx.x >= (unsigned)off ? s_sum[threadIdx.x - off] : 0u;
+        __syncthreads();
+        s_sum[threadIdx.x] += add;
+        __syncthreads();
+    }
+    unsigned pos = s_sum[threadIdx.x] - cnt;
+    if (list) {
+        for (size_t w = w0; w < w1; ++w) {
+            uint32_t bits = active[w];
+            while (bits) {
+                int j = __ffs(bits) - 1;
+                bits &= bits - 1;
+                size_t id = w * 32 + j;
+                if (id < nbricks) list[pos++] = (uint32_t)id;
+            }
+        }
+    }
+    if (threadIdx.x == blockDim.x - 1 && n_active) *n_active = s_sum[threadIdx.x];
+}
+
+inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+cudaError_t launch_ingest(const void* src, int src_dtype, void* dst, int dst_dtype, int vp, int n,
+                          int nvars, cudaStream_t stream) {
+    size_t nvox = (size_t)n * n * n;
+    k_ingest<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, src_dtype, dst, dst_dtype, vp, nvars, nvox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const void* src, int dtype, int vp, void* dst, int n, int nvars,
+                          cudaStream_t stream) {
+    size_t nvox = (size_t)n * n * n;
+    k_export<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, dtype, vp, dst, nvars, nvox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lod(const void* src, int n_src, void* dst, int dtype, int vp, int nvars,
+                       cudaStream_t stream) {
+    size_t m = (size_t)(n_src + 1) / 2;
+    k_lod<<<blocks_for(m * m * m, 256), 256, 0, stream>>>(src, n_src, dst, dtype, vp, nvars);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_minmax(const void* data, int dtype, int vp, int n, int nvars, float* bmin,
+                                float* bmax, cudaStream_t stream) {
+    size_t nb = (size_t)(n + kBrick - 1) / kBrick;
+    size_t threads = nb * nb * nb * 32;
+    k_brick_minmax<<<blocks_for(threads, 256), 256, 0, stream>>>(data, dtype, vp, n, nvars, bmin, bmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const float* bmin, const float* bmax, int n, int nvars, float r_in,
+                            float r_out, const BrushArgs& brush, uint32_t* active,
+                            uint32_t* skippable, uint32_t* list, uint32_t* n_active,
+                            unsigned* pass_count, cudaStream_t stream) {
+    int nb = (n + kBrick - 1) / kBrick;
+    size_t nbricks = (size_t)nb * nb * nb;
+    size_t nwords = (nbricks + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
+    if (e != cudaSuccess) return e;
+    float sc = 2.0f / (float)n;
+    float rin2 = r_in * r_in, rout2 = r_out * r_out;
+    k_classify<<<blocks_for(nbricks, 256), 256, 0, stream>>>(bmin, bmax, n, nvars, sc, rin2, rout2,
+                                                             brush, active, pass_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skippable<<<blocks_for(nbricks, 256), 256, 0, stream>>>(active, nb, skippable);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_compact<<<1, 1024, 0, stream>>>(active, nwords, nbricks, list, n_active);
+    return cudaGetLastError();
+}
+
+}  // namespace raypc

@@ -1,0 +1,300 @@
+"""Python binding of libraypc.so (argument marshalling only).
+
+Every step of rendering, classification and histogramming runs in the CUDA
+kernels behind the C ABI of include/raypc.h; this module only turns torch
+tensors into pointers and streams into handles. If the library is not built
+the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+RAYPC_F32, RAYPC_F16 = 0, 1
+MAX_VARS = 8
+BRICK = 8
+MAX_LOD = 2
+TF_ENTRIES = 256
+NSTATS = 8
+STAT_NAMES = ("marched", "evaluated", "kept", "skipped", "rays", "ert")
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY",
+           6: "NOT_FOUND", 7: "UNSUPPORTED"}
+
+
+class RaypcError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        super().__init__(f"{fn}: {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3),
+                ("up", ctypes.c_float * 3), ("tan_half_vfov", ctypes.c_float)]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_float), ("ert", ctypes.c_int), ("no_skip", ctypes.c_int),
+                ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p)]
+
+
+_lib = None
+
+# C signatures: name -> argument types (all return raypc_status = int)
+_P, _I, _U32, _F, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_float, ctypes.c_size_t
+_SIGS = {
+    "raypc_create": [ctypes.POINTER(_P), _I, _SZ],
+    "raypc_destroy": [_P],
+    "raypc_memory_used": [_P, ctypes.POINTER(_SZ)],
+    "raypc_load_volume": [_P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _F, _P, ctypes.POINTER(_I)],
+    "raypc_free_volume": [_P, _I],
+    "raypc_build_bricks": [_P, _I, _I, _I, _P],
+    "raypc_set_brush": [_P, _I, _P, _P, _U32, _P],
+    "raypc_set_tf": [_P, _I, _P, _I, _F, _F, _P],
+    "raypc_render": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts), _P, _P, _P],
+    "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
+    "raypc_volume_info": [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "raypc_export_volume": [_P, _I, _I, _P, _P],
+    "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
+    "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib():
+    """The loaded libraypc.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libraypc.so not found at {path}; build it with "
+                               "`python -m paper_2207_12011_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.raypc_last_error.argtypes = []
+        L.raypc_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _call(name: str, *args):
+    L = lib()
+    st = getattr(L, name)(*args)
+    if st != 0:
+        raise RaypcError(st, name, L.raypc_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_camera(eye, target, up, tan_half_vfov) -> Camera:
+    c = Camera()
+    for i in range(3):
+        c.eye[i], c.target[i], c.up[i] = float(eye[i]), float(target[i]), float(up[i])
+    c.tan_half_vfov = float(tan_half_vfov)
+    return c
+
+
+def camera_from(cam) -> Camera:
+    """Accept a Camera, an object with eye/target/up/tan_half_vfov, or a 10-float array."""
+    if isinstance(cam, Camera):
+        return cam
+    if hasattr(cam, "eye"):
+        return make_camera(cam.eye, cam.target, cam.up, cam.tan_half_vfov)
+    a = np.asarray(cam, dtype=np.float32).reshape(10)
+    return make_camera(a[0:3], a[3:6], a[6:9], a[9])
+
+
+class Context:
+    """A libraypc context on one CUDA device (owns resident volumes)."""
+
+    def __init__(self, device: int | None = None, hbm_budget_bytes: int = 0):
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _call("raypc_create", ctypes.byref(h), self.device, int(hbm_budget_bytes))
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().raypc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory_used(self) -> int:
+        out = ctypes.c_size_t()
+        _call("raypc_memory_used", self.handle, ctypes.byref(out))
+        return int(out.value)
+
+    def load_volume(self, vol: torch.Tensor, store: str = "f32", r_in: float = 0.547,
+                    r_out: float = 1.0, stream=None) -> "Volume":
+        """Copy a (nvars, n, n, n) float32/float16 tensor (device or host) into the library."""
+        if vol.dim() != 4:
+            raise ValueError("volume must be (nvars, nz, ny, nx)")
+        vol = vol.contiguous()
+        src_dt = {torch.float32: RAYPC_F32, torch.float16: RAYPC_F16}.get(vol.dtype)
+        if src_dt is None:
+            raise ValueError(f"unsupported dtype {vol.dtype}")
+        store_dt = {"f32": RAYPC_F32, "f16": RAYPC_F16}[store]
+        nv, nz, ny, nx = vol.shape
+        vid = ctypes.c_int()
+        _call("raypc_load_volume", self.handle, ctypes.c_void_p(vol.data_ptr()), int(vol.is_cuda),
+              src_dt, store_dt, nx, ny, nz, nv, float(r_in), float(r_out), _stream(stream),
+              ctypes.byref(vid))
+        return Volume(self, vid.value, _keepalive=vol)
+
+
+@dataclass
+class LevelInfo:
+    n: int
+    nvars: int
+    dtype: int
+    bricks_per_axis: int
+
+
+class Volume:
+    """A resident volume: levels, bricks, brush, transfer function."""
+
+    def __init__(self, ctx: Context, vid: int, _keepalive=None):
+        self.ctx = ctx
+        self.id = vid
+        self._src = _keepalive   # source kept alive until the async ingest has consumed it
+        info = self.info(0)
+        self.n, self.nvars, self.dtype = info.n, info.nvars, info.dtype
+
+    def info(self, lod: int = 0) -> LevelInfo:
+        n, nv, dt, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _call("raypc_volume_info", self.ctx.handle, self.id, lod, ctypes.byref(n), ctypes.byref(nv),
+              ctypes.byref(dt), ctypes.byref(nb))
+        return LevelInfo(n.value, nv.value, dt.value, nb.value)
+
+    def free(self):
+        _call("raypc_free_volume", self.ctx.handle, self.id)
+        self.id = -1
+
+    def build_bricks(self, n_lod: int = 0, stream=None):
+        _call("raypc_build_bricks", self.ctx.handle, self.id, BRICK, int(n_lod), _stream(stream))
+
+    def set_brush(self, lo, hi, active_mask: int, stream=None):
+        lo = np.ascontiguousarray(np.asarray(lo, dtype=np.float32).reshape(-1)[: self.nvars])
+        hi = np.ascontiguousarray(np.asarray(hi, dtype=np.float32).reshape(-1)[: self.nvars])
+        _call("raypc_set_brush", self.ctx.handle, self.id, _fptr(lo), _fptr(hi),
+              int(active_mask) & 0xFFFFFFFF, _stream(stream))
+
+    def set_tf(self, rgbs, color_var: int, v_lo: float, v_hi: float, stream=None):
+        t = np.ascontiguousarray(np.asarray(rgbs, dtype=np.float32).reshape(TF_ENTRIES, 4))
+        _call("raypc_set_tf", self.ctx.handle, self.id, _fptr(t), int(color_var), float(v_lo),
+              float(v_hi), _stream(stream))
+
+    def render(self, cam, w: int, h: int, lod: int = 0, step: float = 0.0, ert: bool = True,
+               skip: bool = True, bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
+               counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None, stream=None):
+        """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None)."""
+        dev = torch.device("cuda", self.ctx.device)
+        if out is None:
+            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+        if counts is True:
+            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
+        o = RenderOpts()
+        o.step = float(step)
+        o.ert = int(bool(ert))
+        o.no_skip = int(not skip)
+        for i in range(4):
+            o.bg[i] = float(bg[i])
+        o.counts_dev = counts.data_ptr() if isinstance(counts, torch.Tensor) else None
+        c = camera_from(cam)
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        _call("raypc_render", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
+              ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), sp, _stream(stream))
+        return out, (counts if isinstance(counts, torch.Tensor) else None)
+
+    def pc_histogram(self, axis_order, edges, use_brush: bool = True, lod: int = 0,
+                     out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32))
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
+        naxes, bins = e.shape[0], e.shape[1] - 1
+        if out is None:
+            out = torch.empty((naxes - 1, bins, bins), dtype=torch.int32,
+                              device=torch.device("cuda", self.ctx.device))
+        _call("raypc_pc_histogram", self.ctx.handle, self.id, int(lod), _fptr(order), naxes, bins,
+              _fptr(e), int(bool(use_brush)), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+        return out
+
+    def export(self, lod: int = 0, stream=None) -> torch.Tensor:
+        info = self.info(lod)
+        dt = torch.float16 if info.dtype == RAYPC_F16 else torch.float32
+        out = torch.empty((info.nvars, info.n, info.n, info.n), dtype=dt,
+                          device=torch.device("cuda", self.ctx.device))
+        _call("raypc_export_volume", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream))
+        return out
+
+    def bricks(self, lod: int = 0, stream=None):
+        info = self.info(lod)
+        nb = info.bricks_per_axis
+        dev = torch.device("cuda", self.ctx.device)
+        mn = torch.empty((nb, nb, nb, info.nvars), dtype=torch.float32, device=dev)
+        mx = torch.empty_like(mn)
+        _call("raypc_get_bricks", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(mn.data_ptr()),
+              ctypes.c_void_p(mx.data_ptr()), _stream(stream))
+        return mn, mx
+
+    def skip_list(self, lod: int = 0, stream=None):
+        """(active_bits, skippable_bits, active_list[:n_active]) as device int32 tensors."""
+        info = self.info(lod)
+        nbk = info.bricks_per_axis ** 3
+        words = (nbk + 31) // 32
+        dev = torch.device("cuda", self.ctx.device)
+        act = torch.empty(words, dtype=torch.int32, device=dev)
+        skp = torch.empty(words, dtype=torch.int32, device=dev)
+        lst = torch.empty(nbk, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+        _call("raypc_get_skip_list", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(act.data_ptr()),
+              ctypes.c_void_p(skp.data_ptr()), ctypes.c_void_p(lst.data_ptr()),
+              ctypes.c_void_p(cnt.data_ptr()), _stream(stream))
+        n_active = int(cnt.item())
+        return act, skp, lst[:n_active]
+
+
+def unpack_bits(words: torch.Tensor, nbits: int) -> np.ndarray:
+    """Little-endian bitmask words -> uint8 array of nbits flags."""
+    w = words.detach().cpu().numpy().astype(np.uint32)
+    bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)[None, :]) & 1).astype(np.uint8)
+    return bits.reshape(-1)[:nbits]

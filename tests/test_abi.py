@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every declared symbol (CPU only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(raypc_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2207_12011_gb300 import build
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("raypc_create", "raypc_destroy", "raypc_load_volume", "raypc_build_bricks",
+                     "raypc_set_brush", "raypc_set_tf", "raypc_render", "raypc_pc_histogram",
+                     "raypc_get_skip_list"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(raypc_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_library_is_built_for_sm_103a(libpath):
+    from paper_2207_12011_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
+    if out.returncode == 0:
+        assert "sm_103a" in out.stdout
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2207_12011_gb300.raypc as rp
+    monkeypatch.setattr(rp, "_lib", None)
+    monkeypatch.setattr(rp, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        rp.lib()
+
+
+def test_host_side_validation_without_gpu(libpath):
+    """Argument checks that run before any CUDA call return codes, not crashes."""
+    lib = ctypes.CDLL(libpath)
+    lib.raypc_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]
+    lib.raypc_last_error.restype = ctypes.c_char_p
+    assert lib.raypc_create(None, 0, 0) == 1
+    assert b"NULL" in lib.raypc_last_error()
+    lib.raypc_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.raypc_destroy(None) == 0

@@ -1,0 +1,327 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results (stored FP16 bits, LOD levels, brick min/max, brick
+classification bits and lists, per-pixel sample decisions, histogram counts)
+must match bit for bit. RGBA must match within max-abs 1e-3 (FP32 storage) or
+4e-3 (FP16 storage) against the FP64 oracle run on the same stored values.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2207_12011_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+R_IN, R_OUT = synth.R_IN, synth.R_OUT
+TOL = {"f32": 1e-3, "f16": 4e-3}
+
+
+@pytest.fixture(scope="module")
+def rp():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2207_12011_gb300 import raypc
+    return raypc
+
+
+@pytest.fixture(scope="module")
+def ctx(rp):
+    c = rp.Context(0)
+    yield c
+    c.close()
+
+
+def stored(vol: torch.Tensor, store: str) -> np.ndarray:
+    """The values the library stores, as the oracle sees them (float32)."""
+    return synth.to_storage(vol, store).float().cpu().numpy()
+
+
+def load(ctx, vol, store, n_lod=0, brush=None, tf=None):
+    v = ctx.load_volume(vol.cuda(), store=store)
+    v.build_bricks(n_lod=n_lod)
+    if brush is not None:
+        v.set_brush(brush.lo, brush.hi, brush.active_mask)
+    if tf is not None:
+        v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    return v
+
+
+def oracle_levels(vol_np: np.ndarray, n_lod: int, store: str):
+    levels = [vol_np]
+    for _ in range(n_lod):
+        m = oracle.lod_mean(levels[-1])
+        if store == "f16":
+            m = m.astype(np.float16).astype(np.float32)
+        levels.append(m)
+    return levels
+
+
+def bits(rp, words, nbits):
+    return rp.unpack_bits(words, nbits)
+
+
+# ----------------------------------------------------------------------------
+# ingest, LOD, bricks, classification
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("store", ["f32", "f16"])
+@pytest.mark.parametrize("n,nvars", [(37, 6), (16, 3), (2, 1)])
+def test_ingest_roundtrip(ctx, store, n, nvars):
+    vol = synth.make_shell_volume(n, seed=7)[:nvars].contiguous()
+    v = ctx.load_volume(vol.cuda(), store=store)
+    got = v.export().cpu()
+    want = synth.to_storage(vol, store)
+    assert got.dtype == want.dtype
+    assert torch.equal(got.view(torch.int16 if store == "f16" else torch.int32),
+                       want.view(torch.int16 if store == "f16" else torch.int32))
+    # host source path gives the same stored bits
+    v2 = ctx.load_volume(vol, store=store)
+    assert torch.equal(v2.export().cpu(), got)
+    v.free()
+    v2.free()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+@pytest.mark.parametrize("n", [40, 33])
+def test_lod_and_bricks_bit_exact(rp, ctx, store, n):
+    vol = synth.make_shell_volume(n, seed=2)
+    v = load(ctx, vol, store, n_lod=2)
+    levels = oracle_levels(stored(vol, store), 2, store)
+    for lod in range(3):
+        got = v.export(lod).float().cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), levels[lod].view(np.uint32)), lod
+        mn, mx = v.bricks(lod)
+        omn, omx = oracle.brick_minmax(levels[lod])
+        assert np.array_equal(mn.cpu().numpy(), omn) and np.array_equal(mx.cpu().numpy(), omx)
+    v.free()
+
+
+@pytest.mark.parametrize("brush_name", ["c1", "c2", "c3", "empty", "none"])
+def test_classification_bit_exact(rp, ctx, brush_name):
+    n = 64
+    vol = synth.make_shell_volume(n, seed=4)
+    if brush_name == "empty":
+        b = synth.Brush(np.full(6, 1.0, np.float32), np.full(6, 0.0, np.float32), 0b000100)
+    elif brush_name == "none":
+        b = synth.Brush(np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32), 0)
+    else:
+        b = synth.make_brush(vol, brush_name)
+    v = load(ctx, vol, "f32", n_lod=1, brush=b)
+    levels = oracle_levels(stored(vol, "f32"), 1, "f32")
+    for lod in range(2):
+        act, skp, lst = v.skip_list(lod)
+        omn, omx = oracle.brick_minmax(levels[lod])
+        m = levels[lod].shape[1]
+        oact, oskp = oracle.classify(omn, omx, m, R_IN, R_OUT, b.lo, b.hi, b.active_mask)
+        nbk = oact.size
+        assert np.array_equal(bits(rp, act, nbk), oact.reshape(-1))
+        assert np.array_equal(bits(rp, skp, nbk), oskp.reshape(-1))
+        assert np.array_equal(lst.cpu().numpy(), np.flatnonzero(oact.reshape(-1)).astype(np.int32))
+    if brush_name == "empty":
+        assert lst.numel() == 0
+    v.free()
+
+
+# ----------------------------------------------------------------------------
+# rendering
+# ----------------------------------------------------------------------------
+def render_pair(ctx, vol, store, brush, tf, cam, w, h, ert=True, skip=True, lod=0, bg=(0, 0, 0, 0),
+                n_lod=0, pixels=None):
+    v = load(ctx, vol, store, n_lod=n_lod, brush=brush, tf=tf)
+    img, cnt = v.render(cam, w, h, lod=lod, ert=ert, skip=skip, bg=bg, counts=True)
+    torch.cuda.synchronize()
+    img = img.cpu().numpy().astype(np.float64)
+    cnt = cnt.cpu().numpy().astype(np.uint32)
+    level = oracle_levels(stored(vol, store), lod, store)[lod]
+    m = level.shape[1]
+    ref, rcnt = oracle.render(level, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / m, brush.lo, brush.hi,
+                              brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, bg=bg,
+                              ert=ert, pixels=pixels)
+    v.free()
+    if pixels is not None:
+        img = img.reshape(-1, 4)[pixels]
+        cnt = cnt.reshape(-1, 2)[pixels]
+    return img, cnt, ref, rcnt
+
+
+CASES = [
+    # n, store, brush, colour var, image w x h, camera
+    (64, "f32", "c1", "T_anom", 256, 256, dict(az_deg=30, el_deg=20, dist=3.0)),
+    (48, "f32", "c2", "v_r", 77, 45, dict(az_deg=200, el_deg=-35, dist=2.7)),
+    (64, "f16", "c3", "T_anom", 96, 64, dict(az_deg=30, el_deg=20, dist=3.0)),
+    (33, "f16", "c2", "k", 50, 50, dict(az_deg=95, el_deg=55, dist=3.3)),
+]
+
+
+@pytest.mark.parametrize("n,store,bname,cvar,w,h,camkw", CASES)
+def test_render_matches_oracle(ctx, n, store, bname, cvar, w, h, camkw):
+    vol = synth.make_shell_volume(n)
+    brush = synth.make_brush(vol, bname)
+    tf = synth.make_tf(vol, cvar)
+    cam = synth.orbit_camera(**camkw)
+    for ert in (False, True):
+        img, cnt, ref, rcnt = render_pair(ctx, vol, store, brush, tf, cam, w, h, ert=ert)
+        err = np.abs(img - ref)
+        assert err.max() <= TOL[store], (ert, err.max())
+        if not ert:
+            assert np.array_equal(cnt, rcnt)        # every sample decision identical
+        else:
+            assert np.mean(cnt == rcnt) > 0.999
+    assert rcnt[..., 1].sum() > 0
+
+
+def test_skipping_never_changes_the_image(ctx):
+    n = 64
+    vol = synth.make_shell_volume(n, seed=9)
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(40, 10, 2.9)
+    for bname in ("c1", "c3"):
+        brush = synth.make_brush(vol, bname)
+        v = load(ctx, vol, "f32", brush=brush, tf=tf)
+        stats = {}
+        outs = {}
+        for skip in (True, False):
+            st = torch.zeros(8, dtype=torch.int64, device="cuda")
+            img, cnt = v.render(cam, 128, 96, skip=skip, counts=True, stats=st)
+            outs[skip] = (img.cpu(), cnt.cpu())
+            stats[skip] = st.cpu().numpy()
+        assert torch.equal(outs[True][0], outs[False][0])
+        assert torch.equal(outs[True][1], outs[False][1])
+        assert stats[True][3] > 0 and stats[False][3] == 0        # skipping happened
+        assert stats[True][0] == stats[False][0]                   # same marched lattice samples
+        assert stats[True][0] == int(outs[True][1][..., 0].sum())
+        assert stats[True][2] == int(outs[True][1][..., 1].sum())
+        v.free()
+
+
+def test_render_lod_levels(ctx):
+    n = 64
+    vol = synth.make_shell_volume(n)
+    brush = synth.make_brush(vol, "c2")
+    tf = synth.make_tf(vol, "v_r")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    for lod in (1, 2):
+        img, cnt, ref, rcnt = render_pair(ctx, vol, "f16", brush, tf, cam, 64, 48, ert=False, lod=lod, n_lod=2)
+        assert np.abs(img - ref).max() <= TOL["f16"]
+        assert np.array_equal(cnt, rcnt)
+
+
+def test_brush_closed_forms_on_gpu(ctx):
+    n = 48
+    vol = synth.make_shell_volume(n)
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    bg = (0.25, 0.5, 0.125, 0.75)
+    # (b) all-excluding brush: exactly the background
+    empty = synth.Brush(np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32), 1)
+    empty.lo[0], empty.hi[0] = 2.0, 1.0
+    v = load(ctx, vol, "f32", brush=empty, tf=tf)
+    img, cnt = v.render(cam, 64, 64, bg=bg, counts=True)
+    assert torch.all(img.cpu() == torch.tensor(bg, dtype=torch.float32))
+    assert int(cnt[..., 1].sum()) == 0
+    # (c) all-including brush == unbrushed, bit for bit
+    allin = synth.Brush(np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32), 0b111111)
+    v.set_brush(allin.lo, allin.hi, allin.active_mask)
+    a, _ = v.render(cam, 64, 64)
+    v.set_brush(allin.lo, allin.hi, 0)
+    b, _ = v.render(cam, 64, 64)
+    assert torch.equal(a, b)
+    v.free()
+
+
+def test_constant_shell_closed_form_on_gpu(ctx):
+    n = 64
+    vol = torch.full((2, n, n, n), 0.5)
+    tf = synth.constant_tf((1.0, 0.5, 0.25), 2.0)
+    cam = synth.orbit_camera(30, 20, 3.0)
+    allin = synth.Brush(np.full(2, -np.inf, np.float32), np.full(2, np.inf, np.float32), 0)
+    v = load(ctx, vol, "f32", brush=allin, tf=tf)
+    img, cnt = v.render(cam, 80, 80, ert=False, counts=True)
+    kept = cnt[..., 1].cpu().numpy().astype(np.float64)
+    A = 1 - np.exp(-2.0 * kept / n)
+    assert np.abs(img[..., 3].cpu().numpy() - A).max() < 2e-5
+    assert np.abs(img[..., 1].cpu().numpy() - 0.5 * A).max() < 2e-5
+    v.free()
+
+
+def test_render_edge_cases(ctx, rp):
+    n = 16
+    vol = synth.make_shell_volume(n)
+    brush = synth.make_brush(vol, "c2")
+    tf = synth.make_tf(vol, "v_r")
+    # 1 x 1 image, tiny grid
+    cam = synth.orbit_camera(10, 5, 3.0)
+    img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, cam, 1, 1, ert=False)
+    assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # camera inside the shell (rays start at the eye)
+    inside = synth.Camera((0.0, 0.1, 0.8), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.6)
+    img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, inside, 33, 17, ert=False)
+    assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # smallest grid, one variable
+    v1 = torch.rand(1, 2, 2, 2, generator=torch.Generator().manual_seed(0))
+    b1 = synth.Brush(np.array([0.2], np.float32), np.array([0.9], np.float32), 1)
+    tf1 = synth.TransferFunction(synth.tf_ramp(), 0, 0.0, 1.0)
+    img, cnt, ref, rcnt = render_pair(ctx, v1, "f32", b1, tf1, synth.orbit_camera(0, 0, 3.0), 20, 20, ert=False)
+    assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # invalid arguments are rejected on the host
+    v = load(ctx, vol, "f32", brush=brush, tf=tf)
+    with pytest.raises(rp.RaypcError):
+        v.render(cam, 0, 10)
+    with pytest.raises(rp.RaypcError):
+        v.render(synth.Camera((0, 0, 3), (0, 0, 3), (0, 1, 0), 0.4), 8, 8)
+    with pytest.raises(rp.RaypcError):
+        v.render(cam, 8, 8, lod=2)
+    with pytest.raises(rp.RaypcError):
+        v.set_brush([np.nan] * 6, [1.0] * 6, 1)
+    with pytest.raises(rp.RaypcError):
+        ctx.load_volume(torch.zeros(2, 4, 4, 5, device="cuda"))
+    v.free()
+
+
+# ----------------------------------------------------------------------------
+# histograms
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,store,bname,bins,order", [
+    (64, "f32", "c2", 256, (0, 1, 2, 3, 4, 5)),
+    (45, "f16", "c3", 256, (3, 1, 0, 5, 2, 4)),
+    (32, "f32", "none", 64, (2, 5)),
+    (24, "f16", "c1", 1024, (0, 1, 2)),
+    (16, "f32", "empty", 2, (0, 1, 2, 3, 4, 5)),
+])
+def test_histogram_bit_exact(ctx, n, store, bname, bins, order):
+    vol = synth.make_shell_volume(n, seed=13)
+    if bname == "none":
+        brush = synth.Brush(np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32), 0)
+    elif bname == "empty":
+        brush = synth.Brush(np.full(6, 5.0, np.float32), np.full(6, -5.0, np.float32), 1)
+    else:
+        brush = synth.make_brush(vol, bname)
+    edges = synth.make_edges(synth.to_storage(vol, store).float(), order, bins=bins)
+    v = load(ctx, vol, store, brush=brush)
+    for use in (True, False):
+        H = v.pc_histogram(order, edges, use_brush=use).cpu().numpy().astype(np.uint32)
+        Ho, cells = oracle.histogram(stored(vol, store), R_IN, R_OUT, brush.lo, brush.hi,
+                                     brush.active_mask, order, edges, use_brush=use)
+        assert np.array_equal(H, Ho)
+        assert all(int(H[p].sum()) == cells for p in range(H.shape[0]))
+    v.free()
+
+
+def test_histogram_rejects_bad_edges(ctx, rp):
+    vol = synth.make_shell_volume(16)
+    v = load(ctx, vol, "f32", brush=synth.make_brush(vol, "c1"))
+    e = synth.make_edges(vol, (0, 1), bins=16)
+    bad = e.copy()
+    bad[0, 5] = bad[0, 4] - 1
+    with pytest.raises(rp.RaypcError):
+        v.pc_histogram((0, 1), bad)
+    bad = e.copy()
+    bad[1, 3] = np.nan
+    with pytest.raises(rp.RaypcError):
+        v.pc_histogram((0, 1), bad)
+    with pytest.raises(rp.RaypcError):
+        v.pc_histogram((0, 9), e)
+    v.free()
