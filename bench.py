@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the brushed volume-rendering hot path on GB300.
+
+One step is one pass of the whole hot path over one synthetic volume:
+ingest (re-layout of the FP32 source into the stored volume), two coarser
+levels of detail, brick min/max, brush classification, one 1024x1024 brushed
+render and five adjacent-axis 256x256 parallel-coordinates histograms.
+Workload: 256^3 cells x 6 FP32 variables over the bounding cube of a
+spherical shell (r_in/r_out = 0.547), 8^3 bricks, 4-variable brush,
+transfer function on v_r, orbit camera (az 30, el 20, dist 3, vfov 45).
+
+value      = lattice samples marched per second (all ranks) over the timed steps
+e2e        = the same through the C ABI from pinned host buffers, with the
+             host->device copy of the volume and the device->host copy of the
+             image and histograms inside every step
+roofline   = the render kernel (dominant by time) against the measured HBM copy peak
+cpu_baseline = the CPU oracle on a bounded sample of the same frame
+
+`--impl reference` times the CPU oracle (FP64 ray marcher) as the reference arm.
+Multi-GPU (torchrun): every rank renders its own replica of the workload
+(independent volumes, no collective in the data path), "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2207_12011_gb300 import synth  # noqa: E402
+
+METRIC = "brushed samples/s & frames/s at 1024² (1 GB300), served p50/p99 vs plain FP32"
+UNIT = "samples/s"
+
+WORKLOADS = {
+    "shell256_f32": dict(n=256, store="f32", w=1024, h=1024, brush="c2", tf_var="v_r", n_lod=2,
+                         bins=256, order=(0, 1, 2, 3, 4, 5)),
+    "shell512_f16": dict(n=512, store="f16", w=1920, h=1080, brush="c3", tf_var="T_anom", n_lod=2,
+                         bins=256, order=(0, 1, 2, 3, 4, 5)),
+    "shell64_f32": dict(n=64, store="f32", w=256, h=256, brush="c1", tf_var="T_anom", n_lod=0,
+                        bins=256, order=(0, 1, 2, 3, 4, 5)),
+}
+DEFAULT_WORKLOAD = "shell256_f32"
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (also exercised by the gloo tests)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(elapsed_ms: float, units: float, device="cpu"):
+    """Max elapsed time and summed work over ranks (identity without a process group)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return elapsed_ms, units
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+class Workload:
+    def __init__(self, name: str, seed: int, device):
+        self.name = name
+        self.cfg = WORKLOADS[name]
+        c = self.cfg
+        self.src = synth.make_shell_volume(c["n"], seed=seed, device=device)       # FP32, resident
+        stored = synth.to_storage(self.src, c["store"]).float()
+        self.brush = synth.make_brush(stored, c["brush"])
+        self.tf = synth.make_tf(stored, c["tf_var"])
+        self.cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+        self.edges = synth.make_edges(stored, c["order"], bins=c["bins"])
+        del stored
+
+    def describe(self):
+        c = self.cfg
+        return {"workload": self.name, "grid": f"{c['n']}^3 x 6 vars", "storage": c["store"],
+                "image": f"{c['w']}x{c['h']}", "brush": f"{c['brush']} ({bin(self.brush.active_mask).count('1')} vars)",
+                "lod_levels": c["n_lod"], "bricks": "8^3", "pc_histograms": f"{len(c['order']) - 1} x {c['bins']}^2",
+                "tf_var": c["tf_var"]}
+
+
+def step(rp, vol, wl, img, H, stats, src, ev=None):
+    """One pass of the whole hot path; ev = (start, end) CUDA events around the render."""
+    c = wl.cfg
+    vol.update(src)                                                     # ingest + relayout
+    vol.build_bricks(n_lod=c["n_lod"])                                  # LOD + brick min/max
+    vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)       # classification
+    vol.set_tf(wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi)
+    if ev is not None:
+        ev[0].record()
+    vol.render(wl.cam, c["w"], c["h"], out=img, stats=stats)            # ray marching
+    if ev is not None:
+        ev[1].record()
+    vol.pc_histogram(c["order"], wl.edges, use_brush=True, out=H)       # PC histograms
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2207_12011_gb300 import raypc as rp
+
+    wl = Workload(args.workload, synth.DEFAULT_SEED + rank, dev)
+    c = wl.cfg
+    ctx = rp.Context(local)
+    vol = ctx.load_volume(wl.src, store=c["store"])
+    vol.build_bricks(n_lod=c["n_lod"])
+    vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)
+    vol.set_tf(wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi)
+    img = torch.empty((c["h"], c["w"], 4), dtype=torch.float32, device=dev)
+    naxes = len(c["order"])
+    H = torch.empty((naxes - 1, c["bins"], c["bins"]), dtype=torch.int32, device=dev)
+    stats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+
+    for _ in range(args.warmup):
+        step(rp, vol, wl, img, H, stats, wl.src)
+    torch.cuda.synchronize()
+    _, _, active_list = vol.skip_list(0)
+    n_active = int(active_list.numel())
+
+    # ---- timed region: K whole-path steps ----
+    stats.zero_()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    launches0 = rp.kernel_launches()
+    barrier(dev)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start.record()
+    for i in range(args.steps):
+        step(rp, vol, wl, img, H, stats, wl.src, evs[i])
+    t_end.record()
+    torch.cuda.synchronize()
+    barrier(dev)
+    clk = clocks.stop()
+    launches = rp.kernel_launches() - launches0
+    elapsed_ms = t_start.elapsed_time(t_end)
+    render_ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    st = stats.cpu().numpy()
+    samples = float(st[0])
+    max_ms, all_samples = aggregate(elapsed_ms, samples, dev)
+    value = all_samples / (max_ms / 1e3)
+    ms_per_step = max_ms / args.steps
+
+    # ---- per-frame loop with the volume resident (brush edit + render + histograms) ----
+    fstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nframes = max(args.steps, 10)
+    torch.cuda.synchronize()
+    f0.record()
+    for _ in range(nframes):
+        vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)
+        vol.render(wl.cam, c["w"], c["h"], out=img, stats=fstats)
+        vol.pc_histogram(c["order"], wl.edges, use_brush=True, out=H)
+    f1.record()
+    torch.cuda.synchronize()
+    frame_ms = f0.elapsed_time(f1) / nframes
+
+    # ---- end to end through the C ABI from pinned host buffers ----
+    host_src = torch.empty(wl.src.shape, dtype=wl.src.dtype, pin_memory=True)
+    host_src.copy_(wl.src)
+    host_img = torch.empty(img.shape, dtype=img.dtype, pin_memory=True)
+    host_H = torch.empty(H.shape, dtype=H.dtype, pin_memory=True)
+    estats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        step(rp, vol, wl, img, H, estats, host_src)
+        host_img.copy_(img, non_blocking=True)
+        host_H.copy_(H, non_blocking=True)
+    torch.cuda.synchronize()
+    estats.zero_()
+    barrier(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(rp, vol, wl, img, H, estats, host_src)
+        host_img.copy_(img, non_blocking=True)
+        host_H.copy_(H, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_samples = float(estats[0].item())
+    e2e_max_ms, e2e_all = aggregate(e2e_ms, e2e_samples, dev)
+    small_h2d = wl.brush.lo.nbytes + wl.brush.hi.nbytes + wl.tf.rgbs.nbytes + wl.edges.nbytes + 4 * naxes
+    h2d = host_src.numel() * host_src.element_size() + small_h2d
+    d2h = host_img.numel() * host_img.element_size() + host_H.numel() * host_H.element_size()
+
+    # ---- roofline of the render kernel ----
+    peak, peak_kind = measured_peaks()
+    elem = 2 if c["store"] == "f16" else 4
+    alg_bytes = n_active * 8 ** 3 * 6 * elem + c["w"] * c["h"] * 16
+    achieved = alg_bytes / (render_ms / 1e3) / 1e9
+    roofline = {"kernel": "k_render", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_kind": f"{peak_kind} HBM copy", "render_ms": round(render_ms, 4),
+                "alg_bytes_per_launch": alg_bytes, "active_bricks": n_active}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "frames_per_s": round(1e3 / ms_per_step, 2),
+        "config": {**wl.describe(), "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (403 MB FP32 source re-ingested into a 537 MB stored volume every step)"},
+        "samples_per_step": samples / args.steps,
+        "frame_only": {"ms": round(frame_ms, 4), "fps": round(1e3 / frame_ms, 2),
+                       "samples_per_s": round(float(fstats[0].item()) / (frame_ms * nframes / 1e3), 1),
+                       "what": "brush edit + 1024^2 render + 5 PC histograms, volume resident"},
+        "e2e": {"value": round(e2e_all / (e2e_max_ms / 1e3), 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(e2e_max_ms / e2e_steps, 3)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+        "stats_per_step": {n: float(st[i]) / args.steps for i, n in enumerate(rp.STAT_NAMES)},
+    }
+    if ws == 1 and rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    vol.free()
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: baseline and reference arm
+# ---------------------------------------------------------------------------
+def oracle_frame_sample(wl, vol_np, rows, nthreads=0):
+    import oracle
+    c = wl.cfg
+    w, h = c["w"], c["h"]
+    pix = (np.asarray(rows, dtype=np.int64)[:, None] * w + np.arange(w)[None, :]).reshape(-1)
+    t0 = time.perf_counter()
+    _, cnt = oracle.render(vol_np, synth.R_IN, synth.R_OUT, wl.cam.as_array(), w, h, 1.0 / c["n"],
+                           wl.brush.lo, wl.brush.hi, wl.brush.active_mask, wl.tf.rgbs, wl.tf.color_var,
+                           wl.tf.v_lo, wl.tf.v_hi, ert=True, pixels=pix, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return float(cnt[:, 0].sum()), dt, len(pix)
+
+
+def cpu_baseline(wl, args):
+    import oracle
+    c = wl.cfg
+    vol_np = synth.to_storage(wl.src, c["store"]).float().cpu().numpy()
+    stride = args.cpu_row_stride
+    rows = list(range(stride // 2, c["h"], stride))
+    samples, dt, npix = oracle_frame_sample(wl, vol_np, rows)
+    return {"value": round(samples / dt, 1), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle render of every {stride}th row of the {c['w']}x{c['h']} frame "
+                      f"({npix} rays, {int(samples)} lattice samples, {dt:.2f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = Workload(args.workload, synth.DEFAULT_SEED, "cpu")
+    c = wl.cfg
+    vol_np = synth.to_storage(wl.src, c["store"]).float().numpy()
+    stride = args.ref_row_stride
+    for i in range(args.warmup):
+        oracle_frame_sample(wl, vol_np, [(i * 7) % c["h"]])
+    tot_samples, tot_t = 0.0, 0.0
+    for i in range(args.steps):
+        rows = list(range((i * 13) % stride, c["h"], stride))
+        s, dt, _ = oracle_frame_sample(wl, vol_np, rows)
+        tot_samples += s
+        tot_t += dt
+    value = tot_samples / tot_t
+    sample = (f"each step: FP64 oracle render of every {stride}th row of the {c['w']}x{c['h']} frame "
+              f"(rows offset per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(tot_t / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**wl.describe(), "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-row-stride", type=int, default=16)
+    ap.add_argument("--ref-row-stride", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

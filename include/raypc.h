@@ -136,6 +136,17 @@ raypc_status raypc_load_volume(raypc_ctx *ctx, const void *src, int src_is_devic
 
 raypc_status raypc_free_volume(raypc_ctx *ctx, int vol);
 
+/* Re-ingest new values of the same shape into level 0 of an existing volume
+ * (e.g. the next time step of the simulation, Section 2.1), with the source
+ * layout and conversion of raypc_load_volume. Allocates no device memory
+ * beyond a stream-ordered staging buffer for host sources. A pageable host
+ * source is consumed before the call returns; a pinned host source or a
+ * device source must stay valid until `stream` reaches the copy. Coarser
+ * levels, bricks and the classification become stale: raypc_build_bricks
+ * must run again before raypc_render (RAYPC_ERR_INVALID_ARG until then). */
+raypc_status raypc_update_volume(raypc_ctx *ctx, int vol, const void *src, int src_is_device,
+                                 int src_dtype, void *stream);
+
 /* Level of detail (Section 2.1: an octree-like pyramid with coarser levels of
  * 1/8 of the cells each) and brick min/max (Section 2.2: acceleration data
  * that a brush change does not rebuild). Builds n_lod (0..RAYPC_MAX_LOD)
@@ -213,6 +224,10 @@ raypc_status raypc_pc_histogram(raypc_ctx *ctx, int vol, int lod, const int *axi
 /* ---------------------------------------------------------------------- */
 /* Inspection (testing and tools)                                          */
 /* ---------------------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts, all devices); lets callers verify that work ran on the GPU. */
+raypc_status raypc_kernel_launches(unsigned long long *out);
 
 /* Geometry of a level: cube edge n, variables, storage dtype and bricks per axis. */
 raypc_status raypc_volume_info(raypc_ctx *ctx, int vol, int lod, int *out_n, int *out_nvars,

@@ -9,6 +9,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -18,9 +19,14 @@
 
 using namespace raypc;
 
+namespace raypc {
+void count_launches(int k);
+}
+
 namespace {
 
 thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
 
 raypc_status fail(raypc_status code, const char* fmt, ...) {
     char buf[512];
@@ -78,6 +84,7 @@ struct Level {
 
 struct Volume {
     int nvars = 0, vp = 0, dtype = 0;
+    bool stale = false;       // level 0 updated since the last build_bricks
     float r_in = 0.f, r_out = 1.f;
     int nlev = 0;             // built levels (1 + coarser)
     Level lv[1 + RAYPC_MAX_LOD];
@@ -161,11 +168,41 @@ raypc_status classify_level(Volume* V, Level& L, cudaStream_t s) {
     return RAYPC_OK;
 }
 
+raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_device, int src_dtype,
+                    cudaStream_t s) {
+    (void)ctx;
+    Level& L = V->lv[0];
+    const size_t nvox = (size_t)L.n * L.n * L.n;
+    const void* dsrc = src;
+    void* staging = nullptr;
+    cudaError_t e;
+    if (!src_is_device) {
+        size_t src_bytes = nvox * V->nvars * elem_size(src_dtype);
+        e = cudaMallocAsync(&staging, src_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
+        e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { cudaFreeAsync(staging, s); return cuda_fail(e, "host to device copy"); }
+        dsrc = staging;
+    }
+    e = launch_ingest(dsrc, src_dtype, L.data, V->dtype, V->vp, L.n, V->nvars, s);
+    if (staging) cudaFreeAsync(staging, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
+    return RAYPC_OK;
+}
+
 }  // namespace
+
+void raypc::count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 extern "C" {
 
 const char* raypc_last_error(void) { return g_err.c_str(); }
+
+raypc_status raypc_kernel_launches(unsigned long long* out) {
+    if (!out) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    *out = g_launches.load();
+    return RAYPC_OK;
+}
 
 raypc_status raypc_create(raypc_ctx** out, int device, size_t hbm_budget_bytes) {
     if (!out) return fail(RAYPC_ERR_INVALID_ARG, "out is NULL");
@@ -230,29 +267,32 @@ raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_devic
     L.data_bytes = nvox * V->vp * elem_size(store_dtype);
     raypc_status st = ctx->alloc(&L.data, L.data_bytes, &V->bytes);
     if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
-    const void* dsrc = src;
-    void* staging = nullptr;
-    size_t src_bytes = nvox * nvars * elem_size(src_dtype);
-    cudaError_t e;
+    st = ingest(ctx, V, src, src_is_device, src_dtype, s);
+    if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
     if (!src_is_device) {
-        e = cudaMallocAsync(&staging, src_bytes, s);
-        if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "staging allocation"); }
-        e = cudaMemcpyAsync(staging, src, src_bytes, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) { cudaFreeAsync(staging, s); free_volume(ctx, V); return cuda_fail(e, "host to device copy"); }
-        dsrc = staging;
-    }
-    e = launch_ingest(dsrc, src_dtype, L.data, store_dtype, V->vp, n, nvars, s);
-    if (staging) cudaFreeAsync(staging, s);
-    if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "ingest kernel"); }
-    if (!src_is_device) {
-        // the caller's host buffer may be pageable: finish before returning
-        e = cudaStreamSynchronize(s);
+        // keep the simple contract of this entry point: the host source is consumed on return
+        cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { free_volume(ctx, V); return cuda_fail(e, "ingest"); }
     }
     V->nlev = 1;
     int id = ctx->next_id++;
     ctx->vols[id] = V;
     *out_vol = id;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_update_volume(raypc_ctx* ctx, int vol, const void* src, int src_is_device,
+                                 int src_dtype, void* stream) {
+    if (!ctx || !src) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (src_dtype != RAYPC_F32 && src_dtype != RAYPC_F16) return fail(RAYPC_ERR_INVALID_ARG, "bad src_dtype");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    if ((st = ingest(ctx, V, src, src_is_device, src_dtype, (cudaStream_t)stream))) return st;
+    V->stale = true;
+    for (auto& L : V->lv) L.classified = false;
     return RAYPC_OK;
 }
 
@@ -317,6 +357,9 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
         L.classified = false;
         if (V->brush_set && (st = classify_level(V, L, s))) return st;
     }
+    for (int l = n_lod + 1; l <= RAYPC_MAX_LOD; ++l) V->lv[l].classified = V->lv[l].classified && !V->stale;
+    if (V->stale) V->nlev = 1 + n_lod;   // levels beyond n_lod were not rebuilt from the new data
+    V->stale = false;
     return RAYPC_OK;
 }
 
@@ -403,6 +446,7 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if (st) return st;
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
+    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run before render");
     if (!L->bricks || !L->classified) return fail(RAYPC_ERR_INVALID_ARG, "build_bricks and set_brush must run before render");
     if (!V->tf_set) return fail(RAYPC_ERR_INVALID_ARG, "set_tf must run before render");
     float dt = o.step > 0.f ? o.step : 1.0f / (float)L->n;
@@ -462,6 +506,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     for (int a = 0; a < naxes; ++a)
         if (axis_order[a] < 0 || axis_order[a] >= V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d", a, axis_order[a]);
     if (use_brush && !V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "use_brush needs raypc_set_brush");
+    if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
     cudaStream_t s = (cudaStream_t)stream;
     HistArgs h{};
     h.data = L->data;

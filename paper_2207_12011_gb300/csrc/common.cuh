@@ -161,6 +161,9 @@ struct HistArgs {
     uint32_t* out;                // (naxes-1) x bins x bins
 };
 
+// Process-wide count of launched kernels (defined in api.cu).
+void count_launches(int k);
+
 // Launchers (defined in the .cu files; all enqueue on `stream`).
 cudaError_t launch_ingest(const void* src, int src_dtype, void* dst, int dst_dtype, int vp,
                           int n, int nvars, cudaStream_t stream);

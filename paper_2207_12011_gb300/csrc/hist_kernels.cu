@@ -119,6 +119,7 @@ cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
     if (blocks < 1) blocks = 1;
     size_t smem = sizeof(float) * a.naxes * (a.bins + 1);
     k_hist<DT, VP><<<blocks, kHistThreads, smem, stream>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

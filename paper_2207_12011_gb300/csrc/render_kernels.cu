@@ -263,6 +263,7 @@ template <int DT, int VP>
 cudaError_t launch_t(const RenderArgs& a, cudaStream_t stream) {
     dim3 grid((a.w + kTileW - 1) / kTileW, (a.h + kTileH - 1) / kTileH);
     k_render<DT, VP><<<grid, kThreads, 0, stream>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

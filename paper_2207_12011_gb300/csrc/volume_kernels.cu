@@ -264,6 +264,7 @@ cudaError_t launch_ingest(const void* src, int src_dtype, void* dst, int dst_dty
                           int nvars, cudaStream_t stream) {
     size_t nvox = (size_t)n * n * n;
     k_ingest<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, src_dtype, dst, dst_dtype, vp, nvars, nvox);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -271,6 +272,7 @@ cudaError_t launch_export(const void* src, int dtype, int vp, void* dst, int n, 
                           cudaStream_t stream) {
     size_t nvox = (size_t)n * n * n;
     k_export<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, dtype, vp, dst, nvars, nvox);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -278,6 +280,7 @@ cudaError_t launch_lod(const void* src, int n_src, void* dst, int dtype, int vp,
                        cudaStream_t stream) {
     size_t m = (size_t)(n_src + 1) / 2;
     k_lod<<<blocks_for(m * m * m, 256), 256, 0, stream>>>(src, n_src, dst, dtype, vp, nvars);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -286,6 +289,7 @@ cudaError_t launch_brick_minmax(const void* data, int dtype, int vp, int n, int 
     size_t nb = (size_t)(n + kBrick - 1) / kBrick;
     size_t threads = nb * nb * nb * 32;
     k_brick_minmax<<<blocks_for(threads, 256), 256, 0, stream>>>(data, dtype, vp, n, nvars, bmin, bmax);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -308,6 +312,7 @@ cudaError_t launch_classify(const float* bmin, const float* bmax, int n, int nva
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_compact<<<1, 1024, 0, stream>>>(active, nwords, nbricks, list, n_active);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ _SIGS = {
     "raypc_memory_used": [_P, ctypes.POINTER(_SZ)],
     "raypc_load_volume": [_P, _P, _I, _I, _I, _I, _I, _I, _I, _F, _F, _P, ctypes.POINTER(_I)],
     "raypc_free_volume": [_P, _I],
+    "raypc_update_volume": [_P, _I, _P, _I, _I, _P],
+    "raypc_kernel_launches": [ctypes.POINTER(ctypes.c_ulonglong)],
     "raypc_build_bricks": [_P, _I, _I, _I, _P],
     "raypc_set_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_set_tf": [_P, _I, _P, _I, _F, _F, _P],
@@ -104,6 +106,13 @@ def _stream(stream) -> ctypes.c_void_p:
 
 def _fptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def kernel_launches() -> int:
+    """Kernels libraypc has launched in this process."""
+    out = ctypes.c_ulonglong()
+    _call("raypc_kernel_launches", ctypes.byref(out))
+    return int(out.value)
 
 
 def make_camera(eye, target, up, tan_half_vfov) -> Camera:
@@ -208,6 +217,15 @@ class Volume:
     def free(self):
         _call("raypc_free_volume", self.ctx.handle, self.id)
         self.id = -1
+
+    def update(self, vol: torch.Tensor, stream=None):
+        """Re-ingest new values of the same shape (device or host tensor); bricks become stale."""
+        src_dt = {torch.float32: RAYPC_F32, torch.float16: RAYPC_F16}[vol.dtype]
+        if not vol.is_contiguous():
+            raise ValueError("source must be contiguous")
+        _call("raypc_update_volume", self.ctx.handle, self.id, ctypes.c_void_p(vol.data_ptr()),
+              int(vol.is_cuda), src_dt, _stream(stream))
+        self._src = vol
 
     def build_bricks(self, n_lod: int = 0, stream=None):
         _call("raypc_build_bricks", self.ctx.handle, self.id, BRICK, int(n_lod), _stream(stream))
