@@ -67,8 +67,9 @@ struct DeviceGuard {
 
 struct Level {
     int n = 0, nb = 0;
-    void* data = nullptr;
-    size_t data_bytes = 0;
+    void* cells = nullptr;     // planar values, storage dtype
+    void* pairs = nullptr;     // per-variable x-pairs (render layout)
+    size_t cells_bytes = 0, pairs_bytes = 0;
     float* bmin = nullptr;
     float* bmax = nullptr;
     uint32_t* active = nullptr;
@@ -83,7 +84,7 @@ struct Level {
 };
 
 struct Volume {
-    int nvars = 0, vp = 0, dtype = 0;
+    int nvars = 0, dtype = 0;
     bool stale = false;       // level 0 updated since the last build_bricks
     float r_in = 0.f, r_out = 1.f;
     int nlev = 0;             // built levels (1 + coarser)
@@ -124,7 +125,7 @@ struct raypc_ctx {
 namespace {
 
 void free_level(Level& L) {
-    void* ptrs[] = {L.data, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
+    void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -184,7 +185,7 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
         if (e != cudaSuccess) { cudaFreeAsync(staging, s); return cuda_fail(e, "host to device copy"); }
         dsrc = staging;
     }
-    e = launch_ingest(dsrc, src_dtype, L.data, V->dtype, V->vp, L.n, V->nvars, s);
+    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, s);
     if (staging) cudaFreeAsync(staging, s);
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     return RAYPC_OK;
@@ -258,14 +259,15 @@ raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_devic
     Volume* V = new Volume();
     V->nvars = nvars;
     V->dtype = store_dtype;
-    V->vp = (store_dtype == RAYPC_F16) ? 8 : (nvars <= 4 ? 4 : 8);
     V->r_in = r_in;
     V->r_out = r_out;
     Level& L = V->lv[0];
     L.n = n;
     L.nb = (n + RAYPC_BRICK - 1) / RAYPC_BRICK;
-    L.data_bytes = nvox * V->vp * elem_size(store_dtype);
-    raypc_status st = ctx->alloc(&L.data, L.data_bytes, &V->bytes);
+    L.cells_bytes = nvox * nvars * elem_size(store_dtype);
+    L.pairs_bytes = 2 * L.cells_bytes;
+    raypc_status st = ctx->alloc(&L.cells, L.cells_bytes, &V->bytes);
+    if (st == RAYPC_OK) st = ctx->alloc(&L.pairs, L.pairs_bytes, &V->bytes);
     if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
     st = ingest(ctx, V, src, src_is_device, src_dtype, s);
     if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
@@ -325,14 +327,16 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
         Level& L = V->lv[l];
         int m = (P.n + 1) / 2;
         if (m < 2) return fail(RAYPC_ERR_INVALID_ARG, "level %d would have fewer than 2 cells per axis", l);
-        if (!L.data) {
+        if (!L.cells) {
             L.n = m;
             L.nb = (m + RAYPC_BRICK - 1) / RAYPC_BRICK;
-            L.data_bytes = (size_t)m * m * m * V->vp * elem_size(V->dtype);
-            st = ctx->alloc(&L.data, L.data_bytes, &V->bytes);
+            L.cells_bytes = (size_t)m * m * m * V->nvars * elem_size(V->dtype);
+            L.pairs_bytes = 2 * L.cells_bytes;
+            st = ctx->alloc(&L.cells, L.cells_bytes, &V->bytes);
+            if (st == RAYPC_OK) st = ctx->alloc(&L.pairs, L.pairs_bytes, &V->bytes);
             if (st) return st;
         }
-        CK(launch_lod(P.data, P.n, L.data, V->dtype, V->vp, V->nvars, s), "LOD kernel");
+        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, s), "LOD kernel");
     }
     V->nlev = 1 + n_lod > V->nlev ? 1 + n_lod : V->nlev;
     for (int l = 0; l <= n_lod; ++l) {
@@ -352,7 +356,7 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
                 return st;
             }
         }
-        CK(launch_brick_minmax(L.data, V->dtype, V->vp, L.n, V->nvars, L.bmin, L.bmax, s), "brick min/max kernel");
+        CK(launch_brick_minmax(L.cells, V->dtype, L.n, V->nvars, L.bmin, L.bmax, s), "brick min/max kernel");
         L.bricks = true;
         L.classified = false;
         if (V->brush_set && (st = classify_level(V, L, s))) return st;
@@ -453,7 +457,8 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if (!isfinite(dt) || dt < 2.0f * V->r_out / 4194304.0f)
         return fail(RAYPC_ERR_INVALID_ARG, "step %g too small (at most 2^21 samples per chord)", dt);
     RenderArgs a{};
-    a.lv.data = L->data;
+    a.lv.cells = L->cells;
+    a.lv.pairs = L->pairs;
     a.lv.n = L->n;
     a.lv.nb = L->nb;
     a.lv.bmin = L->bmin;
@@ -480,7 +485,7 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     a.out = reinterpret_cast<float4*>(out_rgba_dev);
     a.counts = o.counts_dev;
     a.stats = stats_dev;
-    CK(launch_render(a, V->dtype, V->vp, (cudaStream_t)stream), "render kernel");
+    CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }
 
@@ -509,7 +514,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
     cudaStream_t s = (cudaStream_t)stream;
     HistArgs h{};
-    h.data = L->data;
+    h.cells = L->cells;
     h.n = L->n;
     h.nvars = V->nvars;
     h.brush = V->brush;
@@ -517,6 +522,8 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     h.naxes = naxes;
     h.bins = bins;
     for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? axis_order[a] : 0;
+    h.need_mask = use_brush ? V->brush.mask : 0u;
+    for (int a = 0; a < naxes; ++a) h.need_mask |= 1u << axis_order[a];
     double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
     h.s_in = (int64_t)ceil(ri * ri);
     h.s_out = (int64_t)floor(ro * ro);
@@ -529,7 +536,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     if (e == cudaSuccess) {
         h.edges = dedges;
         h.out = out_counts_dev;
-        e = launch_histogram(h, V->dtype, V->vp, s);
+        e = launch_histogram(h, V->dtype, s);
     }
     cudaFreeAsync(dedges, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
@@ -561,7 +568,8 @@ raypc_status raypc_export_volume(raypc_ctx* ctx, int vol, int lod, void* out_dev
     if (st) return st;
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
-    CK(launch_export(L->data, V->dtype, V->vp, out_dev, L->n, V->nvars, (cudaStream_t)stream), "export kernel");
+    CK(cudaMemcpyAsync(out_dev, L->cells, L->cells_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+       "export copy");
     return RAYPC_OK;
 }
 

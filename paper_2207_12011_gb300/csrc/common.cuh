@@ -59,62 +59,47 @@ __device__ __forceinline__ float trilerp_rn(float c000, float c100, float c010, 
 }
 
 // ---------------------------------------------------------------------------
-// Storage layout. A level of a volume is n^3 vertices, each holding VP
-// element slots (VP >= nvars, padding is zero), x fastest:
-//   data[((z * n + y) * n + x) * VP + v]
-// FP16 levels use VP = 8 (one 16-byte vector per vertex); FP32 levels use
-// VP = 4 (one 16-byte vector, nvars <= 4) or VP = 8 (two vectors).
+// Storage layouts. Every level of a volume is kept twice in HBM:
+//  - cells: planar, one plane of n^3 values per variable in the storage
+//    dtype, x fastest: cells[((v * n + z) * n + y) * n + x]. Exactly the
+//    method's data; read by the histogram, brick min/max and LOD kernels.
+//  - pairs: per variable, the value at x and at min(x+1, n-1) side by side
+//    (float2 for FP32, half2 in one 32-bit word for FP16):
+//    pairs[((v * n + z) * n + y) * n + x] = (c[x], c[x+1]). One load fetches
+//    both x-corners of a trilinear cell, so a variable costs 4 loads per
+//    sample; read by the render kernel.
 // ---------------------------------------------------------------------------
 enum DType : int { kF32 = 0, kF16 = 1 };
 
-template <int DT, int VP> struct Vertex;
+template <int DT> struct Pair;
 
-template <> struct Vertex<kF16, 8> {
-    uint4 w;
-    __device__ __forceinline__ static Vertex load(const void* base, size_t idx) {
-        Vertex r;
-        r.w = __ldg(reinterpret_cast<const uint4*>(base) + idx);
-        return r;
-    }
-    template <int V> __device__ __forceinline__ float get() const {
-        uint32_t word = (V >> 1) == 0 ? w.x : (V >> 1) == 1 ? w.y : (V >> 1) == 2 ? w.z : w.w;
-        unsigned short bits = (V & 1) ? (unsigned short)(word >> 16) : (unsigned short)(word & 0xFFFFu);
-        return __half2float(__ushort_as_half(bits));
+template <> struct Pair<kF32> {
+    __device__ __forceinline__ static float2 load(const void* base, size_t idx) {
+        return __ldg(reinterpret_cast<const float2*>(base) + idx);
     }
 };
 
-template <> struct Vertex<kF32, 4> {
-    float4 a;
-    __device__ __forceinline__ static Vertex load(const void* base, size_t idx) {
-        Vertex r;
-        r.a = __ldg(reinterpret_cast<const float4*>(base) + idx);
-        return r;
-    }
-    template <int V> __device__ __forceinline__ float get() const {
-        return V == 0 ? a.x : V == 1 ? a.y : V == 2 ? a.z : a.w;
+template <> struct Pair<kF16> {
+    __device__ __forceinline__ static float2 load(const void* base, size_t idx) {
+        unsigned w = __ldg(reinterpret_cast<const unsigned*>(base) + idx);
+        return __half22float2(*reinterpret_cast<const __half2*>(&w));
     }
 };
 
-template <> struct Vertex<kF32, 8> {
-    float4 a, b;
-    __device__ __forceinline__ static Vertex load(const void* base, size_t idx) {
-        Vertex r;
-        const float4* p = reinterpret_cast<const float4*>(base) + 2 * idx;
-        r.a = __ldg(p);
-        r.b = __ldg(p + 1);
-        return r;
-    }
-    template <int V> __device__ __forceinline__ float get() const {
-        return V == 0 ? a.x : V == 1 ? a.y : V == 2 ? a.z : V == 3 ? a.w
-             : V == 4 ? b.x : V == 5 ? b.y : V == 6 ? b.z : b.w;
-    }
-};
+template <int DT> __device__ __forceinline__ float load_cell(const void* base, size_t idx);
+template <> __device__ __forceinline__ float load_cell<kF32>(const void* base, size_t idx) {
+    return __ldg(reinterpret_cast<const float*>(base) + idx);
+}
+template <> __device__ __forceinline__ float load_cell<kF16>(const void* base, size_t idx) {
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(base) + idx)));
+}
 
 // ---------------------------------------------------------------------------
 // Kernel argument blocks.
 // ---------------------------------------------------------------------------
 struct LevelArgs {
-    const void* data;          // interleaved vertices
+    const void* cells;         // planar values
+    const void* pairs;         // x-pairs per variable
     int n;                     // cube edge in cells
     int nb;                    // bricks per axis
     const float* bmin;         // [nb^3][nvars]
@@ -149,11 +134,12 @@ struct RenderArgs {
 };
 
 struct HistArgs {
-    const void* data;
+    const void* cells;
     int n;
     int nvars;
     BrushArgs brush;
     int use_brush;
+    unsigned need_mask;           // variables the kernel must load (brushed and axes)
     int naxes, bins;
     int axis[kMaxVars];
     const float* edges;           // naxes x (bins + 1), device
@@ -165,19 +151,17 @@ struct HistArgs {
 void count_launches(int k);
 
 // Launchers (defined in the .cu files; all enqueue on `stream`).
-cudaError_t launch_ingest(const void* src, int src_dtype, void* dst, int dst_dtype, int vp,
+cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype,
                           int n, int nvars, cudaStream_t stream);
-cudaError_t launch_export(const void* src, int dtype, int vp, void* dst, int n, int nvars,
-                          cudaStream_t stream);
-cudaError_t launch_lod(const void* src, int n_src, void* dst, int dtype, int vp, int nvars,
+cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
                        cudaStream_t stream);
-cudaError_t launch_brick_minmax(const void* data, int dtype, int vp, int n, int nvars,
-                                float* bmin, float* bmax, cudaStream_t stream);
+cudaError_t launch_brick_minmax(const void* cells, int dtype, int n, int nvars, float* bmin,
+                                float* bmax, cudaStream_t stream);
 cudaError_t launch_classify(const float* bmin, const float* bmax, int n, int nvars, float r_in,
                             float r_out, const BrushArgs& brush, uint32_t* active,
                             uint32_t* skippable, uint32_t* list, uint32_t* n_active,
                             unsigned* pass_count, cudaStream_t stream);
-cudaError_t launch_render(const RenderArgs& a, int dtype, int vp, cudaStream_t stream);
-cudaError_t launch_histogram(const HistArgs& a, int dtype, int vp, cudaStream_t stream);
+cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
+cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
 }  // namespace raypc

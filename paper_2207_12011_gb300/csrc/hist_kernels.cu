@@ -3,7 +3,7 @@
 // of adjacent axes (a, a+1), H[a][bin_a][bin_{a+1}] += 1.
 //
 // HBM-bound scan. A warp walks one x-row of cells at a time (lanes over x), so
-// the interleaved vertex loads are fully coalesced; rows whose cells all lie
+// the planar loads of the needed variables are fully coalesced; rows whose cells all lie
 // outside the shell are skipped without touching memory. The in-shell test is
 // integer-exact. Bins come from a binary search over the FP32 edges held in
 // shared memory (comparisons only, so exact). Increments are aggregated per
@@ -28,7 +28,7 @@ __device__ __forceinline__ int bin_of(const float* e, int bins, float v) {
     return lo;
 }
 
-template <int DT, int VP>
+template <int DT>
 __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
     extern __shared__ float s_edges[];
     const int ne = A.naxes * (A.bins + 1);
@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int bins = A.bins;
+    const size_t plane = (size_t)n * n * n;
 
     for (long long r = gwarp; r < rows; r += nwarps) {
         const int y = (int)(r % n), z = (int)(r / n);
@@ -56,20 +57,10 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
                 const long long dx = 2 * x + 1 - n;
                 const long long s = dx * dx + syz;
                 if (s >= A.s_in && s <= A.s_out) {
-                    const Vertex<DT, VP> vx = Vertex<DT, VP>::load(A.data, row_base + x);
                     float val[kMaxVars];
-                    val[0] = vx.template get<0>();
-                    val[1] = vx.template get<1>();
-                    val[2] = vx.template get<2>();
-                    val[3] = vx.template get<3>();
-                    if (VP > 4) {
-                        val[4] = vx.template get<(VP > 4 ? 4 : 0)>();
-                        val[5] = vx.template get<(VP > 4 ? 5 : 0)>();
-                        val[6] = vx.template get<(VP > 4 ? 6 : 0)>();
-                        val[7] = vx.template get<(VP > 4 ? 7 : 0)>();
-                    } else {
-                        val[4] = val[5] = val[6] = val[7] = 0.0f;
-                    }
+#pragma unroll
+                    for (int v = 0; v < kMaxVars; ++v)
+                        val[v] = ((A.need_mask >> v) & 1u) ? load_cell<DT>(A.cells, v * plane + row_base + x) : 0.0f;
                     keep = true;
                     if (A.use_brush) {
 #pragma unroll
@@ -108,7 +99,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
     }
 }
 
-template <int DT, int VP>
+template <int DT>
 cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -118,17 +109,16 @@ cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
     int blocks = (int)(want_blocks < (long long)sms * 8 ? want_blocks : (long long)sms * 8);
     if (blocks < 1) blocks = 1;
     size_t smem = sizeof(float) * a.naxes * (a.bins + 1);
-    k_hist<DT, VP><<<blocks, kHistThreads, smem, stream>>>(a);
+    k_hist<DT><<<blocks, kHistThreads, smem, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_histogram(const HistArgs& a, int dtype, int vp, cudaStream_t stream) {
-    if (dtype == kF16) return launch_t<kF16, 8>(a, stream);
-    if (vp == 4) return launch_t<kF32, 4>(a, stream);
-    return launch_t<kF32, 8>(a, stream);
+cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream) {
+    if (dtype == kF16) return launch_t<kF16>(a, stream);
+    return launch_t<kF32>(a, stream);
 }
 
 }  // namespace raypc

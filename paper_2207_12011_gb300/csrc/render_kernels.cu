@@ -7,8 +7,8 @@
 // cannot pass the brush or the shell test), shell test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
 // selective first; the order cannot change the result), each as an FP32
-// trilinear interpolation of the corner vertices, with exit on the first
-// failure. Kept samples are coloured by the transfer function (from shared
+// trilinear interpolation from four x-pair loads of that variable only, with
+// exit on the first failure. Kept samples are coloured by the transfer function (from shared
 // memory) and composited front to back with early ray termination.
 //
 // Empty-space skipping: when a sample falls in a skippable brick (inactive
@@ -43,33 +43,24 @@ __device__ __forceinline__ bool bit_of(const uint32_t* bits, uint32_t id) {
     return (__ldg(bits + (id >> 5)) >> (id & 31)) & 1u;
 }
 
-template <int DT, int VP, int V>
-__device__ __forceinline__ float interp_var(const Vertex<DT, VP> (&c)[8], float fx, float fy, float fz) {
-    // corner index = dx + 2 dy + 4 dz
-    return trilerp_rn(c[0].template get<V>(), c[1].template get<V>(), c[2].template get<V>(),
-                      c[3].template get<V>(), c[4].template get<V>(), c[5].template get<V>(),
-                      c[6].template get<V>(), c[7].template get<V>(), fx, fy, fz);
+// FP32 trilinear value of one variable: four pair loads give the 8 corners
+// (x0, x0+1) at (y0,z0), (y1,z0), (y0,z1), (y1,z1).
+template <int DT>
+__device__ __forceinline__ float interp_var(const void* plane, size_t base, size_t sy, size_t sz,
+                                            float fx, float fy, float fz) {
+    const float2 a = Pair<DT>::load(plane, base);
+    const float2 b = Pair<DT>::load(plane, base + sy);
+    const float2 c = Pair<DT>::load(plane, base + sz);
+    const float2 d = Pair<DT>::load(plane, base + sz + sy);
+    return trilerp_rn(a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, fx, fy, fz);
 }
 
-// Interpolate variable v (warp-uniform value) with compile-time register
-// selection: the switch is a uniform branch, no dynamic register indexing.
-template <int DT, int VP>
-__device__ __forceinline__ float interp_dyn(int v, const Vertex<DT, VP> (&c)[8], float fx, float fy, float fz) {
-    switch (v) {
-        case 0: return interp_var<DT, VP, 0>(c, fx, fy, fz);
-        case 1: return interp_var<DT, VP, 1>(c, fx, fy, fz);
-        case 2: return interp_var<DT, VP, 2>(c, fx, fy, fz);
-        case 3: return interp_var<DT, VP, 3>(c, fx, fy, fz);
-        case 4: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 4 : 0)>(c, fx, fy, fz); break;
-        case 5: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 5 : 0)>(c, fx, fy, fz); break;
-        case 6: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 6 : 0)>(c, fx, fy, fz); break;
-        case 7: if (VP > 4) return interp_var<DT, VP, (VP > 4 ? 7 : 0)>(c, fx, fy, fz); break;
-        default: break;
-    }
-    return 0.0f;
+__device__ __forceinline__ const void* plane_ptr(const void* pairs, int DT, int v, size_t plane_elems) {
+    const size_t bytes = (DT == kF16 ? 4 : 8) * plane_elems * (size_t)v;
+    return reinterpret_cast<const char*>(pairs) + bytes;
 }
 
-template <int DT, int VP>
+template <int DT>
 __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
     __shared__ float4 s_tf[kTF];
     __shared__ int s_order[kMaxVars];
@@ -137,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
             const int n = A.lv.n, nb = A.lv.nb;
             const float hn = 0.5f * (float)n, off = hn - 0.5f;
             const float dt = A.dt;
-            const size_t sy_ = (size_t)n, sz_ = (size_t)n * n;
+            const size_t sy_ = (size_t)n, sz_ = (size_t)n * n, plane = sz_ * n;
             const int nact = s_nact;
             int k = 0;
             for (;;) {
@@ -191,29 +182,20 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
                 }
                 const float r2 = dot3_rn(pxw, pyw, pzw, pxw, pyw, pzw);
                 if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
-                // fetch the 8 corner vertices (all variables at once)
                 const size_t base = ((size_t)iz * n + iy) * n + ix;
-                Vertex<DT, VP> c[8];
-                c[0] = Vertex<DT, VP>::load(A.lv.data, base);
-                c[1] = Vertex<DT, VP>::load(A.lv.data, base + 1);
-                c[2] = Vertex<DT, VP>::load(A.lv.data, base + sy_);
-                c[3] = Vertex<DT, VP>::load(A.lv.data, base + sy_ + 1);
-                c[4] = Vertex<DT, VP>::load(A.lv.data, base + sz_);
-                c[5] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + 1);
-                c[6] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + sy_);
-                c[7] = Vertex<DT, VP>::load(A.lv.data, base + sz_ + sy_ + 1);
                 ++evald;
                 bool pass = true;
                 float vc = 0.0f;
                 bool have_c = false;
                 for (int j = 0; j < nact; ++j) {
                     const int v = s_order[j];
-                    const float s = interp_dyn<DT, VP>(v, c, fx, fy, fz);
+                    const float s = interp_var<DT>(plane_ptr(A.lv.pairs, DT, v, plane), base, sy_, sz_, fx, fy, fz);
                     if (!(s >= s_lo[v] && s <= s_hi[v])) { pass = false; break; }
                     if (v == A.color_var) { vc = s; have_c = true; }
                 }
                 if (!pass) { ++k; continue; }
-                if (!have_c) vc = interp_dyn<DT, VP>(A.color_var, c, fx, fy, fz);
+                if (!have_c)
+                    vc = interp_var<DT>(plane_ptr(A.lv.pairs, DT, A.color_var, plane), base, sy_, sz_, fx, fy, fz);
                 ++kept;
                 // transfer function (continuous; no rounding contract needed)
                 float sp = (vc - A.tf_lo) * A.tf_scale;
@@ -259,20 +241,19 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
     }
 }
 
-template <int DT, int VP>
+template <int DT>
 cudaError_t launch_t(const RenderArgs& a, cudaStream_t stream) {
     dim3 grid((a.w + kTileW - 1) / kTileW, (a.h + kTileH - 1) / kTileH);
-    k_render<DT, VP><<<grid, kThreads, 0, stream>>>(a);
+    k_render<DT><<<grid, kThreads, 0, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_render(const RenderArgs& a, int dtype, int vp, cudaStream_t stream) {
-    if (dtype == kF16) return launch_t<kF16, 8>(a, stream);
-    if (vp == 4) return launch_t<kF32, 4>(a, stream);
-    return launch_t<kF32, 8>(a, stream);
+cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream) {
+    if (dtype == kF16) return launch_t<kF16>(a, stream);
+    return launch_t<kF32>(a, stream);
 }
 
 }  // namespace raypc

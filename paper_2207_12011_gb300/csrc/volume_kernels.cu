@@ -1,4 +1,4 @@
-// Volume preparation kernels: ingest/relayout, export, level-of-detail mean,
+// Volume preparation kernels: ingest/relayout, level-of-detail mean,
 // brick min/max and brush classification of bricks.
 //
 // Section 2.1 of the paper prepares the data once (levels of detail, derived
@@ -15,88 +15,69 @@ __device__ __forceinline__ float load_src(const void* src, int dtype, size_t i) 
     return reinterpret_cast<const float*>(src)[i];
 }
 
-__device__ __forceinline__ float load_slot(const void* data, int dtype, int vp, size_t vtx, int v) {
-    if (dtype == kF16) return __half2float(reinterpret_cast<const __half*>(data)[vtx * vp + v]);
-    return reinterpret_cast<const float*>(data)[vtx * vp + v];
+// Store one value of a level: planar cell plus its two pair slots (as the
+// left element of its own pair and the right element of the pair at x-1;
+// the last x also fills its own right element).
+template <int DT>
+__device__ __forceinline__ void store_value(void* cells, void* pairs, size_t i, int x, int n, float v);
+
+template <>
+__device__ __forceinline__ void store_value<kF32>(void* cells, void* pairs, size_t i, int x, int n, float v) {
+    reinterpret_cast<float*>(cells)[i] = v;
+    float* p = reinterpret_cast<float*>(pairs);
+    p[2 * i] = v;
+    if (x > 0) p[2 * (i - 1) + 1] = v;
+    if (x == n - 1) p[2 * i + 1] = v;
 }
 
-__device__ __forceinline__ void store_slot(void* data, int dtype, int vp, size_t vtx, int v, float x) {
-    if (dtype == kF16)
-        reinterpret_cast<__half*>(data)[vtx * vp + v] = __float2half_rn(x);
-    else
-        reinterpret_cast<float*>(data)[vtx * vp + v] = x;
+template <>
+__device__ __forceinline__ void store_value<kF16>(void* cells, void* pairs, size_t i, int x, int n, float v) {
+    __half h = __float2half_rn(v);
+    reinterpret_cast<__half*>(cells)[i] = h;
+    __half* p = reinterpret_cast<__half*>(pairs);
+    p[2 * i] = h;
+    if (x > 0) p[2 * (i - 1) + 1] = h;
+    if (x == n - 1) p[2 * i + 1] = h;
 }
 
-// One thread per vertex: gather the nvars planar values, write one interleaved
-// vertex (VP slots, padding zero). Planar reads and vertex writes are both
+// One thread per (variable, cell): convert the source value to the storage
+// dtype and write the planar cell and both pair slots. Reads and writes are
 // coalesced along x.
-__global__ void k_ingest(const void* __restrict__ src, int src_dtype, void* __restrict__ dst,
-                         int dst_dtype, int vp, int nvars, size_t nvox) {
+template <int DT>
+__global__ void k_ingest(const void* __restrict__ src, int src_dtype, void* __restrict__ cells,
+                         void* __restrict__ pairs, int n, size_t total) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nvox) return;
-    float v[kMaxVars];
-#pragma unroll
-    for (int k = 0; k < kMaxVars; ++k) v[k] = (k < nvars) ? load_src(src, src_dtype, (size_t)k * nvox + i) : 0.0f;
-    if (dst_dtype == kF16) {
-        uint32_t w[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t lo = __half_as_ushort(__float2half_rn(v[2 * k]));
-            uint32_t hi = __half_as_ushort(__float2half_rn(v[2 * k + 1]));
-            w[k] = lo | (hi << 16);
-        }
-        reinterpret_cast<uint4*>(dst)[i] = make_uint4(w[0], w[1], w[2], w[3]);
-    } else if (vp == 4) {
-        reinterpret_cast<float4*>(dst)[i] = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-        float4* d = reinterpret_cast<float4*>(dst) + 2 * i;
-        d[0] = make_float4(v[0], v[1], v[2], v[3]);
-        d[1] = make_float4(v[4], v[5], v[6], v[7]);
-    }
-}
-
-__global__ void k_export(const void* __restrict__ src, int dtype, int vp, void* __restrict__ dst,
-                         int nvars, size_t nvox) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nvox) return;
-    for (int k = 0; k < nvars; ++k) {
-        if (dtype == kF16)
-            reinterpret_cast<__half*>(dst)[(size_t)k * nvox + i] = reinterpret_cast<const __half*>(src)[i * vp + k];
-        else
-            reinterpret_cast<float*>(dst)[(size_t)k * nvox + i] = reinterpret_cast<const float*>(src)[i * vp + k];
-    }
+    if (i >= total) return;
+    int x = (int)(i % n);
+    store_value<DT>(cells, pairs, i, x, n, load_src(src, src_dtype, i));
 }
 
 // Coarse cell = FP32 mean of its 2x2x2 fine cells (fine indices clamped):
-// ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
-__global__ void k_lod(const void* __restrict__ src, int n, void* __restrict__ dst, int dtype,
-                      int vp, int nvars) {
-    int m = (n + 1) / 2;
+// ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8,
+// then rounded to the storage dtype. One thread per (variable, coarse cell).
+template <int DT>
+__global__ void k_lod(const void* __restrict__ fine, int n, void* __restrict__ cells,
+                      void* __restrict__ pairs, int nvars) {
+    const int m = (n + 1) / 2;
+    const size_t mm = (size_t)m * m * m;
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t total = (size_t)m * m * m;
-    if (i >= total) return;
-    int x = (int)(i % m), y = (int)((i / m) % m), z = (int)(i / ((size_t)m * m));
-    int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
-    int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1), z1 = min(z0 + 1, n - 1);
-    auto vid = [&](int a, int b, int c) { return ((size_t)c * n + b) * n + a; };
-    size_t v000 = vid(x0, y0, z0), v100 = vid(x1, y0, z0), v010 = vid(x0, y1, z0), v110 = vid(x1, y1, z0);
-    size_t v001 = vid(x0, y0, z1), v101 = vid(x1, y0, z1), v011 = vid(x0, y1, z1), v111 = vid(x1, y1, z1);
-    for (int k = 0; k < vp; ++k) {
-        float r = 0.0f;
-        if (k < nvars) {
-            float s0 = __fadd_rn(__fadd_rn(load_slot(src, dtype, vp, v000, k), load_slot(src, dtype, vp, v100, k)),
-                                 __fadd_rn(load_slot(src, dtype, vp, v010, k), load_slot(src, dtype, vp, v110, k)));
-            float s1 = __fadd_rn(__fadd_rn(load_slot(src, dtype, vp, v001, k), load_slot(src, dtype, vp, v101, k)),
-                                 __fadd_rn(load_slot(src, dtype, vp, v011, k), load_slot(src, dtype, vp, v111, k)));
-            r = __fmul_rn(__fadd_rn(s0, s1), 0.125f);
-        }
-        store_slot(dst, dtype, vp, i, k, r);
-    }
+    if (i >= mm * nvars) return;
+    const int v = (int)(i / mm);
+    const size_t c = i % mm;
+    const int x = (int)(c % m), y = (int)((c / m) % m), z = (int)(c / ((size_t)m * m));
+    const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
+    const int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1), z1 = min(z0 + 1, n - 1);
+    const size_t plane = (size_t)v * n * n * n;
+    auto at = [&](int a, int b, int cz) { return load_cell<DT>(fine, plane + ((size_t)cz * n + b) * n + a); };
+    float s0 = __fadd_rn(__fadd_rn(at(x0, y0, z0), at(x1, y0, z0)), __fadd_rn(at(x0, y1, z0), at(x1, y1, z0)));
+    float s1 = __fadd_rn(__fadd_rn(at(x0, y0, z1), at(x1, y0, z1)), __fadd_rn(at(x0, y1, z1), at(x1, y1, z1)));
+    store_value<DT>(cells, pairs, i, x, m, __fmul_rn(__fadd_rn(s0, s1), 0.125f));
 }
 
 // One warp per brick: the 32 lanes stride over the brick's (up to) 9^3
 // vertices, keep running NaN-ignoring min/max per variable, then reduce.
-__global__ void k_brick_minmax(const void* __restrict__ data, int dtype, int vp, int n, int nvars,
+template <int DT>
+__global__ void k_brick_minmax(const void* __restrict__ cells, int n, int nvars,
                                float* __restrict__ bmin, float* __restrict__ bmax) {
     int nb = (n + kBrick - 1) / kBrick;
     size_t nbricks = (size_t)nb * nb * nb;
@@ -109,35 +90,23 @@ __global__ void k_brick_minmax(const void* __restrict__ data, int dtype, int vp,
     int ey = min(y0 + kBrick, n - 1) - y0 + 1;
     int ez = min(z0 + kBrick, n - 1) - z0 + 1;
     int cnt = ex * ey * ez;
-    float mn[kMaxVars], mx[kMaxVars];
-#pragma unroll
-    for (int k = 0; k < kMaxVars; ++k) { mn[k] = __int_as_float(0x7fffffff); mx[k] = mn[k]; }
-    for (int j = lane; j < cnt; j += 32) {
-        int dx = j % ex, dy = (j / ex) % ey, dz = j / (ex * ey);
-        size_t vtx = ((size_t)(z0 + dz) * n + (y0 + dy)) * n + (x0 + dx);
-#pragma unroll
-        for (int k = 0; k < kMaxVars; ++k) {
-            if (k < nvars) {
-                float a = load_slot(data, dtype, vp, vtx, k);
-                mn[k] = fminf(mn[k], a);
-                mx[k] = fmaxf(mx[k], a);
-            }
+    const size_t plane = (size_t)n * n * n;
+    for (int v = 0; v < nvars; ++v) {
+        float mn = __int_as_float(0x7fffffff), mx = mn;
+        for (int j = lane; j < cnt; j += 32) {
+            int dx = j % ex, dy = (j / ex) % ey, dz = j / (ex * ey);
+            float a = load_cell<DT>(cells, v * plane + ((size_t)(z0 + dz) * n + (y0 + dy)) * n + (x0 + dx));
+            mn = fminf(mn, a);
+            mx = fmaxf(mx, a);
         }
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxVars; ++k) {
         for (int o = 16; o > 0; o >>= 1) {
-            mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
-            mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
-    }
-    if (lane < nvars) {
-        float a = mn[0], b = mx[0];
-#pragma unroll
-        for (int k = 1; k < kMaxVars; ++k)
-            if (lane == k) { a = mn[k]; b = mx[k]; }
-        bmin[warp * nvars + lane] = a;
-        bmax[warp * nvars + lane] = b;
+        if (lane == 0) {
+            bmin[warp * nvars + v] = mn;
+            bmax[warp * nvars + v] = mx;
+        }
     }
 }
 
@@ -260,35 +229,37 @@ inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / 
 
 }  // namespace
 
-cudaError_t launch_ingest(const void* src, int src_dtype, void* dst, int dst_dtype, int vp, int n,
+cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype, int n,
                           int nvars, cudaStream_t stream) {
-    size_t nvox = (size_t)n * n * n;
-    k_ingest<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, src_dtype, dst, dst_dtype, vp, nvars, nvox);
+    size_t total = (size_t)n * n * n * nvars;
+    if (dtype == kF16)
+        k_ingest<kF16><<<blocks_for(total, 256), 256, 0, stream>>>(src, src_dtype, cells, pairs, n, total);
+    else
+        k_ingest<kF32><<<blocks_for(total, 256), 256, 0, stream>>>(src, src_dtype, cells, pairs, n, total);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_export(const void* src, int dtype, int vp, void* dst, int n, int nvars,
-                          cudaStream_t stream) {
-    size_t nvox = (size_t)n * n * n;
-    k_export<<<blocks_for(nvox, 256), 256, 0, stream>>>(src, dtype, vp, dst, nvars, nvox);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lod(const void* src, int n_src, void* dst, int dtype, int vp, int nvars,
+cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
                        cudaStream_t stream) {
-    size_t m = (size_t)(n_src + 1) / 2;
-    k_lod<<<blocks_for(m * m * m, 256), 256, 0, stream>>>(src, n_src, dst, dtype, vp, nvars);
+    size_t m = (size_t)(n_fine + 1) / 2;
+    size_t total = m * m * m * nvars;
+    if (dtype == kF16)
+        k_lod<kF16><<<blocks_for(total, 256), 256, 0, stream>>>(fine, n_fine, cells, pairs, nvars);
+    else
+        k_lod<kF32><<<blocks_for(total, 256), 256, 0, stream>>>(fine, n_fine, cells, pairs, nvars);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_brick_minmax(const void* data, int dtype, int vp, int n, int nvars, float* bmin,
-                                float* bmax, cudaStream_t stream) {
+cudaError_t launch_brick_minmax(const void* cells, int dtype, int n, int nvars, float* bmin, float* bmax,
+                                cudaStream_t stream) {
     size_t nb = (size_t)(n + kBrick - 1) / kBrick;
     size_t threads = nb * nb * nb * 32;
-    k_brick_minmax<<<blocks_for(threads, 256), 256, 0, stream>>>(data, dtype, vp, n, nvars, bmin, bmax);
+    if (dtype == kF16)
+        k_brick_minmax<kF16><<<blocks_for(threads, 256), 256, 0, stream>>>(cells, n, nvars, bmin, bmax);
+    else
+        k_brick_minmax<kF32><<<blocks_for(threads, 256), 256, 0, stream>>>(cells, n, nvars, bmin, bmax);
     count_launches(1);
     return cudaGetLastError();
 }
