@@ -195,6 +195,10 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
 
 void raypc::count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
+namespace raypc {
+void set_last_error(const char* msg) { g_err = msg; }
+}
+
 extern "C" {
 
 const char* raypc_last_error(void) { return g_err.c_str(); }

@@ -65,6 +65,7 @@ _SIGS = {
     "raypc_export_volume": [_P, _I, _I, _P, _P],
     "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
     "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
+    "raypc_pc_histogram_noalloc": [_P, _I, _I, _I, _F, _F, _P, _P, _U32, _I, _P, _I, _I, _P, _P, _P],
 }
 
 
@@ -309,6 +310,31 @@ class Volume:
               ctypes.c_void_p(cnt.data_ptr()), _stream(stream))
         n_active = int(cnt.item())
         return act, skp, lst[:n_active]
+
+
+def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=None, active_mask: int = 0,
+                         use_brush: bool = False, r_in: float = 0.547, r_out: float = 1.0,
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """raypc_pc_histogram_noalloc on a caller-owned planar (nvars, n, n, n) device field.
+
+    The library allocates nothing for this call (the output is the caller's too:
+    pass `out` to keep the whole call allocation-free on the torch side).
+    """
+    if not cells.is_cuda or cells.dim() != 4 or not cells.is_contiguous():
+        raise ValueError("cells must be a contiguous (nvars, n, n, n) CUDA tensor")
+    dt = {torch.float32: RAYPC_F32, torch.float16: RAYPC_F16}[cells.dtype]
+    nv, n = cells.shape[0], cells.shape[-1]
+    order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32))
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
+    naxes, bins = e.shape[0], e.shape[1] - 1
+    lo_a = np.ascontiguousarray(np.asarray(lo if lo is not None else np.full(nv, -np.inf), dtype=np.float32)[:nv])
+    hi_a = np.ascontiguousarray(np.asarray(hi if hi is not None else np.full(nv, np.inf), dtype=np.float32)[:nv])
+    if out is None:
+        out = torch.empty((naxes - 1, bins, bins), dtype=torch.int32, device=cells.device)
+    _call("raypc_pc_histogram_noalloc", ctypes.c_void_p(cells.data_ptr()), dt, n, nv, float(r_in),
+          float(r_out), _fptr(lo_a), _fptr(hi_a), int(active_mask) & 0xFFFFFFFF, int(bool(use_brush)),
+          _fptr(order), naxes, bins, _fptr(e), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    return out
 
 
 def unpack_bits(words: torch.Tensor, nbits: int) -> np.ndarray:
