@@ -14,7 +14,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/raypc.h"
+#include "raypc.h"
 #include "common.cuh"
 
 using namespace raypc;
@@ -161,11 +161,54 @@ raypc_status get_level(Volume* V, int lod, Level** out) {
     return RAYPC_OK;
 }
 
-raypc_status classify_level(Volume* V, Level& L, cudaStream_t s) {
-    CK(launch_classify(L.bmin, L.bmax, L.n, V->nvars, V->r_in, V->r_out, V->brush, L.active,
-                       L.skippable, L.list, L.n_active, L.pass_count, s),
-       "classify kernels");
-    L.classified = true;
+// Classify every built level under the current brush (three launches total).
+raypc_status classify_all(Volume* V, cudaStream_t s) {
+    ClassifyArgs c{};
+    c.nvars = V->nvars;
+    c.rin2 = V->r_in * V->r_in;
+    c.rout2 = V->r_out * V->r_out;
+    c.brush = V->brush;
+    for (int l = 0; l < V->nlev; ++l) {
+        Level& L = V->lv[l];
+        if (!L.bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d are not built", l);
+        ClassifyLevel& C = c.lv[c.nlev++];
+        C.bmin = L.bmin;
+        C.bmax = L.bmax;
+        C.n = L.n;
+        C.active = L.active;
+        C.skippable = L.skippable;
+        C.list = L.list;
+        C.n_active = L.n_active;
+        C.pass_count = L.pass_count;
+    }
+    CK(launch_classify(c, s), "classify kernels");
+    for (int l = 0; l < V->nlev; ++l) V->lv[l].classified = true;
+    return RAYPC_OK;
+}
+
+// Lazily classify when a brush is set but the bricks changed since.
+raypc_status ensure_classified(Volume* V, Level& L, cudaStream_t s) {
+    if (L.classified) return RAYPC_OK;
+    if (!V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "raypc_set_brush must run first");
+    return classify_all(V, s);
+}
+
+raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
+    if (L.bmin) return RAYPC_OK;
+    size_t nbk = L.nbricks();
+    size_t mm = nbk * V->nvars * sizeof(float);
+    size_t words = L.nwords() * sizeof(uint32_t);
+    raypc_status st;
+    if ((st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.bmax, mm, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.active, words, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.skippable, words, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.list, nbk * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.n_active, sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.pass_count, sizeof(unsigned) * kMaxVars, &V->bytes))) {
+        free_bricks(L);
+        return st;
+    }
     return RAYPC_OK;
 }
 
@@ -185,9 +228,11 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
         if (e != cudaSuccess) { cudaFreeAsync(staging, s); return cuda_fail(e, "host to device copy"); }
         dsrc = staging;
     }
-    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, s);
+    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, s);
     if (staging) cudaFreeAsync(staging, s);
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
+    L.bricks = true;               // level-0 brick min/max come out of the ingest pass
+    for (auto& l : V->lv) l.classified = false;
     return RAYPC_OK;
 }
 
@@ -272,6 +317,7 @@ raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_devic
     L.pairs_bytes = 2 * L.cells_bytes;
     raypc_status st = ctx->alloc(&L.cells, L.cells_bytes, &V->bytes);
     if (st == RAYPC_OK) st = ctx->alloc(&L.pairs, L.pairs_bytes, &V->bytes);
+    if (st == RAYPC_OK) st = alloc_bricks(ctx, V, L);
     if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
     st = ingest(ctx, V, src, src_is_device, src_dtype, s);
     if (st != RAYPC_OK) { free_volume(ctx, V); return st; }
@@ -298,7 +344,7 @@ raypc_status raypc_update_volume(raypc_ctx* ctx, int vol, const void* src, int s
     if (st) return st;
     if ((st = ingest(ctx, V, src, src_is_device, src_dtype, (cudaStream_t)stream))) return st;
     V->stale = true;
-    for (auto& L : V->lv) L.classified = false;
+    for (int l = 1; l <= RAYPC_MAX_LOD; ++l) V->lv[l].bricks = false;
     return RAYPC_OK;
 }
 
@@ -325,7 +371,8 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // coarser levels
+    // Level 0 brick min/max come out of every ingest; build the coarser levels,
+    // each fused with its own brick min/max.
     for (int l = 1; l <= n_lod; ++l) {
         Level& P = V->lv[l - 1];
         Level& L = V->lv[l];
@@ -340,34 +387,13 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
             if (st == RAYPC_OK) st = ctx->alloc(&L.pairs, L.pairs_bytes, &V->bytes);
             if (st) return st;
         }
-        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, s), "LOD kernel");
-    }
-    V->nlev = 1 + n_lod > V->nlev ? 1 + n_lod : V->nlev;
-    for (int l = 0; l <= n_lod; ++l) {
-        Level& L = V->lv[l];
-        if (!L.bmin) {
-            size_t nbk = L.nbricks();
-            size_t mm = nbk * V->nvars * sizeof(float);
-            size_t words = L.nwords() * sizeof(uint32_t);
-            if ((st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.bmax, mm, &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.active, words, &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.skippable, words, &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.list, nbk * sizeof(uint32_t), &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.n_active, sizeof(uint32_t), &V->bytes)) ||
-                (st = ctx->alloc((void**)&L.pass_count, sizeof(unsigned) * kMaxVars, &V->bytes))) {
-                free_bricks(L);
-                return st;
-            }
-        }
-        CK(launch_brick_minmax(L.cells, V->dtype, L.n, V->nvars, L.bmin, L.bmax, s), "brick min/max kernel");
+        if ((st = alloc_bricks(ctx, V, L))) return st;
+        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, L.bmin, L.bmax, s), "LOD kernel");
         L.bricks = true;
-        L.classified = false;
-        if (V->brush_set && (st = classify_level(V, L, s))) return st;
     }
-    for (int l = n_lod + 1; l <= RAYPC_MAX_LOD; ++l) V->lv[l].classified = V->lv[l].classified && !V->stale;
-    if (V->stale) V->nlev = 1 + n_lod;   // levels beyond n_lod were not rebuilt from the new data
+    if (V->stale || 1 + n_lod > V->nlev) V->nlev = 1 + n_lod;   // stale coarser levels drop out
     V->stale = false;
+    for (auto& L : V->lv) L.classified = false;
     return RAYPC_OK;
 }
 
@@ -388,13 +414,13 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
         b.hi[v] = hi[v];
     }
     b.mask = active_mask;
-    if (!V->lv[0].bricks) return fail(RAYPC_ERR_INVALID_ARG, "raypc_build_bricks must run before raypc_set_brush");
     V->brush = b;
     V->brush_set = true;
-    cudaStream_t s = (cudaStream_t)stream;
-    for (int l = 0; l < V->nlev; ++l)
-        if (V->lv[l].bricks && (st = classify_level(V, V->lv[l], s))) return st;
-    return RAYPC_OK;
+    if (V->stale) {            // coarser levels are rebuilt by raypc_build_bricks, which classifies lazily
+        for (auto& L : V->lv) L.classified = false;
+        return RAYPC_OK;
+    }
+    return classify_all(V, (cudaStream_t)stream);
 }
 
 raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_var, float v_lo,
@@ -455,7 +481,8 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
     if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run before render");
-    if (!L->bricks || !L->classified) return fail(RAYPC_ERR_INVALID_ARG, "build_bricks and set_brush must run before render");
+    if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d are not built", lod);
+    if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
     if (!V->tf_set) return fail(RAYPC_ERR_INVALID_ARG, "set_tf must run before render");
     float dt = o.step > 0.f ? o.step : 1.0f / (float)L->n;
     if (!isfinite(dt) || dt < 2.0f * V->r_out / 4194304.0f)
@@ -526,6 +553,11 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     h.naxes = naxes;
     h.bins = bins;
     for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? axis_order[a] : 0;
+    for (int a = 0; a < naxes; ++a) {
+        const float e0 = edges[(size_t)a * (bins + 1)], eN = edges[(size_t)a * (bins + 1) + bins];
+        h.guess_e0[a] = e0;
+        h.guess_scale[a] = (eN > e0 && isfinite(eN - e0)) ? (float)bins / (eN - e0) : 0.0f;
+    }
     h.need_mask = use_brush ? V->brush.mask : 0u;
     for (int a = 0; a < naxes; ++a) h.need_mask |= 1u << axis_order[a];
     double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
@@ -606,8 +638,9 @@ raypc_status raypc_get_skip_list(raypc_ctx* ctx, int vol, int lod, uint32_t* act
     if (st) return st;
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
-    if (!L->classified) return fail(RAYPC_ERR_INVALID_ARG, "level %d not classified (set_brush)", lod);
     cudaStream_t s = (cudaStream_t)stream;
+    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
+    if ((st = ensure_classified(V, *L, s))) return st;
     size_t wb = L->nwords() * sizeof(uint32_t);
     if (active_bits_dev) CK(cudaMemcpyAsync(active_bits_dev, L->active, wb, cudaMemcpyDeviceToDevice, s), "copy active bits");
     if (skippable_bits_dev) CK(cudaMemcpyAsync(skippable_bits_dev, L->skippable, wb, cudaMemcpyDeviceToDevice, s), "copy skippable bits");

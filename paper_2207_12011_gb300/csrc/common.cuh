@@ -143,24 +143,45 @@ struct HistArgs {
     int naxes, bins;
     int axis[kMaxVars];
     const float* edges;           // naxes x (bins + 1), device
+    float guess_e0[kMaxVars];     // per axis: first edge and bins / (last - first), for the
+    float guess_scale[kMaxVars];  // starting guess of the bin walk (any value is correct)
     int64_t s_in, s_out;
     uint32_t* out;                // (naxes-1) x bins x bins
+};
+
+// Classification of all built levels of a volume in one launch per kernel.
+struct ClassifyLevel {
+    const float* bmin;
+    const float* bmax;
+    int n;                        // level edge
+    float sc;                     // 2 / n, set by the launcher
+    size_t first;                 // first flat index of this level (multiple of 32), set by the launcher
+    uint32_t* active;
+    uint32_t* skippable;
+    uint32_t* list;
+    uint32_t* n_active;
+    unsigned* pass_count;
+};
+
+struct ClassifyArgs {
+    int nlev;
+    int nvars;
+    float rin2, rout2;            // r_in * r_in, r_out * r_out rounded to FP32
+    BrushArgs brush;
+    size_t total;                 // set by the launcher
+    ClassifyLevel lv[3];
 };
 
 // Process-wide count of launched kernels (defined in api.cu).
 void count_launches(int k);
 
 // Launchers (defined in the .cu files; all enqueue on `stream`).
+// Ingest (level 0) and LOD (coarser level) also write the level's brick min/max.
 cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype,
-                          int n, int nvars, cudaStream_t stream);
+                          int n, int nvars, float* bmin, float* bmax, cudaStream_t stream);
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
-                       cudaStream_t stream);
-cudaError_t launch_brick_minmax(const void* cells, int dtype, int n, int nvars, float* bmin,
-                                float* bmax, cudaStream_t stream);
-cudaError_t launch_classify(const float* bmin, const float* bmax, int n, int nvars, float r_in,
-                            float r_out, const BrushArgs& brush, uint32_t* active,
-                            uint32_t* skippable, uint32_t* list, uint32_t* n_active,
-                            unsigned* pass_count, cudaStream_t stream);
+                       float* bmin, float* bmax, cudaStream_t stream);
+cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 

@@ -17,15 +17,26 @@ namespace {
 
 constexpr int kHistThreads = 256;
 
-// Number of interior edges e_1..e_{bins-1} that are <= v (edges non-decreasing;
-// NaN compares false everywhere and lands in bin 0).
-__device__ __forceinline__ int bin_of(const float* e, int bins, float v) {
-    int lo = 0, hi = bins - 1;   // answer in [0, bins-1]
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (v >= e[mid]) lo = mid; else hi = mid - 1;
-    }
-    return lo;
+// Number of interior edges e_1..e_{bins-1} that are <= v, for non-decreasing
+// edges: start from an affine guess and walk to the answer with comparisons
+// only (exact for any edges; one or two steps for equally spaced ones). NaN
+// compares false everywhere and lands in bin 0.
+__device__ __forceinline__ int bin_of(const float* e, int bins, float v, float e0, float scale) {
+    if (v != v) return 0;
+    float g = (v - e0) * scale;
+    g = fminf(fmaxf(g, 0.0f), (float)(bins - 1));
+    int j = (int)g;
+    while (j > 0 && !(v >= e[j])) --j;
+    while (j < bins - 1 && v >= e[j + 1]) ++j;
+    return j;
+}
+
+// Largest integer m >= 0 with m * m <= a (a >= 0).
+__device__ __forceinline__ long long isqrt_floor(long long a) {
+    long long m = (long long)sqrt((double)a);
+    while (m * m > a) --m;
+    while ((m + 1) * (m + 1) <= a) ++m;
+    return m;
 }
 
 template <int DT>
@@ -42,33 +53,43 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int bins = A.bins;
     const size_t plane = (size_t)n * n * n;
+    const unsigned brush_mask = A.use_brush ? A.brush.mask : 0u;
+    const unsigned rest_mask = A.need_mask & ~brush_mask;
 
     for (long long r = gwarp; r < rows; r += nwarps) {
         const int y = (int)(r % n), z = (int)(r / n);
         const long long dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
         const long long syz = dy * dy + dz * dz;
         if (syz > A.s_out) continue;                       // whole row outside the outer sphere
+        // x range of the row inside the outer sphere: |2x + 1 - n| <= m
+        const long long m = isqrt_floor(A.s_out - syz);
+        const int xa = (int)max(0LL, (n - 1 - m + 1) / 2);
+        const int xb = (int)min((long long)n - 1, (n - 1 + m) / 2);
         const size_t row_base = (size_t)r * n;
-        for (int x0 = 0; x0 < n; x0 += 32) {
+        for (int x0 = xa; x0 <= xb; x0 += 32) {
             const int x = x0 + lane;
             bool keep = false;
             int bn[kMaxVars];
-            if (x < n) {
+            if (x <= xb) {
                 const long long dx = 2 * x + 1 - n;
                 const long long s = dx * dx + syz;
                 if (s >= A.s_in && s <= A.s_out) {
                     float val[kMaxVars];
-#pragma unroll
-                    for (int v = 0; v < kMaxVars; ++v)
-                        val[v] = ((A.need_mask >> v) & 1u) ? load_cell<DT>(A.cells, v * plane + row_base + x) : 0.0f;
                     keep = true;
-                    if (A.use_brush) {
+                    // brushed variables first; the rest only for cells that pass
 #pragma unroll
-                        for (int v = 0; v < kMaxVars; ++v)
-                            if ((A.brush.mask >> v) & 1u)
-                                keep = keep && (val[v] >= A.brush.lo[v]) && (val[v] <= A.brush.hi[v]);
+                    for (int v = 0; v < kMaxVars; ++v) {
+                        if ((brush_mask >> v) & 1u) {
+                            val[v] = load_cell<DT>(A.cells, v * plane + row_base + x);
+                            keep = keep && (val[v] >= A.brush.lo[v]) && (val[v] <= A.brush.hi[v]);
+                        } else {
+                            val[v] = 0.0f;
+                        }
                     }
                     if (keep) {
+#pragma unroll
+                        for (int v = 0; v < kMaxVars; ++v)
+                            if ((rest_mask >> v) & 1u) val[v] = load_cell<DT>(A.cells, v * plane + row_base + x);
 #pragma unroll
                         for (int a = 0; a < kMaxVars; ++a) {
                             if (a < A.naxes) {
@@ -76,7 +97,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
 #pragma unroll
                                 for (int v = 1; v < kMaxVars; ++v)
                                     if (A.axis[a] == v) va = val[v];
-                                bn[a] = bin_of(s_edges + a * (bins + 1), bins, va);
+                                bn[a] = bin_of(s_edges + a * (bins + 1), bins, va, A.guess_e0[a], A.guess_scale[a]);
                             }
                         }
                     }

@@ -14,7 +14,7 @@
 
 #include <mutex>
 
-#include "../../include/raypc.h"
+#include "raypc.h"
 #include "common.cuh"
 
 using namespace raypc;
@@ -117,6 +117,11 @@ raypc_status raypc_pc_histogram_noalloc(const void* cells_dev, int dtype, int n,
     h.naxes = naxes;
     h.bins = bins;
     for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? axis_order[a] : 0;
+    for (int a = 0; a < naxes; ++a) {
+        const float e0 = edges[(size_t)a * (bins + 1)], eN = edges[(size_t)a * (bins + 1) + bins];
+        h.guess_e0[a] = e0;
+        h.guess_scale[a] = (eN > e0 && isfinite(eN - e0)) ? (float)bins / (eN - e0) : 0.0f;
+    }
     h.need_mask = h.brush.mask;
     for (int a = 0; a < naxes; ++a) h.need_mask |= 1u << axis_order[a];
     double ri = (double)r_in * (double)n, ro = (double)r_out * (double)n;

@@ -130,10 +130,17 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
             const float dt = A.dt;
             const size_t sy_ = (size_t)n, sz_ = (size_t)n * n, plane = sz_ * n;
             const int nact = s_nact;
+            // Lattice end: the first k with t_k >= t1, found once per ray from an
+            // estimate corrected with the exact predicate (t_k is non-decreasing in k).
+            const float inv_dt = 1.0f / dt;
+            int n_lat = max(0, (int)floorf((t1 - t0) * inv_dt - 0.5f));
+            while (n_lat > 0 && !(__fmaf_rn(__fadd_rn((float)(n_lat - 1), 0.5f), dt, t0) < t1)) --n_lat;
+            while (__fmaf_rn(__fadd_rn((float)n_lat, 0.5f), dt, t0) < t1) ++n_lat;
+            const float inv_hn = 1.0f / hn;
+            const float idx = 1.0f / dx, idy = 1.0f / dy, idz = 1.0f / dz;
             int k = 0;
-            for (;;) {
-                float t = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, t0);
-                if (!(t < t1)) break;
+            while (k < n_lat) {
+                const float t = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, t0);
                 const float pxw = __fmaf_rn(t, dx, ox), pyw = __fmaf_rn(t, dy, oy), pzw = __fmaf_rn(t, dz, oz);
                 int ix, iy, iz;
                 float fx, fy, fz;
@@ -146,33 +153,18 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
                     if (A.skip && bit_of(A.lv.skippable, bid)) {
                         // exit time from the brick's sample region (any conservative value works)
                         float te = __int_as_float(0x7f800000);
-                        const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz};
+                        const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz}, ii[3] = {idx, idy, idz};
                         const int bb[3] = {bx, by, bz};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            if (dd[a] > 0.0f && bb[a] < nb - 1) {
-                                float pl = ((float)(kBrick * (bb[a] + 1)) + 0.5f) / hn - 1.0f;
-                                te = fminf(te, (pl - oo[a]) / dd[a]);
-                            } else if (dd[a] < 0.0f && bb[a] > 0) {
-                                float pl = ((float)(kBrick * bb[a]) + 0.5f) / hn - 1.0f;
-                                te = fminf(te, (pl - oo[a]) / dd[a]);
-                            }
+                            if (dd[a] > 0.0f && bb[a] < nb - 1)
+                                te = fminf(te, (fmaf((float)(kBrick * (bb[a] + 1)) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
+                            else if (dd[a] < 0.0f && bb[a] > 0)
+                                te = fminf(te, (fmaf((float)(kBrick * bb[a]) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
                         }
-                        float kk = (te - t0) / dt - 0.5f;
-                        kk = fminf(kk, 1.0e9f);
+                        const float kk = fminf((te - t0) * inv_dt - 0.5f, 1.0e9f);
                         int kn = (kk > (float)k) ? (int)ceilf(kk) - 1 : k + 1;
-                        kn = max(kn, k + 1);
-                        float tn = __fmaf_rn(__fadd_rn((float)kn, 0.5f), dt, t0);
-                        if (!(tn < t1)) {
-                            // jumped past the end: find the exact lattice end in (k, kn]
-                            int lo = k + 1, hi = kn;   // first index with t >= t1 lies in [lo, hi]
-                            while (lo < hi) {
-                                int mid = lo + ((hi - lo) >> 1);
-                                float tm = __fmaf_rn(__fadd_rn((float)mid, 0.5f), dt, t0);
-                                if (tm < t1) lo = mid + 1; else hi = mid;
-                            }
-                            kn = lo;
-                        }
+                        kn = min(max(kn, k + 1), n_lat);
                         skipped += (unsigned)(kn - k - 1);
                         k = kn;
                         continue;

@@ -1,5 +1,5 @@
-// Volume preparation kernels: ingest/relayout, level-of-detail mean,
-// brick min/max and brush classification of bricks.
+// Volume preparation kernels: ingest/relayout and level-of-detail mean fused
+// with brick min/max, and brush classification of bricks.
 //
 // Section 2.1 of the paper prepares the data once (levels of detail, derived
 // variables); Section 2.2 relies on that preparation not depending on the
@@ -10,103 +10,139 @@ namespace raypc {
 
 namespace {
 
+constexpr int kRowThreads = 256;
+
 __device__ __forceinline__ float load_src(const void* src, int dtype, size_t i) {
-    if (dtype == kF16) return __half2float(reinterpret_cast<const __half*>(src)[i]);
-    return reinterpret_cast<const float*>(src)[i];
+    if (dtype == kF16) return __half2float(__ldg(reinterpret_cast<const __half*>(src) + i));
+    return __ldg(reinterpret_cast<const float*>(src) + i);
 }
 
-// Store one value of a level: planar cell plus its two pair slots (as the
-// left element of its own pair and the right element of the pair at x-1;
-// the last x also fills its own right element).
-template <int DT>
-__device__ __forceinline__ void store_value(void* cells, void* pairs, size_t i, int x, int n, float v);
+// Round to the storage dtype (the stored value, as a float).
+template <int DT> __device__ __forceinline__ float to_stored(float v);
+template <> __device__ __forceinline__ float to_stored<kF32>(float v) { return v; }
+template <> __device__ __forceinline__ float to_stored<kF16>(float v) { return __half2float(__float2half_rn(v)); }
 
-template <>
-__device__ __forceinline__ void store_value<kF32>(void* cells, void* pairs, size_t i, int x, int n, float v) {
+template <int DT> __device__ __forceinline__ void store_cell(void* cells, size_t i, float v);
+template <> __device__ __forceinline__ void store_cell<kF32>(void* cells, size_t i, float v) {
     reinterpret_cast<float*>(cells)[i] = v;
-    float* p = reinterpret_cast<float*>(pairs);
-    p[2 * i] = v;
-    if (x > 0) p[2 * (i - 1) + 1] = v;
-    if (x == n - 1) p[2 * i + 1] = v;
+}
+template <> __device__ __forceinline__ void store_cell<kF16>(void* cells, size_t i, float v) {
+    reinterpret_cast<__half*>(cells)[i] = __float2half_rn(v);
 }
 
-template <>
-__device__ __forceinline__ void store_value<kF16>(void* cells, void* pairs, size_t i, int x, int n, float v) {
-    __half h = __float2half_rn(v);
-    reinterpret_cast<__half*>(cells)[i] = h;
-    __half* p = reinterpret_cast<__half*>(pairs);
-    p[2 * i] = h;
-    if (x > 0) p[2 * (i - 1) + 1] = h;
-    if (x == n - 1) p[2 * i + 1] = h;
+template <int DT> __device__ __forceinline__ void store_pair(void* pairs, size_t i, float a, float b);
+template <> __device__ __forceinline__ void store_pair<kF32>(void* pairs, size_t i, float a, float b) {
+    reinterpret_cast<float2*>(pairs)[i] = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void store_pair<kF16>(void* pairs, size_t i, float a, float b) {
+    reinterpret_cast<__half2*>(pairs)[i] = __floats2half2_rn(a, b);
 }
 
-// One thread per (variable, cell): convert the source value to the storage
-// dtype and write the planar cell and both pair slots. Reads and writes are
-// coalesced along x.
-template <int DT>
-__global__ void k_ingest(const void* __restrict__ src, int src_dtype, void* __restrict__ cells,
-                         void* __restrict__ pairs, int n, size_t total) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    int x = (int)(i % n);
-    store_value<DT>(cells, pairs, i, x, n, load_src(src, src_dtype, i));
+struct RowsArgs {
+    const void* src;      // ingest: planar source (src_dtype); LOD: planar cells of the finer level
+    int src_dtype;        // ingest only
+    int n_src;            // LOD: edge of the finer level
+    void* cells;          // this level, planar
+    void* pairs;          // this level, x-pairs
+    int n;                // edge of this level
+    int nvars;
+    float* bmin;          // [nb^3][nvars]
+    float* bmax;
+};
+
+// Value of cell (x, y, z) of variable v of the level being produced, rounded
+// to the storage dtype.
+//   MODE 0 (ingest): the converted source value.
+//   MODE 1 (LOD):    FP32 mean of the 2x2x2 fine cells, fine indices clamped,
+//                    ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
+template <int DT, int MODE>
+__device__ __forceinline__ float produce(const RowsArgs& A, int x, int y, int z, int v) {
+    if (MODE == 0) {
+        const size_t n = (size_t)A.n;
+        return to_stored<DT>(load_src(A.src, A.src_dtype, ((v * n + z) * n + y) * n + x));
+    } else {
+        const int nf = A.n_src;
+        const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
+        const int x1 = min(x0 + 1, nf - 1), y1 = min(y0 + 1, nf - 1), z1 = min(z0 + 1, nf - 1);
+        const size_t plane = (size_t)v * nf * nf * nf;
+        auto at = [&](int a, int b, int c) { return load_cell<DT>(A.src, plane + ((size_t)c * nf + b) * nf + a); };
+        float s0 = __fadd_rn(__fadd_rn(at(x0, y0, z0), at(x1, y0, z0)), __fadd_rn(at(x0, y1, z0), at(x1, y1, z0)));
+        float s1 = __fadd_rn(__fadd_rn(at(x0, y0, z1), at(x1, y0, z1)), __fadd_rn(at(x0, y1, z1), at(x1, y1, z1)));
+        return to_stored<DT>(__fmul_rn(__fadd_rn(s0, s1), 0.125f));
+    }
 }
 
-// Coarse cell = FP32 mean of its 2x2x2 fine cells (fine indices clamped):
-// ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8,
-// then rounded to the storage dtype. One thread per (variable, coarse cell).
-template <int DT>
-__global__ void k_lod(const void* __restrict__ fine, int n, void* __restrict__ cells,
-                      void* __restrict__ pairs, int nvars) {
-    const int m = (n + 1) / 2;
-    const size_t mm = (size_t)m * m * m;
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= mm * nvars) return;
-    const int v = (int)(i / mm);
-    const size_t c = i % mm;
-    const int x = (int)(c % m), y = (int)((c / m) % m), z = (int)(c / ((size_t)m * m));
-    const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
-    const int x1 = min(x0 + 1, n - 1), y1 = min(y0 + 1, n - 1), z1 = min(z0 + 1, n - 1);
-    const size_t plane = (size_t)v * n * n * n;
-    auto at = [&](int a, int b, int cz) { return load_cell<DT>(fine, plane + ((size_t)cz * n + b) * n + a); };
-    float s0 = __fadd_rn(__fadd_rn(at(x0, y0, z0), at(x1, y0, z0)), __fadd_rn(at(x0, y1, z0), at(x1, y1, z0)));
-    float s1 = __fadd_rn(__fadd_rn(at(x0, y0, z1), at(x1, y0, z1)), __fadd_rn(at(x0, y1, z1), at(x1, y1, z1)));
-    store_value<DT>(cells, pairs, i, x, m, __fmul_rn(__fadd_rn(s0, s1), 0.125f));
-}
-
-// One warp per brick: the 32 lanes stride over the brick's (up to) 9^3
-// vertices, keep running NaN-ignoring min/max per variable, then reduce.
-template <int DT>
-__global__ void k_brick_minmax(const void* __restrict__ cells, int n, int nvars,
-                               float* __restrict__ bmin, float* __restrict__ bmax) {
-    int nb = (n + kBrick - 1) / kBrick;
-    size_t nbricks = (size_t)nb * nb * nb;
-    size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= nbricks) return;
-    int bx = (int)(warp % nb), by = (int)((warp / nb) % nb), bz = (int)(warp / ((size_t)nb * nb));
-    int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
-    int ex = min(x0 + kBrick, n - 1) - x0 + 1;
-    int ey = min(y0 + kBrick, n - 1) - y0 + 1;
-    int ez = min(z0 + kBrick, n - 1) - z0 + 1;
-    int cnt = ex * ey * ez;
-    const size_t plane = (size_t)n * n * n;
-    for (int v = 0; v < nvars; ++v) {
-        float mn = __int_as_float(0x7fffffff), mx = mn;
-        for (int j = lane; j < cnt; j += 32) {
-            int dx = j % ex, dy = (j / ex) % ey, dz = j / (ex * ey);
-            float a = load_cell<DT>(cells, v * plane + ((size_t)(z0 + dz) * n + (y0 + dy)) * n + (x0 + dx));
-            mn = fminf(mn, a);
-            mx = fmaxf(mx, a);
+// One block per (brick row (by, bz), variable). Threads own x columns; the
+// block streams the (up to) 9 x 9 x-rows y in [8by, 8by+8], z in [8bz, 8bz+8]
+// of the level, writes the 8 x 8 rows it owns (cells and x-pairs; the right
+// element of a pair comes from the neighbouring lane) and folds every row,
+// apron rows included, into per-column NaN-ignoring min/max. Columns are then
+// reduced to bricks in shared memory. Brick (bx, by, bz) covers vertices
+// 8b..min(8b+8, n-1) on each axis.
+template <int DT, int MODE>
+__global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
+    extern __shared__ float s_col[];          // [2][n]: column min, column max
+    const int n = A.n;
+    const int nb = (n + kBrick - 1) / kBrick;
+    const int by = blockIdx.x % nb, bz = blockIdx.x / nb, v = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const float qnan = __int_as_float(0x7fffffff);
+    for (int xc = 0; xc < n; xc += kRowThreads) {
+        const int x = xc + threadIdx.x;
+        const bool valid = x < n;
+        float mn = qnan, mx = qnan;
+        for (int dz = 0; dz <= kBrick; ++dz) {
+            const int z = bz * kBrick + dz;
+            if (z >= n) break;
+            // Ingest: issue the (up to) 9 row loads of this z-slice before using
+            // any of them (9 loads in flight per thread). LOD: one row at a time
+            // (each value already costs 8 loads).
+            constexpr int kAhead = MODE == 0 ? kBrick + 1 : 1;
+            for (int dy0 = 0; dy0 <= kBrick; dy0 += kAhead) {
+                float val[kAhead];
+#pragma unroll
+                for (int j = 0; j < kAhead; ++j) {
+                    const int y = by * kBrick + dy0 + j;
+                    val[j] = (valid && dy0 + j <= kBrick && y < n) ? produce<DT, MODE>(A, x, y, z, v) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < kAhead; ++j) {
+                    const int dy = dy0 + j;
+                    const int y = by * kBrick + dy;
+                    if (dy > kBrick || y >= n) break;
+                    if (valid) {
+                        mn = fminf(mn, val[j]);
+                        mx = fmaxf(mx, val[j]);
+                    }
+                    if (dy < kBrick && dz < kBrick) {
+                        float right = __shfl_down_sync(0xffffffffu, val[j], 1);
+                        if (valid) {
+                            if (x == n - 1) right = val[j];
+                            else if (lane == 31) right = produce<DT, MODE>(A, x + 1, y, z, v);
+                            const size_t i = (((size_t)v * n + z) * n + y) * n + x;
+                            store_cell<DT>(A.cells, i, val[j]);
+                            store_pair<DT>(A.pairs, i, val[j], right);
+                        }
+                    }
+                }
+            }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (valid) {
+            s_col[x] = mn;
+            s_col[n + x] = mx;
         }
-        if (lane == 0) {
-            bmin[warp * nvars + v] = mn;
-            bmax[warp * nvars + v] = mx;
+    }
+    __syncthreads();
+    for (int bx = threadIdx.x; bx < nb; bx += kRowThreads) {
+        const int x0 = bx * kBrick, x1 = min(x0 + kBrick, n - 1);
+        float mn = qnan, mx = qnan;
+        for (int x = x0; x <= x1; ++x) {
+            mn = fminf(mn, s_col[x]);
+            mx = fmaxf(mx, s_col[n + x]);
         }
+        const size_t b = ((size_t)bz * nb + by) * nb + bx;
+        A.bmin[b * A.nvars + v] = mn;
+        A.bmax[b * A.nvars + v] = mx;
     }
 }
 
@@ -120,21 +156,33 @@ __device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, float& l
     if (b == nb - 1) hi = 2.0f;
 }
 
-// One thread per brick: shell test of the widened box and brush test with the
-// rounding margin d = max(|min|, |max|) * 2^-20 + 2^-120. Writes the active
-// bitmask (one ballot word per warp) and counts, per restricted variable, the
-// in-shell bricks that pass that variable alone (a selectivity hint).
-__global__ void k_classify(const float* __restrict__ bmin, const float* __restrict__ bmax, int n,
-                           int nvars, float sc, float rin2, float rout2, BrushArgs brush,
-                           uint32_t* __restrict__ active, unsigned* __restrict__ pass_count) {
-    int nb = (n + kBrick - 1) / kBrick;
-    size_t nbricks = (size_t)nb * nb * nb;
-    size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int lane = threadIdx.x & 31;
-    bool valid = b < nbricks;
+// Locate the level of a flat brick index over all levels (<= 3 levels).
+__device__ __forceinline__ int level_of(const ClassifyArgs& C, size_t g, size_t& b) {
+    int l = 0;
+    while (l + 1 < C.nlev && g >= C.lv[l + 1].first) ++l;
+    b = g - C.lv[l].first;
+    return l;
+}
+
+// One thread per brick of every level: shell test of the widened box and brush
+// test with the rounding margin d = max(|min|, |max|) * 2^-20 + 2^-120. Writes
+// the active bitmask (one ballot word per warp; level ranges start on
+// multiples of 32) and counts, per restricted variable, the in-shell bricks
+// that pass that variable alone (a selectivity hint for the render).
+__global__ void k_classify(ClassifyArgs C) {
+    const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    size_t b = 0;
+    const int l = level_of(C, g, b);
+    const ClassifyLevel& L = C.lv[l];
+    const int nb = (L.n + kBrick - 1) / kBrick;
+    const size_t nbricks = (size_t)nb * nb * nb;
+    const bool in_range = g < C.total;
+    const bool valid = in_range && b < nbricks;
     bool act = false;
     unsigned pass_bits = 0;
     if (valid) {
+        const float sc = L.sc;
         int c[3] = {(int)(b % nb), (int)((b / nb) % nb), (int)(b / ((size_t)nb * nb))};
         float nearc[3], farc[3];
 #pragma unroll
@@ -144,145 +192,163 @@ __global__ void k_classify(const float* __restrict__ bmin, const float* __restri
             nearc[a] = (lo > 0.0f) ? lo : ((hi < 0.0f) ? -hi : 0.0f);
             farc[a] = fmaxf(fabsf(lo), fabsf(hi));
         }
-        float near2 = dot3_rn(nearc[0], nearc[1], nearc[2], nearc[0], nearc[1], nearc[2]);
-        float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
-        act = (near2 <= rout2) && (far2 >= rin2);
+        const float near2 = dot3_rn(nearc[0], nearc[1], nearc[2], nearc[0], nearc[1], nearc[2]);
+        const float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
+        act = (near2 <= C.rout2) && (far2 >= C.rin2);
         if (act) {
             bool all = true;
-            for (int v = 0; v < nvars; ++v) {
-                if (!((brush.mask >> v) & 1u)) continue;
-                float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
-                float m = fmaxf(fabsf(mn), fabsf(mx));
-                float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-                bool ok = (__fadd_rn(mx, d) >= brush.lo[v]) && (__fsub_rn(mn, d) <= brush.hi[v]);
+            for (int v = 0; v < C.nvars; ++v) {
+                if (!((C.brush.mask >> v) & 1u)) continue;
+                const float mn = L.bmin[b * C.nvars + v], mx = L.bmax[b * C.nvars + v];
+                const float m = fmaxf(fabsf(mn), fabsf(mx));
+                const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                const bool ok = (__fadd_rn(mx, d) >= C.brush.lo[v]) && (__fsub_rn(mn, d) <= C.brush.hi[v]);
                 if (ok) pass_bits |= 1u << v;
                 all = all && ok;
             }
             act = all;
         }
     }
-    unsigned word = __ballot_sync(0xffffffffu, act);
-    if (lane == 0 && (b >> 5) < (nbricks + 31) / 32) active[b >> 5] = word;
-    for (int v = 0; v < nvars; ++v) {
-        unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
-        if (lane == 0 && cnt) atomicAdd(&pass_count[v], cnt);
+    const unsigned word = __ballot_sync(0xffffffffu, act);
+    if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.active[b >> 5] = word;
+    for (int v = 0; v < C.nvars; ++v) {
+        const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
+        if (lane == 0 && cnt) atomicAdd(&L.pass_count[v], cnt);
     }
 }
 
 // Skippable = this brick and its existing 26 neighbours are inactive.
-__global__ void k_skippable(const uint32_t* __restrict__ active, int nb, uint32_t* __restrict__ skippable) {
-    size_t nbricks = (size_t)nb * nb * nb;
-    size_t b = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int lane = threadIdx.x & 31;
+__global__ void k_skippable(ClassifyArgs C) {
+    const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    size_t b = 0;
+    const int l = level_of(C, g, b);
+    const ClassifyLevel& L = C.lv[l];
+    const int nb = (L.n + kBrick - 1) / kBrick;
+    const size_t nbricks = (size_t)nb * nb * nb;
+    const bool in_range = g < C.total;
+    const bool valid = in_range && b < nbricks;
     bool s = false;
-    if (b < nbricks) {
-        int x = (int)(b % nb), y = (int)((b / nb) % nb), z = (int)(b / ((size_t)nb * nb));
+    if (valid) {
+        const int x = (int)(b % nb), y = (int)((b / nb) % nb), z = (int)(b / ((size_t)nb * nb));
         s = true;
         for (int dz = -1; dz <= 1 && s; ++dz)
             for (int dy = -1; dy <= 1 && s; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
-                    int xx = x + dx, yy = y + dy, zz = z + dz;
+                    const int xx = x + dx, yy = y + dy, zz = z + dz;
                     if (xx < 0 || yy < 0 || zz < 0 || xx >= nb || yy >= nb || zz >= nb) continue;
-                    size_t id = ((size_t)zz * nb + yy) * nb + xx;
-                    if ((active[id >> 5] >> (id & 31)) & 1u) { s = false; break; }
+                    const size_t id = ((size_t)zz * nb + yy) * nb + xx;
+                    if ((L.active[id >> 5] >> (id & 31)) & 1u) { s = false; break; }
                 }
     }
-    unsigned word = __ballot_sync(0xffffffffu, s);
-    if (lane == 0 && (b >> 5) < (nbricks + 31) / 32) skippable[b >> 5] = word;
+    const unsigned word = __ballot_sync(0xffffffffu, s);
+    if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.skippable[b >> 5] = word;
 }
 
-// Ordered compaction of the active brick ids: one block of 1024 threads, each
-// owning a contiguous run of bitmask words; block-wide exclusive scan of the
-// per-thread popcounts gives every thread its output offset.
-__global__ void __launch_bounds__(1024) k_compact(const uint32_t* __restrict__ active, size_t nwords,
-                                                  size_t nbricks, uint32_t* __restrict__ list,
-                                                  uint32_t* __restrict__ n_active) {
+// Ordered compaction of the active brick ids, one block of 1024 threads per
+// level: each thread owns a contiguous run of bitmask words; a block-wide
+// exclusive scan of the per-thread popcounts gives every thread its offset.
+__global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
     __shared__ unsigned s_sum[1024];
-    size_t per = (nwords + blockDim.x - 1) / blockDim.x;
-    size_t w0 = threadIdx.x * per, w1 = min(nwords, w0 + per);
+    const ClassifyLevel& L = C.lv[blockIdx.x];
+    const int nb = (L.n + kBrick - 1) / kBrick;
+    const size_t nbricks = (size_t)nb * nb * nb;
+    const size_t nwords = (nbricks + 31) / 32;
+    const size_t per = (nwords + blockDim.x - 1) / blockDim.x;
+    const size_t w0 = min(nwords, threadIdx.x * per), w1 = min(nwords, w0 + per);
     unsigned cnt = 0;
-    for (size_t w = w0; w < w1; ++w) cnt += __popc(active[w]);
+    for (size_t w = w0; w < w1; ++w) cnt += __popc(L.active[w]);
     s_sum[threadIdx.x] = cnt;
     __syncthreads();
     for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-        unsigned add = threadIdx.x >= (unsigned)off ? s_sum[threadIdx.x - off] : 0u;
+        const unsigned add = threadIdx.x >= (unsigned)off ? s_sum[threadIdx.x - off] : 0u;
         __syncthreads();
         s_sum[threadIdx.x] += add;
         __syncthreads();
     }
     unsigned pos = s_sum[threadIdx.x] - cnt;
-    if (list) {
-        for (size_t w = w0; w < w1; ++w) {
-            uint32_t bits = active[w];
-            while (bits) {
-                int j = __ffs(bits) - 1;
-                bits &= bits - 1;
-                size_t id = w * 32 + j;
-                if (id < nbricks) list[pos++] = (uint32_t)id;
-            }
+    for (size_t w = w0; w < w1; ++w) {
+        uint32_t bits = L.active[w];
+        while (bits) {
+            const int j = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const size_t id = w * 32 + j;
+            if (id < nbricks) L.list[pos++] = (uint32_t)id;
         }
     }
-    if (threadIdx.x == blockDim.x - 1 && n_active) *n_active = s_sum[threadIdx.x];
+    if (threadIdx.x == blockDim.x - 1) *L.n_active = s_sum[threadIdx.x];
 }
 
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+template <int MODE>
+cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
+    const int nb = (a.n + kBrick - 1) / kBrick;
+    dim3 grid((unsigned)(nb * nb), (unsigned)a.nvars);
+    const size_t smem = sizeof(float) * 2 * (size_t)a.n;
+    if (smem > 48 * 1024) {
+        cudaError_t e = dtype == kF16
+            ? cudaFuncSetAttribute(k_rows<kF16, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(k_rows<kF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (dtype == kF16)
+        k_rows<kF16, MODE><<<grid, kRowThreads, smem, stream>>>(a);
+    else
+        k_rows<kF32, MODE><<<grid, kRowThreads, smem, stream>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype, int n,
-                          int nvars, cudaStream_t stream) {
-    size_t total = (size_t)n * n * n * nvars;
-    if (dtype == kF16)
-        k_ingest<kF16><<<blocks_for(total, 256), 256, 0, stream>>>(src, src_dtype, cells, pairs, n, total);
-    else
-        k_ingest<kF32><<<blocks_for(total, 256), 256, 0, stream>>>(src, src_dtype, cells, pairs, n, total);
-    count_launches(1);
-    return cudaGetLastError();
+                          int nvars, float* bmin, float* bmax, cudaStream_t stream) {
+    RowsArgs a{};
+    a.src = src;
+    a.src_dtype = src_dtype;
+    a.cells = cells;
+    a.pairs = pairs;
+    a.n = n;
+    a.nvars = nvars;
+    a.bmin = bmin;
+    a.bmax = bmax;
+    return launch_rows<0>(a, dtype, stream);
 }
 
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
-                       cudaStream_t stream) {
-    size_t m = (size_t)(n_fine + 1) / 2;
-    size_t total = m * m * m * nvars;
-    if (dtype == kF16)
-        k_lod<kF16><<<blocks_for(total, 256), 256, 0, stream>>>(fine, n_fine, cells, pairs, nvars);
-    else
-        k_lod<kF32><<<blocks_for(total, 256), 256, 0, stream>>>(fine, n_fine, cells, pairs, nvars);
-    count_launches(1);
-    return cudaGetLastError();
+                       float* bmin, float* bmax, cudaStream_t stream) {
+    RowsArgs a{};
+    a.src = fine;
+    a.n_src = n_fine;
+    a.cells = cells;
+    a.pairs = pairs;
+    a.n = (n_fine + 1) / 2;
+    a.nvars = nvars;
+    a.bmin = bmin;
+    a.bmax = bmax;
+    return launch_rows<1>(a, dtype, stream);
 }
 
-cudaError_t launch_brick_minmax(const void* cells, int dtype, int n, int nvars, float* bmin, float* bmax,
-                                cudaStream_t stream) {
-    size_t nb = (size_t)(n + kBrick - 1) / kBrick;
-    size_t threads = nb * nb * nb * 32;
-    if (dtype == kF16)
-        k_brick_minmax<kF16><<<blocks_for(threads, 256), 256, 0, stream>>>(cells, n, nvars, bmin, bmax);
-    else
-        k_brick_minmax<kF32><<<blocks_for(threads, 256), 256, 0, stream>>>(cells, n, nvars, bmin, bmax);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_classify(const float* bmin, const float* bmax, int n, int nvars, float r_in,
-                            float r_out, const BrushArgs& brush, uint32_t* active,
-                            uint32_t* skippable, uint32_t* list, uint32_t* n_active,
-                            unsigned* pass_count, cudaStream_t stream) {
-    int nb = (n + kBrick - 1) / kBrick;
-    size_t nbricks = (size_t)nb * nb * nb;
-    size_t nwords = (nbricks + 31) / 32;
-    cudaError_t e = cudaMemsetAsync(pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
+cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
+    size_t total = 0;
+    for (int l = 0; l < c.nlev; ++l) {
+        ClassifyLevel& L = c.lv[l];
+        const int nb = (L.n + kBrick - 1) / kBrick;
+        L.first = total;
+        L.sc = 2.0f / (float)L.n;
+        total += ((size_t)nb * nb * nb + 31) / 32 * 32;      // level ranges start on warp boundaries
+        cudaError_t e = cudaMemsetAsync(L.pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
+        if (e != cudaSuccess) return e;
+    }
+    c.total = total;
+    k_classify<<<blocks_for(total, 256), 256, 0, stream>>>(c);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    float sc = 2.0f / (float)n;
-    float rin2 = r_in * r_in, rout2 = r_out * r_out;
-    k_classify<<<blocks_for(nbricks, 256), 256, 0, stream>>>(bmin, bmax, n, nvars, sc, rin2, rout2,
-                                                             brush, active, pass_count);
+    k_skippable<<<blocks_for(total, 256), 256, 0, stream>>>(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_skippable<<<blocks_for(nbricks, 256), 256, 0, stream>>>(active, nb, skippable);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_compact<<<1, 1024, 0, stream>>>(active, nwords, nbricks, list, n_active);
+    k_compact<<<c.nlev, 1024, 0, stream>>>(c);
     count_launches(3);
     return cudaGetLastError();
 }
