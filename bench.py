@@ -210,6 +210,9 @@ def run_ours(args):
     H = torch.empty((naxes - 1, c["bins"], c["bins"]), dtype=torch.int32, device=dev)
     stats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
 
+    # autotuned launch choice for this device, dtype and grid (tile variant, skipping)
+    tuned, tuned_all = rp.autotune(ctx, [dict(vol=vol, cam=wl.cam, w=c["w"], h=c["h"], lo=wl.brush.lo,
+                                              hi=wl.brush.hi, mask=wl.brush.active_mask, out=img)], reps=3)
     for _ in range(args.warmup):
         step(rp, vol, wl, img, H, stats, wl.src)
     torch.cuda.synchronize()
@@ -307,19 +310,112 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3)},
         "gpu_launches": int(launches),
+        "autotune": {"chosen": tuned, "candidates": tuned_all},
         "roofline": roofline,
         "clocks": clk,
         "stats_per_step": {n: float(st[i]) / args.steps for i, n in enumerate(rp.STAT_NAMES)},
     }
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args)
+    if not args.no_batched:
+        vol.free()
+        ctx.close()
+        ctx = None
+        del wl.src
+        torch.cuda.empty_cache()
+        bt = run_batched(rp, dev, args, synth.DEFAULT_SEED + 1000 + rank)
+        ms, samples = aggregate(bt["batched_f16"]["ms_per_batch"], bt["samples_per_batch"], dev)
+        bt["batched_f16"]["samples_per_s_all_ranks"] = round(samples / (ms / 1e3), 1)
+        line["batched"] = bt
     if rank == 0:
         print(json.dumps(line), flush=True)
-    vol.free()
-    ctx.close()
+    if ctx is not None:
+        vol.free()
+        ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched views (64 views of a 512^3 volume, one persistent launch in a CUDA graph)
+# ---------------------------------------------------------------------------
+def run_batched(rp, dev, args, seed):
+    """FP16 batched path (one graph replay per batch) against per-frame plain FP32 launches."""
+    n, k = args.batch_n, args.batch_views
+    src = synth.make_shell_volume(n, seed=seed, device=dev)
+    stored = synth.to_storage(src, "f16").float()
+    tf = synth.make_tf(stored, "T_anom")
+    views = synth.random_views(seed + 1, k)
+    brushes = [synth.brush_from_quantiles(stored, synth.jittered_spec("c3", seed + 100 + i, 0.1))
+               for i in range(k)]
+    del stored
+    ctx = rp.Context(dev.index)
+    v16 = ctx.load_volume(src, store="f16")
+    v16.build_bricks(n_lod=2)
+    v16.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    v32 = ctx.load_volume(src, store="f32")
+    v32.build_bricks(n_lod=2)
+    v32.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    del src
+    outs = [torch.empty((h, w, 4), dtype=torch.float32, device=dev) for _, w, h in views]
+    stats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    qs = [dict(vol=v16, cam=c, w=w, h=h, lo=b.lo, hi=b.hi, mask=b.active_mask, out=o, stats=stats)
+          for (c, w, h), b, o in zip(views, brushes, outs)]
+    tune16, _ = rp.autotune(ctx, [dict(q, stats=None) for q in qs[:8]], reps=2)
+    tune32, _ = rp.autotune(ctx, [dict(q, vol=v32, stats=None) for q in qs[:8]], reps=2)
+    batch = rp.Batch(ctx, k)
+    for _ in range(3):
+        batch.render(qs)
+    torch.cuda.synchronize()
+    stats.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = args.batch_reps
+    e0.record()
+    for _ in range(reps):
+        batch.render(qs)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    batch_samples = float(stats[0].item()) / reps
+    # per-frame plain FP32 launches of the same views: brush edit + render, one frame at a time
+    pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+
+    def plain(variant, skip):
+        for (c, w, h), b, o in zip(views, brushes, outs):
+            v32.set_brush(b.lo, b.hi, b.active_mask)
+            v32.render(c, w, h, out=o, stats=pstats, variant=variant, skip=skip)
+
+    def time_plain(variant, skip):
+        plain(variant, skip)
+        torch.cuda.synchronize()
+        pstats.zero_()
+        e0.record()
+        for _ in range(max(1, reps // 2)):
+            plain(variant, skip)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / max(1, reps // 2), float(pstats[0].item()) / max(1, reps // 2)
+
+    plain_ms, plain_samples = time_plain(1, True)                      # default launch choices
+    tuned_ms, _ = time_plain(tune32["variant"], tune32["skip"])         # FP32 with its own tuning
+    pixels = sum(w * h for _, w, h in views)
+    batch.close()
+    v16.free()
+    v32.free()
+    ctx.close()
+    return {"what": f"{k} views of {n}^3 x 6, image sizes uniform in {{256,512,1024,2048}}^2 "
+                    f"({pixels / 1e6:.1f} MP), random orbit cameras, distinct jittered 6-variable brushes",
+            "batched_f16": {"ms_per_batch": round(batch_ms, 3), "samples_per_s": round(batch_samples / (batch_ms / 1e3), 1),
+                            "views_per_s": round(k / (batch_ms / 1e3), 1), "launch": "1 CUDA graph (classify x2 + persistent render)"},
+            "plain_f32_per_frame": {"ms_per_batch": round(plain_ms, 3),
+                                    "samples_per_s": round(plain_samples / (plain_ms / 1e3), 1),
+                                    "launch": f"{k} x (set_brush + render), default launch choices (8x4 tiles, skipping on)"},
+            "plain_f32_per_frame_tuned": {"ms_per_batch": round(tuned_ms, 3), "tuning": tune32},
+            "batched_tuning": tune16,
+            "speedup": round(plain_ms / batch_ms, 3),
+            "speedup_vs_tuned_plain": round(tuned_ms / batch_ms, 3),
+            "samples_per_batch": batch_samples}
 
 
 # ---------------------------------------------------------------------------
@@ -392,6 +488,10 @@ def main(argv=None):
     ap.add_argument("--cpu-row-stride", type=int, default=16)
     ap.add_argument("--ref-row-stride", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batched comparison")
+    ap.add_argument("--batch-n", type=int, default=512)
+    ap.add_argument("--batch-views", type=int, default=64)
+    ap.add_argument("--batch-reps", type=int, default=10)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
     if args.impl == "reference":

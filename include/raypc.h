@@ -86,13 +86,24 @@ typedef struct raypc_camera {
     float tan_half_vfov;
 } raypc_camera;
 
+/* Launch choices of a render. Neither changes any pixel: they only change
+ * speed. RAYPC_AUTO takes the choice raypc_autotune measured fastest for this
+ * device, storage dtype and grid edge, or the default if none was measured. */
+#define RAYPC_AUTO 0
+#define RAYPC_SKIP_ON 1           /* brick-level empty-space skipping on (default) */
+#define RAYPC_SKIP_OFF 2
+#define RAYPC_VARIANT_8x4 1       /* warp tile 8x4 pixels, block tile 16x8 (default) */
+#define RAYPC_VARIANT_16x2 2      /* warp tile 16x2, block tile 32x4 */
+#define RAYPC_VARIANT_4x8 3       /* warp tile 4x8, block tile 8x16 */
+
 /* Options of one render. Zero-initialised = defaults except `ert`, which the
  * caller sets explicitly. */
 typedef struct raypc_render_opts {
     float step;          /* world distance between lattice samples; <= 0: half a
                             voxel of the rendered level, i.e. 1/n_level         */
     int ert;             /* nonzero: stop a ray once its opacity A >= 1 - 2^-12 */
-    int no_skip;         /* nonzero: disable brick-level empty-space skipping   */
+    int skip;            /* RAYPC_AUTO, RAYPC_SKIP_ON or RAYPC_SKIP_OFF          */
+    int variant;         /* RAYPC_AUTO or RAYPC_VARIANT_*                         */
     float bg[4];         /* premultiplied background RGBA composited under     */
     uint32_t *counts_dev;/* optional [h][w][2] uint32: per pixel, lattice
                             samples marched and samples kept (debug/testing)    */
@@ -203,6 +214,75 @@ raypc_status raypc_set_tf(raypc_ctx *ctx, int vol, const float *rgbs, int color_
 raypc_status raypc_render(raypc_ctx *ctx, int vol, int lod, const raypc_camera *cam,
                           int w, int h, const raypc_render_opts *opts,
                           float *out_rgba_dev, unsigned long long *stats_dev, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched rendering (many views and brushes in one launch)                */
+/* ---------------------------------------------------------------------- */
+
+/* One view of a batch: a volume level, a camera and image, its own brush box
+ * (same meaning as raypc_set_brush, applied to this view only; the volume's
+ * own brush is not used or changed), render options and caller-owned outputs
+ * (out_rgba_dev [h][w][4] float32, 16-byte aligned; stats_dev optional). The
+ * transfer function is the volume's (raypc_set_tf). */
+typedef struct raypc_view {
+    int vol;
+    int lod;
+    raypc_camera cam;
+    int w, h;
+    float lo[RAYPC_MAX_VARS];
+    float hi[RAYPC_MAX_VARS];
+    uint32_t active_mask;
+    raypc_render_opts opts;
+    float *out_rgba_dev;
+    unsigned long long *stats_dev;
+} raypc_view;
+
+typedef struct raypc_batch raypc_batch;
+
+/* A reusable batch of up to max_views views (1..4096). It owns a device view
+ * table, per-view classification bitmasks, a tile counter and a CUDA graph of
+ * the batched launch (table upload, per-view brick classification, one
+ * persistent render kernel), captured on first use and replayed afterwards.
+ * Allocates device and pinned host memory. */
+raypc_status raypc_batch_create(raypc_ctx *ctx, int max_views, raypc_batch **out);
+raypc_status raypc_batch_destroy(raypc_batch *batch);
+
+/* Render nviews views in one launch on `stream` (Section 2.2 per view, same
+ * results bit for bit as raypc_render of each view with its brush set). Every
+ * view's volume must have bricks built (not stale after an update), a transfer
+ * function, and the same storage dtype. The tile variant of the launch is view
+ * 0's (after RAYPC_AUTO resolution); skipping is chosen per view. Work is split into 16x8-pixel tiles
+ * pulled dynamically by persistent thread blocks, so large and small images
+ * balance across the GPU. The call returns after enqueueing; it may wait for
+ * the batch submitted two calls earlier on this batch object to finish (the
+ * view table is double-buffered). Concurrent calls on one batch object must be
+ * serialised by the caller. */
+raypc_status raypc_render_batch(raypc_batch *batch, const raypc_view *views, int nviews, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuning of the render launch                                         */
+/* ---------------------------------------------------------------------- */
+
+typedef struct raypc_tuning {
+    int variant;         /* RAYPC_VARIANT_*            */
+    int skip;            /* RAYPC_SKIP_ON / _OFF       */
+    float ms;            /* measured time per round    */
+} raypc_tuning;
+
+/* Time every launch choice (3 tile variants x skipping on/off) on the given
+ * views -- each view classified under its own brush, rendered one frame at a
+ * time, `reps` rounds after one warm-up round -- and remember the fastest for
+ * this device, the views' storage dtype and the grid edge of view 0's level.
+ * Later renders and batches with RAYPC_AUTO use it. If the environment
+ * variable RAYPC_TUNE_CACHE names a file, the table is read from it on first
+ * use and rewritten after each tuning. The views' output buffers are
+ * overwritten. Synchronises `stream`. all_out (optional) receives the 6
+ * measurements in the order variant 1..3, each with skipping on then off. */
+raypc_status raypc_autotune(raypc_ctx *ctx, const raypc_view *views, int nviews, int reps,
+                            raypc_tuning *best_out, raypc_tuning *all_out, void *stream);
+
+/* The tuned choice for (device of ctx, dtype, grid edge n); RAYPC_ERR_NOT_FOUND if none. */
+raypc_status raypc_get_tuning(raypc_ctx *ctx, int dtype, int n, raypc_tuning *out);
 
 /* ---------------------------------------------------------------------- */
 /* Parallel-coordinates histograms (Section 2.1 PC data; Fig. 2)            */

@@ -14,19 +14,16 @@
 #include <mutex>
 #include <string>
 
-#include "raypc.h"
-#include "common.cuh"
+#include "runtime.h"
 
 using namespace raypc;
 
-namespace raypc {
-void count_launches(int k);
-}
-
 namespace {
-
 thread_local std::string g_err;
 std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+namespace raypc {
 
 raypc_status fail(raypc_status code, const char* fmt, ...) {
     char buf[512];
@@ -46,81 +43,7 @@ raypc_status cuda_fail(cudaError_t e, const char* what) {
     return fail(RAYPC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                  \
-    do {                                                \
-        cudaError_t e_ = (call);                        \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) return;
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return;
-        ok = true;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-struct Level {
-    int n = 0, nb = 0;
-    void* cells = nullptr;     // planar values, storage dtype
-    void* pairs = nullptr;     // per-variable x-pairs (render layout)
-    size_t cells_bytes = 0, pairs_bytes = 0;
-    float* bmin = nullptr;
-    float* bmax = nullptr;
-    uint32_t* active = nullptr;
-    uint32_t* skippable = nullptr;
-    uint32_t* list = nullptr;
-    uint32_t* n_active = nullptr;
-    unsigned* pass_count = nullptr;
-    bool bricks = false;
-    bool classified = false;
-    size_t nbricks() const { return (size_t)nb * nb * nb; }
-    size_t nwords() const { return (nbricks() + 31) / 32; }
-};
-
-struct Volume {
-    int nvars = 0, dtype = 0;
-    bool stale = false;       // level 0 updated since the last build_bricks
-    float r_in = 0.f, r_out = 1.f;
-    int nlev = 0;             // built levels (1 + coarser)
-    Level lv[1 + RAYPC_MAX_LOD];
-    bool brush_set = false;
-    BrushArgs brush{};
-    float4* tf = nullptr;
-    bool tf_set = false;
-    int color_var = 0;
-    float tf_lo = 0.f, tf_hi = 1.f;
-    size_t bytes = 0;
-};
-
-size_t elem_size(int dtype) { return dtype == RAYPC_F16 ? 2 : 4; }
-
-}  // namespace
-
-struct raypc_ctx {
-    int device = 0;
-    size_t budget = 0;
-    size_t used = 0;
-    std::mutex mu;
-    std::map<int, Volume*> vols;
-    int next_id = 1;
-
-    // Device allocation charged against the budget.
-    raypc_status alloc(void** p, size_t bytes, size_t* charged) {
-        if (budget && used + bytes > budget)
-            return fail(RAYPC_ERR_OOM, "HBM budget exceeded: %zu used + %zu requested > %zu", used, bytes, budget);
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
-        used += bytes;
-        *charged += bytes;
-        return RAYPC_OK;
-    }
-};
+}  // namespace raypc
 
 namespace {
 
@@ -148,18 +71,6 @@ void free_volume(raypc_ctx* ctx, Volume* V) {
     delete V;
 }
 
-raypc_status get_volume(raypc_ctx* ctx, int vol, Volume** out) {
-    auto it = ctx->vols.find(vol);
-    if (it == ctx->vols.end()) return fail(RAYPC_ERR_NOT_FOUND, "unknown volume id %d", vol);
-    *out = it->second;
-    return RAYPC_OK;
-}
-
-raypc_status get_level(Volume* V, int lod, Level** out) {
-    if (lod < 0 || lod >= V->nlev) return fail(RAYPC_ERR_NOT_FOUND, "level %d not built (have %d)", lod, V->nlev);
-    *out = &V->lv[lod];
-    return RAYPC_OK;
-}
 
 // Classify every built level under the current brush (three launches total).
 raypc_status classify_all(Volume* V, cudaStream_t s) {
@@ -241,8 +152,105 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
 void raypc::count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 
 namespace raypc {
+
 void set_last_error(const char* msg) { g_err = msg; }
+
+raypc_status get_volume(raypc_ctx* ctx, int vol, Volume** out) {
+    auto it = ctx->vols.find(vol);
+    if (it == ctx->vols.end()) return fail(RAYPC_ERR_NOT_FOUND, "unknown volume id %d", vol);
+    *out = it->second;
+    return RAYPC_OK;
 }
+
+raypc_status get_level(Volume* V, int lod, Level** out) {
+    if (lod < 0 || lod >= V->nlev) return fail(RAYPC_ERR_NOT_FOUND, "level %d not built (have %d)", lod, V->nlev);
+    *out = &V->lv[lod];
+    return RAYPC_OK;
+}
+
+raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int w, int h,
+                              const raypc_render_opts* opts, float* out_rgba_dev,
+                              unsigned long long* stats_dev, RenderArgs* out) {
+    if (!cam || !out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (w < 1 || h < 1 || w > 32768 || h > 32768) return fail(RAYPC_ERR_INVALID_ARG, "image size %d x %d out of range", w, h);
+    if (((uintptr_t)out_rgba_dev) & 15u) return fail(RAYPC_ERR_INVALID_ARG, "out_rgba_dev must be 16-byte aligned");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(cam->eye[i]) || !isfinite(cam->target[i]) || !isfinite(cam->up[i]))
+            return fail(RAYPC_ERR_INVALID_ARG, "non-finite camera");
+    if (!(cam->tan_half_vfov > 0.f) || !isfinite(cam->tan_half_vfov)) return fail(RAYPC_ERR_INVALID_ARG, "tan_half_vfov must be > 0");
+    {
+        float fx = cam->target[0] - cam->eye[0], fy = cam->target[1] - cam->eye[1], fz = cam->target[2] - cam->eye[2];
+        if (fx == 0.f && fy == 0.f && fz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "eye == target");
+        float cx = fy * cam->up[2] - fz * cam->up[1], cy = fz * cam->up[0] - fx * cam->up[2], cz = fx * cam->up[1] - fy * cam->up[0];
+        if (cx == 0.f && cy == 0.f && cz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "up is parallel to the view direction");
+    }
+    raypc_render_opts o{};
+    o.ert = 1;
+    if (opts) o = *opts;
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(o.bg[i])) return fail(RAYPC_ERR_INVALID_ARG, "non-finite background");
+    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run before render");
+    if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of the level are not built");
+    if (!V->tf_set) return fail(RAYPC_ERR_INVALID_ARG, "set_tf must run before render");
+    float dt = o.step > 0.f ? o.step : 1.0f / (float)L->n;
+    if (!isfinite(dt) || dt < 2.0f * V->r_out / 4194304.0f)
+        return fail(RAYPC_ERR_INVALID_ARG, "step %g too small (at most 2^21 samples per chord)", dt);
+    RenderArgs a{};
+    a.lv.cells = L->cells;
+    a.lv.pairs = L->pairs;
+    a.lv.n = L->n;
+    a.lv.nb = L->nb;
+    a.lv.bmin = L->bmin;
+    a.lv.bmax = L->bmax;
+    a.lv.active = L->active;
+    a.lv.skippable = L->skippable;
+    a.nvars = V->nvars;
+    a.brush = V->brush;
+    a.pass_count = L->pass_count;
+    for (int i = 0; i < 3; ++i) { a.eye[i] = cam->eye[i]; a.target[i] = cam->target[i]; a.up[i] = cam->up[i]; }
+    a.tan_half = cam->tan_half_vfov;
+    a.w = w;
+    a.h = h;
+    a.dt = dt;
+    a.rin2 = V->r_in * V->r_in;
+    a.rout2 = V->r_out * V->r_out;
+    a.tf = V->tf;
+    a.color_var = V->color_var;
+    a.tf_lo = V->tf_lo;
+    a.tf_scale = 255.0f / (V->tf_hi - V->tf_lo);
+    for (int i = 0; i < 4; ++i) a.bg[i] = o.bg[i];
+    a.ert = o.ert ? 1 : 0;
+    if (o.skip < RAYPC_AUTO || o.skip > RAYPC_SKIP_OFF) return fail(RAYPC_ERR_INVALID_ARG, "bad skip option %d", o.skip);
+    if (o.variant < RAYPC_AUTO || o.variant > kNumVariants) return fail(RAYPC_ERR_INVALID_ARG, "bad variant %d", o.variant);
+    int variant = o.variant, skip = o.skip;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    resolve_launch(dev, V->dtype, L->n, &variant, &skip);
+    a.skip = skip == RAYPC_SKIP_OFF ? 0 : 1;
+    a.variant = variant;
+    a.out = reinterpret_cast<float4*>(out_rgba_dev);
+    a.counts = o.counts_dev;
+    a.stats = stats_dev;
+    *out = a;
+    return RAYPC_OK;
+}
+
+raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, uint32_t active_mask, BrushArgs* out) {
+    if (!lo || !hi) return fail(RAYPC_ERR_INVALID_ARG, "NULL brush bounds");
+    if (active_mask >> V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "active_mask 0x%x names variables >= nvars %d", active_mask, V->nvars);
+    BrushArgs b{};
+    for (int v = 0; v < kMaxVars; ++v) { b.lo[v] = -INFINITY; b.hi[v] = INFINITY; }
+    for (int v = 0; v < V->nvars; ++v) {
+        if (isnan(lo[v]) || isnan(hi[v])) return fail(RAYPC_ERR_INVALID_ARG, "NaN brush bound for variable %d", v);
+        b.lo[v] = lo[v];
+        b.hi[v] = hi[v];
+    }
+    b.mask = active_mask;
+    *out = b;
+    return RAYPC_OK;
+}
+
+}  // namespace raypc
 
 extern "C" {
 
@@ -405,15 +413,8 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
     Volume* V;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    if (active_mask >> V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "active_mask 0x%x names variables >= nvars %d", active_mask, V->nvars);
     BrushArgs b{};
-    for (int v = 0; v < kMaxVars; ++v) { b.lo[v] = -INFINITY; b.hi[v] = INFINITY; }
-    for (int v = 0; v < V->nvars; ++v) {
-        if (isnan(lo[v]) || isnan(hi[v])) return fail(RAYPC_ERR_INVALID_ARG, "NaN brush bound for variable %d", v);
-        b.lo[v] = lo[v];
-        b.hi[v] = hi[v];
-    }
-    b.mask = active_mask;
+    if ((st = brush_from_host(V, lo, hi, active_mask, &b))) return st;
     V->brush = b;
     V->brush_set = true;
     if (V->stale) {            // coarser levels are rebuilt by raypc_build_bricks, which classifies lazily
@@ -455,24 +456,7 @@ raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_
 raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* cam, int w, int h,
                           const raypc_render_opts* opts, float* out_rgba_dev,
                           unsigned long long* stats_dev, void* stream) {
-    if (!ctx || !cam || !out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
-    if (w < 1 || h < 1 || w > 32768 || h > 32768) return fail(RAYPC_ERR_INVALID_ARG, "image size %d x %d out of range", w, h);
-    if (((uintptr_t)out_rgba_dev) & 15u) return fail(RAYPC_ERR_INVALID_ARG, "out_rgba_dev must be 16-byte aligned");
-    for (int i = 0; i < 3; ++i)
-        if (!isfinite(cam->eye[i]) || !isfinite(cam->target[i]) || !isfinite(cam->up[i]))
-            return fail(RAYPC_ERR_INVALID_ARG, "non-finite camera");
-    if (!(cam->tan_half_vfov > 0.f) || !isfinite(cam->tan_half_vfov)) return fail(RAYPC_ERR_INVALID_ARG, "tan_half_vfov must be > 0");
-    {
-        float fx = cam->target[0] - cam->eye[0], fy = cam->target[1] - cam->eye[1], fz = cam->target[2] - cam->eye[2];
-        if (fx == 0.f && fy == 0.f && fz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "eye == target");
-        float cx = fy * cam->up[2] - fz * cam->up[1], cy = fz * cam->up[0] - fx * cam->up[2], cz = fx * cam->up[1] - fy * cam->up[0];
-        if (cx == 0.f && cy == 0.f && cz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "up is parallel to the view direction");
-    }
-    raypc_render_opts o{};
-    o.ert = 1;
-    if (opts) o = *opts;
-    for (int i = 0; i < 4; ++i)
-        if (!isfinite(o.bg[i])) return fail(RAYPC_ERR_INVALID_ARG, "non-finite background");
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     Volume* V;
@@ -480,42 +464,9 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if (st) return st;
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
-    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run before render");
-    if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d are not built", lod);
-    if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
-    if (!V->tf_set) return fail(RAYPC_ERR_INVALID_ARG, "set_tf must run before render");
-    float dt = o.step > 0.f ? o.step : 1.0f / (float)L->n;
-    if (!isfinite(dt) || dt < 2.0f * V->r_out / 4194304.0f)
-        return fail(RAYPC_ERR_INVALID_ARG, "step %g too small (at most 2^21 samples per chord)", dt);
     RenderArgs a{};
-    a.lv.cells = L->cells;
-    a.lv.pairs = L->pairs;
-    a.lv.n = L->n;
-    a.lv.nb = L->nb;
-    a.lv.bmin = L->bmin;
-    a.lv.bmax = L->bmax;
-    a.lv.active = L->active;
-    a.lv.skippable = L->skippable;
-    a.nvars = V->nvars;
-    a.brush = V->brush;
-    a.pass_count = L->pass_count;
-    for (int i = 0; i < 3; ++i) { a.eye[i] = cam->eye[i]; a.target[i] = cam->target[i]; a.up[i] = cam->up[i]; }
-    a.tan_half = cam->tan_half_vfov;
-    a.w = w;
-    a.h = h;
-    a.dt = dt;
-    a.rin2 = V->r_in * V->r_in;
-    a.rout2 = V->r_out * V->r_out;
-    a.tf = V->tf;
-    a.color_var = V->color_var;
-    a.tf_lo = V->tf_lo;
-    a.tf_scale = 255.0f / (V->tf_hi - V->tf_lo);
-    for (int i = 0; i < 4; ++i) a.bg[i] = o.bg[i];
-    a.ert = o.ert ? 1 : 0;
-    a.skip = o.no_skip ? 0 : 1;
-    a.out = reinterpret_cast<float4*>(out_rgba_dev);
-    a.counts = o.counts_dev;
-    a.stats = stats_dev;
+    if ((st = make_render_args(V, L, cam, w, h, opts, out_rgba_dev, stats_dev, &a))) return st;
+    if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }

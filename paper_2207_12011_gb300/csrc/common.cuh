@@ -128,10 +128,40 @@ struct RenderArgs {
     float tf_lo, tf_scale;        // s = (v - tf_lo) * tf_scale
     float bg[4];
     int ert, skip;
+    int variant;                  // 1..kNumVariants (tile shape of the launch)
     float4* out;
     uint32_t* counts;             // optional [h][w][2]
     unsigned long long* stats;    // optional kNStats counters
 };
+
+// One view of a batched render: the march arguments (lv.active / lv.skippable
+// / pass_count point at this view's own classification), the level's brick
+// min/max for that classification, and the view's ranges in the flat brick
+// and tile spaces of the batch.
+struct BatchView {
+    RenderArgs a;
+    const float* bmin;
+    const float* bmax;
+    unsigned long long cls_begin;  // first flat brick index (multiple of 32)
+    int tiles_x;                   // tiles per image row
+    int tile_begin;                // first flat tile index
+};
+
+struct BatchHeader {
+    int nviews;
+    int total_tiles;
+    unsigned long long cls_total;  // flat brick range over all views (multiple of 32)
+};
+
+// Render launch variants: a 128-thread block is 2 x 2 warps; each warp marches
+// a WTW x (32 / WTW) pixel tile. Variant 1: 8 x 4 warps (16 x 8 block tile),
+// 2: 16 x 2 (32 x 4), 3: 4 x 8 (8 x 16). All variants produce identical
+// pixels (the march of a pixel does not depend on the tiling).
+constexpr int kRenderThreads = 128;
+constexpr int kNumVariants = 3;
+__host__ __device__ constexpr int warp_tile_w(int variant) { return variant == 2 ? 16 : variant == 3 ? 4 : 8; }
+__host__ __device__ constexpr int block_tile_w(int variant) { return 2 * warp_tile_w(variant); }
+__host__ __device__ constexpr int block_tile_h(int variant) { return 2 * (32 / warp_tile_w(variant)); }
 
 struct HistArgs {
     const void* cells;
@@ -148,6 +178,65 @@ struct HistArgs {
     int64_t s_in, s_out;
     uint32_t* out;                // (naxes-1) x bins x bins
 };
+
+// World box that the samples assigned to brick b (lower interpolation index in
+// [8b, 8b+8)) can occupy along one axis, widened by 2^-10; the first and last
+// bricks also own the clamped border.
+__device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, float& lo, float& hi) {
+    lo = __fsub_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
+    hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick + kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
+    if (b == 0) lo = -2.0f;
+    if (b == nb - 1) hi = 2.0f;
+}
+
+// Brush classification of brick b of a level with nb bricks per axis
+// (sc = 2/n): active iff its widened sample box meets the shell and, for every
+// restricted v, max_v + d >= lo_v and min_v - d <= hi_v with
+// d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
+// rounding). pass_bits gets bit v set for each restricted variable the brick
+// passes on its own (only meaningful when the box meets the shell).
+__device__ __forceinline__ bool classify_brick(size_t b, int nb, float sc, float rin2, float rout2,
+                                               const BrushArgs& brush, int nvars, const float* bmin,
+                                               const float* bmax, unsigned& pass_bits) {
+    int c[3] = {(int)(b % nb), (int)((b / nb) % nb), (int)(b / ((size_t)nb * nb))};
+    float nearc[3], farc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float lo, hi;
+        brick_box_axis(c[a], nb, sc, lo, hi);
+        nearc[a] = (lo > 0.0f) ? lo : ((hi < 0.0f) ? -hi : 0.0f);
+        farc[a] = fmaxf(fabsf(lo), fabsf(hi));
+    }
+    const float near2 = dot3_rn(nearc[0], nearc[1], nearc[2], nearc[0], nearc[1], nearc[2]);
+    const float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
+    pass_bits = 0;
+    if (!((near2 <= rout2) && (far2 >= rin2))) return false;
+    bool all = true;
+    for (int v = 0; v < nvars; ++v) {
+        if (!((brush.mask >> v) & 1u)) continue;
+        const float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
+        const float m = fmaxf(fabsf(mn), fabsf(mx));
+        const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+        const bool ok = (__fadd_rn(mx, d) >= brush.lo[v]) && (__fsub_rn(mn, d) <= brush.hi[v]);
+        if (ok) pass_bits |= 1u << v;
+        all = all && ok;
+    }
+    return all;
+}
+
+// Skippable = brick b and its existing 26 neighbours are inactive.
+__device__ __forceinline__ bool skippable_brick(size_t b, int nb, const uint32_t* active) {
+    const int x = (int)(b % nb), y = (int)((b / nb) % nb), z = (int)(b / ((size_t)nb * nb));
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int xx = x + dx, yy = y + dy, zz = z + dz;
+                if (xx < 0 || yy < 0 || zz < 0 || xx >= nb || yy >= nb || zz >= nb) continue;
+                const size_t id = ((size_t)zz * nb + yy) * nb + xx;
+                if ((active[id >> 5] >> (id & 31)) & 1u) return false;
+            }
+    return true;
+}
 
 // Classification of all built levels of a volume in one launch per kernel.
 struct ClassifyLevel {
@@ -183,6 +272,14 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
                        float* bmin, float* bmax, cudaStream_t stream);
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
+// Batched render: per-view classification, then a persistent kernel that pulls
+// (view, 16x8 tile) work items from *tile_counter (zeroed by the caller).
+// Grids are fixed by the caller (cls_blocks for the grid-stride classification,
+// blocks for the persistent render) so the launch can be captured in a graph;
+// launches are not counted here (the caller counts each replay).
+cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter,
+                                int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream);
+int render_batch_blocks_per_sm(int dtype, int variant);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
 }  // namespace raypc

@@ -14,14 +14,9 @@
 
 #include <mutex>
 
-#include "raypc.h"
-#include "common.cuh"
+#include "runtime.h"
 
 using namespace raypc;
-
-namespace raypc {
-void set_last_error(const char* msg);
-}
 
 namespace {
 

@@ -2,7 +2,9 @@
 //
 // One thread per ray; a warp covers an 8x4 pixel tile so that neighbouring
 // rays fetch neighbouring vertices, and a 128-thread block covers 16x8
-// pixels. Per lattice sample: position, interpolation cell and brick
+// pixels. The per-pixel march is one device function shared by the
+// single-frame kernel and the persistent batched kernel, so a view renders
+// bit-identically alone and inside a batch. Per lattice sample: position, interpolation cell and brick
 // (exactly rounded FP32), brick activity bit (samples in inactive bricks
 // cannot pass the brush or the shell test), shell test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
@@ -23,7 +25,7 @@ namespace raypc {
 
 namespace {
 
-constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+constexpr int kThreads = kRenderThreads;
 
 __device__ __forceinline__ void normalize_rn(float& x, float& y, float& z) {
     float l = __fsqrt_rn(dot3_rn(x, y, z, x, y, z));
@@ -60,36 +62,47 @@ __device__ __forceinline__ const void* plane_ptr(const void* pairs, int DT, int 
     return reinterpret_cast<const char*>(pairs) + bytes;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
-    __shared__ float4 s_tf[kTF];
-    __shared__ int s_order[kMaxVars];
-    __shared__ int s_nact;
-    __shared__ float s_lo[kMaxVars], s_hi[kMaxVars];
-    for (int i = threadIdx.x; i < kTF; i += kThreads) s_tf[i] = A.tf[i];
+// Per-view block state: the transfer function (staged in shared memory), the
+// restricted variables in increasing order of how many bricks pass them alone
+// (most selective first), and the brush bounds.
+struct ViewShared {
+    float4 tf[kTF];
+    int order[kMaxVars];
+    int nact;
+    float lo[kMaxVars], hi[kMaxVars];
+};
+
+// Fill S for view A (all threads of the block call it; the caller syncs).
+__device__ __forceinline__ void load_view_shared(const RenderArgs& A, ViewShared& S) {
+    for (int i = threadIdx.x; i < kTF; i += blockDim.x) S.tf[i] = A.tf[i];
     if (threadIdx.x == 0) {
-        // restricted variables, most selective (fewest passing bricks) first
         int cnt = 0;
         unsigned pc[kMaxVars];
         for (int v = 0; v < A.nvars; ++v) {
             if (!((A.brush.mask >> v) & 1u)) continue;
             unsigned c = A.pass_count ? A.pass_count[v] : 0u;
             int j = cnt++;
-            while (j > 0 && pc[j - 1] > c) { pc[j] = pc[j - 1]; s_order[j] = s_order[j - 1]; --j; }
+            while (j > 0 && pc[j - 1] > c) { pc[j] = pc[j - 1]; S.order[j] = S.order[j - 1]; --j; }
             pc[j] = c;
-            s_order[j] = v;
+            S.order[j] = v;
         }
-        s_nact = cnt;
+        S.nact = cnt;
     }
     if (threadIdx.x < kMaxVars) {
-        s_lo[threadIdx.x] = A.brush.lo[threadIdx.x];
-        s_hi[threadIdx.x] = A.brush.hi[threadIdx.x];
+        S.lo[threadIdx.x] = A.brush.lo[threadIdx.x];
+        S.hi[threadIdx.x] = A.brush.hi[threadIdx.x];
     }
-    __syncthreads();
+}
 
+// March the ray of this thread's pixel in 16x8 tile (tile_x, tile_y) of view A
+// and write its pixel, optional counts and (warp-aggregated) statistics. All
+// 32 lanes of every warp must call it.
+template <int DT, int VAR>
+__device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShared& S, int tile_x, int tile_y) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = blockIdx.x * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int py = blockIdx.y * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    constexpr int WTW = warp_tile_w(VAR), WTH = 32 / WTW;
+    const int px = tile_x * block_tile_w(VAR) + (warp & 1) * WTW + (lane % WTW);
+    const int py = tile_y * block_tile_h(VAR) + (warp >> 1) * WTH + (lane / WTW);
     const bool inside = px < A.w && py < A.h;
 
     unsigned marched = 0, kept = 0, evald = 0, skipped = 0, hit = 0, ert_hit = 0;
@@ -129,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
             const float hn = 0.5f * (float)n, off = hn - 0.5f;
             const float dt = A.dt;
             const size_t sy_ = (size_t)n, sz_ = (size_t)n * n, plane = sz_ * n;
-            const int nact = s_nact;
+            const int nact = S.nact;
             // Lattice end: the first k with t_k >= t1, found once per ray from an
             // estimate corrected with the exact predicate (t_k is non-decreasing in k).
             const float inv_dt = 1.0f / dt;
@@ -180,9 +193,9 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
                 float vc = 0.0f;
                 bool have_c = false;
                 for (int j = 0; j < nact; ++j) {
-                    const int v = s_order[j];
+                    const int v = S.order[j];
                     const float s = interp_var<DT>(plane_ptr(A.lv.pairs, DT, v, plane), base, sy_, sz_, fx, fy, fz);
-                    if (!(s >= s_lo[v] && s <= s_hi[v])) { pass = false; break; }
+                    if (!(s >= S.lo[v] && s <= S.hi[v])) { pass = false; break; }
                     if (v == A.color_var) { vc = s; have_c = true; }
                 }
                 if (!pass) { ++k; continue; }
@@ -194,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
                 sp = fminf(fmaxf(sp, 0.0f), 255.0f);
                 const int jj = min((int)sp, kTF - 2);
                 const float w = sp - (float)jj;
-                const float4 e0 = s_tf[jj], e1 = s_tf[jj + 1];
+                const float4 e0 = S.tf[jj], e1 = S.tf[jj + 1];
                 const float er = fmaf(w, e1.x - e0.x, e0.x);
                 const float eg = fmaf(w, e1.y - e0.y, e0.y);
                 const float eb = fmaf(w, e1.z - e0.z, e0.z);
@@ -233,19 +246,169 @@ __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
     }
 }
 
-template <int DT>
+template <int DT, int VAR>
+__global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
+    __shared__ ViewShared S;
+    load_view_shared(A, S);
+    __syncthreads();
+    march_pixel<DT, VAR>(A, S, blockIdx.x, blockIdx.y);
+}
+
+// Per-view classification of a batch: one thread per (view, brick); a warp's
+// 32 consecutive flat indices always belong to one view.
+__device__ __forceinline__ int view_of_brick(const BatchHeader& H, const BatchView* V, unsigned long long g) {
+    int lo = 0, hi = H.nviews - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (V[mid].cls_begin <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_classify_views(const BatchHeader* __restrict__ hdr, const BatchView* __restrict__ views) {
+    const BatchHeader H = *hdr;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < H.cls_total; g += stride) {
+        const int vi = view_of_brick(H, views, g - lane);
+        const BatchView& V = views[vi];
+        const int nb = V.a.lv.nb;
+        const size_t nbricks = (size_t)nb * nb * nb;
+        const size_t b = g - V.cls_begin;
+        unsigned pass_bits = 0;
+        const bool act = b < nbricks &&
+            classify_brick(b, nb, 2.0f / (float)V.a.lv.n, V.a.rin2, V.a.rout2, V.a.brush, V.a.nvars, V.bmin, V.bmax, pass_bits);
+        const unsigned word = __ballot_sync(0xffffffffu, act);
+        uint32_t* active = const_cast<uint32_t*>(V.a.lv.active);
+        if (lane == 0) active[b >> 5] = word;
+        for (int v = 0; v < V.a.nvars; ++v) {
+            const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
+            if (lane == 0 && cnt) atomicAdd(const_cast<unsigned*>(V.a.pass_count) + v, cnt);
+        }
+    }
+}
+
+__global__ void k_skippable_views(const BatchHeader* __restrict__ hdr, const BatchView* __restrict__ views) {
+    const BatchHeader H = *hdr;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < H.cls_total; g += stride) {
+        const int vi = view_of_brick(H, views, g - lane);
+        const BatchView& V = views[vi];
+        const int nb = V.a.lv.nb;
+        const size_t b = g - V.cls_begin;
+        const bool s = b < (size_t)nb * nb * nb && skippable_brick(b, nb, V.a.lv.active);
+        const unsigned word = __ballot_sync(0xffffffffu, s);
+        if (lane == 0) const_cast<uint32_t*>(V.a.lv.skippable)[b >> 5] = word;
+    }
+}
+
+// Persistent batched render: every block repeatedly takes the next 16x8 tile
+// of the whole batch from an atomic counter (tiles of one view are
+// contiguous, views in submission order), reloads its per-view shared state
+// when the view changes, and marches the tile. Blocks exit when the tiles run
+// out, so the kernel's lifetime is bounded by the batch.
+template <int DT, int VAR>
+__global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader* __restrict__ hdr,
+                                                           const BatchView* __restrict__ views,
+                                                           unsigned* __restrict__ tile_counter) {
+    __shared__ ViewShared S;
+    __shared__ RenderArgs s_args;
+    __shared__ int s_tile, s_view, s_tx, s_ty;
+    const BatchHeader H = *hdr;
+    int cur_view = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = (int)atomicAdd(tile_counter, 1u);
+            int vi = -1;
+            if (t < H.total_tiles) {
+                int lo = 0, hi = H.nviews - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (views[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+                }
+                vi = lo;
+                const int local = t - views[vi].tile_begin;
+                s_tx = local % views[vi].tiles_x;
+                s_ty = local / views[vi].tiles_x;
+            }
+            s_tile = t;
+            s_view = vi;
+        }
+        __syncthreads();
+        if (s_tile >= H.total_tiles) break;
+        const int vi = s_view;
+        if (vi != cur_view) {
+            if (threadIdx.x == 0) s_args = views[vi].a;
+            __syncthreads();
+            load_view_shared(s_args, S);
+            cur_view = vi;
+            __syncthreads();
+        }
+        march_pixel<DT, VAR>(s_args, S, s_tx, s_ty);
+        __syncthreads();   // s_tile / s_tx / S are rewritten for the next tile
+    }
+}
+
+template <int DT, int VAR>
 cudaError_t launch_t(const RenderArgs& a, cudaStream_t stream) {
-    dim3 grid((a.w + kTileW - 1) / kTileW, (a.h + kTileH - 1) / kTileH);
-    k_render<DT><<<grid, kThreads, 0, stream>>>(a);
+    dim3 grid((a.w + block_tile_w(VAR) - 1) / block_tile_w(VAR), (a.h + block_tile_h(VAR) - 1) / block_tile_h(VAR));
+    k_render<DT, VAR><<<grid, kThreads, 0, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_dt(const RenderArgs& a, cudaStream_t stream) {
+    switch (a.variant) {
+        case 2: return launch_t<DT, 2>(a, stream);
+        case 3: return launch_t<DT, 3>(a, stream);
+        default: return launch_t<DT, 1>(a, stream);
+    }
+}
+
+template <int DT, int VAR>
+void batch_kernels(const BatchHeader* hdr, const BatchView* views, unsigned* counter, int blocks, cudaStream_t s) {
+    k_render_batch<DT, VAR><<<blocks, kThreads, 0, s>>>(hdr, views, counter);
+}
+
+template <int DT, int VAR>
+int batch_occupancy() {
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<DT, VAR>, kThreads, 0);
+    return blocks > 0 ? blocks : 1;
 }
 
 }  // namespace
 
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream) {
-    if (dtype == kF16) return launch_t<kF16>(a, stream);
-    return launch_t<kF32>(a, stream);
+    if (dtype == kF16) return launch_dt<kF16>(a, stream);
+    return launch_dt<kF32>(a, stream);
+}
+
+int render_batch_blocks_per_sm(int dtype, int variant) {
+    if (dtype == kF16) return variant == 2 ? batch_occupancy<kF16, 2>() : variant == 3 ? batch_occupancy<kF16, 3>() : batch_occupancy<kF16, 1>();
+    return variant == 2 ? batch_occupancy<kF32, 2>() : variant == 3 ? batch_occupancy<kF32, 3>() : batch_occupancy<kF32, 1>();
+}
+
+cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter,
+                                int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream) {
+    k_classify_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skippable_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (dtype == kF16) {
+        if (variant == 2) batch_kernels<kF16, 2>(hdr, views, tile_counter, blocks, stream);
+        else if (variant == 3) batch_kernels<kF16, 3>(hdr, views, tile_counter, blocks, stream);
+        else batch_kernels<kF16, 1>(hdr, views, tile_counter, blocks, stream);
+    } else {
+        if (variant == 2) batch_kernels<kF32, 2>(hdr, views, tile_counter, blocks, stream);
+        else if (variant == 3) batch_kernels<kF32, 3>(hdr, views, tile_counter, blocks, stream);
+        else batch_kernels<kF32, 1>(hdr, views, tile_counter, blocks, stream);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace raypc

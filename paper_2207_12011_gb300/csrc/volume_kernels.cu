@@ -146,16 +146,6 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
     }
 }
 
-// World box that the samples assigned to brick b (lower interpolation index in
-// [8b, 8b+8)) can occupy along one axis, widened by 2^-10; the first and
-// last bricks also own the clamped border.
-__device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, float& lo, float& hi) {
-    lo = __fsub_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
-    hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick + kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
-    if (b == 0) lo = -2.0f;
-    if (b == nb - 1) hi = 2.0f;
-}
-
 // Locate the level of a flat brick index over all levels (<= 3 levels).
 __device__ __forceinline__ int level_of(const ClassifyArgs& C, size_t g, size_t& b) {
     int l = 0;
@@ -181,34 +171,8 @@ __global__ void k_classify(ClassifyArgs C) {
     const bool valid = in_range && b < nbricks;
     bool act = false;
     unsigned pass_bits = 0;
-    if (valid) {
-        const float sc = L.sc;
-        int c[3] = {(int)(b % nb), (int)((b / nb) % nb), (int)(b / ((size_t)nb * nb))};
-        float nearc[3], farc[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float lo, hi;
-            brick_box_axis(c[a], nb, sc, lo, hi);
-            nearc[a] = (lo > 0.0f) ? lo : ((hi < 0.0f) ? -hi : 0.0f);
-            farc[a] = fmaxf(fabsf(lo), fabsf(hi));
-        }
-        const float near2 = dot3_rn(nearc[0], nearc[1], nearc[2], nearc[0], nearc[1], nearc[2]);
-        const float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
-        act = (near2 <= C.rout2) && (far2 >= C.rin2);
-        if (act) {
-            bool all = true;
-            for (int v = 0; v < C.nvars; ++v) {
-                if (!((C.brush.mask >> v) & 1u)) continue;
-                const float mn = L.bmin[b * C.nvars + v], mx = L.bmax[b * C.nvars + v];
-                const float m = fmaxf(fabsf(mn), fabsf(mx));
-                const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-                const bool ok = (__fadd_rn(mx, d) >= C.brush.lo[v]) && (__fsub_rn(mn, d) <= C.brush.hi[v]);
-                if (ok) pass_bits |= 1u << v;
-                all = all && ok;
-            }
-            act = all;
-        }
-    }
+    if (valid)
+        act = classify_brick(b, nb, L.sc, C.rin2, C.rout2, C.brush, C.nvars, L.bmin, L.bmax, pass_bits);
     const unsigned word = __ballot_sync(0xffffffffu, act);
     if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.active[b >> 5] = word;
     for (int v = 0; v < C.nvars; ++v) {
@@ -228,19 +192,7 @@ __global__ void k_skippable(ClassifyArgs C) {
     const size_t nbricks = (size_t)nb * nb * nb;
     const bool in_range = g < C.total;
     const bool valid = in_range && b < nbricks;
-    bool s = false;
-    if (valid) {
-        const int x = (int)(b % nb), y = (int)((b / nb) % nb), z = (int)(b / ((size_t)nb * nb));
-        s = true;
-        for (int dz = -1; dz <= 1 && s; ++dz)
-            for (int dy = -1; dy <= 1 && s; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int xx = x + dx, yy = y + dy, zz = z + dz;
-                    if (xx < 0 || yy < 0 || zz < 0 || xx >= nb || yy >= nb || zz >= nb) continue;
-                    const size_t id = ((size_t)zz * nb + yy) * nb + xx;
-                    if ((L.active[id >> 5] >> (id & 31)) & 1u) { s = false; break; }
-                }
-    }
+    const bool s = valid && skippable_brick(b, nb, L.active);
     const unsigned word = __ballot_sync(0xffffffffu, s);
     if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.skippable[b >> 5] = word;
 }

@@ -39,9 +39,26 @@ class Camera(ctypes.Structure):
                 ("up", ctypes.c_float * 3), ("tan_half_vfov", ctypes.c_float)]
 
 
+AUTO = 0
+SKIP_ON, SKIP_OFF = 1, 2
+VARIANTS = {1: "8x4", 2: "16x2", 3: "4x8"}
+
+
 class RenderOpts(ctypes.Structure):
-    _fields_ = [("step", ctypes.c_float), ("ert", ctypes.c_int), ("no_skip", ctypes.c_int),
-                ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p)]
+    _fields_ = [("step", ctypes.c_float), ("ert", ctypes.c_int), ("skip", ctypes.c_int),
+                ("variant", ctypes.c_int), ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("skip", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("vol", ctypes.c_int), ("lod", ctypes.c_int), ("cam", Camera),
+                ("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("lo", ctypes.c_float * MAX_VARS), ("hi", ctypes.c_float * MAX_VARS),
+                ("active_mask", ctypes.c_uint32), ("opts", RenderOpts),
+                ("out_rgba_dev", ctypes.c_void_p), ("stats_dev", ctypes.c_void_p)]
 
 
 _lib = None
@@ -65,6 +82,11 @@ _SIGS = {
     "raypc_export_volume": [_P, _I, _I, _P, _P],
     "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
     "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
+    "raypc_batch_create": [_P, _I, ctypes.POINTER(_P)],
+    "raypc_batch_destroy": [_P],
+    "raypc_render_batch": [_P, ctypes.POINTER(View), _I, _P],
+    "raypc_autotune": [_P, ctypes.POINTER(View), _I, _I, ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), _P],
+    "raypc_get_tuning": [_P, _I, _I, ctypes.POINTER(Tuning)],
     "raypc_pc_histogram_noalloc": [_P, _I, _I, _I, _F, _F, _P, _P, _U32, _I, _P, _I, _I, _P, _P, _P],
 }
 
@@ -243,21 +265,20 @@ class Volume:
               float(v_hi), _stream(stream))
 
     def render(self, cam, w: int, h: int, lod: int = 0, step: float = 0.0, ert: bool = True,
-               skip: bool = True, bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
-               counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None, stream=None):
-        """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None)."""
+               skip: bool | None = None, bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
+               counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None,
+               variant: int = AUTO, stream=None):
+        """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None).
+
+        skip: None = tuned choice (default on), True / False = brick skipping on / off;
+        variant: AUTO or 1..3 (tile shape). Neither changes any pixel.
+        """
         dev = torch.device("cuda", self.ctx.device)
         if out is None:
             out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
         if counts is True:
             counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
-        o = RenderOpts()
-        o.step = float(step)
-        o.ert = int(bool(ert))
-        o.no_skip = int(not skip)
-        for i in range(4):
-            o.bg[i] = float(bg[i])
-        o.counts_dev = counts.data_ptr() if isinstance(counts, torch.Tensor) else None
+        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant)
         c = camera_from(cam)
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _call("raypc_render", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
@@ -335,6 +356,118 @@ def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=Non
           float(r_out), _fptr(lo_a), _fptr(hi_a), int(active_mask) & 0xFFFFFFFF, int(bool(use_brush)),
           _fptr(order), naxes, bins, _fptr(e), ctypes.c_void_p(out.data_ptr()), _stream(stream))
     return out
+
+
+def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, variant=AUTO) -> RenderOpts:
+    o = RenderOpts()
+    o.step = float(step)
+    o.ert = int(bool(ert))
+    o.skip = AUTO if skip is None else (SKIP_ON if skip else SKIP_OFF)
+    o.variant = int(variant)
+    for i in range(4):
+        o.bg[i] = float(bg[i])
+    o.counts_dev = counts.data_ptr() if isinstance(counts, torch.Tensor) else None
+    return o
+
+
+def _view_array(ctx, views):
+    """ctypes array of raypc_view from dicts (see Batch.render); returns (array, outputs)."""
+    n = len(views)
+    arr = (View * n)()
+    outs = []
+    dev = torch.device("cuda", ctx.device)
+    for i, q in enumerate(views):
+        vol = q["vol"]
+        w, h = int(q["w"]), int(q["h"])
+        out = q.get("out")
+        if out is None:
+            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+        counts = q.get("counts")
+        if counts is True:
+            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
+        stats = q.get("stats")
+        v = arr[i]
+        v.vol = vol.id
+        v.lod = int(q.get("lod", 0))
+        v.cam = camera_from(q["cam"])
+        v.w, v.h = w, h
+        lo = np.full(MAX_VARS, -np.inf, np.float32)
+        hi = np.full(MAX_VARS, np.inf, np.float32)
+        lo[: vol.nvars] = np.asarray(q["lo"], np.float32)[: vol.nvars]
+        hi[: vol.nvars] = np.asarray(q["hi"], np.float32)[: vol.nvars]
+        for k in range(MAX_VARS):
+            v.lo[k], v.hi[k] = float(lo[k]), float(hi[k])
+        v.active_mask = int(q.get("mask", 0)) & 0xFFFFFFFF
+        v.opts = _opts(q.get("step", 0.0), q.get("ert", True), q.get("skip", None),
+                       q.get("bg", (0.0, 0.0, 0.0, 0.0)), counts if isinstance(counts, torch.Tensor) else None,
+                       q.get("variant", AUTO))
+        v.out_rgba_dev = out.data_ptr()
+        v.stats_dev = stats.data_ptr() if stats is not None else None
+        outs.append((out, counts if isinstance(counts, torch.Tensor) else None))
+    return arr, outs
+
+
+def autotune(ctx: Context, views, reps: int = 3, stream=None):
+    """Time the launch choices on these views; returns (best, all) as dicts."""
+    arr, outs = _view_array(ctx, views)
+    best = Tuning()
+    allv = (Tuning * 6)()
+    _call("raypc_autotune", ctx.handle, arr, len(views), int(reps), ctypes.byref(best), allv, _stream(stream))
+    conv = lambda t: {"variant": t.variant, "tile": VARIANTS.get(t.variant), "skip": t.skip == SKIP_ON, "ms": t.ms}
+    return conv(best), [conv(t) for t in allv]
+
+
+def get_tuning(ctx: Context, dtype: int, n: int):
+    t = Tuning()
+    L = lib()
+    st = L.raypc_get_tuning(ctx.handle, int(dtype), int(n), ctypes.byref(t))
+    if st == 6:
+        return None
+    if st != 0:
+        raise RaypcError(st, "raypc_get_tuning", L.raypc_last_error().decode(errors="replace"))
+    return {"variant": t.variant, "skip": t.skip == SKIP_ON, "ms": t.ms}
+
+
+class Batch:
+    """A reusable batched render (one persistent launch in a CUDA graph per call)."""
+
+    def __init__(self, ctx: Context, max_views: int):
+        self.ctx = ctx
+        self.max_views = int(max_views)
+        h = ctypes.c_void_p()
+        _call("raypc_batch_create", ctx.handle, self.max_views, ctypes.byref(h))
+        self._h = h
+        self._keep = [None, None]
+        self._slot = 0
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().raypc_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def render(self, views, stream=None):
+        """views: list of dicts with vol (Volume), cam, w, h, lo, hi, mask and optional lod,
+        step, ert, skip, bg, out, counts (True or tensor), stats (tensor). Returns the list of
+        (image, counts or None)."""
+        n = len(views)
+        arr, outs = _view_array(self.ctx, views)
+        _call("raypc_render_batch", self._h, arr, n, _stream(stream))
+        # keep the outputs alive at least until this table slot is reused
+        self._keep[self._slot] = outs
+        self._slot ^= 1
+        return outs
 
 
 def unpack_bits(words: torch.Tensor, nbits: int) -> np.ndarray:

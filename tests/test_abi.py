@@ -69,3 +69,20 @@ def test_host_side_validation_without_gpu(libpath):
     assert b"NULL" in lib.raypc_last_error()
     lib.raypc_destroy.argtypes = [ctypes.c_void_p]
     assert lib.raypc_destroy(None) == 0
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """ctypes mirrors of the public structs have the C sizes and offsets."""
+    import paper_2207_12011_gb300.raypc as rp
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "raypc.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(raypc_camera), sizeof(raypc_render_opts),'
+        ' sizeof(raypc_view), offsetof(raypc_view, opts), offsetof(raypc_view, out_rgba_dev),'
+        ' offsetof(raypc_render_opts, counts_dev)); return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(rp.Camera), ctypes.sizeof(rp.RenderOpts), ctypes.sizeof(rp.View),
+            rp.View.opts.offset, rp.View.out_rgba_dev.offset, rp.RenderOpts.counts_dev.offset]
+    assert got == want
