@@ -260,6 +260,85 @@ raypc_status raypc_batch_destroy(raypc_batch *batch);
 raypc_status raypc_render_batch(raypc_batch *batch, const raypc_view *views, int nviews, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving (continuous batching of render and histogram requests)          */
+/* ---------------------------------------------------------------------- */
+
+/* The paper's client renders asynchronously and progressively: the frame
+ * loop does not wait for the ray tracer, and passes are refined while the
+ * camera rests (Section 2, Section 2.2). The server here is the GPU-side
+ * counterpart for many clients: a request is a brushed render of a resident
+ * volume (optionally a coarse-level pass first, delivered early, then the
+ * full pass) or a brushed PC-histogram request. A server thread admits
+ * queued requests while slots and the output-memory budget allow, packs all
+ * admitted work (coarse passes first) into one batched render launch per loop
+ * turn on one of several streams, so requests that arrive while others run
+ * join the next launch and their work overlaps on the device, and records
+ * per-request timestamps. A request's results are identical to rendering /
+ * histogramming it alone. */
+
+#define RAYPC_REQ_RENDER 0
+#define RAYPC_REQ_HISTOGRAM 1
+
+typedef struct raypc_server raypc_server;
+
+typedef struct raypc_server_config {
+    int max_inflight;            /* admitted requests at once (1..4096)           */
+    size_t output_budget_bytes;  /* device memory for request outputs; 0 = none  */
+    int max_batch_views;         /* render passes per launch (1..4096)            */
+    int num_streams;             /* launch streams (1..8)                         */
+} raypc_server_config;
+
+typedef struct raypc_request {
+    int kind;                    /* RAYPC_REQ_RENDER or RAYPC_REQ_HISTOGRAM       */
+    int vol;                     /* resident volume (bricks built, TF set)         */
+    float lo[RAYPC_MAX_VARS];    /* the request's brush (raypc_set_brush meaning)  */
+    float hi[RAYPC_MAX_VARS];
+    uint32_t active_mask;
+    /* render */
+    raypc_camera cam;
+    int w, h;
+    int lod;                     /* level of the full pass                         */
+    int coarse_lod;              /* level of a first, early pass; -1 = none        */
+    raypc_render_opts opts;      /* counts_dev is ignored                          */
+    /* histogram (level lod) */
+    int axis_order[RAYPC_MAX_VARS];
+    int naxes, bins;
+    const float *edges;          /* host, naxes x (bins + 1); copied on submit     */
+    int use_brush;
+} raypc_request;
+
+typedef struct raypc_result {
+    int status;                  /* RAYPC_OK, or the error that ended the request  */
+    int coarse_ready;            /* coarse image available                         */
+    int done;                    /* all outputs available                          */
+    double t_submit, t_admit, t_coarse, t_done;   /* seconds, steady host clock    */
+    const float *coarse_dev;     /* [h][w][4], server-owned (NULL if none)         */
+    const float *image_dev;      /* [h][w][4], server-owned                        */
+    const uint32_t *hist_dev;    /* [naxes-1][bins][bins], server-owned            */
+    unsigned long long samples;  /* lattice samples marched by the full pass       */
+} raypc_result;
+
+/* Start a server on ctx (which must outlive it). Allocates its streams and
+ * batch objects and starts one host thread. */
+raypc_status raypc_server_create(raypc_ctx *ctx, const raypc_server_config *cfg, raypc_server **out);
+
+/* Stop the thread after the in-flight launches finish; pending requests end
+ * with RAYPC_ERR_BUSY; all outputs are freed. */
+raypc_status raypc_server_destroy(raypc_server *srv);
+
+/* Queue a request (validated now: volume, level, sizes, brush, edges). The
+ * request struct and its edges may be reused as soon as the call returns. */
+raypc_status raypc_serve_submit(raypc_server *srv, const raypc_request *req, uint64_t *out_id);
+
+/* State of a request; waits up to timeout_us for it to finish (0 = do not
+ * wait). Returns RAYPC_ERR_TIMEOUT if it is not done by then (the result
+ * still holds the progress so far), RAYPC_ERR_NOT_FOUND for unknown ids. */
+raypc_status raypc_serve_poll(raypc_server *srv, uint64_t id, int timeout_us, raypc_result *out);
+
+/* Free a finished request's outputs (returns their memory to the budget). */
+raypc_status raypc_serve_release(raypc_server *srv, uint64_t id);
+
+/* ---------------------------------------------------------------------- */
 /* Autotuning of the render launch                                         */
 /* ---------------------------------------------------------------------- */
 

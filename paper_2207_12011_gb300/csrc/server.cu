@@ -1,0 +1,555 @@
+// Serving runtime: continuous batching of brushed render and histogram
+// requests over resident volumes.
+//
+// Clients submit requests from any thread. One server thread loops:
+//   1. completions: query the completion event of every in-flight launch and
+//      publish finished passes (coarse image, full image, histogram);
+//   2. admission: move queued requests (FIFO) into service while fewer than
+//      max_inflight are in service and their outputs fit in the output pool
+//      (the HBM budget for results);
+//   3. launch: for every stream with fewer than two launches in flight, pack
+//      the pending passes of the requests homed on it -- coarse passes first,
+//      then full passes whose coarse pass was already launched, then
+//      histograms -- into one batched render launch (one CUDA graph replay)
+//      plus histogram kernels, and record a completion event.
+// Requests that arrive while launches are running are admitted as slots and
+// pool memory free up and join the next launch, so their work overlaps with
+// the work already on the GPU. Every pass uses the same kernels as a single
+// render / histogram call, so each result is identical alone and in the mix.
+// The server never waits on the GPU without a bound: it only queries events
+// and sleeps at most 100 us between turns while launches are in flight.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace raypc;
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over one preallocated device region (host bookkeeping
+// only, so admission never calls the CUDA allocator).
+struct Pool {
+    char* base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;   // offset -> length
+    size_t used = 0;
+    void init(char* b, size_t s) {
+        base = b;
+        size = s;
+        free_.clear();
+        free_[0] = s;
+        used = 0;
+    }
+    char* alloc(size_t n) {
+        n = align_up(n);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > n) free_[off + n] = len - n;
+                used += n;
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(char* p, size_t n) {
+        n = align_up(n);
+        size_t off = (size_t)(p - base);
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+enum Pass { kCoarse = 0, kFull = 1, kHist = 2 };
+
+struct Req {
+    uint64_t id = 0;
+    raypc_request r{};
+    std::vector<float> edges;
+    int status = RAYPC_OK;
+    int home = 0;                       // stream index
+    bool admitted = false, coarse_launched = false, full_launched = false;
+    bool coarse_ready = false, done = false;
+    double t_submit = 0, t_admit = 0, t_coarse = 0, t_done = 0;
+    char* mem = nullptr;
+    size_t mem_bytes = 0;
+    float* coarse = nullptr;
+    float* image = nullptr;
+    unsigned long long* stats = nullptr;
+    uint32_t* hist = nullptr;
+    float* d_edges = nullptr;
+    int slot = -1;                      // pinned host slot receiving the stats of the full pass
+    unsigned long long samples = 0;
+};
+
+struct Launch {
+    cudaEvent_t ev = nullptr;
+    int stream = 0;
+    std::vector<std::pair<Req*, int>> items;
+};
+
+size_t output_bytes(const raypc_request& r) {
+    if (r.kind == RAYPC_REQ_HISTOGRAM)
+        return align_up(sizeof(uint32_t) * (size_t)(r.naxes - 1) * r.bins * r.bins) +
+               align_up(sizeof(float) * (size_t)r.naxes * (r.bins + 1));
+    size_t img = align_up(sizeof(float) * 4 * (size_t)r.w * r.h);
+    return img * (r.coarse_lod >= 0 ? 2 : 1) + align_up(sizeof(unsigned long long) * kNStats);
+}
+
+}  // namespace
+
+struct raypc_server {
+    raypc_ctx* ctx = nullptr;
+    raypc_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req*> queued;
+    std::vector<Req*> active;           // admitted, not done
+    std::map<uint64_t, Req*> all;
+    std::vector<Launch> inflight;
+    std::vector<int> busy;              // launches in flight per stream
+    std::vector<cudaStream_t> streams;
+    std::vector<raypc_batch*> batches;
+    Pool pool;
+    char* pool_mem = nullptr;
+    unsigned long long* pinned = nullptr;   // max_inflight x kNStats, pinned host
+    std::vector<int> free_slots;
+    uint64_t next_id = 1;
+    int rr = 0;
+    bool stop = false;
+    std::thread th;
+};
+
+namespace {
+
+void finish(raypc_server* S, Req* q, int status) {
+    if (q->done) return;
+    if (q->slot >= 0) {
+        S->free_slots.push_back(q->slot);
+        q->slot = -1;
+    }
+    if (status != RAYPC_OK && q->status == RAYPC_OK) q->status = status;
+    q->done = true;
+    q->t_done = now_s();
+    for (size_t i = 0; i < S->active.size(); ++i)
+        if (S->active[i] == q) {
+            S->active.erase(S->active.begin() + i);
+            break;
+        }
+}
+
+// Histogram of one request on stream s (the request's brush, its own edges).
+raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(S->ctx->mu);
+    DeviceGuard g(S->ctx->device);
+    Volume* V;
+    Level* L;
+    raypc_status st;
+    if ((st = get_volume(S->ctx, q->r.vol, &V)) || (st = get_level(V, q->r.lod, &L))) return st;
+    if (V->stale && q->r.lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level is stale");
+    BrushArgs b{};
+    if ((st = brush_from_host(V, q->r.lo, q->r.hi, q->r.active_mask, &b))) return st;
+    const int naxes = q->r.naxes, bins = q->r.bins;
+    HistArgs h{};
+    h.cells = L->cells;
+    h.n = L->n;
+    h.nvars = V->nvars;
+    h.brush = b;
+    h.use_brush = q->r.use_brush ? 1 : 0;
+    h.naxes = naxes;
+    h.bins = bins;
+    for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? q->r.axis_order[a] : 0;
+    h.need_mask = h.use_brush ? b.mask : 0u;
+    for (int a = 0; a < naxes; ++a) {
+        h.need_mask |= 1u << q->r.axis_order[a];
+        const float e0 = q->edges[(size_t)a * (bins + 1)], eN = q->edges[(size_t)a * (bins + 1) + bins];
+        h.guess_e0[a] = e0;
+        h.guess_scale[a] = (eN > e0 && isfinite(eN - e0)) ? (float)bins / (eN - e0) : 0.0f;
+    }
+    double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
+    h.s_in = (int64_t)ceil(ri * ri);
+    h.s_out = (int64_t)floor(ro * ro);
+    h.edges = q->d_edges;
+    h.out = q->hist;
+    cudaError_t e = cudaMemcpyAsync(q->d_edges, q->edges.data(), sizeof(float) * q->edges.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
+    if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
+    if (e != cudaSuccess) return cuda_fail(e, "server histogram");
+    return RAYPC_OK;
+}
+
+void turn(raypc_server* S) {
+    // 1. completions
+    for (size_t i = 0; i < S->inflight.size();) {
+        Launch& L = S->inflight[i];
+        cudaError_t e = cudaEventQuery(L.ev);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        const double t = now_s();
+        for (auto& it : L.items) {
+            Req* q = it.first;
+            if (e != cudaSuccess) {
+                finish(S, q, RAYPC_ERR_CUDA);
+                continue;
+            }
+            if (it.second == kCoarse) {
+                q->coarse_ready = true;
+                q->t_coarse = t;
+            } else {
+                if (it.second == kFull && q->slot >= 0) q->samples = S->pinned[(size_t)q->slot * kNStats + RAYPC_STAT_MARCHED];
+                finish(S, q, RAYPC_OK);
+                q->t_done = t;
+            }
+        }
+        if (e != cudaSuccess) cudaGetLastError();
+        cudaEventDestroy(L.ev);
+        S->busy[L.stream]--;
+        S->inflight.erase(S->inflight.begin() + i);
+        S->cv_done.notify_all();
+    }
+    // 2. admission (FIFO)
+    while (!S->queued.empty() && (int)S->active.size() < S->cfg.max_inflight) {
+        Req* q = S->queued.front();
+        char* m = S->pool.alloc(q->mem_bytes);
+        if (!m) break;                                  // wait for outputs to be released
+        S->queued.pop_front();
+        q->mem = m;
+        q->admitted = true;
+        q->t_admit = now_s();
+        q->home = S->rr;
+        S->rr = (S->rr + 1) % (int)S->streams.size();
+        char* p = m;
+        if (q->r.kind == RAYPC_REQ_HISTOGRAM) {
+            q->hist = reinterpret_cast<uint32_t*>(p);
+            p += align_up(sizeof(uint32_t) * (size_t)(q->r.naxes - 1) * q->r.bins * q->r.bins);
+            q->d_edges = reinterpret_cast<float*>(p);
+        } else {
+            const size_t img = align_up(sizeof(float) * 4 * (size_t)q->r.w * q->r.h);
+            q->image = reinterpret_cast<float*>(p);
+            p += img;
+            if (q->r.coarse_lod >= 0) {
+                q->coarse = reinterpret_cast<float*>(p);
+                p += img;
+            }
+            q->stats = reinterpret_cast<unsigned long long*>(p);
+            q->slot = S->free_slots.back();
+            S->free_slots.pop_back();
+        }
+        S->active.push_back(q);
+    }
+    // 3. launches, one per stream with room
+    for (int s = 0; s < (int)S->streams.size(); ++s) {
+        if (S->busy[s] >= 2) continue;
+        std::vector<raypc_view> views;
+        Launch L;
+        L.stream = s;
+        std::vector<Req*> hists;
+        for (int pass = kCoarse; pass <= kFull; ++pass)
+            for (Req* q : S->active) {
+                if ((int)views.size() >= S->cfg.max_batch_views) break;
+                if (q->home != s || q->r.kind != RAYPC_REQ_RENDER || q->done) continue;
+                const bool want = pass == kCoarse ? (q->r.coarse_lod >= 0 && !q->coarse_launched)
+                                                  : (!q->full_launched && (q->r.coarse_lod < 0 || q->coarse_launched));
+                if (!want) continue;
+                if (pass == kFull && q->r.coarse_lod >= 0) {
+                    bool same_launch = false;
+                    for (auto& it : L.items)
+                        if (it.first == q) same_launch = true;
+                    if (same_launch) continue;          // full pass goes in a later launch
+                }
+                raypc_view v{};
+                v.vol = q->r.vol;
+                v.lod = pass == kCoarse ? q->r.coarse_lod : q->r.lod;
+                v.cam = q->r.cam;
+                v.w = q->r.w;
+                v.h = q->r.h;
+                memcpy(v.lo, q->r.lo, sizeof(v.lo));
+                memcpy(v.hi, q->r.hi, sizeof(v.hi));
+                v.active_mask = q->r.active_mask;
+                v.opts = q->r.opts;
+                v.opts.counts_dev = nullptr;
+                v.out_rgba_dev = pass == kCoarse ? q->coarse : q->image;
+                v.stats_dev = pass == kCoarse ? nullptr : q->stats;
+                views.push_back(v);
+                L.items.push_back({q, pass});
+            }
+        for (Req* q : S->active)
+            if (q->home == s && q->r.kind == RAYPC_REQ_HISTOGRAM && !q->full_launched) hists.push_back(q);
+        if (views.empty() && hists.empty()) continue;
+        cudaStream_t st = S->streams[s];
+        for (auto& it : L.items)
+            if (it.second == kFull) cudaMemsetAsync(it.first->stats, 0, sizeof(unsigned long long) * kNStats, st);
+        raypc_status rs = views.empty() ? RAYPC_OK
+                                        : raypc_render_batch(S->batches[s], views.data(), (int)views.size(), st);
+        if (rs != RAYPC_OK) {
+            for (auto& it : L.items) finish(S, it.first, rs);
+            L.items.clear();
+        } else {
+            for (auto& it : L.items) {
+                if (it.second == kCoarse) {
+                    it.first->coarse_launched = true;
+                } else {
+                    it.first->full_launched = true;
+                    cudaMemcpyAsync(S->pinned + (size_t)it.first->slot * kNStats, it.first->stats,
+                                    sizeof(unsigned long long) * kNStats, cudaMemcpyDeviceToHost, st);
+                }
+            }
+        }
+        for (Req* q : hists) {
+            raypc_status hs = launch_hist(S, q, st);
+            if (hs != RAYPC_OK) {
+                finish(S, q, hs);
+                continue;
+            }
+            q->full_launched = true;
+            L.items.push_back({q, kHist});
+        }
+        if (L.items.empty()) continue;
+        if (cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(L.ev, st) != cudaSuccess) {
+            cudaStreamSynchronize(st);
+            for (auto& it : L.items) finish(S, it.first, RAYPC_ERR_CUDA);
+            if (L.ev) cudaEventDestroy(L.ev);
+            continue;
+        }
+        S->busy[s]++;
+        S->inflight.push_back(L);
+    }
+}
+
+void loop(raypc_server* S) {
+    DeviceGuard g(S->ctx->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        turn(S);
+        if (S->inflight.empty() && (S->queued.empty() || (int)S->active.size() >= S->cfg.max_inflight))
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        else
+            S->cv_work.wait_for(lk, std::chrono::microseconds(100));
+    }
+    // drain: wait for launches, end everything else
+    for (auto& L : S->inflight) {
+        cudaEventSynchronize(L.ev);
+        cudaEventDestroy(L.ev);
+    }
+    S->inflight.clear();
+    for (auto& kv : S->all)
+        if (!kv.second->done) finish(S, kv.second, RAYPC_ERR_BUSY);
+    S->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+raypc_status raypc_server_create(raypc_ctx* ctx, const raypc_server_config* cfg, raypc_server** out) {
+    if (!ctx || !cfg || !out) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (cfg->max_inflight < 1 || cfg->max_inflight > 4096) return fail(RAYPC_ERR_INVALID_ARG, "max_inflight not in 1..4096");
+    if (cfg->max_batch_views < 1 || cfg->max_batch_views > 4096) return fail(RAYPC_ERR_INVALID_ARG, "max_batch_views not in 1..4096");
+    if (cfg->num_streams < 1 || cfg->num_streams > 8) return fail(RAYPC_ERR_INVALID_ARG, "num_streams not in 1..8");
+    *out = nullptr;
+    raypc_server* S = new raypc_server();
+    S->ctx = ctx;
+    S->cfg = *cfg;
+    if (S->cfg.output_budget_bytes == 0) S->cfg.output_budget_bytes = (size_t)1 << 30;
+    raypc_status st = RAYPC_OK;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        DeviceGuard g(ctx->device);
+        size_t charged = 0;
+        st = ctx->alloc((void**)&S->pool_mem, S->cfg.output_budget_bytes, &charged);
+        if (st == RAYPC_OK) S->pool.init(S->pool_mem, S->cfg.output_budget_bytes);
+        if (st == RAYPC_OK) {
+            cudaError_t e = cudaHostAlloc((void**)&S->pinned, sizeof(unsigned long long) * kNStats * cfg->max_inflight,
+                                          cudaHostAllocDefault);
+            if (e != cudaSuccess) st = cuda_fail(e, "server pinned slots");
+            for (int i = cfg->max_inflight - 1; i >= 0; --i) S->free_slots.push_back(i);
+        }
+        for (int i = 0; i < cfg->num_streams && st == RAYPC_OK; ++i) {
+            cudaStream_t s = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+            if (e != cudaSuccess) { st = cuda_fail(e, "server stream"); break; }
+            S->streams.push_back(s);
+            S->busy.push_back(0);
+        }
+    }
+    for (int i = 0; i < cfg->num_streams && st == RAYPC_OK; ++i) {
+        raypc_batch* b = nullptr;
+        st = raypc_batch_create(ctx, cfg->max_batch_views, &b);
+        if (st == RAYPC_OK) S->batches.push_back(b);
+    }
+    if (st != RAYPC_OK) {
+        raypc_server_destroy(S);
+        return st;
+    }
+    S->th = std::thread(loop, S);
+    *out = S;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_server_destroy(raypc_server* S) {
+    if (!S) return RAYPC_OK;
+    if (S->th.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stop = true;
+        }
+        S->cv_work.notify_all();
+        S->th.join();
+    }
+    for (raypc_batch* b : S->batches) raypc_batch_destroy(b);
+    {
+        std::lock_guard<std::mutex> lk(S->ctx->mu);
+        DeviceGuard g(S->ctx->device);
+        for (cudaStream_t s : S->streams) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        if (S->pinned) cudaFreeHost(S->pinned);
+        if (S->pool_mem) {
+            cudaFree(S->pool_mem);
+            S->ctx->used -= S->cfg.output_budget_bytes < S->ctx->used ? S->cfg.output_budget_bytes : S->ctx->used;
+        }
+    }
+    for (auto& kv : S->all) delete kv.second;
+    delete S;
+    return RAYPC_OK;
+}
+
+raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_t* out_id) {
+    if (!S || !r || !out_id) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    Req* q = new Req();
+    q->r = *r;
+    q->t_submit = now_s();
+    {
+        // validate against the volume now (context lock only)
+        std::lock_guard<std::mutex> lk(S->ctx->mu);
+        DeviceGuard g(S->ctx->device);
+        Volume* V;
+        Level* L;
+        raypc_status st;
+        if ((st = get_volume(S->ctx, r->vol, &V)) || (st = get_level(V, r->lod, &L))) { delete q; return st; }
+        BrushArgs b{};
+        if ((st = brush_from_host(V, r->lo, r->hi, r->active_mask, &b))) { delete q; return st; }
+        if (r->kind == RAYPC_REQ_RENDER) {
+            RenderArgs a{};
+            if (r->w < 1 || r->h < 1 || r->w > 32768 || r->h > 32768) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "image size out of range"); }
+            // validate camera / options with a stand-in aligned output pointer
+            if ((st = make_render_args(V, L, &r->cam, r->w, r->h, &r->opts, reinterpret_cast<float*>(256), nullptr, &a))) { delete q; return st; }
+            if (r->coarse_lod >= 0) {
+                Level* C;
+                if ((st = get_level(V, r->coarse_lod, &C))) { delete q; return st; }
+                if (!C->bricks) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "coarse level has no bricks"); }
+            }
+        } else if (r->kind == RAYPC_REQ_HISTOGRAM) {
+            if (r->naxes < 2 || r->naxes > RAYPC_MAX_VARS || r->bins < 2 || r->bins > 1024 || !r->edges) {
+                delete q;
+                return fail(RAYPC_ERR_INVALID_ARG, "bad histogram request (naxes 2..8, bins 2..1024, edges)");
+            }
+            for (int a = 0; a < r->naxes; ++a) {
+                if (r->axis_order[a] < 0 || r->axis_order[a] >= V->nvars) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "bad axis"); }
+                for (int k = 0; k <= r->bins; ++k) {
+                    float e = r->edges[(size_t)a * (r->bins + 1) + k];
+                    if (isnan(e) || (k && e < r->edges[(size_t)a * (r->bins + 1) + k - 1])) {
+                        delete q;
+                        return fail(RAYPC_ERR_INVALID_ARG, "edges must be non-decreasing and not NaN");
+                    }
+                }
+            }
+            q->edges.assign(r->edges, r->edges + (size_t)r->naxes * (r->bins + 1));
+        } else {
+            delete q;
+            return fail(RAYPC_ERR_INVALID_ARG, "unknown request kind %d", r->kind);
+        }
+    }
+    q->r.edges = nullptr;
+    q->mem_bytes = output_bytes(q->r);
+    if (q->mem_bytes > S->cfg.output_budget_bytes) {
+        delete q;
+        return fail(RAYPC_ERR_OOM, "request outputs (%zu bytes) exceed the server's output budget", q->mem_bytes);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) { delete q; return fail(RAYPC_ERR_BUSY, "server is stopping"); }
+        q->id = S->next_id++;
+        S->all[q->id] = q;
+        S->queued.push_back(q);
+        *out_id = q->id;
+    }
+    S->cv_work.notify_all();
+    return RAYPC_OK;
+}
+
+raypc_status raypc_serve_poll(raypc_server* S, uint64_t id, int timeout_us, raypc_result* out) {
+    if (!S || !out) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(RAYPC_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)id);
+    Req* q = it->second;
+    if (!q->done && timeout_us > 0) {
+        const auto until = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+        S->cv_done.wait_until(lk, until, [&] { return q->done; });
+    }
+    memset(out, 0, sizeof(*out));
+    out->status = q->status;
+    out->coarse_ready = q->coarse_ready ? 1 : 0;
+    out->done = q->done ? 1 : 0;
+    out->t_submit = q->t_submit;
+    out->t_admit = q->t_admit;
+    out->t_coarse = q->t_coarse;
+    out->t_done = q->t_done;
+    out->coarse_dev = q->coarse;
+    out->image_dev = q->image;
+    out->hist_dev = q->hist;
+    out->samples = q->samples;
+    if (!q->done) return fail(RAYPC_ERR_TIMEOUT, "request %llu not done", (unsigned long long)id);
+    return RAYPC_OK;
+}
+
+raypc_status raypc_serve_release(raypc_server* S, uint64_t id) {
+    if (!S) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(RAYPC_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)id);
+    Req* q = it->second;
+    if (!q->done) return fail(RAYPC_ERR_BUSY, "request %llu still in service", (unsigned long long)id);
+    if (q->mem) S->pool.release(q->mem, q->mem_bytes);
+    S->all.erase(it);
+    delete q;
+    S->cv_work.notify_all();
+    return RAYPC_OK;
+}
+
+}  // extern "C"

@@ -49,6 +49,27 @@ class RenderOpts(ctypes.Structure):
                 ("variant", ctypes.c_int), ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int), ("output_budget_bytes", ctypes.c_size_t),
+                ("max_batch_views", ctypes.c_int), ("num_streams", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("vol", ctypes.c_int),
+                ("lo", ctypes.c_float * MAX_VARS), ("hi", ctypes.c_float * MAX_VARS),
+                ("active_mask", ctypes.c_uint32), ("cam", Camera), ("w", ctypes.c_int), ("h", ctypes.c_int),
+                ("lod", ctypes.c_int), ("coarse_lod", ctypes.c_int), ("opts", RenderOpts),
+                ("axis_order", ctypes.c_int * MAX_VARS), ("naxes", ctypes.c_int), ("bins", ctypes.c_int),
+                ("edges", ctypes.c_void_p), ("use_brush", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("coarse_ready", ctypes.c_int), ("done", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_coarse", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("coarse_dev", ctypes.c_void_p), ("image_dev", ctypes.c_void_p),
+                ("hist_dev", ctypes.c_void_p), ("samples", ctypes.c_ulonglong)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("skip", ctypes.c_int), ("ms", ctypes.c_float)]
 
@@ -87,6 +108,11 @@ _SIGS = {
     "raypc_render_batch": [_P, ctypes.POINTER(View), _I, _P],
     "raypc_autotune": [_P, ctypes.POINTER(View), _I, _I, ctypes.POINTER(Tuning), ctypes.POINTER(Tuning), _P],
     "raypc_get_tuning": [_P, _I, _I, ctypes.POINTER(Tuning)],
+    "raypc_server_create": [_P, ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)],
+    "raypc_server_destroy": [_P],
+    "raypc_serve_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
+    "raypc_serve_poll": [_P, ctypes.c_uint64, _I, ctypes.POINTER(Result)],
+    "raypc_serve_release": [_P, ctypes.c_uint64],
     "raypc_pc_histogram_noalloc": [_P, _I, _I, _I, _F, _F, _P, _P, _U32, _I, _P, _I, _I, _P, _P, _P],
 }
 
@@ -468,6 +494,122 @@ class Batch:
         self._keep[self._slot] = outs
         self._slot ^= 1
         return outs
+
+
+REQ_RENDER, REQ_HISTOGRAM = 0, 1
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory (valid until the owner frees it)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def _dev_tensor(ptr, shape, typestr, device):
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device=device)
+
+
+def _fill_brush(req, vol, lo, hi, mask):
+    lo_a = np.full(MAX_VARS, -np.inf, np.float32)
+    hi_a = np.full(MAX_VARS, np.inf, np.float32)
+    if lo is not None:
+        lo_a[: vol.nvars] = np.asarray(lo, np.float32)[: vol.nvars]
+    if hi is not None:
+        hi_a[: vol.nvars] = np.asarray(hi, np.float32)[: vol.nvars]
+    for k in range(MAX_VARS):
+        req.lo[k], req.hi[k] = float(lo_a[k]), float(hi_a[k])
+    req.active_mask = int(mask) & 0xFFFFFFFF
+
+
+class Server:
+    """Continuous-batching render / histogram server on a context (see raypc.h)."""
+
+    def __init__(self, ctx: Context, max_inflight: int = 64, output_budget_bytes: int = 1 << 30,
+                 max_batch_views: int = 64, num_streams: int = 2):
+        self.ctx = ctx
+        cfg = ServerConfig(int(max_inflight), int(output_budget_bytes), int(max_batch_views), int(num_streams))
+        h = ctypes.c_void_p()
+        _call("raypc_server_create", ctx.handle, ctypes.byref(cfg), ctypes.byref(h))
+        self._h = h
+        self._meta = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().raypc_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_render(self, vol, cam, w, h, lo=None, hi=None, mask=0, lod=0, coarse_lod=-1,
+                      ert=True, skip=None, variant=AUTO, bg=(0.0, 0.0, 0.0, 0.0)) -> int:
+        r = Request()
+        r.kind = REQ_RENDER
+        r.vol = vol.id
+        _fill_brush(r, vol, lo, hi, mask)
+        r.cam = camera_from(cam)
+        r.w, r.h = int(w), int(h)
+        r.lod = int(lod)
+        r.coarse_lod = int(coarse_lod)
+        r.opts = _opts(0.0, ert, skip, bg, None, variant)
+        rid = ctypes.c_uint64()
+        _call("raypc_serve_submit", self._h, ctypes.byref(r), ctypes.byref(rid))
+        self._meta[rid.value] = ("render", int(h), int(w), coarse_lod >= 0)
+        return rid.value
+
+    def submit_histogram(self, vol, axis_order, edges, lo=None, hi=None, mask=0, use_brush=True, lod=0) -> int:
+        r = Request()
+        r.kind = REQ_HISTOGRAM
+        r.vol = vol.id
+        _fill_brush(r, vol, lo, hi, mask)
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
+        r.naxes, r.bins = e.shape[0], e.shape[1] - 1
+        for a, v in enumerate(axis_order):
+            r.axis_order[a] = int(v)
+        r.edges = e.ctypes.data
+        r.use_brush = int(bool(use_brush))
+        r.lod = int(lod)
+        rid = ctypes.c_uint64()
+        _call("raypc_serve_submit", self._h, ctypes.byref(r), ctypes.byref(rid))
+        self._meta[rid.value] = ("hist", r.naxes, r.bins)
+        return rid.value
+
+    def poll(self, rid: int, timeout_us: int = 0):
+        """Progress of a request as a dict; image / coarse / hist are zero-copy device tensors."""
+        res = Result()
+        st = lib().raypc_serve_poll(self._h, ctypes.c_uint64(rid), int(timeout_us), ctypes.byref(res))
+        if st not in (0, 4):
+            raise RaypcError(st, "raypc_serve_poll", lib().raypc_last_error().decode(errors="replace"))
+        dev = torch.device("cuda", self.ctx.device)
+        meta = self._meta.get(rid)
+        out = {"status": res.status, "done": bool(res.done), "coarse_ready": bool(res.coarse_ready),
+               "t_submit": res.t_submit, "t_admit": res.t_admit, "t_coarse": res.t_coarse,
+               "t_done": res.t_done, "samples": int(res.samples)}
+        if meta and meta[0] == "render":
+            _, h, w, has_coarse = meta
+            if res.done and res.image_dev:
+                out["image"] = _dev_tensor(res.image_dev, (h, w, 4), "<f4", dev)
+            if res.coarse_ready and res.coarse_dev:
+                out["coarse"] = _dev_tensor(res.coarse_dev, (h, w, 4), "<f4", dev)
+        elif meta and res.done and res.hist_dev:
+            _, naxes, bins = meta
+            out["hist"] = _dev_tensor(res.hist_dev, (naxes - 1, bins, bins), "<i4", dev)
+        return out
+
+    def release(self, rid: int):
+        _call("raypc_serve_release", self._h, ctypes.c_uint64(rid))
+        self._meta.pop(rid, None)
 
 
 def unpack_bits(words: torch.Tensor, nbits: int) -> np.ndarray:

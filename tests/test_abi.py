@@ -79,10 +79,14 @@ def test_struct_layouts_match_the_binding(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "raypc.h"\n'
         'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(raypc_camera), sizeof(raypc_render_opts),'
         ' sizeof(raypc_view), offsetof(raypc_view, opts), offsetof(raypc_view, out_rgba_dev),'
-        ' offsetof(raypc_render_opts, counts_dev)); return 0;}\n')
+        ' offsetof(raypc_render_opts, counts_dev)); printf("%zu %zu %zu %zu %zu\\n", sizeof(raypc_request),'
+        ' sizeof(raypc_result), sizeof(raypc_server_config), offsetof(raypc_request, edges),'
+        ' sizeof(raypc_tuning)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(rp.Camera), ctypes.sizeof(rp.RenderOpts), ctypes.sizeof(rp.View),
-            rp.View.opts.offset, rp.View.out_rgba_dev.offset, rp.RenderOpts.counts_dev.offset]
+            rp.View.opts.offset, rp.View.out_rgba_dev.offset, rp.RenderOpts.counts_dev.offset,
+            ctypes.sizeof(rp.Request), ctypes.sizeof(rp.Result), ctypes.sizeof(rp.ServerConfig),
+            rp.Request.edges.offset, ctypes.sizeof(rp.Tuning)]
     assert got == want
