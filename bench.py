@@ -317,16 +317,20 @@ def run_ours(args):
     }
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args)
-    if not args.no_batched:
+    if not (args.no_batched and args.no_served):
         vol.free()
         ctx.close()
         ctx = None
         del wl.src
+    if not args.no_batched:
         torch.cuda.empty_cache()
         bt = run_batched(rp, dev, args, synth.DEFAULT_SEED + 1000 + rank)
         ms, samples = aggregate(bt["batched_f16"]["ms_per_batch"], bt["samples_per_batch"], dev)
         bt["batched_f16"]["samples_per_s_all_ranks"] = round(samples / (ms / 1e3), 1)
         line["batched"] = bt
+    if not args.no_served:
+        torch.cuda.empty_cache()
+        line["served"] = run_served(rp, dev, args, synth.DEFAULT_SEED + 2000 + rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ctx is not None:
@@ -419,6 +423,152 @@ def run_batched(rp, dev, args, seed):
 
 
 # ---------------------------------------------------------------------------
+# served: Poisson render + histogram stream over 3 resident volumes (time steps)
+# ---------------------------------------------------------------------------
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
+
+
+def run_served(rp, dev, args, seed):
+    n, nreq = args.serve_n, args.serve_requests
+    rng = np.random.default_rng(seed)
+    ctx = rp.Context(dev.index)
+    vols16, vols32, tables, edges_t, tfs = [], [], [], [], []
+    order = (0, 1, 2, 3, 4, 5)
+    for t in range(3):                                   # three time steps
+        src = synth.make_shell_volume(n, seed=seed + t, device=dev)
+        stored = synth.to_storage(src, "f16").float()
+        tables.append(synth.QuantileTable(stored))
+        edges_t.append(synth.make_edges(stored, order, bins=256))
+        tf = synth.make_tf(stored, "T_anom")
+        del stored
+        for store, lst in (("f16", vols16), ("f32", vols32)):
+            v = ctx.load_volume(src, store=store)
+            v.build_bricks(n_lod=1)
+            v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+            lst.append(v)
+        del src
+    torch.cuda.empty_cache()
+    # the request stream
+    reqs = []
+    sizes = (256, 512, 1024, 2048)
+    for i in range(nreq):
+        t = int(rng.integers(3))
+        b = tables[t].brush(synth.edited_spec("c3", seed + 31 * i, 0.1, 0.05))
+        if rng.uniform() < 0.8:
+            cam = synth.orbit_camera(rng.uniform(0, 360), rng.uniform(-60, 60), rng.uniform(2.6, 3.4))
+            sz = int(rng.choice(sizes))
+            reqs.append(("render", t, b, cam, sz))
+        else:
+            reqs.append(("hist", t, b, None, None))
+    outs = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
+    H = torch.empty((len(order) - 1, 256, 256), dtype=torch.int32, device=dev)
+    pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+
+    def plain_one(r):
+        """One request, FP32, per-frame launches: coarse LOD-1 pass, then the full pass."""
+        kind, t, b, cam, sz = r
+        v = vols32[t]
+        v.set_brush(b.lo, b.hi, b.active_mask)
+        if kind == "render":
+            v.render(cam, sz, sz, lod=1, out=outs_c[sz])
+            ev_c = torch.cuda.Event()
+            ev_c.record()
+            v.render(cam, sz, sz, out=outs[sz], stats=pstats)
+            return ev_c
+        v.pc_histogram(order, edges_t[t], use_brush=True, out=H)
+        return None
+
+    outs_c = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
+    # plain FP32 service time (one request at a time) sets the arrival rate
+    for r in reqs[:8]:
+        plain_one(r)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs[: min(64, nreq)]:
+        plain_one(r)
+        torch.cuda.current_stream().synchronize()
+    service = (time.perf_counter() - t0) / min(64, nreq)
+    rate = args.serve_load / service                     # requests per second
+    gaps = rng.exponential(1.0 / rate, nreq)
+    arrivals = np.cumsum(gaps) - gaps[0]
+
+    # plain FP32 FIFO: one worker, per-frame launches, same passes
+    pstats.zero_()
+    lat_plain, lat_plain_c = [], []
+    start = time.perf_counter()
+    for i, r in enumerate(reqs):
+        now = time.perf_counter() - start
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        ev_c = plain_one(r)
+        if ev_c is not None:
+            ev_c.synchronize()
+            lat_plain_c.append(time.perf_counter() - start - arrivals[i])
+        torch.cuda.current_stream().synchronize()
+        lat_plain.append(time.perf_counter() - start - arrivals[i])
+    plain_span = time.perf_counter() - start
+    plain_samples = float(pstats[0].item())
+
+    # served FP16: continuous batching, coarse LOD-1 pass then the full pass
+    import queue
+    import threading
+    srv = rp.Server(ctx, max_inflight=args.serve_inflight, output_budget_bytes=args.serve_budget_mb << 20,
+                    max_batch_views=64, num_streams=args.serve_streams,
+                    max_batch_pixels=int(args.serve_batch_mp * 1e6))
+    lat, lat_c, got = [], [], {"samples": 0.0}
+    pending = queue.Queue()
+
+    def consume():
+        while True:
+            rid = pending.get()
+            if rid is None:
+                return
+            res = srv.poll(rid, timeout_us=120_000_000)
+            lat.append(res["t_done"] - res["t_submit"])
+            if res.get("coarse") is not None:
+                lat_c.append(res["t_coarse"] - res["t_submit"])
+            got["samples"] += res["samples"]
+            srv.release(rid)
+
+    consumer = threading.Thread(target=consume)
+    consumer.start()
+    start = time.perf_counter()
+    for i, (kind, t, b, cam, sz) in enumerate(reqs):
+        now = time.perf_counter() - start
+        if now < arrivals[i]:
+            time.sleep(arrivals[i] - now)
+        if kind == "render":
+            rid = srv.submit_render(vols16[t], cam, sz, sz, b.lo, b.hi, b.active_mask, lod=0, coarse_lod=1)
+        else:
+            rid = srv.submit_histogram(vols16[t], order, edges_t[t], b.lo, b.hi, b.active_mask)
+        pending.put(rid)
+    pending.put(None)
+    consumer.join()
+    served_span = time.perf_counter() - start
+    samples = got["samples"]
+    srv.close()
+    for v in vols16 + vols32:
+        v.free()
+    ctx.close()
+    ms = lambda x: None if x is None else round(1e3 * x, 3)
+    return {"what": f"{nreq} Poisson requests (80% render at 256^2..2048^2, 20% 5x256^2 PC histograms) over "
+                    f"3 resident {n}^3 x 6 time steps, brush edit every request",
+            "arrival_rate_per_s": round(rate, 1), "load_vs_plain_capacity": args.serve_load,
+            "served_f16": {"p50_ms": ms(_pct(lat, 50)), "p99_ms": ms(_pct(lat, 99)),
+                           "coarse_p50_ms": ms(_pct(lat_c, 50)), "coarse_p99_ms": ms(_pct(lat_c, 99)),
+                           "samples_per_s": round(samples / served_span, 1),
+                           "how": f"continuous batching ({args.serve_streams} streams, <= {args.serve_batch_mp} MP per launch), "
+                                  "coarse LOD-1 pass then full pass, per-view completion records"},
+            "plain_f32_fifo": {"p50_ms": ms(_pct(lat_plain, 50)), "p99_ms": ms(_pct(lat_plain, 99)),
+                               "coarse_p50_ms": ms(_pct(lat_plain_c, 50)), "coarse_p99_ms": ms(_pct(lat_plain_c, 99)),
+                               "samples_per_s": round(plain_samples / plain_span, 1),
+                               "how": "one request at a time, per-frame launches, coarse LOD-1 pass then full pass"},
+            "p50_speedup": round(_pct(lat_plain, 50) / _pct(lat, 50), 3) if lat and lat_plain else None,
+            "p99_speedup": round(_pct(lat_plain, 99) / _pct(lat, 99), 3) if lat and lat_plain else None}
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle: baseline and reference arm
 # ---------------------------------------------------------------------------
 def oracle_frame_sample(wl, vol_np, rows, nthreads=0):
@@ -492,6 +642,14 @@ def main(argv=None):
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-reps", type=int, default=10)
+    ap.add_argument("--no-served", action="store_true", help="skip the served-stream comparison")
+    ap.add_argument("--serve-n", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / plain FP32 capacity")
+    ap.add_argument("--serve-inflight", type=int, default=32)
+    ap.add_argument("--serve-budget-mb", type=int, default=4096)
+    ap.add_argument("--serve-streams", type=int, default=3)
+    ap.add_argument("--serve-batch-mp", type=float, default=8.0)
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -269,11 +269,14 @@ raypc_status raypc_render_batch(raypc_batch *batch, const raypc_view *views, int
  * counterpart for many clients: a request is a brushed render of a resident
  * volume (optionally a coarse-level pass first, delivered early, then the
  * full pass) or a brushed PC-histogram request. A server thread admits
- * queued requests while slots and the output-memory budget allow, packs all
- * admitted work (coarse passes first) into one batched render launch per loop
- * turn on one of several streams, so requests that arrive while others run
- * join the next launch and their work overlaps on the device, and records
- * per-request timestamps. A request's results are identical to rendering /
+ * queued requests while slots and the output-memory budget allow, packs the
+ * admitted work into one batched render launch per loop turn and free stream
+ * (a request's coarse and full passes go into the same launch; coarse passes
+ * and small images first), so requests that arrive while others run join the
+ * next launch and their work overlaps on the device. The persistent kernel
+ * publishes each finished view through a record in mapped host memory, so a
+ * request completes when its own passes are done, not when its whole launch
+ * is. Per-request timestamps are recorded. A request's results are identical to rendering /
  * histogramming it alone. */
 
 #define RAYPC_REQ_RENDER 0
@@ -283,9 +286,11 @@ typedef struct raypc_server raypc_server;
 
 typedef struct raypc_server_config {
     int max_inflight;            /* admitted requests at once (1..4096)           */
-    size_t output_budget_bytes;  /* device memory for request outputs; 0 = none  */
+    size_t output_budget_bytes;  /* device memory for request outputs; 0 = 1 GiB */
     int max_batch_views;         /* render passes per launch (1..4096)            */
     int num_streams;             /* launch streams (1..8)                         */
+    long long max_batch_pixels;  /* pixels per launch (a single pass may exceed
+                                    it); 0 = no cap                               */
 } raypc_server_config;
 
 typedef struct raypc_request {

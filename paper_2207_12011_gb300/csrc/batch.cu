@@ -22,6 +22,11 @@ struct raypc_batch {
     char* d_table = nullptr;          // BatchHeader, then max_views BatchView (device)
     unsigned* d_counter = nullptr;    // tile counter
     unsigned* d_pass = nullptr;       // max_views x kMaxVars selectivity counts
+    unsigned* d_tiles = nullptr;      // max_views finished-tile counters
+    ViewDone* h_done[2] = {nullptr, nullptr};   // mapped pinned completion records per table slot
+    ViewDone* d_done[2] = {nullptr, nullptr};   // their device aliases
+    unsigned seq = 0;                 // launch sequence number
+    int last_slot = 0;
     char* h_table[2] = {nullptr, nullptr};   // pinned host copies of the table
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool used[2] = {false, false};
@@ -51,6 +56,7 @@ void release(raypc_batch* b) {
     for (int i = 0; i < 2; ++i) {
         if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
         if (b->h_table[i]) cudaFreeHost(b->h_table[i]);
+        if (b->h_done[i]) cudaFreeHost(b->h_done[i]);
         if (b->done[i]) cudaEventDestroy(b->done[i]);
     }
     for (uint32_t* p : b->bits)
@@ -58,6 +64,7 @@ void release(raypc_batch* b) {
     if (b->d_table) cudaFree(b->d_table);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_pass) cudaFree(b->d_pass);
+    if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->ctx) b->ctx->used -= b->charged < b->ctx->used ? b->charged : b->ctx->used;
 }
@@ -77,6 +84,7 @@ raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
     cudaError_t e = cudaMemcpyAsync(b->d_table, b->h_table[slot], b->table_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_pass, 0, sizeof(unsigned) * kMaxVars * b->max_views, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned) * b->max_views, s);
     if (e == cudaSuccess)
         e = launch_render_batch(hdr_of(b->d_table), views_of(b->d_table), b->d_counter, dtype, variant,
                                 cls_blocks, blocks, s);
@@ -91,6 +99,11 @@ raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
 }
 
 }  // namespace
+
+void raypc::batch_last_records(raypc_batch* b, const ViewDone** records, unsigned* seq) {
+    *records = b->h_done[b->last_slot];
+    *seq = b->seq;
+}
 
 extern "C" {
 
@@ -109,11 +122,17 @@ raypc_status raypc_batch_create(raypc_ctx* ctx, int max_views, raypc_batch** out
     raypc_status st = ctx->alloc((void**)&b->d_table, b->table_bytes, &b->charged);
     if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_counter, sizeof(unsigned), &b->charged);
     if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_pass, sizeof(unsigned) * kMaxVars * max_views, &b->charged);
+    if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_tiles, sizeof(unsigned) * max_views, &b->charged);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && st == RAYPC_OK && e == cudaSuccess; ++i) {
         e = cudaHostAlloc((void**)&b->h_table[i], b->table_bytes, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming);
         if (e == cudaSuccess) memset(b->h_table[i], 0, b->table_bytes);
+        if (e == cudaSuccess) e = cudaHostAlloc((void**)&b->h_done[i], sizeof(ViewDone) * max_views, cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            memset((void*)b->h_done[i], 0, sizeof(ViewDone) * max_views);
+            e = cudaHostGetDevicePointer((void**)&b->d_done[i], b->h_done[i], 0);
+        }
     }
     if (st == RAYPC_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (st == RAYPC_OK && e != cudaSuccess) st = cuda_fail(e, "batch resources");
@@ -186,7 +205,11 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         cls += (unsigned long long)(L->nbricks() + 31) / 32 * 32;
         bv.tiles_x = (q.w + block_tile_w(variant) - 1) / block_tile_w(variant);
         bv.tile_begin = (int)tiles;
-        tiles += (long long)bv.tiles_x * ((q.h + block_tile_h(variant) - 1) / block_tile_h(variant));
+        bv.ntiles = bv.tiles_x * ((q.h + block_tile_h(variant) - 1) / block_tile_h(variant));
+        tiles += (long long)bv.ntiles;
+        bv.tile_done = b->d_tiles + i;
+        bv.done = b->d_done[slot] + i;
+        bv.seq = b->seq + 1;
         if (tiles > 0x7fffffffLL) return fail(RAYPC_ERR_INVALID_ARG, "batch has more than 2^31 tiles");
         T[i] = bv;
     }
@@ -198,6 +221,8 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     CK(cudaGraphLaunch(b->exec[slot], (cudaStream_t)stream), "batch graph launch");
     CK(cudaEventRecord(b->done[slot], (cudaStream_t)stream), "batch completion event");
     b->used[slot] = true;
+    b->last_slot = slot;
+    b->seq += 1;
     b->cur ^= 1;
     count_launches(3);
     return RAYPC_OK;

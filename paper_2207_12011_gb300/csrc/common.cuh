@@ -138,6 +138,16 @@ struct RenderArgs {
 // / pass_count point at this view's own classification), the level's brick
 // min/max for that classification, and the view's ranges in the flat brick
 // and tile spaces of the batch.
+// Completion record of one view, in mapped pinned host memory: the block that
+// finishes the view's last tile copies the view's statistics here and then
+// stores the launch sequence number (after a system-scope fence), so the host
+// sees a finished view without waiting for the whole launch.
+struct ViewDone {
+    volatile unsigned seq;
+    unsigned pad;
+    unsigned long long stats[kNStats];
+};
+
 struct BatchView {
     RenderArgs a;
     const float* bmin;
@@ -145,6 +155,10 @@ struct BatchView {
     unsigned long long cls_begin;  // first flat brick index (multiple of 32)
     int tiles_x;                   // tiles per image row
     int tile_begin;                // first flat tile index
+    int ntiles;                    // tiles of this view
+    unsigned seq;                  // launch sequence number written on completion
+    unsigned* tile_done;           // device counter of finished tiles (zeroed per launch)
+    ViewDone* done;                // device alias of the mapped host record (may be null)
 };
 
 struct BatchHeader {

@@ -346,7 +346,21 @@ __global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader*
             __syncthreads();
         }
         march_pixel<DT, VAR>(s_args, S, s_tx, s_ty);
-        __syncthreads();   // s_tile / s_tx / S are rewritten for the next tile
+        __syncthreads();   // the tile's pixels and statistics are issued; s_* are rewritten next
+        if (threadIdx.x == 0) {
+            const BatchView& V = views[vi];
+            __threadfence();                                  // this block's writes before the count
+            const unsigned prev = atomicAdd(V.tile_done, 1u);
+            if (prev + 1 == (unsigned)V.ntiles && V.done) {
+                // last tile of the view: every other tile's writes precede their counts
+                __threadfence();
+                ViewDone* rec = V.done;
+                for (int k = 0; k < kNStats; ++k)
+                    rec->stats[k] = V.a.stats ? __ldcg(V.a.stats + k) : 0ull;
+                __threadfence_system();                       // record before the flag, as the host sees it
+                rec->seq = V.seq;
+            }
+        }
     }
 }
 

@@ -87,6 +87,11 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
 // Resolve RAYPC_AUTO launch choices from the tuning table (tune.cu).
 void resolve_launch(int device, int dtype, int n, int* variant, int* skip);
 
+// Completion records of a batch's most recent launch: *records points at the
+// mapped host array indexed like the launch's views, *seq is the value a
+// record's seq field takes when that view is finished (see ViewDone).
+void batch_last_records(raypc_batch* b, const ViewDone** records, unsigned* seq);
+
 // Validated brush box of a volume from host arrays (nvars entries each).
 raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, uint32_t active_mask, BrushArgs* out);
 

@@ -7,11 +7,13 @@
 //   2. admission: move queued requests (FIFO) into service while fewer than
 //      max_inflight are in service and their outputs fit in the output pool
 //      (the HBM budget for results);
-//   3. launch: for every stream with fewer than two launches in flight, pack
-//      the pending passes of the requests homed on it -- coarse passes first,
-//      then full passes whose coarse pass was already launched, then
-//      histograms -- into one batched render launch (one CUDA graph replay)
-//      plus histogram kernels, and record a completion event.
+//   3. launch: for every stream with fewer than two launches in flight, take
+//      the oldest unlaunched requests (up to the view and pixel caps): their
+//      histogram kernels first, then one batched render launch (one CUDA graph
+//      replay) holding all their coarse passes and then all their full passes,
+//      each group smallest image first. The persistent kernel writes a
+//      completion record per view into mapped host memory, so each pass is
+//      published as soon as its own tiles are done.
 // Requests that arrive while launches are running are admitted as slots and
 // pool memory free up and join the next launch, so their work overlaps with
 // the work already on the GPU. Every pass uses the same kernels as a single
@@ -21,6 +23,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -96,7 +100,6 @@ struct Req {
     raypc_request r{};
     std::vector<float> edges;
     int status = RAYPC_OK;
-    int home = 0;                       // stream index
     bool admitted = false, coarse_launched = false, full_launched = false;
     bool coarse_ready = false, done = false;
     double t_submit = 0, t_admit = 0, t_coarse = 0, t_done = 0;
@@ -107,14 +110,23 @@ struct Req {
     unsigned long long* stats = nullptr;
     uint32_t* hist = nullptr;
     float* d_edges = nullptr;
-    int slot = -1;                      // pinned host slot receiving the stats of the full pass
     unsigned long long samples = 0;
 };
 
+struct Item {
+    Req* q;
+    int pass;                     // kCoarse, kFull or kHist
+    int view;                     // index in the launch's batch (render passes)
+    bool seen = false;
+};
+
 struct Launch {
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_hist = nullptr;   // after the launch's histogram kernels
+    cudaEvent_t ev = nullptr;        // after the batched render
     int stream = 0;
-    std::vector<std::pair<Req*, int>> items;
+    const ViewDone* recs = nullptr;  // completion records of the batched render
+    unsigned seq = 0;
+    std::vector<Item> items;
 };
 
 size_t output_bytes(const raypc_request& r) {
@@ -141,8 +153,6 @@ struct raypc_server {
     std::vector<raypc_batch*> batches;
     Pool pool;
     char* pool_mem = nullptr;
-    unsigned long long* pinned = nullptr;   // max_inflight x kNStats, pinned host
-    std::vector<int> free_slots;
     uint64_t next_id = 1;
     int rr = 0;
     bool stop = false;
@@ -153,10 +163,6 @@ namespace {
 
 void finish(raypc_server* S, Req* q, int status) {
     if (q->done) return;
-    if (q->slot >= 0) {
-        S->free_slots.push_back(q->slot);
-        q->slot = -1;
-    }
     if (status != RAYPC_OK && q->status == RAYPC_OK) q->status = status;
     q->done = true;
     q->t_done = now_s();
@@ -208,37 +214,64 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     return RAYPC_OK;
 }
 
+void publish(raypc_server* S, Item& it, double t, unsigned long long marched) {
+    Req* q = it.q;
+    it.seen = true;
+    if (it.pass == kCoarse) {
+        q->coarse_ready = true;
+        q->t_coarse = t;
+        return;
+    }
+    if (it.pass == kFull) q->samples = marched;
+    finish(S, q, RAYPC_OK);
+    q->t_done = t;
+}
+
 void turn(raypc_server* S) {
-    // 1. completions
+    // 1. completions: per-view records of the batched renders, histogram events
+    bool any = false;
     for (size_t i = 0; i < S->inflight.size();) {
         Launch& L = S->inflight[i];
-        cudaError_t e = cudaEventQuery(L.ev);
-        if (e == cudaErrorNotReady) {
+        const double t = now_s();
+        const cudaError_t eh = L.ev_hist ? cudaEventQuery(L.ev_hist) : cudaSuccess;
+        const cudaError_t e = cudaEventQuery(L.ev);
+        const bool failed = (eh != cudaSuccess && eh != cudaErrorNotReady) || (e != cudaSuccess && e != cudaErrorNotReady);
+        for (Item& it : L.items) {
+            if (it.seen || it.q->done) continue;
+            if (failed) {
+                it.seen = true;
+                finish(S, it.q, RAYPC_ERR_CUDA);
+                any = true;
+                continue;
+            }
+            if (it.pass == kHist) {
+                if (eh == cudaSuccess) { publish(S, it, t, 0); any = true; }
+                continue;
+            }
+            const ViewDone& r = L.recs[it.view];
+            if (r.seq == L.seq) {
+                std::atomic_thread_fence(std::memory_order_acquire);
+                publish(S, it, t, r.stats[RAYPC_STAT_MARCHED]);
+                any = true;
+            }
+        }
+        if (e == cudaErrorNotReady || (L.ev_hist && eh == cudaErrorNotReady)) {
             ++i;
             continue;
         }
-        const double t = now_s();
-        for (auto& it : L.items) {
-            Req* q = it.first;
-            if (e != cudaSuccess) {
-                finish(S, q, RAYPC_ERR_CUDA);
-                continue;
+        if (failed) cudaGetLastError();
+        for (Item& it : L.items)                 // launch over: every record is final
+            if (!it.seen && !it.q->done) {
+                const unsigned long long m = it.pass == kHist ? 0ull : L.recs[it.view].stats[RAYPC_STAT_MARCHED];
+                publish(S, it, t, m);
+                any = true;
             }
-            if (it.second == kCoarse) {
-                q->coarse_ready = true;
-                q->t_coarse = t;
-            } else {
-                if (it.second == kFull && q->slot >= 0) q->samples = S->pinned[(size_t)q->slot * kNStats + RAYPC_STAT_MARCHED];
-                finish(S, q, RAYPC_OK);
-                q->t_done = t;
-            }
-        }
-        if (e != cudaSuccess) cudaGetLastError();
+        if (L.ev_hist) cudaEventDestroy(L.ev_hist);
         cudaEventDestroy(L.ev);
         S->busy[L.stream]--;
         S->inflight.erase(S->inflight.begin() + i);
-        S->cv_done.notify_all();
     }
+    if (any) S->cv_done.notify_all();
     // 2. admission (FIFO)
     while (!S->queued.empty() && (int)S->active.size() < S->cfg.max_inflight) {
         Req* q = S->queued.front();
@@ -248,8 +281,6 @@ void turn(raypc_server* S) {
         q->mem = m;
         q->admitted = true;
         q->t_admit = now_s();
-        q->home = S->rr;
-        S->rr = (S->rr + 1) % (int)S->streams.size();
         char* p = m;
         if (q->r.kind == RAYPC_REQ_HISTOGRAM) {
             q->hist = reinterpret_cast<uint32_t*>(p);
@@ -264,34 +295,69 @@ void turn(raypc_server* S) {
                 p += img;
             }
             q->stats = reinterpret_cast<unsigned long long*>(p);
-            q->slot = S->free_slots.back();
-            S->free_slots.pop_back();
         }
         S->active.push_back(q);
     }
-    // 3. launches, one per stream with room
-    for (int s = 0; s < (int)S->streams.size(); ++s) {
+    // 3. launches: every stream with room takes the oldest unlaunched requests
+    for (int k = 0; k < (int)S->streams.size(); ++k) {
+        const int s = (S->rr + k) % (int)S->streams.size();
         if (S->busy[s] >= 2) continue;
-        std::vector<raypc_view> views;
+        std::vector<Req*> renders, hists;
+        long long pixels = 0;
+        int nviews = 0;
+        for (Req* q : S->active) {
+            if (q->done || q->full_launched) continue;
+            if (q->r.kind == RAYPC_REQ_HISTOGRAM) {
+                hists.push_back(q);
+                continue;
+            }
+            const int nv = q->r.coarse_lod >= 0 ? 2 : 1;
+            const long long px = (long long)q->r.w * q->r.h * nv;
+            if (nviews + nv > S->cfg.max_batch_views) continue;
+            if (!renders.empty() && S->cfg.max_batch_pixels > 0 && pixels + px > S->cfg.max_batch_pixels) continue;
+            renders.push_back(q);
+            pixels += px;
+            nviews += nv;
+        }
+        if (renders.empty() && hists.empty()) break;    // nothing pending for any stream
+        S->rr = (s + 1) % (int)S->streams.size();
         Launch L;
         L.stream = s;
-        std::vector<Req*> hists;
-        for (int pass = kCoarse; pass <= kFull; ++pass)
-            for (Req* q : S->active) {
-                if ((int)views.size() >= S->cfg.max_batch_views) break;
-                if (q->home != s || q->r.kind != RAYPC_REQ_RENDER || q->done) continue;
-                const bool want = pass == kCoarse ? (q->r.coarse_lod >= 0 && !q->coarse_launched)
-                                                  : (!q->full_launched && (q->r.coarse_lod < 0 || q->coarse_launched));
-                if (!want) continue;
-                if (pass == kFull && q->r.coarse_lod >= 0) {
-                    bool same_launch = false;
-                    for (auto& it : L.items)
-                        if (it.first == q) same_launch = true;
-                    if (same_launch) continue;          // full pass goes in a later launch
-                }
+        cudaStream_t st = S->streams[s];
+        // histograms first (short), with their own completion event
+        for (Req* q : hists) {
+            q->full_launched = true;
+            raypc_status hs = launch_hist(S, q, st);
+            if (hs != RAYPC_OK) { finish(S, q, hs); continue; }
+            L.items.push_back({q, kHist, -1});
+        }
+        if (!L.items.empty() &&
+            (cudaEventCreateWithFlags(&L.ev_hist, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventRecord(L.ev_hist, st) != cudaSuccess)) {
+            cudaStreamSynchronize(st);
+            for (Item& it : L.items) finish(S, it.q, RAYPC_ERR_CUDA);
+            L.items.clear();
+            if (L.ev_hist) cudaEventDestroy(L.ev_hist);
+            L.ev_hist = nullptr;
+        }
+        // render passes: all coarse passes, then all full passes, each smallest first
+        std::vector<std::pair<Req*, int>> passes;
+        for (int pass = kCoarse; pass <= kFull; ++pass) {
+            std::vector<Req*> v;
+            for (Req* q : renders)
+                if (pass == kFull || q->r.coarse_lod >= 0) v.push_back(q);
+            std::stable_sort(v.begin(), v.end(), [](Req* a, Req* b) {
+                return (long long)a->r.w * a->r.h < (long long)b->r.w * b->r.h;
+            });
+            for (Req* q : v) passes.push_back({q, pass});
+        }
+        if (!passes.empty()) {
+            std::vector<raypc_view> views;
+            for (auto& pr : passes) {
+                Req* q = pr.first;
                 raypc_view v{};
                 v.vol = q->r.vol;
-                v.lod = pass == kCoarse ? q->r.coarse_lod : q->r.lod;
+                v.lod = pr.second == kCoarse ? q->r.coarse_lod : q->r.lod;
                 v.cam = q->r.cam;
                 v.w = q->r.w;
                 v.h = q->r.h;
@@ -300,48 +366,34 @@ void turn(raypc_server* S) {
                 v.active_mask = q->r.active_mask;
                 v.opts = q->r.opts;
                 v.opts.counts_dev = nullptr;
-                v.out_rgba_dev = pass == kCoarse ? q->coarse : q->image;
-                v.stats_dev = pass == kCoarse ? nullptr : q->stats;
+                v.out_rgba_dev = pr.second == kCoarse ? q->coarse : q->image;
+                v.stats_dev = pr.second == kCoarse ? nullptr : q->stats;
                 views.push_back(v);
-                L.items.push_back({q, pass});
             }
-        for (Req* q : S->active)
-            if (q->home == s && q->r.kind == RAYPC_REQ_HISTOGRAM && !q->full_launched) hists.push_back(q);
-        if (views.empty() && hists.empty()) continue;
-        cudaStream_t st = S->streams[s];
-        for (auto& it : L.items)
-            if (it.second == kFull) cudaMemsetAsync(it.first->stats, 0, sizeof(unsigned long long) * kNStats, st);
-        raypc_status rs = views.empty() ? RAYPC_OK
-                                        : raypc_render_batch(S->batches[s], views.data(), (int)views.size(), st);
-        if (rs != RAYPC_OK) {
-            for (auto& it : L.items) finish(S, it.first, rs);
-            L.items.clear();
-        } else {
-            for (auto& it : L.items) {
-                if (it.second == kCoarse) {
-                    it.first->coarse_launched = true;
-                } else {
-                    it.first->full_launched = true;
-                    cudaMemcpyAsync(S->pinned + (size_t)it.first->slot * kNStats, it.first->stats,
-                                    sizeof(unsigned long long) * kNStats, cudaMemcpyDeviceToHost, st);
+            for (Req* q : renders) cudaMemsetAsync(q->stats, 0, sizeof(unsigned long long) * kNStats, st);
+            raypc_status rs = raypc_render_batch(S->batches[s], views.data(), (int)views.size(), st);
+            if (rs != RAYPC_OK) {
+                for (Req* q : renders) finish(S, q, rs);
+            } else {
+                batch_last_records(S->batches[s], &L.recs, &L.seq);
+                for (size_t i = 0; i < passes.size(); ++i) {
+                    Req* q = passes[i].first;
+                    if (passes[i].second == kCoarse) q->coarse_launched = true;
+                    else q->full_launched = true;
+                    L.items.push_back({q, passes[i].second, (int)i});
                 }
             }
         }
-        for (Req* q : hists) {
-            raypc_status hs = launch_hist(S, q, st);
-            if (hs != RAYPC_OK) {
-                finish(S, q, hs);
-                continue;
-            }
-            q->full_launched = true;
-            L.items.push_back({q, kHist});
+        if (L.items.empty()) {
+            if (L.ev_hist) cudaEventDestroy(L.ev_hist);
+            continue;
         }
-        if (L.items.empty()) continue;
         if (cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventRecord(L.ev, st) != cudaSuccess) {
             cudaStreamSynchronize(st);
-            for (auto& it : L.items) finish(S, it.first, RAYPC_ERR_CUDA);
+            for (Item& it : L.items) finish(S, it.q, RAYPC_ERR_CUDA);
             if (L.ev) cudaEventDestroy(L.ev);
+            if (L.ev_hist) cudaEventDestroy(L.ev_hist);
             continue;
         }
         S->busy[s]++;
@@ -363,6 +415,7 @@ void loop(raypc_server* S) {
     for (auto& L : S->inflight) {
         cudaEventSynchronize(L.ev);
         cudaEventDestroy(L.ev);
+        if (L.ev_hist) cudaEventDestroy(L.ev_hist);
     }
     S->inflight.clear();
     for (auto& kv : S->all)
@@ -391,12 +444,7 @@ raypc_status raypc_server_create(raypc_ctx* ctx, const raypc_server_config* cfg,
         size_t charged = 0;
         st = ctx->alloc((void**)&S->pool_mem, S->cfg.output_budget_bytes, &charged);
         if (st == RAYPC_OK) S->pool.init(S->pool_mem, S->cfg.output_budget_bytes);
-        if (st == RAYPC_OK) {
-            cudaError_t e = cudaHostAlloc((void**)&S->pinned, sizeof(unsigned long long) * kNStats * cfg->max_inflight,
-                                          cudaHostAllocDefault);
-            if (e != cudaSuccess) st = cuda_fail(e, "server pinned slots");
-            for (int i = cfg->max_inflight - 1; i >= 0; --i) S->free_slots.push_back(i);
-        }
+
         for (int i = 0; i < cfg->num_streams && st == RAYPC_OK; ++i) {
             cudaStream_t s = nullptr;
             cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -437,7 +485,6 @@ raypc_status raypc_server_destroy(raypc_server* S) {
             cudaStreamSynchronize(s);
             cudaStreamDestroy(s);
         }
-        if (S->pinned) cudaFreeHost(S->pinned);
         if (S->pool_mem) {
             cudaFree(S->pool_mem);
             S->ctx->used -= S->cfg.output_budget_bytes < S->ctx->used ? S->cfg.output_budget_bytes : S->ctx->used;

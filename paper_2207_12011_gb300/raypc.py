@@ -51,7 +51,8 @@ class RenderOpts(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int), ("output_budget_bytes", ctypes.c_size_t),
-                ("max_batch_views", ctypes.c_int), ("num_streams", ctypes.c_int)]
+                ("max_batch_views", ctypes.c_int), ("num_streams", ctypes.c_int),
+                ("max_batch_pixels", ctypes.c_longlong)]
 
 
 class Request(ctypes.Structure):
@@ -527,9 +528,10 @@ class Server:
     """Continuous-batching render / histogram server on a context (see raypc.h)."""
 
     def __init__(self, ctx: Context, max_inflight: int = 64, output_budget_bytes: int = 1 << 30,
-                 max_batch_views: int = 64, num_streams: int = 2):
+                 max_batch_views: int = 64, num_streams: int = 2, max_batch_pixels: int = 0):
         self.ctx = ctx
-        cfg = ServerConfig(int(max_inflight), int(output_budget_bytes), int(max_batch_views), int(num_streams))
+        cfg = ServerConfig(int(max_inflight), int(output_budget_bytes), int(max_batch_views), int(num_streams),
+                           int(max_batch_pixels))
         h = ctypes.c_void_p()
         _call("raypc_server_create", ctx.handle, ctypes.byref(cfg), ctypes.byref(h))
         self._h = h

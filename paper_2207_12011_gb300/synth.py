@@ -209,6 +209,43 @@ def brush_from_quantiles(vol: torch.Tensor, spec: dict, nvars: int = 6) -> Brush
     return Brush(lo, hi, mask)
 
 
+class QuantileTable:
+    """Sorted in-shell samples of every variable, for fast brush construction."""
+
+    def __init__(self, vol: torch.Tensor):
+        self.sorted = [_shell_sample(vol, v).cpu() for v in range(vol.shape[0])]
+        self.nvars = vol.shape[0]
+
+    def brush(self, spec: dict) -> Brush:
+        lo = np.full(self.nvars, -np.inf, dtype=np.float32)
+        hi = np.full(self.nvars, np.inf, dtype=np.float32)
+        mask = 0
+        for name, (qlo, qhi) in spec.items():
+            v = VAR_INDEX[name]
+            if qlo is not None:
+                lo[v] = np.float32(quantile_value(self.sorted[v], qlo))
+            if qhi is not None:
+                hi[v] = np.float32(quantile_value(self.sorted[v], qhi))
+            mask |= 1 << v
+        return Brush(lo, hi, mask)
+
+
+def edited_spec(base: str, seed: int, jitter: float = 0.1, edit: float = 0.05) -> dict:
+    """A jittered base brush with one more edit: one random bound moves by U[-edit, edit]."""
+    spec = jittered_spec(base, seed, jitter)
+    rng = np.random.default_rng(seed + 7919)
+    names = sorted(spec)
+    name = names[int(rng.integers(len(names)))]
+    qlo, qhi = spec[name]
+    move = float(rng.uniform(-edit, edit))
+    if qlo is not None and (qhi is None or rng.uniform() < 0.5):
+        qlo = float(np.clip(qlo + move, 0, 1 if qhi is None else qhi))
+    elif qhi is not None:
+        qhi = float(np.clip(qhi + move, 0 if qlo is None else qlo, 1))
+    spec[name] = (qlo, qhi)
+    return spec
+
+
 def make_brush(vol: torch.Tensor, name: str) -> Brush:
     return brush_from_quantiles(vol, BRUSH_SPECS[name], vol.shape[0])
 
