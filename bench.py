@@ -138,6 +138,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic():
+    """DRAM bytes per render launch from the committed ncu summary, if the kernel is unchanged since."""
+    import hashlib
+    import re
+    try:
+        src = os.path.join(ROOT, "paper_2207_12011_gb300", "csrc", "render_kernels.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(os.path.join(ROOT, "profiles", "k_render_shell256_f32.md")).read()
+        m = re.search(r"sha256 prefix at capture: ([0-9a-f]{16})", text)
+        t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+        if m and t and m.group(1) == h:
+            return int(t.group(1))
+    except OSError:
+        pass
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -291,7 +308,7 @@ def run_ours(args):
     alg_bytes = n_active * 8 ** 3 * 6 * elem + c["w"] * c["h"] * 16
     achieved = alg_bytes / (render_ms / 1e3) / 1e9
     roofline = {"kernel": "k_render", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
                 "peak_kind": f"{peak_kind} HBM copy", "render_ms": round(render_ms, 4),
                 "alg_bytes_per_launch": alg_bytes, "active_bricks": n_active}
 
