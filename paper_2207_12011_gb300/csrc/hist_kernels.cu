@@ -2,8 +2,8 @@
 // Fig. 2): for every in-shell (and, optionally, in-brush) cell and every pair
 // of adjacent axes (a, a+1), H[a][bin_a][bin_{a+1}] += 1.
 //
-// HBM-bound scan. A warp walks one x-row of cells at a time (lanes over x), so
-// the planar loads of the needed variables are fully coalesced; rows whose cells all lie
+// HBM-bound scan. A warp walks one x-row of cells (lanes over x, two cells per
+// lane in flight), so the planar loads of the needed variables are coalesced; rows whose cells all lie
 // outside the shell are skipped without touching memory. The in-shell test is
 // integer-exact. Bins come from a binary search over the FP32 edges held in
 // shared memory (comparisons only, so exact). Increments are aggregated per
@@ -66,53 +66,68 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
         const int xa = (int)max(0LL, (n - 1 - m + 1) / 2);
         const int xb = (int)min((long long)n - 1, (n - 1 + m) / 2);
         const size_t row_base = (size_t)r * n;
-        for (int x0 = xa; x0 <= xb; x0 += 32) {
-            const int x = x0 + lane;
-            bool keep = false;
-            int bn[kMaxVars];
-            if (x <= xb) {
-                const long long dx = 2 * x + 1 - n;
-                const long long s = dx * dx + syz;
-                if (s >= A.s_in && s <= A.s_out) {
-                    float val[kMaxVars];
-                    keep = true;
-                    // brushed variables first; the rest only for cells that pass
+        // two cells per lane and iteration: their loads are in flight together
+        for (int x0 = xa; x0 <= xb; x0 += 64) {
+            bool keep[2];
+            int bn[2][kMaxVars];
+            float val[2][kMaxVars];
 #pragma unroll
-                    for (int v = 0; v < kMaxVars; ++v) {
-                        if ((brush_mask >> v) & 1u) {
-                            val[v] = load_cell<DT>(A.cells, v * plane + row_base + x);
-                            keep = keep && (val[v] >= A.brush.lo[v]) && (val[v] <= A.brush.hi[v]);
-                        } else {
-                            val[v] = 0.0f;
-                        }
-                    }
-                    if (keep) {
+            for (int j = 0; j < 2; ++j) {
+                const int x = x0 + lane + 32 * j;
+                keep[j] = false;
+                if (x <= xb) {
+                    const long long dx = 2 * x + 1 - n;
+                    const long long s = dx * dx + syz;
+                    keep[j] = s >= A.s_in && s <= A.s_out;
+                }
+            }
+            // brushed variables first; the rest only for cells that pass
 #pragma unroll
-                        for (int v = 0; v < kMaxVars; ++v)
-                            if ((rest_mask >> v) & 1u) val[v] = load_cell<DT>(A.cells, v * plane + row_base + x);
+            for (int j = 0; j < 2; ++j) {
+                const size_t off = row_base + x0 + lane + 32 * j;
 #pragma unroll
-                        for (int a = 0; a < kMaxVars; ++a) {
-                            if (a < A.naxes) {
-                                float va = val[0];
+                for (int v = 0; v < kMaxVars; ++v)
+                    val[j][v] = (keep[j] && ((brush_mask >> v) & 1u)) ? load_cell<DT>(A.cells, v * plane + off) : 0.0f;
+            }
 #pragma unroll
-                                for (int v = 1; v < kMaxVars; ++v)
-                                    if (A.axis[a] == v) va = val[v];
-                                bn[a] = bin_of(s_edges + a * (bins + 1), bins, va, A.guess_e0[a], A.guess_scale[a]);
-                            }
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int v = 0; v < kMaxVars; ++v)
+                    if ((brush_mask >> v) & 1u)
+                        keep[j] = keep[j] && (val[j][v] >= A.brush.lo[v]) && (val[j][v] <= A.brush.hi[v]);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const size_t off = row_base + x0 + lane + 32 * j;
+#pragma unroll
+                for (int v = 0; v < kMaxVars; ++v)
+                    if (keep[j] && ((rest_mask >> v) & 1u)) val[j][v] = load_cell<DT>(A.cells, v * plane + off);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (keep[j]) {
+#pragma unroll
+                    for (int a = 0; a < kMaxVars; ++a) {
+                        if (a < A.naxes) {
+                            float va = val[j][0];
+#pragma unroll
+                            for (int v = 1; v < kMaxVars; ++v)
+                                if (A.axis[a] == v) va = val[j][v];
+                            bn[j][a] = bin_of(s_edges + a * (bins + 1), bins, va, A.guess_e0[a], A.guess_scale[a]);
                         }
                     }
                 }
-            }
-            const unsigned km = __ballot_sync(0xffffffffu, keep);
-            if (km == 0u) continue;
-            if (keep) {
+                const unsigned km = __ballot_sync(0xffffffffu, keep[j]);
+                if (km == 0u) continue;
+                if (keep[j]) {
 #pragma unroll
-                for (int p = 0; p + 1 < kMaxVars; ++p) {
-                    if (p + 1 < A.naxes) {
-                        const unsigned key = (unsigned)bn[p] * (unsigned)bins + (unsigned)bn[p + 1];
-                        const unsigned peers = __match_any_sync(km, key);
-                        if (lane == __ffs(peers) - 1)
-                            atomicAdd(A.out + (size_t)p * bins * bins + key, (unsigned)__popc(peers));
+                    for (int p = 0; p + 1 < kMaxVars; ++p) {
+                        if (p + 1 < A.naxes) {
+                            const unsigned key = (unsigned)bn[j][p] * (unsigned)bins + (unsigned)bn[j][p + 1];
+                            const unsigned peers = __match_any_sync(km, key);
+                            if (lane == __ffs(peers) - 1)
+                                atomicAdd(A.out + (size_t)p * bins * bins + key, (unsigned)__popc(peers));
+                        }
                     }
                 }
             }
@@ -122,12 +137,10 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
 
 template <int DT>
 cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // one row per warp (rows differ in length; the hardware balances blocks)
     long long rows = (long long)a.n * a.n;
     long long want_blocks = (rows + (kHistThreads / 32) - 1) / (kHistThreads / 32);
-    int blocks = (int)(want_blocks < (long long)sms * 8 ? want_blocks : (long long)sms * 8);
+    int blocks = (int)(want_blocks < 0x7fffffffLL ? want_blocks : 0x7fffffffLL);
     if (blocks < 1) blocks = 1;
     size_t smem = sizeof(float) * a.naxes * (a.bins + 1);
     k_hist<DT><<<blocks, kHistThreads, smem, stream>>>(a);

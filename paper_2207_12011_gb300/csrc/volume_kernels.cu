@@ -72,7 +72,8 @@ __device__ __forceinline__ float produce(const RowsArgs& A, int x, int y, int z,
     }
 }
 
-// One block per (brick row (by, bz), variable). Threads own x columns; the
+// One block per (brick row (by, bz), variable), up to 256 threads (one per x
+// column, striding when the level is wider). Threads own x columns; the
 // block streams the (up to) 9 x 9 x-rows y in [8by, 8by+8], z in [8bz, 8bz+8]
 // of the level, writes the 8 x 8 rows it owns (cells and x-pairs; the right
 // element of a pair comes from the neighbouring lane) and folds every row,
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
     const int by = blockIdx.x % nb, bz = blockIdx.x / nb, v = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const float qnan = __int_as_float(0x7fffffff);
-    for (int xc = 0; xc < n; xc += kRowThreads) {
+    for (int xc = 0; xc < n; xc += blockDim.x) {
         const int x = xc + threadIdx.x;
         const bool valid = x < n;
         float mn = qnan, mx = qnan;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
         }
     }
     __syncthreads();
-    for (int bx = threadIdx.x; bx < nb; bx += kRowThreads) {
+    for (int bx = threadIdx.x; bx < nb; bx += blockDim.x) {
         const int x0 = bx * kBrick, x1 = min(x0 + kBrick, n - 1);
         float mn = qnan, mx = qnan;
         for (int x = x0; x <= x1; ++x) {
@@ -244,10 +245,12 @@ cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
             : cudaFuncSetAttribute(k_rows<kF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
+    // one thread per x column up to kRowThreads (narrow levels use narrow blocks)
+    const int threads = min(kRowThreads, max(32, (a.n + 31) / 32 * 32));
     if (dtype == kF16)
-        k_rows<kF16, MODE><<<grid, kRowThreads, smem, stream>>>(a);
+        k_rows<kF16, MODE><<<grid, threads, smem, stream>>>(a);
     else
-        k_rows<kF32, MODE><<<grid, kRowThreads, smem, stream>>>(a);
+        k_rows<kF32, MODE><<<grid, threads, smem, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
