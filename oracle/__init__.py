@@ -55,8 +55,8 @@ def _load():
             lib = ctypes.CDLL(_LIB_PATH)
             P = ctypes.c_void_p
             i32, u32, f32 = ctypes.c_int, ctypes.c_uint32, ctypes.c_float
-            lib.oracle_brick_minmax.argtypes = [P, i32, i32, P, P]
-            lib.oracle_classify.argtypes = [P, P, i32, i32, f32, f32, P, P, u32, P, P]
+            lib.oracle_brick_minmax.argtypes = [P, i32, i32, i32, P, P]
+            lib.oracle_classify.argtypes = [P, P, i32, i32, i32, f32, f32, P, P, u32, P, P]
             lib.oracle_lod_mean.argtypes = [P, i32, i32, P]
             lib.oracle_shell_bounds.argtypes = [i32, f32, f32, P, P]
             lib.oracle_histogram.argtypes = [P, i32, i32, f32, f32, P, P, u32, i32,
@@ -91,26 +91,26 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
-def brick_minmax(vol):
-    """Per-brick, per-variable min and max over the 9^3 apron vertices -> (bmin, bmax) [nb,nb,nb,V]."""
+def brick_minmax(vol, bs: int = BRICK):
+    """Per-brick (edge bs), per-variable min and max over the (bs+1)^3 apron vertices -> [nb,nb,nb,V]."""
     v = _vol(vol)
     V, n = v.shape[0], v.shape[1]
-    nb = (n + BRICK - 1) // BRICK
+    nb = (n + bs - 1) // bs
     mn = np.empty((nb, nb, nb, V), np.float32)
     mx = np.empty((nb, nb, nb, V), np.float32)
-    _load().oracle_brick_minmax(_ptr(v), n, V, _ptr(mn), _ptr(mx))
+    _load().oracle_brick_minmax(_ptr(v), n, V, int(bs), _ptr(mn), _ptr(mx))
     return mn, mx
 
 
-def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask):
-    """Active and skippable brick flags (uint8 [nb,nb,nb]) from brick min/max and a brush."""
+def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask, bs: int = BRICK):
+    """Active and skippable flags (uint8 [nb,nb,nb]) of bricks of edge bs from their min/max and a brush."""
     bmin, bmax = _f32(bmin), _f32(bmax)
     V = bmin.shape[-1]
     nb = bmin.shape[0]
     lo, hi = _f32(lo), _f32(hi)
     act = np.empty((nb, nb, nb), np.uint8)
     skp = np.empty((nb, nb, nb), np.uint8)
-    _load().oracle_classify(_ptr(bmin), _ptr(bmax), n, V, np.float32(r_in), np.float32(r_out),
+    _load().oracle_classify(_ptr(bmin), _ptr(bmax), n, V, int(bs), np.float32(r_in), np.float32(r_out),
                             _ptr(lo), _ptr(hi), int(active_mask) & 0xFFFFFFFF, _ptr(act), _ptr(skp))
     return act, skp
 

@@ -38,8 +38,6 @@
 #include <string.h>
 #include <unistd.h>
 
-#define BRICK 8
-
 /* ------------------------------------------------------------------ */
 /* Volume access: vol[v][z][y][x] float32 (stored values, exact).       */
 /* ------------------------------------------------------------------ */
@@ -48,13 +46,14 @@ static inline float val(const float *vol, int n, int v, int x, int y, int z) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Brick min/max: for brick (bx,by,bz) and variable v, the min and max  */
-/* of the stored values at vertices 8b .. min(8b+8, n-1) on each axis.  */
-/* A sample whose lower interpolation corner lies in the brick reads    */
-/* only these vertices. NaN values are ignored (fmin/fmax).             */
+/* Brick min/max: for brick (bx,by,bz) of edge bs cells and variable v,  */
+/* the min and max of the stored values at vertices bs*b .. min(bs*b+bs, */
+/* n-1) on each axis. A sample whose lower interpolation corner lies in  */
+/* the brick reads only these vertices. NaN values are ignored.          */
 /* Output layout: [bz][by][bx][v].                                      */
 /* ------------------------------------------------------------------ */
-void oracle_brick_minmax(const float *vol, int n, int nvars, float *out_min, float *out_max) {
+void oracle_brick_minmax(const float *vol, int n, int nvars, int bs, float *out_min, float *out_max) {
+    const int BRICK = bs;
     int nb = (n + BRICK - 1) / BRICK;
     for (int bz = 0; bz < nb; bz++)
         for (int by = 0; by < nb; by++)
@@ -78,7 +77,7 @@ void oracle_brick_minmax(const float *vol, int n, int nvars, float *out_min, flo
 }
 
 /* ------------------------------------------------------------------ */
-/* Brush classification of bricks (FP32 decisions).                     */
+/* Brush classification of bricks of edge bs (FP32 decisions).          */
 /*                                                                      */
 /* A brick is active when (1) the world box its samples can occupy,     */
 /* widened by 2^-10, meets the shell r_in <= |p| <= r_out, and (2) for   */
@@ -90,7 +89,7 @@ void oracle_brick_minmax(const float *vol, int n, int nvars, float *out_min, flo
 /* existing 26 neighbours are inactive.                                 */
 /* Output: active[b], skippable[b] as bytes 0/1, b = (bz*nb+by)*nb+bx.  */
 /* ------------------------------------------------------------------ */
-static void brick_box_axis(int b, int nb, int n, float *lo, float *hi) {
+static void brick_box_axis(int b, int nb, int n, int BRICK, float *lo, float *hi) {
     float sc = 2.0f / (float)n;
     float l = fmaf((float)(b * BRICK) + 0.5f, sc, -1.0f) - 0x1p-10f;
     float h = fmaf((float)(b * BRICK + BRICK) + 0.5f, sc, -1.0f) + 0x1p-10f;
@@ -100,9 +99,10 @@ static void brick_box_axis(int b, int nb, int n, float *lo, float *hi) {
     *hi = h;
 }
 
-void oracle_classify(const float *bmin, const float *bmax, int n, int nvars,
+void oracle_classify(const float *bmin, const float *bmax, int n, int nvars, int bs,
                      float r_in, float r_out, const float *lo, const float *hi,
                      uint32_t active_mask, uint8_t *active, uint8_t *skippable) {
+    const int BRICK = bs;
     int nb = (n + BRICK - 1) / BRICK;
     float rin2 = r_in * r_in, rout2 = r_out * r_out;
     for (int bz = 0; bz < nb; bz++)
@@ -112,7 +112,7 @@ void oracle_classify(const float *bmin, const float *bmax, int n, int nvars,
                 float nearc[3], farc[3];
                 for (int a = 0; a < 3; a++) {
                     float l, h;
-                    brick_box_axis(bc[a], nb, n, &l, &h);
+                    brick_box_axis(bc[a], nb, n, BRICK, &l, &h);
                     nearc[a] = (l > 0.0f) ? l : ((h < 0.0f) ? -h : 0.0f);
                     farc[a] = fmaxf(fabsf(l), fabsf(h));
                 }

@@ -406,18 +406,43 @@ def test_histogram_edge_values_and_clamping():
 # ----------------------------------------------------------------------------
 # bricks: min/max by brute force, classification on fields with a known layout
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("n", [16, 20, 32])
-def test_brick_minmax_brute_force(n):
+@pytest.mark.parametrize("n,bs", [(16, 8), (20, 8), (32, 8), (18, 4), (32, 4)])
+def test_brick_minmax_brute_force(n, bs):
     vol = synth.make_shell_volume(n, seed=3).numpy()
     vol[2, 3, 5, 7] = np.nan                              # NaN values are ignored
-    mn, mx = oracle.brick_minmax(vol)
-    nb = (n + 7) // 8
+    mn, mx = oracle.brick_minmax(vol, bs)
+    nb = (n + bs - 1) // bs
     for bz in range(nb):
         for by in range(nb):
             for bx in range(nb):
-                sl = vol[:, bz * 8:min(bz * 8 + 9, n), by * 8:min(by * 8 + 9, n), bx * 8:min(bx * 8 + 9, n)]
+                sl = vol[:, bz * bs:min(bz * bs + bs + 1, n), by * bs:min(by * bs + bs + 1, n),
+                         bx * bs:min(bx * bs + bs + 1, n)]
                 assert np.array_equal(mn[bz, by, bx], np.nanmin(sl.reshape(vol.shape[0], -1), axis=1))
                 assert np.array_equal(mx[bz, by, bx], np.nanmax(sl.reshape(vol.shape[0], -1), axis=1))
+
+
+def test_classify_affine_field_slabs_edge4():
+    n = 32
+    vol = np.zeros((1, n, n, n), np.float32)
+    vol[0] = np.arange(n, dtype=np.float32)[None, None, :]   # value = x index
+    mn, mx = oracle.brick_minmax(vol, 4)
+    assert np.array_equal(mn[0, 0, :, 0], np.arange(0, 32, 4)) and mx[0, 0, -1, 0] == 31
+    nob = np.ones(1, np.float32)
+    act0, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, -np.inf * nob, np.inf * nob, 0, bs=4)
+    # sub-bricks hold x in [4b, 4b+4]: lo = 10.5, hi = 12 touches b = 2 (8..12) and b = 3 (12..16)
+    for lo, hi, cols in [(10.5, 12.0, {2, 3}), (13.0, 15.5, {3}), (16.0000005, 19.0, {3, 4})]:
+        act, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([lo]), np.float32([hi]), 1, bs=4)
+        want = act0.copy()
+        for bx in range(8):
+            if bx not in cols:
+                want[:, :, bx] = 0
+        assert np.array_equal(act, want), (lo, hi)
+    # an edge-4 active brick always lies inside an edge-8 active brick
+    mn8, mx8 = oracle.brick_minmax(vol, 8)
+    act8, _ = oracle.classify(mn8, mx8, n, R_IN, R_OUT, np.float32([10.5]), np.float32([12.0]), 1)
+    act4, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([10.5]), np.float32([12.0]), 1, bs=4)
+    up = act8.repeat(2, 0).repeat(2, 1).repeat(2, 2)
+    assert np.all(up[act4 == 1] == 1)
 
 
 def test_classify_affine_field_slabs():
@@ -448,18 +473,19 @@ def test_classify_affine_field_slabs():
         assert np.array_equal(skp, (nbr == 0).astype(np.uint8))
 
 
-def test_classify_shell_bracket():
+@pytest.mark.parametrize("bs", [8, 4])
+def test_classify_shell_bracket(bs):
     for n in (32, 64):
-        nb = n // 8
+        nb = n // bs
         vol = np.zeros((1, n, n, n), np.float32)
-        mn, mx = oracle.brick_minmax(vol)
-        act, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([-1]), np.float32([1]), 0)
+        mn, mx = oracle.brick_minmax(vol, bs)
+        act, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([-1]), np.float32([1]), 0, bs=bs)
         ins = _cells_in_shell_exact(n, R_IN, R_OUT)
         # necessary: every brick holding an in-shell cell centre is active
-        holds = ins.reshape(nb, 8, nb, 8, nb, 8).any(axis=(1, 3, 5))
+        holds = ins.reshape(nb, bs, nb, bs, nb, bs).any(axis=(1, 3, 5))
         assert np.all(act[holds] == 1)
         # sufficient: a brick whose sample box lies clearly outside the shell is inactive
-        c = lambda b: ((8 * b + 0.5) * 2 / n - 1, (8 * b + 8.5) * 2 / n - 1)
+        c = lambda b: ((bs * b + 0.5) * 2 / n - 1, (bs * b + bs + 0.5) * 2 / n - 1)
         for bz in range(nb):
             for by in range(nb):
                 for bx in range(nb):
