@@ -136,8 +136,9 @@ raypc_status raypc_memory_used(raypc_ctx *ctx, size_t *out_bytes);
  * of type src_dtype, x fastest: src[((v*nz + z)*ny + y)*nx + x]; it is device
  * memory if src_is_device, else host memory. The stored copy has element type
  * store_dtype (FP16 storage rounds to nearest even; FP16 -> FP32 is exact)
- * in the library's interleaved layout. Only cubic grids (nx == ny == nz >= 2)
- * are supported (RAYPC_ERR_UNSUPPORTED otherwise). 0 <= r_in < r_out.
+ * in the library's interleaved layout. Only cubic grids with
+ * 2 <= nx == ny == nz <= 4096 are supported (RAYPC_ERR_UNSUPPORTED otherwise).
+ * 0 <= r_in < r_out.
  * Writes the new volume id to *out_vol. Allocates; the stored copy lives
  * until raypc_free_volume or raypc_destroy. */
 raypc_status raypc_load_volume(raypc_ctx *ctx, const void *src, int src_is_device,
@@ -165,8 +166,10 @@ raypc_status raypc_update_volume(raypc_ctx *ctx, int vol, const void *src, int s
  * indices clamped at the edge, summed as ((c000+c100)+(c010+c110)) +
  * ((c001+c101)+(c011+c111)) then times 1/8, stored in the volume's dtype --
  * and, for every level, per 8^3 brick and variable, the min and max of the
- * stored values at the brick's vertices 8b..min(8b+8, n-1) (NaN ignored).
- * brick_dim must be RAYPC_BRICK. Calling it again rebuilds. */
+ * stored values at the brick's vertices 8b..min(8b+8, n-1) (NaN ignored),
+ * and the same for the 4^3 sub-bricks (vertices 4s..min(4s+4, n-1)) whose
+ * activity the render tests per sample. brick_dim must be RAYPC_BRICK.
+ * Calling it again rebuilds. */
 raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lod,
                                 void *stream);
 
@@ -180,8 +183,8 @@ raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lo
  * active iff its sample box (widened by 2^-10) meets the shell and, for every
  * restricted v, max_v + d >= lo[v] and min_v - d <= hi[v] with
  * d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
- * rounding); skippable iff it and its 26 neighbours are inactive. Requires
- * raypc_build_bricks. */
+ * rounding); skippable iff it and its 26 neighbours are inactive. The 4^3
+ * sub-bricks are classified by the same rule. Requires raypc_build_bricks. */
 raypc_status raypc_set_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
                              uint32_t active_mask, void *stream);
 
@@ -207,8 +210,11 @@ raypc_status raypc_set_tf(raypc_ctx *ctx, int vol, const float *rgbs, int color_
  * (r, g, b, sigma) from the transfer function, alpha = 1 - exp(-sigma * step),
  * and composite front to back: C += (1 - A) alpha rgb, A += (1 - A) alpha.
  * The integer decisions use correctly rounded FP32 operations in one fixed
- * order, so they do not depend on skipping, tiling or launch shape. Brick
- * skipping never changes the image. Requires set_brush and set_tf.
+ * order, so they do not depend on skipping, tiling or launch shape. Samples
+ * in inactive 4^3 sub-bricks are rejected before any interpolation; with
+ * skipping on, a ray jumps over the rest of an inactive sub-brick (or of an
+ * inactive 8^3 brick), and the jump never changes the image. Requires set_brush
+ * and set_tf.
  * stats_dev: optional RAYPC_NSTATS uint64 device counters the kernel adds to.
  * opts may be NULL only if the defaults with ert = 1 are wanted. */
 raypc_status raypc_render(raypc_ctx *ctx, int vol, int lod, const raypc_camera *cam,
@@ -440,6 +446,15 @@ raypc_status raypc_get_bricks(raypc_ctx *ctx, int vol, int lod, float *out_min_d
 raypc_status raypc_get_skip_list(raypc_ctx *ctx, int vol, int lod, uint32_t *active_bits_dev,
                                  uint32_t *skippable_bits_dev, uint32_t *active_list_dev,
                                  uint32_t *n_active_dev, void *stream);
+
+/* Copy a level's 4^3 sub-brick data (nsb = ceil(n/4) per axis, sub-brick
+ * (sx,sy,sz) at index (sz*nsb + sy)*nsb + sx): min/max as two
+ * [nsb^3][nvars] float32 device arrays over the vertices 4s..min(4s+4, n-1),
+ * and the activity bits under the current brush, ceil(nsb^3/32) uint32 words,
+ * with the activity rule of the 8^3 bricks (Section 2.2 brush test with the
+ * rounding margin). Any output may be NULL. */
+raypc_status raypc_get_sub_bricks(raypc_ctx *ctx, int vol, int lod, float *out_min_dev,
+                                  float *out_max_dev, uint32_t *active_bits_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -48,18 +48,20 @@ raypc_status cuda_fail(cudaError_t e, const char* what) {
 namespace {
 
 void free_level(Level& L) {
-    void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
+    void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
+                    L.sbmin, L.sbmax, L.sactive};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
 }
 
 void free_bricks(Level& L) {
-    void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count};
+    void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
+                    L.sbmin, L.sbmax, L.sactive};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    L.bmin = L.bmax = nullptr;
-    L.active = L.skippable = L.list = L.n_active = nullptr;
+    L.bmin = L.bmax = L.sbmin = L.sbmax = nullptr;
+    L.active = L.skippable = L.list = L.n_active = L.sactive = nullptr;
     L.pass_count = nullptr;
     L.bricks = L.classified = false;
 }
@@ -72,7 +74,8 @@ void free_volume(raypc_ctx* ctx, Volume* V) {
 }
 
 
-// Classify every built level under the current brush (three launches total).
+// Classify the bricks and sub-bricks of every built level under the current
+// brush (three launches total).
 raypc_status classify_all(Volume* V, cudaStream_t s) {
     ClassifyArgs c{};
     c.nvars = V->nvars;
@@ -86,11 +89,22 @@ raypc_status classify_all(Volume* V, cudaStream_t s) {
         C.bmin = L.bmin;
         C.bmax = L.bmax;
         C.n = L.n;
+        C.bs = kBrick;
         C.active = L.active;
         C.skippable = L.skippable;
         C.list = L.list;
         C.n_active = L.n_active;
         C.pass_count = L.pass_count;
+    }
+    c.nbrick = c.nlev;
+    for (int l = 0; l < V->nlev; ++l) {
+        Level& L = V->lv[l];
+        ClassifyLevel& C = c.lv[c.nlev++];
+        C.bmin = L.sbmin;
+        C.bmax = L.sbmax;
+        C.n = L.n;
+        C.bs = kSub;
+        C.active = L.sactive;
     }
     CK(launch_classify(c, s), "classify kernels");
     for (int l = 0; l < V->nlev; ++l) V->lv[l].classified = true;
@@ -109,8 +123,12 @@ raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
     size_t nbk = L.nbricks();
     size_t mm = nbk * V->nvars * sizeof(float);
     size_t words = L.nwords() * sizeof(uint32_t);
+    size_t smm = L.nsbricks() * V->nvars * sizeof(float);
     raypc_status st;
-    if ((st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
+    if ((st = ctx->alloc((void**)&L.sbmin, smm, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.sbmax, smm, &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.sactive, L.nswords() * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.bmax, mm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.active, words, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.skippable, words, &V->bytes)) ||
@@ -139,7 +157,8 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
         if (e != cudaSuccess) { cudaFreeAsync(staging, s); return cuda_fail(e, "host to device copy"); }
         dsrc = staging;
     }
-    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, s);
+    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, L.sbmin,
+                      L.sbmax, s);
     if (staging) cudaFreeAsync(staging, s);
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     L.bricks = true;               // level-0 brick min/max come out of the ingest pass
@@ -200,6 +219,8 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.lv.pairs = L->pairs;
     a.lv.n = L->n;
     a.lv.nb = L->nb;
+    a.lv.nsb = L->nsb;
+    a.lv.sactive = L->sactive;
     a.lv.bmin = L->bmin;
     a.lv.bmax = L->bmax;
     a.lv.active = L->active;
@@ -304,7 +325,7 @@ raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_devic
     if (nvars < 1 || nvars > RAYPC_MAX_VARS) return fail(RAYPC_ERR_INVALID_ARG, "nvars %d not in 1..%d", nvars, RAYPC_MAX_VARS);
     if (nx < 2 || ny < 2 || nz < 2) return fail(RAYPC_ERR_INVALID_ARG, "grid must be at least 2 cells per axis");
     if (nx != ny || ny != nz) return fail(RAYPC_ERR_UNSUPPORTED, "only cubic grids are supported (%d x %d x %d)", nx, ny, nz);
-    if (nx > 8192) return fail(RAYPC_ERR_UNSUPPORTED, "grid edge %d > 8192", nx);
+    if (nx > kMaxRowsEdge) return fail(RAYPC_ERR_UNSUPPORTED, "grid edge %d > %d", nx, kMaxRowsEdge);
     if (!(r_in >= 0.f) || !(r_out > r_in) || !isfinite(r_out))
         return fail(RAYPC_ERR_INVALID_ARG, "need 0 <= r_in < r_out (got %g, %g)", r_in, r_out);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -319,8 +340,7 @@ raypc_status raypc_load_volume(raypc_ctx* ctx, const void* src, int src_is_devic
     V->r_in = r_in;
     V->r_out = r_out;
     Level& L = V->lv[0];
-    L.n = n;
-    L.nb = (n + RAYPC_BRICK - 1) / RAYPC_BRICK;
+    L.set_edge(n);
     L.cells_bytes = nvox * nvars * elem_size(store_dtype);
     L.pairs_bytes = 2 * L.cells_bytes;
     raypc_status st = ctx->alloc(&L.cells, L.cells_bytes, &V->bytes);
@@ -387,8 +407,7 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
         int m = (P.n + 1) / 2;
         if (m < 2) return fail(RAYPC_ERR_INVALID_ARG, "level %d would have fewer than 2 cells per axis", l);
         if (!L.cells) {
-            L.n = m;
-            L.nb = (m + RAYPC_BRICK - 1) / RAYPC_BRICK;
+            L.set_edge(m);
             L.cells_bytes = (size_t)m * m * m * V->nvars * elem_size(V->dtype);
             L.pairs_bytes = 2 * L.cells_bytes;
             st = ctx->alloc(&L.cells, L.cells_bytes, &V->bytes);
@@ -396,7 +415,8 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
             if (st) return st;
         }
         if ((st = alloc_bricks(ctx, V, L))) return st;
-        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, L.bmin, L.bmax, s), "LOD kernel");
+        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, L.bmin, L.bmax, L.sbmin, L.sbmax, s),
+           "LOD kernel");
         L.bricks = true;
     }
     if (V->stale || 1 + n_lod > V->nlev) V->nlev = 1 + n_lod;   // stale coarser levels drop out
@@ -597,6 +617,30 @@ raypc_status raypc_get_skip_list(raypc_ctx* ctx, int vol, int lod, uint32_t* act
     if (skippable_bits_dev) CK(cudaMemcpyAsync(skippable_bits_dev, L->skippable, wb, cudaMemcpyDeviceToDevice, s), "copy skippable bits");
     if (active_list_dev) CK(cudaMemcpyAsync(active_list_dev, L->list, L->nbricks() * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active list");
     if (n_active_dev) CK(cudaMemcpyAsync(n_active_dev, L->n_active, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active count");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_get_sub_bricks(raypc_ctx* ctx, int vol, int lod, float* out_min_dev, float* out_max_dev,
+                                  uint32_t* active_bits_dev, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d not built", lod);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = L->nsbricks() * V->nvars * sizeof(float);
+    if (out_min_dev) CK(cudaMemcpyAsync(out_min_dev, L->sbmin, bytes, cudaMemcpyDeviceToDevice, s), "copy sub-brick min");
+    if (out_max_dev) CK(cudaMemcpyAsync(out_max_dev, L->sbmax, bytes, cudaMemcpyDeviceToDevice, s), "copy sub-brick max");
+    if (active_bits_dev) {
+        if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
+        if ((st = ensure_classified(V, *L, s))) return st;
+        CK(cudaMemcpyAsync(active_bits_dev, L->sactive, L->nswords() * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s),
+           "copy sub-brick active bits");
+    }
     return RAYPC_OK;
 }
 

@@ -31,8 +31,8 @@ struct raypc_batch {
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool used[2] = {false, false};
     int cur = 0;
-    std::vector<uint32_t*> bits;      // per view slot: active words, then skippable words
-    std::vector<size_t> bits_words;   // capacity (words per mask) per slot
+    std::vector<uint32_t*> bits;      // per view slot: active, skippable, then sub-brick active words
+    std::vector<size_t> bits_words;   // capacity (words) per slot
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int exec_key[2] = {-1, -1};       // dtype * 16 + variant of the captured graph
@@ -184,25 +184,29 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;
         if (i == 0) variant = bv.a.variant;
         bv.a.variant = variant;
-        const size_t words = L->nwords();
-        if (b->bits_words[i] < words) {
+        const size_t words = L->nwords(), need = 2 * words + L->nswords();
+        if (b->bits_words[i] < need) {
             // growing a slot's masks: no batch may still be reading the old ones
             wait_idle(b);
             if (b->bits[i]) cudaFree(b->bits[i]);
             b->bits[i] = nullptr;
             b->bits_words[i] = 0;
             size_t ch = 0;
-            if ((st = ctx->alloc((void**)&b->bits[i], 2 * words * sizeof(uint32_t), &ch))) return st;
+            if ((st = ctx->alloc((void**)&b->bits[i], need * sizeof(uint32_t), &ch))) return st;
             b->charged += ch;
-            b->bits_words[i] = words;
+            b->bits_words[i] = need;
         }
         bv.a.lv.active = b->bits[i];
-        bv.a.lv.skippable = b->bits[i] + b->bits_words[i];
+        bv.a.lv.skippable = b->bits[i] + words;
+        bv.a.lv.sactive = b->bits[i] + 2 * words;
         bv.a.pass_count = b->d_pass + (size_t)i * kMaxVars;
         bv.bmin = L->bmin;
         bv.bmax = L->bmax;
+        bv.sbmin = L->sbmin;
+        bv.sbmax = L->sbmax;
         bv.cls_begin = cls;
-        cls += (unsigned long long)(L->nbricks() + 31) / 32 * 32;
+        bv.cls_sub = (unsigned long long)words * 32;
+        cls += (unsigned long long)(words + L->nswords()) * 32;
         bv.tiles_x = (q.w + block_tile_w(variant) - 1) / block_tile_w(variant);
         bv.tile_begin = (int)tiles;
         bv.ntiles = bv.tiles_x * ((q.h + block_tile_h(variant) - 1) / block_tile_h(variant));

@@ -16,6 +16,7 @@
 namespace raypc {
 
 constexpr int kBrick = 8;
+constexpr int kSub = 4;          // edge of the sub-bricks whose activity the render tests per sample
 constexpr int kMaxVars = 8;
 constexpr int kTF = 256;
 constexpr int kNStats = 8;
@@ -102,10 +103,12 @@ struct LevelArgs {
     const void* pairs;         // x-pairs per variable
     int n;                     // cube edge in cells
     int nb;                    // bricks per axis
+    int nsb;                   // sub-bricks per axis
     const float* bmin;         // [nb^3][nvars]
     const float* bmax;
     const uint32_t* active;    // bitmask, ceil(nb^3/32) words
     const uint32_t* skippable; // bitmask
+    const uint32_t* sactive;   // sub-brick bitmask, ceil(nsb^3/32) words
 };
 
 struct BrushArgs {
@@ -134,10 +137,6 @@ struct RenderArgs {
     unsigned long long* stats;    // optional kNStats counters
 };
 
-// One view of a batched render: the march arguments (lv.active / lv.skippable
-// / pass_count point at this view's own classification), the level's brick
-// min/max for that classification, and the view's ranges in the flat brick
-// and tile spaces of the batch.
 // Completion record of one view, in mapped pinned host memory: the block that
 // finishes the view's last tile copies the view's statistics here and then
 // stores the launch sequence number (after a system-scope fence), so the host
@@ -148,11 +147,20 @@ struct ViewDone {
     unsigned long long stats[kNStats];
 };
 
+// One view of a batched render: the march arguments (lv.active / lv.skippable
+// / lv.sactive / pass_count point at this view's own classification), the
+// level's brick and sub-brick min/max for that classification, and the view's
+// ranges in the flat brick and tile spaces of the batch. A view's flat brick
+// range holds its bricks (padded to a multiple of 32) followed by its
+// sub-bricks.
 struct BatchView {
     RenderArgs a;
     const float* bmin;
     const float* bmax;
+    const float* sbmin;
+    const float* sbmax;
     unsigned long long cls_begin;  // first flat brick index (multiple of 32)
+    unsigned long long cls_sub;    // offset of the first sub-brick in the view's range (multiple of 32)
     int tiles_x;                   // tiles per image row
     int tile_begin;                // first flat tile index
     int ntiles;                    // tiles of this view
@@ -193,23 +201,23 @@ struct HistArgs {
     uint32_t* out;                // (naxes-1) x bins x bins
 };
 
-// World box that the samples assigned to brick b (lower interpolation index in
-// [8b, 8b+8)) can occupy along one axis, widened by 2^-10; the first and last
-// bricks also own the clamped border.
-__device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, float& lo, float& hi) {
-    lo = __fsub_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
-    hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * kBrick + kBrick), 0.5f), sc, -1.0f), 0x1p-10f);
+// World box that the samples assigned to brick b of edge bs (lower
+// interpolation index in [bs b, bs b + bs)) can occupy along one axis, widened
+// by 2^-10; the first and last bricks also own the clamped border.
+__device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, int bs, float& lo, float& hi) {
+    lo = __fsub_rn(__fmaf_rn(__fadd_rn((float)(b * bs), 0.5f), sc, -1.0f), 0x1p-10f);
+    hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * bs + bs), 0.5f), sc, -1.0f), 0x1p-10f);
     if (b == 0) lo = -2.0f;
     if (b == nb - 1) hi = 2.0f;
 }
 
-// Brush classification of brick b of a level with nb bricks per axis
-// (sc = 2/n): active iff its widened sample box meets the shell and, for every
+// Brush classification of brick b (edge bs) of a level with nb such bricks per
+// axis (sc = 2/n): active iff its widened sample box meets the shell and, for every
 // restricted v, max_v + d >= lo_v and min_v - d <= hi_v with
 // d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
 // rounding). pass_bits gets bit v set for each restricted variable the brick
 // passes on its own (only meaningful when the box meets the shell).
-__device__ __forceinline__ bool classify_brick(size_t b, int nb, float sc, float rin2, float rout2,
+__device__ __forceinline__ bool classify_brick(size_t b, int nb, int bs, float sc, float rin2, float rout2,
                                                const BrushArgs& brush, int nvars, const float* bmin,
                                                const float* bmax, unsigned& pass_bits) {
     int c[3] = {(int)(b % nb), (int)((b / nb) % nb), (int)(b / ((size_t)nb * nb))};
@@ -217,7 +225,7 @@ __device__ __forceinline__ bool classify_brick(size_t b, int nb, float sc, float
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float lo, hi;
-        brick_box_axis(c[a], nb, sc, lo, hi);
+        brick_box_axis(c[a], nb, sc, bs, lo, hi);
         nearc[a] = (lo > 0.0f) ? lo : ((hi < 0.0f) ? -hi : 0.0f);
         farc[a] = fmaxf(fabsf(lo), fabsf(hi));
     }
@@ -253,12 +261,16 @@ __device__ __forceinline__ bool skippable_brick(size_t b, int nb, const uint32_t
 }
 
 // Classification of all built levels of a volume in one launch per kernel.
+// Entries 0..nbrick-1 are the 8^3 bricks of the levels (active, skippable,
+// compacted list, selectivity counts); the entries after them are sub-brick
+// grids (bs = kSub: active bits only; the other outputs are null).
 struct ClassifyLevel {
     const float* bmin;
     const float* bmax;
     int n;                        // level edge
+    int bs;                       // brick edge (kBrick or kSub)
     float sc;                     // 2 / n, set by the launcher
-    size_t first;                 // first flat index of this level (multiple of 32), set by the launcher
+    size_t first;                 // first flat index of this entry (multiple of 32), set by the launcher
     uint32_t* active;
     uint32_t* skippable;
     uint32_t* list;
@@ -267,23 +279,28 @@ struct ClassifyLevel {
 };
 
 struct ClassifyArgs {
-    int nlev;
+    int nlev;                     // entries in lv
+    int nbrick;                   // leading entries with bs = kBrick
     int nvars;
     float rin2, rout2;            // r_in * r_in, r_out * r_out rounded to FP32
     BrushArgs brush;
-    size_t total;                 // set by the launcher
-    ClassifyLevel lv[3];
+    size_t total;                 // set by the launcher: flat range of all entries
+    size_t total_brick;           // set by the launcher: flat range of the kBrick entries
+    ClassifyLevel lv[6];
 };
 
 // Process-wide count of launched kernels (defined in api.cu).
 void count_launches(int k);
 
 // Launchers (defined in the .cu files; all enqueue on `stream`).
-// Ingest (level 0) and LOD (coarser level) also write the level's brick min/max.
+// Ingest (level 0) and LOD (coarser level) also write the level's brick and
+// sub-brick min/max (n <= kMaxRowsEdge).
+constexpr int kMaxRowsEdge = 4096;
 cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype,
-                          int n, int nvars, float* bmin, float* bmax, cudaStream_t stream);
+                          int n, int nvars, float* bmin, float* bmax, float* sbmin, float* sbmax,
+                          cudaStream_t stream);
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
-                       float* bmin, float* bmax, cudaStream_t stream);
+                       float* bmin, float* bmax, float* sbmin, float* sbmax, cudaStream_t stream);
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
 // Batched render: per-view classification, then a persistent kernel that pulls

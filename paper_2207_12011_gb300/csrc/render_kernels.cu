@@ -4,20 +4,25 @@
 // rays fetch neighbouring vertices, and a 128-thread block covers 16x8
 // pixels. The per-pixel march is one device function shared by the
 // single-frame kernel and the persistent batched kernel, so a view renders
-// bit-identically alone and inside a batch. Per lattice sample: position, interpolation cell and brick
-// (exactly rounded FP32), brick activity bit (samples in inactive bricks
-// cannot pass the brush or the shell test), shell test, then the restricted
+// bit-identically alone and inside a batch. Per lattice sample: position,
+// interpolation cell (exactly rounded FP32), the activity bit of the 4^3
+// sub-brick that holds the cell (samples in inactive sub-bricks cannot pass
+// the brush or the shell test), shell test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
 // selective first; the order cannot change the result), each as an FP32
 // trilinear interpolation from four x-pair loads of that variable only, with
 // exit on the first failure. Kept samples are coloured by the transfer function (from shared
 // memory) and composited front to back with early ray termination.
 //
-// Empty-space skipping: when a sample falls in a skippable brick (inactive
-// with all 26 neighbours inactive), the ray jumps to one lattice point before
-// the one at which it leaves the brick; every jumped sample lies in that brick
-// or, after FP32 rounding, in one of its inactive neighbours, so skipping
-// changes no decision. The lattice itself (t_k = t0 + (k + 1/2) dt) is never
+// Empty-space skipping: when a sample falls in an inactive sub-brick, the ray
+// jumps over the rest of its box -- the whole 8^3 brick when that is inactive
+// too, else the 4^3 sub-brick. The last sample still inside the box is
+// estimated from the box's exit plane and then recomputed with the exact
+// per-sample arithmetic; the jump is taken only if that sample is in the box.
+// Along a ray every step from k to the cell index on one axis (t_k, position,
+// grid coordinate, clamp, floor, min) is monotone in k, so two samples in the
+// box enclose only samples in the box: skipping changes no decision and needs
+// no neighbour condition. The lattice itself (t_k = t0 + (k + 1/2) dt) is never
 // shifted.
 #include "common.cuh"
 
@@ -138,7 +143,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             const float sq = __fsqrt_rn(disc);
             const float t0 = fmaxf(__fsub_rn(-b, sq), 0.0f);
             const float t1 = __fadd_rn(-b, sq);
-            const int n = A.lv.n, nb = A.lv.nb;
+            const int n = A.lv.n, nb = A.lv.nb, nsb = A.lv.nsb;
             const float hn = 0.5f * (float)n, off = hn - 0.5f;
             const float dt = A.dt;
             const size_t sy_ = (size_t)n, sz_ = (size_t)n * n, plane = sz_ * n;
@@ -160,27 +165,39 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 grid_coord_rn(pxw, n, hn, off, ix, fx);
                 grid_coord_rn(pyw, n, hn, off, iy, fy);
                 grid_coord_rn(pzw, n, hn, off, iz, fz);
-                const int bx = ix >> 3, by = iy >> 3, bz = iz >> 3;
-                const uint32_t bid = ((uint32_t)bz * nb + by) * nb + bx;
-                if (!bit_of(A.lv.active, bid)) {
-                    if (A.skip && bit_of(A.lv.skippable, bid)) {
-                        // exit time from the brick's sample region (any conservative value works)
-                        float te = __int_as_float(0x7f800000);
+                const uint32_t sid = ((uint32_t)(iz >> 2) * nsb + (iy >> 2)) * nsb + (ix >> 2);
+                if (!bit_of(A.lv.sactive, sid)) {
+                    if (A.skip) {
+                        const uint32_t bid = ((uint32_t)(iz >> 3) * nb + (iy >> 3)) * nb + (ix >> 3);
+                        const int sh = bit_of(A.lv.active, bid) ? 2 : 3;
+                        const int bw = 1 << sh;
+                        const int lo[3] = {(ix >> sh) << sh, (iy >> sh) << sh, (iz >> sh) << sh};
                         const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz}, ii[3] = {idx, idy, idz};
-                        const int bb[3] = {bx, by, bz};
+                        // estimated exit time from the box (lower index in [lo, lo + bw) per axis)
+                        float te = __int_as_float(0x7f800000);
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            if (dd[a] > 0.0f && bb[a] < nb - 1)
-                                te = fminf(te, (fmaf((float)(kBrick * (bb[a] + 1)) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
-                            else if (dd[a] < 0.0f && bb[a] > 0)
-                                te = fminf(te, (fmaf((float)(kBrick * bb[a]) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
+                            if (dd[a] > 0.0f && lo[a] + bw <= n - 2)
+                                te = fminf(te, (fmaf((float)(lo[a] + bw) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
+                            else if (dd[a] < 0.0f && lo[a] > 0)
+                                te = fminf(te, (fmaf((float)lo[a] + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
                         }
                         const float kk = fminf((te - t0) * inv_dt - 0.5f, 1.0e9f);
-                        int kn = (kk > (float)k) ? (int)ceilf(kk) - 1 : k + 1;
-                        kn = min(max(kn, k + 1), n_lat);
-                        skipped += (unsigned)(kn - k - 1);
-                        k = kn;
-                        continue;
+                        const int kl = kk > (float)(k + 1) ? min((int)ceilf(kk) - 1, n_lat - 1) : k;
+                        if (kl > k) {
+                            // the estimated last sample, recomputed exactly
+                            const float tl = __fmaf_rn(__fadd_rn((float)kl, 0.5f), dt, t0);
+                            int jx, jy, jz;
+                            float gx, gy, gz;
+                            grid_coord_rn(__fmaf_rn(tl, dx, ox), n, hn, off, jx, gx);
+                            grid_coord_rn(__fmaf_rn(tl, dy, oy), n, hn, off, jy, gy);
+                            grid_coord_rn(__fmaf_rn(tl, dz, oz), n, hn, off, jz, gz);
+                            if (((jx ^ ix) >> sh) == 0 && ((jy ^ iy) >> sh) == 0 && ((jz ^ iz) >> sh) == 0) {
+                                skipped += (unsigned)(kl - k);
+                                k = kl + 1;
+                                continue;
+                            }
+                        }
                     }
                     ++k;
                     continue;
@@ -272,15 +289,19 @@ __global__ void k_classify_views(const BatchHeader* __restrict__ hdr, const Batc
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < H.cls_total; g += stride) {
         const int vi = view_of_brick(H, views, g - lane);
         const BatchView& V = views[vi];
-        const int nb = V.a.lv.nb;
+        size_t b = g - V.cls_begin;
+        const bool sub = b >= V.cls_sub;             // uniform per warp: cls_sub is a multiple of 32
+        if (sub) b -= V.cls_sub;
+        const int nb = sub ? V.a.lv.nsb : V.a.lv.nb;
         const size_t nbricks = (size_t)nb * nb * nb;
-        const size_t b = g - V.cls_begin;
         unsigned pass_bits = 0;
         const bool act = b < nbricks &&
-            classify_brick(b, nb, 2.0f / (float)V.a.lv.n, V.a.rin2, V.a.rout2, V.a.brush, V.a.nvars, V.bmin, V.bmax, pass_bits);
+            classify_brick(b, nb, sub ? kSub : kBrick, 2.0f / (float)V.a.lv.n, V.a.rin2, V.a.rout2, V.a.brush,
+                           V.a.nvars, sub ? V.sbmin : V.bmin, sub ? V.sbmax : V.bmax, pass_bits);
         const unsigned word = __ballot_sync(0xffffffffu, act);
-        uint32_t* active = const_cast<uint32_t*>(V.a.lv.active);
+        uint32_t* active = const_cast<uint32_t*>(sub ? V.a.lv.sactive : V.a.lv.active);
         if (lane == 0) active[b >> 5] = word;
+        if (sub) continue;
         for (int v = 0; v < V.a.nvars; ++v) {
             const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
             if (lane == 0 && cnt) atomicAdd(const_cast<unsigned*>(V.a.pass_count) + v, cnt);
@@ -297,6 +318,7 @@ __global__ void k_skippable_views(const BatchHeader* __restrict__ hdr, const Bat
         const BatchView& V = views[vi];
         const int nb = V.a.lv.nb;
         const size_t b = g - V.cls_begin;
+        if (b >= V.cls_sub) continue;                // sub-bricks have no skippable bits
         const bool s = b < (size_t)nb * nb * nb && skippable_brick(b, nb, V.a.lv.active);
         const unsigned word = __ballot_sync(0xffffffffu, s);
         if (lane == 0) const_cast<uint32_t*>(V.a.lv.skippable)[b >> 5] = word;

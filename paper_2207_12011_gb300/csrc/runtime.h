@@ -41,7 +41,7 @@ struct DeviceGuard {
 };
 
 struct Level {
-    int n = 0, nb = 0;
+    int n = 0, nb = 0, nsb = 0;   // edge, 8^3 bricks per axis, 4^3 sub-bricks per axis
     void* cells = nullptr;     // planar values, storage dtype
     void* pairs = nullptr;     // per-variable x-pairs (render layout)
     size_t cells_bytes = 0, pairs_bytes = 0;
@@ -52,10 +52,20 @@ struct Level {
     uint32_t* list = nullptr;
     uint32_t* n_active = nullptr;
     unsigned* pass_count = nullptr;
+    float* sbmin = nullptr;       // [nsb^3][nvars]
+    float* sbmax = nullptr;
+    uint32_t* sactive = nullptr;  // sub-brick activity bits under the current brush
     bool bricks = false;
     bool classified = false;
     size_t nbricks() const { return (size_t)nb * nb * nb; }
     size_t nwords() const { return (nbricks() + 31) / 32; }
+    size_t nsbricks() const { return (size_t)nsb * nsb * nsb; }
+    size_t nswords() const { return (nsbricks() + 31) / 32; }
+    void set_edge(int edge) {
+        n = edge;
+        nb = (edge + kBrick - 1) / kBrick;
+        nsb = (edge + kSub - 1) / kSub;
+    }
 };
 
 struct Volume {

@@ -143,7 +143,7 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         void* bits = nullptr;
         void* list = nullptr;
         void* misc = nullptr;
-        cudaError_t e = cudaMalloc(&bits, 2 * words * sizeof(uint32_t));
+        cudaError_t e = cudaMalloc(&bits, (2 * words + L->nswords()) * sizeof(uint32_t));
         if (e == cudaSuccess) temps.push_back(bits);
         if (e == cudaSuccess) e = cudaMalloc(&list, L->nbricks() * sizeof(uint32_t) + 16);
         if (e == cudaSuccess) temps.push_back(list);
@@ -151,7 +151,8 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         if (e == cudaSuccess) temps.push_back(misc);
         if (e != cudaSuccess) { st = cuda_fail(e, "tuning buffers"); break; }
         ClassifyArgs c{};
-        c.nlev = 1;
+        c.nlev = 2;
+        c.nbrick = 1;
         c.nvars = V->nvars;
         c.rin2 = V->r_in * V->r_in;
         c.rout2 = V->r_out * V->r_out;
@@ -159,15 +160,22 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         c.lv[0].bmin = L->bmin;
         c.lv[0].bmax = L->bmax;
         c.lv[0].n = L->n;
+        c.lv[0].bs = kBrick;
         c.lv[0].active = (uint32_t*)bits;
         c.lv[0].skippable = (uint32_t*)bits + words;
         c.lv[0].list = (uint32_t*)list;
         c.lv[0].pass_count = (unsigned*)misc;
         c.lv[0].n_active = (uint32_t*)misc + kMaxVars;
+        c.lv[1].bmin = L->sbmin;
+        c.lv[1].bmax = L->sbmax;
+        c.lv[1].n = L->n;
+        c.lv[1].bs = kSub;
+        c.lv[1].active = (uint32_t*)bits + 2 * words;
         cudaError_t ce = launch_classify(c, s);
         if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning classification"); break; }
         args[i].lv.active = c.lv[0].active;
         args[i].lv.skippable = c.lv[0].skippable;
+        args[i].lv.sactive = c.lv[1].active;
         args[i].pass_count = c.lv[0].pass_count;
     }
     if (st != RAYPC_OK) {

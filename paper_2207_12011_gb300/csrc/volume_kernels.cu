@@ -12,31 +12,10 @@ namespace {
 
 constexpr int kRowThreads = 256;
 
-__device__ __forceinline__ float load_src(const void* src, int dtype, size_t i) {
-    if (dtype == kF16) return __half2float(__ldg(reinterpret_cast<const __half*>(src) + i));
-    return __ldg(reinterpret_cast<const float*>(src) + i);
-}
-
 // Round to the storage dtype (the stored value, as a float).
 template <int DT> __device__ __forceinline__ float to_stored(float v);
 template <> __device__ __forceinline__ float to_stored<kF32>(float v) { return v; }
 template <> __device__ __forceinline__ float to_stored<kF16>(float v) { return __half2float(__float2half_rn(v)); }
-
-template <int DT> __device__ __forceinline__ void store_cell(void* cells, size_t i, float v);
-template <> __device__ __forceinline__ void store_cell<kF32>(void* cells, size_t i, float v) {
-    reinterpret_cast<float*>(cells)[i] = v;
-}
-template <> __device__ __forceinline__ void store_cell<kF16>(void* cells, size_t i, float v) {
-    reinterpret_cast<__half*>(cells)[i] = __float2half_rn(v);
-}
-
-template <int DT> __device__ __forceinline__ void store_pair(void* pairs, size_t i, float a, float b);
-template <> __device__ __forceinline__ void store_pair<kF32>(void* pairs, size_t i, float a, float b) {
-    reinterpret_cast<float2*>(pairs)[i] = make_float2(a, b);
-}
-template <> __device__ __forceinline__ void store_pair<kF16>(void* pairs, size_t i, float a, float b) {
-    reinterpret_cast<__half2*>(pairs)[i] = __floats2half2_rn(a, b);
-}
 
 struct RowsArgs {
     const void* src;      // ingest: planar source (src_dtype); LOD: planar cells of the finer level
@@ -48,102 +27,253 @@ struct RowsArgs {
     int nvars;
     float* bmin;          // [nb^3][nvars]
     float* bmax;
+    float* sbmin;         // [nsb^3][nvars], sub-bricks of edge kSub
+    float* sbmax;
 };
 
-// Value of cell (x, y, z) of variable v of the level being produced, rounded
-// to the storage dtype.
-//   MODE 0 (ingest): the converted source value.
-//   MODE 1 (LOD):    FP32 mean of the 2x2x2 fine cells, fine indices clamped,
-//                    ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
-template <int DT, int MODE>
-__device__ __forceinline__ float produce(const RowsArgs& A, int x, int y, int z, int v) {
-    if (MODE == 0) {
-        const size_t n = (size_t)A.n;
-        return to_stored<DT>(load_src(A.src, A.src_dtype, ((v * n + z) * n + y) * n + x));
-    } else {
-        const int nf = A.n_src;
-        const int x0 = 2 * x, y0 = 2 * y, z0 = 2 * z;
-        const int x1 = min(x0 + 1, nf - 1), y1 = min(y0 + 1, nf - 1), z1 = min(z0 + 1, nf - 1);
-        const size_t plane = (size_t)v * nf * nf * nf;
-        auto at = [&](int a, int b, int c) { return load_cell<DT>(A.src, plane + ((size_t)c * nf + b) * nf + a); };
-        float s0 = __fadd_rn(__fadd_rn(at(x0, y0, z0), at(x1, y0, z0)), __fadd_rn(at(x0, y1, z0), at(x1, y1, z0)));
-        float s1 = __fadd_rn(__fadd_rn(at(x0, y0, z1), at(x1, y0, z1)), __fadd_rn(at(x0, y1, z1), at(x1, y1, z1)));
-        return to_stored<DT>(__fmul_rn(__fadd_rn(s0, s1), 0.125f));
+__device__ __forceinline__ void fold(float& mn, float& mx, float a_mn, float a_mx) {
+    mn = fminf(mn, a_mn);
+    mx = fmaxf(mx, a_mx);
+}
+
+// VEC consecutive values of a planar array of element type T (kF32 / kF16)
+// starting at element i (aligned to VEC elements when VEC > 1), as floats.
+template <int T, int VEC> __device__ __forceinline__ void load_run(const void* base, size_t i, float* out);
+template <> __device__ __forceinline__ void load_run<kF32, 1>(const void* base, size_t i, float* out) {
+    out[0] = __ldg(reinterpret_cast<const float*>(base) + i);
+}
+template <> __device__ __forceinline__ void load_run<kF16, 1>(const void* base, size_t i, float* out) {
+    out[0] = __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(base) + i)));
+}
+template <> __device__ __forceinline__ void load_run<kF32, 2>(const void* base, size_t i, float* out) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(reinterpret_cast<const float*>(base) + i));
+    out[0] = a.x; out[1] = a.y;
+}
+template <> __device__ __forceinline__ void load_run<kF16, 2>(const void* base, size_t i, float* out) {
+    const unsigned w = __ldg(reinterpret_cast<const unsigned*>(reinterpret_cast<const __half*>(base) + i));
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    out[0] = f.x; out[1] = f.y;
+}
+template <> __device__ __forceinline__ void load_run<kF32, 4>(const void* base, size_t i, float* out) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(base) + i));
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+}
+template <> __device__ __forceinline__ void load_run<kF16, 4>(const void* base, size_t i, float* out) {
+    const uint2 w = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __half*>(base) + i));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+template <> __device__ __forceinline__ void load_run<kF32, 8>(const void* base, size_t i, float* out) {
+    load_run<kF32, 4>(base, i, out);
+    load_run<kF32, 4>(base, i + 4, out + 4);
+}
+template <> __device__ __forceinline__ void load_run<kF16, 8>(const void* base, size_t i, float* out) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const __half*>(base) + i));
+    const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&ws[q]));
+        out[2 * q] = f.x;
+        out[2 * q + 1] = f.y;
     }
 }
 
-// One block per (brick row (by, bz), variable), up to 256 threads (one per x
-// column, striding when the level is wider). Threads own x columns; the
-// block streams the (up to) 9 x 9 x-rows y in [8by, 8by+8], z in [8bz, 8bz+8]
-// of the level, writes the 8 x 8 rows it owns (cells and x-pairs; the right
-// element of a pair comes from the neighbouring lane) and folds every row,
-// apron rows included, into per-column NaN-ignoring min/max. Columns are then
-// reduced to bricks in shared memory. Brick (bx, by, bz) covers vertices
-// 8b..min(8b+8, n-1) on each axis.
-template <int DT, int MODE>
+// Store VEC stored values (already rounded to DT) of one row run: the cells
+// and their x-pairs (c[x], c[x+1]); val[VEC] is the value right of the run.
+template <int DT, int VEC>
+__device__ __forceinline__ void store_run(void* cells, void* pairs, size_t i, const float* val) {
+    if (DT == kF32) {
+        float* c = reinterpret_cast<float*>(cells) + i;
+        float2* p = reinterpret_cast<float2*>(pairs) + i;
+        if (VEC == 4) {
+            *reinterpret_cast<float4*>(c) = make_float4(val[0], val[1], val[2], val[3]);
+            reinterpret_cast<float4*>(p)[0] = make_float4(val[0], val[1], val[1], val[2]);
+            reinterpret_cast<float4*>(p)[1] = make_float4(val[2], val[3], val[3], val[4]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                c[q] = val[q];
+                p[q] = make_float2(val[q], val[q + 1]);
+            }
+        }
+    } else {
+        __half h[VEC + 1];
+#pragma unroll
+        for (int q = 0; q <= VEC; ++q) h[q] = __float2half_rn(val[q]);   // exact: values are stored halves
+        __half* c = reinterpret_cast<__half*>(cells) + i;
+        __half2* p = reinterpret_cast<__half2*>(pairs) + i;
+        if (VEC == 4) {
+            __half2 c01 = __halves2half2(h[0], h[1]), c23 = __halves2half2(h[2], h[3]);
+            uint2 cw;
+            cw.x = *reinterpret_cast<unsigned*>(&c01);
+            cw.y = *reinterpret_cast<unsigned*>(&c23);
+            *reinterpret_cast<uint2*>(c) = cw;
+            __half2 p0 = __halves2half2(h[0], h[1]), p1 = __halves2half2(h[1], h[2]);
+            __half2 p2 = __halves2half2(h[2], h[3]), p3 = __halves2half2(h[3], h[4]);
+            uint4 pw;
+            pw.x = *reinterpret_cast<unsigned*>(&p0);
+            pw.y = *reinterpret_cast<unsigned*>(&p1);
+            pw.z = *reinterpret_cast<unsigned*>(&p2);
+            pw.w = *reinterpret_cast<unsigned*>(&p3);
+            *reinterpret_cast<uint4*>(p) = pw;
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                c[q] = h[q];
+                p[q] = __halves2half2(h[q], h[q + 1]);
+            }
+        }
+    }
+}
+
+// Values of columns X .. X+VEC of row (y, z) of variable v of the level being
+// produced, rounded to the storage dtype DT; column X+VEC is clamped to n-1.
+//   MODE 0 (ingest): the converted source value (source element type SRC).
+//   MODE 1 (LOD):    FP32 mean of the 2x2x2 fine cells, fine indices clamped,
+//                    ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
+// With VEC > 1 the caller guarantees n % VEC == 0 and, for LOD, an even fine edge.
+template <int DT, int MODE, int SRC, int VEC>
+__device__ __forceinline__ void produce_run(const RowsArgs& A, int X, int y, int z, int v, float* val) {
+    const int n = A.n;
+    const bool right = X + VEC < n;
+    if (MODE == 0) {
+        const size_t row = (((size_t)v * n + z) * n + y) * n;
+        load_run<SRC, VEC>(A.src, row + X, val);
+        load_run<SRC, 1>(A.src, row + (right ? X + VEC : X + VEC - 1), val + VEC);
+#pragma unroll
+        for (int q = 0; q <= VEC; ++q) val[q] = to_stored<DT>(val[q]);
+    } else {
+        const int nf = A.n_src;
+        const int y0 = 2 * y, y1 = min(y0 + 1, nf - 1), z0 = 2 * z, z1 = min(z0 + 1, nf - 1);
+        const size_t plane = (size_t)v * nf * nf * nf;
+        const size_t r00 = plane + ((size_t)z0 * nf + y0) * nf, r10 = plane + ((size_t)z0 * nf + y1) * nf;
+        const size_t r01 = plane + ((size_t)z1 * nf + y0) * nf, r11 = plane + ((size_t)z1 * nf + y1) * nf;
+        // fine columns 2X .. 2X+2VEC+1 (the last two for the right neighbour), clamped
+        constexpr int W = 2 * VEC + 2;
+        float f00[W], f10[W], f01[W], f11[W];
+        const int fx = 2 * X;
+        if (VEC > 1) {
+            load_run<DT, 2 * VEC>(A.src, r00 + fx, f00);
+            load_run<DT, 2 * VEC>(A.src, r10 + fx, f10);
+            load_run<DT, 2 * VEC>(A.src, r01 + fx, f01);
+            load_run<DT, 2 * VEC>(A.src, r11 + fx, f11);
+            const int e0 = right ? fx + 2 * VEC : fx + 2 * VEC - 2;    // even: a 2-run stays in the row
+            load_run<DT, 2>(A.src, r00 + e0, f00 + 2 * VEC);
+            load_run<DT, 2>(A.src, r10 + e0, f10 + 2 * VEC);
+            load_run<DT, 2>(A.src, r01 + e0, f01 + 2 * VEC);
+            load_run<DT, 2>(A.src, r11 + e0, f11 + 2 * VEC);
+        } else {
+            // fine columns of X, then of the right neighbour X+1 (of X itself at the edge)
+            const int g = right ? fx + 2 : fx;
+            const int cc[4] = {fx, min(fx + 1, nf - 1), g, min(g + 1, nf - 1)};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                load_run<DT, 1>(A.src, r00 + cc[q], f00 + q);
+                load_run<DT, 1>(A.src, r10 + cc[q], f10 + q);
+                load_run<DT, 1>(A.src, r01 + cc[q], f01 + q);
+                load_run<DT, 1>(A.src, r11 + cc[q], f11 + q);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q <= VEC; ++q) {
+            const int a = 2 * q, b = 2 * q + 1;
+            const float s0 = __fadd_rn(__fadd_rn(f00[a], f00[b]), __fadd_rn(f10[a], f10[b]));
+            const float s1 = __fadd_rn(__fadd_rn(f01[a], f01[b]), __fadd_rn(f11[a], f11[b]));
+            val[q] = to_stored<DT>(__fmul_rn(__fadd_rn(s0, s1), 0.125f));
+        }
+    }
+}
+
+// One block per (brick row (by, bz), variable). Thread t owns the VEC columns
+// X = VEC t .. VEC t + VEC-1 (striding over the level when it is wider than
+// the block) and also reads column X+VEC, the right element of its last pair.
+// The block streams the (up to) 9 x 9 x-rows y in [8by, 8by+8], z in
+// [8bz, 8bz+8]: it writes the 8 x 8 rows it owns (cells and x-pairs) and folds
+// every row, apron rows included, with the right column, into NaN-ignoring
+// min/max kept separately for the four (y half, z half) sub-brick rows: half
+// 0 is rows 0..4 of the brick, half 1 rows 4..8 (row 4 is in both). Lanes are
+// then reduced with shuffles: 4/VEC lanes make a sub-brick of edge 4 (x in
+// 4s..min(4s+4, n-1)), two sub-bricks a brick (x in 8b..min(8b+8, n-1)).
+template <int DT, int MODE, int SRC, int VEC>
 __global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
-    extern __shared__ float s_col[];          // [2][n]: column min, column max
+    constexpr int G = kSub / VEC;                       // lanes per sub-brick column
+    constexpr int kBatch = MODE == 0 ? 3 : 1;          // rows whose loads are issued together
     const int n = A.n;
     const int nb = (n + kBrick - 1) / kBrick;
+    const int nsb = (n + kSub - 1) / kSub;
+    const int ncol = (n + VEC - 1) / VEC;
     const int by = blockIdx.x % nb, bz = blockIdx.x / nb, v = blockIdx.y;
-    const int lane = threadIdx.x & 31;
     const float qnan = __int_as_float(0x7fffffff);
-    for (int xc = 0; xc < n; xc += blockDim.x) {
-        const int x = xc + threadIdx.x;
-        const bool valid = x < n;
-        float mn = qnan, mx = qnan;
+    for (int c0 = 0; c0 < ncol; c0 += blockDim.x) {
+        const int t = c0 + threadIdx.x;
+        const bool valid = t < ncol;
+        const int X = t * VEC;
+        float mn[4] = {qnan, qnan, qnan, qnan}, mx[4] = {qnan, qnan, qnan, qnan};
         for (int dz = 0; dz <= kBrick; ++dz) {
             const int z = bz * kBrick + dz;
             if (z >= n) break;
-            // Ingest: issue the (up to) 9 row loads of this z-slice before using
-            // any of them (9 loads in flight per thread). LOD: one row at a time
-            // (each value already costs 8 loads).
-            constexpr int kAhead = MODE == 0 ? kBrick + 1 : 1;
-            for (int dy0 = 0; dy0 <= kBrick; dy0 += kAhead) {
-                float val[kAhead];
+            float ymn[2] = {qnan, qnan}, ymx[2] = {qnan, qnan};   // this z-slice, y halves 0 and 1
 #pragma unroll
-                for (int j = 0; j < kAhead; ++j) {
+            for (int dy0 = 0; dy0 <= kBrick; dy0 += kBatch) {
+                float val[kBatch][VEC + 1];
+#pragma unroll
+                for (int j = 0; j < kBatch; ++j) {
                     const int y = by * kBrick + dy0 + j;
-                    val[j] = (valid && dy0 + j <= kBrick && y < n) ? produce<DT, MODE>(A, x, y, z, v) : 0.0f;
+                    if (valid && dy0 + j <= kBrick && y < n) produce_run<DT, MODE, SRC, VEC>(A, X, y, z, v, val[j]);
                 }
 #pragma unroll
-                for (int j = 0; j < kAhead; ++j) {
+                for (int j = 0; j < kBatch; ++j) {
                     const int dy = dy0 + j;
                     const int y = by * kBrick + dy;
-                    if (dy > kBrick || y >= n) break;
-                    if (valid) {
-                        mn = fminf(mn, val[j]);
-                        mx = fmaxf(mx, val[j]);
-                    }
-                    if (dy < kBrick && dz < kBrick) {
-                        float right = __shfl_down_sync(0xffffffffu, val[j], 1);
-                        if (valid) {
-                            if (x == n - 1) right = val[j];
-                            else if (lane == 31) right = produce<DT, MODE>(A, x + 1, y, z, v);
-                            const size_t i = (((size_t)v * n + z) * n + y) * n + x;
-                            store_cell<DT>(A.cells, i, val[j]);
-                            store_pair<DT>(A.pairs, i, val[j], right);
-                        }
-                    }
+                    if (!valid || dy > kBrick || y >= n) continue;
+                    float rmn = val[j][0], rmx = val[j][0];
+#pragma unroll
+                    for (int q = 1; q <= VEC; ++q) fold(rmn, rmx, val[j][q], val[j][q]);
+                    if (dy <= kSub) fold(ymn[0], ymx[0], rmn, rmx);
+                    if (dy >= kSub) fold(ymn[1], ymx[1], rmn, rmx);
+                    if (dy < kBrick && dz < kBrick)
+                        store_run<DT, VEC>(A.cells, A.pairs, (((size_t)v * n + z) * n + y) * n + X, val[j]);
+                }
+            }
+            if (dz <= kSub) {
+                fold(mn[0], mx[0], ymn[0], ymx[0]);
+                fold(mn[1], mx[1], ymn[1], ymx[1]);
+            }
+            if (dz >= kSub) {
+                fold(mn[2], mx[2], ymn[0], ymx[0]);
+                fold(mn[3], mx[3], ymn[1], ymx[1]);
+            }
+        }
+        // sub-bricks: reduce over the G lanes of a sub-brick column
+#pragma unroll
+        for (int m = 1; m < G; m <<= 1)
+#pragma unroll
+            for (int h = 0; h < 4; ++h)
+                fold(mn[h], mx[h], __shfl_xor_sync(0xffffffffu, mn[h], m), __shfl_xor_sync(0xffffffffu, mx[h], m));
+        const int sx = t / G;
+        if (valid && t % G == 0) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int sy = 2 * by + (h & 1), sz = 2 * bz + (h >> 1);
+                if (sy < nsb && sz < nsb && sx < nsb) {
+                    const size_t sb = ((size_t)sz * nsb + sy) * nsb + sx;
+                    A.sbmin[sb * A.nvars + v] = mn[h];
+                    A.sbmax[sb * A.nvars + v] = mx[h];
                 }
             }
         }
-        if (valid) {
-            s_col[x] = mn;
-            s_col[n + x] = mx;
+        // bricks: all four halves of two neighbouring sub-brick columns
+        float bmn = mn[0], bmx = mx[0];
+#pragma unroll
+        for (int h = 1; h < 4; ++h) fold(bmn, bmx, mn[h], mx[h]);
+        fold(bmn, bmx, __shfl_xor_sync(0xffffffffu, bmn, G), __shfl_xor_sync(0xffffffffu, bmx, G));
+        const int bx = t / (2 * G);
+        if (valid && t % (2 * G) == 0 && bx < nb) {
+            const size_t b = ((size_t)bz * nb + by) * nb + bx;
+            A.bmin[b * A.nvars + v] = bmn;
+            A.bmax[b * A.nvars + v] = bmx;
         }
-    }
-    __syncthreads();
-    for (int bx = threadIdx.x; bx < nb; bx += blockDim.x) {
-        const int x0 = bx * kBrick, x1 = min(x0 + kBrick, n - 1);
-        float mn = qnan, mx = qnan;
-        for (int x = x0; x <= x1; ++x) {
-            mn = fminf(mn, s_col[x]);
-            mx = fmaxf(mx, s_col[n + x]);
-        }
-        const size_t b = ((size_t)bz * nb + by) * nb + bx;
-        A.bmin[b * A.nvars + v] = mn;
-        A.bmax[b * A.nvars + v] = mx;
     }
 }
 
@@ -155,34 +285,36 @@ __device__ __forceinline__ int level_of(const ClassifyArgs& C, size_t g, size_t&
     return l;
 }
 
-// One thread per brick of every level: shell test of the widened box and brush
-// test with the rounding margin d = max(|min|, |max|) * 2^-20 + 2^-120. Writes
-// the active bitmask (one ballot word per warp; level ranges start on
-// multiples of 32) and counts, per restricted variable, the in-shell bricks
-// that pass that variable alone (a selectivity hint for the render).
+// One thread per brick of every entry (8^3 bricks and 4^3 sub-bricks of every
+// level): shell test of the widened box and brush test with the rounding
+// margin d = max(|min|, |max|) * 2^-20 + 2^-120. Writes the active bitmask
+// (one ballot word per warp; entry ranges start on multiples of 32) and, for
+// the 8^3 bricks, counts per restricted variable the in-shell bricks that pass
+// that variable alone (a selectivity hint for the render).
 __global__ void k_classify(ClassifyArgs C) {
     const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     size_t b = 0;
     const int l = level_of(C, g, b);
     const ClassifyLevel& L = C.lv[l];
-    const int nb = (L.n + kBrick - 1) / kBrick;
+    const int nb = (L.n + L.bs - 1) / L.bs;
     const size_t nbricks = (size_t)nb * nb * nb;
     const bool in_range = g < C.total;
     const bool valid = in_range && b < nbricks;
     bool act = false;
     unsigned pass_bits = 0;
     if (valid)
-        act = classify_brick(b, nb, L.sc, C.rin2, C.rout2, C.brush, C.nvars, L.bmin, L.bmax, pass_bits);
+        act = classify_brick(b, nb, L.bs, L.sc, C.rin2, C.rout2, C.brush, C.nvars, L.bmin, L.bmax, pass_bits);
     const unsigned word = __ballot_sync(0xffffffffu, act);
     if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.active[b >> 5] = word;
+    if (L.pass_count == nullptr) return;        // uniform per warp: entry ranges are warp-aligned
     for (int v = 0; v < C.nvars; ++v) {
         const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
         if (lane == 0 && cnt) atomicAdd(&L.pass_count[v], cnt);
     }
 }
 
-// Skippable = this brick and its existing 26 neighbours are inactive.
+// Skippable = this 8^3 brick and its existing 26 neighbours are inactive.
 __global__ void k_skippable(ClassifyArgs C) {
     const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -191,14 +323,14 @@ __global__ void k_skippable(ClassifyArgs C) {
     const ClassifyLevel& L = C.lv[l];
     const int nb = (L.n + kBrick - 1) / kBrick;
     const size_t nbricks = (size_t)nb * nb * nb;
-    const bool in_range = g < C.total;
+    const bool in_range = g < C.total_brick;
     const bool valid = in_range && b < nbricks;
     const bool s = valid && skippable_brick(b, nb, L.active);
     const unsigned word = __ballot_sync(0xffffffffu, s);
     if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.skippable[b >> 5] = word;
 }
 
-// Ordered compaction of the active brick ids, one block of 1024 threads per
+// Ordered compaction of the active 8^3 brick ids, one block of 1024 threads per
 // level: each thread owns a contiguous run of bitmask words; a block-wide
 // exclusive scan of the per-thread popcounts gives every thread its offset.
 __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
@@ -234,23 +366,37 @@ __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
 
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+template <int DT, int MODE, int SRC, int VEC>
+void launch_rows_t(const RowsArgs& a, dim3 grid, cudaStream_t stream) {
+    const int ncol = (a.n + VEC - 1) / VEC;
+    // one thread per column run up to kRowThreads (narrow levels use narrow blocks)
+    const int threads = min(kRowThreads, max(32, (ncol + 31) / 32 * 32));
+    k_rows<DT, MODE, SRC, VEC><<<grid, threads, 0, stream>>>(a);
+}
+
 template <int MODE>
 cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
+    if (a.n < 2 || a.n > kMaxRowsEdge) return cudaErrorInvalidValue;
     const int nb = (a.n + kBrick - 1) / kBrick;
     dim3 grid((unsigned)(nb * nb), (unsigned)a.nvars);
-    const size_t smem = sizeof(float) * 2 * (size_t)a.n;
-    if (smem > 48 * 1024) {
-        cudaError_t e = dtype == kF16
-            ? cudaFuncSetAttribute(k_rows<kF16, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : cudaFuncSetAttribute(k_rows<kF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    // 4-column runs when every run is aligned: n % 4 == 0, a 16-byte aligned
+    // source (ingest) or an even fine edge (LOD; n % 4 == 0 makes it 8k).
+    bool vec = a.n % 4 == 0;
+    if (MODE == 0) vec = vec && ((uintptr_t)a.src % 16 == 0);
+    else vec = vec && a.n_src == 2 * a.n;
+    if (MODE == 0) {
+        const bool s16 = a.src_dtype == kF16;
+        if (dtype == kF16) {
+            if (vec) { if (s16) launch_rows_t<kF16, 0, kF16, 4>(a, grid, stream); else launch_rows_t<kF16, 0, kF32, 4>(a, grid, stream); }
+            else     { if (s16) launch_rows_t<kF16, 0, kF16, 1>(a, grid, stream); else launch_rows_t<kF16, 0, kF32, 1>(a, grid, stream); }
+        } else {
+            if (vec) { if (s16) launch_rows_t<kF32, 0, kF16, 4>(a, grid, stream); else launch_rows_t<kF32, 0, kF32, 4>(a, grid, stream); }
+            else     { if (s16) launch_rows_t<kF32, 0, kF16, 1>(a, grid, stream); else launch_rows_t<kF32, 0, kF32, 1>(a, grid, stream); }
+        }
+    } else {
+        if (dtype == kF16) { if (vec) launch_rows_t<kF16, 1, kF16, 4>(a, grid, stream); else launch_rows_t<kF16, 1, kF16, 1>(a, grid, stream); }
+        else               { if (vec) launch_rows_t<kF32, 1, kF32, 4>(a, grid, stream); else launch_rows_t<kF32, 1, kF32, 1>(a, grid, stream); }
     }
-    // one thread per x column up to kRowThreads (narrow levels use narrow blocks)
-    const int threads = min(kRowThreads, max(32, (a.n + 31) / 32 * 32));
-    if (dtype == kF16)
-        k_rows<kF16, MODE><<<grid, threads, smem, stream>>>(a);
-    else
-        k_rows<kF32, MODE><<<grid, threads, smem, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -258,7 +404,8 @@ cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
 }  // namespace
 
 cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pairs, int dtype, int n,
-                          int nvars, float* bmin, float* bmax, cudaStream_t stream) {
+                          int nvars, float* bmin, float* bmax, float* sbmin, float* sbmax,
+                          cudaStream_t stream) {
     RowsArgs a{};
     a.src = src;
     a.src_dtype = src_dtype;
@@ -268,11 +415,13 @@ cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pai
     a.nvars = nvars;
     a.bmin = bmin;
     a.bmax = bmax;
+    a.sbmin = sbmin;
+    a.sbmax = sbmax;
     return launch_rows<0>(a, dtype, stream);
 }
 
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
-                       float* bmin, float* bmax, cudaStream_t stream) {
+                       float* bmin, float* bmax, float* sbmin, float* sbmax, cudaStream_t stream) {
     RowsArgs a{};
     a.src = fine;
     a.n_src = n_fine;
@@ -282,6 +431,8 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
     a.nvars = nvars;
     a.bmin = bmin;
     a.bmax = bmax;
+    a.sbmin = sbmin;
+    a.sbmax = sbmax;
     return launch_rows<1>(a, dtype, stream);
 }
 
@@ -289,21 +440,25 @@ cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
     size_t total = 0;
     for (int l = 0; l < c.nlev; ++l) {
         ClassifyLevel& L = c.lv[l];
-        const int nb = (L.n + kBrick - 1) / kBrick;
+        if (L.bs != (l < c.nbrick ? kBrick : kSub)) return cudaErrorInvalidValue;
+        const int nb = (L.n + L.bs - 1) / L.bs;
         L.first = total;
         L.sc = 2.0f / (float)L.n;
-        total += ((size_t)nb * nb * nb + 31) / 32 * 32;      // level ranges start on warp boundaries
-        cudaError_t e = cudaMemsetAsync(L.pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
-        if (e != cudaSuccess) return e;
+        total += ((size_t)nb * nb * nb + 31) / 32 * 32;      // entry ranges start on warp boundaries
+        if (l + 1 == c.nbrick) c.total_brick = total;
+        if (L.pass_count) {
+            cudaError_t e = cudaMemsetAsync(L.pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
+            if (e != cudaSuccess) return e;
+        }
     }
     c.total = total;
     k_classify<<<blocks_for(total, 256), 256, 0, stream>>>(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_skippable<<<blocks_for(total, 256), 256, 0, stream>>>(c);
+    k_skippable<<<blocks_for(c.total_brick, 256), 256, 0, stream>>>(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_compact<<<c.nlev, 1024, 0, stream>>>(c);
+    k_compact<<<c.nbrick, 1024, 0, stream>>>(c);
     count_launches(3);
     return cudaGetLastError();
 }

@@ -104,6 +104,7 @@ _SIGS = {
     "raypc_export_volume": [_P, _I, _I, _P, _P],
     "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
     "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
+    "raypc_get_sub_bricks": [_P, _I, _I, _P, _P, _P, _P],
     "raypc_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "raypc_batch_destroy": [_P],
     "raypc_render_batch": [_P, ctypes.POINTER(View), _I, _P],
@@ -358,6 +359,19 @@ class Volume:
               ctypes.c_void_p(cnt.data_ptr()), _stream(stream))
         n_active = int(cnt.item())
         return act, skp, lst[:n_active]
+
+    def sub_bricks(self, lod: int = 0, classify: bool = True, stream=None):
+        """4^3 sub-brick (min, max [nsb,nsb,nsb,nvars], active_bits int32 or None) as device tensors."""
+        info = self.info(lod)
+        nsb = (info.n + 3) // 4
+        dev = torch.device("cuda", self.ctx.device)
+        mn = torch.empty((nsb, nsb, nsb, info.nvars), dtype=torch.float32, device=dev)
+        mx = torch.empty_like(mn)
+        act = torch.empty((nsb ** 3 + 31) // 32, dtype=torch.int32, device=dev) if classify else None
+        _call("raypc_get_sub_bricks", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(mn.data_ptr()),
+              ctypes.c_void_p(mx.data_ptr()), ctypes.c_void_p(act.data_ptr() if classify else None),
+              _stream(stream))
+        return mn, mx, act
 
 
 def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=None, active_mask: int = 0,

@@ -68,7 +68,7 @@ def bits(rp, words, nbits):
 # ingest, LOD, bricks, classification
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("store", ["f32", "f16"])
-@pytest.mark.parametrize("n,nvars", [(37, 6), (16, 3), (2, 1)])
+@pytest.mark.parametrize("n,nvars", [(37, 6), (16, 3), (2, 1), (4, 2), (68, 2)])
 def test_ingest_roundtrip(ctx, store, n, nvars):
     vol = synth.make_shell_volume(n, seed=7)[:nvars].contiguous()
     v = ctx.load_volume(vol.cuda(), store=store)
@@ -80,12 +80,29 @@ def test_ingest_roundtrip(ctx, store, n, nvars):
     # host source path gives the same stored bits
     v2 = ctx.load_volume(vol, store=store)
     assert torch.equal(v2.export().cpu(), got)
+    # an FP16 source, and a source that is not 16-byte aligned (scalar column runs)
+    v3 = ctx.load_volume(vol.half().cuda(), store=store)
+    assert torch.equal(v3.export().cpu(), synth.to_storage(vol.half().float(), store))
+    buf = torch.empty(vol.numel() + 1, device="cuda")
+    shifted = buf[1:].view(vol.shape)
+    shifted.copy_(vol.cuda())
+    v4 = ctx.load_volume(shifted, store=store)
+    assert torch.equal(v4.export().cpu(), got)
+    for w in (v3, v4):
+        mn, mx = w.bricks()
+        omn, omx = oracle.brick_minmax(w.export().float().cpu().numpy())
+        assert np.array_equal(mn.cpu().numpy(), omn) and np.array_equal(mx.cpu().numpy(), omx)
+        smn, smx, _ = w.sub_bricks(classify=False)
+        omn4, omx4 = oracle.brick_minmax(w.export().float().cpu().numpy(), 4)
+        assert np.array_equal(smn.cpu().numpy(), omn4) and np.array_equal(smx.cpu().numpy(), omx4)
     v.free()
     v2.free()
+    v3.free()
+    v4.free()
 
 
 @pytest.mark.parametrize("store", ["f32", "f16"])
-@pytest.mark.parametrize("n", [40, 33])
+@pytest.mark.parametrize("n", [40, 33, 64, 26])
 def test_lod_and_bricks_bit_exact(rp, ctx, store, n):
     vol = synth.make_shell_volume(n, seed=2)
     v = load(ctx, vol, store, n_lod=2)
@@ -96,6 +113,9 @@ def test_lod_and_bricks_bit_exact(rp, ctx, store, n):
         mn, mx = v.bricks(lod)
         omn, omx = oracle.brick_minmax(levels[lod])
         assert np.array_equal(mn.cpu().numpy(), omn) and np.array_equal(mx.cpu().numpy(), omx)
+        smn, smx, _ = v.sub_bricks(lod, classify=False)
+        omn4, omx4 = oracle.brick_minmax(levels[lod], 4)
+        assert np.array_equal(smn.cpu().numpy(), omn4) and np.array_equal(smx.cpu().numpy(), omx4), lod
     v.free()
 
 
@@ -120,6 +140,10 @@ def test_classification_bit_exact(rp, ctx, brush_name):
         assert np.array_equal(bits(rp, act, nbk), oact.reshape(-1))
         assert np.array_equal(bits(rp, skp, nbk), oskp.reshape(-1))
         assert np.array_equal(lst.cpu().numpy(), np.flatnonzero(oact.reshape(-1)).astype(np.int32))
+        _, _, sact = v.sub_bricks(lod)
+        omn4, omx4 = oracle.brick_minmax(levels[lod], 4)
+        oact4, _ = oracle.classify(omn4, omx4, m, R_IN, R_OUT, b.lo, b.hi, b.active_mask, bs=4)
+        assert np.array_equal(bits(rp, sact, oact4.size), oact4.reshape(-1)), lod
     if brush_name == "empty":
         assert lst.numel() == 0
     v.free()
@@ -162,10 +186,10 @@ def test_render_matches_oracle(ctx, n, store, bname, cvar, w, h, camkw):
     brush = synth.make_brush(vol, bname)
     tf = synth.make_tf(vol, cvar)
     cam = synth.orbit_camera(**camkw)
-    for ert in (False, True):
-        img, cnt, ref, rcnt = render_pair(ctx, vol, store, brush, tf, cam, w, h, ert=ert)
+    for ert, skip in ((False, True), (False, False), (True, True)):
+        img, cnt, ref, rcnt = render_pair(ctx, vol, store, brush, tf, cam, w, h, ert=ert, skip=skip)
         err = np.abs(img - ref)
-        assert err.max() <= TOL[store], (ert, err.max())
+        assert err.max() <= TOL[store], (ert, skip, err.max())
         if not ert:
             assert np.array_equal(cnt, rcnt)        # every sample decision identical
         else:
@@ -262,6 +286,12 @@ def test_render_edge_cases(ctx, rp):
     inside = synth.Camera((0.0, 0.1, 0.8), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.6)
     img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, inside, 33, 17, ert=False)
     assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # axis-aligned rays (the centre pixel of an odd image looks straight down -z;
+    # its x and y direction components are exactly 0), with and without jumps
+    axis = synth.Camera((0.0, 0.0, 2.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    for skip in (True, False):
+        img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, axis, 31, 31, ert=False, skip=skip)
+        assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
     # smallest grid, one variable
     v1 = torch.rand(1, 2, 2, 2, generator=torch.Generator().manual_seed(0))
     b1 = synth.Brush(np.array([0.2], np.float32), np.array([0.9], np.float32), 1)
