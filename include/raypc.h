@@ -183,7 +183,9 @@ raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lo
  * active iff its sample box (widened by 2^-10) meets the shell and, for every
  * restricted v, max_v + d >= lo[v] and min_v - d <= hi[v] with
  * d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
- * rounding); skippable iff it and its 26 neighbours are inactive. The 4^3
+ * rounding), except that a variable with max(|min_v|, |max_v|) > 2^126 never
+ * deactivates a brick (its interpolation can overflow to an infinite value);
+ * skippable iff it and its 26 neighbours are inactive. The 4^3
  * sub-bricks are classified by the same rule. Requires raypc_build_bricks. */
 raypc_status raypc_set_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
                              uint32_t active_mask, void *stream);

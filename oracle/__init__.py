@@ -58,6 +58,7 @@ def _load():
             lib.oracle_brick_minmax.argtypes = [P, i32, i32, i32, P, P]
             lib.oracle_classify.argtypes = [P, P, i32, i32, i32, f32, f32, P, P, u32, P, P]
             lib.oracle_lod_mean.argtypes = [P, i32, i32, P]
+            lib.oracle_cell_classes.argtypes = [P, i32, i32, P, P, u32, P]
             lib.oracle_shell_bounds.argtypes = [i32, f32, f32, P, P]
             lib.oracle_histogram.argtypes = [P, i32, i32, f32, f32, P, P, u32, i32,
                                              P, i32, i32, P, P, P]
@@ -113,6 +114,20 @@ def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask, bs: int = BRICK):
     _load().oracle_classify(_ptr(bmin), _ptr(bmax), n, V, int(bs), np.float32(r_in), np.float32(r_out),
                             _ptr(lo), _ptr(hi), int(active_mask) & 0xFFFFFFFF, _ptr(act), _ptr(skp))
     return act, skp
+
+
+CELL_FAIL = 0x8000
+
+
+def cell_classes(vol, lo, hi, active_mask) -> np.ndarray:
+    """Per interpolation cell (lower corner x,y,z): bit v = variable v must be interpolated,
+    bit 15 = some restricted variable fails for every sample -> uint16 [n][n][n] ([z][y][x])."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    out = np.empty((n, n, n), np.uint16)
+    _load().oracle_cell_classes(_ptr(v), n, V, _ptr(_f32(lo)), _ptr(_f32(hi)),
+                                int(active_mask) & 0xFFFFFFFF, _ptr(out))
+    return out
 
 
 def lod_mean(vol) -> np.ndarray:

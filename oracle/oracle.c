@@ -10,7 +10,9 @@
  *
  * What it computes, plainly and slowly:
  *   - brick min/max per variable over each 8^3 brick plus its +1 apron;
- *   - brush classification of bricks (shell intersection and brush box);
+ *   - brush classification of bricks (shell intersection and brush box)
+ *     and of interpolation cells (every sample fails / passes / must be
+ *     interpolated);
  *   - the 2x2x2 mean used for the coarser levels of detail (Section 2.1);
  *   - front-to-back emission-absorption ray marching where a sample is
  *     discarded when any restricted variable lies outside its brush bounds
@@ -85,8 +87,10 @@ void oracle_brick_minmax(const float *vol, int n, int nvars, int bs, float *out_
 /* d = max(|min_v|, |max_v|) * 2^-20 + 2^-120. The widening d covers     */
 /* the rounding of the FP32 trilinear interpolation (at most about      */
 /* 10 * 2^-24 * max|corner|), so no sample that passes the brush can    */
-/* lie in an inactive brick. A brick is skippable when it and all its   */
-/* existing 26 neighbours are inactive.                                 */
+/* lie in an inactive brick. A variable with max(|min_v|, |max_v|) >    */
+/* 2^126 never deactivates a brick: a corner difference can overflow    */
+/* there and the interpolated value can be infinite. A brick is         */
+/* skippable when it and all its existing 26 neighbours are inactive.   */
 /* Output: active[b], skippable[b] as bytes 0/1, b = (bz*nb+by)*nb+bx.  */
 /* ------------------------------------------------------------------ */
 static void brick_box_axis(int b, int nb, int n, int BRICK, float *lo, float *hi) {
@@ -124,6 +128,7 @@ void oracle_classify(const float *bmin, const float *bmax, int n, int nvars, int
                     if (!((active_mask >> v) & 1u)) continue;
                     float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
                     float m = fmaxf(fabsf(mn), fabsf(mx));
+                    if (m > 0x1p126f) continue;
                     float d = fmaf(m, 0x1p-20f, 0x1p-120f);
                     float up = mx + d, dn = mn - d;
                     if (!(up >= lo[v] && dn <= hi[v])) act = 0;
@@ -142,6 +147,56 @@ void oracle_classify(const float *bmin, const float *bmax, int n, int nvars, int
                             if (active[((size_t)z * nb + y) * nb + x]) s = 0;
                         }
                 skippable[((size_t)bz * nb + by) * nb + bx] = (uint8_t)s;
+            }
+}
+
+/* ------------------------------------------------------------------ */
+/* Cell classes under a brush (FP32 decisions). For the interpolation   */
+/* cell with lower corner (x,y,z), 0 <= x,y,z <= n-2, and each          */
+/* restricted variable v, over its 8 corner values:                     */
+/*   FAIL   if a corner is NaN (the trilinear value is NaN), or, with    */
+/*          m = max(|min|,|max|) <= 2^126 and d as for bricks,          */
+/*          max + d < lo_v or min - d > hi_v (every value fails v);     */
+/*   INSIDE if m <= 2^126, min - d >= lo_v and max + d <= hi_v (every   */
+/*          value passes v);                                            */
+/*   MIXED  otherwise (the value must be interpolated).                 */
+/* The 2^126 bound keeps the FP32 interpolation free of overflow, and d */
+/* covers its rounding (at most about 9 * 2^-24 * m), so FAIL and       */
+/* INSIDE are exact statements about the FP32 trilinear value of every  */
+/* sample whose lower interpolation corner is (x,y,z).                  */
+/* Output word per cell: bit v set iff v is MIXED, bit 15 set iff some  */
+/* restricted v is FAIL; [z][y][x] over n^3 cells, 0 where an index is  */
+/* n-1 (no such cell).                                                   */
+/* ------------------------------------------------------------------ */
+void oracle_cell_classes(const float *vol, int n, int nvars, const float *lo, const float *hi,
+                         uint32_t active_mask, uint16_t *out) {
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                uint16_t word = 0;
+                if (x < n - 1 && y < n - 1 && z < n - 1) {
+                    for (int v = 0; v < nvars; v++) {
+                        if (!((active_mask >> v) & 1u)) continue;
+                        int has_nan = 0;
+                        float mn = INFINITY, mx = -INFINITY;
+                        for (int c = 0; c < 8; c++) {
+                            float a = val(vol, n, v, x + (c & 1), y + ((c >> 1) & 1), z + (c >> 2));
+                            if (a != a) has_nan = 1;
+                            else {
+                                if (a < mn) mn = a;
+                                if (a > mx) mx = a;
+                            }
+                        }
+                        if (has_nan) { word |= 0x8000u; continue; }
+                        float m = fmaxf(fabsf(mn), fabsf(mx));
+                        if (m > 0x1p126f) { word |= (uint16_t)(1u << v); continue; }
+                        float d = fmaf(m, 0x1p-20f, 0x1p-120f);
+                        float up = mx + d, dn = mn - d;
+                        if (up < lo[v] || dn > hi[v]) word |= 0x8000u;
+                        else if (!(dn >= lo[v] && up <= hi[v])) word |= (uint16_t)(1u << v);
+                    }
+                }
+                out[((size_t)z * n + y) * n + x] = word;
             }
 }
 

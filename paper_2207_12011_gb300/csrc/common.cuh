@@ -215,7 +215,9 @@ __device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, int bs, 
 // axis (sc = 2/n): active iff its widened sample box meets the shell and, for every
 // restricted v, max_v + d >= lo_v and min_v - d <= hi_v with
 // d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
-// rounding). pass_bits gets bit v set for each restricted variable the brick
+// rounding). A variable with max(|min_v|, |max_v|) > 2^126 never deactivates
+// a brick (a corner difference can overflow and the interpolated value be
+// infinite). pass_bits gets bit v set for each restricted variable the brick
 // passes on its own (only meaningful when the box meets the shell).
 __device__ __forceinline__ bool classify_brick(size_t b, int nb, int bs, float sc, float rin2, float rout2,
                                                const BrushArgs& brush, int nvars, const float* bmin,
@@ -239,7 +241,7 @@ __device__ __forceinline__ bool classify_brick(size_t b, int nb, int bs, float s
         const float mn = bmin[b * nvars + v], mx = bmax[b * nvars + v];
         const float m = fmaxf(fabsf(mn), fabsf(mx));
         const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-        const bool ok = (__fadd_rn(mx, d) >= brush.lo[v]) && (__fsub_rn(mn, d) <= brush.hi[v]);
+        const bool ok = m > 0x1p126f || ((__fadd_rn(mx, d) >= brush.lo[v]) && (__fsub_rn(mn, d) <= brush.hi[v]));
         if (ok) pass_bits |= 1u << v;
         all = all && ok;
     }

@@ -298,6 +298,25 @@ def test_render_edge_cases(ctx, rp):
     tf1 = synth.TransferFunction(synth.tf_ramp(), 0, 0.0, 1.0)
     img, cnt, ref, rcnt = render_pair(ctx, v1, "f32", b1, tf1, synth.orbit_camera(0, 0, 3.0), 20, 20, ert=False)
     assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # one x-row of corners jumps from -3e38 to 3e38: the FP32 interpolation overflows to +inf,
+    # which passes an upper-open brush above every corner; the bricks there must stay active
+    big = torch.zeros(1, 16, 16, 16)
+    big[0, 8, 8, :8] = -3e38
+    big[0, 8, 8, 8:] = 3e38
+    bb = synth.Brush(np.array([3.2e38], np.float32), np.array([np.inf], np.float32), 1)
+    tfb = synth.TransferFunction(synth.tf_ramp(), 0, 0.0, 1.0)
+    camb = synth.Camera((0.01, 0.01, 3.0), (0.01, 0.01, 0.0), (0.0, 1.0, 0.0), 0.01)
+    vb = ctx.load_volume(big.cuda(), store="f32", r_in=0.0)      # no core: the rays cross the centre
+    vb.build_bricks(n_lod=0)
+    vb.set_brush(bb.lo, bb.hi, bb.active_mask)
+    vb.set_tf(tfb.rgbs, tfb.color_var, tfb.v_lo, tfb.v_hi)
+    _, rcnt = oracle.render(big.numpy(), 0.0, R_OUT, camb.as_array(), 3, 3, 1.0 / 16, bb.lo, bb.hi, 1,
+                            tfb.rgbs, 0, 0.0, 1.0, ert=False)
+    assert rcnt[..., 1].sum() > 0
+    for skip in (True, False):
+        _, cnt = vb.render(camb, 3, 3, ert=False, skip=skip, counts=True)
+        assert np.array_equal(cnt.cpu().numpy().astype(np.uint32), rcnt)
+    vb.free()
     # invalid arguments are rejected on the host
     v = load(ctx, vol, "f32", brush=brush, tf=tf)
     with pytest.raises(rp.RaypcError):

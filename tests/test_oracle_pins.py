@@ -586,3 +586,127 @@ def test_lod_mean_brute_force():
     pad = np.concatenate([pad, pad[:, :, :, -1:]], axis=3)
     want = pad.reshape(1, 3, 2, 3, 2, 3, 2).astype(np.float64).mean(axis=(2, 4, 6))
     assert np.array_equal(got.astype(np.float64), want)
+
+def test_classify_keeps_bricks_whose_interpolation_can_overflow():
+    """One x-row of corners jumps from -3e38 to 3e38, the rest is 0: the FP32
+    corner difference of that row overflows, the x-lerp gives +inf, and the y-
+    and z-lerps against finite neighbours carry +inf through. The sample passes
+    an upper-open brush whose lower bound exceeds every corner, so the bricks
+    holding that row must stay active, and the render keeps such samples."""
+    n = 16
+    vol = np.zeros((1, n, n, n), np.float32)
+    vol[0, n // 2, n // 2, : n // 2] = -3e38
+    vol[0, n // 2, n // 2, n // 2:] = 3e38
+    lo, hi = np.float32([3.2e38]), np.float32([np.inf])
+    mn, mx = oracle.brick_minmax(vol, 4)
+    act, _ = oracle.classify(mn, mx, n, 0.0, R_OUT, lo, hi, 1, bs=4)
+    assert act[2, 2, 1] == 1 and act[0, 0, 0] == 0    # holds the jump (kept) / only zeros (culled)
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, 3] = 1.0
+    cam = np.float32([0.01, 0.01, 3.0, 0.01, 0.01, 0, 0, 1, 0, 0.01])
+    _, cnt = oracle.render(vol, 0.0, R_OUT, cam, 3, 3, 1.0 / n, lo, hi, 1, tf, 0, 0.0, 1.0, ert=False)
+    assert cnt[..., 1].sum() > 0                       # samples do pass via +inf
+
+
+# ----------------------------------------------------------------------------
+# cell classes: every sample of a cell fails / passes / must be interpolated
+# ----------------------------------------------------------------------------
+FAIL = oracle.CELL_FAIL
+
+
+def test_cell_classes_margin_closed_form():
+    """Constant field 1: d = 2^-20, so the pass box of every value is exactly
+    [1 - 2^-20, 1 + 2^-20]; bounds on either side of its ends decide the class."""
+    v = np.ones((1, 4, 4, 4), np.float32)
+    e, u = 2.0 ** -20, 2.0 ** -23
+    cases = [
+        ((1 - e, 2.0), 0),                 # min - d == lo: inside
+        ((1 - e + u / 2, 2.0), 1),         # just above min - d: must interpolate
+        ((0.0, 1 + e), 0),                 # max + d == hi: inside
+        ((0.0, 1 + e - u), 1),
+        ((1 + e, 3.0), 1),                 # max + d == lo: not below lo, must interpolate
+        ((1 + e + u, 3.0), FAIL),          # max + d < lo: every value fails
+        ((-1.0, 1 - e), 1),
+        ((-1.0, 1 - e - u / 2), FAIL),     # min - d > hi
+        ((2.0, 1.0), FAIL),                # empty brush
+    ]
+    for (lo, hi), want in cases:
+        got = oracle.cell_classes(v, np.float32([lo]), np.float32([hi]), 1)
+        assert got[0, 0, 0] == want, (lo, hi, hex(got[0, 0, 0]))
+        assert np.all(got[:3, :3, :3] == want) and np.all(got[3] == 0) and np.all(got[:, :, 3] == 0)
+
+
+def test_cell_classes_corner_set_and_nan():
+    n = 6
+    vol = np.zeros((2, n, n, n), np.float32)
+    vol[0, 2, 3, 4] = 10.0                               # one raised vertex (z, y, x) = (2, 3, 4)
+    vol[1, 1, 1, 1] = np.nan
+    lo = np.float32([5.0, -1.0])
+    hi = np.float32([20.0, 1.0])
+    got = oracle.cell_classes(vol, lo, hi, 0b01)
+    touch = np.zeros((n, n, n), bool)
+    touch[1:3, 2:4, 3:5] = True                          # the 8 cells with that vertex as a corner
+    inner = np.zeros((n, n, n), bool)
+    inner[:n - 1, :n - 1, :n - 1] = True
+    assert np.all(got[touch] == 1)                       # corners 0 and 10 straddle lo: interpolate
+    assert np.all(got[inner & ~touch] == FAIL)           # all-zero corners are below lo
+    # variable 1 restricted too: the NaN vertex fails its 8 cells whatever the brush
+    got2 = oracle.cell_classes(vol, lo, hi, 0b10)
+    nan_cells = np.zeros((n, n, n), bool)
+    nan_cells[0:2, 0:2, 0:2] = True
+    assert np.all(got2[nan_cells] == FAIL) and np.all(got2[inner & ~nan_cells] == 0)
+    # unrestricted variables never set bits
+    assert np.all(oracle.cell_classes(vol, lo, hi, 0) == 0)
+
+
+def _trilinear_real(c, fx, fy, fz):
+    c00 = c[0, 0, 0] + fx * (c[0, 0, 1] - c[0, 0, 0])
+    c10 = c[0, 1, 0] + fx * (c[0, 1, 1] - c[0, 1, 0])
+    c01 = c[1, 0, 0] + fx * (c[1, 0, 1] - c[1, 0, 0])
+    c11 = c[1, 1, 0] + fx * (c[1, 1, 1] - c[1, 1, 0])
+    c0 = c00 + fy * (c10 - c00)
+    c1 = c01 + fy * (c11 - c01)
+    return c0 + fz * (c1 - c0)
+
+
+def test_cell_classes_bound_the_interpolated_values():
+    """Brute force: inside a cell classed 'every value fails/passes' for a variable,
+    trilinear values at random points (float64) fail/pass that variable's brush."""
+    n = 10
+    rng = np.random.default_rng(5)
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    vol = np.stack([np.sin(0.5 * x) + np.cos(0.4 * y), 0.3 * z - 1.0,
+                    x * y / 20.0 + 0.05 * rng.normal(size=x.shape)]).astype(np.float32)
+    lo = np.float32([-0.3, 0.2, -np.inf])
+    hi = np.float32([0.8, np.inf, 2.0])
+    got = oracle.cell_classes(vol, lo, hi, 0b111)
+    pts = rng.random((24, 3))
+    seen = {"fail": 0, "inside": 0, "mixed": 0}
+    for z in range(n - 1):
+        for y in range(n - 1):
+            for x in range(n - 1):
+                w = int(got[z, y, x])
+                vals = []
+                for v in range(3):
+                    c = vol[v, z:z + 2, y:y + 2, x:x + 2].astype(np.float64)
+                    s = np.array([_trilinear_real(c, *p) for p in pts])
+                    vals.append((s >= lo[v]) & (s <= hi[v]))
+                    if (w >> v) & 1:
+                        seen["mixed"] += 1
+                    elif not (w & FAIL):
+                        seen["inside"] += 1
+                        assert vals[-1].all(), (z, y, x, v)
+                if w & FAIL:
+                    seen["fail"] += 1
+                    assert not np.logical_and.reduce(vals).any(), (z, y, x)
+    assert min(seen.values()) > 50, seen
+
+
+def test_cell_classes_overflow_guard():
+    n = 16
+    vol = np.zeros((1, n, n, n), np.float32)
+    vol[0, 8, 8, :8] = -3e38
+    vol[0, 8, 8, 8:] = 3e38
+    got = oracle.cell_classes(vol, np.float32([3.2e38]), np.float32([np.inf]), 1)
+    assert got[7, 7, 7] == 1 and got[8, 8, 7] == 1       # corners of both signs: interpolate
+    assert got[0, 0, 0] == FAIL and got[7, 7, 8] == 1    # zeros only fail; 3e38 and 0 straddle
