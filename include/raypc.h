@@ -458,6 +458,18 @@ raypc_status raypc_get_skip_list(raypc_ctx *ctx, int vol, int lod, uint32_t *act
 raypc_status raypc_get_sub_bricks(raypc_ctx *ctx, int vol, int lod, float *out_min_dev,
                                   float *out_max_dev, uint32_t *active_bits_dev, void *stream);
 
+/* Copy a level's cell classes under the current brush (computed if needed):
+ * out_dev receives n^3 uint16 words, [z][y][x] for the interpolation cell
+ * with lower corner (x,y,z). Over the cell's 8 corner values, a restricted
+ * variable v FAILS if a corner is NaN or, with m = max(|min|,|max|) <= 2^126
+ * and d = m * 2^-20 + 2^-120, max + d < lo[v] or min - d > hi[v]; it is
+ * INSIDE if m <= 2^126, min - d >= lo[v] and max + d <= hi[v]; else it must
+ * be interpolated. Bit v of a word is set iff v must be interpolated; bit 15
+ * iff some restricted variable fails. Words of cells with an index of n-1 are
+ * 0. raypc_render uses them to decide samples without interpolating (Section
+ * 2.2 brush test, same decisions). */
+raypc_status raypc_get_cell_classes(raypc_ctx *ctx, int vol, int lod, uint16_t *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

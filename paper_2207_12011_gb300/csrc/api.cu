@@ -49,7 +49,7 @@ namespace {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive};
+                    L.sbmin, L.sbmax, L.sactive, L.cls};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -63,7 +63,7 @@ void free_bricks(Level& L) {
     L.bmin = L.bmax = L.sbmin = L.sbmax = nullptr;
     L.active = L.skippable = L.list = L.n_active = L.sactive = nullptr;
     L.pass_count = nullptr;
-    L.bricks = L.classified = false;
+    L.bricks = L.classified = L.cls_valid = false;
 }
 
 void free_volume(raypc_ctx* ctx, Volume* V) {
@@ -107,7 +107,10 @@ raypc_status classify_all(Volume* V, cudaStream_t s) {
         C.active = L.sactive;
     }
     CK(launch_classify(c, s), "classify kernels");
-    for (int l = 0; l < V->nlev; ++l) V->lv[l].classified = true;
+    for (int l = 0; l < V->nlev; ++l) {
+        V->lv[l].classified = true;
+        V->lv[l].cls_valid = false;          // cell classes follow the brush; computed on demand
+    }
     return RAYPC_OK;
 }
 
@@ -162,7 +165,7 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
     if (staging) cudaFreeAsync(staging, s);
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     L.bricks = true;               // level-0 brick min/max come out of the ingest pass
-    for (auto& l : V->lv) l.classified = false;
+    for (auto& l : V->lv) l.classified = l.cls_valid = false;
     return RAYPC_OK;
 }
 
@@ -253,6 +256,26 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.counts = o.counts_dev;
     a.stats = stats_dev;
     *out = a;
+    return RAYPC_OK;
+}
+
+raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream_t s) {
+    if (L.cls_valid) return RAYPC_OK;
+    if (!V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "raypc_set_brush must run first");
+    if (!L.cls) {
+        const size_t bytes = (size_t)L.n * L.n * L.n * sizeof(uint16_t);
+        raypc_status st = ctx->alloc((void**)&L.cls, bytes, &V->bytes);
+        if (st) return st;
+        CK(cudaMemsetAsync(L.cls, 0, bytes, s), "clear cell classes");
+    }
+    CellClassArgs c{};
+    c.cells = L.cells;
+    c.n = L.n;
+    c.nvars = V->nvars;
+    c.brush = V->brush;
+    c.out = L.cls;
+    CK(launch_cell_classes(c, V->dtype, s), "cell class kernel");
+    L.cls_valid = true;
     return RAYPC_OK;
 }
 
@@ -421,7 +444,7 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
     }
     if (V->stale || 1 + n_lod > V->nlev) V->nlev = 1 + n_lod;   // stale coarser levels drop out
     V->stale = false;
-    for (auto& L : V->lv) L.classified = false;
+    for (auto& L : V->lv) L.classified = L.cls_valid = false;
     return RAYPC_OK;
 }
 
@@ -438,7 +461,7 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
     V->brush = b;
     V->brush_set = true;
     if (V->stale) {            // coarser levels are rebuilt by raypc_build_bricks, which classifies lazily
-        for (auto& L : V->lv) L.classified = false;
+        for (auto& L : V->lv) L.classified = L.cls_valid = false;
         return RAYPC_OK;
     }
     return classify_all(V, (cudaStream_t)stream);
@@ -487,6 +510,8 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     RenderArgs a{};
     if ((st = make_render_args(V, L, cam, w, h, opts, out_rgba_dev, stats_dev, &a))) return st;
     if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
+    if ((st = ensure_cell_classes(ctx, V, *L, (cudaStream_t)stream))) return st;
+    a.cls = L->cls;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }
@@ -617,6 +642,23 @@ raypc_status raypc_get_skip_list(raypc_ctx* ctx, int vol, int lod, uint32_t* act
     if (skippable_bits_dev) CK(cudaMemcpyAsync(skippable_bits_dev, L->skippable, wb, cudaMemcpyDeviceToDevice, s), "copy skippable bits");
     if (active_list_dev) CK(cudaMemcpyAsync(active_list_dev, L->list, L->nbricks() * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active list");
     if (n_active_dev) CK(cudaMemcpyAsync(n_active_dev, L->n_active, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s), "copy active count");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_get_cell_classes(raypc_ctx* ctx, int vol, int lod, uint16_t* out_dev, void* stream) {
+    if (!ctx || !out_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_cell_classes(ctx, V, *L, s))) return st;
+    CK(cudaMemcpyAsync(out_dev, L->cls, (size_t)L->n * L->n * L->n * sizeof(uint16_t), cudaMemcpyDeviceToDevice, s),
+       "copy cell classes");
     return RAYPC_OK;
 }
 

@@ -132,6 +132,7 @@ struct RenderArgs {
     float bg[4];
     int ert, skip;
     int variant;                  // 1..kNumVariants (tile shape of the launch)
+    const uint16_t* cls;          // optional cell classes under this brush (kCellFail / need bits), n^3
     float4* out;
     uint32_t* counts;             // optional [h][w][2]
     unsigned long long* stats;    // optional kNStats counters
@@ -291,6 +292,23 @@ struct ClassifyArgs {
     ClassifyLevel lv[6];
 };
 
+// Cell classes under a brush: for the interpolation cell with lower corner
+// (x, y, z) and each restricted variable v, over its 8 corner values: FAIL if
+// a corner is NaN or, with m = max(|min|, |max|) <= 2^126 and the brick
+// margin d, max + d < lo_v or min - d > hi_v (every sample value fails);
+// INSIDE if m <= 2^126, min - d >= lo_v and max + d <= hi_v (every value
+// passes); else the value must be interpolated. Word per cell: bit v = v must
+// be interpolated, kCellFail = some restricted variable fails; [z][y][x] over
+// n^3 (entries with an index of n-1 are not written).
+constexpr unsigned kCellFail = 0x8000u;
+struct CellClassArgs {
+    const void* cells;            // planar level values
+    int n;
+    int nvars;
+    BrushArgs brush;
+    uint16_t* out;
+};
+
 // Process-wide count of launched kernels (defined in api.cu).
 void count_launches(int k);
 
@@ -304,6 +322,7 @@ cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pai
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
                        float* bmin, float* bmax, float* sbmin, float* sbmax, cudaStream_t stream);
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
+cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
 // Batched render: per-view classification, then a persistent kernel that pulls
 // (view, 16x8 tile) work items from *tile_counter (zeroed by the caller).

@@ -9,7 +9,8 @@
 // sub-brick that holds the cell (samples in inactive sub-bricks cannot pass
 // the brush or the shell test), shell test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
-// selective first; the order cannot change the result), each as an FP32
+// selective first; the order cannot change the result) that the sample's cell
+// class does not already decide (single-view renders), each as an FP32
 // trilinear interpolation from four x-pair loads of that variable only, with
 // exit on the first failure. Kept samples are coloured by the transfer function (from shared
 // memory) and composited front to back with early ray termination.
@@ -206,11 +207,20 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
                 const size_t base = ((size_t)iz * n + iy) * n + ix;
                 ++evald;
+                // cell class: a variable whose 8 corners all pass needs no interpolation,
+                // one whose corners all fail (or hold a NaN) rejects the sample outright
+                unsigned need = 0xffu;
+                if (A.cls) {
+                    const unsigned c = __ldg(A.cls + base);
+                    if (c & kCellFail) { ++k; continue; }
+                    need = c;
+                }
                 bool pass = true;
                 float vc = 0.0f;
                 bool have_c = false;
                 for (int j = 0; j < nact; ++j) {
                     const int v = S.order[j];
+                    if (!((need >> v) & 1u)) continue;
                     const float s = interp_var<DT>(plane_ptr(A.lv.pairs, DT, v, plane), base, sy_, sz_, fx, fy, fz);
                     if (!(s >= S.lo[v] && s <= S.hi[v])) { pass = false; break; }
                     if (v == A.color_var) { vc = s; have_c = true; }

@@ -55,6 +55,8 @@ struct Level {
     float* sbmin = nullptr;       // [nsb^3][nvars]
     float* sbmax = nullptr;
     uint32_t* sactive = nullptr;  // sub-brick activity bits under the current brush
+    uint16_t* cls = nullptr;      // cell classes under the current brush (n^3), computed on demand
+    bool cls_valid = false;
     bool bricks = false;
     bool classified = false;
     size_t nbricks() const { return (size_t)nb * nb * nb; }
@@ -101,6 +103,10 @@ void resolve_launch(int device, int dtype, int n, int* variant, int* skip);
 // mapped host array indexed like the launch's views, *seq is the value a
 // record's seq field takes when that view is finished (see ViewDone).
 void batch_last_records(raypc_batch* b, const ViewDone** records, unsigned* seq);
+
+// Compute the cell classes of level L under the volume's brush if they are
+// not current (allocates them on first use).
+raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream_t s);
 
 // Validated brush box of a volume from host arrays (nvars entries each).
 raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, uint32_t active_mask, BrushArgs* out);

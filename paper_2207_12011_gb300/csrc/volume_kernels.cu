@@ -364,6 +364,63 @@ __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
     if (threadIdx.x == blockDim.x - 1) *L.n_active = s_sum[threadIdx.x];
 }
 
+// Cell classes (see CellClassArgs). A 32 x 8 block covers 31 x 8 cell columns
+// (lane 31 only supplies the right corners of lane 30) and a run of kCellZ
+// cells along z. Per slice and restricted variable each thread loads its
+// corners at (x, y) and (x, y+1), takes x+1 from the next lane, and keeps the
+// min/max/NaN of that 2 x 2 footprint; a cell combines two consecutive slices.
+constexpr int kCellZ = 16;
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_cell_classes(CellClassArgs A) {
+    const int n = A.n;
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * 31 + lane, y = blockIdx.y * 8 + threadIdx.y;
+    const int z0 = blockIdx.z * kCellZ, z1 = min(z0 + kCellZ, n - 1);     // cells z0 .. z1-1
+    const bool cell = lane < 31 && x < n - 1 && y < n - 1;
+    const int xl = min(x, n - 1), yl = min(y, n - 1), yb = min(y + 1, n - 1);
+    const size_t plane = (size_t)n * n * n;
+    float pmn[kMaxVars], pmx[kMaxVars];
+    bool pnan[kMaxVars];
+#pragma unroll
+    for (int v = 0; v < kMaxVars; ++v) { pmn[v] = 0.0f; pmx[v] = 0.0f; pnan[v] = false; }
+    for (int z = z0; z <= z1; ++z) {
+        unsigned word = 0;
+#pragma unroll
+        for (int v = 0; v < kMaxVars; ++v) {
+            if (v >= A.nvars || !((A.brush.mask >> v) & 1u)) continue;
+            const size_t row = (size_t)v * plane + (size_t)z * n * n;
+            const float a = load_cell<DT>(A.cells, row + (size_t)yl * n + xl);
+            const float b = load_cell<DT>(A.cells, row + (size_t)yb * n + xl);
+            const float a1 = __shfl_down_sync(0xffffffffu, a, 1);
+            const float b1 = __shfl_down_sync(0xffffffffu, b, 1);
+            const bool nan4 = (a != a) || (b != b) || (a1 != a1) || (b1 != b1);
+            const float mn4 = fminf(fminf(a, b), fminf(a1, b1));
+            const float mx4 = fmaxf(fmaxf(a, b), fmaxf(a1, b1));
+            if (z > z0) {
+                const float mn = fminf(pmn[v], mn4), mx = fmaxf(pmx[v], mx4);
+                if (pnan[v] || nan4) {
+                    word |= kCellFail;
+                } else {
+                    const float m = fmaxf(fabsf(mn), fabsf(mx));
+                    if (m > 0x1p126f) {
+                        word |= 1u << v;
+                    } else {
+                        const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                        const float up = __fadd_rn(mx, d), dn = __fsub_rn(mn, d);
+                        if (up < A.brush.lo[v] || dn > A.brush.hi[v]) word |= kCellFail;
+                        else if (!(dn >= A.brush.lo[v] && up <= A.brush.hi[v])) word |= 1u << v;
+                    }
+                }
+            }
+            pmn[v] = mn4;
+            pmx[v] = mx4;
+            pnan[v] = nan4;
+        }
+        if (z > z0 && cell) A.out[((size_t)(z - 1) * n + y) * n + x] = (uint16_t)word;
+    }
+}
+
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <int DT, int MODE, int SRC, int VEC>
@@ -434,6 +491,17 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
     a.sbmin = sbmin;
     a.sbmax = sbmax;
     return launch_rows<1>(a, dtype, stream);
+}
+
+cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream) {
+    if (a.n < 2) return cudaErrorInvalidValue;
+    const int cells = a.n - 1;
+    dim3 grid(blocks_for(cells, 31), blocks_for(cells, 8), blocks_for(cells, kCellZ));
+    dim3 block(32, 8);
+    if (dtype == kF16) k_cell_classes<kF16><<<grid, block, 0, stream>>>(a);
+    else k_cell_classes<kF32><<<grid, block, 0, stream>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {

@@ -105,6 +105,7 @@ _SIGS = {
     "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
     "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
     "raypc_get_sub_bricks": [_P, _I, _I, _P, _P, _P, _P],
+    "raypc_get_cell_classes": [_P, _I, _I, _P, _P],
     "raypc_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "raypc_batch_destroy": [_P],
     "raypc_render_batch": [_P, ctypes.POINTER(View), _I, _P],
@@ -359,6 +360,14 @@ class Volume:
               ctypes.c_void_p(cnt.data_ptr()), _stream(stream))
         n_active = int(cnt.item())
         return act, skp, lst[:n_active]
+
+    def cell_classes(self, lod: int = 0, stream=None) -> torch.Tensor:
+        """Cell classes under the current brush: int16 device tensor (n, n, n), [z][y][x]."""
+        n = self.info(lod).n
+        out = torch.empty((n, n, n), dtype=torch.int16, device=torch.device("cuda", self.ctx.device))
+        _call("raypc_get_cell_classes", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream))
+        return out
 
     def sub_bricks(self, lod: int = 0, classify: bool = True, stream=None):
         """4^3 sub-brick (min, max [nsb,nsb,nsb,nvars], active_bits int32 or None) as device tensors."""

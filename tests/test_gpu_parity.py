@@ -149,6 +149,31 @@ def test_classification_bit_exact(rp, ctx, brush_name):
     v.free()
 
 
+@pytest.mark.parametrize("store", ["f32", "f16"])
+@pytest.mark.parametrize("n,brush_name", [(37, "c2"), (64, "c3"), (33, "c1"), (20, "none"), (20, "empty")])
+def test_cell_classes_bit_exact(ctx, store, n, brush_name):
+    vol = synth.make_shell_volume(n, seed=6)
+    vol[1, 3, 4, 5] = float("nan")
+    if brush_name == "empty":
+        b = synth.Brush(np.full(6, 1.0, np.float32), np.full(6, 0.0, np.float32), 0b000110)
+    elif brush_name == "none":
+        b = synth.Brush(np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32), 0)
+    else:
+        b = synth.make_brush(torch.nan_to_num(vol), brush_name)
+    v = load(ctx, vol, store, n_lod=1, brush=b)
+    levels = oracle_levels(stored(vol, store), 1, store)
+    for lod in range(2):
+        got = v.cell_classes(lod).cpu().numpy().view(np.uint16)
+        want = oracle.cell_classes(levels[lod], b.lo, b.hi, b.active_mask)
+        assert np.array_equal(got, want), (lod, np.argwhere(got != want)[:5])
+    # a brush change recomputes them
+    b2 = synth.Brush(np.full(6, -0.5, np.float32), np.full(6, 0.5, np.float32), 0b100001)
+    v.set_brush(b2.lo, b2.hi, b2.active_mask)
+    got = v.cell_classes(0).cpu().numpy().view(np.uint16)
+    assert np.array_equal(got, oracle.cell_classes(levels[0], b2.lo, b2.hi, b2.active_mask))
+    v.free()
+
+
 # ----------------------------------------------------------------------------
 # rendering
 # ----------------------------------------------------------------------------
