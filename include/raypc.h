@@ -465,9 +465,11 @@ raypc_status raypc_get_sub_bricks(raypc_ctx *ctx, int vol, int lod, float *out_m
  * and d = m * 2^-20 + 2^-120, max + d < lo[v] or min - d > hi[v]; it is
  * INSIDE if m <= 2^126, min - d >= lo[v] and max + d <= hi[v]; else it must
  * be interpolated. Bit v of a word is set iff v must be interpolated; bit 15
- * iff some restricted variable fails. Words of cells with an index of n-1 are
- * 0. raypc_render uses them to decide samples without interpolating (Section
- * 2.2 brush test, same decisions). */
+ * iff some restricted variable fails. Only the words of cells inside active
+ * 4^3 sub-bricks (see raypc_get_sub_bricks) are computed -- the only cells a
+ * render consults; the other words are unspecified. raypc_render uses them to
+ * decide samples without interpolating (Section 2.2 brush test, same
+ * decisions). */
 raypc_status raypc_get_cell_classes(raypc_ctx *ctx, int vol, int lod, uint16_t *out_dev, void *stream);
 
 #ifdef __cplusplus

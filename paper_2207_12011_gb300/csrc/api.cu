@@ -49,7 +49,7 @@ namespace {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive, L.cls};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.cls};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -57,11 +57,11 @@ void free_level(Level& L) {
 
 void free_bricks(Level& L) {
     void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L.bmin = L.bmax = L.sbmin = L.sbmax = nullptr;
-    L.active = L.skippable = L.list = L.n_active = L.sactive = nullptr;
+    L.active = L.skippable = L.list = L.n_active = L.sactive = L.slist = L.scount = nullptr;
     L.pass_count = nullptr;
     L.bricks = L.classified = L.cls_valid = false;
 }
@@ -105,6 +105,8 @@ raypc_status classify_all(Volume* V, cudaStream_t s) {
         C.n = L.n;
         C.bs = kSub;
         C.active = L.sactive;
+        C.alist = L.slist;
+        C.acount = L.scount;
     }
     CK(launch_classify(c, s), "classify kernels");
     for (int l = 0; l < V->nlev; ++l) {
@@ -131,6 +133,8 @@ raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
     if ((st = ctx->alloc((void**)&L.sbmin, smm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.sbmax, smm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.sactive, L.nswords() * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.slist, L.nsbricks() * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.scount, sizeof(uint32_t), &V->bytes)) ||
         (st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.bmax, mm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.active, words, &V->bytes)) ||
@@ -261,7 +265,8 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
 
 raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream_t s) {
     if (L.cls_valid) return RAYPC_OK;
-    if (!V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "raypc_set_brush must run first");
+    raypc_status cst = ensure_classified(V, L, s);           // the classes cover the active sub-bricks
+    if (cst) return cst;
     if (!L.cls) {
         const size_t bytes = (size_t)L.n * L.n * L.n * sizeof(uint16_t);
         raypc_status st = ctx->alloc((void**)&L.cls, bytes, &V->bytes);
@@ -273,6 +278,8 @@ raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream
     c.n = L.n;
     c.nvars = V->nvars;
     c.brush = V->brush;
+    c.slist = L.slist;
+    c.scount = L.scount;
     c.out = L.cls;
     CK(launch_cell_classes(c, V->dtype, s), "cell class kernel");
     L.cls_valid = true;

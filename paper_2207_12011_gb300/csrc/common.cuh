@@ -279,6 +279,8 @@ struct ClassifyLevel {
     uint32_t* list;
     uint32_t* n_active;
     unsigned* pass_count;
+    uint32_t* alist;              // optional: active ids in no particular order ...
+    uint32_t* acount;             // ... and their number (zeroed by the launcher)
 };
 
 struct ClassifyArgs {
@@ -306,7 +308,9 @@ struct CellClassArgs {
     int n;
     int nvars;
     BrushArgs brush;
-    uint16_t* out;
+    const uint32_t* slist;        // active sub-brick ids under this brush (any order) ...
+    const uint32_t* scount;       // ... and their number (device)
+    uint16_t* out;                // written for the cells of the listed sub-bricks only
 };
 
 // Process-wide count of launched kernels (defined in api.cu).

@@ -55,6 +55,8 @@ struct Level {
     float* sbmin = nullptr;       // [nsb^3][nvars]
     float* sbmax = nullptr;
     uint32_t* sactive = nullptr;  // sub-brick activity bits under the current brush
+    uint32_t* slist = nullptr;    // active sub-brick ids (any order) and their number
+    uint32_t* scount = nullptr;
     uint16_t* cls = nullptr;      // cell classes under the current brush (n^3), computed on demand
     bool cls_valid = false;
     bool bricks = false;

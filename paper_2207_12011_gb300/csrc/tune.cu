@@ -1,5 +1,6 @@
 // Render-launch autotuner: times the tile variants with brick skipping on and
-// off on caller-given views and keeps the fastest per (device, storage dtype,
+// off on caller-given views (each with its own brush classification and cell
+// classes, as a single-view render runs) and keeps the fastest per (device, storage dtype,
 // grid edge). Renders and batches asked for RAYPC_AUTO use the table. None of
 // the choices changes a pixel; they only change speed. The table can persist
 // in a small JSON-lines file named by RAYPC_TUNE_CACHE.
@@ -143,12 +144,19 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         void* bits = nullptr;
         void* list = nullptr;
         void* misc = nullptr;
+        void* cls = nullptr;
         cudaError_t e = cudaMalloc(&bits, (2 * words + L->nswords()) * sizeof(uint32_t));
         if (e == cudaSuccess) temps.push_back(bits);
         if (e == cudaSuccess) e = cudaMalloc(&list, L->nbricks() * sizeof(uint32_t) + 16);
         if (e == cudaSuccess) temps.push_back(list);
         if (e == cudaSuccess) e = cudaMalloc(&misc, sizeof(unsigned) * (kMaxVars + 4));
         if (e == cudaSuccess) temps.push_back(misc);
+        // cell classes under the view's brush, as a single-view render uses them
+        if (e == cudaSuccess) e = cudaMalloc(&cls, (size_t)L->n * L->n * L->n * sizeof(uint16_t));
+        if (e == cudaSuccess) temps.push_back(cls);
+        void* slist = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&slist, L->nsbricks() * sizeof(uint32_t) + 16);
+        if (e == cudaSuccess) temps.push_back(slist);
         if (e != cudaSuccess) { st = cuda_fail(e, "tuning buffers"); break; }
         ClassifyArgs c{};
         c.nlev = 2;
@@ -171,11 +179,24 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         c.lv[1].n = L->n;
         c.lv[1].bs = kSub;
         c.lv[1].active = (uint32_t*)bits + 2 * words;
+        c.lv[1].alist = (uint32_t*)slist;
+        c.lv[1].acount = (uint32_t*)misc + kMaxVars + 1;
         cudaError_t ce = launch_classify(c, s);
         if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning classification"); break; }
         args[i].lv.active = c.lv[0].active;
         args[i].lv.skippable = c.lv[0].skippable;
         args[i].lv.sactive = c.lv[1].active;
+        CellClassArgs cc{};
+        cc.cells = L->cells;
+        cc.n = L->n;
+        cc.nvars = V->nvars;
+        cc.brush = args[i].brush;
+        cc.slist = c.lv[1].alist;
+        cc.scount = c.lv[1].acount;
+        cc.out = (uint16_t*)cls;
+        ce = launch_cell_classes(cc, V->dtype, s);
+        if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning cell classes"); break; }
+        args[i].cls = cc.out;
         args[i].pass_count = c.lv[0].pass_count;
     }
     if (st != RAYPC_OK) {

@@ -4,13 +4,13 @@
 // Section 2.1 of the paper prepares the data once (levels of detail, derived
 // variables); Section 2.2 relies on that preparation not depending on the
 // restrictions, so a brush edit only re-runs the (cheap) classification.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace raypc {
 
 namespace {
-
-constexpr int kRowThreads = 256;
 
 // Round to the storage dtype (the stored value, as a float).
 template <int DT> __device__ __forceinline__ float to_stored(float v);
@@ -185,95 +185,107 @@ __device__ __forceinline__ void produce_run(const RowsArgs& A, int X, int y, int
     }
 }
 
-// One block per (brick row (by, bz), variable). Thread t owns the VEC columns
-// X = VEC t .. VEC t + VEC-1 (striding over the level when it is wider than
-// the block) and also reads column X+VEC, the right element of its last pair.
-// The block streams the (up to) 9 x 9 x-rows y in [8by, 8by+8], z in
-// [8bz, 8bz+8]: it writes the 8 x 8 rows it owns (cells and x-pairs) and folds
-// every row, apron rows included, with the right column, into NaN-ignoring
-// min/max kept separately for the four (y half, z half) sub-brick rows: half
-// 0 is rows 0..4 of the brick, half 1 rows 4..8 (row 4 is in both). Lanes are
-// then reduced with shuffles: 4/VEC lanes make a sub-brick of edge 4 (x in
+// One block per (brick row (by, bz), variable), threads (t, dz): thread t owns
+// the VEC columns X = VEC t .. VEC t + VEC-1 (striding over the level when it
+// is wider than the block) of z-slice z = 8bz + dz, dz in 0..8, and also reads
+// column X+VEC, the right element of its last pair. Each thread streams the
+// (up to) 9 x-rows y in [8by, 8by+8] of its slice, writes the rows it owns
+// (dy, dz < 8: cells and x-pairs) and folds every row, apron rows included,
+// with the right column, into NaN-ignoring min/max for the two y halves of
+// the brick (half 0 is rows 0..4, half 1 rows 4..8; row 4 is in both). The
+// slices are folded into the two z halves in shared memory, then lanes are
+// reduced with shuffles: 4/VEC lanes make a sub-brick of edge 4 (x in
 // 4s..min(4s+4, n-1)), two sub-bricks a brick (x in 8b..min(8b+8, n-1)).
+constexpr int kRowCols = 64;                            // column threads per block (blockDim.x)
+constexpr int kRowSlices = kBrick + 1;                  // blockDim.y
+
 template <int DT, int MODE, int SRC, int VEC>
-__global__ void __launch_bounds__(kRowThreads) k_rows(RowsArgs A) {
+__global__ void __launch_bounds__(kRowCols * kRowSlices) k_rows(RowsArgs A) {
     constexpr int G = kSub / VEC;                       // lanes per sub-brick column
     constexpr int kBatch = MODE == 0 ? 3 : 1;          // rows whose loads are issued together
+    __shared__ float s_half[kRowSlices][4][kRowCols];  // per slice: min, max of y half 0, then of half 1
     const int n = A.n;
     const int nb = (n + kBrick - 1) / kBrick;
     const int nsb = (n + kSub - 1) / kSub;
     const int ncol = (n + VEC - 1) / VEC;
     const int by = blockIdx.x % nb, bz = blockIdx.x / nb, v = blockIdx.y;
+    const int dz = threadIdx.y, tx = threadIdx.x;
+    const int z = bz * kBrick + dz;
     const float qnan = __int_as_float(0x7fffffff);
     for (int c0 = 0; c0 < ncol; c0 += blockDim.x) {
-        const int t = c0 + threadIdx.x;
-        const bool valid = t < ncol;
+        const int t = c0 + tx;
+        const bool valid = t < ncol && z < n;
         const int X = t * VEC;
-        float mn[4] = {qnan, qnan, qnan, qnan}, mx[4] = {qnan, qnan, qnan, qnan};
-        for (int dz = 0; dz <= kBrick; ++dz) {
-            const int z = bz * kBrick + dz;
-            if (z >= n) break;
-            float ymn[2] = {qnan, qnan}, ymx[2] = {qnan, qnan};   // this z-slice, y halves 0 and 1
+        float ymn[2] = {qnan, qnan}, ymx[2] = {qnan, qnan};
 #pragma unroll
-            for (int dy0 = 0; dy0 <= kBrick; dy0 += kBatch) {
-                float val[kBatch][VEC + 1];
+        for (int dy0 = 0; dy0 <= kBrick; dy0 += kBatch) {
+            float val[kBatch][VEC + 1];
 #pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int y = by * kBrick + dy0 + j;
-                    if (valid && dy0 + j <= kBrick && y < n) produce_run<DT, MODE, SRC, VEC>(A, X, y, z, v, val[j]);
-                }
-#pragma unroll
-                for (int j = 0; j < kBatch; ++j) {
-                    const int dy = dy0 + j;
-                    const int y = by * kBrick + dy;
-                    if (!valid || dy > kBrick || y >= n) continue;
-                    float rmn = val[j][0], rmx = val[j][0];
-#pragma unroll
-                    for (int q = 1; q <= VEC; ++q) fold(rmn, rmx, val[j][q], val[j][q]);
-                    if (dy <= kSub) fold(ymn[0], ymx[0], rmn, rmx);
-                    if (dy >= kSub) fold(ymn[1], ymx[1], rmn, rmx);
-                    if (dy < kBrick && dz < kBrick)
-                        store_run<DT, VEC>(A.cells, A.pairs, (((size_t)v * n + z) * n + y) * n + X, val[j]);
-                }
+            for (int j = 0; j < kBatch; ++j) {
+                const int y = by * kBrick + dy0 + j;
+                if (valid && dy0 + j <= kBrick && y < n) produce_run<DT, MODE, SRC, VEC>(A, X, y, z, v, val[j]);
             }
-            if (dz <= kSub) {
-                fold(mn[0], mx[0], ymn[0], ymx[0]);
-                fold(mn[1], mx[1], ymn[1], ymx[1]);
-            }
-            if (dz >= kSub) {
-                fold(mn[2], mx[2], ymn[0], ymx[0]);
-                fold(mn[3], mx[3], ymn[1], ymx[1]);
+#pragma unroll
+            for (int j = 0; j < kBatch; ++j) {
+                const int dy = dy0 + j;
+                const int y = by * kBrick + dy;
+                if (!valid || dy > kBrick || y >= n) continue;
+                float rmn = val[j][0], rmx = val[j][0];
+#pragma unroll
+                for (int q = 1; q <= VEC; ++q) fold(rmn, rmx, val[j][q], val[j][q]);
+                if (dy <= kSub) fold(ymn[0], ymx[0], rmn, rmx);
+                if (dy >= kSub) fold(ymn[1], ymx[1], rmn, rmx);
+                if (dy < kBrick && dz < kBrick)
+                    store_run<DT, VEC>(A.cells, A.pairs, (((size_t)v * n + z) * n + y) * n + X, val[j]);
             }
         }
-        // sub-bricks: reduce over the G lanes of a sub-brick column
+        s_half[dz][0][tx] = ymn[0];
+        s_half[dz][1][tx] = ymx[0];
+        s_half[dz][2][tx] = ymn[1];
+        s_half[dz][3][tx] = ymx[1];
+        __syncthreads();
+        if (dz == 0) {
+            // (y half, z half) h = j + 2i: slices 0..4 make z half 0, slices 4..8 z half 1
+            float mn[4] = {qnan, qnan, qnan, qnan}, mx[4] = {qnan, qnan, qnan, qnan};
 #pragma unroll
-        for (int m = 1; m < G; m <<= 1)
+            for (int sl = 0; sl < kRowSlices; ++sl) {
+                const float a0 = s_half[sl][0][tx], b0 = s_half[sl][1][tx];
+                const float a1 = s_half[sl][2][tx], b1 = s_half[sl][3][tx];
+                if (sl <= kSub) { fold(mn[0], mx[0], a0, b0); fold(mn[1], mx[1], a1, b1); }
+                if (sl >= kSub) { fold(mn[2], mx[2], a0, b0); fold(mn[3], mx[3], a1, b1); }
+            }
+            // sub-bricks: reduce over the G lanes of a sub-brick column
 #pragma unroll
-            for (int h = 0; h < 4; ++h)
-                fold(mn[h], mx[h], __shfl_xor_sync(0xffffffffu, mn[h], m), __shfl_xor_sync(0xffffffffu, mx[h], m));
-        const int sx = t / G;
-        if (valid && t % G == 0) {
+            for (int m = 1; m < G; m <<= 1)
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int sy = 2 * by + (h & 1), sz = 2 * bz + (h >> 1);
-                if (sy < nsb && sz < nsb && sx < nsb) {
-                    const size_t sb = ((size_t)sz * nsb + sy) * nsb + sx;
-                    A.sbmin[sb * A.nvars + v] = mn[h];
-                    A.sbmax[sb * A.nvars + v] = mx[h];
+                for (int h = 0; h < 4; ++h)
+                    fold(mn[h], mx[h], __shfl_xor_sync(0xffffffffu, mn[h], m), __shfl_xor_sync(0xffffffffu, mx[h], m));
+            const bool tcol = t < ncol;
+            const int sx = t / G;
+            if (tcol && t % G == 0) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int sy = 2 * by + (h & 1), sz = 2 * bz + (h >> 1);
+                    if (sy < nsb && sz < nsb && sx < nsb) {
+                        const size_t sb = ((size_t)sz * nsb + sy) * nsb + sx;
+                        A.sbmin[sb * A.nvars + v] = mn[h];
+                        A.sbmax[sb * A.nvars + v] = mx[h];
+                    }
                 }
             }
-        }
-        // bricks: all four halves of two neighbouring sub-brick columns
-        float bmn = mn[0], bmx = mx[0];
+            // bricks: all four halves of two neighbouring sub-brick columns
+            float bmn = mn[0], bmx = mx[0];
 #pragma unroll
-        for (int h = 1; h < 4; ++h) fold(bmn, bmx, mn[h], mx[h]);
-        fold(bmn, bmx, __shfl_xor_sync(0xffffffffu, bmn, G), __shfl_xor_sync(0xffffffffu, bmx, G));
-        const int bx = t / (2 * G);
-        if (valid && t % (2 * G) == 0 && bx < nb) {
-            const size_t b = ((size_t)bz * nb + by) * nb + bx;
-            A.bmin[b * A.nvars + v] = bmn;
-            A.bmax[b * A.nvars + v] = bmx;
+            for (int h = 1; h < 4; ++h) fold(bmn, bmx, mn[h], mx[h]);
+            fold(bmn, bmx, __shfl_xor_sync(0xffffffffu, bmn, G), __shfl_xor_sync(0xffffffffu, bmx, G));
+            const int bx = t / (2 * G);
+            if (tcol && t % (2 * G) == 0 && bx < nb) {
+                const size_t b = ((size_t)bz * nb + by) * nb + bx;
+                A.bmin[b * A.nvars + v] = bmn;
+                A.bmax[b * A.nvars + v] = bmx;
+            }
         }
+        __syncthreads();                                 // s_half is rewritten by the next column chunk
     }
 }
 
@@ -307,7 +319,13 @@ __global__ void k_classify(ClassifyArgs C) {
         act = classify_brick(b, nb, L.bs, L.sc, C.rin2, C.rout2, C.brush, C.nvars, L.bmin, L.bmax, pass_bits);
     const unsigned word = __ballot_sync(0xffffffffu, act);
     if (lane == 0 && in_range && b < ((nbricks + 31) & ~(size_t)31)) L.active[b >> 5] = word;
-    if (L.pass_count == nullptr) return;        // uniform per warp: entry ranges are warp-aligned
+    if (L.alist && word) {                      // uniform per warp: entry ranges are warp-aligned
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(L.acount, (unsigned)__popc(word));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (act) L.alist[base + __popc(word & ((1u << lane) - 1u))] = (uint32_t)b;
+    }
+    if (L.pass_count == nullptr) return;
     for (int v = 0; v < C.nvars; ++v) {
         const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
         if (lane == 0 && cnt) atomicAdd(&L.pass_count[v], cnt);
@@ -364,60 +382,84 @@ __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
     if (threadIdx.x == blockDim.x - 1) *L.n_active = s_sum[threadIdx.x];
 }
 
-// Cell classes (see CellClassArgs). A 32 x 8 block covers 31 x 8 cell columns
-// (lane 31 only supplies the right corners of lane 30) and a run of kCellZ
-// cells along z. Per slice and restricted variable each thread loads its
-// corners at (x, y) and (x, y+1), takes x+1 from the next lane, and keeps the
-// min/max/NaN of that 2 x 2 footprint; a cell combines two consecutive slices.
-constexpr int kCellZ = 16;
+// Cell classes (see CellClassArgs) of the cells of the active sub-bricks only
+// (the render consults a cell's class only for samples in an active sub-brick).
+// One warp per listed sub-brick (4 x 4 x 4 cells): lane (lx, ly, lz) takes
+// the cells (4sx + lx, 4sy + ly, 4sz + 2lz + {0, 1}). Per restricted variable
+// a lane loads its 2 x 2 x 3 corner columns at once; the corner max
+// propagates NaN (max.NaN), so a NaN corner shows as a NaN cell max.
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Restricted variables of a launch in a fixed order: ids packed 4 bits each,
+// bounds in the same order.
+struct CellVars {
+    int nr;
+    unsigned ids;
+    float lo[kMaxVars], hi[kMaxVars];
+};
+
+constexpr int kCellWarps = 4;                           // warps per block
 
 template <int DT>
-__global__ void __launch_bounds__(256) k_cell_classes(CellClassArgs A) {
-    const int n = A.n;
-    const int lane = threadIdx.x;
-    const int x = blockIdx.x * 31 + lane, y = blockIdx.y * 8 + threadIdx.y;
-    const int z0 = blockIdx.z * kCellZ, z1 = min(z0 + kCellZ, n - 1);     // cells z0 .. z1-1
-    const bool cell = lane < 31 && x < n - 1 && y < n - 1;
-    const int xl = min(x, n - 1), yl = min(y, n - 1), yb = min(y + 1, n - 1);
-    const size_t plane = (size_t)n * n * n;
-    float pmn[kMaxVars], pmx[kMaxVars];
-    bool pnan[kMaxVars];
+__global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes(const void* __restrict__ cells, int n,
+                                                                 const uint32_t* __restrict__ slist,
+                                                                 const uint32_t* __restrict__ scount,
+                                                                 uint16_t* __restrict__ out, CellVars R) {
+    const int lane = threadIdx.x & 31;
+    const int lx = lane & 3, ly = (lane >> 2) & 3, lz = lane >> 4;
+    const int nsb = (n + kSub - 1) / kSub;
+    const unsigned count = *scount;
+    const size_t nn = (size_t)n * n;
+    for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps) {
+        const uint32_t id = __ldg(slist + i);
+        const int sx = (int)(id % nsb), sy = (int)((id / nsb) % nsb), sz = (int)(id / ((uint32_t)nsb * nsb));
+        const int x = sx * kSub + lx, y = sy * kSub + ly, z = sz * kSub + 2 * lz;
+        // corner indices (clamped; cells past n-2 are not written)
+        const int x1 = min(x + 1, n - 1), y0 = min(y, n - 1), y1 = min(y + 1, n - 1), x0 = min(x, n - 1);
+        const int zc[3] = {min(z, n - 1), min(z + 1, n - 1), min(z + 2, n - 1)};
+        unsigned word[2] = {0u, 0u};
 #pragma unroll
-    for (int v = 0; v < kMaxVars; ++v) { pmn[v] = 0.0f; pmx[v] = 0.0f; pnan[v] = false; }
-    for (int z = z0; z <= z1; ++z) {
-        unsigned word = 0;
+        for (int j = 0; j < kMaxVars; ++j) {
+            if (j >= R.nr) break;
+            const int v = (R.ids >> (4 * j)) & 15u;
+            const size_t pv = (size_t)v * nn * n;
+            float mn3[3], mx3[3];
 #pragma unroll
-        for (int v = 0; v < kMaxVars; ++v) {
-            if (v >= A.nvars || !((A.brush.mask >> v) & 1u)) continue;
-            const size_t row = (size_t)v * plane + (size_t)z * n * n;
-            const float a = load_cell<DT>(A.cells, row + (size_t)yl * n + xl);
-            const float b = load_cell<DT>(A.cells, row + (size_t)yb * n + xl);
-            const float a1 = __shfl_down_sync(0xffffffffu, a, 1);
-            const float b1 = __shfl_down_sync(0xffffffffu, b, 1);
-            const bool nan4 = (a != a) || (b != b) || (a1 != a1) || (b1 != b1);
-            const float mn4 = fminf(fminf(a, b), fminf(a1, b1));
-            const float mx4 = fmaxf(fmaxf(a, b), fmaxf(a1, b1));
-            if (z > z0) {
-                const float mn = fminf(pmn[v], mn4), mx = fmaxf(pmx[v], mx4);
-                if (pnan[v] || nan4) {
-                    word |= kCellFail;
+            for (int q = 0; q < 3; ++q) {
+                const size_t r0 = pv + zc[q] * nn + (size_t)y0 * n, r1 = pv + zc[q] * nn + (size_t)y1 * n;
+                const float a = load_cell<DT>(cells, r0 + x0), b = load_cell<DT>(cells, r0 + x1);
+                const float c = load_cell<DT>(cells, r1 + x0), d = load_cell<DT>(cells, r1 + x1);
+                mn3[q] = fminf(fminf(a, b), fminf(c, d));
+                mx3[q] = max_nan(max_nan(a, b), max_nan(c, d));
+            }
+            const float lo = R.lo[j], hi = R.hi[j];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float mn = fminf(mn3[c], mn3[c + 1]), mx = max_nan(mx3[c], mx3[c + 1]);
+                unsigned w;
+                if (mx != mx) {
+                    w = kCellFail;                                     // a NaN corner
                 } else {
                     const float m = fmaxf(fabsf(mn), fabsf(mx));
-                    if (m > 0x1p126f) {
-                        word |= 1u << v;
-                    } else {
-                        const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-                        const float up = __fadd_rn(mx, d), dn = __fsub_rn(mn, d);
-                        if (up < A.brush.lo[v] || dn > A.brush.hi[v]) word |= kCellFail;
-                        else if (!(dn >= A.brush.lo[v] && up <= A.brush.hi[v])) word |= 1u << v;
-                    }
+                    const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                    const float up = __fadd_rn(mx, d), dn = __fsub_rn(mn, d);
+                    if (m > 0x1p126f) w = 1u << v;
+                    else if (up < lo || dn > hi) w = kCellFail;
+                    else if (dn >= lo && up <= hi) w = 0u;
+                    else w = 1u << v;
                 }
+                word[c] |= w;
             }
-            pmn[v] = mn4;
-            pmx[v] = mx4;
-            pnan[v] = nan4;
         }
-        if (z > z0 && cell) A.out[((size_t)(z - 1) * n + y) * n + x] = (uint16_t)word;
+        if (x < n - 1 && y < n - 1) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+                if (z + c < n - 1) out[((size_t)(z + c) * n + y) * n + x] = (uint16_t)word[c];
+        }
     }
 }
 
@@ -426,9 +468,9 @@ inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / 
 template <int DT, int MODE, int SRC, int VEC>
 void launch_rows_t(const RowsArgs& a, dim3 grid, cudaStream_t stream) {
     const int ncol = (a.n + VEC - 1) / VEC;
-    // one thread per column run up to kRowThreads (narrow levels use narrow blocks)
-    const int threads = min(kRowThreads, max(32, (ncol + 31) / 32 * 32));
-    k_rows<DT, MODE, SRC, VEC><<<grid, threads, 0, stream>>>(a);
+    // one thread per column run up to kRowCols (narrow levels use narrow blocks), per z-slice
+    const dim3 block(min(kRowCols, max(32, (ncol + 31) / 32 * 32)), kRowSlices);
+    k_rows<DT, MODE, SRC, VEC><<<grid, block, 0, stream>>>(a);
 }
 
 template <int MODE>
@@ -436,9 +478,10 @@ cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
     if (a.n < 2 || a.n > kMaxRowsEdge) return cudaErrorInvalidValue;
     const int nb = (a.n + kBrick - 1) / kBrick;
     dim3 grid((unsigned)(nb * nb), (unsigned)a.nvars);
-    // 4-column runs when every run is aligned: n % 4 == 0, a 16-byte aligned
-    // source (ingest) or an even fine edge (LOD; n % 4 == 0 makes it 8k).
-    bool vec = a.n % 4 == 0;
+    // 4-column runs when every run is aligned -- n % 4 == 0, a 16-byte aligned
+    // source (ingest) or an even fine edge (LOD; n % 4 == 0 makes it 8k) -- and
+    // the level is wide enough to fill a warp with runs.
+    bool vec = a.n % 4 == 0 && a.n >= 128;
     if (MODE == 0) vec = vec && ((uintptr_t)a.src % 16 == 0);
     else vec = vec && a.n_src == 2 * a.n;
     if (MODE == 0) {
@@ -494,12 +537,24 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
 }
 
 cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream) {
-    if (a.n < 2) return cudaErrorInvalidValue;
-    const int cells = a.n - 1;
-    dim3 grid(blocks_for(cells, 31), blocks_for(cells, 8), blocks_for(cells, kCellZ));
-    dim3 block(32, 8);
-    if (dtype == kF16) k_cell_classes<kF16><<<grid, block, 0, stream>>>(a);
-    else k_cell_classes<kF32><<<grid, block, 0, stream>>>(a);
+    if (a.n < 2 || !a.slist || !a.scount) return cudaErrorInvalidValue;
+    CellVars R{};
+    for (int v = 0; v < a.nvars && v < kMaxVars; ++v)
+        if ((a.brush.mask >> v) & 1u) {
+            R.ids |= (unsigned)v << (4 * R.nr);
+            R.lo[R.nr] = a.brush.lo[v];
+            R.hi[R.nr] = a.brush.hi[v];
+            ++R.nr;
+        }
+    // grid fixed on the host (the list length is on the device): enough warps
+    // for every listed sub-brick of a small level, a few waves for a large one
+    const size_t nsb = (size_t)((a.n + kSub - 1) / kSub);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned blocks = (unsigned)std::min<size_t>(blocks_for(nsb * nsb * nsb, kCellWarps), (size_t)sms * 16);
+    if (dtype == kF16) k_cell_classes<kF16><<<blocks, 32 * kCellWarps, 0, stream>>>(a.cells, a.n, a.slist, a.scount, a.out, R);
+    else k_cell_classes<kF32><<<blocks, 32 * kCellWarps, 0, stream>>>(a.cells, a.n, a.slist, a.scount, a.out, R);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -516,6 +571,10 @@ cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
         if (l + 1 == c.nbrick) c.total_brick = total;
         if (L.pass_count) {
             cudaError_t e = cudaMemsetAsync(L.pass_count, 0, sizeof(unsigned) * kMaxVars, stream);
+            if (e != cudaSuccess) return e;
+        }
+        if (L.alist) {
+            cudaError_t e = cudaMemsetAsync(L.acount, 0, sizeof(uint32_t), stream);
             if (e != cudaSuccess) return e;
         }
     }
