@@ -3,12 +3,15 @@
 // of adjacent axes (a, a+1), H[a][bin_a][bin_{a+1}] += 1.
 //
 // HBM-bound scan. A warp walks one x-row of cells (lanes over x, two cells per
-// lane in flight), so the planar loads of the needed variables are coalesced; rows whose cells all lie
-// outside the shell are skipped without touching memory. The in-shell test is
+// lane in flight), so the planar loads are coalesced; rows whose cells all lie
+// outside the shell are skipped without touching memory, and a cell loads its
+// axis values only after its brushed values pass. The in-shell test is
 // integer-exact. Bins come from a binary search over the FP32 edges held in
 // shared memory (comparisons only, so exact). Increments are aggregated per
 // warp with __match_any_sync on the (bin_a, bin_{a+1}) key: one atomicAdd per
 // distinct key per warp and pair.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace raypc {
@@ -31,16 +34,32 @@ __device__ __forceinline__ int bin_of(const float* e, int bins, float v, float e
     return j;
 }
 
-// Largest integer m >= 0 with m * m <= a (a >= 0).
-__device__ __forceinline__ long long isqrt_floor(long long a) {
-    long long m = (long long)sqrt((double)a);
-    while (m * m > a) --m;
-    while ((m + 1) * (m + 1) <= a) ++m;
+// Largest integer m >= 0 with m * m <= a (0 <= a < 2^31).
+__device__ __forceinline__ int isqrt_floor(int a) {
+    int m = (int)sqrtf((float)a);
+    while ((long long)m * m > a) --m;
+    while ((long long)(m + 1) * (m + 1) <= a) ++m;
     return m;
 }
 
+// Kernel view of a histogram call: the brushed variables and the axes as
+// compact lists (the host builds it from HistArgs).
+struct HistLaunch {
+    const void* cells;
+    int n, bins;
+    int nbr;                       // brushed variables tested per cell
+    int bvar[kMaxVars];
+    float blo[kMaxVars], bhi[kMaxVars];
+    int naxes;
+    int avar[kMaxVars];            // variable of each axis
+    const float* edges;            // naxes x (bins + 1), device
+    float guess_e0[kMaxVars], guess_scale[kMaxVars];
+    int s_in, s_out;               // shell test on 2x+1-n etc., clamped to int
+    uint32_t* out;
+};
+
 template <int DT>
-__global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
+__global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
     extern __shared__ float s_edges[];
     const int ne = A.naxes * (A.bins + 1);
     for (int i = threadIdx.x; i < ne; i += blockDim.x) s_edges[i] = A.edges[i];
@@ -53,81 +72,71 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int bins = A.bins;
     const size_t plane = (size_t)n * n * n;
-    const unsigned brush_mask = A.use_brush ? A.brush.mask : 0u;
-    const unsigned rest_mask = A.need_mask & ~brush_mask;
 
     for (long long r = gwarp; r < rows; r += nwarps) {
         const int y = (int)(r % n), z = (int)(r / n);
-        const long long dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
-        const long long syz = dy * dy + dz * dz;
-        if (syz > A.s_out) continue;                       // whole row outside the outer sphere
+        const int dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
+        const int syz = dy * dy + dz * dz;                  // < 2^31 for n <= 4096
+        if (syz > A.s_out) continue;                        // whole row outside the outer sphere
         // x range of the row inside the outer sphere: |2x + 1 - n| <= m
-        const long long m = isqrt_floor(A.s_out - syz);
-        const int xa = (int)max(0LL, (n - 1 - m + 1) / 2);
-        const int xb = (int)min((long long)n - 1, (n - 1 + m) / 2);
+        const int m = isqrt_floor(A.s_out - syz);
+        const int xa = max(0, (n - m) / 2);
+        const int xb = min(n - 1, (n - 1 + m) / 2);
         const size_t row_base = (size_t)r * n;
         // two cells per lane and iteration: their loads are in flight together
         for (int x0 = xa; x0 <= xb; x0 += 64) {
             bool keep[2];
-            int bn[2][kMaxVars];
-            float val[2][kMaxVars];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int x = x0 + lane + 32 * j;
                 keep[j] = false;
                 if (x <= xb) {
-                    const long long dx = 2 * x + 1 - n;
-                    const long long s = dx * dx + syz;
+                    const int dx = 2 * x + 1 - n;
+                    const int s = dx * dx + syz;
                     keep[j] = s >= A.s_in && s <= A.s_out;
                 }
             }
-            // brushed variables first; the rest only for cells that pass
+            // brushed variables first
+            float bv[2][kMaxVars];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const size_t off = row_base + x0 + lane + 32 * j;
+            for (int k = 0; k < kMaxVars; ++k) {
+                if (k >= A.nbr) break;
 #pragma unroll
-                for (int v = 0; v < kMaxVars; ++v)
-                    val[j][v] = (keep[j] && ((brush_mask >> v) & 1u)) ? load_cell<DT>(A.cells, v * plane + off) : 0.0f;
+                for (int j = 0; j < 2; ++j)
+                    bv[j][k] = keep[j] ? load_cell<DT>(A.cells, A.bvar[k] * plane + row_base + x0 + lane + 32 * j) : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < kMaxVars; ++k) {
+                if (k >= A.nbr) break;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) keep[j] = keep[j] && bv[j][k] >= A.blo[k] && bv[j][k] <= A.bhi[k];
+            }
+            if (__ballot_sync(0xffffffffu, keep[0] || keep[1]) == 0u) continue;
+            // axis values of the cells that pass (brushed ones come back from L1)
+            int bn[2][kMaxVars];
+#pragma unroll
+            for (int a = 0; a < kMaxVars; ++a) {
+                if (a >= A.naxes) break;
+                float va[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    va[j] = keep[j] ? load_cell<DT>(A.cells, A.avar[a] * plane + row_base + x0 + lane + 32 * j) : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    bn[j][a] = keep[j] ? bin_of(s_edges + a * (bins + 1), bins, va[j], A.guess_e0[a], A.guess_scale[a]) : 0;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-#pragma unroll
-                for (int v = 0; v < kMaxVars; ++v)
-                    if ((brush_mask >> v) & 1u)
-                        keep[j] = keep[j] && (val[j][v] >= A.brush.lo[v]) && (val[j][v] <= A.brush.hi[v]);
-            }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const size_t off = row_base + x0 + lane + 32 * j;
-#pragma unroll
-                for (int v = 0; v < kMaxVars; ++v)
-                    if (keep[j] && ((rest_mask >> v) & 1u)) val[j][v] = load_cell<DT>(A.cells, v * plane + off);
-            }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (keep[j]) {
-#pragma unroll
-                    for (int a = 0; a < kMaxVars; ++a) {
-                        if (a < A.naxes) {
-                            float va = val[j][0];
-#pragma unroll
-                            for (int v = 1; v < kMaxVars; ++v)
-                                if (A.axis[a] == v) va = val[j][v];
-                            bn[j][a] = bin_of(s_edges + a * (bins + 1), bins, va, A.guess_e0[a], A.guess_scale[a]);
-                        }
-                    }
-                }
                 const unsigned km = __ballot_sync(0xffffffffu, keep[j]);
                 if (km == 0u) continue;
                 if (keep[j]) {
 #pragma unroll
                     for (int p = 0; p + 1 < kMaxVars; ++p) {
-                        if (p + 1 < A.naxes) {
-                            const unsigned key = (unsigned)bn[j][p] * (unsigned)bins + (unsigned)bn[j][p + 1];
-                            const unsigned peers = __match_any_sync(km, key);
-                            if (lane == __ffs(peers) - 1)
-                                atomicAdd(A.out + (size_t)p * bins * bins + key, (unsigned)__popc(peers));
-                        }
+                        if (p + 1 >= A.naxes) break;
+                        const unsigned key = (unsigned)bn[j][p] * (unsigned)bins + (unsigned)bn[j][p + 1];
+                        const unsigned peers = __match_any_sync(km, key);
+                        if (lane == __ffs(peers) - 1)
+                            atomicAdd(A.out + (size_t)p * bins * bins + key, (unsigned)__popc(peers));
                     }
                 }
             }
@@ -136,7 +145,31 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistArgs A) {
 }
 
 template <int DT>
-cudaError_t launch_t(const HistArgs& a, cudaStream_t stream) {
+cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
+    HistLaunch a{};
+    a.cells = h.cells;
+    a.n = h.n;
+    a.bins = h.bins;
+    if (h.use_brush)
+        for (int v = 0; v < h.nvars && v < kMaxVars; ++v)
+            if ((h.brush.mask >> v) & 1u) {
+                a.bvar[a.nbr] = v;
+                a.blo[a.nbr] = h.brush.lo[v];
+                a.bhi[a.nbr] = h.brush.hi[v];
+                ++a.nbr;
+            }
+    a.naxes = h.naxes;
+    for (int i = 0; i < h.naxes && i < kMaxVars; ++i) {
+        a.avar[i] = h.axis[i];
+        a.guess_e0[i] = h.guess_e0[i];
+        a.guess_scale[i] = h.guess_scale[i];
+    }
+    a.edges = h.edges;
+    const int64_t imax = 0x7fffffff;
+    a.s_in = (int)std::min<int64_t>(std::max<int64_t>(h.s_in, 0), imax);
+    a.s_out = (int)std::min<int64_t>(h.s_out, imax);
+    a.out = h.out;
+    if (h.s_out < 0) return cudaSuccess;                 // no cell in the shell: the zeroed output is the answer
     // one row per warp (rows differ in length; the hardware balances blocks)
     long long rows = (long long)a.n * a.n;
     long long want_blocks = (rows + (kHistThreads / 32) - 1) / (kHistThreads / 32);
