@@ -138,8 +138,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def profiled_traffic():
-    """DRAM bytes per render launch from the committed ncu summary, if the kernel is unchanged since."""
+def profiled(field):
+    """A per-launch figure of the render kernel from the committed ncu summary
+    (`traffic_bytes_per_launch`, `warp_instructions_per_launch`), if the kernel
+    source is unchanged since the capture; else None."""
     import hashlib
     import re
     try:
@@ -147,7 +149,7 @@ def profiled_traffic():
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         text = open(os.path.join(ROOT, "profiles", "k_render_shell256_f32.md")).read()
         m = re.search(r"sha256 prefix at capture: ([0-9a-f]{16})", text)
-        t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+        t = re.search(field + r" \| (\d+)", text)
         if m and t and m.group(1) == h:
             return int(t.group(1))
     except OSError:
@@ -348,9 +350,20 @@ def run_ours(args):
     alg_bytes = n_active * 8 ** 3 * 6 * elem + c["w"] * c["h"] * 16
     achieved = alg_bytes / (render_ms / 1e3) / 1e9
     roofline = {"kernel": "k_render", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled("traffic_bytes_per_launch"),
                 "peak_kind": f"{peak_kind} HBM copy", "render_ms": round(render_ms, 4),
                 "alg_bytes_per_launch": alg_bytes, "active_bricks": n_active}
+    # the roof that binds the render: warp-instruction issue (4 schedulers per SM)
+    insts = profiled("warp_instructions_per_launch")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    issue_peak = sms * 4 * mhz * 1e6 / 1e9
+    roofline["binding"] = {
+        "bound": "issue", "unit": "G warp-instructions/s", "peak": round(issue_peak, 1),
+        "peak_kind": f"{sms} SMs x 4 schedulers x median SM clock {mhz:.0f} MHz",
+        "achieved": round(insts / (render_ms / 1e3) / 1e9, 1) if insts else None,
+        "frac": round(insts / (render_ms / 1e3) / 1e9 / issue_peak, 4) if insts else None,
+        "warp_instructions_per_launch": insts}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,

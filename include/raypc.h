@@ -186,7 +186,9 @@ raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lo
  * rounding), except that a variable with max(|min_v|, |max_v|) > 2^126 never
  * deactivates a brick (its interpolation can overflow to an infinite value);
  * skippable iff it and its 26 neighbours are inactive. The 4^3
- * sub-bricks are classified by the same rule. Requires raypc_build_bricks. */
+ * sub-bricks are classified by the same rule, and the cell classes of level 0
+ * (see raypc_get_cell_classes) are computed too; those of coarser levels are
+ * computed by their first render. Requires raypc_build_bricks. */
 raypc_status raypc_set_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
                              uint32_t active_mask, void *stream);
 

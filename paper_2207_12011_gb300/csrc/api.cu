@@ -471,7 +471,10 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
         for (auto& L : V->lv) L.classified = L.cls_valid = false;
         return RAYPC_OK;
     }
-    return classify_all(V, (cudaStream_t)stream);
+    if ((st = classify_all(V, (cudaStream_t)stream))) return st;
+    // the full-resolution level's cell classes now, so that a render runs its kernel
+    // alone (coarser levels get theirs when first rendered)
+    return ensure_cell_classes(ctx, V, V->lv[0], (cudaStream_t)stream);
 }
 
 raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_var, float v_lo,

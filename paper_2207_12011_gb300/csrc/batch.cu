@@ -22,7 +22,7 @@ struct raypc_batch {
     char* d_table = nullptr;          // BatchHeader, then max_views BatchView (device)
     unsigned* d_counter = nullptr;    // tile counter
     unsigned* d_pass = nullptr;       // max_views x kMaxVars selectivity counts
-    unsigned* d_tiles = nullptr;      // max_views finished-tile counters
+    unsigned* d_tiles = nullptr;      // max_views finished-tile counters, then max_views sub-brick list lengths
     ViewDone* h_done[2] = {nullptr, nullptr};   // mapped pinned completion records per table slot
     ViewDone* d_done[2] = {nullptr, nullptr};   // their device aliases
     unsigned seq = 0;                 // launch sequence number
@@ -31,8 +31,10 @@ struct raypc_batch {
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool used[2] = {false, false};
     int cur = 0;
-    std::vector<uint32_t*> bits;      // per view slot: active, skippable, then sub-brick active words
+    std::vector<uint32_t*> bits;      // per view slot: active, skippable, sub-brick active words, sub-brick list
     std::vector<size_t> bits_words;   // capacity (words) per slot
+    std::vector<uint16_t*> cls;       // per view slot: cell classes under the view's brush (n^3 words)
+    std::vector<size_t> cls_cells;    // capacity (cells) per slot
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int exec_key[2] = {-1, -1};       // dtype * 16 + variant of the captured graph
@@ -61,6 +63,8 @@ void release(raypc_batch* b) {
     }
     for (uint32_t* p : b->bits)
         if (p) cudaFree(p);
+    for (uint16_t* p : b->cls)
+        if (p) cudaFree(p);
     if (b->d_table) cudaFree(b->d_table);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_pass) cudaFree(b->d_pass);
@@ -84,7 +88,7 @@ raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
     cudaError_t e = cudaMemcpyAsync(b->d_table, b->h_table[slot], b->table_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_pass, 0, sizeof(unsigned) * kMaxVars * b->max_views, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned) * b->max_views, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned) * 2 * b->max_views, s);
     if (e == cudaSuccess)
         e = launch_render_batch(hdr_of(b->d_table), views_of(b->d_table), b->d_counter, dtype, variant,
                                 cls_blocks, blocks, s);
@@ -119,10 +123,12 @@ raypc_status raypc_batch_create(raypc_ctx* ctx, int max_views, raypc_batch** out
     b->table_bytes = kHeaderBytes + sizeof(BatchView) * (size_t)max_views;
     b->bits.assign(max_views, nullptr);
     b->bits_words.assign(max_views, 0);
+    b->cls.assign(max_views, nullptr);
+    b->cls_cells.assign(max_views, 0);
     raypc_status st = ctx->alloc((void**)&b->d_table, b->table_bytes, &b->charged);
     if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_counter, sizeof(unsigned), &b->charged);
     if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_pass, sizeof(unsigned) * kMaxVars * max_views, &b->charged);
-    if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_tiles, sizeof(unsigned) * max_views, &b->charged);
+    if (st == RAYPC_OK) st = ctx->alloc((void**)&b->d_tiles, sizeof(unsigned) * 2 * max_views, &b->charged);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && st == RAYPC_OK && e == cudaSuccess; ++i) {
         e = cudaHostAlloc((void**)&b->h_table[i], b->table_bytes, cudaHostAllocDefault);
@@ -184,7 +190,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;
         if (i == 0) variant = bv.a.variant;
         bv.a.variant = variant;
-        const size_t words = L->nwords(), need = 2 * words + L->nswords();
+        const size_t words = L->nwords(), need = 2 * words + L->nswords() + L->nsbricks();
         if (b->bits_words[i] < need) {
             // growing a slot's masks: no batch may still be reading the old ones
             wait_idle(b);
@@ -199,6 +205,21 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         bv.a.lv.active = b->bits[i];
         bv.a.lv.skippable = b->bits[i] + words;
         bv.a.lv.sactive = b->bits[i] + 2 * words;
+        bv.slist = b->bits[i] + 2 * words + L->nswords();
+        bv.scount = b->d_tiles + b->max_views + i;
+        const size_t cells = (size_t)L->n * L->n * L->n;
+        if (b->cls_cells[i] < cells) {
+            // growing a slot's cell classes: no batch may still be reading the old ones
+            wait_idle(b);
+            if (b->cls[i]) cudaFree(b->cls[i]);
+            b->cls[i] = nullptr;
+            b->cls_cells[i] = 0;
+            size_t ch = 0;
+            if ((st = ctx->alloc((void**)&b->cls[i], cells * sizeof(uint16_t), &ch))) return st;
+            b->charged += ch;
+            b->cls_cells[i] = cells;
+        }
+        bv.a.cls = b->cls[i];
         bv.a.pass_count = b->d_pass + (size_t)i * kMaxVars;
         bv.bmin = L->bmin;
         bv.bmax = L->bmax;

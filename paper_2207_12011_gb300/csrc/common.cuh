@@ -162,6 +162,8 @@ struct BatchView {
     const float* sbmax;
     unsigned long long cls_begin;  // first flat brick index (multiple of 32)
     unsigned long long cls_sub;    // offset of the first sub-brick in the view's range (multiple of 32)
+    uint32_t* slist;               // active sub-bricks of the view (any order), for its cell classes
+    uint32_t* scount;              // their number (zeroed per launch)
     int tiles_x;                   // tiles per image row
     int tile_begin;                // first flat tile index
     int ntiles;                    // tiles of this view
@@ -313,6 +315,91 @@ struct CellClassArgs {
     uint16_t* out;                // written for the cells of the listed sub-bricks only
 };
 
+// NaN-propagating max (a NaN operand gives NaN).
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Restricted variables of a brush in increasing order: ids packed 4 bits
+// each, bounds in the same order.
+struct CellVars {
+    int nr;
+    unsigned ids;
+    float lo[kMaxVars], hi[kMaxVars];
+};
+
+__host__ __device__ inline void cell_vars_of(const BrushArgs& b, int nvars, CellVars& R) {
+    R.nr = 0;
+    R.ids = 0;
+    for (int v = 0; v < nvars && v < kMaxVars; ++v)
+        if ((b.mask >> v) & 1u) {
+            R.ids |= (unsigned)v << (4 * R.nr);
+            R.lo[R.nr] = b.lo[v];
+            R.hi[R.nr] = b.hi[v];
+            ++R.nr;
+        }
+}
+
+constexpr int kCellWarps = 4;                           // warps per block of the cell-class kernels
+
+// Cell class words of the 4 x 4 x 4 cells of sub-brick `id` (see
+// CellClassArgs), computed by one warp: lane (lx, ly, lz) takes the cells
+// (4sx + lx, 4sy + ly, 4sz + 2lz + {0, 1}). Per restricted variable a lane
+// loads its 2 x 2 x 3 corner columns at once; the corner max propagates NaN,
+// so a NaN corner shows as a NaN cell max. Cells with an index of n-1 do not
+// exist and are not written.
+template <int DT>
+__device__ __forceinline__ void cell_classes_of_subbrick(const void* __restrict__ cells, int n, int nsb, uint32_t id,
+                                                         int lane, const CellVars& R, uint16_t* __restrict__ out) {
+    const int lx = lane & 3, ly = (lane >> 2) & 3, lz = lane >> 4;
+    const size_t nn = (size_t)n * n;
+    const int sx = (int)(id % nsb), sy = (int)((id / nsb) % nsb), sz = (int)(id / ((uint32_t)nsb * nsb));
+    const int x = sx * kSub + lx, y = sy * kSub + ly, z = sz * kSub + 2 * lz;
+    const int x1 = min(x + 1, n - 1), y0 = min(y, n - 1), y1 = min(y + 1, n - 1), x0 = min(x, n - 1);
+    const int zc[3] = {min(z, n - 1), min(z + 1, n - 1), min(z + 2, n - 1)};
+    unsigned word[2] = {0u, 0u};
+#pragma unroll
+    for (int j = 0; j < kMaxVars; ++j) {
+        if (j >= R.nr) break;
+        const int v = (R.ids >> (4 * j)) & 15u;
+        const size_t pv = (size_t)v * nn * n;
+        float mn3[3], mx3[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const size_t r0 = pv + zc[q] * nn + (size_t)y0 * n, r1 = pv + zc[q] * nn + (size_t)y1 * n;
+            const float a = load_cell<DT>(cells, r0 + x0), b = load_cell<DT>(cells, r0 + x1);
+            const float c = load_cell<DT>(cells, r1 + x0), d = load_cell<DT>(cells, r1 + x1);
+            mn3[q] = fminf(fminf(a, b), fminf(c, d));
+            mx3[q] = max_nan(max_nan(a, b), max_nan(c, d));
+        }
+        const float lo = R.lo[j], hi = R.hi[j];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float mn = fminf(mn3[c], mn3[c + 1]), mx = max_nan(mx3[c], mx3[c + 1]);
+            unsigned w;
+            if (mx != mx) {
+                w = kCellFail;                                         // a NaN corner
+            } else {
+                const float m = fmaxf(fabsf(mn), fabsf(mx));
+                const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                const float up = __fadd_rn(mx, d), dn = __fsub_rn(mn, d);
+                if (m > 0x1p126f) w = 1u << v;
+                else if (up < lo || dn > hi) w = kCellFail;
+                else if (dn >= lo && up <= hi) w = 0u;
+                else w = 1u << v;
+            }
+            word[c] |= w;
+        }
+    }
+    if (x < n - 1 && y < n - 1) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            if (z + c < n - 1) out[((size_t)(z + c) * n + y) * n + x] = (uint16_t)word[c];
+    }
+}
+
 // Process-wide count of launched kernels (defined in api.cu).
 void count_launches(int k);
 
@@ -328,8 +415,9 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
 cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
-// Batched render: per-view classification, then a persistent kernel that pulls
-// (view, 16x8 tile) work items from *tile_counter (zeroed by the caller).
+// Batched render: per-view classification (bricks, sub-bricks and the cell
+// classes of the active sub-bricks, into a.cls), then a persistent kernel that
+// pulls (view, tile) work items from *tile_counter (zeroed by the caller).
 // Grids are fixed by the caller (cls_blocks for the grid-stride classification,
 // blocks for the persistent render) so the launch can be captured in a graph;
 // launches are not counted here (the caller counts each replay).

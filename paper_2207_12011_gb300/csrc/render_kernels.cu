@@ -311,7 +311,16 @@ __global__ void k_classify_views(const BatchHeader* __restrict__ hdr, const Batc
         const unsigned word = __ballot_sync(0xffffffffu, act);
         uint32_t* active = const_cast<uint32_t*>(sub ? V.a.lv.sactive : V.a.lv.active);
         if (lane == 0) active[b >> 5] = word;
-        if (sub) continue;
+        if (sub) {
+            // list the active sub-bricks for the view's cell classes
+            if (V.slist && word) {
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(V.scount, (unsigned)__popc(word));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (act) V.slist[base + __popc(word & ((1u << lane) - 1u))] = (uint32_t)b;
+            }
+            continue;
+        }
         for (int v = 0; v < V.a.nvars; ++v) {
             const unsigned cnt = __popc(__ballot_sync(0xffffffffu, (pass_bits >> v) & 1u));
             if (lane == 0 && cnt) atomicAdd(const_cast<unsigned*>(V.a.pass_count) + v, cnt);
@@ -332,6 +341,29 @@ __global__ void k_skippable_views(const BatchHeader* __restrict__ hdr, const Bat
         const bool s = b < (size_t)nb * nb * nb && skippable_brick(b, nb, V.a.lv.active);
         const unsigned word = __ballot_sync(0xffffffffu, s);
         if (lane == 0) const_cast<uint32_t*>(V.a.lv.skippable)[b >> 5] = word;
+    }
+}
+
+// Cell classes of every view of a batch (see cell_classes_of_subbrick): the
+// blocks walk the views in order, each warp taking listed sub-bricks of the
+// current view; a view's restricted-variable list is built once per block.
+template <int DT>
+__global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes_views(const BatchHeader* __restrict__ hdr,
+                                                                       const BatchView* __restrict__ views) {
+    __shared__ CellVars s_vars;
+    const int nviews = hdr->nviews;
+    const int lane = threadIdx.x & 31;
+    for (int vi = 0; vi < nviews; ++vi) {
+        const BatchView& V = views[vi];
+        if (!V.slist || !V.a.cls) continue;                 // uniform: the view's table entry
+        __syncthreads();                                    // previous view's s_vars no longer read
+        if (threadIdx.x == 0) cell_vars_of(V.a.brush, V.a.nvars, s_vars);
+        __syncthreads();
+        const unsigned count = *V.scount;
+        const int n = V.a.lv.n, nsb = V.a.lv.nsb;
+        uint16_t* out = const_cast<uint16_t*>(V.a.cls);
+        for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps)
+            cell_classes_of_subbrick<DT>(V.a.lv.cells, n, nsb, __ldg(V.slist + i), lane, s_vars, out);
     }
 }
 
@@ -443,6 +475,10 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_skippable_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (dtype == kF16) k_cell_classes_views<kF16><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
+    else k_cell_classes_views<kF32><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (dtype == kF16) {

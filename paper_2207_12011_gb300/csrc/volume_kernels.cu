@@ -383,84 +383,18 @@ __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
 }
 
 // Cell classes (see CellClassArgs) of the cells of the active sub-bricks only
-// (the render consults a cell's class only for samples in an active sub-brick).
-// One warp per listed sub-brick (4 x 4 x 4 cells): lane (lx, ly, lz) takes
-// the cells (4sx + lx, 4sy + ly, 4sz + 2lz + {0, 1}). Per restricted variable
-// a lane loads its 2 x 2 x 3 corner columns at once; the corner max
-// propagates NaN (max.NaN), so a NaN corner shows as a NaN cell max.
-__device__ __forceinline__ float max_nan(float a, float b) {
-    float d;
-    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
-    return d;
-}
-
-// Restricted variables of a launch in a fixed order: ids packed 4 bits each,
-// bounds in the same order.
-struct CellVars {
-    int nr;
-    unsigned ids;
-    float lo[kMaxVars], hi[kMaxVars];
-};
-
-constexpr int kCellWarps = 4;                           // warps per block
-
+// (the render consults a cell's class only for samples in an active
+// sub-brick): one warp per listed sub-brick (see cell_classes_of_subbrick).
 template <int DT>
 __global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes(const void* __restrict__ cells, int n,
                                                                  const uint32_t* __restrict__ slist,
                                                                  const uint32_t* __restrict__ scount,
                                                                  uint16_t* __restrict__ out, CellVars R) {
     const int lane = threadIdx.x & 31;
-    const int lx = lane & 3, ly = (lane >> 2) & 3, lz = lane >> 4;
     const int nsb = (n + kSub - 1) / kSub;
     const unsigned count = *scount;
-    const size_t nn = (size_t)n * n;
-    for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps) {
-        const uint32_t id = __ldg(slist + i);
-        const int sx = (int)(id % nsb), sy = (int)((id / nsb) % nsb), sz = (int)(id / ((uint32_t)nsb * nsb));
-        const int x = sx * kSub + lx, y = sy * kSub + ly, z = sz * kSub + 2 * lz;
-        // corner indices (clamped; cells past n-2 are not written)
-        const int x1 = min(x + 1, n - 1), y0 = min(y, n - 1), y1 = min(y + 1, n - 1), x0 = min(x, n - 1);
-        const int zc[3] = {min(z, n - 1), min(z + 1, n - 1), min(z + 2, n - 1)};
-        unsigned word[2] = {0u, 0u};
-#pragma unroll
-        for (int j = 0; j < kMaxVars; ++j) {
-            if (j >= R.nr) break;
-            const int v = (R.ids >> (4 * j)) & 15u;
-            const size_t pv = (size_t)v * nn * n;
-            float mn3[3], mx3[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const size_t r0 = pv + zc[q] * nn + (size_t)y0 * n, r1 = pv + zc[q] * nn + (size_t)y1 * n;
-                const float a = load_cell<DT>(cells, r0 + x0), b = load_cell<DT>(cells, r0 + x1);
-                const float c = load_cell<DT>(cells, r1 + x0), d = load_cell<DT>(cells, r1 + x1);
-                mn3[q] = fminf(fminf(a, b), fminf(c, d));
-                mx3[q] = max_nan(max_nan(a, b), max_nan(c, d));
-            }
-            const float lo = R.lo[j], hi = R.hi[j];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float mn = fminf(mn3[c], mn3[c + 1]), mx = max_nan(mx3[c], mx3[c + 1]);
-                unsigned w;
-                if (mx != mx) {
-                    w = kCellFail;                                     // a NaN corner
-                } else {
-                    const float m = fmaxf(fabsf(mn), fabsf(mx));
-                    const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-                    const float up = __fadd_rn(mx, d), dn = __fsub_rn(mn, d);
-                    if (m > 0x1p126f) w = 1u << v;
-                    else if (up < lo || dn > hi) w = kCellFail;
-                    else if (dn >= lo && up <= hi) w = 0u;
-                    else w = 1u << v;
-                }
-                word[c] |= w;
-            }
-        }
-        if (x < n - 1 && y < n - 1) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-                if (z + c < n - 1) out[((size_t)(z + c) * n + y) * n + x] = (uint16_t)word[c];
-        }
-    }
+    for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps)
+        cell_classes_of_subbrick<DT>(cells, n, nsb, __ldg(slist + i), lane, R, out);
 }
 
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -538,14 +472,8 @@ cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, i
 
 cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream) {
     if (a.n < 2 || !a.slist || !a.scount) return cudaErrorInvalidValue;
-    CellVars R{};
-    for (int v = 0; v < a.nvars && v < kMaxVars; ++v)
-        if ((a.brush.mask >> v) & 1u) {
-            R.ids |= (unsigned)v << (4 * R.nr);
-            R.lo[R.nr] = a.brush.lo[v];
-            R.hi[R.nr] = a.brush.hi[v];
-            ++R.nr;
-        }
+    CellVars R;
+    cell_vars_of(a.brush, a.nvars, R);
     // grid fixed on the host (the list length is on the device): enough warps
     // for every listed sub-brick of a small level, a few waves for a large one
     const size_t nsb = (size_t)((a.n + kSub - 1) / kSub);
