@@ -274,7 +274,7 @@ raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream
         CK(cudaMemsetAsync(L.cls, 0, bytes, s), "clear cell classes");
     }
     CellClassArgs c{};
-    c.cells = L.cells;
+    c.pairs = L.pairs;
     c.n = L.n;
     c.nvars = V->nvars;
     c.brush = V->brush;

@@ -306,7 +306,7 @@ struct ClassifyArgs {
 // n^3 (entries with an index of n-1 are not written).
 constexpr unsigned kCellFail = 0x8000u;
 struct CellClassArgs {
-    const void* cells;            // planar level values
+    const void* pairs;            // x-pair layout of the level (see Pair)
     int n;
     int nvars;
     BrushArgs brush;
@@ -347,17 +347,17 @@ constexpr int kCellWarps = 4;                           // warps per block of th
 // Cell class words of the 4 x 4 x 4 cells of sub-brick `id` (see
 // CellClassArgs), computed by one warp: lane (lx, ly, lz) takes the cells
 // (4sx + lx, 4sy + ly, 4sz + 2lz + {0, 1}). Per restricted variable a lane
-// loads its 2 x 2 x 3 corner columns at once; the corner max propagates NaN,
-// so a NaN corner shows as a NaN cell max. Cells with an index of n-1 do not
-// exist and are not written.
+// loads its 2 x 3 corner x-pairs (the render's layout: one load gives both
+// x-corners) at once; the corner max propagates NaN, so a NaN corner shows as
+// a NaN cell max. Cells with an index of n-1 do not exist and are not written.
 template <int DT>
-__device__ __forceinline__ void cell_classes_of_subbrick(const void* __restrict__ cells, int n, int nsb, uint32_t id,
+__device__ __forceinline__ void cell_classes_of_subbrick(const void* __restrict__ pairs, int n, int nsb, uint32_t id,
                                                          int lane, const CellVars& R, uint16_t* __restrict__ out) {
     const int lx = lane & 3, ly = (lane >> 2) & 3, lz = lane >> 4;
     const size_t nn = (size_t)n * n;
     const int sx = (int)(id % nsb), sy = (int)((id / nsb) % nsb), sz = (int)(id / ((uint32_t)nsb * nsb));
     const int x = sx * kSub + lx, y = sy * kSub + ly, z = sz * kSub + 2 * lz;
-    const int x1 = min(x + 1, n - 1), y0 = min(y, n - 1), y1 = min(y + 1, n - 1), x0 = min(x, n - 1);
+    const int y0 = min(y, n - 1), y1 = min(y + 1, n - 1), x0 = min(x, n - 1);   // pair x0 = (c[x0], c[min(x0+1, n-1)])
     const int zc[3] = {min(z, n - 1), min(z + 1, n - 1), min(z + 2, n - 1)};
     unsigned word[2] = {0u, 0u};
 #pragma unroll
@@ -369,10 +369,9 @@ __device__ __forceinline__ void cell_classes_of_subbrick(const void* __restrict_
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const size_t r0 = pv + zc[q] * nn + (size_t)y0 * n, r1 = pv + zc[q] * nn + (size_t)y1 * n;
-            const float a = load_cell<DT>(cells, r0 + x0), b = load_cell<DT>(cells, r0 + x1);
-            const float c = load_cell<DT>(cells, r1 + x0), d = load_cell<DT>(cells, r1 + x1);
-            mn3[q] = fminf(fminf(a, b), fminf(c, d));
-            mx3[q] = max_nan(max_nan(a, b), max_nan(c, d));
+            const float2 p0 = Pair<DT>::load(pairs, r0 + x0), p1 = Pair<DT>::load(pairs, r1 + x0);
+            mn3[q] = fminf(fminf(p0.x, p0.y), fminf(p1.x, p1.y));
+            mx3[q] = max_nan(max_nan(p0.x, p0.y), max_nan(p1.x, p1.y));
         }
         const float lo = R.lo[j], hi = R.hi[j];
 #pragma unroll

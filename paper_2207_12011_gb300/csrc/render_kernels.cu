@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes_views(const Ba
         const int n = V.a.lv.n, nsb = V.a.lv.nsb;
         uint16_t* out = const_cast<uint16_t*>(V.a.cls);
         for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps)
-            cell_classes_of_subbrick<DT>(V.a.lv.cells, n, nsb, __ldg(V.slist + i), lane, s_vars, out);
+            cell_classes_of_subbrick<DT>(V.a.lv.pairs, n, nsb, __ldg(V.slist + i), lane, s_vars, out);
     }
 }
 

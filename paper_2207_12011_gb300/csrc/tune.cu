@@ -187,7 +187,7 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         args[i].lv.skippable = c.lv[0].skippable;
         args[i].lv.sactive = c.lv[1].active;
         CellClassArgs cc{};
-        cc.cells = L->cells;
+        cc.pairs = L->pairs;
         cc.n = L->n;
         cc.nvars = V->nvars;
         cc.brush = args[i].brush;

@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(1024) k_compact(ClassifyArgs C) {
 // (the render consults a cell's class only for samples in an active
 // sub-brick): one warp per listed sub-brick (see cell_classes_of_subbrick).
 template <int DT>
-__global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes(const void* __restrict__ cells, int n,
+__global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes(const void* __restrict__ pairs, int n,
                                                                  const uint32_t* __restrict__ slist,
                                                                  const uint32_t* __restrict__ scount,
                                                                  uint16_t* __restrict__ out, CellVars R) {
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes(const void* __
     const int nsb = (n + kSub - 1) / kSub;
     const unsigned count = *scount;
     for (unsigned i = blockIdx.x * kCellWarps + (threadIdx.x >> 5); i < count; i += gridDim.x * kCellWarps)
-        cell_classes_of_subbrick<DT>(cells, n, nsb, __ldg(slist + i), lane, R, out);
+        cell_classes_of_subbrick<DT>(pairs, n, nsb, __ldg(slist + i), lane, R, out);
 }
 
 inline unsigned blocks_for(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -481,8 +481,8 @@ cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned blocks = (unsigned)std::min<size_t>(blocks_for(nsb * nsb * nsb, kCellWarps), (size_t)sms * 16);
-    if (dtype == kF16) k_cell_classes<kF16><<<blocks, 32 * kCellWarps, 0, stream>>>(a.cells, a.n, a.slist, a.scount, a.out, R);
-    else k_cell_classes<kF32><<<blocks, 32 * kCellWarps, 0, stream>>>(a.cells, a.n, a.slist, a.scount, a.out, R);
+    if (dtype == kF16) k_cell_classes<kF16><<<blocks, 32 * kCellWarps, 0, stream>>>(a.pairs, a.n, a.slist, a.scount, a.out, R);
+    else k_cell_classes<kF32><<<blocks, 32 * kCellWarps, 0, stream>>>(a.pairs, a.n, a.slist, a.scount, a.out, R);
     count_launches(1);
     return cudaGetLastError();
 }
