@@ -550,6 +550,9 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     if (use_brush && !V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "use_brush needs raypc_set_brush");
     if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
     cudaStream_t s = (cudaStream_t)stream;
+    // with the volume's brush, its sub-brick classification lets the kernel skip inactive sub-bricks
+    const bool use_activity = use_brush && !V->stale;
+    if (use_activity && (st = ensure_classified(V, *L, s))) return st;
     HistArgs h{};
     h.cells = L->cells;
     h.n = L->n;
@@ -578,6 +581,8 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     if (e == cudaSuccess) {
         h.edges = dedges;
         h.out = out_counts_dev;
+        h.sactive = use_activity ? L->sactive : nullptr;
+        h.nsb = L->nsb;
         e = launch_histogram(h, V->dtype, s);
     }
     cudaFreeAsync(dedges, s);

@@ -202,6 +202,8 @@ struct HistArgs {
     float guess_scale[kMaxVars];  // starting guess of the bin walk (any value is correct)
     int64_t s_in, s_out;
     uint32_t* out;                // (naxes-1) x bins x bins
+    const uint32_t* sactive;      // optional: 4^3 sub-brick activity under this brush (cells of inactive
+    int nsb;                      // sub-bricks are never counted), sub-bricks per axis
 };
 
 // World box that the samples assigned to brick b of edge bs (lower

@@ -5,7 +5,11 @@
 // HBM-bound scan. A warp walks one x-row of cells (lanes over x, two cells per
 // lane in flight), so the planar loads are coalesced; rows whose cells all lie
 // outside the shell are skipped without touching memory, and a cell loads its
-// axis values only after its brushed values pass. The in-shell test is
+// axis values only after its brushed values pass. With the volume's own brush
+// the cells of inactive 4^3 sub-bricks are skipped without loads: every
+// vertex of such a sub-brick fails the brush (its values lie between the
+// sub-brick's min and max) or lies outside the shell (the sub-brick's widened
+// box, which holds the vertex centres, misses the shell). The in-shell test is
 // integer-exact. Bins come from a binary search over the FP32 edges held in
 // shared memory (comparisons only, so exact). Increments are aggregated per
 // warp with __match_any_sync on the (bin_a, bin_{a+1}) key: one atomicAdd per
@@ -56,6 +60,8 @@ struct HistLaunch {
     float guess_e0[kMaxVars], guess_scale[kMaxVars];
     int s_in, s_out;               // shell test on 2x+1-n etc., clamped to int
     uint32_t* out;
+    const uint32_t* sactive;       // optional sub-brick activity (see HistArgs)
+    int nsb;
 };
 
 template <int DT>
@@ -83,6 +89,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
         const int xa = max(0, (n - m) / 2);
         const int xb = min(n - 1, (n - 1 + m) / 2);
         const size_t row_base = (size_t)r * n;
+        const uint32_t srow = ((uint32_t)(z >> 2) * A.nsb + (uint32_t)(y >> 2)) * A.nsb;
         // two cells per lane and iteration: their loads are in flight together
         for (int x0 = xa; x0 <= xb; x0 += 64) {
             bool keep[2];
@@ -94,6 +101,11 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
                     const int dx = 2 * x + 1 - n;
                     const int s = dx * dx + syz;
                     keep[j] = s >= A.s_in && s <= A.s_out;
+                    if (keep[j] && A.sactive) {
+                        // a vertex of an inactive sub-brick fails the brush or lies outside the shell
+                        const uint32_t sid = srow + (uint32_t)(x >> 2);
+                        keep[j] = (__ldg(A.sactive + (sid >> 5)) >> (sid & 31)) & 1u;
+                    }
                 }
             }
             // brushed variables first
@@ -169,6 +181,8 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     a.s_in = (int)std::min<int64_t>(std::max<int64_t>(h.s_in, 0), imax);
     a.s_out = (int)std::min<int64_t>(h.s_out, imax);
     a.out = h.out;
+    a.sactive = h.sactive;
+    a.nsb = h.nsb;
     if (h.s_out < 0) return cudaSuccess;                 // no cell in the shell: the zeroed output is the answer
     // one row per warp (rows differ in length; the hardware balances blocks)
     long long rows = (long long)a.n * a.n;
