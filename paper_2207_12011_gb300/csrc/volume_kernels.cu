@@ -200,7 +200,7 @@ constexpr int kRowCols = 64;                            // column threads per bl
 constexpr int kRowSlices = kBrick + 1;                  // blockDim.y
 
 template <int DT, int MODE, int SRC, int VEC>
-__global__ void __launch_bounds__(kRowCols * kRowSlices) k_rows(RowsArgs A) {
+__global__ void __launch_bounds__(kRowCols * kRowSlices, 2) k_rows(RowsArgs A) {
     constexpr int G = kSub / VEC;                       // lanes per sub-brick column
     constexpr int kBatch = MODE == 0 ? 3 : 1;          // rows whose loads are issued together
     __shared__ float s_half[kRowSlices][4][kRowCols];  // per slice: min, max of y half 0, then of half 1

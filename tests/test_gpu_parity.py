@@ -398,6 +398,30 @@ def test_histogram_bit_exact(ctx, n, store, bname, bins, order):
     v.free()
 
 
+def test_histogram_on_coarse_levels_and_stale_volumes(ctx):
+    """With the volume's brush the kernel skips inactive sub-bricks of the level it
+    scans; after an update the classification is stale and it scans every cell.
+    Both must count exactly what the oracle counts."""
+    n = 40
+    vol = synth.make_shell_volume(n, seed=21)
+    brush = synth.make_brush(vol, "c2")
+    order = (0, 1, 2, 3, 4, 5)
+    v = load(ctx, vol, "f32", n_lod=2, brush=brush)
+    levels = oracle_levels(stored(vol, "f32"), 2, "f32")
+    for lod in range(3):
+        edges = synth.make_edges(torch.from_numpy(levels[lod]), order, bins=64)
+        H = v.pc_histogram(order, edges, lod=lod, use_brush=True).cpu().numpy().astype(np.uint32)
+        Ho, _ = oracle.histogram(levels[lod], R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, order, edges)
+        assert np.array_equal(H, Ho), lod
+    vol2 = synth.make_shell_volume(n, seed=22)
+    v.update(vol2.cuda())                                 # level 0 re-ingested, classification stale
+    edges = synth.make_edges(vol2, order, bins=64)
+    H = v.pc_histogram(order, edges, use_brush=True).cpu().numpy().astype(np.uint32)
+    Ho, _ = oracle.histogram(stored(vol2, "f32"), R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, order, edges)
+    assert np.array_equal(H, Ho)
+    v.free()
+
+
 def test_histogram_rejects_bad_edges(ctx, rp):
     vol = synth.make_shell_volume(16)
     v = load(ctx, vol, "f32", brush=synth.make_brush(vol, "c1"))
