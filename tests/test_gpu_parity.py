@@ -323,6 +323,11 @@ def test_render_edge_cases(ctx, rp):
     inside = synth.Camera((0.0, 0.1, 0.8), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.6)
     img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, inside, 33, 17, ert=False)
     assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
+    # eye inside the inner core: the analytic core jump starts at the first sample
+    core_eye = synth.Camera((0.05, 0.1, 0.2), (0.6, 0.3, -0.4), (0.0, 1.0, 0.0), 0.7)
+    for skip in (True, False):
+        img, cnt, ref, rcnt = render_pair(ctx, vol, "f32", brush, tf, core_eye, 29, 23, ert=False, skip=skip)
+        assert np.abs(img - ref).max() <= 1e-3 and np.array_equal(cnt, rcnt)
     # axis-aligned rays (the centre pixel of an odd image looks straight down -z;
     # its x and y direction components are exactly 0), with and without jumps
     axis = synth.Camera((0.0, 0.0, 2.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
