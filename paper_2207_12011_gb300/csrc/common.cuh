@@ -46,6 +46,19 @@ __device__ __forceinline__ void grid_coord_rn(float p, int n, float hn, float of
     f = __fsub_rn(u, (float)i);
 }
 
+// The same lower index from the integer side, for tests that need no weight:
+// min(max(floor(u), 0), n-2) equals min(floor(clamp(u, 0, n-1)), n-2) for
+// every u. u is returned for grid_weight_rn.
+__device__ __forceinline__ int grid_index_rn(float p, int n, float hn, float off, float& u) {
+    u = __fmaf_rn(p, hn, off);
+    return min(max(__float2int_rd(u), 0), n - 2);
+}
+
+// The weight of grid_coord_rn from u and the index of grid_index_rn.
+__device__ __forceinline__ float grid_weight_rn(float u, int i, float nm1) {
+    return __fsub_rn(fminf(fmaxf(u, 0.0f), nm1), (float)i);
+}
+
 // Trilinear interpolation of corner values c[dz][dy][dx]: x, then y, then z.
 __device__ __forceinline__ float trilerp_rn(float c000, float c100, float c010, float c110,
                                             float c001, float c101, float c011, float c111,

@@ -200,10 +200,10 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 const float t = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, t0);
                 const float pxw = __fmaf_rn(t, dx, ox), pyw = __fmaf_rn(t, dy, oy), pzw = __fmaf_rn(t, dz, oz);
                 int ix, iy, iz;
-                float fx, fy, fz;
-                grid_coord_rn(pxw, n, hn, off, ix, fx);
-                grid_coord_rn(pyw, n, hn, off, iy, fy);
-                grid_coord_rn(pzw, n, hn, off, iz, fz);
+                float ux, uy, uz;
+                ix = grid_index_rn(pxw, n, hn, off, ux);
+                iy = grid_index_rn(pyw, n, hn, off, uy);
+                iz = grid_index_rn(pzw, n, hn, off, uz);
                 const uint32_t sid = ((uint32_t)(iz >> 2) * nsb + (iy >> 2)) * nsb + (ix >> 2);
                 if (!bit_of(A.lv.sactive, sid)) {
                     if (A.skip) {
@@ -226,11 +226,10 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                         if (kl > k) {
                             // the estimated last sample, recomputed exactly
                             const float tl = __fmaf_rn(__fadd_rn((float)kl, 0.5f), dt, t0);
-                            int jx, jy, jz;
                             float gx, gy, gz;
-                            grid_coord_rn(__fmaf_rn(tl, dx, ox), n, hn, off, jx, gx);
-                            grid_coord_rn(__fmaf_rn(tl, dy, oy), n, hn, off, jy, gy);
-                            grid_coord_rn(__fmaf_rn(tl, dz, oz), n, hn, off, jz, gz);
+                            const int jx = grid_index_rn(__fmaf_rn(tl, dx, ox), n, hn, off, gx);
+                            const int jy = grid_index_rn(__fmaf_rn(tl, dy, oy), n, hn, off, gy);
+                            const int jz = grid_index_rn(__fmaf_rn(tl, dz, oz), n, hn, off, gz);
                             if (((jx ^ ix) >> sh) == 0 && ((jy ^ iy) >> sh) == 0 && ((jz ^ iz) >> sh) == 0) {
                                 skipped += (unsigned)(kl - k);
                                 k = kl + 1;
@@ -244,6 +243,8 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 const float r2 = dot3_rn(pxw, pyw, pzw, pxw, pyw, pzw);
                 if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
                 const size_t base = ((size_t)iz * n + iy) * n + ix;
+                const float nm1 = (float)(n - 1);
+                const float fx = grid_weight_rn(ux, ix, nm1), fy = grid_weight_rn(uy, iy, nm1), fz = grid_weight_rn(uz, iz, nm1);
                 ++evald;
                 // cell class: a variable whose 8 corners all pass needs no interpolation,
                 // one whose corners all fail (or hold a NaN) rejects the sample outright
