@@ -231,7 +231,6 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.lv.bmin = L->bmin;
     a.lv.bmax = L->bmax;
     a.lv.active = L->active;
-    a.lv.skippable = L->skippable;
     a.nvars = V->nvars;
     a.brush = V->brush;
     a.pass_count = L->pass_count;

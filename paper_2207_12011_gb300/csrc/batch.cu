@@ -31,7 +31,7 @@ struct raypc_batch {
     cudaEvent_t done[2] = {nullptr, nullptr};
     bool used[2] = {false, false};
     int cur = 0;
-    std::vector<uint32_t*> bits;      // per view slot: active, skippable, sub-brick active words, sub-brick list
+    std::vector<uint32_t*> bits;      // per view slot: active words, sub-brick active words, sub-brick list
     std::vector<size_t> bits_words;   // capacity (words) per slot
     std::vector<uint16_t*> cls;       // per view slot: cell classes under the view's brush (n^3 words)
     std::vector<size_t> cls_cells;    // capacity (cells) per slot
@@ -190,7 +190,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;
         if (i == 0) variant = bv.a.variant;
         bv.a.variant = variant;
-        const size_t words = L->nwords(), need = 2 * words + L->nswords() + L->nsbricks();
+        const size_t words = L->nwords(), need = words + L->nswords() + L->nsbricks();
         if (b->bits_words[i] < need) {
             // growing a slot's masks: no batch may still be reading the old ones
             wait_idle(b);
@@ -203,9 +203,8 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
             b->bits_words[i] = need;
         }
         bv.a.lv.active = b->bits[i];
-        bv.a.lv.skippable = b->bits[i] + words;
-        bv.a.lv.sactive = b->bits[i] + 2 * words;
-        bv.slist = b->bits[i] + 2 * words + L->nswords();
+        bv.a.lv.sactive = b->bits[i] + words;
+        bv.slist = b->bits[i] + words + L->nswords();
         bv.scount = b->d_tiles + b->max_views + i;
         const size_t cells = (size_t)L->n * L->n * L->n;
         if (b->cls_cells[i] < cells) {

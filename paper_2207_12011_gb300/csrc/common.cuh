@@ -35,26 +35,16 @@ __device__ __forceinline__ float dot3_rn(float ax, float ay, float az, float bx,
 }
 
 // Clamped cell-centred grid coordinate of world coordinate p on an n-cell
-// axis: u = p * n/2 + (n/2 - 1/2), clamped to [0, n-1]; lower index
-// i0 = min(floor(u), n-2); weight f = u - i0 (exact).
-__device__ __forceinline__ void grid_coord_rn(float p, int n, float hn, float off, int& i0, float& f) {
-    float u = __fmaf_rn(p, hn, off);
-    u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
-    int i = (int)floorf(u);
-    i = min(i, n - 2);
-    i0 = i;
-    f = __fsub_rn(u, (float)i);
-}
-
-// The same lower index from the integer side, for tests that need no weight:
-// min(max(floor(u), 0), n-2) equals min(floor(clamp(u, 0, n-1)), n-2) for
-// every u. u is returned for grid_weight_rn.
+// axis: u = p * n/2 + (n/2 - 1/2) clamped to [0, n-1], lower index
+// i0 = min(floor(u), n-2), weight f = u - i0 (exact). grid_index_rn gives i0
+// from the integer side -- min(max(floor(u), 0), n-2) equals
+// min(floor(clamp(u, 0, n-1)), n-2) for every u -- and returns the unclamped
+// u, from which grid_weight_rn (nm1 = n-1) gives f when a sample needs it.
 __device__ __forceinline__ int grid_index_rn(float p, int n, float hn, float off, float& u) {
     u = __fmaf_rn(p, hn, off);
     return min(max(__float2int_rd(u), 0), n - 2);
 }
 
-// The weight of grid_coord_rn from u and the index of grid_index_rn.
 __device__ __forceinline__ float grid_weight_rn(float u, int i, float nm1) {
     return __fsub_rn(fminf(fmaxf(u, 0.0f), nm1), (float)i);
 }
@@ -120,7 +110,6 @@ struct LevelArgs {
     const float* bmin;         // [nb^3][nvars]
     const float* bmax;
     const uint32_t* active;    // bitmask, ceil(nb^3/32) words
-    const uint32_t* skippable; // bitmask
     const uint32_t* sactive;   // sub-brick bitmask, ceil(nsb^3/32) words
 };
 
@@ -161,8 +150,8 @@ struct ViewDone {
     unsigned long long stats[kNStats];
 };
 
-// One view of a batched render: the march arguments (lv.active / lv.skippable
-// / lv.sactive / pass_count point at this view's own classification), the
+// One view of a batched render: the march arguments (lv.active / lv.sactive /
+// pass_count point at this view's own classification), the
 // level's brick and sub-brick min/max for that classification, and the view's
 // ranges in the flat brick and tile spaces of the batch. A view's flat brick
 // range holds its bricks (padded to a multiple of 32) followed by its

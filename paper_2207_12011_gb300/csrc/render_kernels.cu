@@ -367,22 +367,6 @@ __global__ void k_classify_views(const BatchHeader* __restrict__ hdr, const Batc
     }
 }
 
-__global__ void k_skippable_views(const BatchHeader* __restrict__ hdr, const BatchView* __restrict__ views) {
-    const BatchHeader H = *hdr;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < H.cls_total; g += stride) {
-        const int vi = view_of_brick(H, views, g - lane);
-        const BatchView& V = views[vi];
-        const int nb = V.a.lv.nb;
-        const size_t b = g - V.cls_begin;
-        if (b >= V.cls_sub) continue;                // sub-bricks have no skippable bits
-        const bool s = b < (size_t)nb * nb * nb && skippable_brick(b, nb, V.a.lv.active);
-        const unsigned word = __ballot_sync(0xffffffffu, s);
-        if (lane == 0) const_cast<uint32_t*>(V.a.lv.skippable)[b >> 5] = word;
-    }
-}
-
 // Cell classes of every view of a batch (see cell_classes_of_subbrick): the
 // blocks walk the views in order, each warp taking listed sub-bricks of the
 // current view; a view's restricted-variable list is built once per block.
@@ -512,9 +496,6 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
                                 int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream) {
     k_classify_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_skippable_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (dtype == kF16) k_cell_classes_views<kF16><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
     else k_cell_classes_views<kF32><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);

@@ -184,7 +184,6 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         cudaError_t ce = launch_classify(c, s);
         if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning classification"); break; }
         args[i].lv.active = c.lv[0].active;
-        args[i].lv.skippable = c.lv[0].skippable;
         args[i].lv.sactive = c.lv[1].active;
         CellClassArgs cc{};
         cc.pairs = L->pairs;
