@@ -250,10 +250,14 @@ typedef struct raypc_view {
 typedef struct raypc_batch raypc_batch;
 
 /* A reusable batch of up to max_views views (1..4096). It owns a device view
- * table, per-view classification bitmasks, a tile counter and a CUDA graph of
- * the batched launch (table upload, per-view brick classification, one
- * persistent render kernel), captured on first use and replayed afterwards.
- * Allocates device and pinned host memory. */
+ * table, per-view classification bitmasks and sub-brick lists, per-view cell
+ * classes, a tile counter and a CUDA graph of the batched launch (table
+ * upload, per-view brick and sub-brick classification, per-view cell classes,
+ * one persistent render kernel), captured on first use and replayed
+ * afterwards. Allocates device and pinned host memory; the per-view buffers
+ * are allocated for a view slot on its first use and grown for larger levels:
+ * n^3 * 2 bytes of cell classes plus about n^3 / 16 bytes of masks and lists
+ * per used slot (268 MB at 512^3), charged to the context's budget. */
 raypc_status raypc_batch_create(raypc_ctx *ctx, int max_views, raypc_batch **out);
 raypc_status raypc_batch_destroy(raypc_batch *batch);
 
@@ -287,7 +291,9 @@ raypc_status raypc_render_batch(raypc_batch *batch, const raypc_view *views, int
  * publishes each finished view through a record in mapped host memory, so a
  * request completes when its own passes are done, not when its whole launch
  * is. Per-request timestamps are recorded. A request's results are identical to rendering /
- * histogramming it alone. */
+ * histogramming it alone. Besides the output pool, each stream's batch holds
+ * per-view buffers (see raypc_batch_create) for the view slots its launches
+ * have used, at most num_streams * max_batch_views slots. */
 
 #define RAYPC_REQ_RENDER 0
 #define RAYPC_REQ_HISTOGRAM 1
