@@ -138,19 +138,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def render_code_hash():
+    """sha256 prefix of the render kernels' code: comments removed and whitespace
+    collapsed, so that a comment edit does not void a profile of unchanged code."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_2207_12011_gb300", "csrc", "render_kernels.cu")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
+
+
 def profiled(field):
     """A per-launch figure of the render kernel from the committed ncu summary
     (`traffic_bytes_per_launch`, `warp_instructions_per_launch`), if the kernel
-    source is unchanged since the capture; else None."""
-    import hashlib
+    code is unchanged since the capture; else None."""
     import re
     try:
-        src = os.path.join(ROOT, "paper_2207_12011_gb300", "csrc", "render_kernels.cu")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         text = open(os.path.join(ROOT, "profiles", "k_render_shell256_f32.md")).read()
-        m = re.search(r"sha256 prefix at capture: ([0-9a-f]{16})", text)
+        m = re.search(r"code sha256 prefix at capture: ([0-9a-f]{16})", text)
         t = re.search(field + r" \| (\d+)", text)
-        if m and t and m.group(1) == h:
+        if m and t and m.group(1) == render_code_hash():
             return int(t.group(1))
     except OSError:
         pass

@@ -1,8 +1,8 @@
 // Brushed emission-absorption ray marching (Section 2.2 of the paper).
 //
-// One thread per ray; a warp covers an 8x4 pixel tile so that neighbouring
-// rays fetch neighbouring vertices, and a 128-thread block covers 16x8
-// pixels. The per-pixel march is one device function shared by the
+// One thread per ray; a warp covers a small pixel tile (8x4, 16x2 or 4x8: the
+// launch variant) so that neighbouring rays fetch neighbouring vertices, and a
+// 128-thread block covers 2x2 warp tiles. The per-pixel march is one device function shared by the
 // single-frame kernel and the persistent batched kernel, so a view renders
 // bit-identically alone and inside a batch. Per lattice sample: position,
 // interpolation cell (exactly rounded FP32), the activity bit of the 4^3
@@ -10,7 +10,7 @@
 // the brush or the shell test), shell test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
 // selective first; the order cannot change the result) that the sample's cell
-// class does not already decide (single-view renders), each as an FP32
+// class does not already decide, each as an FP32
 // trilinear interpolation from four x-pair loads of that variable only, with
 // exit on the first failure. Kept samples are coloured by the transfer function (from shared
 // memory) and composited front to back with early ray termination.
@@ -101,7 +101,7 @@ __device__ __forceinline__ void load_view_shared(const RenderArgs& A, ViewShared
     }
 }
 
-// March the ray of this thread's pixel in 16x8 tile (tile_x, tile_y) of view A
+// March the ray of this thread's pixel in block tile (tile_x, tile_y) of view A
 // and write its pixel, optional counts and (warp-aggregated) statistics. All
 // 32 lanes of every warp must call it.
 template <int DT, int VAR>
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes_views(const Ba
     }
 }
 
-// Persistent batched render: every block repeatedly takes the next 16x8 tile
+// Persistent batched render: every block repeatedly takes the next block tile
 // of the whole batch from an atomic counter (tiles of one view are
 // contiguous, views in submission order), reloads its per-view shared state
 // when the view changes, and marches the tile. Blocks exit when the tiles run
