@@ -66,6 +66,14 @@ def _load():
                                           P, P, u32, P, i32, f32, f32, P, i32, P,
                                           ctypes.c_int64, P, P, i32]
             lib.oracle_render.restype = i32
+            lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
+                                               P, P, u32, P, i32, f32, f32, P, i32, P,
+                                               ctypes.c_int64, P, P, i32, u32, u32]
+            lib.oracle_render_pass.restype = i32
+            lib.oracle_jitter.argtypes = [u32, u32, ctypes.c_uint64]
+            lib.oracle_jitter.restype = f32
+            lib.oracle_splitmix64_output.argtypes = [ctypes.c_uint64]
+            lib.oracle_splitmix64_output.restype = ctypes.c_uint64
             lib.oracle_num_threads.restype = i32
             _lib = lib
     return _lib
@@ -164,8 +172,19 @@ def histogram(vol, r_in, r_out, lo, hi, active_mask, axis_order, edges, use_brus
     return out, int(cells[0])
 
 
+def jitter(seed, pass_, pix) -> float:
+    """Lattice offset of pixel index pix in progressive pass pass_ (pass 0: 0.5)."""
+    return float(_load().oracle_jitter(int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF, int(pix)))
+
+
+def splitmix64_output(z) -> int:
+    """SplitMix64's output function of a 64-bit state."""
+    return int(_load().oracle_splitmix64_output(int(z) & 0xFFFFFFFFFFFFFFFF))
+
+
 def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
-           tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0):
+           tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0,
+           seed=0, pass_=0):
     """Render (or render a subset of pixels) -> (rgba float64 [npix,4], counts uint32 [npix,2]).
 
     counts[:, 0] = lattice samples marched (entry to termination),
@@ -188,11 +207,12 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
         pix_ptr = _ptr(pix)
     out = np.zeros((npix, 4), np.float64)
     cnt = np.zeros((npix, 2), np.uint32)
-    rc = _load().oracle_render(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(cam),
-                               int(w), int(h), np.float32(dt), _ptr(_f32(lo)), _ptr(_f32(hi)),
-                               int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
-                               np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
-                               pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads))
+    rc = _load().oracle_render_pass(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(cam),
+                                    int(w), int(h), np.float32(dt), _ptr(_f32(lo)), _ptr(_f32(hi)),
+                                    int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
+                                    np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
+                                    pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads),
+                                    int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF)
     if rc != 0:
         raise ValueError("oracle_render: invalid arguments")
     if pixels is None:

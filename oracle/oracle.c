@@ -14,6 +14,7 @@
  *     and of interpolation cells (every sample fails / passes / must be
  *     interpolated);
  *   - the 2x2x2 mean used for the coarser levels of detail (Section 2.1);
+ *   - progressive passes with a per-pixel jittered lattice offset;
  *   - front-to-back emission-absorption ray marching where a sample is
  *     discarded when any restricted variable lies outside its brush bounds
  *     (Section 2.2), colour from a 1D transfer function, early termination;
@@ -303,9 +304,33 @@ typedef struct {
     int64_t npix;
     double *out;            /* npix x 4 */
     uint32_t *counts;       /* npix x 2: marched lattice samples, kept samples (may be NULL) */
+    uint32_t seed, pass;    /* progressive pass: lattice offset of every pixel (pass 0: 1/2) */
     int64_t next;           /* shared work counter */
     pthread_mutex_t lock;
 } render_job;
+
+/* ------------------------------------------------------------------ */
+/* Progressive passes (Section 2: passes keep refining the image while  */
+/* the camera rests). Pass p >= 1 of a pixel places its lattice at      */
+/* t_k = t0 + (k + j) dt instead of t0 + (k + 1/2) dt, with the sub-step */
+/* offset j drawn from SplitMix64 used as a counter-based generator:    */
+/* its output function at the state key + (pix + 1) * gamma, key =     */
+/* seed * 2^32 + p, gamma = 0x9E3779B97F4A7C15 (the generator's golden   */
+/* increment), pix = py * w + px; j is the top 24 bits as a fraction in */
+/* [0, 1). Pass 0 keeps j = 1/2, the unjittered lattice.                 */
+/* ------------------------------------------------------------------ */
+uint64_t oracle_splitmix64_output(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+float oracle_jitter(uint32_t seed, uint32_t pass, uint64_t pix) {
+    if (pass == 0) return 0.5f;
+    uint64_t key = ((uint64_t)seed << 32) | pass;
+    uint64_t z = oracle_splitmix64_output(key + (pix + 1) * 0x9E3779B97F4A7C15ULL);
+    return (float)(z >> 40) * 0x1p-24f;
+}
 
 /* FP32 decision geometry of the ray through pixel (px, py). */
 typedef struct { float o[3], d[3], t0, t1; int hit; } ray32;
@@ -446,13 +471,14 @@ static double interp64(const render_job *J, int v, const double p[3]) {
 static void render_pixel(const render_job *J, int px, int py, double *out, uint32_t *cnt) {
     ray32 r = make_ray32(J, px, py);
     ray64 q = make_ray64(J, px, py);
+    const float jit = oracle_jitter(J->seed, J->pass, (uint64_t)py * J->w + px);
     double C[3] = {0, 0, 0}, A = 0.0;
     uint32_t marched = 0, kept = 0;
     const double thr = 1.0 - ldexp(1.0, -12);
     float rin2 = J->r_in * J->r_in, rout2 = J->r_out * J->r_out;
     if (r.hit) {
         for (int k = 0;; k++) {
-            float t = fmaf((float)k + 0.5f, J->dt, r.t0);
+            float t = fmaf((float)k + jit, J->dt, r.t0);
             if (!(t < r.t1)) break;
             marched++;
             float p[3];
@@ -471,7 +497,7 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
             if (!keep) continue;
             kept++;
             /* Colour: FP64 value at the FP64 sample position. */
-            double tk = q.t0 + ((double)k + 0.5) * (double)J->dt;
+            double tk = q.t0 + ((double)k + (double)jit) * (double)J->dt;
             double p64[3];
             for (int a = 0; a < 3; a++) p64[a] = q.o[a] + tk * q.d[a];
             double vc = interp64(J, J->color_var, p64);
@@ -516,14 +542,15 @@ static void *render_worker(void *arg) {
     return NULL;
 }
 
-int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
-                  const float *cam, int w, int h, float dt,
-                  const float *lo, const float *hi, uint32_t active_mask,
-                  const float *tf, int color_var, float tf_lo, float tf_hi,
-                  const double *bg, int ert, const int64_t *pixels, int64_t npix,
-                  double *out, uint32_t *counts, int nthreads) {
+int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_out,
+                       const float *cam, int w, int h, float dt,
+                       const float *lo, const float *hi, uint32_t active_mask,
+                       const float *tf, int color_var, float tf_lo, float tf_hi,
+                       const double *bg, int ert, const int64_t *pixels, int64_t npix,
+                       double *out, uint32_t *counts, int nthreads, uint32_t seed, uint32_t pass) {
     if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
     render_job J;
+    J.seed = seed; J.pass = pass;
     J.vol = vol; J.n = n; J.nvars = nvars; J.r_in = r_in; J.r_out = r_out;
     J.cam = cam; J.w = w; J.h = h; J.dt = dt; J.lo = lo; J.hi = hi;
     J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
@@ -539,6 +566,16 @@ int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
     free(th);
     pthread_mutex_destroy(&J.lock);
     return 0;
+}
+
+int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
+                  const float *cam, int w, int h, float dt,
+                  const float *lo, const float *hi, uint32_t active_mask,
+                  const float *tf, int color_var, float tf_lo, float tf_hi,
+                  const double *bg, int ert, const int64_t *pixels, int64_t npix,
+                  double *out, uint32_t *counts, int nthreads) {
+    return oracle_render_pass(vol, n, nvars, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf, color_var,
+                              tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u);
 }
 
 int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }

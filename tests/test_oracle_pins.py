@@ -710,3 +710,56 @@ def test_cell_classes_overflow_guard():
     got = oracle.cell_classes(vol, np.float32([3.2e38]), np.float32([np.inf]), 1)
     assert got[7, 7, 7] == 1 and got[8, 8, 7] == 1       # corners of both signs: interpolate
     assert got[0, 0, 0] == FAIL and got[7, 7, 8] == 1    # zeros only fail; 3e38 and 0 straddle
+
+
+# ----------------------------------------------------------------------------
+# progressive passes: jittered lattice offsets
+# ----------------------------------------------------------------------------
+def test_splitmix64_output_matches_the_published_sequence():
+    """SplitMix64 seeded with 0 outputs E220A8397B1DCDAF, 6E789E6AA1B965F4 first:
+    the output function at states gamma and 2 gamma."""
+    g = 0x9E3779B97F4A7C15
+    assert oracle.splitmix64_output(g) == 0xE220A8397B1DCDAF
+    assert oracle.splitmix64_output((2 * g) % 2 ** 64) == 0x6E789E6AA1B965F4
+
+
+def test_jitter_is_uniform_and_pass_zero_is_unjittered():
+    assert all(oracle.jitter(s, 0, p) == 0.5 for s in (0, 3) for p in (0, 17))
+    j = np.array([oracle.jitter(11, 3, p) for p in range(40000)])
+    assert j.min() >= 0.0 and j.max() < 1.0
+    assert np.all(np.floor(j * 2 ** 24) == j * 2 ** 24)           # 24-bit fractions
+    # Kolmogorov-Smirnov distance to U[0, 1): critical value at 1e-4 is about 2.2 / sqrt(N)
+    xs = np.sort(j)
+    ecdf_hi = np.arange(1, xs.size + 1) / xs.size
+    ecdf_lo = np.arange(xs.size) / xs.size
+    ks = max(np.max(ecdf_hi - xs), np.max(xs - ecdf_lo))
+    assert ks < 2.2 / np.sqrt(xs.size), ks
+    # other passes and seeds are decorrelated from this one
+    j2 = np.array([oracle.jitter(11, 4, p) for p in range(40000)])
+    j3 = np.array([oracle.jitter(12, 3, p) for p in range(40000)])
+    assert abs(np.corrcoef(j, j2)[0, 1]) < 0.03 and abs(np.corrcoef(j, j3)[0, 1]) < 0.03
+
+
+def test_jittered_lattice_count_is_unbiased():
+    """A chord of length L holds ceil(L/dt - j) lattice points for offset j, so
+    uniform jitter makes the expected count exactly L/dt, while the fixed
+    lattice (j = 1/2) rounds it to the nearest integer."""
+    n = 16
+    dt = 1.0 / n
+    x = 30.35                                          # L / dt with a fractional part of 0.35
+    half = x * dt / 2.0
+    off = float(np.sqrt(1.0 - half * half))            # ray offset giving a chord of 2 * half
+    vol = np.ones((1, n, n, n), np.float32)
+    tf = np.zeros((256, 4), np.float32)
+    cam = np.float32([0.0, off, 3.0, 0.0, off, 0.0, 0.0, 1.0, 0.0, 0.01])
+    lo, hi = np.float32([-np.inf]), np.float32([np.inf])
+    counts = []
+    for p in range(1, 1201):
+        _, cnt = oracle.render(vol, 0.0, 1.0, cam, 1, 1, dt, lo, hi, 0, tf, 0, 0.0, 1.0,
+                               ert=False, seed=5, pass_=p)
+        counts.append(int(cnt[0, 0, 0]))
+    counts = np.array(counts)
+    assert set(counts.tolist()) <= {30, 31}
+    assert abs(counts.mean() - x) < 5 * 0.5 / np.sqrt(counts.size), counts.mean()
+    _, c0 = oracle.render(vol, 0.0, 1.0, cam, 1, 1, dt, lo, hi, 0, tf, 0, 0.0, 1.0, ert=False)
+    assert int(c0[0, 0, 0]) == 30                       # the fixed lattice: round(30.35)
