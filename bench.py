@@ -139,11 +139,13 @@ class ClockSampler:
 
 
 def render_code_hash():
-    """sha256 prefix of the render kernels' code: comments removed and whitespace
-    collapsed, so that a comment edit does not void a profile of unchanged code."""
+    """sha256 prefix of the render kernels' code (render_kernels.cu and the shared
+    common.cuh): comments removed and whitespace collapsed, so that a comment edit
+    does not void a profile of unchanged code."""
     import hashlib
     import re
-    src = open(os.path.join(ROOT, "paper_2207_12011_gb300", "csrc", "render_kernels.cu")).read()
+    csrc = os.path.join(ROOT, "paper_2207_12011_gb300", "csrc")
+    src = "".join(open(os.path.join(csrc, f)).read() for f in ("render_kernels.cu", "common.cuh"))
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
@@ -285,6 +287,32 @@ def run_ours(args):
     torch.cuda.synchronize()
     frame_ms = f0.elapsed_time(f1) / nframes
 
+    # ---- progressive passes with the view at rest (jittered lattice, running mean) ----
+    npass = 16
+    acc = torch.empty_like(img)
+    pimg = torch.empty_like(img)
+    pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    for p in range(3):
+        vol.render_progressive(wl.cam, c["w"], c["h"], 1, p, acc, out=pimg)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for p in range(npass):
+        vol.render_progressive(wl.cam, c["w"], c["h"], 1, p, acc, out=pimg, stats=pstats)
+    p1.record()
+    torch.cuda.synchronize()
+    pass_ms = p0.elapsed_time(p1) / npass
+    # distance to the ray integral, approximated by an 8x finer fixed lattice
+    fine, _ = vol.render(wl.cam, c["w"], c["h"], step=1.0 / (8 * c["n"]))
+    fixed, _ = vol.render(wl.cam, c["w"], c["h"])
+    torch.cuda.synchronize()
+    rms = lambda a: float(torch.sqrt(torch.mean((a.double() - fine.double()) ** 2)))
+    progressive = {"passes": npass, "ms_per_pass": round(pass_ms, 4),
+                   "samples_per_s": round(float(pstats[0].item()) / (pass_ms * npass / 1e3), 1),
+                   "rms_to_fine_fixed_lattice": rms(fixed), f"rms_to_fine_mean_of_{npass}": rms(acc),
+                   "what": "1024^2 passes of the resting view; rms against one render at 1/8 of the step"}
+    del acc, pimg, fine, fixed
+
     # ---- end to end through the C ABI from pinned host buffers ----
     # Every step copies its volume host -> device (pinned source) and reads its
     # image and histograms back device -> host. The copy of step i+1 runs on a
@@ -384,6 +412,7 @@ def run_ours(args):
         "frame_only": {"ms": round(frame_ms, 4), "fps": round(1e3 / frame_ms, 2),
                        "samples_per_s": round(float(fstats[0].item()) / (frame_ms * nframes / 1e3), 1),
                        "what": "brush edit + 1024^2 render + 5 PC histograms, volume resident"},
+        "progressive": progressive,
         "e2e": {"value": round(e2e_all / (e2e_max_ms / 1e3), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3),

@@ -225,6 +225,29 @@ raypc_status raypc_render(raypc_ctx *ctx, int vol, int lod, const raypc_camera *
                           int w, int h, const raypc_render_opts *opts,
                           float *out_rgba_dev, unsigned long long *stats_dev, void *stream);
 
+/* One progressive pass (Section 2: while the view rests, further passes
+ * refine the image). Pass `pass` of a sequence renders exactly like
+ * raypc_render except for the lattice: t_k = t0 + (k + j) * step with one
+ * offset j in [0, 1) per pixel and pass. Pass 0 takes j = 1/2 (the
+ * raypc_render image, bit for bit); pass p >= 1 takes the top 24 bits of
+ * SplitMix64's output function (Steele, Lea and Flood 2014) evaluated at the
+ * state key + (pix + 1) * 0x9E3779B97F4A7C15 (mod 2^64), key = seed * 2^32 + p,
+ * pix = y * w + x, times 2^-24. Over the passes each sample position is
+ * uniform in its step, so the running mean converges to the image of the
+ * continuous ray integral without the fixed lattice's aliasing.
+ * out_rgba_dev receives this pass's image. accum_rgba_dev (optional, [h][w][4]
+ * float32, 16-byte aligned, caller-owned, not aliasing out_rgba_dev) holds the
+ * running mean M of passes 0..pass and is updated in place:
+ * pass 0 writes M = image; pass p >= 1 writes M = fma(1/(p+1), image - M, M)
+ * per channel (1/(p+1) rounded to FP32), so the caller renders passes
+ * 0, 1, 2, ... in order on one stream. pass = 2^32 - 1 is rejected
+ * (RAYPC_ERR_INVALID_ARG), as is any argument raypc_render rejects. */
+raypc_status raypc_render_progressive(raypc_ctx *ctx, int vol, int lod, const raypc_camera *cam,
+                                      int w, int h, const raypc_render_opts *opts,
+                                      uint32_t seed, uint32_t pass, float *accum_rgba_dev,
+                                      float *out_rgba_dev, unsigned long long *stats_dev,
+                                      void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Batched rendering (many views and brushes in one launch)                */
 /* ---------------------------------------------------------------------- */

@@ -525,6 +525,34 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     return RAYPC_OK;
 }
 
+raypc_status raypc_render_progressive(raypc_ctx* ctx, int vol, int lod, const raypc_camera* cam, int w, int h,
+                                      const raypc_render_opts* opts, uint32_t seed, uint32_t pass,
+                                      float* accum_rgba_dev, float* out_rgba_dev,
+                                      unsigned long long* stats_dev, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    if (pass == 0xFFFFFFFFu) return fail(RAYPC_ERR_INVALID_ARG, "pass index 2^32 - 1 out of range");
+    if (((uintptr_t)accum_rgba_dev) & 15u) return fail(RAYPC_ERR_INVALID_ARG, "accum_rgba_dev must be 16-byte aligned");
+    if (accum_rgba_dev && accum_rgba_dev == out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "accum_rgba_dev and out_rgba_dev alias");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    RenderArgs a{};
+    if ((st = make_render_args(V, L, cam, w, h, opts, out_rgba_dev, stats_dev, &a))) return st;
+    if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
+    if ((st = ensure_cell_classes(ctx, V, *L, (cudaStream_t)stream))) return st;
+    a.cls = L->cls;
+    a.jit_seed = seed;
+    a.jit_pass = pass;
+    a.accum = reinterpret_cast<float4*>(accum_rgba_dev);
+    a.accum_w = 1.0f / (float)((double)pass + 1.0);
+    CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
+    return RAYPC_OK;
+}
+
 raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axis_order, int naxes,
                                 int bins, const float* edges, int use_brush, uint32_t* out_counts_dev,
                                 void* stream) {

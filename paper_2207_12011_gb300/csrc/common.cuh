@@ -62,6 +62,21 @@ __device__ __forceinline__ float trilerp_rn(float c000, float c100, float c010, 
     return lerp_rn(c0, c1, fz);
 }
 
+// Lattice offset of pixel index pix in progressive pass `pass` (Section 2:
+// passes keep refining the image while the camera rests): pass 0 uses 1/2 (the
+// fixed lattice t0 + (k + 1/2) dt); pass p >= 1 draws the offset from
+// SplitMix64 used as a counter-based generator -- its output function at the
+// state key + (pix + 1) * 0x9E3779B97F4A7C15, key = seed * 2^32 + p -- as the
+// top 24 bits of the output, a fraction in [0, 1).
+__device__ __forceinline__ float lattice_offset(uint32_t seed, uint32_t pass, unsigned long long pix) {
+    if (pass == 0u) return 0.5f;
+    unsigned long long z = ((((unsigned long long)seed) << 32) | pass) + (pix + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)(unsigned)(z >> 40) * 0x1p-24f;
+}
+
 // ---------------------------------------------------------------------------
 // Storage layouts. Every level of a volume is kept twice in HBM:
 //  - cells: planar, one plane of n^3 values per variable in the storage
@@ -134,6 +149,9 @@ struct RenderArgs {
     float bg[4];
     int ert, skip;
     int variant;                  // 1..kNumVariants (tile shape of the launch)
+    uint32_t jit_seed, jit_pass;  // progressive pass (0: the fixed lattice t0 + (k + 1/2) dt)
+    float4* accum;                // optional running mean of the passes ([h][w], updated in place)
+    float accum_w;                // 1 / (jit_pass + 1)
     const uint16_t* cls;          // optional cell classes under this brush (kCellFail / need bits), n^3
     float4* out;
     uint32_t* counts;             // optional [h][w][2]

@@ -24,8 +24,8 @@
 // Along a ray every step from k to the cell index on one axis (t_k, position,
 // grid coordinate, clamp, floor, min) is monotone in k, so two samples in the
 // box enclose only samples in the box: skipping changes no decision and needs
-// no neighbour condition. The lattice itself (t_k = t0 + (k + 1/2) dt) is never
-// shifted.
+// no neighbour condition. The lattice itself (t_k = t0 + (k + j) dt, j = 1/2
+// except in jittered progressive passes) is never shifted by a jump.
 #include "common.cuh"
 
 namespace raypc {
@@ -153,9 +153,11 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             // Lattice end: the first k with t_k >= t1, found once per ray from an
             // estimate corrected with the exact predicate (t_k is non-decreasing in k).
             const float inv_dt = 1.0f / dt;
-            int n_lat = max(0, (int)floorf((t1 - t0) * inv_dt - 0.5f));
-            while (n_lat > 0 && !(__fmaf_rn(__fadd_rn((float)(n_lat - 1), 0.5f), dt, t0) < t1)) --n_lat;
-            while (__fmaf_rn(__fadd_rn((float)n_lat, 0.5f), dt, t0) < t1) ++n_lat;
+            // lattice offset of this pixel (1/2 unless this is a jittered progressive pass)
+            const float jo = lattice_offset(A.jit_seed, A.jit_pass, (unsigned long long)py * A.w + px);
+            int n_lat = max(0, (int)floorf((t1 - t0) * inv_dt - jo));
+            while (n_lat > 0 && !(__fmaf_rn(__fadd_rn((float)(n_lat - 1), jo), dt, t0) < t1)) --n_lat;
+            while (__fmaf_rn(__fadd_rn((float)n_lat, jo), dt, t0) < t1) ++n_lat;
             const float inv_hn = 1.0f / hn;
             const float idx = 1.0f / dx, idy = 1.0f / dy, idz = 1.0f / dz;
             // Inner core: the samples core_a..core_b lie inside r_in and fail the shell
@@ -173,12 +175,12 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 if (hh < shrink) {
                     const float sc = __fsqrt_rn(__fsub_rn(shrink, hh));
                     const float tc0 = __fsub_rn(-b, sc), tc1 = __fadd_rn(-b, sc);
-                    const int ka = max(0, (int)ceilf(fminf((tc0 - t0) * inv_dt - 0.5f, 1.0e9f)));
-                    const int kb = min(n_lat - 1, (int)floorf(fminf((tc1 - t0) * inv_dt - 0.5f, 1.0e9f)));
+                    const int ka = max(0, (int)ceilf(fminf((tc0 - t0) * inv_dt - jo, 1.0e9f)));
+                    const int kb = min(n_lat - 1, (int)floorf(fminf((tc1 - t0) * inv_dt - jo, 1.0e9f)));
                     if (ka < kb) {
                         const float lim = __fmul_rn(A.rin2, 1.0f - 0x1p-10f);
-                        const float ta = __fmaf_rn(__fadd_rn((float)ka, 0.5f), dt, t0);
-                        const float tb = __fmaf_rn(__fadd_rn((float)kb, 0.5f), dt, t0);
+                        const float ta = __fmaf_rn(__fadd_rn((float)ka, jo), dt, t0);
+                        const float tb = __fmaf_rn(__fadd_rn((float)kb, jo), dt, t0);
                         const float ax = __fmaf_rn(ta, dx, ox), ay = __fmaf_rn(ta, dy, oy), az = __fmaf_rn(ta, dz, oz);
                         const float bx = __fmaf_rn(tb, dx, ox), by = __fmaf_rn(tb, dy, oy), bz = __fmaf_rn(tb, dz, oz);
                         if (dot3_rn(ax, ay, az, ax, ay, az) <= lim && dot3_rn(bx, by, bz, bx, by, bz) <= lim) {
@@ -197,7 +199,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                     kend = n_lat;
                     continue;
                 }
-                const float t = __fmaf_rn(__fadd_rn((float)k, 0.5f), dt, t0);
+                const float t = __fmaf_rn(__fadd_rn((float)k, jo), dt, t0);
                 const float pxw = __fmaf_rn(t, dx, ox), pyw = __fmaf_rn(t, dy, oy), pzw = __fmaf_rn(t, dz, oz);
                 int ix, iy, iz;
                 float ux, uy, uz;
@@ -221,11 +223,11 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                             else if (dd[a] < 0.0f && lo[a] > 0)
                                 te = fminf(te, (fmaf((float)lo[a] + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
                         }
-                        const float kk = fminf((te - t0) * inv_dt - 0.5f, 1.0e9f);
+                        const float kk = fminf((te - t0) * inv_dt - jo, 1.0e9f);
                         const int kl = kk > (float)(k + 1) ? min((int)ceilf(kk) - 1, n_lat - 1) : k;
                         if (kl > k) {
                             // the estimated last sample, recomputed exactly
-                            const float tl = __fmaf_rn(__fadd_rn((float)kl, 0.5f), dt, t0);
+                            const float tl = __fmaf_rn(__fadd_rn((float)kl, jo), dt, t0);
                             float gx, gy, gz;
                             const int jx = grid_index_rn(__fmaf_rn(tl, dx, ox), n, hn, off, gx);
                             const int jy = grid_index_rn(__fmaf_rn(tl, dy, oy), n, hn, off, gy);
@@ -297,6 +299,18 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
         o.w = fmaf(tr, A.bg[3], Aa);
         const size_t pix = (size_t)py * A.w + px;
         A.out[pix] = o;
+        if (A.accum) {
+            // running mean of the passes 0..jit_pass
+            float4 m = o;
+            if (A.jit_pass != 0u) {
+                const float4 prev = A.accum[pix];
+                m.x = fmaf(A.accum_w, o.x - prev.x, prev.x);
+                m.y = fmaf(A.accum_w, o.y - prev.y, prev.y);
+                m.z = fmaf(A.accum_w, o.z - prev.z, prev.z);
+                m.w = fmaf(A.accum_w, o.w - prev.w, prev.w);
+            }
+            A.accum[pix] = m;
+        }
         if (A.counts) {
             A.counts[2 * pix] = marched;
             A.counts[2 * pix + 1] = kept;

@@ -99,6 +99,8 @@ _SIGS = {
     "raypc_set_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_set_tf": [_P, _I, _P, _I, _F, _F, _P],
     "raypc_render": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts), _P, _P, _P],
+    "raypc_render_progressive": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts),
+                                 _U32, _U32, _P, _P, _P, _P],
     "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
     "raypc_volume_info": [_P, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "raypc_export_volume": [_P, _I, _I, _P, _P],
@@ -312,6 +314,27 @@ class Volume:
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _call("raypc_render", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
               ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), sp, _stream(stream))
+        return out, (counts if isinstance(counts, torch.Tensor) else None)
+
+    def render_progressive(self, cam, w: int, h: int, seed: int, pass_: int, accum: torch.Tensor | None,
+                           lod: int = 0, step: float = 0.0, ert: bool = True, skip: bool | None = None,
+                           bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
+                           counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None,
+                           variant: int = AUTO, stream=None):
+        """One progressive pass (jittered lattice; pass 0 equals render). accum, an (h, w, 4)
+        float32 device tensor or None, holds the running mean of passes 0..pass_ and is
+        updated in place. Returns (this pass's image, counts or None)."""
+        dev = torch.device("cuda", self.ctx.device)
+        if out is None:
+            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+        if counts is True:
+            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
+        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant)
+        c = camera_from(cam)
+        sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
+        ap = ctypes.c_void_p(accum.data_ptr()) if accum is not None else None
+        _call("raypc_render_progressive", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
+              ctypes.byref(o), int(seed), int(pass_), ap, ctypes.c_void_p(out.data_ptr()), sp, _stream(stream))
         return out, (counts if isinstance(counts, torch.Tensor) else None)
 
     def pc_histogram(self, axis_order, edges, use_brush: bool = True, lod: int = 0,

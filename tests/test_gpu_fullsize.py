@@ -60,6 +60,17 @@ def test_full_size_frame_and_histograms(rp, wl_name):
             if not ert:
                 assert np.array_equal(gc, rc)
             assert rc[:, 1].sum() > 0
+        # one jittered progressive pass, sampled
+        img, cnt = vol.render_progressive(wl.cam, c["w"], c["h"], 7, 5, None, ert=False, counts=True)
+        torch.cuda.synchronize()
+        g = img.cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)
+        gc = cnt.cpu().numpy().reshape(-1, 2)[pix].astype(np.uint32)
+        ref, rc = oracle.render(stored, synth.R_IN, synth.R_OUT, wl.cam.as_array(), c["w"], c["h"],
+                                1.0 / c["n"], wl.brush.lo, wl.brush.hi, wl.brush.active_mask,
+                                wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi, ert=False,
+                                pixels=pix, seed=7, pass_=5)
+        assert np.abs(g - ref).max() <= tol
+        assert np.array_equal(gc, rc)
         if c["store"] == "f16":
             # storage error: FP16 render against the oracle on the FP32 source (reported)
             src = wl.src.cpu().numpy()

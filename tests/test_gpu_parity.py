@@ -260,6 +260,74 @@ def test_skipping_never_changes_the_image(ctx):
         v.free()
 
 
+# ----------------------------------------------------------------------------
+# progressive passes (jittered lattice, running mean)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,store,bname,cvar,w,h,seed", [
+    (48, "f32", "c2", "v_r", 77, 45, 11),
+    (33, "f16", "c1", "T_anom", 50, 38, 0xFFFFFFFF),
+])
+def test_progressive_passes_match_oracle(ctx, n, store, bname, cvar, w, h, seed):
+    vol = synth.make_shell_volume(n, seed=3)
+    brush = synth.make_brush(vol, bname)
+    tf = synth.make_tf(vol, cvar)
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    v = load(ctx, vol, store, brush=brush, tf=tf)
+    level = stored(vol, store)
+    dev = torch.device("cuda", 0)
+    for ert in (False, True):
+        plain, plain_cnt = v.render(cam, w, h, ert=ert, counts=True)
+        accum = torch.full((h, w, 4), np.nan, dtype=torch.float32, device=dev)
+        refs = []
+        for p in range(4):
+            for skip in (True, False):
+                img, cnt = v.render_progressive(cam, w, h, seed, p, accum if skip else None, ert=ert,
+                                                skip=skip, counts=True)
+                torch.cuda.synchronize()
+                if skip:
+                    first = (img.clone(), cnt.clone())
+                else:   # skipping never changes a pass either
+                    assert torch.equal(img, first[0]) and torch.equal(cnt, first[1])
+            if p == 0:  # pass 0 is the fixed lattice of render, bit for bit
+                assert torch.equal(img, plain) and torch.equal(cnt, plain_cnt)
+            ref, rcnt = oracle.render(level, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
+                                      brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=ert,
+                                      seed=seed, pass_=p)
+            refs.append(ref)
+            g = img.cpu().numpy().astype(np.float64)
+            assert np.abs(g - ref).max() <= TOL[store], (ert, p)
+            c = cnt.cpu().numpy().astype(np.uint32)
+            if not ert:
+                assert np.array_equal(c, rcnt), p
+            else:
+                assert np.mean(c == rcnt) > 0.999
+            if p > 0:   # the jitter moves the lattice: some sample counts differ from pass 0
+                assert np.any(c[..., 0] != plain_cnt.cpu().numpy()[..., 0])
+            mean = np.mean(refs, axis=0)
+            assert np.abs(accum.cpu().numpy().astype(np.float64) - mean).max() <= TOL[store] + 1e-5, p
+    v.free()
+
+
+def test_progressive_rejects_bad_arguments(ctx, rp):
+    vol = synth.make_shell_volume(16)
+    brush = synth.make_brush(vol, "c1")
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    v = load(ctx, vol, "f32", brush=brush, tf=tf)
+    out = torch.zeros((8, 8, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(rp.RaypcError):
+        v.render_progressive(cam, 8, 8, 1, 0xFFFFFFFF, None, out=out)
+    with pytest.raises(rp.RaypcError):
+        v.render_progressive(cam, 8, 8, 1, 1, out, out=out)
+    buf = torch.zeros(8 * 8 * 4 + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(rp.RaypcError):
+        v.render_progressive(cam, 8, 8, 1, 1, buf[1:].view(8, 8, 4), out=out)
+    v.render_progressive(cam, 8, 8, 1, 0xFFFFFFFE, None, out=out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    v.free()
+
+
 def test_render_lod_levels(ctx):
     n = 64
     vol = synth.make_shell_volume(n)
