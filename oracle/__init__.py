@@ -56,19 +56,24 @@ def _load():
             P = ctypes.c_void_p
             i32, u32, f32 = ctypes.c_int, ctypes.c_uint32, ctypes.c_float
             lib.oracle_brick_minmax.argtypes = [P, i32, i32, i32, P, P]
-            lib.oracle_classify.argtypes = [P, P, i32, i32, i32, f32, f32, P, P, u32, P, P]
+            lib.oracle_classify.argtypes = [P, P, i32, i32, i32, f32, f32, P, P, u32, P, P, u32, P, P]
             lib.oracle_lod_mean.argtypes = [P, i32, i32, P]
             lib.oracle_cell_classes.argtypes = [P, i32, i32, P, P, u32, P]
             lib.oracle_shell_bounds.argtypes = [i32, f32, f32, P, P]
-            lib.oracle_histogram.argtypes = [P, i32, i32, f32, f32, P, P, u32, i32,
+            lib.oracle_histogram.argtypes = [P, i32, i32, f32, f32, P, P, u32, P, P, u32, i32,
                                              P, i32, i32, P, P, P]
+            lib.oracle_pc_subsample.argtypes = [P, i32, i32, f32, f32, P, P, u32, P, P, u32, u32,
+                                                ctypes.c_int64, P, i32, P, P, P]
+            lib.oracle_pc_subsample.restype = ctypes.c_int64
+            lib.oracle_subsample_key.argtypes = [u32, ctypes.c_int64]
+            lib.oracle_subsample_key.restype = ctypes.c_uint64
             lib.oracle_render.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                           P, P, u32, P, i32, f32, f32, P, i32, P,
                                           ctypes.c_int64, P, P, i32]
             lib.oracle_render.restype = i32
             lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                                P, P, u32, P, i32, f32, f32, P, i32, P,
-                                               ctypes.c_int64, P, P, i32, u32, u32]
+                                               ctypes.c_int64, P, P, i32, u32, u32, P, P, u32]
             lib.oracle_render_pass.restype = i32
             lib.oracle_jitter.argtypes = [u32, u32, ctypes.c_uint64]
             lib.oracle_jitter.restype = f32
@@ -96,6 +101,18 @@ def _vol(vol) -> np.ndarray:
     return vol
 
 
+POS_X, POS_Y, POS_Z, POS_R = 0, 1, 2, 3
+POS_AXIS_BASE = 8          # PC axis id of position axis a is 8 + a
+
+
+def _pos(pos):
+    """Position brush (lo[4], hi[4], mask) over the axes x, y, z, radius; None = unrestricted."""
+    if pos is None:
+        return np.full(4, -np.inf, np.float32), np.full(4, np.inf, np.float32), 0
+    lo, hi, mask = pos
+    return _f32(lo).reshape(4), _f32(hi).reshape(4), int(mask) & 0xF
+
+
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
@@ -111,8 +128,10 @@ def brick_minmax(vol, bs: int = BRICK):
     return mn, mx
 
 
-def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask, bs: int = BRICK):
-    """Active and skippable flags (uint8 [nb,nb,nb]) of bricks of edge bs from their min/max and a brush."""
+def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask, bs: int = BRICK, pos=None):
+    """Active and skippable flags (uint8 [nb,nb,nb]) of bricks of edge bs from their min/max, a brush
+    and an optional position brush pos = (lo[4], hi[4], mask)."""
+    plo, phi, pmask = _pos(pos)
     bmin, bmax = _f32(bmin), _f32(bmax)
     V = bmin.shape[-1]
     nb = bmin.shape[0]
@@ -120,7 +139,8 @@ def classify(bmin, bmax, n, r_in, r_out, lo, hi, active_mask, bs: int = BRICK):
     act = np.empty((nb, nb, nb), np.uint8)
     skp = np.empty((nb, nb, nb), np.uint8)
     _load().oracle_classify(_ptr(bmin), _ptr(bmax), n, V, int(bs), np.float32(r_in), np.float32(r_out),
-                            _ptr(lo), _ptr(hi), int(active_mask) & 0xFFFFFFFF, _ptr(act), _ptr(skp))
+                            _ptr(lo), _ptr(hi), int(active_mask) & 0xFFFFFFFF, _ptr(plo), _ptr(phi), pmask,
+                            _ptr(act), _ptr(skp))
     return act, skp
 
 
@@ -155,8 +175,10 @@ def shell_bounds(n, r_in, r_out):
     return int(a[0]), int(b[0])
 
 
-def histogram(vol, r_in, r_out, lo, hi, active_mask, axis_order, edges, use_brush=True):
-    """Adjacent-axis PC histograms -> (uint32 [naxes-1, bins, bins], counted cells)."""
+def histogram(vol, r_in, r_out, lo, hi, active_mask, axis_order, edges, use_brush=True, pos=None):
+    """Adjacent-axis PC histograms -> (uint32 [naxes-1, bins, bins], counted cells). Axis ids
+    0..nvars-1 are stored variables, 8 + a position axis a (x, y, z, radius at the cell centre)."""
+    plo, phi, pmask = _pos(pos)
     v = _vol(vol)
     V, n = v.shape[0], v.shape[1]
     edges = _f32(edges)
@@ -167,9 +189,36 @@ def histogram(vol, r_in, r_out, lo, hi, active_mask, axis_order, edges, use_brus
     cells = np.zeros(1, np.uint64)
     _load().oracle_histogram(_ptr(v), n, V, np.float32(r_in), np.float32(r_out),
                              _ptr(_f32(lo)), _ptr(_f32(hi)), int(active_mask) & 0xFFFFFFFF,
+                             _ptr(plo), _ptr(phi), pmask,
                              int(bool(use_brush)), _ptr(order), naxes, bins, _ptr(edges),
                              _ptr(out), _ptr(cells))
     return out, int(cells[0])
+
+
+def pc_subsample(vol, r_in, r_out, lo, hi, active_mask, seed, k, axis_order, pos=None):
+    """PC line data: the min(k, N) in-shell cells with the smallest subsample keys, in increasing
+    cell index -> (int64 cells [m], float32 values [m, naxes], uint8 in_brush [m])."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    plo, phi, pmask = _pos(pos)
+    order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32))
+    naxes = order.shape[0]
+    cap = max(0, min(int(k), n ** 3))
+    cells = np.zeros(max(cap, 1), np.int64)
+    vals = np.zeros((max(cap, 1), max(naxes, 1)), np.float32)
+    flags = np.zeros(max(cap, 1), np.uint8)
+    m = _load().oracle_pc_subsample(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(_f32(lo)),
+                                    _ptr(_f32(hi)), int(active_mask) & 0xFFFFFFFF, _ptr(plo), _ptr(phi),
+                                    pmask, int(seed) & 0xFFFFFFFF, cap, _ptr(order), naxes,
+                                    _ptr(cells), _ptr(vals), _ptr(flags))
+    if m < 0:
+        raise ValueError("oracle_pc_subsample: invalid arguments")
+    return cells[:m], vals[:m, :naxes], flags[:m]
+
+
+def subsample_key(seed, cell) -> int:
+    """Subsample key of cell index `cell` under `seed`."""
+    return int(_load().oracle_subsample_key(int(seed) & 0xFFFFFFFF, int(cell)))
 
 
 def jitter(seed, pass_, pix) -> float:
@@ -184,7 +233,7 @@ def splitmix64_output(z) -> int:
 
 def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
            tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0,
-           seed=0, pass_=0):
+           seed=0, pass_=0, pos=None):
     """Render (or render a subset of pixels) -> (rgba float64 [npix,4], counts uint32 [npix,2]).
 
     counts[:, 0] = lattice samples marched (entry to termination),
@@ -198,6 +247,7 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
     tf = _f32(tf_rgbs)
     assert tf.shape == (256, 4)
     bg = np.ascontiguousarray(np.asarray(bg, dtype=np.float64))
+    plo, phi, pmask = _pos(pos)
     if pixels is None:
         npix = w * h
         pix_ptr = None
@@ -212,7 +262,8 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
                                     int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
                                     np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
                                     pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads),
-                                    int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF)
+                                    int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF,
+                                    _ptr(plo), _ptr(phi), pmask)
     if rc != 0:
         raise ValueError("oracle_render: invalid arguments")
     if pixels is None:

@@ -19,7 +19,12 @@
  *     discarded when any restricted variable lies outside its brush bounds
  *     (Section 2.2), colour from a 1D transfer function, early termination;
  *   - adjacent-axis parallel-coordinates density histograms of the in-shell,
- *     in-brush cells (Section 2.1 PC data, Fig. 2).
+ *     in-brush cells (Section 2.1 PC data, Fig. 2);
+ *   - implicit position axes (x, y, z and radius of a sample or cell centre)
+ *     as brush and PC axes (Section 2.1 derived altitude, Section 3 cuts on
+ *     Cartesian coordinates);
+ *   - the random subsample of cells whose polylines the PC plot draws
+ *     (Section 2.1).
  *
  * Precision. Every continuous quantity (ray geometry for the colour value,
  * transfer-function lookup, opacity, compositing) is FP64. Every quantity that
@@ -92,6 +97,47 @@ void oracle_brick_minmax(const float *vol, int n, int nvars, int bs, float *out_
 /* 2^126 never deactivates a brick: a corner difference can overflow    */
 /* there and the interpolated value can be infinite. A brick is         */
 /* skippable when it and all its existing 26 neighbours are inactive.   */
+/* Implicit position axes (Section 2.1 derives altitude, Section 3 cuts   */
+/* the volume on Cartesian coordinates). Axis a of a point p: a = 0, 1, 2 */
+/* the coordinate p[a]; a = 3 the radius sqrtf(fmaf(z, z, fmaf(y, y,     */
+/* x * x))). A position brush restricts axis a (bit a of pmask) to       */
+/* plo[a] <= value <= phi[a]. In PC axis lists, axis id 8 + a names      */
+/* position axis a (ids 0..nvars-1 name stored variables).               */
+/* The position of a sample is its FP32 lattice point; that of a cell is */
+/* its centre, coordinate (float)(2i + 1 - n) / (float)n.                */
+/* ------------------------------------------------------------------ */
+static float sq3_f32(const float p[3]) {
+    return fmaf(p[2], p[2], fmaf(p[1], p[1], p[0] * p[0]));
+}
+
+static float pos_axis(const float p[3], int a) {
+    return a < 3 ? p[a] : sqrtf(sq3_f32(p));
+}
+
+static int pos_pass(const float p[3], const float *plo, const float *phi, uint32_t pmask) {
+    for (int a = 0; a < 4; a++) {
+        if (!((pmask >> a) & 1u)) continue;
+        float v = pos_axis(p, a);
+        if (!(v >= plo[a] && v <= phi[a])) return 0;
+    }
+    return 1;
+}
+
+static void cell_centre(int n, int x, int y, int z, float p[3]) {
+    p[0] = (float)(2 * x + 1 - n) / (float)n;
+    p[1] = (float)(2 * y + 1 - n) / (float)n;
+    p[2] = (float)(2 * z + 1 - n) / (float)n;
+}
+
+/* ------------------------------------------------------------------ */
+/* Brick classification. A brick is active iff its widened sample box   */
+/* meets the shell, every restricted variable's range can pass, and the */
+/* box can meet the position brush: for a = 0..2 the box's [l_a, h_a]   */
+/* meets [plo_a, phi_a]; for the radius sqrtf(far^2) >= plo_3 and        */
+/* sqrtf(near^2) <= phi_3 (near/far: the box's closest and farthest     */
+/* corner distances, squared with the same FP32 chain as a sample's).   */
+/* The squared-distance chain is monotone in each |coordinate| and       */
+/* sqrtf is monotone, so no sample of an inactive brick passes.          */
 /* Output: active[b], skippable[b] as bytes 0/1, b = (bz*nb+by)*nb+bx.  */
 /* ------------------------------------------------------------------ */
 static void brick_box_axis(int b, int nb, int n, int BRICK, float *lo, float *hi) {
@@ -106,7 +152,8 @@ static void brick_box_axis(int b, int nb, int n, int BRICK, float *lo, float *hi
 
 void oracle_classify(const float *bmin, const float *bmax, int n, int nvars, int bs,
                      float r_in, float r_out, const float *lo, const float *hi,
-                     uint32_t active_mask, uint8_t *active, uint8_t *skippable) {
+                     uint32_t active_mask, const float *plo, const float *phi, uint32_t pmask,
+                     uint8_t *active, uint8_t *skippable) {
     const int BRICK = bs;
     int nb = (n + BRICK - 1) / BRICK;
     float rin2 = r_in * r_in, rout2 = r_out * r_out;
@@ -115,15 +162,18 @@ void oracle_classify(const float *bmin, const float *bmax, int n, int nvars, int
             for (int bx = 0; bx < nb; bx++) {
                 int bc[3] = {bx, by, bz};
                 float nearc[3], farc[3];
+                int act = 1;
                 for (int a = 0; a < 3; a++) {
                     float l, h;
                     brick_box_axis(bc[a], nb, n, BRICK, &l, &h);
                     nearc[a] = (l > 0.0f) ? l : ((h < 0.0f) ? -h : 0.0f);
                     farc[a] = fmaxf(fabsf(l), fabsf(h));
+                    if (((pmask >> a) & 1u) && !(h >= plo[a] && l <= phi[a])) act = 0;
                 }
-                float near2 = fmaf(nearc[2], nearc[2], fmaf(nearc[1], nearc[1], nearc[0] * nearc[0]));
-                float far2 = fmaf(farc[2], farc[2], fmaf(farc[1], farc[1], farc[0] * farc[0]));
-                int act = (near2 <= rout2) && (far2 >= rin2);
+                float near2 = sq3_f32(nearc);
+                float far2 = sq3_f32(farc);
+                act = act && (near2 <= rout2) && (far2 >= rin2);
+                if (((pmask >> 3) & 1u) && !(sqrtf(far2) >= plo[3] && sqrtf(near2) <= phi[3])) act = 0;
                 size_t b = ((size_t)bz * nb + by) * nb + bx;
                 for (int v = 0; v < nvars && act; v++) {
                     if (!((active_mask >> v) & 1u)) continue;
@@ -250,8 +300,36 @@ static int bin_of(float v, const float *edges, int bins) {
     return c;
 }
 
+/* Value of PC axis id `axis` at cell (x, y, z): a stored variable, or  */
+/* (id 8 + a) position axis a at the cell centre.                         */
+static float cell_axis(const float *vol, int n, int axis, int x, int y, int z) {
+    if (axis < 8) return val(vol, n, axis, x, y, z);
+    float p[3];
+    cell_centre(n, x, y, z, p);
+    return pos_axis(p, axis - 8);
+}
+
+/* In-brush test of a cell: restricted stored values and the position    */
+/* brush at the cell centre.                                              */
+static int cell_in_brush(const float *vol, int n, int nvars, const float *lo, const float *hi,
+                         uint32_t active_mask, const float *plo, const float *phi, uint32_t pmask,
+                         int x, int y, int z) {
+    for (int v = 0; v < nvars; v++) {
+        if (!((active_mask >> v) & 1u)) continue;
+        float a = val(vol, n, v, x, y, z);
+        if (!(a >= lo[v] && a <= hi[v])) return 0;
+    }
+    if (pmask) {
+        float p[3];
+        cell_centre(n, x, y, z, p);
+        if (!pos_pass(p, plo, phi, pmask)) return 0;
+    }
+    return 1;
+}
+
 void oracle_histogram(const float *vol, int n, int nvars, float r_in, float r_out,
-                      const float *lo, const float *hi, uint32_t active_mask, int use_brush,
+                      const float *lo, const float *hi, uint32_t active_mask,
+                      const float *plo, const float *phi, uint32_t pmask, int use_brush,
                       const int *axis_order, int naxes, int bins, const float *edges,
                       uint32_t *out /* (naxes-1)*bins*bins */, uint64_t *out_cells) {
     int64_t s_in, s_out;
@@ -265,22 +343,85 @@ void oracle_histogram(const float *vol, int n, int nvars, float r_in, float r_ou
                 int64_t dx = 2 * x + 1 - n, dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
                 int64_t s = dx * dx + dy * dy + dz * dz;
                 if (s < s_in || s > s_out) continue;
-                int keep = 1;
-                if (use_brush)
-                    for (int v = 0; v < nvars; v++) {
-                        if (!((active_mask >> v) & 1u)) continue;
-                        float a = val(vol, n, v, x, y, z);
-                        if (!(a >= lo[v] && a <= hi[v])) { keep = 0; break; }
-                    }
-                if (!keep) continue;
+                if (use_brush && !cell_in_brush(vol, n, nvars, lo, hi, active_mask, plo, phi, pmask, x, y, z))
+                    continue;
                 cells++;
                 for (int a = 0; a < naxes; a++)
-                    b[a] = bin_of(val(vol, n, axis_order[a], x, y, z), edges + (size_t)a * (bins + 1), bins);
+                    b[a] = bin_of(cell_axis(vol, n, axis_order[a], x, y, z), edges + (size_t)a * (bins + 1), bins);
                 for (int p = 0; p + 1 < naxes; p++)
                     out[((size_t)p * bins + b[p]) * bins + b[p + 1]] += 1u;
             }
     free(b);
     if (out_cells) *out_cells = cells;
+}
+
+/* ------------------------------------------------------------------ */
+/* PC line data (Section 2.1: the plot draws the polylines of a random  */
+/* subsample of at most 100 000 cells). Among the in-shell cells (the    */
+/* histograms' integer test), take the min(k, N) cells with the          */
+/* smallest keys K(c) = SplitMix64 output at the state                   */
+/* (seed * 2^32 + 2^32 - 1) + (c + 1) * 0x9E3779B97F4A7C15, c =          */
+/* (z*n + y)*n + x (the progressive passes use the states of pass        */
+/* indices below 2^32 - 1). The output function is a bijection and the   */
+/* increment is odd, so keys are distinct and the subsample is exactly    */
+/* defined. Output in increasing c: the cell index, the values of the    */
+/* given PC axes (stored variables or position axes), and whether the    */
+/* cell passes the brush (stored values, position brush at the centre).  */
+/* Returns the number of cells written, or -1 on bad arguments.          */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t key; int64_t cell; } keyed_cell;
+
+static int by_key(const void *a, const void *b) {
+    uint64_t x = ((const keyed_cell *)a)->key, y = ((const keyed_cell *)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static int by_cell(const void *a, const void *b) {
+    int64_t x = ((const keyed_cell *)a)->cell, y = ((const keyed_cell *)b)->cell;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+uint64_t oracle_splitmix64_output(uint64_t z);
+
+uint64_t oracle_subsample_key(uint32_t seed, int64_t cell) {
+    uint64_t key = ((uint64_t)seed << 32) | 0xFFFFFFFFull;
+    return oracle_splitmix64_output(key + (uint64_t)(cell + 1) * 0x9E3779B97F4A7C15ULL);
+}
+
+int64_t oracle_pc_subsample(const float *vol, int n, int nvars, float r_in, float r_out,
+                            const float *lo, const float *hi, uint32_t active_mask,
+                            const float *plo, const float *phi, uint32_t pmask,
+                            uint32_t seed, int64_t k, const int *axis_order, int naxes,
+                            int64_t *out_cells, float *out_values, uint8_t *out_in_brush) {
+    if (n < 1 || k < 0 || naxes < 0) return -1;
+    int64_t s_in, s_out;
+    oracle_shell_bounds(n, r_in, r_out, &s_in, &s_out);
+    int64_t ncell = (int64_t)n * n * n, cnt = 0;
+    keyed_cell *all = (keyed_cell *)malloc(sizeof(keyed_cell) * (size_t)(ncell > 0 ? ncell : 1));
+    if (!all) return -1;
+    for (int z = 0; z < n; z++)
+        for (int y = 0; y < n; y++)
+            for (int x = 0; x < n; x++) {
+                int64_t dx = 2 * x + 1 - n, dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
+                int64_t s = dx * dx + dy * dy + dz * dz;
+                if (s < s_in || s > s_out) continue;
+                int64_t c = ((int64_t)z * n + y) * n + x;
+                all[cnt].key = oracle_subsample_key(seed, c);
+                all[cnt].cell = c;
+                cnt++;
+            }
+    qsort(all, (size_t)cnt, sizeof(keyed_cell), by_key);
+    int64_t m = k < cnt ? k : cnt;
+    qsort(all, (size_t)m, sizeof(keyed_cell), by_cell);
+    for (int64_t i = 0; i < m; i++) {
+        int64_t c = all[i].cell;
+        int x = (int)(c % n), y = (int)((c / n) % n), z = (int)(c / ((int64_t)n * n));
+        out_cells[i] = c;
+        for (int a = 0; a < naxes; a++) out_values[i * naxes + a] = cell_axis(vol, n, axis_order[a], x, y, z);
+        out_in_brush[i] = (uint8_t)cell_in_brush(vol, n, nvars, lo, hi, active_mask, plo, phi, pmask, x, y, z);
+    }
+    free(all);
+    return m;
 }
 
 /* ------------------------------------------------------------------ */
@@ -295,6 +436,8 @@ typedef struct {
     float dt;
     const float *lo, *hi;
     uint32_t active_mask;
+    const float *plo, *phi; /* position brush (axes x, y, z, radius) */
+    uint32_t pmask;
     const float *tf;        /* 256 x (r,g,b,sigma) */
     int color_var;
     float tf_lo, tf_hi;
@@ -485,6 +628,7 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
             for (int a = 0; a < 3; a++) p[a] = fmaf(t, r.d[a], r.o[a]);
             float r2 = dot_f32(p, p);
             if (!(r2 >= rin2 && r2 <= rout2)) continue;
+            if (J->pmask && !pos_pass(p, J->plo, J->phi, J->pmask)) continue;
             int i0[3];
             float f[3];
             for (int a = 0; a < 3; a++) grid_coord32(p[a], J->n, &i0[a], &f[a]);
@@ -547,10 +691,12 @@ int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_o
                        const float *lo, const float *hi, uint32_t active_mask,
                        const float *tf, int color_var, float tf_lo, float tf_hi,
                        const double *bg, int ert, const int64_t *pixels, int64_t npix,
-                       double *out, uint32_t *counts, int nthreads, uint32_t seed, uint32_t pass) {
+                       double *out, uint32_t *counts, int nthreads, uint32_t seed, uint32_t pass,
+                       const float *plo, const float *phi, uint32_t pmask) {
     if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
     render_job J;
     J.seed = seed; J.pass = pass;
+    J.plo = plo; J.phi = phi; J.pmask = pmask;
     J.vol = vol; J.n = n; J.nvars = nvars; J.r_in = r_in; J.r_out = r_out;
     J.cam = cam; J.w = w; J.h = h; J.dt = dt; J.lo = lo; J.hi = hi;
     J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
@@ -575,7 +721,8 @@ int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
                   const double *bg, int ert, const int64_t *pixels, int64_t npix,
                   double *out, uint32_t *counts, int nthreads) {
     return oracle_render_pass(vol, n, nvars, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf, color_var,
-                              tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u);
+                              tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u,
+                              NULL, NULL, 0u);
 }
 
 int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }

@@ -763,3 +763,232 @@ def test_jittered_lattice_count_is_unbiased():
     assert abs(counts.mean() - x) < 5 * 0.5 / np.sqrt(counts.size), counts.mean()
     _, c0 = oracle.render(vol, 0.0, 1.0, cam, 1, 1, dt, lo, hi, 0, tf, 0, 0.0, 1.0, ert=False)
     assert int(c0[0, 0, 0]) == 30                       # the fixed lattice: round(30.35)
+
+
+# ----------------------------------------------------------------------------
+# implicit position axes (x, y, z, radius) and the PC line subsample
+# ----------------------------------------------------------------------------
+def _sqrt_f32(x: float) -> float:
+    """Correctly rounded float32 square root of a float32 x, decided with exact rationals:
+    of two neighbouring floats f < g, f is nearer to sqrt(x) iff x < ((f + g) / 2)^2."""
+    if x == 0:
+        return 0.0
+    c = np.float32(np.sqrt(np.float64(x)))
+    X = Fraction(float(x))
+    for _ in range(4):
+        lo = np.nextafter(c, np.float32(-np.inf))
+        hi = np.nextafter(c, np.float32(np.inf))
+        if X < ((Fraction(float(lo)) + Fraction(float(c))) / 2) ** 2:
+            c = lo
+        elif X > ((Fraction(float(c)) + Fraction(float(hi))) / 2) ** 2:
+            c = hi
+        else:
+            return float(c)
+    raise AssertionError("no convergence")
+
+
+def _centre_axes_exact(n):
+    """Exact FP32 position axes of every cell centre: x, y, z = RN((2i+1-n)/n) and
+    radius = sqrtf(RN(z*z + RN(y*y + RN(x*x)))), each step rounded from exact rationals."""
+    co = [_round_f32(Fraction(2 * i + 1 - n, n)) for i in range(n)]
+    sq = {}
+    r = np.zeros((n, n, n), np.float32)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                key = (abs(co[x]), abs(co[y]), abs(co[z]))
+                if key not in sq:
+                    a = _round_f32(Fraction(co[x]) ** 2)
+                    b = _round_f32(Fraction(co[y]) ** 2 + Fraction(a))
+                    c = _round_f32(Fraction(co[z]) ** 2 + Fraction(b))
+                    sq[key] = _sqrt_f32(c)
+                r[z, y, x] = sq[key]
+    c = np.array(co, np.float32)
+    X = np.broadcast_to(c[None, None, :], (n, n, n))
+    Y = np.broadcast_to(c[None, :, None], (n, n, n))
+    Z = np.broadcast_to(c[:, None, None], (n, n, n))
+    return [X, Y, Z, r]
+
+
+@pytest.mark.parametrize("n", [12, 13])
+def test_position_axes_and_brush_of_cells_exact(n):
+    vol = synth.make_shell_volume(n, seed=6).numpy()
+    axes = _centre_axes_exact(n)
+    order = [8 + 0, 8 + 3, 2, 8 + 2]            # x, radius, stored variable 2, z
+    vals = [axes[0], axes[3], vol[2], axes[2]]
+    bins = 7
+    edges = np.stack([np.linspace(-0.9, 0.9, bins + 1), np.linspace(0.5, 1.0, bins + 1),
+                      np.linspace(vol[2].min(), vol[2].max(), bins + 1),
+                      np.linspace(-0.8, 0.8, bins + 1)]).astype(np.float32)
+    # the position brush: x in [centre 2, centre n-3], radius in [0.62, the radius of
+    # cell (1, n//2, n//2)] (bounds that cells sit on exactly), z unrestricted
+    plo = np.float32([axes[0][0, 0, 2], -np.inf, -np.inf, 0.62])
+    phi = np.float32([axes[0][0, 0, n - 3], np.inf, np.inf, axes[3][n // 2, n // 2, 1]])
+    pos = (plo, phi, 0b1001)
+    lo = np.full(6, -np.inf, np.float32)
+    hi = np.full(6, np.inf, np.float32)
+    lo[1], hi[1] = np.quantile(vol[1], 0.2), np.quantile(vol[1], 0.9)
+    keep = _cells_in_shell_exact(n, R_IN, R_OUT) & (vol[1] >= lo[1]) & (vol[1] <= hi[1])
+    keep &= (axes[0] >= plo[0]) & (axes[0] <= phi[0]) & (axes[3] >= plo[3]) & (axes[3] <= phi[3])
+    H, cells = oracle.histogram(vol, R_IN, R_OUT, lo, hi, 0b10, order, edges, use_brush=True, pos=pos)
+    assert cells == int(keep.sum()) > 0
+    b = [np.searchsorted(edges[a, 1:bins], vals[a][keep], side="right") for a in range(4)]
+    for p in range(3):
+        want = np.zeros((bins, bins), np.int64)
+        np.add.at(want, (b[p], b[p + 1]), 1)
+        assert np.array_equal(H[p].astype(np.int64), want), p
+    # the same cells as PC lines: values and brush flags
+    cells_all, v_all, f_all = oracle.pc_subsample(vol, R_IN, R_OUT, lo, hi, 0b10, 3, n ** 3, order, pos=pos)
+    ins = _cells_in_shell_exact(n, R_IN, R_OUT).reshape(-1)
+    assert np.array_equal(cells_all, np.flatnonzero(ins))
+    for a in range(4):
+        assert np.array_equal(v_all[:, a], vals[a].reshape(-1)[cells_all]), a
+    assert np.array_equal(f_all.astype(bool), keep.reshape(-1)[cells_all])
+
+
+def _render_pos(vol, pos, w=36, h=30, cam=None, tf=None, ert=False):
+    n = vol.shape[1]
+    if tf is None:
+        tf = tf_const((1, 1, 1), 2.0)
+    cam = cam or synth.orbit_camera(35, 25, 3.0)
+    lo, hi = np.full(vol.shape[0], -np.inf, np.float32), np.full(vol.shape[0], np.inf, np.float32)
+    return oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, lo, hi, 0, tf.rgbs, 0, 0.0, 1.0,
+                         ert=ert, pos=pos)
+
+
+def test_position_brush_partitions_the_samples():
+    """Per pixel, the kept samples with axis a <= m plus those with axis a >= the next float
+    above m are all kept samples (inclusive bounds, one FP32 value per sample)."""
+    vol = const_volume(24, nvars=1)
+    inf = np.inf
+    _, c_all = _render_pos(vol, None)
+    _, c_open = _render_pos(vol, (np.full(4, -inf, np.float32), np.full(4, inf, np.float32), 0xF))
+    assert np.array_equal(c_open, c_all)
+    for a, m in ((0, 0.1), (1, -0.23), (2, 0.4), (3, 0.8)):
+        m = np.float32(m)
+        m_up = np.nextafter(m, np.float32(inf))
+        lo_a, hi_a = np.full(4, -inf, np.float32), np.full(4, inf, np.float32)
+        hi_a[a] = m
+        _, c1 = _render_pos(vol, (lo_a, hi_a, 1 << a))
+        lo_b, hi_b = np.full(4, -inf, np.float32), np.full(4, inf, np.float32)
+        lo_b[a] = m_up
+        _, c2 = _render_pos(vol, (lo_b, hi_b, 1 << a))
+        assert np.array_equal(c1[..., 0], c_all[..., 0])          # marching is unchanged
+        assert np.array_equal(c1[..., 1] + c2[..., 1], c_all[..., 1]), a
+        assert c1[..., 1].sum() > 0 and c2[..., 1].sum() > 0
+    # an empty position brush keeps nothing
+    _, c0 = _render_pos(vol, (np.float32([1, -inf, -inf, -inf]), np.float32([0, inf, inf, inf]), 1))
+    assert c0[..., 1].sum() == 0
+
+
+def test_position_brush_matches_the_analytic_chord():
+    """Constant extinction inside shell AND radius band AND x slab: A = 1 - exp(-sigma L)."""
+    n = 64
+    sigma = 2.5
+    vol = const_volume(n, nvars=1)
+    tf = tf_const((1, 1, 1), sigma)
+    cam = synth.orbit_camera(70, 25, 3.0)
+    w = h = 40
+    r0, r1, x0, x1 = 0.68, 0.9, -0.3, 0.45
+    pos = (np.float32([x0, -np.inf, -np.inf, r0]), np.float32([x1, np.inf, np.inf, r1]), 0b1001)
+    img, _ = _render_pos(vol, pos, w, h, cam, tf)
+    eye, d = pixel_rays64(cam, w, h)
+    L = np.zeros((h, w))
+    for y in range(h):
+        for x in range(w):
+            dd = d[y, x]
+            b = eye @ dd
+            c2 = eye @ eye - b * b
+            if r1 ** 2 - c2 <= 0:
+                continue
+            sa = math.sqrt(r1 ** 2 - c2)
+            segs = [(-b - sa, -b + sa)]
+            if r0 ** 2 - c2 > 0:
+                si = math.sqrt(r0 ** 2 - c2)
+                segs = [(-b - sa, -b - si), (-b + si, -b + sa)]
+            tx = sorted([(x0 - eye[0]) / dd[0], (x1 - eye[0]) / dd[0]])
+            L[y, x] = sum(max(0.0, min(s1, tx[1]) - max(s0, tx[0])) for s0, s1 in segs)
+    A = 1 - np.exp(-sigma * L)
+    _, bimp = shell_chord(eye, d)
+    ok = (np.abs(bimp - r0) > 0.03) & (np.abs(bimp - r1) > 0.03)
+    assert np.max(np.abs(img[..., 3] - A)[ok]) <= sigma * 6.0 / n
+    assert np.mean(np.abs(img[..., 3] - A)[ok]) <= sigma * 1.0 / n
+    assert np.count_nonzero(L > 0.1) > 100
+
+
+@pytest.mark.parametrize("bs", [8, 4])
+def test_classify_position_bracket(bs):
+    n = 32
+    nb = n // bs
+    vol = np.zeros((1, n, n, n), np.float32)
+    mn, mx = oracle.brick_minmax(vol, bs)
+    x0, x1, r0, r1 = -0.2, 0.35, 0.7, 0.85
+    pos = (np.float32([x0, -np.inf, -np.inf, r0]), np.float32([x1, np.inf, np.inf, r1]), 0b1001)
+    act, _ = oracle.classify(mn, mx, n, R_IN, R_OUT, np.float32([-1]), np.float32([1]), 0, bs=bs, pos=pos)
+    axes = _centre_axes_exact(n)
+    passing = (_cells_in_shell_exact(n, R_IN, R_OUT) & (axes[0] >= np.float32(x0)) & (axes[0] <= np.float32(x1))
+               & (axes[3] >= np.float32(r0)) & (axes[3] <= np.float32(r1)))
+    # necessary: every brick holding a passing cell centre is active
+    holds = passing.reshape(nb, bs, nb, bs, nb, bs).any(axis=(1, 3, 5))
+    assert np.all(act[holds] == 1)
+    # sufficient: a brick whose sample box misses the x slab or the radius band by 0.01 is inactive
+    c = lambda b: ((bs * b + 0.5) * 2 / n - 1, (bs * b + bs + 0.5) * 2 / n - 1)
+    for bz in range(nb):
+        for by in range(nb):
+            for bx in range(nb):
+                boxes = [c(b) for b in (bx, by, bz)]
+                boxes = [(-2 if b == 0 else l, 2 if b == nb - 1 else h)
+                         for (l, h), b in zip(boxes, (bx, by, bz))]
+                near = math.sqrt(sum(0 if l <= 0 <= h else min(abs(l), abs(h)) ** 2 for l, h in boxes))
+                far = math.sqrt(sum(max(abs(l), abs(h)) ** 2 for l, h in boxes))
+                (lx, hx) = boxes[0]
+                if hx < x0 - 0.01 or lx > x1 + 0.01 or near > r1 + 0.01 or far < r0 - 0.01:
+                    assert act[bz, by, bx] == 0
+    assert 0 < act.sum() < act.size
+
+
+def test_pc_subsample_takes_the_smallest_keys_in_cell_order():
+    n = 10
+    vol = synth.make_shell_volume(n, seed=2).numpy()
+    ins = np.flatnonzero(_cells_in_shell_exact(n, R_IN, R_OUT).reshape(-1))
+    N = ins.size
+    seed = 77
+    keys = np.array([oracle.subsample_key(seed, int(c)) for c in ins], dtype=np.uint64)
+    assert np.unique(keys).size == N                                  # distinct keys
+    by_key = ins[np.argsort(keys, kind="stable")]
+    lo, hi = ALL_IN
+    prev = None
+    for k in (0, 1, 7, 100, N - 1, N, N + 5):
+        cells, vals, flags = oracle.pc_subsample(vol, R_IN, R_OUT, lo, hi, 0, seed, k, [0, 8 + 1])
+        assert cells.size == min(k, N)
+        assert np.array_equal(cells, np.sort(by_key[:min(k, N)]))
+        assert np.all(np.diff(cells) > 0)
+        assert np.array_equal(vals[:, 0], vol[0].reshape(-1)[cells])
+        assert np.all(flags == 1)                                     # no brush: every line passes
+        if prev is not None:
+            assert np.all(np.isin(prev, cells))                       # nested in k
+        prev = cells
+
+
+def test_pc_subsample_is_uniform_and_pairwise_independent():
+    """Over seeds, each in-shell cell is drawn with probability k/N, and two cells
+    together with probability about k(k-1)/(N(N-1))."""
+    n = 8
+    vol = np.zeros((1, n, n, n), np.float32)
+    ins = np.flatnonzero(_cells_in_shell_exact(n, R_IN, R_OUT).reshape(-1))
+    N, k, S = ins.size, 40, 3000
+    lo, hi = np.float32([-np.inf]), np.float32([np.inf])
+    hits = np.zeros(n ** 3, np.int64)
+    pair = 0
+    a, b = int(ins[0]), int(ins[N // 2])
+    for s in range(S):
+        cells, _, _ = oracle.pc_subsample(vol, R_IN, R_OUT, lo, hi, 0, s, k, [0])
+        hits[cells] += 1
+        pair += int(a in cells and b in cells)
+    assert hits[np.setdiff1d(np.arange(n ** 3), ins)].sum() == 0       # only in-shell cells
+    p = k / N
+    obs = hits[ins]
+    chi2 = float(np.sum((obs - S * p) ** 2 / (S * p * (1 - p))))
+    assert chi2 < N + 5 * math.sqrt(2 * N), (chi2, N)                 # about N +- sqrt(2N)
+    q = k * (k - 1) / (N * (N - 1))
+    assert abs(pair - S * q) < 5 * math.sqrt(S * q), (pair, S * q)
