@@ -313,6 +313,37 @@ def run_ours(args):
                    "what": "1024^2 passes of the resting view; rms against one render at 1/8 of the step"}
     del acc, pimg, fine, fixed
 
+    # ---- position axes (brush and PC axis) and the PC line subsample ----
+    pos = (np.float32([-0.5, -np.inf, -np.inf, 0.6]), np.float32([0.5, np.inf, np.inf, 0.95]), 0b1001)
+    porder = [rp.AXIS_POS(rp.POS_R)] + list(c["order"][:4])
+    pedges = np.concatenate([np.linspace(0.5, 1.0, c["bins"] + 1, dtype=np.float32)[None], wl.edges[:4]])
+    vol.set_position_brush(*pos)
+    pstats.zero_()
+    reps = 10
+    q0, q1, q2, q3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    torch.cuda.synchronize()
+    q0.record()
+    for _ in range(reps):
+        vol.render(wl.cam, c["w"], c["h"], out=img, stats=pstats)
+    q1.record()
+    for _ in range(reps):
+        vol.pc_histogram(porder, pedges, use_brush=True, out=H[:4])
+    q2.record()
+    for _ in range(reps):
+        sub_cells, _, sub_flags = vol.pc_subsample(3, 100000, c["order"])
+    q3.record()
+    torch.cuda.synchronize()
+    vol.set_position_brush(np.zeros(4), np.zeros(4), 0)
+    n_shell = int(synth.in_shell_mask_approx(c["n"]).sum())
+    position = {"render_ms": round(q0.elapsed_time(q1) / reps, 4),
+                "render_samples_per_s": round(float(pstats[0].item()) / (q0.elapsed_time(q1) / 1e3), 1),
+                "histogram_ms": round(q1.elapsed_time(q2) / reps, 4),
+                "subsample_ms": round(q2.elapsed_time(q3) / reps, 4),
+                "subsample_lines": int(sub_cells.numel()), "subsample_lines_in_brush": int(sub_flags.sum()),
+                "subsample_in_shell_cells_per_s": round(n_shell / (q2.elapsed_time(q3) / reps / 1e3), 1),
+                "what": "x in [-0.5, 0.5] and radius in [0.6, 0.95] on top of the brush: 1024^2 render, "
+                        "4 histograms with the radius as first axis, 100 000-cell PC line subsample"}
+
     # ---- end to end through the C ABI from pinned host buffers ----
     # Every step copies its volume host -> device (pinned source) and reads its
     # image and histograms back device -> host. The copy of step i+1 runs on a
@@ -413,6 +444,7 @@ def run_ours(args):
                        "samples_per_s": round(float(fstats[0].item()) / (frame_ms * nframes / 1e3), 1),
                        "what": "brush edit + 1024^2 render + 5 PC histograms, volume resident"},
         "progressive": progressive,
+        "position_axes": position,
         "e2e": {"value": round(e2e_all / (e2e_max_ms / 1e3), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3),

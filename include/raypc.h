@@ -72,6 +72,21 @@ typedef int raypc_status;
 #define RAYPC_STAT_ERT 5          /* rays ended by early ray termination        */
 #define RAYPC_NSTATS 8
 
+/* Implicit position axes (Section 2.1 derives altitude from the position;
+ * Section 3 cuts the volume by brushing Cartesian coordinates). Axis a of a
+ * point p: RAYPC_POS_X/Y/Z the coordinate, RAYPC_POS_R the radius
+ * sqrt_rn(fma(z, z, fma(y, y, x * x))) (altitude is r_out minus it), all in
+ * FP32. A sample's point is its lattice position; a cell's is its centre,
+ * coordinate RN((2i + 1 - n) / n). In PC axis lists (raypc_pc_histogram,
+ * raypc_pc_subsample) RAYPC_AXIS_POS(a) names position axis a; ids
+ * 0..nvars-1 name stored variables. */
+#define RAYPC_POS_X 0
+#define RAYPC_POS_Y 1
+#define RAYPC_POS_Z 2
+#define RAYPC_POS_R 3
+#define RAYPC_NPOS 4
+#define RAYPC_AXIS_POS(a) (8 + (a))
+
 typedef struct raypc_ctx raypc_ctx;
 
 /* Pinhole camera. The view direction is normalize(target - eye); right =
@@ -192,6 +207,23 @@ raypc_status raypc_build_bricks(raypc_ctx *ctx, int vol, int brick_dim, int n_lo
 raypc_status raypc_set_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
                              uint32_t active_mask, void *stream);
 
+/* Set the position brush of a volume: position axis a (RAYPC_POS_*) is
+ * restricted iff bit a of pos_mask is set, to lo[a] <= value <= hi[a]
+ * (inclusive; NaN bounds rejected; lo > hi is a legal empty range; lo, hi:
+ * host arrays of RAYPC_NPOS floats, read only for restricted axes, may be
+ * NULL when pos_mask is 0). A sample (render) or cell (histograms with
+ * use_brush, subsample flags) must pass it as well as the variable brush of
+ * raypc_set_brush, which leaves the position brush unchanged (and this call
+ * leaves the variable brush unchanged; before any raypc_set_brush no
+ * variable is restricted). Bricks and sub-bricks are re-classified as by
+ * raypc_set_brush, with one more condition: the widened sample box meets
+ * every restricted coordinate range, and for the radius sqrt_rn(far^2) >= lo
+ * and sqrt_rn(near^2) <= hi (far/near: the box's farthest and nearest
+ * corner distances, squared like a sample's), so no passing sample lies in an
+ * inactive brick. pos_mask bits >= RAYPC_NPOS are rejected. */
+raypc_status raypc_set_position_brush(raypc_ctx *ctx, int vol, const float *lo, const float *hi,
+                                      uint32_t pos_mask, void *stream);
+
 /* Set the 1D transfer function (Section 3 and Fig. 4: colour by one chosen
  * variable). rgbs: host array of 256 x (r, g, b, sigma); sigma is the
  * extinction per world unit. The colour variable's value v maps to the
@@ -208,7 +240,8 @@ raypc_status raypc_set_tf(raypc_ctx *ctx, int vol, const float *rgbs, int color_
  * premultiplied RGBA, 16-byte aligned, caller-owned). Per pixel the ray enters
  * the sphere r_out at t0 (or starts at the eye when inside) and leaves at t1;
  * lattice samples sit at t_k = t0 + (k + 1/2) * step for t_k < t1. A sample is
- * kept iff r_in^2 <= |p|^2 <= r_out^2 and every restricted variable's FP32
+ * kept iff r_in^2 <= |p|^2 <= r_out^2, p passes the position brush
+ * (raypc_set_position_brush) and every restricted variable's FP32
  * trilinear value (clamped cell-centred interpolation, lerps along x, then y,
  * then z, each as fma(f, b - a, a)) lies in the brush. Kept samples take
  * (r, g, b, sigma) from the transfer function, alpha = 1 - exp(-sigma * step),
@@ -268,6 +301,9 @@ typedef struct raypc_view {
     raypc_render_opts opts;
     float *out_rgba_dev;
     unsigned long long *stats_dev;
+    float pos_lo[RAYPC_NPOS];    /* this view's position brush (raypc_set_position_brush meaning) */
+    float pos_hi[RAYPC_NPOS];
+    uint32_t pos_mask;
 } raypc_view;
 
 typedef struct raypc_batch raypc_batch;
@@ -349,6 +385,9 @@ typedef struct raypc_request {
     int naxes, bins;
     const float *edges;          /* host, naxes x (bins + 1); copied on submit     */
     int use_brush;
+    float pos_lo[RAYPC_NPOS];    /* the request's position brush                   */
+    float pos_hi[RAYPC_NPOS];
+    uint32_t pos_mask;
 } raypc_request;
 
 typedef struct raypc_result {
@@ -412,17 +451,42 @@ raypc_status raypc_get_tuning(raypc_ctx *ctx, int dtype, int n, raypc_tuning *ou
 /* ---------------------------------------------------------------------- */
 
 /* Density histograms of adjacent parallel-coordinates axes. axis_order: host
- * array of naxes (2..8) variable indices; edges: host array of naxes rows of
+ * array of naxes (2..8) axis ids (stored variables, or RAYPC_AXIS_POS(a) for
+ * the position axes at the cell centre); edges: host array of naxes rows of
  * bins+1 floats (non-decreasing, no NaN); bins in 2..1024. A cell counts iff
  * its centre is in the shell -- S_in <= sum_a (2 i_a + 1 - n)^2 <= S_out with
  * S_in = ceil((r_in n)^2), S_out = floor((r_out n)^2) in double -- and, when
- * use_brush is nonzero, its stored values pass the brush. Its bin on axis a is
+ * use_brush is nonzero, its stored values pass the brush and its centre the
+ * position brush. Its bin on axis a is
  * the number of interior edges e_1..e_{bins-1} of row a that are <= its value.
  * out_counts_dev ([naxes-1][bins][bins] uint32, caller-owned) is zeroed and
  * filled: H[p][bin_p][bin_{p+1}] counts cells. Counts are exact integers. */
 raypc_status raypc_pc_histogram(raypc_ctx *ctx, int vol, int lod, const int *axis_order,
                                 int naxes, int bins, const float *edges, int use_brush,
                                 uint32_t *out_counts_dev, void *stream);
+
+/* PC line data (Section 2.1: the plot draws the polylines of a random
+ * subsample of at most 100 000 cells). Among the in-shell cells of level lod
+ * (the histograms' integer test), N of them, takes the m = min(k, N) cells
+ * with the smallest keys K(c): the output of SplitMix64's output function
+ * (Steele, Lea and Flood 2014) at the state
+ * (seed * 2^32 + 2^32 - 1) + (c + 1) * 0x9E3779B97F4A7C15 mod 2^64,
+ * c = (z * n + y) * n + x. Keys are distinct (the output function is a
+ * bijection), so the subsample is exactly defined; across seeds it is a
+ * uniform random m-subset. Writes, in increasing c, out_cells_dev[i] = c
+ * (int64, 8-byte aligned), out_values_dev[i * naxes + a] = the value of PC
+ * axis axis_order[a] at the cell (float32; stored value, or position axis at
+ * the centre) and out_in_brush_dev[i] = 1 iff the cell passes the volume's
+ * brush (stored values and the position brush at the centre; 1 when no brush
+ * was set), 0 otherwise. All three are caller-owned device arrays of at least
+ * m entries (m x naxes values). *out_count (host) receives m when the call
+ * returns, before the stream has run. k in 0..2^31-1; naxes 0..8 (axis_order
+ * may be NULL when naxes is 0). Reads no field data for the selection:
+ * an exact radix select over the keys, then an ordered compaction. */
+raypc_status raypc_pc_subsample(raypc_ctx *ctx, int vol, int lod, uint32_t seed, long long k,
+                                const int *axis_order, int naxes, long long *out_cells_dev,
+                                float *out_values_dev, uint8_t *out_in_brush_dev,
+                                long long *out_count, void *stream);
 
 /* Same histograms as raypc_pc_histogram, for callers that cannot let the
  * library allocate device memory: hosts whose GPU memory is reserved up front

@@ -296,7 +296,24 @@ raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, 
         b.hi[v] = hi[v];
     }
     b.mask = active_mask;
+    for (int a = 0; a < kNumPos; ++a) { b.plo[a] = -INFINITY; b.phi[a] = INFINITY; }
+    b.pmask = 0u;
     *out = b;
+    return RAYPC_OK;
+}
+
+raypc_status pos_from_host(const float* lo, const float* hi, uint32_t pos_mask, BrushArgs* b) {
+    if (pos_mask >> kNumPos) return fail(RAYPC_ERR_INVALID_ARG, "pos_mask 0x%x names axes >= %d", pos_mask, kNumPos);
+    for (int a = 0; a < kNumPos; ++a) { b->plo[a] = -INFINITY; b->phi[a] = INFINITY; }
+    b->pmask = pos_mask;
+    if (!pos_mask) return RAYPC_OK;
+    if (!lo || !hi) return fail(RAYPC_ERR_INVALID_ARG, "NULL position bounds");
+    for (int a = 0; a < kNumPos; ++a) {
+        if (!((pos_mask >> a) & 1u)) continue;
+        if (isnan(lo[a]) || isnan(hi[a])) return fail(RAYPC_ERR_INVALID_ARG, "NaN bound for position axis %d", a);
+        b->plo[a] = lo[a];
+        b->phi[a] = hi[a];
+    }
     return RAYPC_OK;
 }
 
@@ -454,6 +471,20 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
     return RAYPC_OK;
 }
 
+// Re-classify every built level under the volume's (new) brush and compute the
+// cell classes of level 0.
+static raypc_status reclassify(raypc_ctx* ctx, Volume* V, cudaStream_t s) {
+    if (V->stale) {            // coarser levels are rebuilt by raypc_build_bricks, which classifies lazily
+        for (auto& L : V->lv) L.classified = L.cls_valid = false;
+        return RAYPC_OK;
+    }
+    raypc_status st = classify_all(V, s);
+    if (st) return st;
+    // the full-resolution level's cell classes now, so that a render runs its kernel
+    // alone (coarser levels get theirs when first rendered)
+    return ensure_cell_classes(ctx, V, V->lv[0], s);
+}
+
 raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const float* hi,
                              uint32_t active_mask, void* stream) {
     if (!ctx || !lo || !hi) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
@@ -464,16 +495,31 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
     if (st) return st;
     BrushArgs b{};
     if ((st = brush_from_host(V, lo, hi, active_mask, &b))) return st;
+    // the position brush stays as raypc_set_position_brush left it
+    for (int a = 0; a < kNumPos; ++a) { b.plo[a] = V->brush.plo[a]; b.phi[a] = V->brush.phi[a]; }
+    b.pmask = V->brush.pmask;
     V->brush = b;
     V->brush_set = true;
-    if (V->stale) {            // coarser levels are rebuilt by raypc_build_bricks, which classifies lazily
-        for (auto& L : V->lv) L.classified = L.cls_valid = false;
-        return RAYPC_OK;
+    return reclassify(ctx, V, (cudaStream_t)stream);
+}
+
+raypc_status raypc_set_position_brush(raypc_ctx* ctx, int vol, const float* lo, const float* hi,
+                                      uint32_t pos_mask, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    BrushArgs b = V->brush;
+    if (!V->brush_set) {           // no variable brush yet: nothing restricted
+        for (int v = 0; v < kMaxVars; ++v) { b.lo[v] = -INFINITY; b.hi[v] = INFINITY; }
+        b.mask = 0u;
     }
-    if ((st = classify_all(V, (cudaStream_t)stream))) return st;
-    // the full-resolution level's cell classes now, so that a render runs its kernel
-    // alone (coarser levels get theirs when first rendered)
-    return ensure_cell_classes(ctx, V, V->lv[0], (cudaStream_t)stream);
+    if ((st = pos_from_host(lo, hi, pos_mask, &b))) return st;
+    V->brush = b;
+    V->brush_set = true;
+    return reclassify(ctx, V, (cudaStream_t)stream);
 }
 
 raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_var, float v_lo,
@@ -553,6 +599,16 @@ raypc_status raypc_render_progressive(raypc_ctx* ctx, int vol, int lod, const ra
     return RAYPC_OK;
 }
 
+// PC axis ids: stored variables 0..nvars-1 and position axes RAYPC_AXIS_POS(0..3).
+static raypc_status check_axes(const Volume* V, const int* axis_order, int naxes) {
+    for (int a = 0; a < naxes; ++a) {
+        const int id = axis_order[a];
+        const bool ok = (id >= 0 && id < V->nvars) || (id >= kPosAxisBase && id < kPosAxisBase + kNumPos);
+        if (!ok) return fail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d", a, id);
+    }
+    return RAYPC_OK;
+}
+
 raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axis_order, int naxes,
                                 int bins, const float* edges, int use_brush, uint32_t* out_counts_dev,
                                 void* stream) {
@@ -572,8 +628,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     if (st) return st;
     Level* L;
     if ((st = get_level(V, lod, &L))) return st;
-    for (int a = 0; a < naxes; ++a)
-        if (axis_order[a] < 0 || axis_order[a] >= V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d", a, axis_order[a]);
+    if ((st = check_axes(V, axis_order, naxes))) return st;
     if (use_brush && !V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "use_brush needs raypc_set_brush");
     if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
     cudaStream_t s = (cudaStream_t)stream;
@@ -595,7 +650,8 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         h.guess_scale[a] = (eN > e0 && isfinite(eN - e0)) ? (float)bins / (eN - e0) : 0.0f;
     }
     h.need_mask = use_brush ? V->brush.mask : 0u;
-    for (int a = 0; a < naxes; ++a) h.need_mask |= 1u << axis_order[a];
+    for (int a = 0; a < naxes; ++a)
+        if (axis_order[a] < kPosAxisBase) h.need_mask |= 1u << axis_order[a];
     double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
     h.s_in = (int64_t)ceil(ri * ri);
     h.s_out = (int64_t)floor(ro * ro);
@@ -614,6 +670,87 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     }
     cudaFreeAsync(dedges, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
+    return RAYPC_OK;
+}
+
+// Number of cells whose centre offsets d = 2i + 1 - n satisfy s_in <= dx^2 + dy^2 + dz^2 <= s_out.
+static unsigned long long count_in_shell(int n, int64_t s_in, int64_t s_out) {
+    // cells of one row (fixed y, z) with dx^2 <= a: |2x + 1 - n| <= floor(sqrt(a))
+    auto upto = [n](int64_t a) -> int64_t {
+        if (a < 0) return 0;
+        int64_t m = (int64_t)sqrt((double)a);
+        while (m * m > a) --m;
+        while ((m + 1) * (m + 1) <= a) ++m;
+        const int64_t xa = std::max<int64_t>(0, (n - 1 - m + 1) / 2), xb = std::min<int64_t>(n - 1, (n - 1 + m) / 2);
+        return xb >= xa ? xb - xa + 1 : 0;
+    };
+    unsigned long long total = 0;
+    for (int z = 0; z < n; ++z)
+        for (int y = 0; y < n; ++y) {
+            const int64_t dy = 2 * y + 1 - n, dz = 2 * z + 1 - n, syz = dy * dy + dz * dz;
+            total += (unsigned long long)(upto(s_out - syz) - upto(s_in - 1 - syz));
+        }
+    return total;
+}
+
+raypc_status raypc_pc_subsample(raypc_ctx* ctx, int vol, int lod, uint32_t seed, long long k,
+                                const int* axis_order, int naxes, long long* out_cells_dev,
+                                float* out_values_dev, uint8_t* out_in_brush_dev, long long* out_count,
+                                void* stream) {
+    if (!ctx || !out_count) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (k < 0 || k > 0x7fffffffLL) return fail(RAYPC_ERR_INVALID_ARG, "k %lld not in 0..2^31-1", k);
+    if (naxes < 0 || naxes > RAYPC_MAX_VARS) return fail(RAYPC_ERR_INVALID_ARG, "naxes %d not in 0..%d", naxes, RAYPC_MAX_VARS);
+    if (naxes > 0 && !axis_order) return fail(RAYPC_ERR_INVALID_ARG, "NULL axis_order");
+    if (k > 0 && (!out_cells_dev || !out_in_brush_dev || (naxes > 0 && !out_values_dev)))
+        return fail(RAYPC_ERR_INVALID_ARG, "NULL output");
+    if (((uintptr_t)out_cells_dev) & 7u) return fail(RAYPC_ERR_INVALID_ARG, "out_cells_dev must be 8-byte aligned");
+    if (((uintptr_t)out_values_dev) & 3u) return fail(RAYPC_ERR_INVALID_ARG, "out_values_dev must be 4-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if ((st = check_axes(V, axis_order, naxes))) return st;
+    if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
+    const double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
+    const int64_t s_in = (int64_t)ceil(ri * ri), s_out = (int64_t)floor(ro * ro);
+    const unsigned long long N = s_out < 0 ? 0ull : count_in_shell(L->n, s_in, s_out);
+    const unsigned long long m = std::min<unsigned long long>((unsigned long long)k, N);
+    *out_count = (long long)m;
+    if (m == 0) return RAYPC_OK;
+    SubsampleArgs a{};
+    a.cells = L->cells;
+    a.n = L->n;
+    a.nvars = V->nvars;
+    const int64_t imax = 0x7fffffff;
+    a.s_in = (int)std::min<int64_t>(std::max<int64_t>(s_in, 0), imax);
+    a.s_out = (int)std::min<int64_t>(s_out, imax);
+    a.key = ((unsigned long long)seed << 32) | 0xFFFFFFFFull;
+    if (V->brush_set) {
+        a.brush = V->brush;
+    } else {
+        for (int v = 0; v < kMaxVars; ++v) { a.brush.lo[v] = -INFINITY; a.brush.hi[v] = INFINITY; }
+        for (int p = 0; p < kNumPos; ++p) { a.brush.plo[p] = -INFINITY; a.brush.phi[p] = INFINITY; }
+    }
+    a.naxes = naxes;
+    for (int i = 0; i < naxes; ++i) {
+        a.axis[i] = axis_order[i];
+        if (axis_order[i] >= kPosAxisBase) a.use_pos = 1;
+    }
+    if (a.brush.pmask) a.use_pos = 1;
+    a.m = m;
+    a.out_cells = out_cells_dev;
+    a.out_values = out_values_dev;
+    a.out_flags = out_in_brush_dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    // select state and per-block counts: a small device buffer owned by this call (freed in stream order)
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, pc_subsample_scratch_bytes(), s), "subsample scratch");
+    cudaError_t e = launch_pc_subsample(a, V->dtype, m, N, scratch, s);
+    cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pc subsample");
     return RAYPC_OK;
 }
 

@@ -62,18 +62,24 @@ __device__ __forceinline__ float trilerp_rn(float c000, float c100, float c010, 
     return lerp_rn(c0, c1, fz);
 }
 
-// Lattice offset of pixel index pix in progressive pass `pass` (Section 2:
-// passes keep refining the image while the camera rests): pass 0 uses 1/2 (the
-// fixed lattice t0 + (k + 1/2) dt); pass p >= 1 draws the offset from
-// SplitMix64 used as a counter-based generator -- its output function at the
-// state key + (pix + 1) * 0x9E3779B97F4A7C15, key = seed * 2^32 + p -- as the
-// top 24 bits of the output, a fraction in [0, 1).
-__device__ __forceinline__ float lattice_offset(uint32_t seed, uint32_t pass, unsigned long long pix) {
-    if (pass == 0u) return 0.5f;
-    unsigned long long z = ((((unsigned long long)seed) << 32) | pass) + (pix + 1ull) * 0x9E3779B97F4A7C15ull;
+// SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator: the
+// output function of the state key + (i + 1) * 0x9E3779B97F4A7C15 for stream
+// `key` and counter i. The output function is a bijection of 64-bit words.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long key, unsigned long long i) {
+    unsigned long long z = key + (i + 1ull) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
+    return z ^ (z >> 31);
+}
+
+// Lattice offset of pixel index pix in progressive pass `pass` (Section 2:
+// passes keep refining the image while the camera rests): pass 0 uses 1/2 (the
+// fixed lattice t0 + (k + 1/2) dt); pass p >= 1 takes the top 24 bits of
+// splitmix64_at(seed * 2^32 + p, pix) as a fraction in [0, 1). The stream
+// seed * 2^32 + 2^32 - 1 is reserved for the PC line subsample.
+__device__ __forceinline__ float lattice_offset(uint32_t seed, uint32_t pass, unsigned long long pix) {
+    if (pass == 0u) return 0.5f;
+    const unsigned long long z = splitmix64_at((((unsigned long long)seed) << 32) | pass, pix);
     return (float)(unsigned)(z >> 40) * 0x1p-24f;
 }
 
@@ -128,11 +134,41 @@ struct LevelArgs {
     const uint32_t* sactive;   // sub-brick bitmask, ceil(nsb^3/32) words
 };
 
+// Implicit position axes (x, y, z, radius) usable in brushes and as PC axes;
+// PC axis id kPosAxisBase + a names position axis a.
+constexpr int kNumPos = 4;
+constexpr int kPosAxisBase = 8;
+
 struct BrushArgs {
     float lo[kMaxVars];
     float hi[kMaxVars];
     uint32_t mask;
+    float plo[kNumPos];           // position brush: axis a restricted iff bit a of pmask
+    float phi[kNumPos];
+    uint32_t pmask;
 };
+
+// Position axis a of point (x, y, z) whose squared radius r2 =
+// dot3_rn(p, p) is known: the coordinate, or (a = 3) the radius sqrt_rn(r2).
+__device__ __forceinline__ float pos_axis(float x, float y, float z, float r2, int a) {
+    return a == 0 ? x : (a == 1 ? y : (a == 2 ? z : __fsqrt_rn(r2)));
+}
+
+// Whether a point passes the position brush (inclusive bounds, every restricted axis).
+__device__ __forceinline__ bool pos_pass(float x, float y, float z, float r2, const BrushArgs& b) {
+#pragma unroll
+    for (int a = 0; a < kNumPos; ++a) {
+        if (!((b.pmask >> a) & 1u)) continue;
+        const float v = pos_axis(x, y, z, r2, a);
+        if (!(v >= b.plo[a] && v <= b.phi[a])) return false;
+    }
+    return true;
+}
+
+// Centre coordinate of cell index i on an axis of n cells: RN((2i + 1 - n) / n).
+__device__ __forceinline__ float cell_centre_rn(int i, int n) {
+    return __fdiv_rn((float)(2 * i + 1 - n), (float)n);
+}
 
 struct RenderArgs {
     LevelArgs lv;
@@ -240,7 +276,8 @@ __device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, int bs, 
 // axis (sc = 2/n): active iff its widened sample box meets the shell and, for every
 // restricted v, max_v + d >= lo_v and min_v - d <= hi_v with
 // d = max(|min_v|, |max_v|) * 2^-20 + 2^-120 (covers FP32 interpolation
-// rounding). A variable with max(|min_v|, |max_v|) > 2^126 never deactivates
+// rounding), and the box meets the position brush. A variable with
+// max(|min_v|, |max_v|) > 2^126 never deactivates
 // a brick (a corner difference can overflow and the interpolated value be
 // infinite). pass_bits gets bit v set for each restricted variable the brick
 // passes on its own (only meaningful when the box meets the shell).
@@ -260,6 +297,19 @@ __device__ __forceinline__ bool classify_brick(size_t b, int nb, int bs, float s
     const float far2 = dot3_rn(farc[0], farc[1], farc[2], farc[0], farc[1], farc[2]);
     pass_bits = 0;
     if (!((near2 <= rout2) && (far2 >= rin2))) return false;
+    if (brush.pmask) {
+        // the box must meet every restricted coordinate range, and its radius range
+        // [sqrt(near2), sqrt(far2)] the radius range (dot3_rn is monotone in each |coordinate|)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!((brush.pmask >> a) & 1u)) continue;
+            float lo, hi;
+            brick_box_axis(c[a], nb, sc, bs, lo, hi);
+            if (!(hi >= brush.plo[a] && lo <= brush.phi[a])) return false;
+        }
+        if (((brush.pmask >> 3) & 1u) && !(__fsqrt_rn(far2) >= brush.plo[3] && __fsqrt_rn(near2) <= brush.phi[3]))
+            return false;
+    }
     bool all = true;
     for (int v = 0; v < nvars; ++v) {
         if (!((brush.mask >> v) & 1u)) continue;
@@ -446,5 +496,25 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
                                 int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream);
 int render_batch_blocks_per_sm(int dtype, int variant);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
+
+// PC line subsample (pcsub_kernels.cu).
+constexpr int kSubMaxBlocks = 1024;     // blocks of the ordered compaction
+struct SubsampleArgs {
+    const void* cells;            // planar level values, storage dtype
+    int n, nvars;
+    int s_in, s_out;              // integer shell test on (2x+1-n)^2 + ..., clamped to int
+    unsigned long long key;       // generator stream: seed * 2^32 + 2^32 - 1
+    BrushArgs brush;              // for the per-cell brush flag (mask 0 / pmask 0: no restriction)
+    int naxes;
+    int axis[kMaxVars];           // stored variable or kPosAxisBase + position axis
+    int use_pos;                  // position brush or a position axis in use
+    unsigned long long m;         // cells to write, min(k, in-shell cells) < 2^31
+    long long* out_cells;         // m
+    float* out_values;            // m x naxes
+    uint8_t* out_flags;           // m
+};
+size_t pc_subsample_scratch_bytes();
+cudaError_t launch_pc_subsample(const SubsampleArgs& a, int dtype, unsigned long long m, unsigned long long N,
+                                void* scratch, cudaStream_t stream);
 
 }  // namespace raypc

@@ -5,7 +5,8 @@
 // HBM-bound scan. A warp walks one x-row of cells (lanes over x, two cells per
 // lane in flight), so the planar loads are coalesced; rows whose cells all lie
 // outside the shell are skipped without touching memory, and a cell loads its
-// axis values only after its brushed values pass. With the volume's own brush
+// axis values only after its brushed values pass. Position axes and the
+// position brush use the cell centre, coordinate RN((2i + 1 - n) / n). With the volume's own brush
 // the cells of inactive 4^3 sub-bricks are skipped without loads: every
 // vertex of such a sub-brick fails the brush (its values lie between the
 // sub-brick's min and max) or lies outside the shell (the sub-brick's widened
@@ -55,7 +56,10 @@ struct HistLaunch {
     int bvar[kMaxVars];
     float blo[kMaxVars], bhi[kMaxVars];
     int naxes;
-    int avar[kMaxVars];            // variable of each axis
+    int avar[kMaxVars];            // variable of each axis, or kPosAxisBase + position axis
+    float plo[kNumPos], phi[kNumPos];
+    uint32_t pmask;                // position brush at the cell centre (0: none)
+    int use_pos;                   // the position brush or a position axis is in use
     const float* edges;            // naxes x (bins + 1), device
     float guess_e0[kMaxVars], guess_scale[kMaxVars];
     int s_in, s_out;               // shell test on 2x+1-n etc., clamped to int
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
     for (long long r = gwarp; r < rows; r += nwarps) {
         const int y = (int)(r % n), z = (int)(r / n);
         const int dy = 2 * y + 1 - n, dz = 2 * z + 1 - n;
+        const float cy = A.use_pos ? cell_centre_rn(y, n) : 0.0f, cz = A.use_pos ? cell_centre_rn(z, n) : 0.0f;
         const int syz = dy * dy + dz * dz;                  // < 2^31 for n <= 4096
         if (syz > A.s_out) continue;                        // whole row outside the outer sphere
         // x range of the row inside the outer sphere: |2x + 1 - n| <= m
@@ -93,10 +98,12 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
         // two cells per lane and iteration: their loads are in flight together
         for (int x0 = xa; x0 <= xb; x0 += 64) {
             bool keep[2];
+            float cx[2], cr2[2];           // centre x and squared radius (position axes)
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int x = x0 + lane + 32 * j;
                 keep[j] = false;
+                cx[j] = cr2[j] = 0.0f;
                 if (x <= xb) {
                     const int dx = 2 * x + 1 - n;
                     const int s = dx * dx + syz;
@@ -105,6 +112,17 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
                         // a vertex of an inactive sub-brick fails the brush or lies outside the shell
                         const uint32_t sid = srow + (uint32_t)(x >> 2);
                         keep[j] = (__ldg(A.sactive + (sid >> 5)) >> (sid & 31)) & 1u;
+                    }
+                    if (keep[j] && A.use_pos) {
+                        cx[j] = cell_centre_rn(x, n);
+                        cr2[j] = dot3_rn(cx[j], cy, cz, cx[j], cy, cz);
+                        if (A.pmask) {
+                            BrushArgs pb;
+#pragma unroll
+                            for (int a = 0; a < kNumPos; ++a) { pb.plo[a] = A.plo[a]; pb.phi[a] = A.phi[a]; }
+                            pb.pmask = A.pmask;
+                            keep[j] = pos_pass(cx[j], cy, cz, cr2[j], pb);
+                        }
                     }
                 }
             }
@@ -130,9 +148,12 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(HistLaunch A) {
             for (int a = 0; a < kMaxVars; ++a) {
                 if (a >= A.naxes) break;
                 float va[2];
+                const int av = A.avar[a];
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
-                    va[j] = keep[j] ? load_cell<DT>(A.cells, A.avar[a] * plane + row_base + x0 + lane + 32 * j) : 0.0f;
+                    va[j] = !keep[j] ? 0.0f
+                          : av >= kPosAxisBase ? pos_axis(cx[j], cy, cz, cr2[j], av - kPosAxisBase)
+                                               : load_cell<DT>(A.cells, av * plane + row_base + x0 + lane + 32 * j);
 #pragma unroll
                 for (int j = 0; j < 2; ++j)
                     bn[j][a] = keep[j] ? bin_of(s_edges + a * (bins + 1), bins, va[j], A.guess_e0[a], A.guess_scale[a]) : 0;
@@ -170,9 +191,15 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
                 a.bhi[a.nbr] = h.brush.hi[v];
                 ++a.nbr;
             }
+    if (h.use_brush && h.brush.pmask) {
+        for (int i = 0; i < kNumPos; ++i) { a.plo[i] = h.brush.plo[i]; a.phi[i] = h.brush.phi[i]; }
+        a.pmask = h.brush.pmask;
+        a.use_pos = 1;
+    }
     a.naxes = h.naxes;
     for (int i = 0; i < h.naxes && i < kMaxVars; ++i) {
         a.avar[i] = h.axis[i];
+        if (h.axis[i] >= kPosAxisBase) a.use_pos = 1;
         a.guess_e0[i] = h.guess_e0[i];
         a.guess_scale[i] = h.guess_scale[i];
     }

@@ -7,7 +7,7 @@
 // bit-identically alone and inside a batch. Per lattice sample: position,
 // interpolation cell (exactly rounded FP32), the activity bit of the 4^3
 // sub-brick that holds the cell (samples in inactive sub-bricks cannot pass
-// the brush or the shell test), shell test, then the restricted
+// the brush or the shell test), shell test, position brush, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
 // selective first; the order cannot change the result) that the sample's cell
 // class does not already decide, each as an FP32
@@ -244,6 +244,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 }
                 const float r2 = dot3_rn(pxw, pyw, pzw, pxw, pyw, pzw);
                 if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
+                if (A.brush.pmask && !pos_pass(pxw, pyw, pzw, r2, A.brush)) { ++k; continue; }
                 const size_t base = ((size_t)iz * n + iy) * n + ix;
                 const float nm1 = (float)(n - 1);
                 const float fx = grid_weight_rn(ux, ix, nm1), fy = grid_weight_rn(uy, iy, nm1), fz = grid_weight_rn(uz, iz, nm1);

@@ -110,8 +110,11 @@ void batch_last_records(raypc_batch* b, const ViewDone** records, unsigned* seq)
 // not current (allocates them on first use).
 raypc_status ensure_cell_classes(raypc_ctx* ctx, Volume* V, Level& L, cudaStream_t s);
 
-// Validated brush box of a volume from host arrays (nvars entries each).
+// Validated brush box of a volume from host arrays (nvars entries each); no position brush.
 raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, uint32_t active_mask, BrushArgs* out);
+
+// Validated position brush (axes x, y, z, radius; bounds read only for axes in pos_mask) into b.
+raypc_status pos_from_host(const float* lo, const float* hi, uint32_t pos_mask, BrushArgs* b);
 
 }  // namespace raypc
 

@@ -184,6 +184,7 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     if (V->stale && q->r.lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level is stale");
     BrushArgs b{};
     if ((st = brush_from_host(V, q->r.lo, q->r.hi, q->r.active_mask, &b))) return st;
+    if ((st = pos_from_host(q->r.pos_lo, q->r.pos_hi, q->r.pos_mask, &b))) return st;
     const int naxes = q->r.naxes, bins = q->r.bins;
     HistArgs h{};
     h.cells = L->cells;
@@ -196,7 +197,7 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     for (int a = 0; a < kMaxVars; ++a) h.axis[a] = a < naxes ? q->r.axis_order[a] : 0;
     h.need_mask = h.use_brush ? b.mask : 0u;
     for (int a = 0; a < naxes; ++a) {
-        h.need_mask |= 1u << q->r.axis_order[a];
+        if (q->r.axis_order[a] < kPosAxisBase) h.need_mask |= 1u << q->r.axis_order[a];
         const float e0 = q->edges[(size_t)a * (bins + 1)], eN = q->edges[(size_t)a * (bins + 1) + bins];
         h.guess_e0[a] = e0;
         h.guess_scale[a] = (eN > e0 && isfinite(eN - e0)) ? (float)bins / (eN - e0) : 0.0f;
@@ -364,6 +365,9 @@ void turn(raypc_server* S) {
                 memcpy(v.lo, q->r.lo, sizeof(v.lo));
                 memcpy(v.hi, q->r.hi, sizeof(v.hi));
                 v.active_mask = q->r.active_mask;
+                memcpy(v.pos_lo, q->r.pos_lo, sizeof(v.pos_lo));
+                memcpy(v.pos_hi, q->r.pos_hi, sizeof(v.pos_hi));
+                v.pos_mask = q->r.pos_mask;
                 v.opts = q->r.opts;
                 v.opts.counts_dev = nullptr;
                 v.out_rgba_dev = pr.second == kCoarse ? q->coarse : q->image;
@@ -510,6 +514,7 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
         if ((st = get_volume(S->ctx, r->vol, &V)) || (st = get_level(V, r->lod, &L))) { delete q; return st; }
         BrushArgs b{};
         if ((st = brush_from_host(V, r->lo, r->hi, r->active_mask, &b))) { delete q; return st; }
+        if ((st = pos_from_host(r->pos_lo, r->pos_hi, r->pos_mask, &b))) { delete q; return st; }
         if (r->kind == RAYPC_REQ_RENDER) {
             RenderArgs a{};
             if (r->w < 1 || r->h < 1 || r->w > 32768 || r->h > 32768) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "image size out of range"); }
@@ -526,7 +531,11 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
                 return fail(RAYPC_ERR_INVALID_ARG, "bad histogram request (naxes 2..8, bins 2..1024, edges)");
             }
             for (int a = 0; a < r->naxes; ++a) {
-                if (r->axis_order[a] < 0 || r->axis_order[a] >= V->nvars) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "bad axis"); }
+                if (!((r->axis_order[a] >= 0 && r->axis_order[a] < V->nvars) ||
+                      (r->axis_order[a] >= kPosAxisBase && r->axis_order[a] < kPosAxisBase + kNumPos))) {
+                    delete q;
+                    return fail(RAYPC_ERR_INVALID_ARG, "bad axis");
+                }
                 for (int k = 0; k <= r->bins; ++k) {
                     float e = r->edges[(size_t)a * (r->bins + 1) + k];
                     if (isnan(e) || (k && e < r->edges[(size_t)a * (r->bins + 1) + k - 1])) {

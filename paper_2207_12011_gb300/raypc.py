@@ -18,11 +18,18 @@ from . import build as _build
 
 RAYPC_F32, RAYPC_F16 = 0, 1
 MAX_VARS = 8
+NPOS = 4
+POS_X, POS_Y, POS_Z, POS_R = 0, 1, 2, 3
 BRICK = 8
 MAX_LOD = 2
 TF_ENTRIES = 256
 NSTATS = 8
 STAT_NAMES = ("marched", "evaluated", "kept", "skipped", "rays", "ert")
+
+
+def AXIS_POS(a: int) -> int:
+    """PC axis id of position axis a (POS_X, POS_Y, POS_Z, POS_R)."""
+    return 8 + int(a)
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "TIMEOUT", 5: "BUSY",
            6: "NOT_FOUND", 7: "UNSUPPORTED"}
@@ -61,7 +68,8 @@ class Request(ctypes.Structure):
                 ("active_mask", ctypes.c_uint32), ("cam", Camera), ("w", ctypes.c_int), ("h", ctypes.c_int),
                 ("lod", ctypes.c_int), ("coarse_lod", ctypes.c_int), ("opts", RenderOpts),
                 ("axis_order", ctypes.c_int * MAX_VARS), ("naxes", ctypes.c_int), ("bins", ctypes.c_int),
-                ("edges", ctypes.c_void_p), ("use_brush", ctypes.c_int)]
+                ("edges", ctypes.c_void_p), ("use_brush", ctypes.c_int),
+                ("pos_lo", ctypes.c_float * NPOS), ("pos_hi", ctypes.c_float * NPOS), ("pos_mask", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -80,7 +88,8 @@ class View(ctypes.Structure):
                 ("w", ctypes.c_int), ("h", ctypes.c_int),
                 ("lo", ctypes.c_float * MAX_VARS), ("hi", ctypes.c_float * MAX_VARS),
                 ("active_mask", ctypes.c_uint32), ("opts", RenderOpts),
-                ("out_rgba_dev", ctypes.c_void_p), ("stats_dev", ctypes.c_void_p)]
+                ("out_rgba_dev", ctypes.c_void_p), ("stats_dev", ctypes.c_void_p),
+                ("pos_lo", ctypes.c_float * NPOS), ("pos_hi", ctypes.c_float * NPOS), ("pos_mask", ctypes.c_uint32)]
 
 
 _lib = None
@@ -99,6 +108,8 @@ _SIGS = {
     "raypc_set_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_set_tf": [_P, _I, _P, _I, _F, _F, _P],
     "raypc_render": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts), _P, _P, _P],
+    "raypc_set_position_brush": [_P, _I, _P, _P, _U32, _P],
+    "raypc_pc_subsample": [_P, _I, _I, _U32, ctypes.c_longlong, _P, _I, _P, _P, _P, _P, _P],
     "raypc_render_progressive": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts),
                                  _U32, _U32, _P, _P, _P, _P],
     "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
@@ -290,6 +301,31 @@ class Volume:
         _call("raypc_set_brush", self.ctx.handle, self.id, _fptr(lo), _fptr(hi),
               int(active_mask) & 0xFFFFFFFF, _stream(stream))
 
+    def set_position_brush(self, lo, hi, pos_mask: int, stream=None):
+        """Restrict the position axes x, y, z, radius (bit a of pos_mask) to [lo[a], hi[a]]."""
+        lo = np.ascontiguousarray(np.asarray(lo, dtype=np.float32).reshape(NPOS))
+        hi = np.ascontiguousarray(np.asarray(hi, dtype=np.float32).reshape(NPOS))
+        _call("raypc_set_position_brush", self.ctx.handle, self.id, _fptr(lo), _fptr(hi),
+              int(pos_mask) & 0xFFFFFFFF, _stream(stream))
+
+    def pc_subsample(self, seed: int, k: int, axis_order, lod: int = 0, stream=None):
+        """PC line data: (cells int64 [m], values float32 [m, naxes], in_brush uint8 [m]) device tensors."""
+        order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32).reshape(-1))
+        naxes = int(order.size)
+        info = self.info(lod)
+        cap = max(1, min(int(k), info.n ** 3))
+        dev = torch.device("cuda", self.ctx.device)
+        cells = torch.empty(cap, dtype=torch.int64, device=dev)
+        vals = torch.empty((cap, max(naxes, 1)), dtype=torch.float32, device=dev)
+        flags = torch.empty(cap, dtype=torch.uint8, device=dev)
+        m = ctypes.c_longlong()
+        _call("raypc_pc_subsample", self.ctx.handle, self.id, int(lod), int(seed) & 0xFFFFFFFF, int(k),
+              _fptr(order) if naxes else None, naxes, ctypes.c_void_p(cells.data_ptr()),
+              ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(flags.data_ptr()), ctypes.byref(m),
+              _stream(stream))
+        m = m.value
+        return cells[:m], vals[:m, :naxes], flags[:m]
+
     def set_tf(self, rgbs, color_var: int, v_lo: float, v_hi: float, stream=None):
         t = np.ascontiguousarray(np.asarray(rgbs, dtype=np.float32).reshape(TF_ENTRIES, 4))
         _call("raypc_set_tf", self.ctx.handle, self.id, _fptr(t), int(color_var), float(v_lo),
@@ -476,6 +512,7 @@ def _view_array(ctx, views):
                        q.get("variant", AUTO))
         v.out_rgba_dev = out.data_ptr()
         v.stats_dev = stats.data_ptr() if stats is not None else None
+        _fill_pos(v, q.get("pos"))
         outs.append((out, counts if isinstance(counts, torch.Tensor) else None))
     return arr, outs
 
@@ -531,7 +568,8 @@ class Batch:
             pass
 
     def render(self, views, stream=None):
-        """views: list of dicts with vol (Volume), cam, w, h, lo, hi, mask and optional lod,
+        """views: list of dicts with vol (Volume), cam, w, h, lo, hi, mask and optional pos
+        (position brush (lo[4], hi[4], mask)), lod,
         step, ert, skip, bg, out, counts (True or tensor), stats (tensor). Returns the list of
         (image, counts or None)."""
         n = len(views)
@@ -556,6 +594,16 @@ class _DevArray:
 
 def _dev_tensor(ptr, shape, typestr, device):
     return torch.as_tensor(_DevArray(ptr, shape, typestr), device=device)
+
+
+def _fill_pos(req, pos):
+    """Position brush fields from pos = (lo[4], hi[4], mask) or None."""
+    lo, hi, mask = pos if pos is not None else ((-np.inf,) * NPOS, (np.inf,) * NPOS, 0)
+    lo = np.asarray(lo, np.float32).reshape(NPOS)
+    hi = np.asarray(hi, np.float32).reshape(NPOS)
+    for a in range(NPOS):
+        req.pos_lo[a], req.pos_hi[a] = float(lo[a]), float(hi[a])
+    req.pos_mask = int(mask) & 0xFFFFFFFF
 
 
 def _fill_brush(req, vol, lo, hi, mask):
@@ -601,11 +649,12 @@ class Server:
             pass
 
     def submit_render(self, vol, cam, w, h, lo=None, hi=None, mask=0, lod=0, coarse_lod=-1,
-                      ert=True, skip=None, variant=AUTO, bg=(0.0, 0.0, 0.0, 0.0)) -> int:
+                      ert=True, skip=None, variant=AUTO, bg=(0.0, 0.0, 0.0, 0.0), pos=None) -> int:
         r = Request()
         r.kind = REQ_RENDER
         r.vol = vol.id
         _fill_brush(r, vol, lo, hi, mask)
+        _fill_pos(r, pos)
         r.cam = camera_from(cam)
         r.w, r.h = int(w), int(h)
         r.lod = int(lod)
@@ -616,11 +665,13 @@ class Server:
         self._meta[rid.value] = ("render", int(h), int(w), coarse_lod >= 0)
         return rid.value
 
-    def submit_histogram(self, vol, axis_order, edges, lo=None, hi=None, mask=0, use_brush=True, lod=0) -> int:
+    def submit_histogram(self, vol, axis_order, edges, lo=None, hi=None, mask=0, use_brush=True, lod=0,
+                         pos=None) -> int:
         r = Request()
         r.kind = REQ_HISTOGRAM
         r.vol = vol.id
         _fill_brush(r, vol, lo, hi, mask)
+        _fill_pos(r, pos)
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
         r.naxes, r.bins = e.shape[0], e.shape[1] - 1
         for a, v in enumerate(axis_order):

@@ -89,6 +89,14 @@ def test_full_size_frame_and_histograms(rp, wl_name):
                                      wl.brush.active_mask, c["order"], wl.edges, use_brush=True)
         assert np.array_equal(H, Ho)
         assert all(int(H[p].sum()) == cells for p in range(H.shape[0]))
+        # the PC line subsample at its published size (100 000 cells), with a position axis
+        order = list(c["order"][:3]) + [rp.AXIS_POS(rp.POS_R)]
+        cells, vals, flags = vol.pc_subsample(9, 100000, order)
+        oc, ov, of = oracle.pc_subsample(stored, synth.R_IN, synth.R_OUT, wl.brush.lo, wl.brush.hi,
+                                         wl.brush.active_mask, 9, 100000, order)
+        assert np.array_equal(cells.cpu().numpy(), oc)
+        assert np.array_equal(vals.cpu().numpy().view(np.uint32), ov.view(np.uint32))
+        assert np.array_equal(flags.cpu().numpy(), of)
         # a re-ingested volume (next time step path) renders identically after rebuilding
         a, _ = vol.render(wl.cam, c["w"], c["h"])
         a = a.clone()

@@ -507,6 +507,156 @@ def test_histogram_rejects_bad_edges(ctx, rp):
     bad[1, 3] = np.nan
     with pytest.raises(rp.RaypcError):
         v.pc_histogram((0, 1), bad)
+    for bad_axis in (6, 7, 12, -1):          # neither a stored variable nor a position axis
+        with pytest.raises(rp.RaypcError):
+            v.pc_histogram((0, bad_axis), e)
+    v.free()
+
+
+# ----------------------------------------------------------------------------
+# position axes: brush, classification, histograms, PC line subsample
+# ----------------------------------------------------------------------------
+POS = (np.float32([-0.45, -np.inf, -np.inf, 0.62]), np.float32([0.5, np.inf, np.inf, 0.9]), 0b1001)
+
+
+@pytest.mark.parametrize("n,store,bname", [(48, "f32", "c2"), (33, "f16", "c1")])
+def test_position_brush_render_and_classification(ctx, rp, n, store, bname):
+    vol = synth.make_shell_volume(n, seed=8)
+    brush = synth.make_brush(vol, bname)
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    w, h = 61, 47
+    v = load(ctx, vol, store, n_lod=1, brush=brush, tf=tf)
+    v.set_position_brush(*POS)
+    levels = oracle_levels(stored(vol, store), 1, store)
+    for lod in range(2):
+        act, _, _ = v.skip_list(lod)
+        omn, omx = oracle.brick_minmax(levels[lod])
+        m = levels[lod].shape[1]
+        oact, _ = oracle.classify(omn, omx, m, R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, pos=POS)
+        assert np.array_equal(bits(rp, act, oact.size), oact.reshape(-1)), lod
+        _, _, sact = v.sub_bricks(lod)
+        omn4, omx4 = oracle.brick_minmax(levels[lod], 4)
+        oact4, _ = oracle.classify(omn4, omx4, m, R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, bs=4, pos=POS)
+        assert np.array_equal(bits(rp, sact, oact4.size), oact4.reshape(-1)), lod
+    for ert, skip in ((False, True), (False, False), (True, True)):
+        img, cnt = v.render(cam, w, h, ert=ert, skip=skip, counts=True)
+        torch.cuda.synchronize()
+        ref, rcnt = oracle.render(levels[0], R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
+                                  brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=ert, pos=POS)
+        assert np.abs(img.cpu().numpy().astype(np.float64) - ref).max() <= TOL[store], (ert, skip)
+        c = cnt.cpu().numpy().astype(np.uint32)
+        if not ert:
+            assert np.array_equal(c, rcnt), skip
+            rcnt_all = rcnt
+        else:
+            assert np.mean(c == rcnt) > 0.999
+    rcnt = rcnt_all
+    assert rcnt[..., 1].sum() > 0
+    # a new variable brush keeps the position brush; clearing it restores the plain render
+    v.set_brush(brush.lo, brush.hi, brush.active_mask)
+    _, cnt2 = v.render(cam, w, h, ert=False, counts=True)
+    assert np.array_equal(cnt2.cpu().numpy().astype(np.uint32), rcnt)
+    v.set_position_brush(np.zeros(4), np.zeros(4), 0)
+    _, cnt3 = v.render(cam, w, h, ert=False, counts=True)
+    _, rcnt3 = oracle.render(levels[0], R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
+                             brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=False)
+    assert np.array_equal(cnt3.cpu().numpy().astype(np.uint32), rcnt3)
+    assert rcnt3[..., 1].sum() > rcnt[..., 1].sum()
     with pytest.raises(rp.RaypcError):
-        v.pc_histogram((0, 9), e)
+        v.set_position_brush(np.float32([np.nan, 0, 0, 0]), np.ones(4), 1)
+    with pytest.raises(rp.RaypcError):
+        v.set_position_brush(np.zeros(4), np.ones(4), 0x10)
+    v.free()
+
+
+@pytest.mark.parametrize("store", ["f32", "f16"])
+def test_histogram_with_position_axes_bit_exact(ctx, rp, store):
+    n = 45
+    vol = synth.make_shell_volume(n, seed=12)
+    brush = synth.make_brush(vol, "c3")
+    v = load(ctx, vol, store, n_lod=1, brush=brush)
+    v.set_position_brush(*POS)
+    order = [rp.AXIS_POS(rp.POS_R), 1, rp.AXIS_POS(rp.POS_X), 4, rp.AXIS_POS(rp.POS_Z)]
+    bins = 37
+    edges = np.stack([np.linspace(0.5, 1.0, bins + 1), synth.make_edges(vol, [1], bins)[0],
+                      np.linspace(-1, 1, bins + 1), synth.make_edges(vol, [4], bins)[0],
+                      np.linspace(-0.9, 0.9, bins + 1)]).astype(np.float32)
+    levels = oracle_levels(stored(vol, store), 1, store)
+    for lod in range(2):
+        for use_brush in (True, False):
+            H = v.pc_histogram(order, edges, use_brush=use_brush, lod=lod).cpu().numpy().astype(np.uint32)
+            Ho, cells = oracle.histogram(levels[lod], R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, order,
+                                         edges, use_brush=use_brush, pos=POS)
+            assert np.array_equal(H, Ho), (lod, use_brush)
+            assert cells > 0
+    with pytest.raises(rp.RaypcError):
+        v.pc_histogram([0, 12], edges[:2], use_brush=False)
+    v.free()
+
+
+@pytest.mark.parametrize("n,store,seed", [(37, "f32", 0), (40, "f16", 0xFFFFFFFF), (3, "f32", 5)])
+def test_pc_subsample_matches_oracle(ctx, rp, n, store, seed):
+    vol = synth.make_shell_volume(n, seed=4)
+    brush = synth.make_brush(vol, "c1")
+    v = load(ctx, vol, store, n_lod=1, brush=brush)
+    v.set_position_brush(*POS)
+    blo, bhi, bmask = brush.lo, brush.hi, brush.active_mask
+    order = [0, rp.AXIS_POS(rp.POS_R), 4, rp.AXIS_POS(rp.POS_X)]
+    levels = oracle_levels(stored(vol, store), 1, store)
+    for lod in range(2):
+        m = levels[lod].shape[1]
+        N = oracle.pc_subsample(levels[lod], R_IN, R_OUT, blo, bhi, bmask, seed, m ** 3, [0], pos=POS)[0].size
+        for k in (0, 1, 1000, N - 1, N, N + 10):
+            cells, vals, flags = v.pc_subsample(seed, k, order, lod=lod)
+            oc, ov, of = oracle.pc_subsample(levels[lod], R_IN, R_OUT, blo, bhi, bmask, seed, k, order, pos=POS)
+            assert np.array_equal(cells.cpu().numpy(), oc), (lod, k)
+            assert np.array_equal(vals.cpu().numpy().view(np.uint32), ov.view(np.uint32)), (lod, k)
+            assert np.array_equal(flags.cpu().numpy(), of), (lod, k)
+    # the flags follow the volume's brush: without a position brush more lines pass
+    _, _, f_pos = v.pc_subsample(seed, N, order, lod=1)
+    v.set_position_brush(np.zeros(4), np.zeros(4), 0)
+    _, _, f_all = v.pc_subsample(seed, N, order, lod=1)
+    assert int(f_all.sum()) >= int(f_pos.sum())
+    with pytest.raises(rp.RaypcError):
+        v.pc_subsample(seed, -1, order)
+    with pytest.raises(rp.RaypcError):
+        v.pc_subsample(seed, 10, [0, 13])
+    v.free()
+
+
+def test_batch_and_server_take_position_brushes(ctx, rp):
+    n = 40
+    vol = synth.make_shell_volume(n, seed=13)
+    brush = synth.make_brush(vol, "c2")
+    tf = synth.make_tf(vol, "v_r")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    v = load(ctx, vol, "f32", brush=brush, tf=tf)
+    v.set_position_brush(*POS)
+    ref, rcnt = v.render(cam, 50, 40, ert=False, counts=True)
+    b = rp.Batch(ctx, 4)
+    views = [dict(vol=v, cam=cam, w=50, h=40, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, pos=POS,
+                  ert=False, counts=True)]
+    (img, cnt), = b.render(views)
+    torch.cuda.synchronize()
+    assert torch.equal(img, ref) and torch.equal(cnt, rcnt)
+    b.close()
+    edges = synth.make_edges(vol, [0, 1], 16)
+    edges[1] = np.linspace(0.5, 1.0, 17, dtype=np.float32)
+    order = [0, rp.AXIS_POS(rp.POS_R)]
+    H = v.pc_histogram(order, edges, use_brush=True)
+    with rp.Server(ctx) as srv:
+        r1 = srv.submit_render(v, cam, 50, 40, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, pos=POS, ert=False)
+        r2 = srv.submit_histogram(v, order, edges, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, pos=POS)
+        for rid, want in ((r1, None), (r2, H)):
+            for _ in range(2000):
+                out = srv.poll(rid, 10000)
+                if out["done"]:
+                    break
+            assert out["done"] and out["status"] == 0
+            if want is None:
+                assert torch.equal(out["image"], ref)
+            else:
+                assert torch.equal(out["hist"], want)
+            srv.release(rid)
     v.free()
