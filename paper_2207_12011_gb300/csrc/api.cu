@@ -194,6 +194,48 @@ raypc_status get_level(Volume* V, int lod, Level** out) {
     return RAYPC_OK;
 }
 
+// Smallest float f >= 0 with sqrt_rn(f) >= lo, or the largest with sqrt_rn(f) <= hi
+// (upper = true): sqrt_rn is monotone, so a bisection over the ordered bit patterns of
+// the non-negative floats finds the exact threshold. Host sqrtf is correctly rounded,
+// like the kernels' __fsqrt_rn.
+static float radius_threshold2(float r, bool upper) {
+    uint32_t l = 0u, h = 0x7f800000u;                   // +0 .. +inf
+    // predicate true from some bit pattern on: sqrt(f) >= r (lower) or sqrt(f) > r (upper)
+    auto pred = [&](uint32_t bits) {
+        float f;
+        memcpy(&f, &bits, 4);
+        const float s = sqrtf(f);
+        return upper ? (s > r) : (s >= r);
+    };
+    if (!pred(h)) return INFINITY;                      // lower: nothing reaches r; upper: r = +inf
+    while (l < h) {
+        const uint32_t m = l + (h - l) / 2;
+        if (pred(m)) h = m; else l = m + 1;
+    }
+    if (upper) {                                        // last pattern with sqrt <= r
+        if (l == 0u) return -1.0f;                      // even sqrt(0) = 0 > r: nothing passes
+        const uint32_t b = l - 1u;
+        float f;
+        memcpy(&f, &b, 4);
+        return f;
+    }
+    float f;
+    memcpy(&f, &l, 4);
+    return f;
+}
+
+void finish_position_brush(RenderArgs& a) {
+    a.keep_lo2 = a.rin2;
+    a.keep_hi2 = a.rout2;
+    if ((a.brush.pmask >> 3) & 1u) {
+        // lo_r <= sqrt_rn(|p|^2) <= hi_r  <=>  L <= |p|^2 <= H for the exact thresholds L, H
+        const float L = radius_threshold2(a.brush.plo[3], false), H = radius_threshold2(a.brush.phi[3], true);
+        a.keep_lo2 = fmaxf(a.keep_lo2, L);
+        a.keep_hi2 = fminf(a.keep_hi2, H);
+    }
+    a.keep_lo2 = fminf(a.keep_lo2, 0x1p100f);          // finite (the core-jump bound scales it)
+}
+
 raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int w, int h,
                               const raypc_render_opts* opts, float* out_rgba_dev,
                               unsigned long long* stats_dev, RenderArgs* out) {
@@ -241,6 +283,7 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.dt = dt;
     a.rin2 = V->r_in * V->r_in;
     a.rout2 = V->r_out * V->r_out;
+    finish_position_brush(a);
     a.tf = V->tf;
     a.color_var = V->color_var;
     a.tf_lo = V->tf_lo;

@@ -189,6 +189,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = make_render_args(V, L, &q.cam, q.w, q.h, &q.opts, q.out_rgba_dev, q.stats_dev, &bv.a))) return st;
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;
         if ((st = pos_from_host(q.pos_lo, q.pos_hi, q.pos_mask, &bv.a.brush))) return st;
+        finish_position_brush(bv.a);
         if (i == 0) variant = bv.a.variant;
         bv.a.variant = variant;
         const size_t words = L->nwords(), need = words + L->nswords() + L->nsbricks();

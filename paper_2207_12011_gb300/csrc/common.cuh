@@ -179,6 +179,8 @@ struct RenderArgs {
     int w, h;
     float dt;
     float rin2, rout2;            // r_in * r_in, r_out * r_out rounded to FP32
+    float keep_lo2, keep_hi2;     // per-sample |p|^2 range of the shell and the radius brush
+                                  // (set by finish_position_brush)
     const float4* tf;             // 256 entries (r, g, b, sigma)
     int color_var;
     float tf_lo, tf_scale;        // s = (v - tf_lo) * tf_scale
@@ -498,7 +500,7 @@ int render_batch_blocks_per_sm(int dtype, int variant);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
 // PC line subsample (pcsub_kernels.cu).
-constexpr int kSubMaxBlocks = 1024;     // blocks of the ordered compaction
+constexpr int kSubMaxSegments = 8192;   // warp-owned row segments of the ordered compaction
 struct SubsampleArgs {
     const void* cells;            // planar level values, storage dtype
     int n, nvars;

@@ -14,9 +14,10 @@
 // fill that bucket exactly, the select is done: the subsample is every cell
 // whose key's resolved top bits are <= the prefix. Distinct keys guarantee
 // this by 64 bits, i.e. within six rounds; rounds after the select is done
-// return at once. An ordered compaction follows: blocks own contiguous row
-// ranges, count their selected cells, and write them in cell order at the
-// offset given by the counts of the blocks before them.
+// return at once. An ordered compaction follows: warps own contiguous row
+// segments, count their selected cells, one block scans the counts, and each
+// warp writes its cells' indices in cell order from its segment's offset; one
+// thread per line then gathers the line's axis values and brush flag.
 #include "common.cuh"
 
 namespace raypc {
@@ -34,7 +35,8 @@ struct SubState {
     int nbits;                         // resolved bits, 0..64
     int done;                          // selection final: top nbits bits <= prefix (nbits 0: all)
     unsigned long long hist[kDigits];
-    unsigned block_cnt[kSubMaxBlocks];
+    unsigned seg_cnt[kSubMaxSegments];   // selected cells per compaction segment
+    unsigned seg_off[kSubMaxSegments];   // their exclusive prefix sums
 };
 
 // Largest integer m >= 0 with m * m <= a (0 <= a < 2^31).
@@ -71,7 +73,6 @@ __device__ __forceinline__ bool selected(unsigned long long key, int nbits, unsi
 
 __global__ void k_sub_init(SubState* S, unsigned long long m, int all) {
     for (int i = threadIdx.x; i < kDigits; i += blockDim.x) S->hist[i] = 0ull;
-    for (int i = threadIdx.x; i < kSubMaxBlocks; i += blockDim.x) S->block_cnt[i] = 0u;
     if (threadIdx.x == 0) {
         S->prefix = 0ull;
         S->need = m;
@@ -150,23 +151,24 @@ __global__ void __launch_bounds__(1024) k_sub_pick(SubState* S) {
     for (int i = 0; i < kPer; ++i) S->hist[t * kPer + i] = 0ull;
 }
 
-// Rows [r0, r1) owned by block b of the compaction.
-__device__ __forceinline__ void block_rows(const SubsampleArgs& A, int b, long long& r0, long long& r1) {
+// Rows [r0, r1) of compaction segment g (one warp per segment, segments in row order).
+__device__ __forceinline__ void segment_rows(const SubsampleArgs& A, long long g, int nseg, long long& r0, long long& r1) {
     const long long rows = (long long)A.n * A.n;
-    const long long per = (rows + gridDim.x - 1) / gridDim.x;
-    r0 = min(rows, (long long)b * per);
+    const long long per = (rows + nseg - 1) / nseg;
+    r0 = min(rows, g * per);
     r1 = min(rows, r0 + per);
 }
 
-__global__ void __launch_bounds__(kSubThreads) k_sub_count(SubsampleArgs A, SubState* S) {
-    __shared__ unsigned s_warp[kSubThreads / 32];
+__global__ void __launch_bounds__(kSubThreads) k_sub_count(SubsampleArgs A, SubState* S, int nseg) {
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nseg) return;                                     // whole warps
+    const int lane = threadIdx.x & 31;
     const int nbits = S->nbits;
     const unsigned long long prefix = S->prefix;
     long long r0, r1;
-    block_rows(A, blockIdx.x, r0, r1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    segment_rows(A, g, nseg, r0, r1);
     unsigned cnt = 0;
-    for (long long r = r0 + warp; r < r1; r += kSubThreads / 32) {
+    for (long long r = r0; r < r1; ++r) {
         int xa, xb, syz;
         if (!row_range(A, r, xa, xb, syz)) continue;
         for (int x = xa + lane; x <= xb; x += 32)
@@ -174,85 +176,93 @@ __global__ void __launch_bounds__(kSubThreads) k_sub_count(SubsampleArgs A, SubS
                 ++cnt;
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if (lane == 0) s_warp[warp] = cnt;
+    if (lane == 0) S->seg_cnt[g] = cnt;
+}
+
+// One block of 1024 threads: exclusive scan of the segment counts (m < 2^31).
+__global__ void __launch_bounds__(1024) k_sub_scan(SubState* S, int nseg) {
+    __shared__ unsigned s_sum[1024];
+    constexpr int kPer = kSubMaxSegments / 1024;
+    const int t = threadIdx.x;
+    unsigned loc[kPer], tot = 0u;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int g = t * kPer + i;
+        loc[i] = g < nseg ? S->seg_cnt[g] : 0u;
+        tot += loc[i];
+    }
+    s_sum[t] = tot;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int w = 0; w < kSubThreads / 32; ++w) t += s_warp[w];
-        S->block_cnt[blockIdx.x] = t;
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned add = t >= off ? s_sum[t - off] : 0u;
+        __syncthreads();
+        s_sum[t] += add;
+        __syncthreads();
+    }
+    unsigned run = s_sum[t] - tot;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int g = t * kPer + i;
+        if (g < nseg) S->seg_off[g] = run;
+        run += loc[i];
     }
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kSubThreads) k_sub_write(SubsampleArgs A, SubState* S) {
-    __shared__ unsigned long long s_base;
-    __shared__ unsigned s_part[kSubThreads / 32];
+__global__ void __launch_bounds__(kSubThreads) k_sub_write(SubsampleArgs A, SubState* S, int nseg) {
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= nseg) return;                                     // whole warps
+    const int lane = threadIdx.x & 31;
     const int nbits = S->nbits;
     const unsigned long long prefix = S->prefix;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // offset of this block: the selected cells of the blocks before it
-    {
-        unsigned long long part = 0ull;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += kSubThreads) part += S->block_cnt[b];
-        part = __reduce_add_sync(0xffffffffu, (unsigned)part);   // m < 2^31
-        if (lane == 0) s_part[warp] = (unsigned)part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long t = 0ull;
-            for (int w = 0; w < kSubThreads / 32; ++w) t += s_part[w];
-            s_base = t;
-        }
-        __syncthreads();
-    }
+    unsigned long long base = S->seg_off[g];
     long long r0, r1;
-    block_rows(A, blockIdx.x, r0, r1);
+    segment_rows(A, g, nseg, r0, r1);
     const int n = A.n;
-    const size_t plane = (size_t)n * n * n;
     for (long long r = r0; r < r1; ++r) {
         int xa, xb, syz;
-        if (!row_range(A, r, xa, xb, syz)) continue;        // uniform over the block
-        const int y = (int)(r % n), z = (int)(r / n);
-        for (int x0 = xa; x0 <= xb; x0 += kSubThreads) {
-            const int x = x0 + threadIdx.x;
+        if (!row_range(A, r, xa, xb, syz)) continue;        // uniform over the warp
+        for (int x0 = xa; x0 <= xb; x0 += 32) {
+            const int x = x0 + lane;
             const unsigned long long c = (unsigned long long)r * n + x;
             const bool sel = x <= xb && in_shell(A, x, syz) && selected(splitmix64_at(A.key, c), nbits, prefix);
             const unsigned ball = __ballot_sync(0xffffffffu, sel);
-            if (lane == 0) s_part[warp] = __popc(ball);
-            __syncthreads();
-            unsigned before = 0, total = 0;
-            for (int w = 0; w < kSubThreads / 32; ++w) {
-                if (w < warp) before += s_part[w];
-                total += s_part[w];
-            }
-            const unsigned long long pos = s_base + before + __popc(ball & ((1u << lane) - 1u));
-            if (sel && pos < A.m) {                            // the select yields exactly m cells
-                A.out_cells[pos] = (long long)c;
-                float cx = 0.0f, cy = 0.0f, cz = 0.0f, r2 = 0.0f;
-                if (A.use_pos) {
-                    cx = cell_centre_rn(x, n);
-                    cy = cell_centre_rn(y, n);
-                    cz = cell_centre_rn(z, n);
-                    r2 = dot3_rn(cx, cy, cz, cx, cy, cz);
-                }
-                for (int a = 0; a < A.naxes; ++a) {
-                    const int av = A.axis[a];
-                    A.out_values[pos * A.naxes + a] = av >= kPosAxisBase ? pos_axis(cx, cy, cz, r2, av - kPosAxisBase)
-                                                                         : load_cell<DT>(A.cells, av * plane + c);
-                }
-                bool pass = true;
-                for (int v = 0; v < A.nvars && pass; ++v) {
-                    if (!((A.brush.mask >> v) & 1u)) continue;
-                    const float s = load_cell<DT>(A.cells, v * plane + c);
-                    pass = s >= A.brush.lo[v] && s <= A.brush.hi[v];
-                }
-                if (pass && A.brush.pmask) pass = pos_pass(cx, cy, cz, r2, A.brush);
-                A.out_flags[pos] = pass ? 1u : 0u;
-            }
-            __syncthreads();                                   // s_part is reused
-            if (threadIdx.x == 0) s_base += total;
-            __syncthreads();
+            const unsigned long long pos = base + __popc(ball & ((1u << lane) - 1u));
+            base += __popc(ball);
+            if (sel && pos < A.m) A.out_cells[pos] = (long long)c;   // the select yields exactly m cells
         }
     }
+}
+
+// One thread per written line: PC axis values and the brush flag of its cell.
+template <int DT>
+__global__ void __launch_bounds__(kSubThreads) k_sub_gather(SubsampleArgs A) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.m) return;
+    const int n = A.n;
+    const size_t plane = (size_t)n * n * n;
+    const unsigned long long c = (unsigned long long)A.out_cells[i];
+    if (c >= (unsigned long long)plane) return;              // written by k_sub_write; never out of range
+    const int x = (int)(c % n), y = (int)((c / n) % n), z = (int)(c / ((unsigned long long)n * n));
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f, r2 = 0.0f;
+    if (A.use_pos) {
+        cx = cell_centre_rn(x, n);
+        cy = cell_centre_rn(y, n);
+        cz = cell_centre_rn(z, n);
+        r2 = dot3_rn(cx, cy, cz, cx, cy, cz);
+    }
+    for (int a = 0; a < A.naxes; ++a) {
+        const int av = A.axis[a];
+        A.out_values[i * A.naxes + a] = av >= kPosAxisBase ? pos_axis(cx, cy, cz, r2, av - kPosAxisBase)
+                                                           : load_cell<DT>(A.cells, av * plane + c);
+    }
+    bool pass = true;
+    for (int v = 0; v < A.nvars && pass; ++v) {
+        if (!((A.brush.mask >> v) & 1u)) continue;
+        const float sv = load_cell<DT>(A.cells, v * plane + c);
+        pass = sv >= A.brush.lo[v] && sv <= A.brush.hi[v];
+    }
+    if (pass && A.brush.pmask) pass = pos_pass(cx, cy, cz, r2, A.brush);
+    A.out_flags[i] = pass ? 1u : 0u;
 }
 
 }  // namespace
@@ -264,18 +274,22 @@ cudaError_t launch_pc_subsample(const SubsampleArgs& a, int dtype, unsigned long
     k_sub_init<<<1, 1024, 0, stream>>>(S, m, m >= N ? 1 : 0);
     const long long rows = (long long)a.n * a.n;
     const long long want = (rows + (kSubThreads / 32) - 1) / (kSubThreads / 32);
-    const int hist_blocks = (int)(want < 4096 ? want : 4096);
+    const int hist_blocks = (int)(want < 1024 ? want : 1024);
     for (int round = 0; round < kRounds; ++round) {
         k_sub_hist<<<hist_blocks, kSubThreads, 0, stream>>>(a, S);
         k_sub_pick<<<1, 1024, 0, stream>>>(S);
     }
-    const int blocks = (int)(rows < kSubMaxBlocks ? rows : kSubMaxBlocks);
-    k_sub_count<<<blocks, kSubThreads, 0, stream>>>(a, S);
+    const int nseg = (int)(rows < kSubMaxSegments ? rows : kSubMaxSegments);
+    const int seg_blocks = (nseg + kSubThreads / 32 - 1) / (kSubThreads / 32);
+    k_sub_count<<<seg_blocks, kSubThreads, 0, stream>>>(a, S, nseg);
+    k_sub_scan<<<1, 1024, 0, stream>>>(S, nseg);
+    k_sub_write<<<seg_blocks, kSubThreads, 0, stream>>>(a, S, nseg);
+    const int gblocks = (int)((m + kSubThreads - 1) / kSubThreads);
     if (dtype == kF16)
-        k_sub_write<kF16><<<blocks, kSubThreads, 0, stream>>>(a, S);
+        k_sub_gather<kF16><<<gblocks, kSubThreads, 0, stream>>>(a);
     else
-        k_sub_write<kF32><<<blocks, kSubThreads, 0, stream>>>(a, S);
-    count_launches(3 + 2 * kRounds);
+        k_sub_gather<kF32><<<gblocks, kSubThreads, 0, stream>>>(a);
+    count_launches(5 + 2 * kRounds);
     return cudaGetLastError();
 }
 

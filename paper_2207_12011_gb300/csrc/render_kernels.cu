@@ -7,7 +7,7 @@
 // bit-identically alone and inside a batch. Per lattice sample: position,
 // interpolation cell (exactly rounded FP32), the activity bit of the 4^3
 // sub-brick that holds the cell (samples in inactive sub-bricks cannot pass
-// the brush or the shell test), shell test, position brush, then the restricted
+// the brush or the shell test), shell and radius test, then the restricted
 // variables in increasing order of how many bricks pass them alone (most
 // selective first; the order cannot change the result) that the sample's cell
 // class does not already decide, each as an FP32
@@ -171,14 +171,14 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             int core_a = n_lat, core_b = n_lat - 1;               // empty unless verified
             {
                 const float hh = dot3_rn(hx, hy, hz, hx, hy, hz);
-                const float shrink = __fmul_rn(A.rin2, 1.0f - 0x1p-9f);
+                const float shrink = __fmul_rn(A.keep_lo2, 1.0f - 0x1p-9f);
                 if (hh < shrink) {
                     const float sc = __fsqrt_rn(__fsub_rn(shrink, hh));
                     const float tc0 = __fsub_rn(-b, sc), tc1 = __fadd_rn(-b, sc);
                     const int ka = max(0, (int)ceilf(fminf((tc0 - t0) * inv_dt - jo, 1.0e9f)));
                     const int kb = min(n_lat - 1, (int)floorf(fminf((tc1 - t0) * inv_dt - jo, 1.0e9f)));
                     if (ka < kb) {
-                        const float lim = __fmul_rn(A.rin2, 1.0f - 0x1p-10f);
+                        const float lim = __fmul_rn(A.keep_lo2, 1.0f - 0x1p-10f);
                         const float ta = __fmaf_rn(__fadd_rn((float)ka, jo), dt, t0);
                         const float tb = __fmaf_rn(__fadd_rn((float)kb, jo), dt, t0);
                         const float ax = __fmaf_rn(ta, dx, ox), ay = __fmaf_rn(ta, dy, oy), az = __fmaf_rn(ta, dz, oz);
@@ -190,13 +190,48 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                     }
                 }
             }
-            int k = 0;
-            int kend = core_a;                                    // first stretch ends at the core
+            // Coordinate brushes: along the ray each coordinate fma(t_k, d, o) is
+            // monotone in k, so the samples inside every restricted coordinate range
+            // form one index range [k_first, k_last); the rest are marched but never kept.
+            int k_first = 0, k_last = n_lat;
+            if (A.brush.pmask & 7u) {
+                const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz};
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (!((A.brush.pmask >> a) & 1u)) continue;
+                    const float lo = A.brush.plo[a], hi = A.brush.phi[a];
+                    const float d = dd[a], o = oo[a];
+                    if (d == 0.0f) {                                   // constant coordinate o
+                        if (!(o >= lo && o <= hi)) k_last = 0;
+                        continue;
+                    }
+                    // smallest k in [0, n_lat] whose coordinate has entered (leave = false)
+                    // or left (leave = true) the range
+                    auto first = [&](bool leave) {
+                        int l = 0, h = n_lat;
+                        while (l < h) {
+                            const int m = (l + h) >> 1;
+                            const float c = __fmaf_rn(__fmaf_rn(__fadd_rn((float)m, jo), dt, t0), d, o);
+                            const bool p = d > 0.0f ? (leave ? c > hi : c >= lo) : (leave ? c < lo : c <= hi);
+                            if (p) h = m; else l = m + 1;
+                        }
+                        return l;
+                    };
+                    k_first = max(k_first, first(false));
+                    k_last = min(k_last, first(true));
+                }
+            }
+            // n_lat is needed again only for the count after the loop: park it in shared
+            // memory rather than in a register across the loop
+            __shared__ int s_lat[kThreads];
+            reinterpret_cast<volatile int*>(s_lat)[threadIdx.x] = n_lat;
+            int k = k_first;
+            int kend = min(core_a, k_last);                       // first stretch ends at the core
             for (;;) {
                 if (k >= kend) {
-                    if (kend >= n_lat) break;
+                    if (kend >= k_last) break;
                     k = max(k, core_b + 1);                      // the rest after the core
-                    kend = n_lat;
+                    kend = k_last;
                     continue;
                 }
                 const float t = __fmaf_rn(__fadd_rn((float)k, jo), dt, t0);
@@ -224,7 +259,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                                 te = fminf(te, (fmaf((float)lo[a] + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
                         }
                         const float kk = fminf((te - t0) * inv_dt - jo, 1.0e9f);
-                        const int kl = kk > (float)(k + 1) ? min((int)ceilf(kk) - 1, n_lat - 1) : k;
+                        const int kl = kk > (float)(k + 1) ? min((int)ceilf(kk) - 1, k_last - 1) : k;
                         if (kl > k) {
                             // the estimated last sample, recomputed exactly
                             const float tl = __fmaf_rn(__fadd_rn((float)kl, jo), dt, t0);
@@ -243,8 +278,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                     continue;
                 }
                 const float r2 = dot3_rn(pxw, pyw, pzw, pxw, pyw, pzw);
-                if (!(r2 >= A.rin2 && r2 <= A.rout2)) { ++k; continue; }
-                if (A.brush.pmask && !pos_pass(pxw, pyw, pzw, r2, A.brush)) { ++k; continue; }
+                if (!(r2 >= A.keep_lo2 && r2 <= A.keep_hi2)) { ++k; continue; }
                 const size_t base = ((size_t)iz * n + iy) * n + ix;
                 const float nm1 = (float)(n - 1);
                 const float fx = grid_weight_rn(ux, ix, nm1), fy = grid_weight_rn(uy, iy, nm1), fz = grid_weight_rn(uz, iz, nm1);
@@ -290,7 +324,8 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 if (A.ert && Aa >= kErtThreshold) { ert_hit = 1; ++k; break; }
                 ++k;
             }
-            marched = (unsigned)k;
+            // every lattice sample up to termination
+            marched = ert_hit ? (unsigned)k : (unsigned)reinterpret_cast<volatile int*>(s_lat)[threadIdx.x];
         }
         const float tr = 1.0f - Aa;
         float4 o;

@@ -116,6 +116,10 @@ raypc_status brush_from_host(const Volume* V, const float* lo, const float* hi, 
 // Validated position brush (axes x, y, z, radius; bounds read only for axes in pos_mask) into b.
 raypc_status pos_from_host(const float* lo, const float* hi, uint32_t pos_mask, BrushArgs* b);
 
+// Per-sample |p|^2 range of a render (keep_lo2, keep_hi2) from its shell radii and the radius
+// brush; call after the brush is final.
+void finish_position_brush(RenderArgs& a);
+
 }  // namespace raypc
 
 struct raypc_ctx {

@@ -141,6 +141,7 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         args[i].counts = nullptr;
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &args[i].brush))) break;
         if ((st = pos_from_host(q.pos_lo, q.pos_hi, q.pos_mask, &args[i].brush))) break;
+        finish_position_brush(args[i]);
         const size_t words = L->nwords();
         void* bits = nullptr;
         void* list = nullptr;

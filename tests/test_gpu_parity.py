@@ -557,6 +557,16 @@ def test_position_brush_render_and_classification(ctx, rp, n, store, bname):
     v.set_brush(brush.lo, brush.hi, brush.active_mask)
     _, cnt2 = v.render(cam, w, h, ert=False, counts=True)
     assert np.array_equal(cnt2.cpu().numpy().astype(np.uint32), rcnt)
+    # all four axes restricted, also on axis-aligned rays (direction components exactly 0)
+    pos_b = (np.float32([-0.3, -0.2, -np.inf, 0.7]), np.float32([0.4, 0.25, 0.6, np.inf]), 0b1111)
+    v.set_position_brush(*pos_b)
+    axis = synth.Camera((0.0, 0.0, 2.5), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    for cm, ww, hh in ((cam, w, h), (axis, 31, 31)):
+        _, rc = oracle.render(levels[0], R_IN, R_OUT, cm.as_array(), ww, hh, 1.0 / n, brush.lo, brush.hi,
+                              brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=False, pos=pos_b)
+        for skip in (True, False):
+            _, c = v.render(cm, ww, hh, ert=False, skip=skip, counts=True)
+            assert np.array_equal(c.cpu().numpy().astype(np.uint32), rc), skip
     v.set_position_brush(np.zeros(4), np.zeros(4), 0)
     _, cnt3 = v.render(cam, w, h, ert=False, counts=True)
     _, rcnt3 = oracle.render(levels[0], R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
