@@ -65,6 +65,8 @@ def _load():
             lib.oracle_pc_subsample.argtypes = [P, i32, i32, f32, f32, P, P, u32, P, P, u32, u32,
                                                 ctypes.c_int64, P, i32, P, P, P]
             lib.oracle_pc_subsample.restype = ctypes.c_int64
+            lib.oracle_filter_points.argtypes = [P, i32, i32, f32, f32, P, P, u32, P, P, u32, P,
+                                                 ctypes.c_int64, P]
             lib.oracle_subsample_key.argtypes = [u32, ctypes.c_int64]
             lib.oracle_subsample_key.restype = ctypes.c_uint64
             lib.oracle_render.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
@@ -214,6 +216,19 @@ def pc_subsample(vol, r_in, r_out, lo, hi, active_mask, seed, k, axis_order, pos
     if m < 0:
         raise ValueError("oracle_pc_subsample: invalid arguments")
     return cells[:m], vals[:m, :naxes], flags[:m]
+
+
+def filter_points(vol, r_in, r_out, lo, hi, active_mask, points, pos=None) -> np.ndarray:
+    """Brush test of points [npts, 3] (the render's per-sample test) -> uint8 [npts]."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    plo, phi, pmask = _pos(pos)
+    pts = _f32(points).reshape(-1, 3)
+    out = np.zeros(pts.shape[0], np.uint8)
+    _load().oracle_filter_points(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(_f32(lo)),
+                                 _ptr(_f32(hi)), int(active_mask) & 0xFFFFFFFF, _ptr(plo), _ptr(phi), pmask,
+                                 _ptr(pts), pts.shape[0], _ptr(out))
+    return out
 
 
 def subsample_key(seed, cell) -> int:

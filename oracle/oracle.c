@@ -24,7 +24,9 @@
  *     as brush and PC axes (Section 2.1 derived altitude, Section 3 cuts on
  *     Cartesian coordinates);
  *   - the random subsample of cells whose polylines the PC plot draws
- *     (Section 2.1).
+ *     (Section 2.1);
+ *   - the brush test of given points (pathline seeds inside the current
+ *     selection, Section 3).
  *
  * Precision. Every continuous quantity (ray geometry for the colour value,
  * transfer-function lookup, opacity, compositing) is FP64. Every quantity that
@@ -572,9 +574,7 @@ static void grid_coord32(float p, int n, int *i0, float *f) {
     *f = u - (float)i;
 }
 
-static float interp32(const render_job *J, int v, const int i[3], const float f[3]) {
-    const float *vol = J->vol;
-    int n = J->n;
+static float interp32_at(const float *vol, int n, int v, const int i[3], const float f[3]) {
     float c[2][2][2];
     for (int dz = 0; dz < 2; dz++)
         for (int dy = 0; dy < 2; dy++)
@@ -586,6 +586,42 @@ static float interp32(const render_job *J, int v, const int i[3], const float f[
     float c0 = lerp32(c00, c10, f[1]);
     float c1 = lerp32(c01, c11, f[1]);
     return lerp32(c0, c1, f[2]);
+}
+
+static float interp32(const render_job *J, int v, const int i[3], const float f[3]) {
+    return interp32_at(J->vol, J->n, v, i, f);
+}
+
+/* ------------------------------------------------------------------ */
+/* Seed filtering (Section 3: only the pathlines whose seed lies in the */
+/* current selection are shown). A point p (FP32 world coordinates)     */
+/* passes iff it lies in the shell (FP32 |p|^2 as for a sample), passes */
+/* the position brush, and every restricted variable's FP32 trilinear   */
+/* value at p passes the brush: exactly the per-sample test of the ray  */
+/* march. NaN coordinates fail. out[i] = 1 / 0.                          */
+/* ------------------------------------------------------------------ */
+void oracle_filter_points(const float *vol, int n, int nvars, float r_in, float r_out,
+                          const float *lo, const float *hi, uint32_t active_mask,
+                          const float *plo, const float *phi, uint32_t pmask,
+                          const float *pts, int64_t npts, uint8_t *out) {
+    float rin2 = r_in * r_in, rout2 = r_out * r_out;
+    for (int64_t q = 0; q < npts; q++) {
+        const float *p = pts + 3 * q;
+        float r2 = fmaf(p[2], p[2], fmaf(p[1], p[1], p[0] * p[0]));
+        int keep = (r2 >= rin2 && r2 <= rout2);
+        if (keep && pmask) keep = pos_pass(p, plo, phi, pmask);
+        if (keep) {
+            int i0[3];
+            float f[3];
+            for (int a = 0; a < 3; a++) grid_coord32(p[a], n, &i0[a], &f[a]);
+            for (int v = 0; v < nvars && keep; v++) {
+                if (!((active_mask >> v) & 1u)) continue;
+                float s = interp32_at(vol, n, v, i0, f);
+                if (!(s >= lo[v] && s <= hi[v])) keep = 0;
+            }
+        }
+        out[q] = (uint8_t)keep;
+    }
 }
 
 /* FP64 trilinear interpolation at an FP64 world position (same clamping). */

@@ -992,3 +992,66 @@ def test_pc_subsample_is_uniform_and_pairwise_independent():
     assert chi2 < N + 5 * math.sqrt(2 * N), (chi2, N)                 # about N +- sqrt(2N)
     q = k * (k - 1) / (N * (N - 1))
     assert abs(pair - S * q) < 5 * math.sqrt(S * q), (pair, S * q)
+
+
+# ----------------------------------------------------------------------------
+# seed filtering: the per-sample brush test at given points
+# ----------------------------------------------------------------------------
+def test_filter_points_at_vertices_reads_the_stored_values():
+    """At an interior vertex (n = 16: its centre coordinate is exact and the interpolation
+    weight is 0) the FP32 trilinear value is the stored value, and |p|^2 is exact."""
+    n = 16
+    vol = synth.make_shell_volume(n, seed=21).numpy()
+    lo = np.full(6, -np.inf, np.float32)
+    hi = np.full(6, np.inf, np.float32)
+    idx = np.stack(np.meshgrid(np.arange(n - 1), np.arange(n - 1), np.arange(n - 1), indexing="ij"), -1).reshape(-1, 3)
+    # bounds equal to the stored values of passing in-shell vertices, so that vertices sit on them
+    rr = ((2 * idx + 1 - n) ** 2).sum(axis=1) / n ** 2
+    shell_v = idx[(rr > 0.4) & (rr < 0.95)]
+    v2 = vol[2][shell_v[:, 0], shell_v[:, 1], shell_v[:, 2]]
+    v5 = vol[5][shell_v[:, 0], shell_v[:, 1], shell_v[:, 2]]
+    q2, q5 = np.quantile(v2, [0.3, 0.8]), np.quantile(v5, [0.1, 0.9])
+    ok = (v2 > q2[0]) & (v2 < q2[1]) & (v5 > q5[0]) & (v5 < q5[1])
+    j = np.flatnonzero(ok)
+    lo[2], hi[2] = v2[j[0]], q2[1]                   # vertex j[0] sits on the lower bound of variable 2
+    cand = j[v2[j] >= v2[j[0]]]
+    lo[5], hi[5] = q5[0], v5[cand].max()             # and a passing vertex on the upper bound of variable 5
+    mask = (1 << 2) | (1 << 5)
+    pts = ((2 * idx[:, ::-1] + 1 - n) / n).astype(np.float32)          # (x, y, z) of vertex [z][y][x]
+    got = oracle.filter_points(vol, R_IN, R_OUT, lo, hi, mask, pts)
+    k = (2 * idx + 1 - n).astype(np.int64)
+    s = (k ** 2).sum(axis=1)                                             # |p|^2 n^2, exact
+    rin2 = np.float32(R_IN) * np.float32(R_IN)
+    rout2 = np.float32(R_OUT) * np.float32(R_OUT)
+    in_shell = (s / n ** 2 >= rin2) & (s / n ** 2 <= rout2)
+    z, y, x = idx[:, 0], idx[:, 1], idx[:, 2]
+    want = in_shell.copy()
+    for v in (2, 5):
+        val = vol[v][z, y, x]
+        want &= (val >= lo[v]) & (val <= hi[v])
+    assert np.array_equal(got.astype(bool), want)
+    assert 0 < want.sum() < want.size
+
+
+def test_filter_points_on_an_affine_field_and_a_position_brush():
+    """v0 = x coordinate of the cell centre: away from the bounds, a point passes iff
+    x0 <= p.x <= x1, it lies in the shell, and it passes the position brush (y <= 0.2)."""
+    n = 40
+    c = (np.arange(n) + 0.5) * 2 / n - 1
+    vol = np.zeros((1, n, n, n), np.float32)
+    vol[0] = c[None, None, :]
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-1.0, 1.0, (20000, 3)).astype(np.float32)
+    x0, x1 = -0.35, 0.5
+    pos = (np.float32([-np.inf, -np.inf, -np.inf, -np.inf]), np.float32([np.inf, 0.2, np.inf, np.inf]), 0b0010)
+    got = oracle.filter_points(vol, R_IN, R_OUT, np.float32([x0]), np.float32([x1]), 1, pts, pos=pos)
+    p64 = pts.astype(np.float64)
+    r = np.sqrt((p64 ** 2).sum(axis=1))
+    xs = np.clip(p64[:, 0], c[0], c[-1])                                 # clamped at the border cells
+    want = (r >= R_IN) & (r <= R_OUT) & (xs >= x0) & (xs <= x1) & (p64[:, 1] <= 0.2)
+    clear = ((np.abs(xs - x0) > 1e-5) & (np.abs(xs - x1) > 1e-5) & (np.abs(r - R_IN) > 1e-5)
+             & (np.abs(r - R_OUT) > 1e-5) & (np.abs(p64[:, 1] - 0.2) > 1e-6))
+    assert np.array_equal(got.astype(bool)[clear], want[clear])
+    assert want[clear].sum() > 1000
+    nan_pt = np.float32([[np.nan, 0.7, 0.0]])
+    assert oracle.filter_points(vol, R_IN, R_OUT, np.float32([-np.inf]), np.float32([np.inf]), 1, nan_pt)[0] == 0
