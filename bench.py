@@ -320,7 +320,9 @@ def run_ours(args):
     vol.set_position_brush(*pos)
     pstats.zero_()
     reps = 10
-    q0, q1, q2, q3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+    seeds = torch.rand((1 << 22, 3), generator=torch.Generator(device=dev).manual_seed(5), device=dev) * 2 - 1
+    seed_flags = torch.empty(seeds.shape[0], dtype=torch.uint8, device=dev)
+    q0, q1, q2, q3, q4 = (torch.cuda.Event(enable_timing=True) for _ in range(5))
     torch.cuda.synchronize()
     q0.record()
     for _ in range(reps):
@@ -332,6 +334,9 @@ def run_ours(args):
     for _ in range(reps):
         sub_cells, _, sub_flags = vol.pc_subsample(3, 100000, c["order"])
     q3.record()
+    for _ in range(reps):
+        vol.filter_points(seeds, out=seed_flags)
+    q4.record()
     torch.cuda.synchronize()
     vol.set_position_brush(np.zeros(4), np.zeros(4), 0)
     n_shell = int(synth.in_shell_mask_approx(c["n"]).sum())
@@ -341,8 +346,13 @@ def run_ours(args):
                 "subsample_ms": round(q2.elapsed_time(q3) / reps, 4),
                 "subsample_lines": int(sub_cells.numel()), "subsample_lines_in_brush": int(sub_flags.sum()),
                 "subsample_in_shell_cells_per_s": round(n_shell / (q2.elapsed_time(q3) / reps / 1e3), 1),
+                "seed_filter_ms": round(q3.elapsed_time(q4) / reps, 4),
+                "seed_filter_points_per_s": round(seeds.shape[0] / (q3.elapsed_time(q4) / reps / 1e3), 1),
+                "seed_filter_passing": int(seed_flags.sum()),
                 "what": "x in [-0.5, 0.5] and radius in [0.6, 0.95] on top of the brush: 1024^2 render, "
-                        "4 histograms with the radius as first axis, 100 000-cell PC line subsample"}
+                        "4 histograms with the radius as first axis, 100 000-cell PC line subsample, "
+                        "brush test of 4 Mi uniform seed points"}
+    del seeds, seed_flags
 
     # ---- end to end through the C ABI from pinned host buffers ----
     # Every step copies its volume host -> device (pinned source) and reads its

@@ -488,6 +488,18 @@ raypc_status raypc_pc_subsample(raypc_ctx *ctx, int vol, int lod, uint32_t seed,
                                 float *out_values_dev, uint8_t *out_in_brush_dev,
                                 long long *out_count, void *stream);
 
+/* Brush test of given points, e.g. pathline seeds (Section 3: only the
+ * pathlines whose seed lies in the current selection are shown).
+ * points_dev: [npts][3] float32 world coordinates (x, y, z), device,
+ * 4-byte aligned; out_pass_dev[i] (uint8, device) receives 1 iff point i
+ * passes exactly the per-sample test of raypc_render on level lod: FP32
+ * |p|^2 in the shell, the position brush, and every restricted variable's
+ * FP32 trilinear value in the volume's brush (NaN coordinates fail). Before
+ * any raypc_set_brush only the shell restricts. Caller-owned buffers;
+ * npts >= 0. */
+raypc_status raypc_filter_points(raypc_ctx *ctx, int vol, int lod, const float *points_dev,
+                                 long long npts, uint8_t *out_pass_dev, void *stream);
+
 /* Same histograms as raypc_pc_histogram, for callers that cannot let the
  * library allocate device memory: hosts whose GPU memory is reserved up front
  * by their own pool (where a cudaMalloc would fail or fragment it), real-time

@@ -797,6 +797,44 @@ raypc_status raypc_pc_subsample(raypc_ctx* ctx, int vol, int lod, uint32_t seed,
     return RAYPC_OK;
 }
 
+raypc_status raypc_filter_points(raypc_ctx* ctx, int vol, int lod, const float* points_dev, long long npts,
+                                 uint8_t* out_pass_dev, void* stream) {
+    if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
+    if (npts < 0) return fail(RAYPC_ERR_INVALID_ARG, "npts %lld < 0", npts);
+    if (npts > 0 && (!points_dev || !out_pass_dev)) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    if (((uintptr_t)points_dev) & 3u) return fail(RAYPC_ERR_INVALID_ARG, "points_dev must be 4-byte aligned");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
+    RenderArgs r{};                       // the brush and the per-sample |p|^2 range of a render
+    if (V->brush_set) {
+        r.brush = V->brush;
+    } else {
+        for (int v = 0; v < kMaxVars; ++v) { r.brush.lo[v] = -INFINITY; r.brush.hi[v] = INFINITY; }
+        for (int p = 0; p < kNumPos; ++p) { r.brush.plo[p] = -INFINITY; r.brush.phi[p] = INFINITY; }
+    }
+    r.rin2 = V->r_in * V->r_in;
+    r.rout2 = V->r_out * V->r_out;
+    finish_position_brush(r);
+    PointFilterArgs a{};
+    a.pairs = L->pairs;
+    a.n = L->n;
+    a.nvars = V->nvars;
+    a.brush = r.brush;
+    a.keep_lo2 = r.keep_lo2;
+    a.keep_hi2 = r.keep_hi2;
+    a.pts = points_dev;
+    a.npts = npts;
+    a.out = out_pass_dev;
+    CK(launch_filter_points(a, V->dtype, (cudaStream_t)stream), "point filter kernel");
+    return RAYPC_OK;
+}
+
 raypc_status raypc_volume_info(raypc_ctx* ctx, int vol, int lod, int* out_n, int* out_nvars,
                                int* out_dtype, int* out_bricks_per_axis) {
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");

@@ -516,6 +516,18 @@ struct SubsampleArgs {
     uint8_t* out_flags;           // m
 };
 size_t pc_subsample_scratch_bytes();
+
+// Brush test of given points (points_kernels.cu).
+struct PointFilterArgs {
+    const void* pairs;            // render layout of the level, storage dtype
+    int n, nvars;
+    BrushArgs brush;              // variable brush and coordinate brushes (pmask bits 0..2)
+    float keep_lo2, keep_hi2;     // |p|^2 range of the shell and the radius brush
+    const float* pts;             // npts x 3 (x, y, z), device
+    long long npts;
+    uint8_t* out;                 // npts flags, device
+};
+cudaError_t launch_filter_points(const PointFilterArgs& a, int dtype, cudaStream_t stream);
 cudaError_t launch_pc_subsample(const SubsampleArgs& a, int dtype, unsigned long long m, unsigned long long N,
                                 void* scratch, cudaStream_t stream);
 

@@ -110,6 +110,7 @@ _SIGS = {
     "raypc_render": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts), _P, _P, _P],
     "raypc_set_position_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_pc_subsample": [_P, _I, _I, _U32, ctypes.c_longlong, _P, _I, _P, _P, _P, _P, _P],
+    "raypc_filter_points": [_P, _I, _I, _P, ctypes.c_longlong, _P, _P],
     "raypc_render_progressive": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts),
                                  _U32, _U32, _P, _P, _P, _P],
     "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
@@ -325,6 +326,17 @@ class Volume:
               _stream(stream))
         m = m.value
         return cells[:m], vals[:m, :naxes], flags[:m]
+
+    def filter_points(self, points: torch.Tensor, lod: int = 0, out: torch.Tensor | None = None, stream=None):
+        """Brush test of points ([npts, 3] float32 device tensor) -> uint8 device tensor [npts]."""
+        pts = points.contiguous()
+        if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 3:
+            raise ValueError("points must be a float32 [npts, 3] tensor")
+        if out is None:
+            out = torch.empty(pts.shape[0], dtype=torch.uint8, device=pts.device)
+        _call("raypc_filter_points", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(pts.data_ptr()),
+              int(pts.shape[0]), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+        return out
 
     def set_tf(self, rgbs, color_var: int, v_lo: float, v_hi: float, stream=None):
         t = np.ascontiguousarray(np.asarray(rgbs, dtype=np.float32).reshape(TF_ENTRIES, 4))

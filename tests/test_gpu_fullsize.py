@@ -97,6 +97,13 @@ def test_full_size_frame_and_histograms(rp, wl_name):
         assert np.array_equal(cells.cpu().numpy(), oc)
         assert np.array_equal(vals.cpu().numpy().view(np.uint32), ov.view(np.uint32))
         assert np.array_equal(flags.cpu().numpy(), of)
+        # seed filtering of a million points
+        rng = np.random.default_rng(1)
+        pts = rng.uniform(-1.0, 1.0, (1 << 20, 3)).astype(np.float32)
+        got = vol.filter_points(torch.from_numpy(pts).cuda()).cpu().numpy()
+        want = oracle.filter_points(stored, synth.R_IN, synth.R_OUT, wl.brush.lo, wl.brush.hi,
+                                    wl.brush.active_mask, pts)
+        assert np.array_equal(got, want) and want.sum() > 0
         # a re-ingested volume (next time step path) renders identically after rebuilding
         a, _ = vol.render(wl.cam, c["w"], c["h"])
         a = a.clone()

@@ -670,3 +670,32 @@ def test_batch_and_server_take_position_brushes(ctx, rp):
                 assert torch.equal(out["hist"], want)
             srv.release(rid)
     v.free()
+
+
+@pytest.mark.parametrize("n,store", [(48, "f32"), (33, "f16")])
+def test_filter_points_bit_exact(ctx, rp, n, store):
+    vol = synth.make_shell_volume(n, seed=17)
+    brush = synth.make_brush(vol, "c2")
+    v = load(ctx, vol, store, n_lod=1, brush=brush)
+    levels = oracle_levels(stored(vol, store), 1, store)
+    rng = np.random.default_rng(n)
+    pts = rng.uniform(-1.1, 1.1, (50000, 3)).astype(np.float32)
+    c = ((2 * np.arange(n) + 1 - n) / n).astype(np.float32)
+    pts[:n] = np.stack([c, c[::-1], np.zeros(n, np.float32)], 1)       # cell centres and an axis plane
+    pts[n] = [np.nan, 0.7, 0.0]
+    pts[n + 1] = [0.0, 0.0, 0.8]
+    for pos in (None, POS):
+        if pos is None:
+            v.set_position_brush(np.zeros(4), np.zeros(4), 0)
+        else:
+            v.set_position_brush(*pos)
+        for lod in range(2):
+            got = v.filter_points(torch.from_numpy(pts).cuda(), lod=lod).cpu().numpy()
+            want = oracle.filter_points(levels[lod], R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, pts, pos=pos)
+            assert np.array_equal(got, want), (pos is None, lod)
+            assert 0 < want.sum() < want.size
+    assert got[n] == 0
+    with pytest.raises(rp.RaypcError):
+        v.filter_points(torch.zeros((4, 3), device="cuda"), lod=3)
+    assert v.filter_points(torch.zeros((0, 3), device="cuda")).numel() == 0
+    v.free()
