@@ -75,7 +75,8 @@ def _load():
             lib.oracle_render.restype = i32
             lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                                P, P, u32, P, i32, f32, f32, P, i32, P,
-                                               ctypes.c_int64, P, P, i32, u32, u32, P, P, u32]
+                                               ctypes.c_int64, P, P, i32, u32, u32, P, P, u32, i32]
+            lib.oracle_tf_visibility.argtypes = [P, i32, i32, i32, P, f32, f32, P]
             lib.oracle_render_pass.restype = i32
             lib.oracle_jitter.argtypes = [u32, u32, ctypes.c_uint64]
             lib.oracle_jitter.restype = f32
@@ -231,6 +232,17 @@ def filter_points(vol, r_in, r_out, lo, hi, active_mask, points, pos=None) -> np
     return out
 
 
+def tf_visibility(vol, color_var, tf_rgbs, tf_lo, tf_hi) -> np.ndarray:
+    """TF visibility of the 4^3 sub-bricks -> uint8 [nsb, nsb, nsb]."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    nsb = (n + 3) // 4
+    out = np.zeros((nsb, nsb, nsb), np.uint8)
+    _load().oracle_tf_visibility(_ptr(v), n, V, int(color_var), _ptr(_f32(tf_rgbs)), np.float32(tf_lo),
+                                 np.float32(tf_hi), _ptr(out))
+    return out
+
+
 def subsample_key(seed, cell) -> int:
     """Subsample key of cell index `cell` under `seed`."""
     return int(_load().oracle_subsample_key(int(seed) & 0xFFFFFFFF, int(cell)))
@@ -248,7 +260,7 @@ def splitmix64_output(z) -> int:
 
 def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
            tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0,
-           seed=0, pass_=0, pos=None):
+           seed=0, pass_=0, pos=None, tf_skip=False):
     """Render (or render a subset of pixels) -> (rgba float64 [npix,4], counts uint32 [npix,2]).
 
     counts[:, 0] = lattice samples marched (entry to termination),
@@ -278,7 +290,7 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
                                     np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
                                     pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads),
                                     int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF,
-                                    _ptr(plo), _ptr(phi), pmask)
+                                    _ptr(plo), _ptr(phi), pmask, int(bool(tf_skip)))
     if rc != 0:
         raise ValueError("oracle_render: invalid arguments")
     if pixels is None:

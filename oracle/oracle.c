@@ -440,6 +440,8 @@ typedef struct {
     uint32_t active_mask;
     const float *plo, *phi; /* position brush (axes x, y, z, radius) */
     uint32_t pmask;
+    const uint8_t *tfvis;   /* TF visibility of the 4^3 sub-bricks (NULL: no TF skipping) */
+    int nsb;
     const float *tf;        /* 256 x (r,g,b,sigma) */
     int color_var;
     float tf_lo, tf_hi;
@@ -668,6 +670,8 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
             int i0[3];
             float f[3];
             for (int a = 0; a < 3; a++) grid_coord32(p[a], J->n, &i0[a], &f[a]);
+            if (J->tfvis && !J->tfvis[((size_t)(i0[2] >> 2) * J->nsb + (i0[1] >> 2)) * J->nsb + (i0[0] >> 2)])
+                continue;
             int keep = 1;
             for (int v = 0; v < J->nvars && keep; v++) {
                 if (!((J->active_mask >> v) & 1u)) continue;
@@ -722,17 +726,69 @@ static void *render_worker(void *arg) {
     return NULL;
 }
 
+/* ------------------------------------------------------------------ */
+/* TF-aware skipping (a reading of the no-rebuild design of Section 2.2 */
+/* applied to the transfer function). A sample contributes nothing when */
+/* both TF entries it interpolates have sigma = 0: alpha is then exactly */
+/* 0. The FP32 colour value of a sample in a 4^3 sub-brick lies in      */
+/* [min - d, max + d] of the sub-brick's colour values (the brush       */
+/* margin d; no bound when m > 2^126), and the entry index             */
+/* J(v) = min(floor(clamp((v - tf_lo) * tf_scale, 0, 255)), 254), with  */
+/* FP32 tf_scale = 255 / (tf_hi - tf_lo), is non-decreasing in v, so    */
+/* its samples touch only entries J(min - d) .. J(max + d) + 1 -- and    */
+/* entry 0 when the colour value is NaN. A sub-brick is TF-visible iff   */
+/* sigma > 0 at one of those entries or at entry 0. With TF skipping,    */
+/* samples in TF-invisible sub-bricks are not kept (the image is the     */
+/* same; only the kept counts drop).                                     */
+/* ------------------------------------------------------------------ */
+static int tf_entry(float v, float tf_lo, float tf_scale) {
+    float sp = (v - tf_lo) * tf_scale;
+    sp = fminf(fmaxf(sp, 0.0f), 255.0f);
+    int j = (int)sp;
+    return j > 254 ? 254 : j;
+}
+
+void oracle_tf_visibility(const float *vol, int n, int nvars, int color_var, const float *tf,
+                          float tf_lo, float tf_hi, uint8_t *vis /* nsb^3, nsb = ceil(n/4) */) {
+    int nsb = (n + 3) / 4;
+    size_t nsub = (size_t)nsb * nsb * nsb;
+    float *mn = (float *)malloc(sizeof(float) * nsub * nvars), *mx = (float *)malloc(sizeof(float) * nsub * nvars);
+    oracle_brick_minmax(vol, n, nvars, 4, mn, mx);
+    float scale = 255.0f / (tf_hi - tf_lo);
+    for (size_t b = 0; b < nsub; b++) {
+        float lo = mn[b * nvars + color_var], hi = mx[b * nvars + color_var];
+        float m = fmaxf(fabsf(lo), fabsf(hi));
+        int visible = tf[3] > 0.0f || !(m <= 0x1p126f);
+        if (!visible) {
+            float d = fmaf(m, 0x1p-20f, 0x1p-120f);
+            int j0 = tf_entry(lo - d, tf_lo, scale), j1 = tf_entry(hi + d, tf_lo, scale) + 1;
+            for (int j = j0; j <= j1 && !visible; j++)
+                if (tf[4 * j + 3] > 0.0f) visible = 1;
+        }
+        vis[b] = (uint8_t)visible;
+    }
+    free(mn);
+    free(mx);
+}
+
 int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_out,
                        const float *cam, int w, int h, float dt,
                        const float *lo, const float *hi, uint32_t active_mask,
                        const float *tf, int color_var, float tf_lo, float tf_hi,
                        const double *bg, int ert, const int64_t *pixels, int64_t npix,
                        double *out, uint32_t *counts, int nthreads, uint32_t seed, uint32_t pass,
-                       const float *plo, const float *phi, uint32_t pmask) {
+                       const float *plo, const float *phi, uint32_t pmask, int tf_skip) {
     if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
     render_job J;
     J.seed = seed; J.pass = pass;
     J.plo = plo; J.phi = phi; J.pmask = pmask;
+    J.nsb = (n + 3) / 4;
+    uint8_t *vis = NULL;
+    if (tf_skip) {
+        vis = (uint8_t *)malloc((size_t)J.nsb * J.nsb * J.nsb);
+        oracle_tf_visibility(vol, n, nvars, color_var, tf, tf_lo, tf_hi, vis);
+    }
+    J.tfvis = vis;
     J.vol = vol; J.n = n; J.nvars = nvars; J.r_in = r_in; J.r_out = r_out;
     J.cam = cam; J.w = w; J.h = h; J.dt = dt; J.lo = lo; J.hi = hi;
     J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
@@ -746,6 +802,7 @@ int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_o
     for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, render_worker, &J);
     for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
     free(th);
+    free(vis);
     pthread_mutex_destroy(&J.lock);
     return 0;
 }
@@ -758,7 +815,7 @@ int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
                   double *out, uint32_t *counts, int nthreads) {
     return oracle_render_pass(vol, n, nvars, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf, color_var,
                               tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u,
-                              NULL, NULL, 0u);
+                              NULL, NULL, 0u, 0);
 }
 
 int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }

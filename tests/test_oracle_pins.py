@@ -1055,3 +1055,64 @@ def test_filter_points_on_an_affine_field_and_a_position_brush():
     assert want[clear].sum() > 1000
     nan_pt = np.float32([[np.nan, 0.7, 0.0]])
     assert oracle.filter_points(vol, R_IN, R_OUT, np.float32([-np.inf]), np.float32([np.inf]), 1, nan_pt)[0] == 0
+
+
+# ----------------------------------------------------------------------------
+# TF-aware skipping: samples whose two TF entries have sigma = 0 add nothing
+# ----------------------------------------------------------------------------
+def _tf_variants():
+    base = synth.tf_ramp()                                   # sigma = 0 over the lowest 30 %
+    band = base.copy()
+    band[:, 3] = 0.0
+    band[100:141, 3] = 30.0                                  # one opaque band
+    comb = base.copy()
+    comb[:, 3] = np.where((np.arange(256) // 7) % 3 == 1, 25.0, 0.0)   # many band edges, entry 0 clear
+    zero = base.copy()
+    zero[:, 3] = 0.0
+    return {"ramp": base, "band": band, "comb": comb, "zero": zero}
+
+
+@pytest.mark.parametrize("name", ["ramp", "band", "comb", "zero"])
+def test_tf_skipping_keeps_the_image_exactly(shell32, name):
+    vol = shell32
+    tf_rgbs = _tf_variants()[name]
+    tfv = synth.make_tf(torch.from_numpy(vol), "T_anom")
+    brush = synth.make_brush(torch.from_numpy(vol), "c1")
+    cam = synth.orbit_camera(30, 20, 3.0)
+    args = (vol, R_IN, R_OUT, cam.as_array(), 48, 40, 1.0 / 32, brush.lo, brush.hi, brush.active_mask,
+            tf_rgbs, tfv.color_var, tfv.v_lo, tfv.v_hi)
+    for ert in (False, True):
+        img0, c0 = oracle.render(*args, ert=ert)
+        img1, c1 = oracle.render(*args, ert=ert, tf_skip=True)
+        assert np.array_equal(img0, img1), ert                 # skipped samples have alpha exactly 0
+        assert np.array_equal(c0[..., 0], c1[..., 0])
+        assert np.all(c1[..., 1] <= c0[..., 1])
+    if name == "zero":
+        assert c1[..., 1].sum() == 0
+    elif name != "comb":                                       # comb: every sub-brick meets a band
+        assert 0 < c1[..., 1].sum() < c0[..., 1].sum()
+
+
+def test_tf_visibility_of_constant_sub_bricks():
+    """A sub-brick whose colour values are all v is visible iff sigma > 0 at entry J(v),
+    J(v) + 1 or 0 (d is far below an entry's width here)."""
+    n = 16
+    vals = np.linspace(0.02, 0.98, 64).astype(np.float32).reshape(4, 4, 4)
+    vol = np.repeat(np.repeat(np.repeat(vals, 4, 0), 4, 1), 4, 2)[None].astype(np.float32)
+    # vertices 4s..4s+4 include the next sub-brick's first vertex: make each sub-brick's
+    # values constant over its apron by reading the visibility of interior-constant blocks only
+    tf = _tf_variants()["comb"]
+    vis = oracle.tf_visibility(vol, 0, tf, 0.0, 1.0)
+    sig = tf[:, 3] > 0
+    for z in range(4):
+        for y in range(4):
+            for x in range(4):
+                lo = vals[z, y, x]
+                hi = max(vals[min(z + 1, 3), y, x], vals[z, min(y + 1, 3), x], vals[z, y, min(x + 1, 3)],
+                         vals[min(z + 1, 3), min(y + 1, 3), min(x + 1, 3)], lo,
+                         vals[min(z + 1, 3), min(y + 1, 3), x], vals[min(z + 1, 3), y, min(x + 1, 3)],
+                         vals[z, min(y + 1, 3), min(x + 1, 3)])
+                j0 = int(np.floor(np.float32(lo) * np.float32(255.0)))
+                j1 = min(int(np.floor(np.float32(hi) * np.float32(255.0))), 254) + 1
+                want = bool(sig[0] or sig[j0:j1 + 1].any())
+                assert bool(vis[z, y, x]) == want, (z, y, x)
