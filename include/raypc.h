@@ -122,6 +122,18 @@ typedef struct raypc_render_opts {
     float bg[4];         /* premultiplied background RGBA composited under     */
     uint32_t *counts_dev;/* optional [h][w][2] uint32: per pixel, lattice
                             samples marched and samples kept (debug/testing)    */
+    int tf_skip;         /* nonzero: TF-aware skipping (single-frame renders;
+                            raypc_render_batch rejects it). A sample whose two
+                            transfer-function entries both have sigma = 0 adds
+                            exactly nothing; a 4^3 sub-brick is skipped when its
+                            colour values v in [min - d, max + d] (brush margin
+                            d; never when max(|min|,|max|) > 2^126) reach only
+                            entries J(v) .. J(v)+1 with sigma = 0 and entry 0
+                            (where a NaN colour lands) has sigma = 0 too, with
+                            J(v) = min(floor(clamp((v - v_lo) * (255 / (v_hi -
+                            v_lo)), 0, 255)), 254) in FP32. The image is
+                            unchanged bit for bit; samples in skipped
+                            sub-bricks are not counted as kept.                 */
 } raypc_render_opts;
 
 /* ---------------------------------------------------------------------- */

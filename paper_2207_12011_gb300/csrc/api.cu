@@ -49,7 +49,7 @@ namespace {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.cls};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.cls, L.tf_active, L.tf_sactive};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -57,11 +57,12 @@ void free_level(Level& L) {
 
 void free_bricks(Level& L) {
     void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.tf_active, L.tf_sactive};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L.bmin = L.bmax = L.sbmin = L.sbmax = nullptr;
     L.active = L.skippable = L.list = L.n_active = L.sactive = L.slist = L.scount = nullptr;
+    L.tf_active = L.tf_sactive = nullptr;
     L.pass_count = nullptr;
     L.bricks = L.classified = L.cls_valid = false;
 }
@@ -133,6 +134,8 @@ raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
     if ((st = ctx->alloc((void**)&L.sbmin, smm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.sbmax, smm, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.sactive, L.nswords() * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.tf_sactive, L.nswords() * sizeof(uint32_t), &V->bytes)) ||
+        (st = ctx->alloc((void**)&L.tf_active, words, &V->bytes)) ||
         (st = ctx->alloc((void**)&L.slist, L.nsbricks() * sizeof(uint32_t), &V->bytes)) ||
         (st = ctx->alloc((void**)&L.scount, sizeof(uint32_t), &V->bytes)) ||
         (st = ctx->alloc((void**)&L.bmin, mm, &V->bytes)) ||
@@ -594,6 +597,33 @@ raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_
     return RAYPC_OK;
 }
 
+// With tf_skip, the render reads the activity bits ANDed with the TF visibility of
+// the level's bricks and sub-bricks (computed for this render on its stream).
+static raypc_status apply_tf_skip(Volume* V, Level& L, const raypc_render_opts* opts, RenderArgs& a, cudaStream_t s) {
+    if (!opts || !opts->tf_skip) return RAYPC_OK;
+    TfVisArgs t{};
+    t.n = L.n;
+    t.nb = L.nb;
+    t.nsb = L.nsb;
+    t.nvars = V->nvars;
+    t.color_var = V->color_var;
+    t.bmin = L.bmin;
+    t.bmax = L.bmax;
+    t.sbmin = L.sbmin;
+    t.sbmax = L.sbmax;
+    t.active = L.active;
+    t.sactive = L.sactive;
+    t.tf = V->tf;
+    t.tf_lo = a.tf_lo;
+    t.tf_scale = a.tf_scale;
+    t.out_active = L.tf_active;
+    t.out_sactive = L.tf_sactive;
+    CK(launch_tf_visibility(t, s), "TF visibility kernel");
+    a.lv.active = L.tf_active;
+    a.lv.sactive = L.tf_sactive;
+    return RAYPC_OK;
+}
+
 raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* cam, int w, int h,
                           const raypc_render_opts* opts, float* out_rgba_dev,
                           unsigned long long* stats_dev, void* stream) {
@@ -610,6 +640,7 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if ((st = ensure_classified(V, *L, (cudaStream_t)stream))) return st;
     if ((st = ensure_cell_classes(ctx, V, *L, (cudaStream_t)stream))) return st;
     a.cls = L->cls;
+    if ((st = apply_tf_skip(V, *L, opts, a, (cudaStream_t)stream))) return st;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }
@@ -638,6 +669,7 @@ raypc_status raypc_render_progressive(raypc_ctx* ctx, int vol, int lod, const ra
     a.jit_pass = pass;
     a.accum = reinterpret_cast<float4*>(accum_rgba_dev);
     a.accum_w = 1.0f / (float)((double)pass + 1.0);
+    if ((st = apply_tf_skip(V, *L, opts, a, (cudaStream_t)stream))) return st;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }

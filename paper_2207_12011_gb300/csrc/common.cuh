@@ -499,6 +499,23 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
 int render_batch_blocks_per_sm(int dtype, int variant);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
+// TF-aware skipping (volume_kernels.cu): activity bits of the 8^3 bricks and
+// 4^3 sub-bricks of a level ANDed with their TF visibility.
+struct TfVisArgs {
+    int n, nb, nsb, nvars, color_var;
+    const float* bmin;            // [nb^3][nvars]
+    const float* bmax;
+    const float* sbmin;           // [nsb^3][nvars]
+    const float* sbmax;
+    const uint32_t* active;       // brush activity bits
+    const uint32_t* sactive;
+    const float4* tf;             // 256 entries (r, g, b, sigma)
+    float tf_lo, tf_scale;
+    uint32_t* out_active;         // nwords / nswords
+    uint32_t* out_sactive;
+};
+cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream);
+
 // PC line subsample (pcsub_kernels.cu).
 constexpr int kSubMaxSegments = 8192;   // warp-owned row segments of the ordered compaction
 struct SubsampleArgs {

@@ -58,6 +58,8 @@ struct Level {
     uint32_t* slist = nullptr;    // active sub-brick ids (any order) and their number
     uint32_t* scount = nullptr;
     uint16_t* cls = nullptr;      // cell classes under the current brush (n^3), computed on demand
+    uint32_t* tf_active = nullptr;   // activity AND TF visibility (renders with tf_skip)
+    uint32_t* tf_sactive = nullptr;
     bool cls_valid = false;
     bool bricks = false;
     bool classified = false;

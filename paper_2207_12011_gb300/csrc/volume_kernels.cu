@@ -518,4 +518,68 @@ cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
+namespace {
+
+// Entry index J(v) of a colour value, as the march computes it (FP32, monotone in v).
+__device__ __forceinline__ int tf_entry(float v, float tf_lo, float tf_scale) {
+    float sp = __fmul_rn(__fsub_rn(v, tf_lo), tf_scale);
+    sp = fminf(fmaxf(sp, 0.0f), 255.0f);
+    return min((int)sp, kTF - 2);
+}
+
+// One thread per brick (entries 0..nbricks-1, padded to whole words) and per
+// sub-brick (the entries after them): activity AND TF visibility. Visible iff
+// sigma > 0 at entry 0 (a NaN colour value lands there), or the colour range
+// cannot be bounded (max(|min|,|max|) > 2^126), or sigma > 0 at an entry of
+// J(min - d) .. J(max + d) + 1 (d the brush margin). A brick's range holds
+// its sub-bricks' ranges, so an invisible brick has only invisible sub-bricks.
+__global__ void __launch_bounds__(256) k_tf_visibility(TfVisArgs A) {
+    __shared__ int s_pre[kTF + 1];             // s_pre[j] = entries < j with sigma > 0
+    if (threadIdx.x < 32) {
+        int run = 0;
+        for (int base = 0; base < kTF; base += 32) {
+            const bool nz = A.tf[base + threadIdx.x].w > 0.0f;
+            const unsigned b = __ballot_sync(0xffffffffu, nz);
+            s_pre[base + threadIdx.x] = run + __popc(b & ((1u << threadIdx.x) - 1u));
+            run += __popc(b);
+        }
+        if (threadIdx.x == 0) s_pre[kTF] = run;
+    }
+    __syncthreads();
+    const size_t nbr = (size_t)A.nb * A.nb * A.nb, nsub = (size_t)A.nsb * A.nsb * A.nsb;
+    const size_t nbr_pad = (nbr + 31) & ~(size_t)31;
+    const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool is_sub = g >= nbr_pad;
+    const size_t b = is_sub ? g - nbr_pad : g;
+    const size_t cnt = is_sub ? nsub : nbr;
+    bool bit = false;
+    if (b < cnt) {
+        const uint32_t* act = is_sub ? A.sactive : A.active;
+        bit = (act[b >> 5] >> (b & 31)) & 1u;
+        if (bit && s_pre[1] == 0) {                 // entry 0 transparent: the range decides
+            const float mn = (is_sub ? A.sbmin : A.bmin)[b * A.nvars + A.color_var];
+            const float mx = (is_sub ? A.sbmax : A.bmax)[b * A.nvars + A.color_var];
+            const float m = fmaxf(fabsf(mn), fabsf(mx));
+            if (m <= 0x1p126f) {
+                const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+                const int j0 = tf_entry(__fsub_rn(mn, d), A.tf_lo, A.tf_scale);
+                const int j1 = tf_entry(__fadd_rn(mx, d), A.tf_lo, A.tf_scale) + 1;
+                bit = j0 <= j1 && s_pre[j1 + 1] - s_pre[j0] > 0;
+            }
+        }
+    }
+    const unsigned word = __ballot_sync(0xffffffffu, bit);
+    if ((threadIdx.x & 31) == 0 && b < ((cnt + 31) & ~(size_t)31)) (is_sub ? A.out_sactive : A.out_active)[b >> 5] = word;
+}
+
+}  // namespace
+
+cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream) {
+    const size_t nbr = (size_t)a.nb * a.nb * a.nb, nsub = (size_t)a.nsb * a.nsb * a.nsb;
+    const size_t total = ((nbr + 31) & ~(size_t)31) + nsub;
+    k_tf_visibility<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace raypc

@@ -53,7 +53,8 @@ VARIANTS = {1: "8x4", 2: "16x2", 3: "4x8"}
 
 class RenderOpts(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("ert", ctypes.c_int), ("skip", ctypes.c_int),
-                ("variant", ctypes.c_int), ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p)]
+                ("variant", ctypes.c_int), ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p),
+                ("tf_skip", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -346,7 +347,7 @@ class Volume:
     def render(self, cam, w: int, h: int, lod: int = 0, step: float = 0.0, ert: bool = True,
                skip: bool | None = None, bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
                counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None,
-               variant: int = AUTO, stream=None):
+               variant: int = AUTO, tf_skip: bool = False, stream=None):
         """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None).
 
         skip: None = tuned choice (default on), True / False = brick skipping on / off;
@@ -357,7 +358,7 @@ class Volume:
             out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
         if counts is True:
             counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
-        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant)
+        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip)
         c = camera_from(cam)
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _call("raypc_render", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
@@ -368,7 +369,7 @@ class Volume:
                            lod: int = 0, step: float = 0.0, ert: bool = True, skip: bool | None = None,
                            bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
                            counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None,
-                           variant: int = AUTO, stream=None):
+                           variant: int = AUTO, tf_skip: bool = False, stream=None):
         """One progressive pass (jittered lattice; pass 0 equals render). accum, an (h, w, 4)
         float32 device tensor or None, holds the running mean of passes 0..pass_ and is
         updated in place. Returns (this pass's image, counts or None)."""
@@ -377,7 +378,7 @@ class Volume:
             out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
         if counts is True:
             counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
-        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant)
+        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip)
         c = camera_from(cam)
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         ap = ctypes.c_void_p(accum.data_ptr()) if accum is not None else None
@@ -479,7 +480,8 @@ def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=Non
     return out
 
 
-def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, variant=AUTO) -> RenderOpts:
+def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, variant=AUTO,
+          tf_skip=False) -> RenderOpts:
     o = RenderOpts()
     o.step = float(step)
     o.ert = int(bool(ert))
@@ -488,6 +490,7 @@ def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, v
     for i in range(4):
         o.bg[i] = float(bg[i])
     o.counts_dev = counts.data_ptr() if isinstance(counts, torch.Tensor) else None
+    o.tf_skip = int(bool(tf_skip))
     return o
 
 
@@ -521,7 +524,7 @@ def _view_array(ctx, views):
         v.active_mask = int(q.get("mask", 0)) & 0xFFFFFFFF
         v.opts = _opts(q.get("step", 0.0), q.get("ert", True), q.get("skip", None),
                        q.get("bg", (0.0, 0.0, 0.0, 0.0)), counts if isinstance(counts, torch.Tensor) else None,
-                       q.get("variant", AUTO))
+                       q.get("variant", AUTO), q.get("tf_skip", False))
         v.out_rgba_dev = out.data_ptr()
         v.stats_dev = stats.data_ptr() if stats is not None else None
         _fill_pos(v, q.get("pos"))

@@ -699,3 +699,52 @@ def test_filter_points_bit_exact(ctx, rp, n, store):
         v.filter_points(torch.zeros((4, 3), device="cuda"), lod=3)
     assert v.filter_points(torch.zeros((0, 3), device="cuda")).numel() == 0
     v.free()
+
+
+# ----------------------------------------------------------------------------
+# TF-aware skipping
+# ----------------------------------------------------------------------------
+def _tf_with(tf, kind):
+    rgbs = tf.rgbs.copy()
+    if kind == "band":
+        rgbs[:, 3] = 0.0
+        rgbs[100:141, 3] = 30.0
+    elif kind == "comb":
+        rgbs[:, 3] = np.where((np.arange(256) // 7) % 3 == 1, 25.0, 0.0)
+    elif kind == "zero":
+        rgbs[:, 3] = 0.0
+    return synth.TransferFunction(rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+
+
+@pytest.mark.parametrize("n,store", [(48, "f32"), (33, "f16")])
+def test_tf_skip_keeps_the_image_and_matches_oracle(ctx, rp, n, store):
+    vol = synth.make_shell_volume(n, seed=19)
+    brush = synth.make_brush(vol, "c1")
+    base_tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    w, h = 67, 41
+    v = load(ctx, vol, store, n_lod=1, brush=brush, tf=base_tf)
+    levels = oracle_levels(stored(vol, store), 1, store)
+    for kind in ("ramp", "band", "comb", "zero"):
+        tf = _tf_with(base_tf, kind)
+        v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+        for lod in (0, 1):
+            m = levels[lod].shape[1]
+            for ert, skip in ((False, True), (False, False), (True, True)):
+                img0, c0 = v.render(cam, w, h, lod=lod, ert=ert, skip=skip, counts=True)
+                img1, c1 = v.render(cam, w, h, lod=lod, ert=ert, skip=skip, counts=True, tf_skip=True)
+                torch.cuda.synchronize()
+                assert torch.equal(img0, img1), (kind, lod, ert, skip)      # bit for bit
+                assert torch.equal(c0[..., 0], c1[..., 0])
+                if not ert:
+                    _, rc = oracle.render(levels[lod], R_IN, R_OUT, cam.as_array(), w, h, 1.0 / m, brush.lo,
+                                          brush.hi, brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi,
+                                          ert=False, tf_skip=True)
+                    assert np.array_equal(c1.cpu().numpy().astype(np.uint32), rc), (kind, lod, skip)
+            if kind == "zero":
+                assert int(c1[..., 1].sum()) == 0
+    b = rp.Batch(ctx, 2)
+    with pytest.raises(rp.RaypcError):
+        b.render([dict(vol=v, cam=cam, w=8, h=8, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, tf_skip=True)])
+    b.close()
+    v.free()
