@@ -134,6 +134,11 @@ typedef struct raypc_render_opts {
                             v_lo)), 0, 255)), 254) in FP32. The image is
                             unchanged bit for bit; samples in skipped
                             sub-bricks are not counted as kept.                 */
+    float *depth_dev;    /* optional [h][w] float32: per pixel the ray parameter
+                            t (world distance from the eye) of the first kept
+                            sample, t0 + (k + j) * step in FP32 exactly as the
+                            march computes it; +inf where no sample is kept.
+                            The depth that raypc_warp_image reprojects.         */
 } raypc_render_opts;
 
 /* ---------------------------------------------------------------------- */

@@ -75,7 +75,8 @@ def _load():
             lib.oracle_render.restype = i32
             lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                                P, P, u32, P, i32, f32, f32, P, i32, P,
-                                               ctypes.c_int64, P, P, i32, u32, u32, P, P, u32, i32]
+                                               ctypes.c_int64, P, P, i32, u32, u32, P, P, u32, i32, P]
+            lib.oracle_warp.argtypes = [P, P, P, P, i32, i32, P, P, P]
             lib.oracle_tf_visibility.argtypes = [P, i32, i32, i32, P, f32, f32, P]
             lib.oracle_render_pass.restype = i32
             lib.oracle_jitter.argtypes = [u32, u32, ctypes.c_uint64]
@@ -260,7 +261,7 @@ def splitmix64_output(z) -> int:
 
 def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
            tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0,
-           seed=0, pass_=0, pos=None, tf_skip=False):
+           seed=0, pass_=0, pos=None, tf_skip=False, return_depth=False):
     """Render (or render a subset of pixels) -> (rgba float64 [npix,4], counts uint32 [npix,2]).
 
     counts[:, 0] = lattice samples marched (entry to termination),
@@ -284,15 +285,29 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
         pix_ptr = _ptr(pix)
     out = np.zeros((npix, 4), np.float64)
     cnt = np.zeros((npix, 2), np.uint32)
+    depth = np.zeros(npix, np.float32)
     rc = _load().oracle_render_pass(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(cam),
                                     int(w), int(h), np.float32(dt), _ptr(_f32(lo)), _ptr(_f32(hi)),
                                     int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
                                     np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
                                     pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads),
                                     int(seed) & 0xFFFFFFFF, int(pass_) & 0xFFFFFFFF,
-                                    _ptr(plo), _ptr(phi), pmask, int(bool(tf_skip)))
+                                    _ptr(plo), _ptr(phi), pmask, int(bool(tf_skip)), _ptr(depth))
     if rc != 0:
         raise ValueError("oracle_render: invalid arguments")
     if pixels is None:
-        return out.reshape(h, w, 4), cnt.reshape(h, w, 2)
-    return out, cnt
+        out, cnt, depth = out.reshape(h, w, 4), cnt.reshape(h, w, 2), depth.reshape(h, w)
+    return (out, cnt, depth) if return_depth else (out, cnt)
+
+
+def warp(src_rgba, src_depth, cam_from, cam_to, bg=(0.0, 0.0, 0.0, 0.0)):
+    """Forward-warp an (h, w, 4) float32 image with its (h, w) depth to a new camera ->
+    (float32 image (h, w, 4), int32 source index per pixel or -1)."""
+    src = _f32(src_rgba)
+    h, w = src.shape[0], src.shape[1]
+    dep = _f32(src_depth).reshape(h, w)
+    out = np.zeros((h, w, 4), np.float32)
+    idx = np.zeros((h, w), np.int32)
+    _load().oracle_warp(_ptr(src), _ptr(dep), _ptr(_f32(cam_from)), _ptr(_f32(cam_to)), int(w), int(h),
+                        _ptr(_f32(bg)), _ptr(out), _ptr(idx))
+    return out, idx

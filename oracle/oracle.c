@@ -26,7 +26,8 @@
  *   - the random subsample of cells whose polylines the PC plot draws
  *     (Section 2.1);
  *   - the brush test of given points (pathline seeds inside the current
- *     selection, Section 3).
+ *     selection, Section 3);
+ *   - image warping of a rendered frame to a new camera (Section 2.2).
  *
  * Precision. Every continuous quantity (ray geometry for the colour value,
  * transfer-function lookup, opacity, compositing) is FP64. Every quantity that
@@ -451,6 +452,7 @@ typedef struct {
     int64_t npix;
     double *out;            /* npix x 4 */
     uint32_t *counts;       /* npix x 2: marched lattice samples, kept samples (may be NULL) */
+    float *depth;           /* npix: FP32 t of the first kept sample, +inf if none (may be NULL) */
     uint32_t seed, pass;    /* progressive pass: lattice offset of every pixel (pass 0: 1/2) */
     int64_t next;           /* shared work counter */
     pthread_mutex_t lock;
@@ -497,25 +499,36 @@ static void normalize_f32(float a[3]) {
     a[0] = a[0] / l; a[1] = a[1] / l; a[2] = a[2] / l;
 }
 
-static ray32 make_ray32(const render_job *J, int px, int py) {
-    ray32 r;
-    const float *c = J->cam;
-    float F[3] = {c[3] - c[0], c[4] - c[1], c[5] - c[2]};
+/* Pinhole camera basis (FP32, fixed order): view F = normalize(target - eye),  */
+/* right R = normalize(cross(F, up)), true up U = cross(R, F).                   */
+static void camera_basis32(const float *c, float F[3], float R[3], float U[3]) {
+    F[0] = c[3] - c[0]; F[1] = c[4] - c[1]; F[2] = c[5] - c[2];
     normalize_f32(F);
-    float R[3], U[3];
     cross_f32(F, c + 6, R);
     normalize_f32(R);
     cross_f32(R, F, U);
+}
+
+/* Direction of the ray through pixel (px, py) of a w x h image (FP32). */
+static void camera_ray32(const float *c, int w, int h, int px, int py, float d[3]) {
+    float F[3], R[3], U[3];
+    camera_basis32(c, F, R, U);
     float th = c[9];
-    float aspect = (float)J->w / (float)J->h;
+    float aspect = (float)w / (float)h;
     float sxs = th * aspect;
-    float qx = (float)(2 * px + 1) / (float)J->w;
-    float qy = (float)(2 * py + 1) / (float)J->h;
+    float qx = (float)(2 * px + 1) / (float)w;
+    float qy = (float)(2 * py + 1) / (float)h;
     float sx = (qx - 1.0f) * sxs;
     float sy = (1.0f - qy) * th;
-    float d[3];
     for (int a = 0; a < 3; a++) d[a] = fmaf(sy, U[a], fmaf(sx, R[a], F[a]));
     normalize_f32(d);
+}
+
+static ray32 make_ray32(const render_job *J, int px, int py) {
+    ray32 r;
+    const float *c = J->cam;
+    float d[3];
+    camera_ray32(c, J->w, J->h, px, py, d);
     for (int a = 0; a < 3; a++) { r.o[a] = c[a]; r.d[a] = d[a]; }
     /* Sphere entry/exit through the closest point to the centre. */
     float b = dot_f32(r.o, r.d);
@@ -649,7 +662,7 @@ static double interp64(const render_job *J, int v, const double p[3]) {
     return s;
 }
 
-static void render_pixel(const render_job *J, int px, int py, double *out, uint32_t *cnt) {
+static void render_pixel(const render_job *J, int px, int py, double *out, uint32_t *cnt, float *depth) {
     ray32 r = make_ray32(J, px, py);
     ray64 q = make_ray64(J, px, py);
     const float jit = oracle_jitter(J->seed, J->pass, (uint64_t)py * J->w + px);
@@ -679,6 +692,7 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
                 if (!(s >= J->lo[v] && s <= J->hi[v])) keep = 0;
             }
             if (!keep) continue;
+            if (depth && kept == 0) *depth = t;
             kept++;
             /* Colour: FP64 value at the FP64 sample position. */
             double tk = q.t0 + ((double)k + (double)jit) * (double)J->dt;
@@ -705,6 +719,7 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
     out[2] = C[2] + (1.0 - A) * J->bg[2];
     out[3] = A + (1.0 - A) * J->bg[3];
     if (cnt) { cnt[0] = marched; cnt[1] = kept; }
+    if (depth && kept == 0) *depth = INFINITY;
 }
 
 static void *render_worker(void *arg) {
@@ -720,7 +735,8 @@ static void *render_worker(void *arg) {
         for (int64_t i = s; i < e; i++) {
             int64_t pix = J->pixels ? J->pixels[i] : i;
             int px = (int)(pix % J->w), py = (int)(pix / J->w);
-            render_pixel(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL);
+            render_pixel(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL,
+                         J->depth ? J->depth + i : NULL);
         }
     }
     return NULL;
@@ -777,7 +793,7 @@ int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_o
                        const float *tf, int color_var, float tf_lo, float tf_hi,
                        const double *bg, int ert, const int64_t *pixels, int64_t npix,
                        double *out, uint32_t *counts, int nthreads, uint32_t seed, uint32_t pass,
-                       const float *plo, const float *phi, uint32_t pmask, int tf_skip) {
+                       const float *plo, const float *phi, uint32_t pmask, int tf_skip, float *depth) {
     if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
     render_job J;
     J.seed = seed; J.pass = pass;
@@ -794,7 +810,7 @@ int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_o
     J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
     J.tf_lo = tf_lo; J.tf_hi = tf_hi; J.bg = bg; J.ert = ert;
     J.pixels = pixels; J.npix = pixels ? npix : (int64_t)w * h;
-    J.out = out; J.counts = counts; J.next = 0;
+    J.out = out; J.counts = counts; J.depth = depth; J.next = 0;
     pthread_mutex_init(&J.lock, NULL);
     if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
     if (nthreads < 1) nthreads = 1;
@@ -815,7 +831,57 @@ int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
                   double *out, uint32_t *counts, int nthreads) {
     return oracle_render_pass(vol, n, nvars, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf, color_var,
                               tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u,
-                              NULL, NULL, 0u, 0);
+                              NULL, NULL, 0u, 0, NULL);
 }
 
 int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }
+
+/* ------------------------------------------------------------------ */
+/* Image warping (Section 2.2: frames the renderer has not finished are  */
+/* interpolated by warping the last image). Source pixel s = y*w + x    */
+/* with a finite depth D becomes the world point P = eye + D * d, d its  */
+/* ray direction (FP32 as in the march, P by fmaf per component). P is   */
+/* projected into the new camera (basis F', R', U'): v = P - eye',       */
+/* z = v.F', X = v.R', Y = v.U' (FP32 fma dot products); points with     */
+/* z <= 0 are dropped; qx = X / (z * (tan' * aspect)), qy = Y / (z *     */
+/* tan'); target column floor((qx + 1) * (w/2)), row floor((1 - qy) *    */
+/* (h/2)), dropped outside the image. Each target pixel takes the        */
+/* colour of the source of smallest z, ties to the smallest source       */
+/* index; pixels no source reaches take the background. out_src gets    */
+/* the chosen source index or -1.                                         */
+/* ------------------------------------------------------------------ */
+void oracle_warp(const float *src_rgba, const float *src_depth, const float *cam_from, const float *cam_to,
+                 int w, int h, const float *bg, float *out_rgba, int32_t *out_src) {
+    size_t npix = (size_t)w * h;
+    float *best = (float *)malloc(sizeof(float) * npix);
+    for (size_t i = 0; i < npix; i++) { best[i] = INFINITY; out_src[i] = -1; }
+    float F[3], R[3], U[3];
+    camera_basis32(cam_to, F, R, U);
+    float aspect = (float)w / (float)h;
+    float sxs = cam_to[9] * aspect, th = cam_to[9];
+    float hw = (float)w * 0.5f, hh = (float)h * 0.5f;
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            size_t s = (size_t)y * w + x;
+            float D = src_depth[s];
+            if (!(D < INFINITY)) continue;                 /* no depth (also NaN) */
+            float d[3], v[3];
+            camera_ray32(cam_from, w, h, x, y, d);
+            for (int a = 0; a < 3; a++) v[a] = fmaf(D, d[a], cam_from[a]) - cam_to[a];
+            float z = dot_f32(v, F);
+            if (!(z > 0.0f)) continue;
+            float X = dot_f32(v, R), Y = dot_f32(v, U);
+            float qx = X / (z * sxs), qy = Y / (z * th);
+            float fi = floorf((qx + 1.0f) * hw), fj = floorf((1.0f - qy) * hh);
+            if (!(fi >= 0.0f && fi < (float)w && fj >= 0.0f && fj < (float)h)) continue;
+            size_t t = (size_t)fj * w + (size_t)fi;
+            if (z < best[t] || (z == best[t] && (int32_t)s < out_src[t])) {
+                best[t] = z;
+                out_src[t] = (int32_t)s;
+            }
+        }
+    for (size_t t = 0; t < npix; t++)
+        for (int c = 0; c < 4; c++)
+            out_rgba[4 * t + c] = out_src[t] >= 0 ? src_rgba[4 * (size_t)out_src[t] + c] : bg[c];
+    free(best);
+}

@@ -303,6 +303,7 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.variant = variant;
     a.out = reinterpret_cast<float4*>(out_rgba_dev);
     a.counts = o.counts_dev;
+    a.depth = o.depth_dev;
     a.stats = stats_dev;
     *out = a;
     return RAYPC_OK;

@@ -193,6 +193,7 @@ struct RenderArgs {
     const uint16_t* cls;          // optional cell classes under this brush (kCellFail / need bits), n^3
     float4* out;
     uint32_t* counts;             // optional [h][w][2]
+    float* depth;                 // optional [h][w]: t of the first kept sample, +inf if none
     unsigned long long* stats;    // optional kNStats counters
 };
 

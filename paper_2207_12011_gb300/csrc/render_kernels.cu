@@ -304,6 +304,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 if (!pass) { ++k; continue; }
                 if (!have_c)
                     vc = interp_var<DT>(plane_ptr(A.lv.pairs, DT, A.color_var, plane), base, sy_, sz_, fx, fy, fz);
+                if (A.depth && kept == 0u) A.depth[(size_t)py * A.w + px] = t;   // first kept sample
                 ++kept;
                 // transfer function (continuous; no rounding contract needed)
                 float sp = (vc - A.tf_lo) * A.tf_scale;
@@ -351,6 +352,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             A.counts[2 * pix] = marched;
             A.counts[2 * pix + 1] = kept;
         }
+        if (A.depth && kept == 0u) A.depth[pix] = __int_as_float(0x7f800000);   // no kept sample: +inf
     }
     if (A.stats) {
         unsigned vals[6] = {marched, evald, kept, skipped, hit, ert_hit};

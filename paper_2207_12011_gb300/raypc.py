@@ -54,7 +54,7 @@ VARIANTS = {1: "8x4", 2: "16x2", 3: "4x8"}
 class RenderOpts(ctypes.Structure):
     _fields_ = [("step", ctypes.c_float), ("ert", ctypes.c_int), ("skip", ctypes.c_int),
                 ("variant", ctypes.c_int), ("bg", ctypes.c_float * 4), ("counts_dev", ctypes.c_void_p),
-                ("tf_skip", ctypes.c_int)]
+                ("tf_skip", ctypes.c_int), ("depth_dev", ctypes.c_void_p)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -481,7 +481,7 @@ def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=Non
 
 
 def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, variant=AUTO,
-          tf_skip=False) -> RenderOpts:
+          tf_skip=False, depth=None) -> RenderOpts:
     o = RenderOpts()
     o.step = float(step)
     o.ert = int(bool(ert))
@@ -491,6 +491,7 @@ def _opts(step=0.0, ert=True, skip=None, bg=(0.0, 0.0, 0.0, 0.0), counts=None, v
         o.bg[i] = float(bg[i])
     o.counts_dev = counts.data_ptr() if isinstance(counts, torch.Tensor) else None
     o.tf_skip = int(bool(tf_skip))
+    o.depth_dev = depth.data_ptr() if isinstance(depth, torch.Tensor) else None
     return o
 
 

@@ -1116,3 +1116,118 @@ def test_tf_visibility_of_constant_sub_bricks():
                 j1 = min(int(np.floor(np.float32(hi) * np.float32(255.0))), 254) + 1
                 want = bool(sig[0] or sig[j0:j1 + 1].any())
                 assert bool(vis[z, y, x]) == want, (z, y, x)
+
+
+# ----------------------------------------------------------------------------
+# depth of the first kept sample and image warping
+# ----------------------------------------------------------------------------
+def test_depth_is_the_first_lattice_point_inside_the_shell():
+    n = 32
+    vol = const_volume(n)
+    tf = tf_const((1, 1, 1), 2.0)
+    cam = synth.orbit_camera(25, 15, 3.0)
+    w = h = 40
+    dt = 1.0 / n
+    _, cnt, depth = oracle.render(vol, R_IN, R_OUT, cam.as_array(), w, h, dt, *ALL_IN, 0, tf.rgbs, 0, 0.0, 1.0,
+                                  ert=False, return_depth=True)
+    eye, d = pixel_rays64(cam, w, h)
+    b = np.sum(eye[None, None, :] * d, axis=-1)
+    disc = R_OUT ** 2 - (np.sum(eye ** 2) - b * b)
+    t_entry = -b - np.sqrt(np.clip(disc, 0, None))
+    _, bimp = shell_chord(eye, d)
+    hit = cnt[..., 1] > 0
+    assert np.all(np.isinf(depth[~hit]))
+    ok = hit & (bimp < 0.95)
+    assert np.max(np.abs(depth[ok] - (t_entry[ok] + 0.5 * dt))) < 1e-5
+    assert ok.sum() > 500
+
+
+def _plane_depth(cam, w, h, plane_dist):
+    """Depth along each pixel ray of the plane at distance plane_dist in front of the camera."""
+    eye, d = pixel_rays64(cam, w, h)
+    F = np.array(cam.target, np.float64) - eye
+    F /= np.linalg.norm(F)
+    return (plane_dist / (d @ F)).astype(np.float32)
+
+
+def test_identity_warp_reproduces_the_image():
+    rng = np.random.default_rng(4)
+    cam = synth.orbit_camera(40, -10, 3.0)
+    w, h = 48, 36
+    img = rng.random((h, w, 4)).astype(np.float32)
+    depth = rng.uniform(1.5, 4.0, (h, w)).astype(np.float32)
+    depth[rng.random((h, w)) < 0.2] = np.inf
+    bg = np.float32([0.1, 0.2, 0.3, 1.0])
+    out, src = oracle.warp(img, depth, cam.as_array(), cam.as_array(), bg)
+    fin = np.isfinite(depth)
+    assert np.array_equal(src[fin], np.flatnonzero(fin.reshape(-1)))
+    assert np.array_equal(out[fin], img[fin])
+    assert np.all(src[~fin] == -1) and np.all(out[~fin] == bg)
+
+
+def test_sideways_camera_shifts_a_plane_by_whole_pixels():
+    """A fronto-parallel plane at distance 3 seen by a camera moved sideways by 3 s / w
+    (tan_half = 0.5, square image) moves by exactly s pixels."""
+    w = h = 64
+    s = 4
+    cam = synth.Camera((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    delta = 3.0 * s / w
+    moved = synth.Camera((delta, 0.0, 3.0), (delta, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    rng = np.random.default_rng(5)
+    img = rng.random((h, w, 4)).astype(np.float32)
+    depth = _plane_depth(cam, w, h, 3.0)
+    out, src = oracle.warp(img, depth, cam.as_array(), moved.as_array())
+    assert np.array_equal(out[:, : w - s], img[:, s:])
+    yy, xx = np.mgrid[0:h, s:w]
+    assert np.array_equal(src[:, : w - s], yy * w + xx)
+    assert np.all(src[:, w - s:] == -1) and np.all(out[:, w - s:] == 0)
+
+
+def test_warp_keeps_the_nearest_source():
+    """Random depths and a rotated, advanced camera: where the projections are clear of
+    pixel edges and depths, each target shows the source of smallest z (FP64 brute force)."""
+    rng = np.random.default_rng(6)
+    w, h = 40, 30
+    cam = synth.orbit_camera(30, 10, 3.0)
+    new = synth.orbit_camera(36, 14, 2.6)
+    img = rng.random((h, w, 4)).astype(np.float32)
+    depth = rng.uniform(1.8, 3.5, (h, w)).astype(np.float32)
+    out, src = oracle.warp(img, depth, cam.as_array(), new.as_array())
+    eye, d = pixel_rays64(cam, w, h)
+    P = eye[None, None, :] + depth[..., None].astype(np.float64) * d
+    e2 = np.array(new.eye, np.float64)
+    F = np.array(new.target, np.float64) - e2
+    F /= np.linalg.norm(F)
+    R = np.cross(F, np.array(new.up, np.float64))
+    R /= np.linalg.norm(R)
+    U = np.cross(R, F)
+    v = P - e2
+    z, X, Y = v @ F, v @ R, v @ U
+    th = float(new.tan_half_vfov)
+    fx = (X / (z * th * (w / h)) + 1) * (w / 2)
+    fy = (1 - Y / (z * th)) * (h / 2)
+    clear = (np.abs(fx - np.round(fx)) > 1e-3) & (np.abs(fy - np.round(fy)) > 1e-3) & (z > 0)
+    ti, tj = np.floor(fx).astype(int), np.floor(fy).astype(int)
+    inside = clear & (ti >= 0) & (ti < w) & (tj >= 0) & (tj < h)
+    # targets that a source near a pixel edge might reach are left out
+    ambiguous = set()
+    for sidx in np.flatnonzero(~clear.reshape(-1) & (z.reshape(-1) > 0)):
+        for ex in (-1e-3, 1e-3):
+            for ey in (-1e-3, 1e-3):
+                a, b = int(np.floor(fx.reshape(-1)[sidx] + ex)), int(np.floor(fy.reshape(-1)[sidx] + ey))
+                if 0 <= a < w and 0 <= b < h:
+                    ambiguous.add(b * w + a)
+    cands = {}
+    for sidx in np.flatnonzero(inside.reshape(-1)):
+        t = tj.reshape(-1)[sidx] * w + ti.reshape(-1)[sidx]
+        cands.setdefault(t, []).append((z.reshape(-1)[sidx], sidx))
+    checked = collided = 0
+    for t, lst in cands.items():
+        lst.sort()
+        if t in ambiguous or (len(lst) > 1 and lst[1][0] - lst[0][0] < 1e-4):
+            continue
+        assert src.reshape(-1)[t] == lst[0][1]
+        assert np.array_equal(out.reshape(-1, 4)[t], img.reshape(-1, 4)[lst[0][1]])
+        checked += 1
+        collided += len(lst) > 1
+    assert checked > 300 and collided > 20
