@@ -335,6 +335,29 @@ def run_ours(args):
                        "lowest 30 % of the colour range"}
     del timg
 
+    # ---- image warping of the frame to a slightly moved camera ----
+    wimg, _, wdepth = vol.render(wl.cam, c["w"], c["h"], depth=True)
+    cam2 = synth.orbit_camera(synth.DEFAULT_CAMERA["az_deg"] + 2.0, synth.DEFAULT_CAMERA["el_deg"] + 1.0,
+                              synth.DEFAULT_CAMERA["dist"] * 0.98)
+    wout = torch.empty_like(wimg)
+    for _ in range(3):
+        _, widx = rp.warp_image(ctx, wl.cam, cam2, wimg, wdepth, out=wout, with_src=True)
+    ww = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ww[0].record()
+    for _ in range(10):
+        rp.warp_image(ctx, wl.cam, cam2, wimg, wdepth, out=wout)
+    ww[1].record()
+    torch.cuda.synchronize()
+    fin = torch.isfinite(wdepth)
+    warp = {"ms": round(ww[0].elapsed_time(ww[1]) / 10, 4),
+            "render_ms": round(render_ms, 4),
+            "pixels_with_depth": int(fin.sum()),
+            "warped_pixels_filled": int((widx >= 0).sum()),
+            "what": "1024^2 frame with first-kept-sample depth warped to the camera moved by 2 deg azimuth, "
+                    "1 deg elevation and 2 % closer"}
+    del wimg, wdepth, wout, widx
+
     # ---- position axes (brush and PC axis) and the PC line subsample ----
     pos = (np.float32([-0.5, -np.inf, -np.inf, 0.6]), np.float32([0.5, np.inf, np.inf, 0.95]), 0b1001)
     porder = [rp.AXIS_POS(rp.POS_R)] + list(c["order"][:4])
@@ -478,6 +501,7 @@ def run_ours(args):
         "progressive": progressive,
         "position_axes": position,
         "tf_skip": tf_skip,
+        "warp": warp,
         "e2e": {"value": round(e2e_all / (e2e_max_ms / 1e3), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3),

@@ -138,7 +138,10 @@ typedef struct raypc_render_opts {
                             t (world distance from the eye) of the first kept
                             sample, t0 + (k + j) * step in FP32 exactly as the
                             march computes it; +inf where no sample is kept.
-                            The depth that raypc_warp_image reprojects.         */
+                            The depth that raypc_warp_image reprojects.
+                            Single-frame renders (raypc_render,
+                            raypc_render_progressive; always 8x4 tiles);
+                            raypc_render_batch rejects it.                      */
 } raypc_render_opts;
 
 /* ---------------------------------------------------------------------- */
@@ -297,6 +300,27 @@ raypc_status raypc_render_progressive(raypc_ctx *ctx, int vol, int lod, const ra
                                       uint32_t seed, uint32_t pass, float *accum_rgba_dev,
                                       float *out_rgba_dev, unsigned long long *stats_dev,
                                       void *stream);
+
+/* Image warping (Section 2.2: while a frame is being rendered, the last image
+ * is warped to the current view to fill the missing frames). Forward
+ * reprojection of a w x h image rendered with camera `from` (its premultiplied
+ * RGBA src_rgba_dev [h][w][4] float32 and depth src_depth_dev [h][w] float32,
+ * e.g. the render's depth_dev output) to camera `to`, same size. Source pixel
+ * s = y*w + x with a finite depth D becomes P = eye + D * d (d its ray
+ * direction as in raypc_render); with the new camera's basis F', R', U'
+ * (raypc_camera meaning) and v = P - eye': z = v.F', X = v.R', Y = v.U' as
+ * FP32 fma dot products; z <= 0 drops the point; qx = X / (z * tan' * w/h),
+ * qy = Y / (z * tan'); it lands in column floor((qx + 1) * w/2) and row
+ * floor((1 - qy) * h/2) if inside the image. Every target pixel takes the
+ * colour of the landed source of smallest z (ties: smallest s); target pixels
+ * that no source reaches take bg (host array of 4 floats, NULL = 0).
+ * out_src_dev (optional, [h][w] int32) receives the chosen s or -1. All
+ * decisions use correctly rounded FP32 operations in one fixed order.
+ * Buffers are caller-owned device memory; out_rgba_dev must not alias
+ * src_rgba_dev; RGBA buffers 16-byte aligned. */
+raypc_status raypc_warp_image(raypc_ctx *ctx, const raypc_camera *from, const raypc_camera *to, int w, int h,
+                              const float *src_rgba_dev, const float *src_depth_dev, const float *bg,
+                              float *out_rgba_dev, int32_t *out_src_dev, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched rendering (many views and brushes in one launch)                */

@@ -868,6 +868,58 @@ raypc_status raypc_filter_points(raypc_ctx* ctx, int vol, int lod, const float* 
     return RAYPC_OK;
 }
 
+static raypc_status check_camera(const raypc_camera* cam) {
+    if (!cam) return fail(RAYPC_ERR_INVALID_ARG, "NULL camera");
+    for (int i = 0; i < 3; ++i)
+        if (!isfinite(cam->eye[i]) || !isfinite(cam->target[i]) || !isfinite(cam->up[i]))
+            return fail(RAYPC_ERR_INVALID_ARG, "non-finite camera");
+    if (!(cam->tan_half_vfov > 0.f) || !isfinite(cam->tan_half_vfov)) return fail(RAYPC_ERR_INVALID_ARG, "tan_half_vfov must be > 0");
+    float fx = cam->target[0] - cam->eye[0], fy = cam->target[1] - cam->eye[1], fz = cam->target[2] - cam->eye[2];
+    if (fx == 0.f && fy == 0.f && fz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "eye == target");
+    float cx = fy * cam->up[2] - fz * cam->up[1], cy = fz * cam->up[0] - fx * cam->up[2], cz = fx * cam->up[1] - fy * cam->up[0];
+    if (cx == 0.f && cy == 0.f && cz == 0.f) return fail(RAYPC_ERR_INVALID_ARG, "up is parallel to the view direction");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_warp_image(raypc_ctx* ctx, const raypc_camera* from, const raypc_camera* to, int w, int h,
+                              const float* src_rgba_dev, const float* src_depth_dev, const float* bg,
+                              float* out_rgba_dev, int32_t* out_src_dev, void* stream) {
+    if (!ctx || !src_rgba_dev || !src_depth_dev || !out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    raypc_status st;
+    if ((st = check_camera(from)) || (st = check_camera(to))) return st;
+    if (w < 1 || h < 1 || w > 32768 || h > 32768) return fail(RAYPC_ERR_INVALID_ARG, "image size %d x %d out of range", w, h);
+    if ((((uintptr_t)src_rgba_dev) | ((uintptr_t)out_rgba_dev)) & 15u)
+        return fail(RAYPC_ERR_INVALID_ARG, "src_rgba_dev and out_rgba_dev must be 16-byte aligned");
+    if (((uintptr_t)src_depth_dev) & 3u || ((uintptr_t)out_src_dev) & 3u) return fail(RAYPC_ERR_INVALID_ARG, "misaligned depth or source index buffer");
+    if (src_rgba_dev == out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "out_rgba_dev must not alias src_rgba_dev");
+    WarpArgs a{};
+    for (int i = 0; i < 3; ++i) {
+        a.from_eye[i] = from->eye[i]; a.from_target[i] = from->target[i]; a.from_up[i] = from->up[i];
+        a.to_eye[i] = to->eye[i]; a.to_target[i] = to->target[i]; a.to_up[i] = to->up[i];
+    }
+    a.from_tan_half = from->tan_half_vfov;
+    a.to_tan_half = to->tan_half_vfov;
+    a.w = w;
+    a.h = h;
+    a.src_rgba = reinterpret_cast<const float4*>(src_rgba_dev);
+    a.src_depth = src_depth_dev;
+    for (int c = 0; c < 4; ++c) {
+        a.bg[c] = bg ? bg[c] : 0.0f;
+        if (!isfinite(a.bg[c])) return fail(RAYPC_ERR_INVALID_ARG, "non-finite background");
+    }
+    a.out = reinterpret_cast<float4*>(out_rgba_dev);
+    a.out_src = out_src_dev;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // per-pixel selection keys: a device buffer owned by this call (freed in stream order)
+    CK(cudaMallocAsync((void**)&a.keys, sizeof(unsigned long long) * (size_t)w * h, s), "warp keys");
+    cudaError_t e = launch_warp(a, s);
+    cudaFreeAsync(a.keys, s);
+    if (e != cudaSuccess) return cuda_fail(e, "warp kernels");
+    return RAYPC_OK;
+}
+
 raypc_status raypc_volume_info(raypc_ctx* ctx, int vol, int lod, int* out_n, int* out_nvars,
                                int* out_dtype, int* out_bricks_per_axis) {
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");

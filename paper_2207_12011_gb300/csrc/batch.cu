@@ -185,7 +185,8 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = get_level(V, q.lod, &L))) return st;
         if (dtype < 0) dtype = V->dtype;
         if (V->dtype != dtype) return fail(RAYPC_ERR_INVALID_ARG, "view %d: all views of a batch need one storage dtype", i);
-        if (q.opts.tf_skip) return fail(RAYPC_ERR_UNSUPPORTED, "view %d: tf_skip is for single-frame renders", i);
+        if (q.opts.tf_skip || q.opts.depth_dev)
+            return fail(RAYPC_ERR_UNSUPPORTED, "view %d: tf_skip and depth_dev are for single-frame renders", i);
         BatchView bv{};
         if ((st = make_render_args(V, L, &q.cam, q.w, q.h, &q.opts, q.out_rgba_dev, q.stats_dev, &bv.a))) return st;
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;

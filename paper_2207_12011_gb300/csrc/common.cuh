@@ -500,6 +500,20 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
 int render_batch_blocks_per_sm(int dtype, int variant);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
+// Image warping (render_kernels.cu).
+struct WarpArgs {
+    float from_eye[3], from_target[3], from_up[3], from_tan_half;
+    float to_eye[3], to_target[3], to_up[3], to_tan_half;
+    int w, h;                     // both images (w * h < 2^32 pixels)
+    const float4* src_rgba;       // [h][w]
+    const float* src_depth;       // [h][w], +inf: no depth
+    float bg[4];
+    unsigned long long* keys;     // [h][w] scratch
+    float4* out;                  // [h][w]
+    int* out_src;                 // optional [h][w]: chosen source pixel or -1
+};
+cudaError_t launch_warp(const WarpArgs& a, cudaStream_t stream);
+
 // TF-aware skipping (volume_kernels.cu): activity bits of the 8^3 bricks and
 // 4^3 sub-bricks of a level ANDed with their TF visibility.
 struct TfVisArgs {

@@ -48,6 +48,37 @@ __device__ __forceinline__ void cross_rn(float ax, float ay, float az, float bx,
     cz = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
 }
 
+// Pinhole camera basis (exactly rounded, fixed order): F = normalize(target - eye),
+// R = normalize(cross(F, up)), U = cross(R, F).
+__device__ __forceinline__ void camera_basis_rn(const float* eye, const float* target, const float* up,
+                                                float& Fx, float& Fy, float& Fz, float& Rx, float& Ry, float& Rz,
+                                                float& Ux, float& Uy, float& Uz) {
+    Fx = __fsub_rn(target[0], eye[0]);
+    Fy = __fsub_rn(target[1], eye[1]);
+    Fz = __fsub_rn(target[2], eye[2]);
+    normalize_rn(Fx, Fy, Fz);
+    cross_rn(Fx, Fy, Fz, up[0], up[1], up[2], Rx, Ry, Rz);
+    normalize_rn(Rx, Ry, Rz);
+    cross_rn(Rx, Ry, Rz, Fx, Fy, Fz, Ux, Uy, Uz);
+}
+
+// Unit direction of the ray through pixel (px, py) of a w x h image.
+__device__ __forceinline__ void camera_ray_rn(const float* eye, const float* target, const float* up, float tan_half,
+                                              int w, int h, int px, int py, float& dx, float& dy, float& dz) {
+    float Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz;
+    camera_basis_rn(eye, target, up, Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz);
+    const float aspect = __fdiv_rn((float)w, (float)h);
+    const float sxs = __fmul_rn(tan_half, aspect);
+    const float qx = __fdiv_rn((float)(2 * px + 1), (float)w);
+    const float qy = __fdiv_rn((float)(2 * py + 1), (float)h);
+    const float sx = __fmul_rn(__fsub_rn(qx, 1.0f), sxs);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, qy), tan_half);
+    dx = __fmaf_rn(sy, Ux, __fmaf_rn(sx, Rx, Fx));
+    dy = __fmaf_rn(sy, Uy, __fmaf_rn(sx, Ry, Fy));
+    dz = __fmaf_rn(sy, Uz, __fmaf_rn(sx, Rz, Fz));
+    normalize_rn(dx, dy, dz);
+}
+
 __device__ __forceinline__ bool bit_of(const uint32_t* bits, uint32_t id) {
     return (__ldg(bits + (id >> 5)) >> (id & 31)) & 1u;
 }
@@ -103,8 +134,10 @@ __device__ __forceinline__ void load_view_shared(const RenderArgs& A, ViewShared
 
 // March the ray of this thread's pixel in block tile (tile_x, tile_y) of view A
 // and write its pixel, optional counts and (warp-aggregated) statistics. All
-// 32 lanes of every warp must call it.
-template <int DT, int VAR>
+// 32 lanes of every warp must call it. DEPTH: the depth output may be requested
+// (A.depth; single-frame renders only); without it the march keeps no trace of
+// the first kept sample.
+template <int DT, int VAR, bool DEPTH>
 __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShared& S, int tile_x, int tile_y) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int WTW = warp_tile_w(VAR), WTH = 32 / WTW;
@@ -114,9 +147,11 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
 
     unsigned marched = 0, kept = 0, evald = 0, skipped = 0, hit = 0, ert_hit = 0;
     float Cr = 0.f, Cg = 0.f, Cb = 0.f, Aa = 0.f;
+    float depth = __int_as_float(0x7f800000);       // t of the first kept sample; +inf if none
 
     if (inside) {
-        // Camera basis and pixel direction (exactly rounded, fixed order).
+        // Camera basis and pixel direction (exactly rounded, fixed order; the same
+        // arithmetic as camera_ray_rn, written out here for the register allocation).
         float Fx = __fsub_rn(A.target[0], A.eye[0]);
         float Fy = __fsub_rn(A.target[1], A.eye[1]);
         float Fz = __fsub_rn(A.target[2], A.eye[2]);
@@ -304,7 +339,8 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 if (!pass) { ++k; continue; }
                 if (!have_c)
                     vc = interp_var<DT>(plane_ptr(A.lv.pairs, DT, A.color_var, plane), base, sy_, sz_, fx, fy, fz);
-                if (A.depth && kept == 0u) A.depth[(size_t)py * A.w + px] = t;   // first kept sample
+                // index of the first kept sample, parked in the depth output until the end
+                if (DEPTH && kept == 0u && A.depth) A.depth[(size_t)py * A.w + px] = __int_as_float(k);
                 ++kept;
                 // transfer function (continuous; no rounding contract needed)
                 float sp = (vc - A.tf_lo) * A.tf_scale;
@@ -327,6 +363,8 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             }
             // every lattice sample up to termination
             marched = ert_hit ? (unsigned)k : (unsigned)reinterpret_cast<volatile int*>(s_lat)[threadIdx.x];
+            if (DEPTH && kept && A.depth)                         // t of the first kept sample
+                depth = __fmaf_rn(__fadd_rn((float)__float_as_int(A.depth[(size_t)py * A.w + px]), jo), dt, t0);
         }
         const float tr = 1.0f - Aa;
         float4 o;
@@ -352,7 +390,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             A.counts[2 * pix] = marched;
             A.counts[2 * pix + 1] = kept;
         }
-        if (A.depth && kept == 0u) A.depth[pix] = __int_as_float(0x7f800000);   // no kept sample: +inf
+        if (DEPTH && A.depth) A.depth[pix] = depth;
     }
     if (A.stats) {
         unsigned vals[6] = {marched, evald, kept, skipped, hit, ert_hit};
@@ -364,12 +402,12 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
     }
 }
 
-template <int DT, int VAR>
+template <int DT, int VAR, bool DEPTH>
 __global__ void __launch_bounds__(kThreads) k_render(RenderArgs A) {
     __shared__ ViewShared S;
     load_view_shared(A, S);
     __syncthreads();
-    march_pixel<DT, VAR>(A, S, blockIdx.x, blockIdx.y);
+    march_pixel<DT, VAR, DEPTH>(A, S, blockIdx.x, blockIdx.y);
 }
 
 // Per-view classification of a batch: one thread per (view, brick); a warp's
@@ -484,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader*
             cur_view = vi;
             __syncthreads();
         }
-        march_pixel<DT, VAR>(s_args, S, s_tx, s_ty);
+        march_pixel<DT, VAR, false>(s_args, S, s_tx, s_ty);
         __syncthreads();   // the tile's pixels and statistics are issued; s_* are rewritten next
         if (threadIdx.x == 0) {
             const BatchView& V = views[vi];
@@ -503,20 +541,21 @@ __global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader*
     }
 }
 
-template <int DT, int VAR>
+template <int DT, int VAR, bool DEPTH>
 cudaError_t launch_t(const RenderArgs& a, cudaStream_t stream) {
     dim3 grid((a.w + block_tile_w(VAR) - 1) / block_tile_w(VAR), (a.h + block_tile_h(VAR) - 1) / block_tile_h(VAR));
-    k_render<DT, VAR><<<grid, kThreads, 0, stream>>>(a);
+    k_render<DT, VAR, DEPTH><<<grid, kThreads, 0, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <int DT>
 cudaError_t launch_dt(const RenderArgs& a, cudaStream_t stream) {
+    if (a.depth) return launch_t<DT, 1, true>(a, stream);   // depth renders use the 8x4 tiles
     switch (a.variant) {
-        case 2: return launch_t<DT, 2>(a, stream);
-        case 3: return launch_t<DT, 3>(a, stream);
-        default: return launch_t<DT, 1>(a, stream);
+        case 2: return launch_t<DT, 2, false>(a, stream);
+        case 3: return launch_t<DT, 3, false>(a, stream);
+        default: return launch_t<DT, 1, false>(a, stream);
     }
 }
 
@@ -562,6 +601,71 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
         else if (variant == 3) batch_kernels<kF32, 3>(hdr, views, tile_counter, blocks, stream);
         else batch_kernels<kF32, 1>(hdr, views, tile_counter, blocks, stream);
     }
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Image warping (Section 2.2: frames the renderer has not finished are
+// interpolated by warping the last image). Source pixel s with a finite depth
+// D becomes P = eye + D d (d its ray direction as in the march); P is projected
+// into the new camera with exactly rounded FP32 operations in a fixed order,
+// and every target pixel keeps the source of smallest camera-space z, ties to
+// the smallest s: one 64-bit atomicMin per source on the key (z bits << 32) | s
+// (z > 0, so the float bits order like the values).
+__global__ void __launch_bounds__(256) k_warp_clear(unsigned long long* keys, long long npix) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
+        keys[i] = ~0ull;
+}
+
+__global__ void __launch_bounds__(256) k_warp_scatter(WarpArgs A) {
+    const long long npix = (long long)A.w * A.h;
+    float Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz;
+    camera_basis_rn(A.to_eye, A.to_target, A.to_up, Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz);
+    const float aspect = __fdiv_rn((float)A.w, (float)A.h);
+    const float sxs = __fmul_rn(A.to_tan_half, aspect), th = A.to_tan_half;
+    const float hw = __fmul_rn((float)A.w, 0.5f), hh = __fmul_rn((float)A.h, 0.5f);
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < npix; s += (long long)gridDim.x * blockDim.x) {
+        const float D = A.src_depth[s];
+        if (!(D < __int_as_float(0x7f800000))) continue;    // no depth (also NaN)
+        const int x = (int)(s % A.w), y = (int)(s / A.w);
+        float dx, dy, dz;
+        camera_ray_rn(A.from_eye, A.from_target, A.from_up, A.from_tan_half, A.w, A.h, x, y, dx, dy, dz);
+        const float vx = __fsub_rn(__fmaf_rn(D, dx, A.from_eye[0]), A.to_eye[0]);
+        const float vy = __fsub_rn(__fmaf_rn(D, dy, A.from_eye[1]), A.to_eye[1]);
+        const float vz = __fsub_rn(__fmaf_rn(D, dz, A.from_eye[2]), A.to_eye[2]);
+        const float z = dot3_rn(vx, vy, vz, Fx, Fy, Fz);
+        if (!(z > 0.0f)) continue;
+        const float X = dot3_rn(vx, vy, vz, Rx, Ry, Rz), Y = dot3_rn(vx, vy, vz, Ux, Uy, Uz);
+        const float qx = __fdiv_rn(X, __fmul_rn(z, sxs)), qy = __fdiv_rn(Y, __fmul_rn(z, th));
+        const float fi = floorf(__fmul_rn(__fadd_rn(qx, 1.0f), hw)), fj = floorf(__fmul_rn(__fsub_rn(1.0f, qy), hh));
+        if (!(fi >= 0.0f && fi < (float)A.w && fj >= 0.0f && fj < (float)A.h)) continue;
+        const long long t = (long long)fj * A.w + (long long)fi;
+        atomicMin(A.keys + t, ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)s);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_warp_gather(WarpArgs A) {
+    const long long npix = (long long)A.w * A.h;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < npix; t += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = A.keys[t];
+        const bool hit = key != ~0ull;
+        const long long s = hit ? (long long)(key & 0xffffffffull) : -1;
+        A.out[t] = hit ? A.src_rgba[s] : make_float4(A.bg[0], A.bg[1], A.bg[2], A.bg[3]);
+        if (A.out_src) A.out_src[t] = (int)s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_warp(const WarpArgs& a, cudaStream_t stream) {
+    const long long npix = (long long)a.w * a.h;
+    const long long want = (npix + 255) / 256;
+    const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
+    k_warp_clear<<<blocks, 256, 0, stream>>>(a.keys, npix);
+    k_warp_scatter<<<blocks, 256, 0, stream>>>(a);
+    k_warp_gather<<<blocks, 256, 0, stream>>>(a);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,7 @@ _SIGS = {
     "raypc_set_position_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_pc_subsample": [_P, _I, _I, _U32, ctypes.c_longlong, _P, _I, _P, _P, _P, _P, _P],
     "raypc_filter_points": [_P, _I, _I, _P, ctypes.c_longlong, _P, _P],
+    "raypc_warp_image": [_P, ctypes.POINTER(Camera), ctypes.POINTER(Camera), _I, _I, _P, _P, _P, _P, _P, _P],
     "raypc_render_progressive": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts),
                                  _U32, _U32, _P, _P, _P, _P],
     "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
@@ -347,8 +348,9 @@ class Volume:
     def render(self, cam, w: int, h: int, lod: int = 0, step: float = 0.0, ert: bool = True,
                skip: bool | None = None, bg=(0.0, 0.0, 0.0, 0.0), out: torch.Tensor | None = None,
                counts: bool | torch.Tensor = False, stats: torch.Tensor | None = None,
-               variant: int = AUTO, tf_skip: bool = False, stream=None):
-        """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None).
+               variant: int = AUTO, tf_skip: bool = False, depth: bool | torch.Tensor = False, stream=None):
+        """Render into an (h, w, 4) float32 device tensor; returns (image, counts or None), plus the
+        (h, w) depth of the first kept sample when depth is requested.
 
         skip: None = tuned choice (default on), True / False = brick skipping on / off;
         variant: AUTO or 1..3 (tile shape). Neither changes any pixel.
@@ -358,12 +360,16 @@ class Volume:
             out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
         if counts is True:
             counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
-        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip)
+        if depth is True:
+            depth = torch.empty((h, w), dtype=torch.float32, device=dev)
+        o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip,
+                  depth if isinstance(depth, torch.Tensor) else None)
         c = camera_from(cam)
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
         _call("raypc_render", self.ctx.handle, self.id, int(lod), ctypes.byref(c), int(w), int(h),
               ctypes.byref(o), ctypes.c_void_p(out.data_ptr()), sp, _stream(stream))
-        return out, (counts if isinstance(counts, torch.Tensor) else None)
+        res = (out, (counts if isinstance(counts, torch.Tensor) else None))
+        return res + (depth,) if isinstance(depth, torch.Tensor) else res
 
     def render_progressive(self, cam, w: int, h: int, seed: int, pass_: int, accum: torch.Tensor | None,
                            lod: int = 0, step: float = 0.0, ert: bool = True, skip: bool | None = None,
@@ -531,6 +537,24 @@ def _view_array(ctx, views):
         _fill_pos(v, q.get("pos"))
         outs.append((out, counts if isinstance(counts, torch.Tensor) else None))
     return arr, outs
+
+
+def warp_image(ctx: Context, cam_from, cam_to, src: torch.Tensor, depth: torch.Tensor, bg=(0.0, 0.0, 0.0, 0.0),
+               out: torch.Tensor | None = None, with_src: bool = False, stream=None):
+    """Forward-warp an (h, w, 4) float32 image with its (h, w) depth from cam_from to cam_to.
+    Returns the warped image, and the chosen source pixel per target pixel (int32, -1: none)
+    when with_src."""
+    h, w = int(src.shape[0]), int(src.shape[1])
+    if out is None:
+        out = torch.empty_like(src)
+    idx = torch.empty((h, w), dtype=torch.int32, device=src.device) if with_src else None
+    cf, ct = camera_from(cam_from), camera_from(cam_to)
+    b = np.ascontiguousarray(np.asarray(bg, dtype=np.float32).reshape(4))
+    _call("raypc_warp_image", ctx.handle, ctypes.byref(cf), ctypes.byref(ct), w, h,
+          ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(depth.data_ptr()), _fptr(b),
+          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(idx.data_ptr()) if idx is not None else None,
+          _stream(stream))
+    return (out, idx) if with_src else out
 
 
 def autotune(ctx: Context, views, reps: int = 3, stream=None):

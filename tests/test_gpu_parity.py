@@ -748,3 +748,56 @@ def test_tf_skip_keeps_the_image_and_matches_oracle(ctx, rp, n, store):
         b.render([dict(vol=v, cam=cam, w=8, h=8, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, tf_skip=True)])
     b.close()
     v.free()
+
+
+# ----------------------------------------------------------------------------
+# depth of the first kept sample and image warping
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,store", [(48, "f32"), (33, "f16")])
+def test_depth_and_warp_match_oracle(ctx, rp, n, store):
+    vol = synth.make_shell_volume(n, seed=23)
+    brush = synth.make_brush(vol, "c2")
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    w, h = 71, 53
+    v = load(ctx, vol, store, brush=brush, tf=tf)
+    level = stored(vol, store)
+    for ert, skip in ((False, True), (True, True), (True, False)):
+        img, _, depth = v.render(cam, w, h, ert=ert, skip=skip, depth=True)
+        torch.cuda.synchronize()
+        _, _, rdepth = oracle.render(level, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
+                                     brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=ert,
+                                     return_depth=True)
+        assert np.array_equal(depth.cpu().numpy(), rdepth), (ert, skip)     # bit for bit, +inf included
+    assert np.isfinite(rdepth).sum() > 100 and np.isinf(rdepth).sum() > 100
+    bg = (0.05, 0.1, 0.2, 1.0)
+    src, dep = img.cpu().numpy(), depth.cpu().numpy()
+    for new in (cam, synth.orbit_camera(33, 22, 2.9), synth.orbit_camera(20, 10, 3.4)):
+        out, idx = rp.warp_image(ctx, cam, new, img, depth, bg=bg, with_src=True)
+        torch.cuda.synchronize()
+        ro, ridx = oracle.warp(src, dep, cam.as_array(), new.as_array(), bg)
+        assert np.array_equal(idx.cpu().numpy(), ridx)
+        assert np.array_equal(out.cpu().numpy(), ro)
+    fin = np.isfinite(dep)
+    out, idx = rp.warp_image(ctx, cam, cam, img, depth, with_src=True)
+    assert np.array_equal(out.cpu().numpy()[fin], src[fin])                  # identity warp
+    with pytest.raises(rp.RaypcError):
+        rp.warp_image(ctx, cam, cam, img, depth, out=img)                      # aliasing
+    v.free()
+
+
+def test_batch_rejects_single_frame_options(ctx, rp):
+    vol = synth.make_shell_volume(16)
+    brush = synth.make_brush(vol, "c1")
+    tf = synth.make_tf(vol, "T_anom")
+    v = load(ctx, vol, "f32", brush=brush, tf=tf)
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    b = rp.Batch(ctx, 2)
+    view = dict(vol=v, cam=cam, w=8, h=8, lo=brush.lo, hi=brush.hi, mask=brush.active_mask)
+    arr, _ = rp._view_array(ctx, [view])
+    d = torch.empty((8, 8), device="cuda")
+    arr[0].opts.depth_dev = d.data_ptr()
+    with pytest.raises(rp.RaypcError):
+        rp._call("raypc_render_batch", b._h, arr, 1, rp._stream(None))
+    b.close()
+    v.free()
