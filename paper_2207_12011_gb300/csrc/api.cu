@@ -70,6 +70,7 @@ void free_bricks(Level& L) {
 void free_volume(raypc_ctx* ctx, Volume* V) {
     for (auto& L : V->lv) free_level(L);
     if (V->tf) cudaFree(V->tf);
+    if (V->tf_prefix) cudaFree(V->tf_prefix);
     ctx->used -= V->bytes < ctx->used ? V->bytes : ctx->used;
     delete V;
 }
@@ -304,6 +305,8 @@ raypc_status make_render_args(Volume* V, Level* L, const raypc_camera* cam, int 
     a.out = reinterpret_cast<float4*>(out_rgba_dev);
     a.counts = o.counts_dev;
     a.depth = o.depth_dev;
+    a.tf_prefix = V->tf_prefix;
+    a.tf_skip = o.tf_skip ? 1 : 0;
     a.stats = stats_dev;
     *out = a;
     return RAYPC_OK;
@@ -588,6 +591,16 @@ raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_
         if ((st = ctx->alloc((void**)&V->tf, sizeof(float4) * RAYPC_TF_ENTRIES, &dummy))) return st;
         V->bytes += dummy;
     }
+    if (!V->tf_prefix) {
+        size_t dummy = 0;
+        if ((st = ctx->alloc((void**)&V->tf_prefix, sizeof(int) * (RAYPC_TF_ENTRIES + 1), &dummy))) return st;
+        V->bytes += dummy;
+    }
+    int prefix[RAYPC_TF_ENTRIES + 1];
+    prefix[0] = 0;
+    for (int i = 0; i < RAYPC_TF_ENTRIES; ++i) prefix[i + 1] = prefix[i] + (rgbs[4 * i + 3] > 0.f ? 1 : 0);
+    CK(cudaMemcpyAsync(V->tf_prefix, prefix, sizeof(prefix), cudaMemcpyHostToDevice, (cudaStream_t)stream),
+       "transfer function prefix upload");
     // pageable host source: cudaMemcpyAsync stages it before returning
     CK(cudaMemcpyAsync(V->tf, rgbs, sizeof(float4) * RAYPC_TF_ENTRIES, cudaMemcpyHostToDevice, (cudaStream_t)stream),
        "transfer function upload");

@@ -73,11 +73,11 @@ void release(raypc_batch* b) {
     if (b->ctx) b->ctx->used -= b->charged < b->ctx->used ? b->charged : b->ctx->used;
 }
 
-raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
+raypc_status capture(raypc_batch* b, int slot, int dtype, int variant, bool depth) {
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    const int blocks = sms * render_batch_blocks_per_sm(dtype, variant);
+    const int blocks = sms * render_batch_blocks_per_sm(dtype, variant, depth);
     const unsigned cls_blocks = (unsigned)sms * 8u;
     if (b->exec[slot]) {
         cudaGraphExecDestroy(b->exec[slot]);
@@ -90,7 +90,7 @@ raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_pass, 0, sizeof(unsigned) * kMaxVars * b->max_views, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tiles, 0, sizeof(unsigned) * 2 * b->max_views, s);
     if (e == cudaSuccess)
-        e = launch_render_batch(hdr_of(b->d_table), views_of(b->d_table), b->d_counter, dtype, variant,
+        e = launch_render_batch(hdr_of(b->d_table), views_of(b->d_table), b->d_counter, depth, dtype, variant,
                                 cls_blocks, blocks, s);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &graph);
@@ -98,7 +98,7 @@ raypc_status capture(raypc_batch* b, int slot, int dtype, int variant) {
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "batch graph capture");
-    b->exec_key[slot] = dtype * 16 + variant;
+    b->exec_key[slot] = dtype * 16 + variant + (depth ? 8 : 0);
     return RAYPC_OK;
 }
 
@@ -174,6 +174,9 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     BatchHeader* H = hdr_of(b->h_table[slot]);
     BatchView* T = views_of(b->h_table[slot]);
     int dtype = -1, variant = 0;
+    // a depth output in any view selects the depth instance of the kernel (8x4 tiles)
+    bool depth = false;
+    for (int i = 0; i < nviews; ++i) depth = depth || views[i].opts.depth_dev != nullptr;
     unsigned long long cls = 0;
     long long tiles = 0;
     raypc_status st;
@@ -185,14 +188,12 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         if ((st = get_level(V, q.lod, &L))) return st;
         if (dtype < 0) dtype = V->dtype;
         if (V->dtype != dtype) return fail(RAYPC_ERR_INVALID_ARG, "view %d: all views of a batch need one storage dtype", i);
-        if (q.opts.tf_skip || q.opts.depth_dev)
-            return fail(RAYPC_ERR_UNSUPPORTED, "view %d: tf_skip and depth_dev are for single-frame renders", i);
         BatchView bv{};
         if ((st = make_render_args(V, L, &q.cam, q.w, q.h, &q.opts, q.out_rgba_dev, q.stats_dev, &bv.a))) return st;
         if ((st = brush_from_host(V, q.lo, q.hi, q.active_mask, &bv.a.brush))) return st;
         if ((st = pos_from_host(q.pos_lo, q.pos_hi, q.pos_mask, &bv.a.brush))) return st;
         finish_position_brush(bv.a);
-        if (i == 0) variant = bv.a.variant;
+        if (i == 0) variant = depth ? 1 : bv.a.variant;
         bv.a.variant = variant;
         const size_t words = L->nwords(), need = words + L->nswords() + L->nsbricks();
         if (b->bits_words[i] < need) {
@@ -244,8 +245,8 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     H->nviews = nviews;
     H->total_tiles = (int)tiles;
     H->cls_total = cls;
-    if (!b->exec[slot] || b->exec_key[slot] != dtype * 16 + variant)
-        if ((st = capture(b, slot, dtype, variant))) return st;
+    if (!b->exec[slot] || b->exec_key[slot] != dtype * 16 + variant + (depth ? 8 : 0))
+        if ((st = capture(b, slot, dtype, variant, depth))) return st;
     CK(cudaGraphLaunch(b->exec[slot], (cudaStream_t)stream), "batch graph launch");
     CK(cudaEventRecord(b->done[slot], (cudaStream_t)stream), "batch completion event");
     b->used[slot] = true;

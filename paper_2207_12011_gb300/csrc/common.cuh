@@ -194,6 +194,8 @@ struct RenderArgs {
     float4* out;
     uint32_t* counts;             // optional [h][w][2]
     float* depth;                 // optional [h][w]: t of the first kept sample, +inf if none
+    const int* tf_prefix;         // [kTF + 1]: entries < j with sigma > 0 (TF visibility)
+    int tf_skip;                  // batched views: classify against the TF visibility too
     unsigned long long* stats;    // optional kNStats counters
 };
 
@@ -273,6 +275,29 @@ __device__ __forceinline__ void brick_box_axis(int b, int nb, float sc, int bs, 
     hi = __fadd_rn(__fmaf_rn(__fadd_rn((float)(b * bs + bs), 0.5f), sc, -1.0f), 0x1p-10f);
     if (b == 0) lo = -2.0f;
     if (b == nb - 1) hi = 2.0f;
+}
+
+// TF entry index J(v) of a colour value, as the march computes it (FP32, monotone in v).
+__device__ __forceinline__ int tf_entry(float v, float tf_lo, float tf_scale) {
+    float sp = __fmul_rn(__fsub_rn(v, tf_lo), tf_scale);
+    sp = fminf(fmaxf(sp, 0.0f), 255.0f);
+    return min((int)sp, kTF - 2);
+}
+
+// TF visibility of a brick whose colour values lie in [mn, mx] (prefix[j] =
+// entries < j with sigma > 0): visible iff sigma > 0 at entry 0 (a NaN colour
+// value lands there), or the range cannot be bounded (max(|mn|,|mx|) > 2^126),
+// or sigma > 0 at an entry of J(mn - d) .. J(mx + d) + 1, d the brush margin
+// that bounds the FP32 interpolation. A sample whose two entries both have
+// sigma = 0 adds exactly nothing to the image.
+__device__ __forceinline__ bool tf_range_visible(float mn, float mx, const int* prefix, float tf_lo, float tf_scale) {
+    if (prefix[1] > 0) return true;
+    const float m = fmaxf(fabsf(mn), fabsf(mx));
+    if (!(m <= 0x1p126f)) return true;
+    const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
+    const int j0 = tf_entry(__fsub_rn(mn, d), tf_lo, tf_scale);
+    const int j1 = tf_entry(__fadd_rn(mx, d), tf_lo, tf_scale) + 1;
+    return j0 <= j1 && prefix[j1 + 1] - prefix[j0] > 0;
 }
 
 // Brush classification of brick b (edge bs) of a level with nb such bricks per
@@ -495,9 +520,9 @@ cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);
 // Grids are fixed by the caller (cls_blocks for the grid-stride classification,
 // blocks for the persistent render) so the launch can be captured in a graph;
 // launches are not counted here (the caller counts each replay).
-cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter,
+cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter, bool depth,
                                 int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream);
-int render_batch_blocks_per_sm(int dtype, int variant);
+int render_batch_blocks_per_sm(int dtype, int variant, bool depth);
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream);
 
 // Image warping (render_kernels.cu).

@@ -434,9 +434,14 @@ __global__ void k_classify_views(const BatchHeader* __restrict__ hdr, const Batc
         const int nb = sub ? V.a.lv.nsb : V.a.lv.nb;
         const size_t nbricks = (size_t)nb * nb * nb;
         unsigned pass_bits = 0;
-        const bool act = b < nbricks &&
+        bool act = b < nbricks &&
             classify_brick(b, nb, sub ? kSub : kBrick, 2.0f / (float)V.a.lv.n, V.a.rin2, V.a.rout2, V.a.brush,
                            V.a.nvars, sub ? V.sbmin : V.bmin, sub ? V.sbmax : V.bmax, pass_bits);
+        if (act && V.a.tf_skip) {                    // TF-aware skipping of this view
+            const size_t o = b * V.a.nvars + V.a.color_var;
+            act = tf_range_visible((sub ? V.sbmin : V.bmin)[o], (sub ? V.sbmax : V.bmax)[o], V.a.tf_prefix,
+                                   V.a.tf_lo, V.a.tf_scale);
+        }
         const unsigned word = __ballot_sync(0xffffffffu, act);
         uint32_t* active = const_cast<uint32_t*>(sub ? V.a.lv.sactive : V.a.lv.active);
         if (lane == 0) active[b >> 5] = word;
@@ -485,7 +490,7 @@ __global__ void __launch_bounds__(32 * kCellWarps) k_cell_classes_views(const Ba
 // contiguous, views in submission order), reloads its per-view shared state
 // when the view changes, and marches the tile. Blocks exit when the tiles run
 // out, so the kernel's lifetime is bounded by the batch.
-template <int DT, int VAR>
+template <int DT, int VAR, bool DEPTH>
 __global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader* __restrict__ hdr,
                                                            const BatchView* __restrict__ views,
                                                            unsigned* __restrict__ tile_counter) {
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, 9) k_render_batch(const BatchHeader*
             cur_view = vi;
             __syncthreads();
         }
-        march_pixel<DT, VAR, false>(s_args, S, s_tx, s_ty);
+        march_pixel<DT, VAR, DEPTH>(s_args, S, s_tx, s_ty);
         __syncthreads();   // the tile's pixels and statistics are issued; s_* are rewritten next
         if (threadIdx.x == 0) {
             const BatchView& V = views[vi];
@@ -559,15 +564,15 @@ cudaError_t launch_dt(const RenderArgs& a, cudaStream_t stream) {
     }
 }
 
-template <int DT, int VAR>
+template <int DT, int VAR, bool DEPTH>
 void batch_kernels(const BatchHeader* hdr, const BatchView* views, unsigned* counter, int blocks, cudaStream_t s) {
-    k_render_batch<DT, VAR><<<blocks, kThreads, 0, s>>>(hdr, views, counter);
+    k_render_batch<DT, VAR, DEPTH><<<blocks, kThreads, 0, s>>>(hdr, views, counter);
 }
 
-template <int DT, int VAR>
+template <int DT, int VAR, bool DEPTH>
 int batch_occupancy() {
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<DT, VAR>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_batch<DT, VAR, DEPTH>, kThreads, 0);
     return blocks > 0 ? blocks : 1;
 }
 
@@ -578,12 +583,17 @@ cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream) {
     return launch_dt<kF32>(a, stream);
 }
 
-int render_batch_blocks_per_sm(int dtype, int variant) {
-    if (dtype == kF16) return variant == 2 ? batch_occupancy<kF16, 2>() : variant == 3 ? batch_occupancy<kF16, 3>() : batch_occupancy<kF16, 1>();
-    return variant == 2 ? batch_occupancy<kF32, 2>() : variant == 3 ? batch_occupancy<kF32, 3>() : batch_occupancy<kF32, 1>();
+// A batch with a depth output in any view runs the depth instance with 8x4 tiles.
+int render_batch_blocks_per_sm(int dtype, int variant, bool depth) {
+    if (depth) return dtype == kF16 ? batch_occupancy<kF16, 1, true>() : batch_occupancy<kF32, 1, true>();
+    if (dtype == kF16)
+        return variant == 2 ? batch_occupancy<kF16, 2, false>() : variant == 3 ? batch_occupancy<kF16, 3, false>()
+                                                                : batch_occupancy<kF16, 1, false>();
+    return variant == 2 ? batch_occupancy<kF32, 2, false>() : variant == 3 ? batch_occupancy<kF32, 3, false>()
+                                                            : batch_occupancy<kF32, 1, false>();
 }
 
-cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter,
+cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, unsigned* tile_counter, bool depth,
                                 int dtype, int variant, unsigned cls_blocks, int blocks, cudaStream_t stream) {
     k_classify_views<<<cls_blocks, 256, 0, stream>>>(hdr, views);
     cudaError_t e = cudaGetLastError();
@@ -592,14 +602,17 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
     else k_cell_classes_views<kF32><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (dtype == kF16) {
-        if (variant == 2) batch_kernels<kF16, 2>(hdr, views, tile_counter, blocks, stream);
-        else if (variant == 3) batch_kernels<kF16, 3>(hdr, views, tile_counter, blocks, stream);
-        else batch_kernels<kF16, 1>(hdr, views, tile_counter, blocks, stream);
+    if (depth) {
+        if (dtype == kF16) batch_kernels<kF16, 1, true>(hdr, views, tile_counter, blocks, stream);
+        else batch_kernels<kF32, 1, true>(hdr, views, tile_counter, blocks, stream);
+    } else if (dtype == kF16) {
+        if (variant == 2) batch_kernels<kF16, 2, false>(hdr, views, tile_counter, blocks, stream);
+        else if (variant == 3) batch_kernels<kF16, 3, false>(hdr, views, tile_counter, blocks, stream);
+        else batch_kernels<kF16, 1, false>(hdr, views, tile_counter, blocks, stream);
     } else {
-        if (variant == 2) batch_kernels<kF32, 2>(hdr, views, tile_counter, blocks, stream);
-        else if (variant == 3) batch_kernels<kF32, 3>(hdr, views, tile_counter, blocks, stream);
-        else batch_kernels<kF32, 1>(hdr, views, tile_counter, blocks, stream);
+        if (variant == 2) batch_kernels<kF32, 2, false>(hdr, views, tile_counter, blocks, stream);
+        else if (variant == 3) batch_kernels<kF32, 3, false>(hdr, views, tile_counter, blocks, stream);
+        else batch_kernels<kF32, 1, false>(hdr, views, tile_counter, blocks, stream);
     }
     return cudaGetLastError();
 }

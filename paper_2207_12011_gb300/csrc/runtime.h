@@ -83,6 +83,7 @@ struct Volume {
     bool brush_set = false;
     BrushArgs brush{};
     float4* tf = nullptr;
+    int* tf_prefix = nullptr;     // [257]: TF entries < j with sigma > 0 (TF-aware skipping)
     bool tf_set = false;
     int color_var = 0;
     float tf_lo = 0.f, tf_hi = 1.f;

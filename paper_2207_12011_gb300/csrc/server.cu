@@ -517,9 +517,9 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
         if ((st = pos_from_host(r->pos_lo, r->pos_hi, r->pos_mask, &b))) { delete q; return st; }
         if (r->kind == RAYPC_REQ_RENDER) {
             RenderArgs a{};
-            if (r->opts.tf_skip || r->opts.depth_dev) {
+            if (r->opts.depth_dev) {          // outputs of a request are server-owned
                 delete q;
-                return fail(RAYPC_ERR_UNSUPPORTED, "tf_skip and depth_dev are for single-frame renders");
+                return fail(RAYPC_ERR_UNSUPPORTED, "depth_dev is not available for served requests");
             }
             if (r->w < 1 || r->h < 1 || r->w > 32768 || r->h > 32768) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "image size out of range"); }
             // validate camera / options with a stand-in aligned output pointer

@@ -520,19 +520,10 @@ cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
 
 namespace {
 
-// Entry index J(v) of a colour value, as the march computes it (FP32, monotone in v).
-__device__ __forceinline__ int tf_entry(float v, float tf_lo, float tf_scale) {
-    float sp = __fmul_rn(__fsub_rn(v, tf_lo), tf_scale);
-    sp = fminf(fmaxf(sp, 0.0f), 255.0f);
-    return min((int)sp, kTF - 2);
-}
-
 // One thread per brick (entries 0..nbricks-1, padded to whole words) and per
-// sub-brick (the entries after them): activity AND TF visibility. Visible iff
-// sigma > 0 at entry 0 (a NaN colour value lands there), or the colour range
-// cannot be bounded (max(|min|,|max|) > 2^126), or sigma > 0 at an entry of
-// J(min - d) .. J(max + d) + 1 (d the brush margin). A brick's range holds
-// its sub-bricks' ranges, so an invisible brick has only invisible sub-bricks.
+// sub-brick (the entries after them): activity AND TF visibility
+// (tf_range_visible). A brick's range holds its sub-bricks' ranges, so an
+// invisible brick has only invisible sub-bricks.
 __global__ void __launch_bounds__(256) k_tf_visibility(TfVisArgs A) {
     __shared__ int s_pre[kTF + 1];             // s_pre[j] = entries < j with sigma > 0
     if (threadIdx.x < 32) {
@@ -556,16 +547,10 @@ __global__ void __launch_bounds__(256) k_tf_visibility(TfVisArgs A) {
     if (b < cnt) {
         const uint32_t* act = is_sub ? A.sactive : A.active;
         bit = (act[b >> 5] >> (b & 31)) & 1u;
-        if (bit && s_pre[1] == 0) {                 // entry 0 transparent: the range decides
+        if (bit) {
             const float mn = (is_sub ? A.sbmin : A.bmin)[b * A.nvars + A.color_var];
             const float mx = (is_sub ? A.sbmax : A.bmax)[b * A.nvars + A.color_var];
-            const float m = fmaxf(fabsf(mn), fabsf(mx));
-            if (m <= 0x1p126f) {
-                const float d = __fmaf_rn(m, 0x1p-20f, 0x1p-120f);
-                const int j0 = tf_entry(__fsub_rn(mn, d), A.tf_lo, A.tf_scale);
-                const int j1 = tf_entry(__fadd_rn(mx, d), A.tf_lo, A.tf_scale) + 1;
-                bit = j0 <= j1 && s_pre[j1 + 1] - s_pre[j0] > 0;
-            }
+            bit = tf_range_visible(mn, mx, s_pre, A.tf_lo, A.tf_scale);
         }
     }
     const unsigned word = __ballot_sync(0xffffffffu, bit);

@@ -743,10 +743,6 @@ def test_tf_skip_keeps_the_image_and_matches_oracle(ctx, rp, n, store):
                     assert np.array_equal(c1.cpu().numpy().astype(np.uint32), rc), (kind, lod, skip)
             if kind == "zero":
                 assert int(c1[..., 1].sum()) == 0
-    b = rp.Batch(ctx, 2)
-    with pytest.raises(rp.RaypcError):
-        b.render([dict(vol=v, cam=cam, w=8, h=8, lo=brush.lo, hi=brush.hi, mask=brush.active_mask, tf_skip=True)])
-    b.close()
     v.free()
 
 
@@ -786,18 +782,48 @@ def test_depth_and_warp_match_oracle(ctx, rp, n, store):
     v.free()
 
 
-def test_batch_rejects_single_frame_options(ctx, rp):
-    vol = synth.make_shell_volume(16)
-    brush = synth.make_brush(vol, "c1")
+def test_batch_views_take_tf_skip_and_depth(ctx, rp):
+    """Batched views with TF-aware skipping and a depth output equal the single-frame renders."""
+    vol = synth.make_shell_volume(40, seed=29)
+    brush = synth.make_brush(vol, "c2")
     tf = synth.make_tf(vol, "T_anom")
-    v = load(ctx, vol, "f32", brush=brush, tf=tf)
-    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
-    b = rp.Batch(ctx, 2)
-    view = dict(vol=v, cam=cam, w=8, h=8, lo=brush.lo, hi=brush.hi, mask=brush.active_mask)
-    arr, _ = rp._view_array(ctx, [view])
-    d = torch.empty((8, 8), device="cuda")
-    arr[0].opts.depth_dev = d.data_ptr()
-    with pytest.raises(rp.RaypcError):
-        rp._call("raypc_render_batch", b._h, arr, 1, rp._stream(None))
+    v = load(ctx, vol, "f32", n_lod=1, brush=brush, tf=tf)
+    cams = [synth.orbit_camera(**synth.DEFAULT_CAMERA), synth.orbit_camera(120, -20, 2.8)]
+    b = rp.Batch(ctx, 4)
+    for use_depth in (False, True):
+        views, refs = [], []
+        for i, cam in enumerate(cams):
+            w, h = 45 + 8 * i, 37
+            d = torch.empty((h, w), dtype=torch.float32, device="cuda") if use_depth else None
+            views.append(dict(vol=v, cam=cam, w=w, h=h, lo=brush.lo, hi=brush.hi, mask=brush.active_mask,
+                              lod=i, tf_skip=bool(i == 0) or use_depth, counts=True, ert=False))
+            r = v.render(cam, w, h, lod=i, tf_skip=views[-1]["tf_skip"], counts=True, ert=False,
+                         depth=bool(use_depth))
+            refs.append(r)
+        arr, outs = rp._view_array(ctx, views)
+        depths = []
+        if use_depth:
+            for i, q in enumerate(views):
+                dd = torch.full((q["h"], q["w"]), -1.0, device="cuda")
+                arr[i].opts.depth_dev = dd.data_ptr()
+                depths.append(dd)
+        rp._call("raypc_render_batch", b._h, arr, len(views), rp._stream(None))
+        torch.cuda.synchronize()
+        for i, (img, cnt) in enumerate(outs):
+            assert torch.equal(img, refs[i][0]) and torch.equal(cnt, refs[i][1]), (use_depth, i)
+            if use_depth:
+                assert torch.equal(depths[i], refs[i][2]), i
     b.close()
+    with rp.Server(ctx) as srv:
+        r = rp.Request()
+        r.kind = rp.REQ_RENDER
+        r.vol = v.id
+        rp._fill_brush(r, v, brush.lo, brush.hi, brush.active_mask)
+        rp._fill_pos(r, None)
+        r.cam = rp.camera_from(cams[0])
+        r.w, r.h, r.lod, r.coarse_lod = 8, 8, 0, -1
+        r.opts = rp._opts(depth=torch.empty((8, 8), device="cuda"))
+        rid = rp.ctypes.c_uint64()
+        with pytest.raises(rp.RaypcError):
+            rp._call("raypc_serve_submit", srv._h, rp.ctypes.byref(r), rp.ctypes.byref(rid))
     v.free()
