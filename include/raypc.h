@@ -122,8 +122,8 @@ typedef struct raypc_render_opts {
     float bg[4];         /* premultiplied background RGBA composited under     */
     uint32_t *counts_dev;/* optional [h][w][2] uint32: per pixel, lattice
                             samples marched and samples kept (debug/testing)    */
-    int tf_skip;         /* nonzero: TF-aware skipping (single-frame renders;
-                            raypc_render_batch rejects it). A sample whose two
+    int tf_skip;         /* nonzero: TF-aware skipping (single frames and
+                            batched views; served requests too). A sample whose two
                             transfer-function entries both have sigma = 0 adds
                             exactly nothing; a 4^3 sub-brick is skipped when its
                             colour values v in [min - d, max + d] (brush margin
@@ -139,9 +139,9 @@ typedef struct raypc_render_opts {
                             sample, t0 + (k + j) * step in FP32 exactly as the
                             march computes it; +inf where no sample is kept.
                             The depth that raypc_warp_image reprojects.
-                            Single-frame renders (raypc_render,
-                            raypc_render_progressive; always 8x4 tiles);
-                            raypc_render_batch rejects it.                      */
+                            raypc_render, raypc_render_progressive and
+                            batched views (a batch with any depth output
+                            runs 8x4 tiles); served requests reject it.         */
 } raypc_render_opts;
 
 /* ---------------------------------------------------------------------- */

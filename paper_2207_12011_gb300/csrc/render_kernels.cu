@@ -135,8 +135,7 @@ __device__ __forceinline__ void load_view_shared(const RenderArgs& A, ViewShared
 // March the ray of this thread's pixel in block tile (tile_x, tile_y) of view A
 // and write its pixel, optional counts and (warp-aggregated) statistics. All
 // 32 lanes of every warp must call it. DEPTH: the depth output may be requested
-// (A.depth; single-frame renders only); without it the march keeps no trace of
-// the first kept sample.
+// (A.depth); without it the march keeps no trace of the first kept sample.
 template <int DT, int VAR, bool DEPTH>
 __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShared& S, int tile_x, int tile_y) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
