@@ -342,21 +342,26 @@ def run_ours(args):
     wout = torch.empty_like(wimg)
     for _ in range(3):
         _, widx = rp.warp_image(ctx, wl.cam, cam2, wimg, wdepth, out=wout, with_src=True)
-    ww = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ww = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     ww[0].record()
     for _ in range(10):
         rp.warp_image(ctx, wl.cam, cam2, wimg, wdepth, out=wout)
     ww[1].record()
+    for _ in range(10):
+        _, fidx = rp.warp_image(ctx, wl.cam, cam2, wimg, wdepth, out=wout, with_src=True, fill_holes=True)
+    ww[2].record()
     torch.cuda.synchronize()
     fin = torch.isfinite(wdepth)
     warp = {"ms": round(ww[0].elapsed_time(ww[1]) / 10, 4),
             "render_ms": round(render_ms, 4),
             "pixels_with_depth": int(fin.sum()),
             "warped_pixels_filled": int((widx >= 0).sum()),
+            "ms_fill_holes": round(ww[1].elapsed_time(ww[2]) / 10, 4),
+            "pixels_filled_with_holes_filled": int((fidx >= 0).sum()),
             "what": "1024^2 frame with first-kept-sample depth warped to the camera moved by 2 deg azimuth, "
                     "1 deg elevation and 2 % closer"}
-    del wimg, wdepth, wout, widx
+    del wimg, wdepth, wout, widx, fidx
 
     # ---- position axes (brush and PC axis) and the PC line subsample ----
     pos = (np.float32([-0.5, -np.inf, -np.inf, 0.6]), np.float32([0.5, np.inf, np.inf, 0.95]), 0b1001)

@@ -313,14 +313,17 @@ raypc_status raypc_render_progressive(raypc_ctx *ctx, int vol, int lod, const ra
  * qy = Y / (z * tan'); it lands in column floor((qx + 1) * w/2) and row
  * floor((1 - qy) * h/2) if inside the image. Every target pixel takes the
  * colour of the landed source of smallest z (ties: smallest s); target pixels
- * that no source reaches take bg (host array of 4 floats, NULL = 0).
+ * that no source reaches take bg (host array of 4 floats, NULL = 0) -- or,
+ * with fill_holes nonzero, the source chosen for the reached neighbour (of
+ * their 8) whose source has the smallest z (ties: smallest s), in one pass
+ * over the forward result (bg if no neighbour was reached).
  * out_src_dev (optional, [h][w] int32) receives the chosen s or -1. All
  * decisions use correctly rounded FP32 operations in one fixed order.
  * Buffers are caller-owned device memory; out_rgba_dev must not alias
  * src_rgba_dev; RGBA buffers 16-byte aligned. */
 raypc_status raypc_warp_image(raypc_ctx *ctx, const raypc_camera *from, const raypc_camera *to, int w, int h,
                               const float *src_rgba_dev, const float *src_depth_dev, const float *bg,
-                              float *out_rgba_dev, int32_t *out_src_dev, void *stream);
+                              int fill_holes, float *out_rgba_dev, int32_t *out_src_dev, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched rendering (many views and brushes in one launch)                */

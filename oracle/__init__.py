@@ -76,7 +76,7 @@ def _load():
             lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                                P, P, u32, P, i32, f32, f32, P, i32, P,
                                                ctypes.c_int64, P, P, i32, u32, u32, P, P, u32, i32, P]
-            lib.oracle_warp.argtypes = [P, P, P, P, i32, i32, P, P, P]
+            lib.oracle_warp.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
             lib.oracle_tf_visibility.argtypes = [P, i32, i32, i32, P, f32, f32, P]
             lib.oracle_render_pass.restype = i32
             lib.oracle_jitter.argtypes = [u32, u32, ctypes.c_uint64]
@@ -300,14 +300,15 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
     return (out, cnt, depth) if return_depth else (out, cnt)
 
 
-def warp(src_rgba, src_depth, cam_from, cam_to, bg=(0.0, 0.0, 0.0, 0.0)):
+def warp(src_rgba, src_depth, cam_from, cam_to, bg=(0.0, 0.0, 0.0, 0.0), fill_holes=False):
     """Forward-warp an (h, w, 4) float32 image with its (h, w) depth to a new camera ->
-    (float32 image (h, w, 4), int32 source index per pixel or -1)."""
+    (float32 image (h, w, 4), int32 source index per pixel or -1); fill_holes fills
+    unreached pixels from their nearest-z reached neighbour."""
     src = _f32(src_rgba)
     h, w = src.shape[0], src.shape[1]
     dep = _f32(src_depth).reshape(h, w)
     out = np.zeros((h, w, 4), np.float32)
     idx = np.zeros((h, w), np.int32)
     _load().oracle_warp(_ptr(src), _ptr(dep), _ptr(_f32(cam_from)), _ptr(_f32(cam_to)), int(w), int(h),
-                        _ptr(_f32(bg)), _ptr(out), _ptr(idx))
+                        _ptr(_f32(bg)), int(bool(fill_holes)), _ptr(out), _ptr(idx))
     return out, idx

@@ -847,11 +847,14 @@ int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }
 /* tan'); target column floor((qx + 1) * (w/2)), row floor((1 - qy) *    */
 /* (h/2)), dropped outside the image. Each target pixel takes the        */
 /* colour of the source of smallest z, ties to the smallest source       */
-/* index; pixels no source reaches take the background. out_src gets    */
-/* the chosen source index or -1.                                         */
+/* index; pixels no source reaches take the background. With fill_holes,*/
+/* a pixel no source reaches takes, among its 8 neighbours that a source */
+/* reached, the one whose source has the smallest z (ties: smallest      */
+/* source index), one pass over the forward result. out_src gets the     */
+/* chosen source index or -1.                                            */
 /* ------------------------------------------------------------------ */
 void oracle_warp(const float *src_rgba, const float *src_depth, const float *cam_from, const float *cam_to,
-                 int w, int h, const float *bg, float *out_rgba, int32_t *out_src) {
+                 int w, int h, const float *bg, int fill_holes, float *out_rgba, int32_t *out_src) {
     size_t npix = (size_t)w * h;
     float *best = (float *)malloc(sizeof(float) * npix);
     for (size_t i = 0; i < npix; i++) { best[i] = INFINITY; out_src[i] = -1; }
@@ -880,6 +883,30 @@ void oracle_warp(const float *src_rgba, const float *src_depth, const float *cam
                 out_src[t] = (int32_t)s;
             }
         }
+    if (fill_holes) {
+        int32_t *fwd = (int32_t *)malloc(sizeof(int32_t) * npix);
+        memcpy(fwd, out_src, sizeof(int32_t) * npix);
+        for (int y = 0; y < h; y++)
+            for (int x = 0; x < w; x++) {
+                size_t t = (size_t)y * w + x;
+                if (fwd[t] >= 0) continue;
+                float bz = INFINITY;
+                int32_t bs = -1;
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int xx = x + dx, yy = y + dy;
+                        if ((dx == 0 && dy == 0) || xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                        size_t u = (size_t)yy * w + xx;
+                        if (fwd[u] < 0) continue;
+                        if (best[u] < bz || (best[u] == bz && fwd[u] < bs)) {
+                            bz = best[u];
+                            bs = fwd[u];
+                        }
+                    }
+                out_src[t] = bs;
+            }
+        free(fwd);
+    }
     for (size_t t = 0; t < npix; t++)
         for (int c = 0; c < 4; c++)
             out_rgba[4 * t + c] = out_src[t] >= 0 ? src_rgba[4 * (size_t)out_src[t] + c] : bg[c];

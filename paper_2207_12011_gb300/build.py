@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(LIB_DIR, "libraypc.so")
 HEADER = os.path.join(ROOT, "include", "raypc.h")
 
 SOURCES = ["api.cu", "volume_kernels.cu", "render_kernels.cu", "hist_kernels.cu", "hist_noalloc.cu", "pcsub_kernels.cu",
-           "points_kernels.cu",
+           "points_kernels.cu", "warp_kernels.cu",
            "batch.cu", "tune.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",

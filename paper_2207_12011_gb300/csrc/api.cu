@@ -896,7 +896,7 @@ static raypc_status check_camera(const raypc_camera* cam) {
 
 raypc_status raypc_warp_image(raypc_ctx* ctx, const raypc_camera* from, const raypc_camera* to, int w, int h,
                               const float* src_rgba_dev, const float* src_depth_dev, const float* bg,
-                              float* out_rgba_dev, int32_t* out_src_dev, void* stream) {
+                              int fill_holes, float* out_rgba_dev, int32_t* out_src_dev, void* stream) {
     if (!ctx || !src_rgba_dev || !src_depth_dev || !out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     raypc_status st;
     if ((st = check_camera(from)) || (st = check_camera(to))) return st;
@@ -922,6 +922,7 @@ raypc_status raypc_warp_image(raypc_ctx* ctx, const raypc_camera* from, const ra
     }
     a.out = reinterpret_cast<float4*>(out_rgba_dev);
     a.out_src = out_src_dev;
+    a.fill_holes = fill_holes ? 1 : 0;
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;

@@ -62,6 +62,52 @@ __device__ __forceinline__ float trilerp_rn(float c000, float c100, float c010, 
     return lerp_rn(c0, c1, fz);
 }
 
+// Exactly rounded vector helpers of the camera model.
+__device__ __forceinline__ void normalize_rn(float& x, float& y, float& z) {
+    float l = __fsqrt_rn(dot3_rn(x, y, z, x, y, z));
+    x = __fdiv_rn(x, l);
+    y = __fdiv_rn(y, l);
+    z = __fdiv_rn(z, l);
+}
+
+__device__ __forceinline__ void cross_rn(float ax, float ay, float az, float bx, float by, float bz,
+                                         float& cx, float& cy, float& cz) {
+    cx = __fmaf_rn(ay, bz, -__fmul_rn(az, by));
+    cy = __fmaf_rn(az, bx, -__fmul_rn(ax, bz));
+    cz = __fmaf_rn(ax, by, -__fmul_rn(ay, bx));
+}
+
+// Pinhole camera basis (exactly rounded, fixed order): F = normalize(target - eye),
+// R = normalize(cross(F, up)), U = cross(R, F).
+__device__ __forceinline__ void camera_basis_rn(const float* eye, const float* target, const float* up,
+                                                float& Fx, float& Fy, float& Fz, float& Rx, float& Ry, float& Rz,
+                                                float& Ux, float& Uy, float& Uz) {
+    Fx = __fsub_rn(target[0], eye[0]);
+    Fy = __fsub_rn(target[1], eye[1]);
+    Fz = __fsub_rn(target[2], eye[2]);
+    normalize_rn(Fx, Fy, Fz);
+    cross_rn(Fx, Fy, Fz, up[0], up[1], up[2], Rx, Ry, Rz);
+    normalize_rn(Rx, Ry, Rz);
+    cross_rn(Rx, Ry, Rz, Fx, Fy, Fz, Ux, Uy, Uz);
+}
+
+// Unit direction of the ray through pixel (px, py) of a w x h image.
+__device__ __forceinline__ void camera_ray_rn(const float* eye, const float* target, const float* up, float tan_half,
+                                              int w, int h, int px, int py, float& dx, float& dy, float& dz) {
+    float Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz;
+    camera_basis_rn(eye, target, up, Fx, Fy, Fz, Rx, Ry, Rz, Ux, Uy, Uz);
+    const float aspect = __fdiv_rn((float)w, (float)h);
+    const float sxs = __fmul_rn(tan_half, aspect);
+    const float qx = __fdiv_rn((float)(2 * px + 1), (float)w);
+    const float qy = __fdiv_rn((float)(2 * py + 1), (float)h);
+    const float sx = __fmul_rn(__fsub_rn(qx, 1.0f), sxs);
+    const float sy = __fmul_rn(__fsub_rn(1.0f, qy), tan_half);
+    dx = __fmaf_rn(sy, Ux, __fmaf_rn(sx, Rx, Fx));
+    dy = __fmaf_rn(sy, Uy, __fmaf_rn(sx, Ry, Fy));
+    dz = __fmaf_rn(sy, Uz, __fmaf_rn(sx, Rz, Fz));
+    normalize_rn(dx, dy, dz);
+}
+
 // SplitMix64 (Steele, Lea and Flood 2014) as a counter-based generator: the
 // output function of the state key + (i + 1) * 0x9E3779B97F4A7C15 for stream
 // `key` and counter i. The output function is a bijection of 64-bit words.
@@ -536,6 +582,7 @@ struct WarpArgs {
     unsigned long long* keys;     // [h][w] scratch
     float4* out;                  // [h][w]
     int* out_src;                 // optional [h][w]: chosen source pixel or -1
+    int fill_holes;               // unreached pixels take their nearest-z reached neighbour
 };
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t stream);
 

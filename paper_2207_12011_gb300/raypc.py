@@ -112,7 +112,7 @@ _SIGS = {
     "raypc_set_position_brush": [_P, _I, _P, _P, _U32, _P],
     "raypc_pc_subsample": [_P, _I, _I, _U32, ctypes.c_longlong, _P, _I, _P, _P, _P, _P, _P],
     "raypc_filter_points": [_P, _I, _I, _P, ctypes.c_longlong, _P, _P],
-    "raypc_warp_image": [_P, ctypes.POINTER(Camera), ctypes.POINTER(Camera), _I, _I, _P, _P, _P, _P, _P, _P],
+    "raypc_warp_image": [_P, ctypes.POINTER(Camera), ctypes.POINTER(Camera), _I, _I, _P, _P, _P, _I, _P, _P, _P],
     "raypc_render_progressive": [_P, _I, _I, ctypes.POINTER(Camera), _I, _I, ctypes.POINTER(RenderOpts),
                                  _U32, _U32, _P, _P, _P, _P],
     "raypc_pc_histogram": [_P, _I, _I, _P, _I, _I, _P, _I, _P, _P],
@@ -540,7 +540,7 @@ def _view_array(ctx, views):
 
 
 def warp_image(ctx: Context, cam_from, cam_to, src: torch.Tensor, depth: torch.Tensor, bg=(0.0, 0.0, 0.0, 0.0),
-               out: torch.Tensor | None = None, with_src: bool = False, stream=None):
+               out: torch.Tensor | None = None, with_src: bool = False, fill_holes: bool = False, stream=None):
     """Forward-warp an (h, w, 4) float32 image with its (h, w) depth from cam_from to cam_to.
     Returns the warped image, and the chosen source pixel per target pixel (int32, -1: none)
     when with_src."""
@@ -551,7 +551,7 @@ def warp_image(ctx: Context, cam_from, cam_to, src: torch.Tensor, depth: torch.T
     cf, ct = camera_from(cam_from), camera_from(cam_to)
     b = np.ascontiguousarray(np.asarray(bg, dtype=np.float32).reshape(4))
     _call("raypc_warp_image", ctx.handle, ctypes.byref(cf), ctypes.byref(ct), w, h,
-          ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(depth.data_ptr()), _fptr(b),
+          ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(depth.data_ptr()), _fptr(b), int(bool(fill_holes)),
           ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(idx.data_ptr()) if idx is not None else None,
           _stream(stream))
     return (out, idx) if with_src else out

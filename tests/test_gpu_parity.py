@@ -769,11 +769,12 @@ def test_depth_and_warp_match_oracle(ctx, rp, n, store):
     bg = (0.05, 0.1, 0.2, 1.0)
     src, dep = img.cpu().numpy(), depth.cpu().numpy()
     for new in (cam, synth.orbit_camera(33, 22, 2.9), synth.orbit_camera(20, 10, 3.4)):
-        out, idx = rp.warp_image(ctx, cam, new, img, depth, bg=bg, with_src=True)
-        torch.cuda.synchronize()
-        ro, ridx = oracle.warp(src, dep, cam.as_array(), new.as_array(), bg)
-        assert np.array_equal(idx.cpu().numpy(), ridx)
-        assert np.array_equal(out.cpu().numpy(), ro)
+        for fill in (False, True):
+            out, idx = rp.warp_image(ctx, cam, new, img, depth, bg=bg, with_src=True, fill_holes=fill)
+            torch.cuda.synchronize()
+            ro, ridx = oracle.warp(src, dep, cam.as_array(), new.as_array(), bg, fill_holes=fill)
+            assert np.array_equal(idx.cpu().numpy(), ridx), fill
+            assert np.array_equal(out.cpu().numpy(), ro), fill
     fin = np.isfinite(dep)
     out, idx = rp.warp_image(ctx, cam, cam, img, depth, with_src=True)
     assert np.array_equal(out.cpu().numpy()[fin], src[fin])                  # identity warp

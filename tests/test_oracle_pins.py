@@ -1231,3 +1231,53 @@ def test_warp_keeps_the_nearest_source():
         checked += 1
         collided += len(lst) > 1
     assert checked > 300 and collided > 20
+
+
+def test_warp_hole_filling_takes_the_nearest_reached_neighbour():
+    w = h = 64
+    s = 4
+    cam = synth.Camera((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    delta = 3.0 * s / w
+    moved = synth.Camera((delta, 0.0, 3.0), (delta, 0.0, 0.0), (0.0, 1.0, 0.0), 0.5)
+    rng = np.random.default_rng(7)
+    img = rng.random((h, w, 4)).astype(np.float32)
+    depth = _plane_depth(cam, w, h, 3.0)
+    _, src0 = oracle.warp(img, depth, cam.as_array(), moved.as_array())
+    out, src = oracle.warp(img, depth, cam.as_array(), moved.as_array(), fill_holes=True)
+    assert np.array_equal(src[:, : w - s], src0[:, : w - s])          # reached pixels unchanged
+    assert np.all(src[:, w - s + 1:] == -1)                           # no reached neighbour: still a hole
+    for y in range(h):                                                # the first hole column: a neighbour's source
+        nb = {int(src0[yy, w - s - 1]) for yy in (y - 1, y, y + 1) if 0 <= yy < h}
+        assert int(src[y, w - s]) in nb
+        assert np.array_equal(out[y, w - s], img.reshape(-1, 4)[src[y, w - s]])
+    # random depths: each filled pixel takes the reached neighbour of smallest source z (FP64, clear cases)
+    rng = np.random.default_rng(8)
+    w, h = 40, 30
+    cam = synth.orbit_camera(30, 10, 3.0)
+    new = synth.orbit_camera(38, 16, 2.4)
+    img = rng.random((h, w, 4)).astype(np.float32)
+    depth = rng.uniform(1.8, 3.5, (h, w)).astype(np.float32)
+    _, src0 = oracle.warp(img, depth, cam.as_array(), new.as_array())
+    _, src = oracle.warp(img, depth, cam.as_array(), new.as_array(), fill_holes=True)
+    eye, d = pixel_rays64(cam, w, h)
+    P = eye[None, None, :] + depth[..., None].astype(np.float64) * d
+    e2 = np.array(new.eye, np.float64)
+    F = np.array(new.target, np.float64) - e2
+    F /= np.linalg.norm(F)
+    zsrc = ((P - e2) @ F).reshape(-1)
+    filled = 0
+    for y in range(h):
+        for x in range(w):
+            if src0[y, x] >= 0:
+                continue
+            cand = [(zsrc[src0[yy, xx]], int(src0[yy, xx])) for yy in range(y - 1, y + 2) for xx in range(x - 1, x + 2)
+                    if (yy, xx) != (y, x) and 0 <= yy < h and 0 <= xx < w and src0[yy, xx] >= 0]
+            if not cand:
+                assert src[y, x] == -1
+                continue
+            cand.sort()
+            if len(cand) > 1 and cand[1][0] - cand[0][0] < 1e-4:
+                continue
+            assert src[y, x] == cand[0][1]
+            filled += 1
+    assert filled > 20
