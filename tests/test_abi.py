@@ -31,7 +31,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("raypc_create", "raypc_destroy", "raypc_load_volume", "raypc_build_bricks",
                      "raypc_set_brush", "raypc_set_tf", "raypc_render", "raypc_pc_histogram",
-                     "raypc_get_skip_list"):
+                     "raypc_get_skip_list", "raypc_render_progressive", "raypc_set_position_brush",
+                     "raypc_pc_subsample", "raypc_filter_points", "raypc_warp_image"):
         assert required in names
 
 
@@ -81,12 +82,16 @@ def test_struct_layouts_match_the_binding(tmp_path):
         ' sizeof(raypc_view), offsetof(raypc_view, opts), offsetof(raypc_view, out_rgba_dev),'
         ' offsetof(raypc_render_opts, counts_dev)); printf("%zu %zu %zu %zu %zu\\n", sizeof(raypc_request),'
         ' sizeof(raypc_result), sizeof(raypc_server_config), offsetof(raypc_request, edges),'
-        ' sizeof(raypc_tuning)); return 0;}\n')
+        ' sizeof(raypc_tuning)); printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(raypc_render_opts, tf_skip),'
+        ' offsetof(raypc_render_opts, depth_dev), offsetof(raypc_view, pos_lo), offsetof(raypc_view, pos_mask),'
+        ' offsetof(raypc_request, pos_lo), offsetof(raypc_request, pos_mask)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(rp.Camera), ctypes.sizeof(rp.RenderOpts), ctypes.sizeof(rp.View),
             rp.View.opts.offset, rp.View.out_rgba_dev.offset, rp.RenderOpts.counts_dev.offset,
             ctypes.sizeof(rp.Request), ctypes.sizeof(rp.Result), ctypes.sizeof(rp.ServerConfig),
-            rp.Request.edges.offset, ctypes.sizeof(rp.Tuning)]
+            rp.Request.edges.offset, ctypes.sizeof(rp.Tuning), rp.RenderOpts.tf_skip.offset,
+            rp.RenderOpts.depth_dev.offset, rp.View.pos_lo.offset, rp.View.pos_mask.offset,
+            rp.Request.pos_lo.offset, rp.Request.pos_mask.offset]
     assert got == want
