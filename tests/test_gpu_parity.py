@@ -828,3 +828,42 @@ def test_batch_views_take_tf_skip_and_depth(ctx, rp):
         with pytest.raises(rp.RaypcError):
             rp._call("raypc_serve_submit", srv._h, rp.ctypes.byref(r), rp.ctypes.byref(rid))
     v.free()
+
+
+def test_feature_combinations_match_oracle(ctx, rp):
+    """Progressive pass + position brush + TF skipping together; warping with NaN and
+    infinite depths; the point filter with the position brush on a coarse level."""
+    n = 40
+    vol = synth.make_shell_volume(n, seed=31)
+    brush = synth.make_brush(vol, "c3")
+    tf = synth.make_tf(vol, "T_anom")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    w, h = 57, 43
+    v = load(ctx, vol, "f32", n_lod=1, brush=brush, tf=tf)
+    v.set_position_brush(*POS)
+    level = stored(vol, "f32")
+    for p in (0, 3):
+        img, cnt = v.render_progressive(cam, w, h, 9, p, None, ert=False, counts=True, tf_skip=True)
+        torch.cuda.synchronize()
+        ref, rc = oracle.render(level, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n, brush.lo, brush.hi,
+                                brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=False,
+                                seed=9, pass_=p, pos=POS, tf_skip=True)
+        assert np.array_equal(cnt.cpu().numpy().astype(np.uint32), rc), p
+        assert np.abs(img.cpu().numpy().astype(np.float64) - ref).max() <= TOL["f32"], p
+    img, _, depth = v.render(cam, w, h, depth=True)
+    dep = depth.cpu().numpy().copy()
+    dep[::7, ::5] = np.nan
+    dep[3::11, 2::9] = np.inf
+    dd = torch.from_numpy(dep).cuda()
+    new = synth.orbit_camera(41, 18, 2.7)
+    for fill in (False, True):
+        out, idx = rp.warp_image(ctx, cam, new, img, dd, with_src=True, fill_holes=fill)
+        torch.cuda.synchronize()
+        ro, ridx = oracle.warp(img.cpu().numpy(), dep, cam.as_array(), new.as_array(), fill_holes=fill)
+        assert np.array_equal(idx.cpu().numpy(), ridx) and np.array_equal(out.cpu().numpy(), ro), fill
+    pts = np.random.default_rng(2).uniform(-1, 1, (20000, 3)).astype(np.float32)
+    got = v.filter_points(torch.from_numpy(pts).cuda(), lod=1).cpu().numpy()
+    want = oracle.filter_points(oracle_levels(level, 1, "f32")[1], R_IN, R_OUT, brush.lo, brush.hi,
+                                brush.active_mask, pts, pos=POS)
+    assert np.array_equal(got, want)
+    v.free()
