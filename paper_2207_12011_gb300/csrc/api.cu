@@ -463,7 +463,7 @@ raypc_status raypc_update_volume(raypc_ctx* ctx, int vol, const void* src, int s
     if (src_dtype != RAYPC_F32 && src_dtype != RAYPC_F16) return fail(RAYPC_ERR_INVALID_ARG, "bad src_dtype");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     if ((st = ingest(ctx, V, src, src_is_device, src_dtype, (cudaStream_t)stream))) return st;
@@ -476,7 +476,7 @@ raypc_status raypc_free_volume(raypc_ctx* ctx, int vol) {
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     ctx->vols.erase(vol);
@@ -491,7 +491,7 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
     if (n_lod < 0 || n_lod > RAYPC_MAX_LOD) return fail(RAYPC_ERR_INVALID_ARG, "n_lod %d not in 0..%d", n_lod, RAYPC_MAX_LOD);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -540,7 +540,7 @@ raypc_status raypc_set_brush(raypc_ctx* ctx, int vol, const float* lo, const flo
     if (!ctx || !lo || !hi) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     BrushArgs b{};
@@ -558,7 +558,7 @@ raypc_status raypc_set_position_brush(raypc_ctx* ctx, int vol, const float* lo, 
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     BrushArgs b = V->brush;
@@ -582,7 +582,7 @@ raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_
         if (rgbs[4 * i + 3] < 0.f) return fail(RAYPC_ERR_INVALID_ARG, "negative extinction at entry %d", i);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
     if (color_var < 0 || color_var >= V->nvars) return fail(RAYPC_ERR_INVALID_ARG, "color_var %d out of range", color_var);
@@ -644,10 +644,10 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     RenderArgs a{};
     if ((st = make_render_args(V, L, cam, w, h, opts, out_rgba_dev, stats_dev, &a))) return st;
@@ -669,10 +669,10 @@ raypc_status raypc_render_progressive(raypc_ctx* ctx, int vol, int lod, const ra
     if (accum_rgba_dev && accum_rgba_dev == out_rgba_dev) return fail(RAYPC_ERR_INVALID_ARG, "accum_rgba_dev and out_rgba_dev alias");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     RenderArgs a{};
     if ((st = make_render_args(V, L, cam, w, h, opts, out_rgba_dev, stats_dev, &a))) return st;
@@ -712,10 +712,10 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         }
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if ((st = check_axes(V, axis_order, naxes))) return st;
     if (use_brush && !V->brush_set) return fail(RAYPC_ERR_INVALID_ARG, "use_brush needs raypc_set_brush");
@@ -796,10 +796,10 @@ raypc_status raypc_pc_subsample(raypc_ctx* ctx, int vol, int lod, uint32_t seed,
     if (((uintptr_t)out_values_dev) & 3u) return fail(RAYPC_ERR_INVALID_ARG, "out_values_dev must be 4-byte aligned");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if ((st = check_axes(V, axis_order, naxes))) return st;
     if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
@@ -851,10 +851,10 @@ raypc_status raypc_filter_points(raypc_ctx* ctx, int vol, int lod, const float* 
     if (((uintptr_t)points_dev) & 3u) return fail(RAYPC_ERR_INVALID_ARG, "points_dev must be 4-byte aligned");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if (V->stale && lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level %d is stale after raypc_update_volume", lod);
     RenderArgs r{};                       // the brush and the per-sample |p|^2 range of a render
@@ -938,10 +938,10 @@ raypc_status raypc_volume_info(raypc_ctx* ctx, int vol, int lod, int* out_n, int
                                int* out_dtype, int* out_bricks_per_axis) {
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if (out_n) *out_n = L->n;
     if (out_nvars) *out_nvars = V->nvars;
@@ -954,10 +954,10 @@ raypc_status raypc_export_volume(raypc_ctx* ctx, int vol, int lod, void* out_dev
     if (!ctx || !out_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     CK(cudaMemcpyAsync(out_dev, L->cells, L->cells_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
        "export copy");
@@ -969,10 +969,10 @@ raypc_status raypc_get_bricks(raypc_ctx* ctx, int vol, int lod, float* out_min_d
     if (!ctx || !out_min_dev || !out_max_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d not built", lod);
     size_t bytes = L->nbricks() * V->nvars * sizeof(float);
@@ -988,10 +988,10 @@ raypc_status raypc_get_skip_list(raypc_ctx* ctx, int vol, int lod, uint32_t* act
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
@@ -1008,10 +1008,10 @@ raypc_status raypc_get_cell_classes(raypc_ctx* ctx, int vol, int lod, uint16_t* 
     if (!ctx || !out_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1026,10 +1026,10 @@ raypc_status raypc_get_sub_bricks(raypc_ctx* ctx, int vol, int lod, float* out_m
     if (!ctx) return fail(RAYPC_ERR_INVALID_ARG, "NULL context");
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeviceGuard g(ctx->device);
-    Volume* V;
+    Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    Level* L;
+    Level* L = nullptr;
     if ((st = get_level(V, lod, &L))) return st;
     if (!L->bricks) return fail(RAYPC_ERR_INVALID_ARG, "bricks of level %d not built", lod);
     cudaStream_t s = (cudaStream_t)stream;

@@ -182,9 +182,9 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     raypc_status st;
     for (int i = 0; i < nviews; ++i) {
         const raypc_view& q = views[i];
-        Volume* V;
+        Volume* V = nullptr;
         if ((st = get_volume(ctx, q.vol, &V))) return st;
-        Level* L;
+        Level* L = nullptr;
         if ((st = get_level(V, q.lod, &L))) return st;
         if (dtype < 0) dtype = V->dtype;
         if (V->dtype != dtype) return fail(RAYPC_ERR_INVALID_ARG, "view %d: all views of a batch need one storage dtype", i);

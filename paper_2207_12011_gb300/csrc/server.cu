@@ -177,8 +177,8 @@ void finish(raypc_server* S, Req* q, int status) {
 raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(S->ctx->mu);
     DeviceGuard g(S->ctx->device);
-    Volume* V;
-    Level* L;
+    Volume* V = nullptr;
+    Level* L = nullptr;
     raypc_status st;
     if ((st = get_volume(S->ctx, q->r.vol, &V)) || (st = get_level(V, q->r.lod, &L))) return st;
     if (V->stale && q->r.lod > 0) return fail(RAYPC_ERR_INVALID_ARG, "level is stale");
@@ -508,8 +508,8 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
         // validate against the volume now (context lock only)
         std::lock_guard<std::mutex> lk(S->ctx->mu);
         DeviceGuard g(S->ctx->device);
-        Volume* V;
-        Level* L;
+        Volume* V = nullptr;
+        Level* L = nullptr;
         raypc_status st;
         if ((st = get_volume(S->ctx, r->vol, &V)) || (st = get_level(V, r->lod, &L))) { delete q; return st; }
         BrushArgs b{};
@@ -525,7 +525,7 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
             // validate camera / options with a stand-in aligned output pointer
             if ((st = make_render_args(V, L, &r->cam, r->w, r->h, &r->opts, reinterpret_cast<float*>(256), nullptr, &a))) { delete q; return st; }
             if (r->coarse_lod >= 0) {
-                Level* C;
+                Level* C = nullptr;
                 if ((st = get_level(V, r->coarse_lod, &C))) { delete q; return st; }
                 if (!C->bricks) { delete q; return fail(RAYPC_ERR_INVALID_ARG, "coarse level has no bricks"); }
             }
@@ -557,8 +557,9 @@ raypc_status raypc_serve_submit(raypc_server* S, const raypc_request* r, uint64_
     q->r.edges = nullptr;
     q->mem_bytes = output_bytes(q->r);
     if (q->mem_bytes > S->cfg.output_budget_bytes) {
+        const size_t bytes = q->mem_bytes;
         delete q;
-        return fail(RAYPC_ERR_OOM, "request outputs (%zu bytes) exceed the server's output budget", q->mem_bytes);
+        return fail(RAYPC_ERR_OOM, "request outputs (%zu bytes) exceed the server's output budget", bytes);
     }
     {
         std::lock_guard<std::mutex> lk(S->mu);

@@ -129,8 +129,8 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
     raypc_status st = RAYPC_OK;
     for (int i = 0; i < nviews && st == RAYPC_OK; ++i) {
         const raypc_view& q = views[i];
-        Volume* V;
-        Level* L;
+        Volume* V = nullptr;
+        Level* L = nullptr;
         if ((st = get_volume(ctx, q.vol, &V)) || (st = get_level(V, q.lod, &L))) break;
         if (dtype < 0) { dtype = V->dtype; n0 = L->n; }
         if (V->dtype != dtype) { st = fail(RAYPC_ERR_INVALID_ARG, "view %d: all views need one storage dtype", i); break; }
