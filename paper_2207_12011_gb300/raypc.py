@@ -176,6 +176,34 @@ def _fptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _need(t, shape, dtype, name: str):
+    """A caller-provided tensor must be exactly what the C call reads or writes: a contiguous
+    CUDA tensor of this shape and dtype (the library sees only a pointer)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if tuple(t.shape) != tuple(int(x) for x in shape) or t.dtype != dtype or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    return t
+
+
+def _outputs(w, h, out, counts, stats, dev, depth=False):
+    """The output tensors of a render: allocated when not given, checked when given."""
+    out = torch.empty((h, w, 4), dtype=torch.float32, device=dev) if out is None else \
+        _need(out, (h, w, 4), torch.float32, "out")
+    if counts is True:
+        counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
+    elif isinstance(counts, torch.Tensor):
+        _need(counts, (h, w, 2), torch.int32, "counts")
+    if stats is not None:
+        _need(stats, (NSTATS,), torch.int64, "stats")
+    if depth is True:
+        depth = torch.empty((h, w), dtype=torch.float32, device=dev)
+    elif isinstance(depth, torch.Tensor):
+        _need(depth, (h, w), torch.float32, "depth")
+    return out, counts, depth
+
+
 def kernel_launches() -> int:
     """Kernels libraypc has launched in this process."""
     out = ctypes.c_ulonglong()
@@ -336,6 +364,8 @@ class Volume:
             raise ValueError("points must be a float32 [npts, 3] tensor")
         if out is None:
             out = torch.empty(pts.shape[0], dtype=torch.uint8, device=pts.device)
+        else:
+            _need(out, (pts.shape[0],), torch.uint8, "out")
         _call("raypc_filter_points", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(pts.data_ptr()),
               int(pts.shape[0]), ctypes.c_void_p(out.data_ptr()), _stream(stream))
         return out
@@ -356,12 +386,7 @@ class Volume:
         variant: AUTO or 1..3 (tile shape). Neither changes any pixel.
         """
         dev = torch.device("cuda", self.ctx.device)
-        if out is None:
-            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
-        if counts is True:
-            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
-        if depth is True:
-            depth = torch.empty((h, w), dtype=torch.float32, device=dev)
+        out, counts, depth = _outputs(int(w), int(h), out, counts, stats, dev, depth)
         o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip,
                   depth if isinstance(depth, torch.Tensor) else None)
         c = camera_from(cam)
@@ -380,10 +405,9 @@ class Volume:
         float32 device tensor or None, holds the running mean of passes 0..pass_ and is
         updated in place. Returns (this pass's image, counts or None)."""
         dev = torch.device("cuda", self.ctx.device)
-        if out is None:
-            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
-        if counts is True:
-            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
+        out, counts, _ = _outputs(int(w), int(h), out, counts, stats, dev)
+        if accum is not None:
+            _need(accum, (h, w, 4), torch.float32, "accum")
         o = _opts(step, ert, skip, bg, counts if isinstance(counts, torch.Tensor) else None, variant, tf_skip)
         c = camera_from(cam)
         sp = ctypes.c_void_p(stats.data_ptr()) if stats is not None else None
@@ -400,6 +424,8 @@ class Volume:
         if out is None:
             out = torch.empty((naxes - 1, bins, bins), dtype=torch.int32,
                               device=torch.device("cuda", self.ctx.device))
+        else:
+            _need(out, (naxes - 1, bins, bins), torch.int32, "out")
         _call("raypc_pc_histogram", self.ctx.handle, self.id, int(lod), _fptr(order), naxes, bins,
               _fptr(e), int(bool(use_brush)), ctypes.c_void_p(out.data_ptr()), _stream(stream))
         return out
@@ -510,13 +536,8 @@ def _view_array(ctx, views):
     for i, q in enumerate(views):
         vol = q["vol"]
         w, h = int(q["w"]), int(q["h"])
-        out = q.get("out")
-        if out is None:
-            out = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
-        counts = q.get("counts")
-        if counts is True:
-            counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
         stats = q.get("stats")
+        out, counts, _ = _outputs(w, h, q.get("out"), q.get("counts"), stats, dev)
         v = arr[i]
         v.vol = vol.id
         v.lod = int(q.get("lod", 0))
@@ -545,8 +566,9 @@ def warp_image(ctx: Context, cam_from, cam_to, src: torch.Tensor, depth: torch.T
     Returns the warped image, and the chosen source pixel per target pixel (int32, -1: none)
     when with_src."""
     h, w = int(src.shape[0]), int(src.shape[1])
-    if out is None:
-        out = torch.empty_like(src)
+    _need(src, (h, w, 4), torch.float32, "src")
+    _need(depth, (h, w), torch.float32, "depth")
+    out = torch.empty_like(src) if out is None else _need(out, (h, w, 4), torch.float32, "out")
     idx = torch.empty((h, w), dtype=torch.int32, device=src.device) if with_src else None
     cf, ct = camera_from(cam_from), camera_from(cam_to)
     b = np.ascontiguousarray(np.asarray(bg, dtype=np.float32).reshape(4))

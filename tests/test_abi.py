@@ -6,7 +6,9 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
+import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
@@ -95,3 +97,26 @@ def test_struct_layouts_match_the_binding(tmp_path):
             rp.RenderOpts.depth_dev.offset, rp.View.pos_lo.offset, rp.View.pos_mask.offset,
             rp.Request.pos_lo.offset, rp.Request.pos_mask.offset]
     assert got == want
+
+
+def test_binding_checks_caller_tensors():
+    """Tensors handed to the library as raw pointers are checked first: shape, dtype,
+    contiguity and device (a wrong one would be read or written out of bounds)."""
+    import paper_2207_12011_gb300.raypc as rp
+    with pytest.raises(ValueError, match="CUDA"):
+        rp._need(torch.zeros((4, 5, 4)), (4, 5, 4), torch.float32, "out")        # host tensor
+    with pytest.raises(TypeError):
+        rp._need(np.zeros((4, 5, 4), np.float32), (4, 5, 4), torch.float32, "out")
+    meta = torch.empty((4, 5, 4), device="meta")
+    for bad in (torch.empty((5, 4, 4), device="meta"), torch.empty((4, 5, 4), dtype=torch.float64, device="meta"),
+                torch.empty((4, 4, 5), device="meta").transpose(1, 2)):
+        with pytest.raises(ValueError):
+            rp._need(bad, (4, 5, 4), torch.float32, "out")
+    # allocation path: nothing given, everything made with the right shapes
+    out, counts, depth = rp._outputs(5, 4, None, True, None, "cpu", depth=True)
+    assert out.shape == (4, 5, 4) and counts.shape == (4, 5, 2) and depth.shape == (4, 5)
+    assert counts.dtype == torch.int32 and depth.dtype == torch.float32
+    out, counts, depth = rp._outputs(5, 4, None, False, None, "cpu")
+    assert counts is False and depth is False
+    with pytest.raises(ValueError):
+        rp._outputs(5, 4, None, None, torch.zeros(7, dtype=torch.int64), "cpu")  # stats of the wrong size
