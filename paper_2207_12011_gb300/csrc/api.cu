@@ -14,6 +14,7 @@
 #include <mutex>
 #include <string>
 
+#include "host_math.h"
 #include "runtime.h"
 
 using namespace raypc;
@@ -196,36 +197,6 @@ raypc_status get_level(Volume* V, int lod, Level** out) {
     if (lod < 0 || lod >= V->nlev) return fail(RAYPC_ERR_NOT_FOUND, "level %d not built (have %d)", lod, V->nlev);
     *out = &V->lv[lod];
     return RAYPC_OK;
-}
-
-// Smallest float f >= 0 with sqrt_rn(f) >= lo, or the largest with sqrt_rn(f) <= hi
-// (upper = true): sqrt_rn is monotone, so a bisection over the ordered bit patterns of
-// the non-negative floats finds the exact threshold. Host sqrtf is correctly rounded,
-// like the kernels' __fsqrt_rn.
-static float radius_threshold2(float r, bool upper) {
-    uint32_t l = 0u, h = 0x7f800000u;                   // +0 .. +inf
-    // predicate true from some bit pattern on: sqrt(f) >= r (lower) or sqrt(f) > r (upper)
-    auto pred = [&](uint32_t bits) {
-        float f;
-        memcpy(&f, &bits, 4);
-        const float s = sqrtf(f);
-        return upper ? (s > r) : (s >= r);
-    };
-    if (!pred(h)) return INFINITY;                      // lower: nothing reaches r; upper: r = +inf
-    while (l < h) {
-        const uint32_t m = l + (h - l) / 2;
-        if (pred(m)) h = m; else l = m + 1;
-    }
-    if (upper) {                                        // last pattern with sqrt <= r
-        if (l == 0u) return -1.0f;                      // even sqrt(0) = 0 > r: nothing passes
-        const uint32_t b = l - 1u;
-        float f;
-        memcpy(&f, &b, 4);
-        return f;
-    }
-    float f;
-    memcpy(&f, &l, 4);
-    return f;
 }
 
 void finish_position_brush(RenderArgs& a) {
@@ -760,26 +731,6 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     cudaFreeAsync(dedges, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
     return RAYPC_OK;
-}
-
-// Number of cells whose centre offsets d = 2i + 1 - n satisfy s_in <= dx^2 + dy^2 + dz^2 <= s_out.
-static unsigned long long count_in_shell(int n, int64_t s_in, int64_t s_out) {
-    // cells of one row (fixed y, z) with dx^2 <= a: |2x + 1 - n| <= floor(sqrt(a))
-    auto upto = [n](int64_t a) -> int64_t {
-        if (a < 0) return 0;
-        int64_t m = (int64_t)sqrt((double)a);
-        while (m * m > a) --m;
-        while ((m + 1) * (m + 1) <= a) ++m;
-        const int64_t xa = std::max<int64_t>(0, (n - 1 - m + 1) / 2), xb = std::min<int64_t>(n - 1, (n - 1 + m) / 2);
-        return xb >= xa ? xb - xa + 1 : 0;
-    };
-    unsigned long long total = 0;
-    for (int z = 0; z < n; ++z)
-        for (int y = 0; y < n; ++y) {
-            const int64_t dy = 2 * y + 1 - n, dz = 2 * z + 1 - n, syz = dy * dy + dz * dz;
-            total += (unsigned long long)(upto(s_out - syz) - upto(s_in - 1 - syz));
-        }
-    return total;
 }
 
 raypc_status raypc_pc_subsample(raypc_ctx* ctx, int vol, int lod, uint32_t seed, long long k,
