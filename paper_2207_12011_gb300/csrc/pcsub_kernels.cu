@@ -117,7 +117,9 @@ __global__ void __launch_bounds__(1024) k_sub_pick(SubState* S) {
     if (S->done) return;
     constexpr int kPer = kDigits / 1024;
     const int t = threadIdx.x;
+    // the state is read before the first barrier: the owner thread rewrites it after the last one
     const int width = min(kDigitBits, 64 - S->nbits);
+    const unsigned long long need = S->need;
     unsigned long long loc[kPer], tot = 0ull;
 #pragma unroll
     for (int i = 0; i < kPer; ++i) { loc[i] = S->hist[t * kPer + i]; tot += loc[i]; }
@@ -129,7 +131,6 @@ __global__ void __launch_bounds__(1024) k_sub_pick(SubState* S) {
         s_sum[t] += add;
         __syncthreads();
     }
-    const unsigned long long need = S->need;
     unsigned long long before = s_sum[t] - tot;
     // exactly one thread owns the digit with before < need <= before + count
     if (before < need && need <= s_sum[t]) {
