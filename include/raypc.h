@@ -551,19 +551,23 @@ raypc_status raypc_filter_points(raypc_ctx *ctx, int vol, int lod, const float *
  * of the device. The paper has no counterpart; this is a deployment variant.
  * It needs no context and no resident volume: cells_dev is the caller's field
  * in the planar layout of raypc_load_volume (nvars planes of n^3 values, x
- * fastest) and dtype is its element type; lo/hi/active_mask/use_brush, the
- * shell r_in/r_out and every other argument mean what they mean above. It
- * runs on the calling thread's current device and calls no cudaMalloc,
- * cudaFree or other allocating routine: the bin edges go into a fixed
- * 32.8 KB device array (RAYPC_MAX_VARS x 1025 floats) compiled into the
- * library, which every GPU that loads the library holds until exit. Larger
- * edge tables (naxes > 8 or bins > 1024) are rejected with
- * RAYPC_ERR_INVALID_ARG. The first call on each device looks up that array's
- * device address (cudaGetSymbolAddress), so make it before any stream
- * capture. All calls share the array and it keeps the last call's edges;
- * every call rewrites the part it reads and zeroes out_counts_dev itself.
- * Calls whose work overlaps on the GPU (different streams, no ordering)
- * race on the array and must be serialised by the caller. */
+ * fastest, 2 <= n <= 4096), aligned to its element size, and dtype is its
+ * element type; out_counts_dev is 4-byte aligned. Axis ids name stored
+ * variables 0..nvars-1 only: position axes (RAYPC_AXIS_POS) and the position
+ * brush are not accepted here. lo/hi/active_mask/use_brush, the shell
+ * r_in/r_out and the remaining arguments mean what they mean above. It runs
+ * on the calling thread's current device and calls no cudaMalloc, cudaFree or
+ * other allocating routine: the bin edges go into a fixed 32.8 KB device
+ * array (RAYPC_MAX_VARS x 1025 floats) compiled into the library, which every
+ * GPU that loads the library holds until exit. Larger edge tables (naxes > 8
+ * or bins > 1024) are rejected with RAYPC_ERR_INVALID_ARG. The first call in
+ * each context of a device (the first call on the device, and the first after
+ * a device reset or a switch to another context) looks up that array's device
+ * address with cudaGetSymbolAddress, so make it before any stream capture.
+ * All calls share the array and it keeps the last call's edges; every call
+ * rewrites the part it reads and zeroes out_counts_dev itself. Calls whose
+ * work overlaps on the GPU (different streams, no ordering) race on the array
+ * and must be serialised by the caller. */
 raypc_status raypc_pc_histogram_noalloc(const void *cells_dev, int dtype, int n, int nvars,
                                         float r_in, float r_out, const float *lo, const float *hi,
                                         uint32_t active_mask, int use_brush, const int *axis_order,

@@ -12,7 +12,11 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <stdint.h>
+
 #include <mutex>
+
+#include <cuda.h>
 
 #include "runtime.h"
 
@@ -28,7 +32,23 @@ static __device__ __align__(256) float g_edge_scratch[kMaxEdges];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-float* g_edge_ptr[kMaxDevices] = {nullptr};
+
+// The array's device address belongs to the context the library's module was
+// loaded into, so it is cached per device together with that context's unique
+// id (cuCtxGetId; ids are never reused within a process). A device reset or a
+// new context therefore makes the next call look the address up again
+// instead of passing a stale one to the kernel.
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    float* ptr = nullptr;
+};
+ScratchAddr g_edge_addr[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_driver_fns_tried = false;
 
 // Reports through raypc_last_error (the message store lives in api.cu).
 raypc_status nfail(raypc_status code, const char* fmt, ...) {
@@ -41,19 +61,49 @@ raypc_status nfail(raypc_status code, const char* fmt, ...) {
     return code;
 }
 
-// Device address of the scratch array on the current device. The host-side
-// name g_edge_scratch is only a stand-in, never a device address, so it is
-// looked up once per device with that device current.
+// Unique id of the calling thread's current context, or 0 when none is current
+// or the driver entry points are unavailable (then nothing is cached).
+unsigned long long current_ctx_id() {
+    if (!g_driver_fns_tried) {
+        g_driver_fns_tried = true;
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess) {
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f1);
+        }
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current context of device dev.
+// The host-side name g_edge_scratch is only a stand-in, never a device
+// address, so it is looked up (cudaGetSymbolAddress, with dev current) once
+// per device and context.
 raypc_status edge_scratch(int dev, float** out) {
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_edge_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_edge_scratch);
-        if (e != cudaSuccess)
-            return nfail(RAYPC_ERR_CUDA, "cudaGetSymbolAddress of the edge scratch: %s", cudaGetErrorString(e));
-        g_edge_ptr[dev] = static_cast<float*>(p);
+    ScratchAddr& a = g_edge_addr[dev];
+    const unsigned long long before = current_ctx_id();
+    if (before != 0 && a.ptr && a.ctx_id == before) {
+        *out = a.ptr;
+        return RAYPC_OK;
     }
-    *out = g_edge_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_edge_scratch);
+    if (e != cudaSuccess)
+        return nfail(RAYPC_ERR_CUDA, "cudaGetSymbolAddress of the edge scratch: %s", cudaGetErrorString(e));
+    // the lookup may have created the context: key the address on the one now current
+    a.ctx_id = current_ctx_id();
+    a.ptr = a.ctx_id ? static_cast<float*>(p) : nullptr;
+    *out = static_cast<float*>(p);
     return RAYPC_OK;
 }
 
@@ -69,7 +119,11 @@ raypc_status raypc_pc_histogram_noalloc(const void* cells_dev, int dtype, int n,
     if (!cells_dev || !axis_order || !edges || !out_counts_dev)
         return nfail(RAYPC_ERR_INVALID_ARG, "NULL argument");
     if (dtype != RAYPC_F32 && dtype != RAYPC_F16) return nfail(RAYPC_ERR_INVALID_ARG, "dtype must be RAYPC_F32 or RAYPC_F16");
-    if (n < 2 || n > 8192) return nfail(RAYPC_ERR_INVALID_ARG, "grid edge %d not in 2..8192", n);
+    if (n < 2 || n > kMaxRowsEdge) return nfail(RAYPC_ERR_INVALID_ARG, "grid edge %d not in 2..%d", n, kMaxRowsEdge);
+    if (reinterpret_cast<uintptr_t>(cells_dev) % (dtype == RAYPC_F32 ? 4 : 2) != 0)
+        return nfail(RAYPC_ERR_INVALID_ARG, "cells_dev is not aligned to its element size");
+    if (reinterpret_cast<uintptr_t>(out_counts_dev) % 4 != 0)
+        return nfail(RAYPC_ERR_INVALID_ARG, "out_counts_dev is not 4-byte aligned");
     if (nvars < 1 || nvars > RAYPC_MAX_VARS) return nfail(RAYPC_ERR_INVALID_ARG, "nvars %d not in 1..%d", nvars, RAYPC_MAX_VARS);
     if (!(r_in >= 0.f) || !(r_out > r_in) || !isfinite(r_out)) return nfail(RAYPC_ERR_INVALID_ARG, "need 0 <= r_in < r_out");
     if (naxes < 2 || naxes > RAYPC_MAX_VARS) return nfail(RAYPC_ERR_INVALID_ARG, "naxes %d not in 2..%d", naxes, RAYPC_MAX_VARS);
@@ -78,7 +132,9 @@ raypc_status raypc_pc_histogram_noalloc(const void* cells_dev, int dtype, int n,
     if ((size_t)naxes * (bins + 1) > (size_t)kMaxEdges)
         return nfail(RAYPC_ERR_INVALID_ARG, "edge table of %d x %d exceeds the %d-float scratch", naxes, bins + 1, kMaxEdges);
     for (int a = 0; a < naxes; ++a) {
-        if (axis_order[a] < 0 || axis_order[a] >= nvars) return nfail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d", a, axis_order[a]);
+        if (axis_order[a] < 0 || axis_order[a] >= nvars)
+            return nfail(RAYPC_ERR_INVALID_ARG, "axis %d names variable %d (stored variables 0..%d only; no position axes here)",
+                         a, axis_order[a], nvars - 1);
         for (int k = 0; k <= bins; ++k) {
             float e = edges[(size_t)a * (bins + 1) + k];
             if (isnan(e)) return nfail(RAYPC_ERR_INVALID_ARG, "NaN edge (axis %d, edge %d)", a, k);

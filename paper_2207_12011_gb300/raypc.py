@@ -176,31 +176,34 @@ def _fptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _need(t, shape, dtype, name: str):
+def _need(t, shape, dtype, name: str, device=None):
     """A caller-provided tensor must be exactly what the C call reads or writes: a contiguous
-    CUDA tensor of this shape and dtype (the library sees only a pointer)."""
+    CUDA tensor of this shape and dtype (the library sees only a pointer), on `device` when
+    one is given."""
     if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a torch tensor")
     if tuple(t.shape) != tuple(int(x) for x in shape) or t.dtype != dtype or not t.is_contiguous() or not t.is_cuda:
         raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}, "
                          f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+    if device is not None and t.device != torch.device(device):
+        raise ValueError(f"{name} is on {t.device}, the call runs on {torch.device(device)}")
     return t
 
 
 def _outputs(w, h, out, counts, stats, dev, depth=False):
     """The output tensors of a render: allocated when not given, checked when given."""
     out = torch.empty((h, w, 4), dtype=torch.float32, device=dev) if out is None else \
-        _need(out, (h, w, 4), torch.float32, "out")
+        _need(out, (h, w, 4), torch.float32, "out", dev)
     if counts is True:
         counts = torch.empty((h, w, 2), dtype=torch.int32, device=dev)
     elif isinstance(counts, torch.Tensor):
-        _need(counts, (h, w, 2), torch.int32, "counts")
+        _need(counts, (h, w, 2), torch.int32, "counts", dev)
     if stats is not None:
-        _need(stats, (NSTATS,), torch.int64, "stats")
+        _need(stats, (NSTATS,), torch.int64, "stats", dev)
     if depth is True:
         depth = torch.empty((h, w), dtype=torch.float32, device=dev)
     elif isinstance(depth, torch.Tensor):
-        _need(depth, (h, w), torch.float32, "depth")
+        _need(depth, (h, w), torch.float32, "depth", dev)
     return out, counts, depth
 
 
@@ -362,10 +365,11 @@ class Volume:
         pts = points.contiguous()
         if pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != 3:
             raise ValueError("points must be a float32 [npts, 3] tensor")
+        _need(pts, tuple(pts.shape), torch.float32, "points", torch.device("cuda", self.ctx.device))
         if out is None:
             out = torch.empty(pts.shape[0], dtype=torch.uint8, device=pts.device)
         else:
-            _need(out, (pts.shape[0],), torch.uint8, "out")
+            _need(out, (pts.shape[0],), torch.uint8, "out", pts.device)
         _call("raypc_filter_points", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(pts.data_ptr()),
               int(pts.shape[0]), ctypes.c_void_p(out.data_ptr()), _stream(stream))
         return out
@@ -425,7 +429,7 @@ class Volume:
             out = torch.empty((naxes - 1, bins, bins), dtype=torch.int32,
                               device=torch.device("cuda", self.ctx.device))
         else:
-            _need(out, (naxes - 1, bins, bins), torch.int32, "out")
+            _need(out, (naxes - 1, bins, bins), torch.int32, "out", torch.device("cuda", self.ctx.device))
         _call("raypc_pc_histogram", self.ctx.handle, self.id, int(lod), _fptr(order), naxes, bins,
               _fptr(e), int(bool(use_brush)), ctypes.c_void_p(out.data_ptr()), _stream(stream))
         return out
@@ -487,28 +491,60 @@ class Volume:
         return mn, mx, act
 
 
+def _noalloc_args(cells, axis_order, edges, lo, hi, out, cuda: bool = True):
+    """Checked arguments of raypc_pc_histogram_noalloc: every pointer the C call receives must
+    cover what the kernel reads or writes. cuda=False skips only the device checks (CPU tests
+    use meta tensors)."""
+    if not isinstance(cells, torch.Tensor) or cells.dim() != 4 or not cells.is_contiguous() or \
+            (cuda and not cells.is_cuda):
+        raise ValueError("cells must be a contiguous (nvars, n, n, n) CUDA tensor")
+    if not (cells.shape[1] == cells.shape[2] == cells.shape[3]):
+        raise ValueError(f"cells must be (nvars, n, n, n), got {tuple(cells.shape)}")
+    if cells.dtype not in (torch.float32, torch.float16):
+        raise ValueError(f"cells must be float32 or float16, got {cells.dtype}")
+    dt = RAYPC_F32 if cells.dtype == torch.float32 else RAYPC_F16
+    nv, n = cells.shape[0], cells.shape[-1]
+    order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32)).reshape(-1)
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
+    if e.ndim != 2 or e.shape[1] < 3:
+        raise ValueError(f"edges must be (naxes, bins + 1) with bins >= 2, got shape {e.shape}")
+    naxes, bins = e.shape[0], e.shape[1] - 1
+    if order.shape[0] != naxes:
+        raise ValueError(f"axis_order has {order.shape[0]} entries, the edge table {naxes} rows")
+    lo_a = np.asarray(lo if lo is not None else np.full(nv, -np.inf), dtype=np.float32).reshape(-1)
+    hi_a = np.asarray(hi if hi is not None else np.full(nv, np.inf), dtype=np.float32).reshape(-1)
+    if lo_a.shape[0] < nv or hi_a.shape[0] < nv:
+        raise ValueError(f"lo and hi need {nv} entries")
+    lo_a, hi_a = np.ascontiguousarray(lo_a[:nv]), np.ascontiguousarray(hi_a[:nv])
+    if out is not None:
+        shape = (naxes - 1, bins, bins)
+        if not isinstance(out, torch.Tensor):
+            raise TypeError("out must be a torch tensor")
+        if tuple(out.shape) != shape or out.dtype != torch.int32 or not out.is_contiguous():
+            raise ValueError(f"out must be a contiguous int32 tensor of shape {shape}, "
+                             f"got {out.dtype} {tuple(out.shape)}")
+        if cuda and out.device != cells.device:
+            raise ValueError(f"out is on {out.device}, cells on {cells.device}")
+    return dt, nv, n, order, e, lo_a, hi_a, naxes, bins
+
+
 def pc_histogram_noalloc(cells: torch.Tensor, axis_order, edges, lo=None, hi=None, active_mask: int = 0,
                          use_brush: bool = False, r_in: float = 0.547, r_out: float = 1.0,
                          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """raypc_pc_histogram_noalloc on a caller-owned planar (nvars, n, n, n) device field.
 
     The library allocates nothing for this call (the output is the caller's too:
-    pass `out` to keep the whole call allocation-free on the torch side).
+    pass `out` to keep the whole call allocation-free on the torch side). The call
+    runs on the device that holds `cells`.
     """
-    if not cells.is_cuda or cells.dim() != 4 or not cells.is_contiguous():
-        raise ValueError("cells must be a contiguous (nvars, n, n, n) CUDA tensor")
-    dt = {torch.float32: RAYPC_F32, torch.float16: RAYPC_F16}[cells.dtype]
-    nv, n = cells.shape[0], cells.shape[-1]
-    order = np.ascontiguousarray(np.asarray(axis_order, dtype=np.int32))
-    e = np.ascontiguousarray(np.asarray(edges, dtype=np.float32))
-    naxes, bins = e.shape[0], e.shape[1] - 1
-    lo_a = np.ascontiguousarray(np.asarray(lo if lo is not None else np.full(nv, -np.inf), dtype=np.float32)[:nv])
-    hi_a = np.ascontiguousarray(np.asarray(hi if hi is not None else np.full(nv, np.inf), dtype=np.float32)[:nv])
+    dt, nv, n, order, e, lo_a, hi_a, naxes, bins = _noalloc_args(cells, axis_order, edges, lo, hi, out)
     if out is None:
         out = torch.empty((naxes - 1, bins, bins), dtype=torch.int32, device=cells.device)
-    _call("raypc_pc_histogram_noalloc", ctypes.c_void_p(cells.data_ptr()), dt, n, nv, float(r_in),
-          float(r_out), _fptr(lo_a), _fptr(hi_a), int(active_mask) & 0xFFFFFFFF, int(bool(use_brush)),
-          _fptr(order), naxes, bins, _fptr(e), ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    with torch.cuda.device(cells.device):
+        _call("raypc_pc_histogram_noalloc", ctypes.c_void_p(cells.data_ptr()), dt, n, nv, float(r_in),
+              float(r_out), _fptr(lo_a), _fptr(hi_a), int(active_mask) & 0xFFFFFFFF, int(bool(use_brush)),
+              _fptr(order), naxes, bins, _fptr(e), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream if stream is not None else torch.cuda.current_stream(cells.device)))
     return out
 
 
@@ -566,9 +602,10 @@ def warp_image(ctx: Context, cam_from, cam_to, src: torch.Tensor, depth: torch.T
     Returns the warped image, and the chosen source pixel per target pixel (int32, -1: none)
     when with_src."""
     h, w = int(src.shape[0]), int(src.shape[1])
-    _need(src, (h, w, 4), torch.float32, "src")
-    _need(depth, (h, w), torch.float32, "depth")
-    out = torch.empty_like(src) if out is None else _need(out, (h, w, 4), torch.float32, "out")
+    dev = torch.device("cuda", ctx.device)
+    _need(src, (h, w, 4), torch.float32, "src", dev)
+    _need(depth, (h, w), torch.float32, "depth", dev)
+    out = torch.empty_like(src) if out is None else _need(out, (h, w, 4), torch.float32, "out", dev)
     idx = torch.empty((h, w), dtype=torch.int32, device=src.device) if with_src else None
     cf, ct = camera_from(cam_from), camera_from(cam_to)
     b = np.ascontiguousarray(np.asarray(bg, dtype=np.float32).reshape(4))

@@ -120,3 +120,35 @@ def test_binding_checks_caller_tensors():
     assert counts is False and depth is False
     with pytest.raises(ValueError):
         rp._outputs(5, 4, None, None, torch.zeros(7, dtype=torch.int64), "cpu")  # stats of the wrong size
+
+
+def test_noalloc_binding_checks_its_arguments():
+    """The allocation-free histogram's binding rejects, before any GPU work, every argument
+    that would make the kernel read or write past a buffer: a non-cubic field, an axis list
+    shorter than the edge table, a flat edge table, short brush bounds, and a wrong output."""
+    import paper_2207_12011_gb300.raypc as rp
+    cells = torch.empty((6, 16, 16, 16), device="meta")
+    edges = np.tile(np.linspace(0, 1, 65, dtype=np.float32), (3, 1))
+    ok = rp._noalloc_args(cells, (0, 1, 2), edges, None, None, None, cuda=False)
+    assert ok[-2:] == (3, 64) and ok[1:3] == (6, 16)
+    with pytest.raises(ValueError, match="nvars, n, n, n"):
+        rp._noalloc_args(torch.empty((6, 16, 16, 8), device="meta"), (0, 1, 2), edges, None, None, None, cuda=False)
+    with pytest.raises(ValueError, match="axis_order"):
+        rp._noalloc_args(cells, (0, 1), edges, None, None, None, cuda=False)
+    with pytest.raises(ValueError, match="edges"):
+        rp._noalloc_args(cells, (0, 1, 2), edges.reshape(-1), None, None, None, cuda=False)
+    with pytest.raises(ValueError, match="lo and hi"):
+        rp._noalloc_args(cells, (0, 1, 2), edges, np.zeros(3), np.ones(3), None, cuda=False)
+    with pytest.raises(ValueError, match="float32 or float16"):
+        rp._noalloc_args(torch.empty((6, 16, 16, 16), dtype=torch.float64, device="meta"), (0, 1, 2), edges,
+                         None, None, None, cuda=False)
+    for bad in (torch.empty((2, 64, 32), dtype=torch.int32, device="meta"),
+                torch.empty((2, 64, 64), dtype=torch.float32, device="meta"),
+                torch.empty((2, 64, 64), dtype=torch.int32, device="meta").transpose(1, 2)[:, :, :64]):
+        with pytest.raises(ValueError, match="out"):
+            rp._noalloc_args(cells, (0, 1, 2), edges, None, None, bad, cuda=False)
+    with pytest.raises(TypeError):
+        rp._noalloc_args(cells, (0, 1, 2), edges, None, None, np.zeros((2, 64, 64), np.int32), cuda=False)
+    # the real entry point insists on device tensors
+    with pytest.raises(ValueError, match="CUDA"):
+        rp.pc_histogram_noalloc(torch.zeros((6, 16, 16, 16)), (0, 1, 2), edges)

@@ -55,3 +55,6 @@ def test_noalloc_histogram_matches_regular_entry_point_twice():
     big = np.tile(np.linspace(0, 1, 2050, dtype=np.float32), (2, 1))
     with pytest.raises(rp.RaypcError, match="bins"):
         rp.pc_histogram_noalloc(cells, (0, 1), big)
+    # position axes are not accepted by this entry point
+    with pytest.raises(rp.RaypcError, match="position axes"):
+        rp.pc_histogram_noalloc(cells, (0, rp.AXIS_POS(rp.POS_R)), big[:, :65])
