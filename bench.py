@@ -565,16 +565,22 @@ def run_ours(args):
 # ---------------------------------------------------------------------------
 # batched views (64 views of a 512^3 volume, one persistent launch in a CUDA graph)
 # ---------------------------------------------------------------------------
-def run_batched(rp, dev, args, seed):
-    """FP16 batched path (one graph replay per batch) against per-frame plain FP32 launches."""
-    n, k = args.batch_n, args.batch_views
+def batched_workload(n, k, seed, dev):
+    """The batched workload: an n^3 x 6 volume, its FP16 transfer function on T_anom, k random
+    orbit views with sizes in {256..2048}^2, and one jittered 6-variable brush per view."""
     src = synth.make_shell_volume(n, seed=seed, device=dev)
     stored = synth.to_storage(src, "f16").float()
     tf = synth.make_tf(stored, "T_anom")
     views = synth.random_views(seed + 1, k)
     brushes = [synth.brush_from_quantiles(stored, synth.jittered_spec("c3", seed + 100 + i, 0.1))
                for i in range(k)]
-    del stored
+    return src, tf, views, brushes
+
+
+def run_batched(rp, dev, args, seed):
+    """FP16 batched path (one graph replay per batch) against per-frame plain FP32 launches."""
+    n, k = args.batch_n, args.batch_views
+    src, tf, views, brushes = batched_workload(n, k, seed, dev)
     ctx = rp.Context(dev.index)
     v16 = ctx.load_volume(src, store="f16")
     v16.build_bricks(n_lod=2)
@@ -650,31 +656,27 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
 
 
-def run_served(rp, dev, args, seed):
-    n, nreq = args.serve_n, args.serve_requests
-    rng = np.random.default_rng(seed)
-    ctx = rp.Context(dev.index)
-    vols16, vols32, tables, edges_t, tfs = [], [], [], [], []
-    order = (0, 1, 2, 3, 4, 5)
-    for t in range(3):                                   # three time steps
-        src = synth.make_shell_volume(n, seed=seed + t, device=dev)
-        stored = synth.to_storage(src, "f16").float()
-        tables.append(synth.QuantileTable(stored))
-        edges_t.append(synth.make_edges(stored, order, bins=256))
-        tf = synth.make_tf(stored, "T_anom")
-        del stored
-        for store, lst in (("f16", vols16), ("f32", vols32)):
-            v = ctx.load_volume(src, store=store)
-            v.build_bricks(n_lod=1)
-            v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
-            lst.append(v)
-        del src
-    torch.cuda.empty_cache()
-    # the request stream
+SERVED_ORDER = (0, 1, 2, 3, 4, 5)
+
+
+def served_time_step(n, seed, t, dev):
+    """Time step t of the served workload: the FP32 source, its FP16-stored quantile table,
+    histogram edges and transfer function."""
+    src = synth.make_shell_volume(n, seed=seed + t, device=dev)
+    stored = synth.to_storage(src, "f16").float()
+    table = synth.QuantileTable(stored)
+    edges = synth.make_edges(stored, SERVED_ORDER, bins=256)
+    tf = synth.make_tf(stored, "T_anom")
+    return src, table, edges, tf
+
+
+def served_requests(nreq, seed, tables, rng):
+    """The request stream: 80 % renders (random orbit camera, size in {256..2048}^2) and 20 %
+    histograms, each on a random time step with its own edited brush."""
     reqs = []
     sizes = (256, 512, 1024, 2048)
     for i in range(nreq):
-        t = int(rng.integers(3))
+        t = int(rng.integers(len(tables)))
         b = tables[t].brush(synth.edited_spec("c3", seed + 31 * i, 0.1, 0.05))
         if rng.uniform() < 0.8:
             cam = synth.orbit_camera(rng.uniform(0, 360), rng.uniform(-60, 60), rng.uniform(2.6, 3.4))
@@ -682,6 +684,27 @@ def run_served(rp, dev, args, seed):
             reqs.append(("render", t, b, cam, sz))
         else:
             reqs.append(("hist", t, b, None, None))
+    return reqs
+
+
+def run_served(rp, dev, args, seed):
+    n, nreq = args.serve_n, args.serve_requests
+    rng = np.random.default_rng(seed)
+    ctx = rp.Context(dev.index)
+    vols16, vols32, tables, edges_t = [], [], [], []
+    order = SERVED_ORDER
+    for t in range(3):                                   # three time steps
+        src, table, edges, tf = served_time_step(n, seed, t, dev)
+        tables.append(table)
+        edges_t.append(edges)
+        for store, lst in (("f16", vols16), ("f32", vols32)):
+            v = ctx.load_volume(src, store=store)
+            v.build_bricks(n_lod=1)
+            v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+            lst.append(v)
+        del src
+    torch.cuda.empty_cache()
+    reqs = served_requests(nreq, seed, tables, rng)
     outs = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
     H = torch.empty((len(order) - 1, 256, 256), dtype=torch.int32, device=dev)
     pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)

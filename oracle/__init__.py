@@ -76,6 +76,10 @@ def _load():
             lib.oracle_render_pass.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
                                                P, P, u32, P, i32, f32, f32, P, i32, P,
                                                ctypes.c_int64, P, P, i32, u32, u32, P, P, u32, i32, P]
+            lib.oracle_render_exact.argtypes = [P, i32, i32, f32, f32, P, i32, i32, f32,
+                                                P, P, u32, P, i32, f32, f32, P, i32, P,
+                                                ctypes.c_int64, P, P, i32]
+            lib.oracle_render_exact.restype = i32
             lib.oracle_warp.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
             lib.oracle_tf_visibility.argtypes = [P, i32, i32, i32, P, f32, f32, P]
             lib.oracle_render_pass.restype = i32
@@ -298,6 +302,38 @@ def render(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_
     if pixels is None:
         out, cnt, depth = out.reshape(h, w, 4), cnt.reshape(h, w, 2), depth.reshape(h, w)
     return (out, cnt, depth) if return_depth else (out, cnt)
+
+
+def render_exact(vol, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf_rgbs, color_var,
+                 tf_lo, tf_hi, bg=(0.0, 0.0, 0.0, 0.0), ert=True, pixels=None, nthreads=0):
+    """The render with every decision in FP64 on the plain definition (FP64 ray, sample
+    position, shell test and trilinear brush test) -> (rgba float64, counts uint32) shaped like
+    render(). It measures how far the method's FP32 decisions sit from the real-valued
+    definition; the parity tests use render()."""
+    v = _vol(vol)
+    V, n = v.shape[0], v.shape[1]
+    cam = _f32(cam)
+    assert cam.shape == (10,)
+    tf = _f32(tf_rgbs)
+    assert tf.shape == (256, 4)
+    bg = np.ascontiguousarray(np.asarray(bg, dtype=np.float64))
+    if pixels is None:
+        npix, pix_ptr = w * h, None
+    else:
+        pix = np.ascontiguousarray(np.asarray(pixels, dtype=np.int64))
+        npix, pix_ptr = pix.shape[0], _ptr(pix)
+    out = np.zeros((npix, 4), np.float64)
+    cnt = np.zeros((npix, 2), np.uint32)
+    rc = _load().oracle_render_exact(_ptr(v), n, V, np.float32(r_in), np.float32(r_out), _ptr(cam),
+                                     int(w), int(h), np.float32(dt), _ptr(_f32(lo)), _ptr(_f32(hi)),
+                                     int(active_mask) & 0xFFFFFFFF, _ptr(tf), int(color_var),
+                                     np.float32(tf_lo), np.float32(tf_hi), _ptr(bg), int(bool(ert)),
+                                     pix_ptr, int(npix), _ptr(out), _ptr(cnt), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle_render_exact: invalid arguments")
+    if pixels is None:
+        out, cnt = out.reshape(h, w, 4), cnt.reshape(h, w, 2)
+    return out, cnt
 
 
 def warp(src_rgba, src_depth, cam_from, cam_to, bg=(0.0, 0.0, 0.0, 0.0), fill_holes=False):

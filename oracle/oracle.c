@@ -454,6 +454,7 @@ typedef struct {
     uint32_t *counts;       /* npix x 2: marched lattice samples, kept samples (may be NULL) */
     float *depth;           /* npix: FP32 t of the first kept sample, +inf if none (may be NULL) */
     uint32_t seed, pass;    /* progressive pass: lattice offset of every pixel (pass 0: 1/2) */
+    int exact;              /* 1: every decision in FP64 on the plain definition (render_pixel_exact) */
     int64_t next;           /* shared work counter */
     pthread_mutex_t lock;
 } render_job;
@@ -547,8 +548,9 @@ static ray32 make_ray32(const render_job *J, int px, int py) {
     return r;
 }
 
-/* FP64 geometry of the same ray, for the colour value. */
-typedef struct { double o[3], d[3], t0; } ray64;
+/* FP64 geometry of the same ray, for the colour value (and, in the FP64-decision */
+/* mode, for everything).                                                          */
+typedef struct { double o[3], d[3], t0, t1; int hit; } ray64;
 
 static ray64 make_ray64(const render_job *J, int px, int py) {
     ray64 r;
@@ -571,7 +573,9 @@ static ray64 make_ray64(const render_job *J, int px, int py) {
     double b = r.o[0] * r.d[0] + r.o[1] * r.d[1] + r.o[2] * r.d[2];
     double cc = r.o[0] * r.o[0] + r.o[1] * r.o[1] + r.o[2] * r.o[2] - (double)J->r_out * J->r_out;
     double disc = b * b - cc;
+    r.hit = disc > 0;
     r.t0 = disc > 0 ? fmax(-b - sqrt(disc), 0.0) : 0.0;
+    r.t1 = disc > 0 ? -b + sqrt(disc) : 0.0;
     return r;
 }
 
@@ -722,6 +726,60 @@ static void render_pixel(const render_job *J, int px, int py, double *out, uint3
     if (depth && kept == 0) *depth = INFINITY;
 }
 
+/* The same render with every decision taken in FP64 on the plain definition  */
+/* (Section 2.2 restated without the method's FP32 arithmetic): the ray and    */
+/* its outer-sphere interval in FP64, samples t_k = t0 + (k + 1/2) dt < t1,    */
+/* p = o + t_k d, the shell test r_in^2 <= |p|^2 <= r_out^2, and the brush     */
+/* test on the FP64 trilinear value at the FP64 position. Colour, transfer     */
+/* function and compositing as in render_pixel. It measures how far the FP32   */
+/* decisions of the method sit from the real-valued definition; it is not the  */
+/* reference of the parity tests (those need the method's own decisions).     */
+static void render_pixel_exact(const render_job *J, int px, int py, double *out, uint32_t *cnt) {
+    ray64 q = make_ray64(J, px, py);
+    double C[3] = {0, 0, 0}, A = 0.0;
+    uint32_t marched = 0, kept = 0;
+    const double thr = 1.0 - ldexp(1.0, -12);
+    const double rin2 = (double)J->r_in * J->r_in, rout2 = (double)J->r_out * J->r_out;
+    if (q.hit) {
+        for (int k = 0;; k++) {
+            double t = q.t0 + ((double)k + 0.5) * (double)J->dt;
+            if (!(t < q.t1)) break;
+            marched++;
+            double p[3];
+            for (int a = 0; a < 3; a++) p[a] = q.o[a] + t * q.d[a];
+            double r2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+            if (!(r2 >= rin2 && r2 <= rout2)) continue;
+            int keep = 1;
+            for (int v = 0; v < J->nvars && keep; v++) {
+                if (!((J->active_mask >> v) & 1u)) continue;
+                double s = interp64(J, v, p);
+                if (!(s >= (double)J->lo[v] && s <= (double)J->hi[v])) keep = 0;
+            }
+            if (!keep) continue;
+            kept++;
+            double vc = interp64(J, J->color_var, p);
+            double s = (vc - J->tf_lo) / ((double)J->tf_hi - J->tf_lo) * 255.0;
+            if (s < 0) s = 0;
+            if (s > 255) s = 255;
+            int j = (int)floor(s);
+            if (j > 254) j = 254;
+            double w = s - j;
+            double e[4];
+            for (int c = 0; c < 4; c++) e[c] = J->tf[j * 4 + c] * (1.0 - w) + J->tf[(j + 1) * 4 + c] * w;
+            double alpha = 1.0 - exp(-e[3] * (double)J->dt);
+            double tr = 1.0 - A;
+            for (int c = 0; c < 3; c++) C[c] += tr * alpha * e[c];
+            A += tr * alpha;
+            if (J->ert && A >= thr) break;
+        }
+    }
+    out[0] = C[0] + (1.0 - A) * J->bg[0];
+    out[1] = C[1] + (1.0 - A) * J->bg[1];
+    out[2] = C[2] + (1.0 - A) * J->bg[2];
+    out[3] = A + (1.0 - A) * J->bg[3];
+    if (cnt) { cnt[0] = marched; cnt[1] = kept; }
+}
+
 static void *render_worker(void *arg) {
     render_job *J = (render_job *)arg;
     const int64_t chunk = 64;
@@ -735,8 +793,11 @@ static void *render_worker(void *arg) {
         for (int64_t i = s; i < e; i++) {
             int64_t pix = J->pixels ? J->pixels[i] : i;
             int px = (int)(pix % J->w), py = (int)(pix / J->w);
-            render_pixel(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL,
-                         J->depth ? J->depth + i : NULL);
+            if (J->exact)
+                render_pixel_exact(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL);
+            else
+                render_pixel(J, px, py, J->out + 4 * i, J->counts ? J->counts + 2 * i : NULL,
+                             J->depth ? J->depth + i : NULL);
         }
     }
     return NULL;
@@ -796,6 +857,7 @@ int oracle_render_pass(const float *vol, int n, int nvars, float r_in, float r_o
                        const float *plo, const float *phi, uint32_t pmask, int tf_skip, float *depth) {
     if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
     render_job J;
+    J.exact = 0;
     J.seed = seed; J.pass = pass;
     J.plo = plo; J.phi = phi; J.pmask = pmask;
     J.nsb = (n + 3) / 4;
@@ -832,6 +894,34 @@ int oracle_render(const float *vol, int n, int nvars, float r_in, float r_out,
     return oracle_render_pass(vol, n, nvars, r_in, r_out, cam, w, h, dt, lo, hi, active_mask, tf, color_var,
                               tf_lo, tf_hi, bg, ert, pixels, npix, out, counts, nthreads, 0u, 0u,
                               NULL, NULL, 0u, 0, NULL);
+}
+
+/* FP64-decision render (render_pixel_exact) of all pixels or of a list. */
+int oracle_render_exact(const float *vol, int n, int nvars, float r_in, float r_out,
+                        const float *cam, int w, int h, float dt,
+                        const float *lo, const float *hi, uint32_t active_mask,
+                        const float *tf, int color_var, float tf_lo, float tf_hi,
+                        const double *bg, int ert, const int64_t *pixels, int64_t npix,
+                        double *out, uint32_t *counts, int nthreads) {
+    if (n < 2 || w < 1 || h < 1 || !(dt > 0.0f)) return 1;
+    render_job J;
+    memset(&J, 0, sizeof(J));
+    J.exact = 1;
+    J.vol = vol; J.n = n; J.nvars = nvars; J.r_in = r_in; J.r_out = r_out;
+    J.cam = cam; J.w = w; J.h = h; J.dt = dt; J.lo = lo; J.hi = hi;
+    J.active_mask = active_mask; J.tf = tf; J.color_var = color_var;
+    J.tf_lo = tf_lo; J.tf_hi = tf_hi; J.bg = bg; J.ert = ert;
+    J.pixels = pixels; J.npix = pixels ? npix : (int64_t)w * h;
+    J.out = out; J.counts = counts; J.next = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (nthreads <= 0) nthreads = (int)sysconf(_SC_NPROCESSORS_ONLN);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, render_worker, &J);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    pthread_mutex_destroy(&J.lock);
+    return 0;
 }
 
 int oracle_num_threads(void) { return (int)sysconf(_SC_NPROCESSORS_ONLN); }

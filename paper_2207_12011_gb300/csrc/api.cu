@@ -715,11 +715,16 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
     double ri = (double)V->r_in * (double)L->n, ro = (double)V->r_out * (double)L->n;
     h.s_in = (int64_t)ceil(ri * ri);
     h.s_out = (int64_t)floor(ro * ro);
-    // edges: a small device copy owned by this call (freed in stream order)
-    size_t eb = sizeof(float) * naxes * (bins + 1);
+    // edges: in the launch parameters when the table is small, else a device copy owned by
+    // this call (freed in stream order)
+    const size_t ne = (size_t)naxes * (bins + 1);
     float* dedges = nullptr;
-    CK(cudaMallocAsync((void**)&dedges, eb, s), "edge buffer");
-    cudaError_t e = cudaMemcpyAsync(dedges, edges, eb, cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    h.edges_host = edges;
+    if (ne > (size_t)kHistInlineEdges) {
+        CK(cudaMallocAsync((void**)&dedges, sizeof(float) * ne, s), "edge buffer");
+        e = cudaMemcpyAsync(dedges, edges, sizeof(float) * ne, cudaMemcpyHostToDevice, s);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(out_counts_dev, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
     if (e == cudaSuccess) {
         h.edges = dedges;
@@ -728,7 +733,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         h.nsb = L->nsb;
         e = launch_histogram(h, V->dtype, s);
     }
-    cudaFreeAsync(dedges, s);
+    if (dedges) cudaFreeAsync(dedges, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
     return RAYPC_OK;
 }

@@ -295,6 +295,10 @@ __host__ __device__ constexpr int warp_tile_w(int variant) { return variant == 2
 __host__ __device__ constexpr int block_tile_w(int variant) { return 2 * warp_tile_w(variant); }
 __host__ __device__ constexpr int block_tile_h(int variant) { return 2 * (32 / warp_tile_w(variant)); }
 
+// Histogram edge tables of at most this many floats (8 axes x 257 edges) are
+// passed to the kernel in its launch parameters; larger ones need a device copy.
+constexpr int kHistInlineEdges = 8 * 257;
+
 struct HistArgs {
     const void* cells;
     int n;
@@ -304,7 +308,8 @@ struct HistArgs {
     unsigned need_mask;           // variables the kernel must load (brushed and axes)
     int naxes, bins;
     int axis[kMaxVars];
-    const float* edges;           // naxes x (bins + 1), device
+    const float* edges;           // naxes x (bins + 1), device (may be null when edges_host is given)
+    const float* edges_host;      // naxes x (bins + 1), host: small tables travel in the launch parameters
     float guess_e0[kMaxVars];     // per axis: first edge and bins / (last - first), for the
     float guess_scale[kMaxVars];  // starting guess of the bin walk (any value is correct)
     int64_t s_in, s_out;

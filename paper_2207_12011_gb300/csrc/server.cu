@@ -206,9 +206,11 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     h.s_in = (int64_t)ceil(ri * ri);
     h.s_out = (int64_t)floor(ro * ro);
     h.edges = q->d_edges;
+    h.edges_host = q->edges.data();       // small tables travel in the launch parameters
     h.out = q->hist;
-    cudaError_t e = cudaMemcpyAsync(q->d_edges, q->edges.data(), sizeof(float) * q->edges.size(),
-                                    cudaMemcpyHostToDevice, s);
+    cudaError_t e = cudaSuccess;
+    if (q->edges.size() > (size_t)kHistInlineEdges)
+        e = cudaMemcpyAsync(q->d_edges, q->edges.data(), sizeof(float) * q->edges.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
     if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
     if (e != cudaSuccess) return cuda_fail(e, "server histogram");

@@ -519,6 +519,41 @@ def test_histogram_rejects_bad_edges(ctx, rp):
 POS = (np.float32([-0.45, -np.inf, -np.inf, 0.62]), np.float32([0.5, np.inf, np.inf, 0.9]), 0b1001)
 
 
+@pytest.mark.parametrize("n,store", [(48, "f16"), (64, "f32"), (47, "f16"), (42, "f32")])
+def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
+    """Grid edges that are a multiple of the 16-byte chunk (8 FP16 / 4 FP32 cells) take the
+    vector kernel, the others the scalar one; both must count what the oracle counts, with
+    position axes, a repeated axis variable, brushed variables that are no axis, the position
+    brush, inactive sub-bricks, and the edges in the launch parameters or on the device."""
+    vol = synth.make_shell_volume(n, seed=17)
+    st = stored(vol, store)
+    cases = [
+        ("c3", (0, 1, 2, 3, 4, 5), 256, None),
+        ("c2", [rp.AXIS_POS(rp.POS_R), 1, 4, 1], 64, POS),
+        ("c1", (3, 5), 1024, None),                               # table too large for the parameters
+        ("c2", (0, 5, rp.AXIS_POS(rp.POS_Y)), 16, None),
+    ]
+    for bname, order, bins, pos in cases:
+        brush = synth.make_brush(vol, bname)
+        v = load(ctx, vol, store, brush=brush)
+        if pos is not None:
+            v.set_position_brush(*pos)
+        rows = []
+        for a in order:
+            if a >= 8:
+                rows.append(np.linspace(-1.0 if a != rp.AXIS_POS(rp.POS_R) else 0.5, 1.0, bins + 1))
+            else:
+                rows.append(synth.make_edges(torch.from_numpy(st), [a], bins)[0])
+        edges = np.stack(rows).astype(np.float32)
+        for use in (True, False):
+            H = v.pc_histogram(order, edges, use_brush=use).cpu().numpy().astype(np.uint32)
+            Ho, cells = oracle.histogram(st, R_IN, R_OUT, brush.lo, brush.hi, brush.active_mask, order, edges,
+                                         use_brush=use, pos=pos if use else None)
+            assert np.array_equal(H, Ho), (bname, order, use)
+            assert cells > 0 and all(int(H[p].sum()) == cells for p in range(H.shape[0]))
+        v.free()
+
+
 @pytest.mark.parametrize("n,store,bname", [(48, "f32", "c2"), (33, "f16", "c1")])
 def test_position_brush_render_and_classification(ctx, rp, n, store, bname):
     vol = synth.make_shell_volume(n, seed=8)

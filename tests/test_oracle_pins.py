@@ -1281,3 +1281,115 @@ def test_warp_hole_filling_takes_the_nearest_reached_neighbour():
             assert src[y, x] == cand[0][1]
             filled += 1
     assert filled > 20
+
+
+# ----------------------------------------------------------------------------
+# FP64-decision mode: every decision on the plain real-valued definition
+# ----------------------------------------------------------------------------
+def _lattice_counts64(cam, w, h, dt, keep):
+    """Per pixel, the lattice points t_k = t0 + (k + 1/2) dt < t1 of the outer-sphere interval
+    (FP64, from the pinhole definition) whose position p satisfies keep(p)."""
+    eye, d = pixel_rays64(cam, w, h)
+    out = np.zeros((h, w), np.int64)
+    for y in range(h):
+        for x in range(w):
+            dd = d[y, x]
+            b = eye @ dd
+            disc = b * b - (eye @ eye - R_OUT ** 2)
+            if disc <= 0:
+                continue
+            t0, t1 = max(-b - math.sqrt(disc), 0.0), -b + math.sqrt(disc)
+            ks = np.arange(int((t1 - t0) / dt) + 2)
+            tk = t0 + (ks + 0.5) * dt
+            tk = tk[tk < t1]
+            p = eye[None, :] + tk[:, None] * dd[None, :]
+            out[y, x] = np.count_nonzero(keep(p))
+    return out
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_exact_mode_constant_shell_closed_form(n):
+    """(a) in FP64 decisions: kept = the FP64 count of lattice points in the shell, and
+    A = 1 - exp(-sigma dt kept), C = c A."""
+    sigma, rgb = 2.0, (1.0, 0.5, 0.25)
+    tf = tf_const(rgb, sigma)
+    cam = synth.orbit_camera(30, 20, 3.0)
+    w = h = 40
+    dt = 1.0 / n
+    img, cnt = oracle.render_exact(const_volume(n), R_IN, R_OUT, cam.as_array(), w, h, dt, *ALL_IN, 0,
+                                   tf.rgbs, 0, 0.0, 1.0, ert=False)
+    kept = cnt[..., 1].astype(np.float64)
+    A = 1 - np.exp(-sigma * dt * kept)
+    assert np.max(np.abs(img[..., 3] - A)) < 1e-12
+    for c in range(3):
+        assert np.max(np.abs(img[..., c] - rgb[c] * A)) < 1e-12
+    r2 = lambda p: np.sum(p * p, axis=1)
+    want = _lattice_counts64(cam, w, h, dt, lambda p: (r2(p) >= R_IN ** 2) & (r2(p) <= R_OUT ** 2))
+    assert np.array_equal(cnt[..., 1].astype(np.int64), want)
+    assert want.sum() > 0
+
+
+def test_exact_mode_slab_brush_on_affine_field_counts():
+    """An affine field is interpolated exactly in FP64, so a slab brush keeps exactly the lattice
+    points of the shell whose x lies in the slab (FP64 count from the definition)."""
+    n = 64
+    c = (np.arange(n) + 0.5) * 2 / n - 1
+    vol = np.zeros((2, n, n, n), np.float32)
+    vol[0] = c[None, None, :]
+    vol[1] = 0.5
+    x0, x1 = np.float32(-0.3), np.float32(0.45)
+    tf = tf_const((1, 1, 1), 2.5)
+    cam = synth.orbit_camera(70, 25, 3.0)
+    w = h = 36
+    _, cnt = oracle.render_exact(vol, R_IN, R_OUT, cam.as_array(), w, h, 1.0 / n,
+                                 np.array([x0, -np.inf], np.float32), np.array([x1, np.inf], np.float32),
+                                 1, tf.rgbs, 1, 0.0, 1.0, ert=False)
+    r2 = lambda p: np.sum(p * p, axis=1)
+    want = _lattice_counts64(cam, w, h, 1.0 / n, lambda p: (r2(p) >= R_IN ** 2) & (r2(p) <= R_OUT ** 2)
+                             & (p[:, 0] >= float(x0)) & (p[:, 0] <= float(x1)))
+    assert np.array_equal(cnt[..., 1].astype(np.int64), want)
+    assert want.sum() > 0
+
+
+def test_exact_mode_brush_pins(shell32):
+    """(b) an all-excluding brush gives the background, (c) an all-including brush the
+    unbrushed image, (d) narrowing a brush never raises the opacity (ERT off) -- all with
+    FP64 decisions."""
+    tf = synth.make_tf(torch.from_numpy(shell32), "T_anom")
+    cam = synth.orbit_camera(30, 20, 3.0)
+
+    def run(lo, hi, mask, ert=False, bg=(0, 0, 0, 0)):
+        return oracle.render_exact(shell32, R_IN, R_OUT, cam.as_array(), 40, 32, 1.0 / 32, lo, hi, mask,
+                                   tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, bg=bg, ert=ert)
+    lo, hi = np.full(6, -np.inf, np.float32), np.full(6, np.inf, np.float32)
+    lo[0], hi[0] = 1.0, 0.0
+    bg = (0.25, 0.5, 0.125, 0.75)
+    img, cnt = run(lo, hi, 1, ert=True, bg=bg)
+    assert np.all(cnt[..., 1] == 0) and np.all(img == np.array(bg)[None, None, :])
+    img0, cnt0 = run(*ALL_IN, 0)
+    img1, cnt1 = run(*ALL_IN, 0b111111)
+    assert np.array_equal(img0, img1) and np.array_equal(cnt0, cnt1) and cnt0[..., 1].sum() > 0
+    base = synth.brush_from_quantiles(torch.from_numpy(shell32), synth.jittered_spec("c3", 7, 0.05))
+    narrow = base.copy()
+    for v in range(6):
+        if (base.active_mask >> v) & 1 and np.isfinite(base.lo[v]):
+            narrow.lo[v] = np.float32(base.lo[v] + 0.02)
+    wi, wc = run(base.lo, base.hi, base.active_mask)
+    ni, nc = run(narrow.lo, narrow.hi, narrow.active_mask)
+    assert np.all(ni[..., 3] <= wi[..., 3]) and np.all(nc[..., 1] <= wc[..., 1])
+    assert nc[..., 1].sum() < wc[..., 1].sum()
+
+
+def test_exact_mode_is_close_to_the_fp32_decisions(shell32):
+    """The FP32-decision oracle and the FP64-decision mode disagree only where a sample sits
+    within rounding of a boundary: few pixels, small differences."""
+    b = synth.make_brush(torch.from_numpy(shell32), "c2")
+    tf = synth.make_tf(torch.from_numpy(shell32), "v_r")
+    cam = synth.orbit_camera(30, 20, 3.0)
+    args = (shell32, R_IN, R_OUT, cam.as_array(), 48, 40, 1.0 / 32, b.lo, b.hi, b.active_mask,
+            tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    i32, c32 = oracle.render(*args, ert=False)
+    i64, c64 = oracle.render_exact(*args, ert=False)
+    assert np.array_equal(c32[..., 0], c64[..., 0]) or np.mean(c32[..., 0] != c64[..., 0]) < 0.01
+    assert np.mean(c32[..., 1] != c64[..., 1]) < 0.05
+    assert np.mean(np.abs(i32 - i64)) < 1e-3
