@@ -221,6 +221,161 @@ def step(rp, vol, wl, img, H, stats, src, ev=None, hev=None):
         hev[1].record()
 
 
+def cpu_model():
+    """CPU model of the host (for the oracle timings), or the machine name."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def accuracy_report(wl, gpu_img, vol_np, src_np=None, count_row_stride=4):
+    """Full-frame error of a GPU frame against the oracle on the same stored values (the
+    arithmetic error), against the oracle with every decision in FP64 on the plain definition
+    (how far the method's FP32 decisions sit from the real-valued one), and -- for FP16 storage
+    -- against the oracle on the FP32 source (the storage error); the oracle's full-frame time on
+    all host cores."""
+    import oracle
+    c = wl.cfg
+    w, h = c["w"], c["h"]
+    tol = 1e-3 if c["store"] == "f32" else 4e-3
+    common = (synth.R_IN, synth.R_OUT, wl.cam.as_array(), w, h, 1.0 / c["n"], wl.brush.lo, wl.brush.hi,
+              wl.brush.active_mask, wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi)
+    g = gpu_img.cpu().numpy().astype(np.float64)
+
+    def err(ref):
+        e = np.abs(g - ref)
+        px = e.max(axis=-1)
+        return {"max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e ** 2))),
+                "frac_pixels_above_tol": float(np.mean(px > tol))}
+
+    t0 = time.perf_counter()
+    ref, cnt = oracle.render(vol_np, *common, ert=True)
+    t_oracle = time.perf_counter() - t0
+    out = {"tol": tol, "pixels": w * h, "vs_oracle": err(ref)}
+    t1 = time.perf_counter()
+    ex, _ = oracle.render_exact(vol_np, *common, ert=True)
+    t_exact = time.perf_counter() - t1
+    out["vs_fp64_decision_oracle"] = err(ex)
+    rows = np.arange(count_row_stride // 2, h, count_row_stride)
+    pix = (rows[:, None] * w + np.arange(w)[None, :]).reshape(-1)
+    _, c32 = oracle.render(vol_np, *common, ert=False, pixels=pix)
+    _, c64 = oracle.render_exact(vol_np, *common, ert=False, pixels=pix)
+    hit = c64[:, 0] > 0
+    out["fp64_decisions"] = {
+        "pixels": int(len(pix)), "sample": f"every {count_row_stride}th row, ERT off",
+        "frac_pixels_kept_count_differs": float(np.mean(c32[:, 1] != c64[:, 1])),
+        "frac_hit_pixels_kept_count_differs": float(np.mean((c32[:, 1] != c64[:, 1])[hit])) if hit.any() else 0.0,
+        "frac_pixels_lattice_count_differs": float(np.mean(c32[:, 0] != c64[:, 0])),
+        "kept_samples_abs_diff_over_kept": float(np.abs(c32[:, 1].astype(np.int64) - c64[:, 1]).sum()
+                                                 / max(1, int(c64[:, 1].sum())))}
+    if src_np is not None:
+        ref32, _ = oracle.render(src_np, *common, ert=True)
+        out["fp16_storage_error"] = {**err(ref32), "what": "FP16-stored GPU frame against the oracle on the "
+                                                           "FP32 source (reported, not asserted)"}
+    out["oracle_full_frame"] = {"s": round(t_oracle, 3), "s_fp64_decisions": round(t_exact, 3),
+                                "lattice_samples": int(cnt[..., 0].sum()),
+                                "samples_per_s": round(float(cnt[..., 0].sum()) / t_oracle, 1),
+                                "cores": oracle.num_threads(), "cpu": cpu_model()}
+    return out
+
+
+def config_section(rp, name, args, dev, seed, rank):
+    """One BASELINE configuration measured on its own: K whole-path steps (ingest, LOD, bricks,
+    brush, render, histograms) with CUDA events around the render and the histograms, the
+    resident-volume frame loop, the render and histogram rooflines, and (rank 0) the full-frame
+    accuracy against the oracle."""
+    wl = Workload(name, seed, dev)
+    c = wl.cfg
+    ctx = rp.Context(dev.index)
+    vol = ctx.load_volume(wl.src, store=c["store"])
+    vol.build_bricks(n_lod=c["n_lod"])
+    vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)
+    vol.set_tf(wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi)
+    img = torch.empty((c["h"], c["w"], 4), dtype=torch.float32, device=dev)
+    naxes = len(c["order"])
+    H = torch.empty((naxes - 1, c["bins"], c["bins"]), dtype=torch.int32, device=dev)
+    stats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    tuned, _ = rp.autotune(ctx, [dict(vol=vol, cam=wl.cam, w=c["w"], h=c["h"], lo=wl.brush.lo,
+                                      hi=wl.brush.hi, mask=wl.brush.active_mask, out=img)], reps=3)
+    for _ in range(3):
+        step(rp, vol, wl, img, H, stats, wl.src)
+    torch.cuda.synchronize()
+    _, _, active_list = vol.skip_list(0)
+    n_active = int(active_list.numel())
+    K = args.config_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    hevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats.zero_()
+    torch.cuda.synchronize()
+    t0.record()
+    for i in range(K):
+        step(rp, vol, wl, img, H, stats, wl.src, evs[i], hevs[i])
+    t1.record()
+    torch.cuda.synchronize()
+    step_ms = t0.elapsed_time(t1) / K
+    render_ms = sum(a.elapsed_time(b) for a, b in evs) / K
+    hist_ms = sum(a.elapsed_time(b) for a, b in hevs) / K
+    st = stats.cpu().numpy() / K
+    nframes = max(K, 10)
+    fstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    t0.record()
+    for _ in range(nframes):
+        vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)
+        vol.render(wl.cam, c["w"], c["h"], out=img, stats=fstats)
+        vol.pc_histogram(c["order"], wl.edges, use_brush=True, out=H)
+    t1.record()
+    torch.cuda.synchronize()
+    frame_ms = t0.elapsed_time(t1) / nframes
+    peak, peak_kind = measured_peaks()
+    elem = 2 if c["store"] == "f16" else 4
+    nvars = wl.src.shape[0]
+    alg = n_active * 8 ** 3 * nvars * elem + c["w"] * c["h"] * 16
+    hist_bytes = c["n"] ** 3 * nvars * elem + (naxes - 1) * c["bins"] ** 2 * 4
+    sec = {"workload": wl.describe(), "autotune": tuned,
+           "step_ms": round(step_ms, 4), "frame_only_ms": round(frame_ms, 4), "fps_frame_only": round(1e3 / frame_ms, 2),
+           "render_ms": round(render_ms, 4), "hist_ms": round(hist_ms, 4),
+           "lattice_samples_per_frame": float(st[0]), "evaluated_per_frame": float(st[1]),
+           "kept_per_frame": float(st[2]), "skipped_per_frame": float(st[3]),
+           "lattice_samples_per_s_step": round(float(st[0]) / (step_ms / 1e3), 1),
+           "lattice_samples_per_s_render": round(float(st[0]) / (render_ms / 1e3), 1),
+           "roofline": {"kernel": "k_render", "bound": "hbm", "achieved": round(alg / render_ms / 1e6, 1),
+                        "peak": peak, "unit": "GB/s", "frac": round(alg / render_ms / 1e6 / peak, 4),
+                        "alg_bytes_per_launch": int(alg), "active_bricks": n_active,
+                        "peak_kind": f"{peak_kind} HBM copy"},
+           "roofline_histogram": {"kernel": "k_hist", "bound": "hbm", "achieved": round(hist_bytes / hist_ms / 1e6, 1),
+                                  "peak": peak, "unit": "GB/s", "frac": round(hist_bytes / hist_ms / 1e6 / peak, 4),
+                                  "alg_bytes_per_launch": int(hist_bytes), "peak_kind": f"{peak_kind} HBM copy"}}
+    if rank == 0 and not args.no_accuracy:
+        vol.render(wl.cam, c["w"], c["h"], out=img)
+        torch.cuda.synchronize()
+        vol_np = synth.to_storage(wl.src, c["store"]).float().cpu().numpy()
+        src_np = wl.src.cpu().numpy() if c["store"] == "f16" else None
+        vol.free()
+        ctx.close()
+        del wl.src
+        torch.cuda.empty_cache()
+        sec["accuracy"] = accuracy_report(wl, img, vol_np, src_np)
+        del vol_np, src_np
+    else:
+        vol.free()
+        ctx.close()
+        del wl.src
+    torch.cuda.empty_cache()
+    return sec
+
+
 def run_ours(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -412,41 +567,23 @@ def run_ours(args):
     del seeds, seed_flags
 
     # ---- end to end through the C ABI from pinned host buffers ----
-    # Every step copies its volume host -> device (pinned source) and reads its
-    # image and histograms back device -> host. The copy of step i+1 runs on a
-    # copy stream into the other half of a double-buffered device staging area
-    # while step i computes; the host reads step i's results (a checksum of
-    # the histograms) one step later.
+    # Every step hands the pinned host volume to raypc_update_volume (the library copies it
+    # host -> device on its own copy stream into the volume's staging buffer; the copy of step
+    # i+1 overlaps the render and histograms of step i) and reads its image and histograms back
+    # device -> host; the host reads step i's histograms one step later.
     host_src = torch.empty(wl.src.shape, dtype=wl.src.dtype, pin_memory=True)
     host_src.copy_(wl.src)
     host_img = [torch.empty(img.shape, dtype=img.dtype, pin_memory=True) for _ in range(2)]
     host_H = [torch.empty(H.shape, dtype=H.dtype, pin_memory=True) for _ in range(2)]
-    stage = [torch.empty_like(wl.src) for _ in range(2)]
-    copy_stream = torch.cuda.Stream(device=dev)
     comp = torch.cuda.current_stream()
     estats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
     e2e_steps = max(3, min(args.steps, 20))
 
     def e2e_run(nsteps):
-        copied = [torch.cuda.Event() for _ in range(2)]
-        consumed = [torch.cuda.Event() for _ in range(2)]
         read = [torch.cuda.Event() for _ in range(2)]
         checks = []
-
-        def enqueue_copy(i):
-            with torch.cuda.stream(copy_stream):
-                if i >= 2:
-                    copy_stream.wait_event(consumed[i % 2])       # staging half free again
-                stage[i % 2].copy_(host_src, non_blocking=True)
-                copied[i % 2].record(copy_stream)
-
-        enqueue_copy(0)
         for i in range(nsteps):
-            if i + 1 < nsteps:
-                enqueue_copy(i + 1)
-            comp.wait_event(copied[i % 2])
-            vol.update(stage[i % 2])
-            consumed[i % 2].record(comp)
+            vol.update(host_src)                                  # C ABI, host source
             vol.build_bricks(n_lod=c["n_lod"])
             vol.set_brush(wl.brush.lo, wl.brush.hi, wl.brush.active_mask)
             vol.set_tf(wl.tf.rgbs, wl.tf.color_var, wl.tf.v_lo, wl.tf.v_hi)
@@ -476,7 +613,7 @@ def run_ours(args):
     small_h2d = wl.brush.lo.nbytes + wl.brush.hi.nbytes + wl.tf.rgbs.nbytes + wl.edges.nbytes + 4 * naxes
     h2d = host_src.numel() * host_src.element_size() + small_h2d
     d2h = host_img[0].numel() * host_img[0].element_size() + host_H[0].numel() * host_H[0].element_size()
-    del stage
+    del host_src
 
     # ---- roofline of the render kernel ----
     peak, peak_kind = measured_peaks()
@@ -507,7 +644,8 @@ def run_ours(args):
                      "unit": "GB/s", "frac": round(hist_gbs / peak, 4), "traffic": None,
                      "peak_kind": f"{peak_kind} HBM copy", "hist_ms": round(hist_ms, 4),
                      "alg_bytes_per_launch": int(hist_bytes),
-                     "note": "time includes the call's output clear and edge upload on the stream"}
+                     "note": "CUDA events around the raypc_pc_histogram call: its output clear (memset) and the "
+                             "kernel; the edges travel in the launch parameters"}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -527,8 +665,10 @@ def run_ours(args):
         "e2e": {"value": round(e2e_all / (e2e_max_ms / 1e3), 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3),
-                "how": "pinned host volume copied per step on a copy stream (double-buffered) while the "
-                       "previous step computes; image + histograms read back per step"},
+                "how": "raypc_update_volume with the pinned host volume every step (C ABI host path: the "
+                       "library copies it on its own copy stream into the volume's staging buffer, overlapping "
+                       "the previous step's render and histograms); image + histograms read back per step",
+                "copies_declared": True},
         "gpu_launches": int(launches),
         "autotune": {"chosen": tuned, "candidates": tuned_all},
         "roofline": roofline,
@@ -538,11 +678,21 @@ def run_ours(args):
     }
     if ws == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args)
-    if not (args.no_batched and args.no_served):
+    if rank == 0 and not args.no_accuracy:
+        vol.render(wl.cam, c["w"], c["h"], out=img)
+        torch.cuda.synchronize()
+        line["accuracy"] = accuracy_report(wl, img, synth.to_storage(wl.src, c["store"]).float().cpu().numpy())
+    configs = [x for x in args.configs.split(",") if x] if args.configs else []
+    if not (args.no_batched and args.no_served) or configs:
         vol.free()
         ctx.close()
         ctx = None
         del wl.src
+    if configs:
+        line["configs"] = {}
+        for name in configs:
+            torch.cuda.empty_cache()
+            line["configs"][name] = config_section(rp, name, args, dev, synth.DEFAULT_SEED + rank, rank)
     if not args.no_batched:
         torch.cuda.empty_cache()
         bt = run_batched(rp, dev, args, synth.DEFAULT_SEED + 1000 + rank)
@@ -609,6 +759,14 @@ def run_batched(rp, dev, args, seed):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / reps
     batch_samples = float(stats[0].item()) / reps
+    # algorithmic bytes of the batch: per view, its active bricks' values under its own brush
+    # plus its image (the per-view classification inside the graph uses the same rule)
+    alg_bytes = 0
+    for (c, w, h), b in zip(views, brushes):
+        v16.set_brush(b.lo, b.hi, b.active_mask)
+        _, _, al = v16.skip_list(0)
+        alg_bytes += int(al.numel()) * 8 ** 3 * 6 * 2 + w * h * 16
+    peak, peak_kind = measured_peaks()
     # per-frame plain FP32 launches of the same views: brush edit + render, one frame at a time
     pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
 
@@ -644,6 +802,10 @@ def run_batched(rp, dev, args, seed):
                                     "launch": f"{k} x (set_brush + render), default launch choices (8x4 tiles, skipping on)"},
             "plain_f32_per_frame_tuned": {"ms_per_batch": round(tuned_ms, 3), "tuning": tune32},
             "batched_tuning": tune16,
+            "roofline": {"kernel": "batched graph (classification + cell classes + k_render_batch)", "bound": "hbm",
+                         "achieved": round(alg_bytes / batch_ms / 1e6, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(alg_bytes / batch_ms / 1e6 / peak, 4), "alg_bytes_per_batch": alg_bytes,
+                         "peak_kind": f"{peak_kind} HBM copy"},
             "speedup": round(plain_ms / batch_ms, 3),
             "speedup_vs_tuned_plain": round(tuned_ms / batch_ms, 3),
             "samples_per_batch": batch_samples}
@@ -705,7 +867,9 @@ def run_served(rp, dev, args, seed):
         del src
     torch.cuda.empty_cache()
     reqs = served_requests(nreq, seed, tables, rng)
+    sizes = (256, 512, 1024, 2048)
     outs = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
+    outs_c = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
     H = torch.empty((len(order) - 1, 256, 256), dtype=torch.int32, device=dev)
     pstats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
 
@@ -723,8 +887,7 @@ def run_served(rp, dev, args, seed):
         v.pc_histogram(order, edges_t[t], use_brush=True, out=H)
         return None
 
-    outs_c = {sz: torch.empty((sz, sz, 4), dtype=torch.float32, device=dev) for sz in sizes}
-    # plain FP32 service time (one request at a time) sets the arrival rate
+    # plain FP32 service time (one request at a time) sets the arrival rates
     for r in reqs[:8]:
         plain_one(r)
     torch.cuda.synchronize()
@@ -733,83 +896,97 @@ def run_served(rp, dev, args, seed):
         plain_one(r)
         torch.cuda.current_stream().synchronize()
     service = (time.perf_counter() - t0) / min(64, nreq)
-    rate = args.serve_load / service                     # requests per second
-    gaps = rng.exponential(1.0 / rate, nreq)
-    arrivals = np.cumsum(gaps) - gaps[0]
 
-    # plain FP32 FIFO: one worker, per-frame launches, same passes
-    pstats.zero_()
-    lat_plain, lat_plain_c = [], []
-    start = time.perf_counter()
-    for i, r in enumerate(reqs):
-        now = time.perf_counter() - start
-        if now < arrivals[i]:
-            time.sleep(arrivals[i] - now)
-        ev_c = plain_one(r)
-        if ev_c is not None:
-            ev_c.synchronize()
-            lat_plain_c.append(time.perf_counter() - start - arrivals[i])
-        torch.cuda.current_stream().synchronize()
-        lat_plain.append(time.perf_counter() - start - arrivals[i])
-    plain_span = time.perf_counter() - start
-    plain_samples = float(pstats[0].item())
+    def run_fifo(arrivals):
+        """Plain FP32 FIFO: one worker, per-frame launches, same passes."""
+        pstats.zero_()
+        lat, lat_c = [], []
+        start = time.perf_counter()
+        for i, r in enumerate(reqs):
+            now = time.perf_counter() - start
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            ev_c = plain_one(r)
+            if ev_c is not None:
+                ev_c.synchronize()
+                lat_c.append(time.perf_counter() - start - arrivals[i])
+            torch.cuda.current_stream().synchronize()
+            lat.append(time.perf_counter() - start - arrivals[i])
+        return lat, lat_c, float(pstats[0].item()), time.perf_counter() - start
 
-    # served FP16: continuous batching, coarse LOD-1 pass then the full pass
     import queue
     import threading
-    srv = rp.Server(ctx, max_inflight=args.serve_inflight, output_budget_bytes=args.serve_budget_mb << 20,
-                    max_batch_views=64, num_streams=args.serve_streams,
-                    max_batch_pixels=int(args.serve_batch_mp * 1e6))
-    lat, lat_c, got = [], [], {"samples": 0.0}
-    pending = queue.Queue()
 
-    def consume():
-        while True:
-            rid = pending.get()
-            if rid is None:
-                return
-            res = srv.poll(rid, timeout_us=120_000_000)
-            lat.append(res["t_done"] - res["t_submit"])
-            if res.get("coarse") is not None:
-                lat_c.append(res["t_coarse"] - res["t_submit"])
-            got["samples"] += res["samples"]
-            srv.release(rid)
+    def run_server(arrivals):
+        """Served FP16: continuous batching, coarse LOD-1 pass then the full pass."""
+        srv = rp.Server(ctx, max_inflight=args.serve_inflight, output_budget_bytes=args.serve_budget_mb << 20,
+                        max_batch_views=64, num_streams=args.serve_streams,
+                        max_batch_pixels=int(args.serve_batch_mp * 1e6))
+        lat, lat_c, got = [], [], {"samples": 0.0}
+        pending = queue.Queue()
 
-    consumer = threading.Thread(target=consume)
-    consumer.start()
-    start = time.perf_counter()
-    for i, (kind, t, b, cam, sz) in enumerate(reqs):
-        now = time.perf_counter() - start
-        if now < arrivals[i]:
-            time.sleep(arrivals[i] - now)
-        if kind == "render":
-            rid = srv.submit_render(vols16[t], cam, sz, sz, b.lo, b.hi, b.active_mask, lod=0, coarse_lod=1)
-        else:
-            rid = srv.submit_histogram(vols16[t], order, edges_t[t], b.lo, b.hi, b.active_mask)
-        pending.put(rid)
-    pending.put(None)
-    consumer.join()
-    served_span = time.perf_counter() - start
-    samples = got["samples"]
-    srv.close()
+        def consume():
+            while True:
+                rid = pending.get()
+                if rid is None:
+                    return
+                res = srv.poll(rid, timeout_us=120_000_000)
+                lat.append(res["t_done"] - res["t_submit"])
+                if res.get("coarse") is not None:
+                    lat_c.append(res["t_coarse"] - res["t_submit"])
+                got["samples"] += res["samples"]
+                srv.release(rid)
+
+        consumer = threading.Thread(target=consume)
+        consumer.start()
+        start = time.perf_counter()
+        for i, (kind, t, b, cam, sz) in enumerate(reqs):
+            now = time.perf_counter() - start
+            if now < arrivals[i]:
+                time.sleep(arrivals[i] - now)
+            if kind == "render":
+                rid = srv.submit_render(vols16[t], cam, sz, sz, b.lo, b.hi, b.active_mask, lod=0, coarse_lod=1)
+            else:
+                rid = srv.submit_histogram(vols16[t], order, edges_t[t], b.lo, b.hi, b.active_mask)
+            pending.put(rid)
+        pending.put(None)
+        consumer.join()
+        span = time.perf_counter() - start
+        srv.close()
+        return lat, lat_c, got["samples"], span
+
+    ms = lambda x: None if x is None else round(1e3 * x, 3)
+
+    def point(load):
+        rate = load / service                                # requests per second
+        gaps = np.random.default_rng(seed + int(round(1000 * load))).exponential(1.0 / rate, nreq)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        lp, lpc, ps, pspan = run_fifo(arrivals)
+        ls, lsc, ss, sspan = run_server(arrivals)
+        return {"load_vs_plain_capacity": load, "arrival_rate_per_s": round(rate, 1),
+                "served_f16": {"p50_ms": ms(_pct(ls, 50)), "p99_ms": ms(_pct(ls, 99)),
+                               "coarse_p50_ms": ms(_pct(lsc, 50)), "coarse_p99_ms": ms(_pct(lsc, 99)),
+                               "samples_per_s": round(ss / sspan, 1), "span_s": round(sspan, 3)},
+                "plain_f32_fifo": {"p50_ms": ms(_pct(lp, 50)), "p99_ms": ms(_pct(lp, 99)),
+                                   "coarse_p50_ms": ms(_pct(lpc, 50)), "coarse_p99_ms": ms(_pct(lpc, 99)),
+                                   "samples_per_s": round(ps / pspan, 1), "span_s": round(pspan, 3)},
+                "p50_speedup": round(_pct(lp, 50) / _pct(ls, 50), 3) if ls and lp else None,
+                "p99_speedup": round(_pct(lp, 99) / _pct(ls, 99), 3) if ls and lp else None,
+                "throughput_ratio": round((ss / sspan) / (ps / pspan), 3) if ps > 0 and ss > 0 else None}
+
+    main = point(args.serve_load)
+    sweep = [point(float(x)) for x in args.serve_sweep.split(",") if x] if args.serve_sweep else []
     for v in vols16 + vols32:
         v.free()
     ctx.close()
-    ms = lambda x: None if x is None else round(1e3 * x, 3)
-    return {"what": f"{nreq} Poisson requests (80% render at 256^2..2048^2, 20% 5x256^2 PC histograms) over "
-                    f"3 resident {n}^3 x 6 time steps, brush edit every request",
-            "arrival_rate_per_s": round(rate, 1), "load_vs_plain_capacity": args.serve_load,
-            "served_f16": {"p50_ms": ms(_pct(lat, 50)), "p99_ms": ms(_pct(lat, 99)),
-                           "coarse_p50_ms": ms(_pct(lat_c, 50)), "coarse_p99_ms": ms(_pct(lat_c, 99)),
-                           "samples_per_s": round(samples / served_span, 1),
-                           "how": f"continuous batching ({args.serve_streams} streams, <= {args.serve_batch_mp} MP per launch), "
-                                  "coarse LOD-1 pass then full pass, per-view completion records"},
-            "plain_f32_fifo": {"p50_ms": ms(_pct(lat_plain, 50)), "p99_ms": ms(_pct(lat_plain, 99)),
-                               "coarse_p50_ms": ms(_pct(lat_plain_c, 50)), "coarse_p99_ms": ms(_pct(lat_plain_c, 99)),
-                               "samples_per_s": round(plain_samples / plain_span, 1),
-                               "how": "one request at a time, per-frame launches, coarse LOD-1 pass then full pass"},
-            "p50_speedup": round(_pct(lat_plain, 50) / _pct(lat, 50), 3) if lat and lat_plain else None,
-            "p99_speedup": round(_pct(lat_plain, 99) / _pct(lat, 99), 3) if lat and lat_plain else None}
+    out = {"what": f"{nreq} Poisson requests (80% render at 256^2..2048^2, 20% 5x256^2 PC histograms) over "
+                   f"3 resident {n}^3 x 6 time steps, brush edit every request",
+           "plain_f32_service_ms": round(service * 1e3, 3), **main}
+    out["served_f16"]["how"] = (f"continuous batching ({args.serve_streams} streams, <= {args.serve_batch_mp} MP "
+                                "per launch), coarse LOD-1 pass then full pass, per-view completion records")
+    out["plain_f32_fifo"]["how"] = "one request at a time, per-frame launches, coarse LOD-1 pass then full pass"
+    out["sweep"] = sweep
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -882,6 +1059,10 @@ def main(argv=None):
     ap.add_argument("--cpu-row-stride", type=int, default=16)
     ap.add_argument("--ref-row-stride", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the full-frame oracle comparisons")
+    ap.add_argument("--configs", default="shell64_f32,shell512_f16",
+                    help="comma-separated workloads measured in their own sections besides the headline")
+    ap.add_argument("--config-steps", type=int, default=10)
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batched comparison")
     ap.add_argument("--batch-n", type=int, default=512)
     ap.add_argument("--batch-views", type=int, default=64)
@@ -890,6 +1071,7 @@ def main(argv=None):
     ap.add_argument("--serve-n", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / plain FP32 capacity")
+    ap.add_argument("--serve-sweep", default="0.3,0.6,0.9,1.2", help="further loads, comma-separated")
     ap.add_argument("--serve-inflight", type=int, default=32)
     ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--serve-streams", type=int, default=3)

@@ -185,12 +185,20 @@ raypc_status raypc_free_volume(raypc_ctx *ctx, int vol);
 
 /* Re-ingest new values of the same shape into level 0 of an existing volume
  * (e.g. the next time step of the simulation, Section 2.1), with the source
- * layout and conversion of raypc_load_volume. Allocates no device memory
- * beyond a stream-ordered staging buffer for host sources. A pageable host
- * source is consumed before the call returns; a pinned host source or a
- * device source must stay valid until `stream` reaches the copy. Coarser
- * levels, bricks and the classification become stale: raypc_build_bricks
- * must run again before raypc_render (RAYPC_ERR_INVALID_ARG until then). */
+ * layout and conversion of raypc_load_volume. A device source allocates
+ * nothing and must stay valid until `stream` reaches the ingest. A host
+ * source goes through a staging buffer of the source's size that the volume
+ * keeps (allocated by the first host update, charged to the HBM budget, freed
+ * with the volume; if the budget has no room, a stream-ordered temporary is
+ * used instead). The host-to-device copy runs on a copy stream of the
+ * volume's own that waits only until the previous update's ingest has read
+ * the staging buffer, so the copy of the next time step overlaps the work
+ * still running on `stream` (from a pinned source); `stream` waits for the
+ * copy before the ingest. A pageable host source is consumed before the call
+ * returns; a pinned host source must stay unchanged until the work this call
+ * enqueues on `stream` has completed. Coarser levels, bricks and the
+ * classification become stale: raypc_build_bricks must run again before
+ * raypc_render (RAYPC_ERR_INVALID_ARG until then). */
 raypc_status raypc_update_volume(raypc_ctx *ctx, int vol, const void *src, int src_is_device,
                                  int src_dtype, void *stream);
 
@@ -626,6 +634,15 @@ raypc_status raypc_get_sub_bricks(raypc_ctx *ctx, int vol, int lod, float *out_m
  * decide samples without interpolating (Section 2.2 brush test, same
  * decisions). */
 raypc_status raypc_get_cell_classes(raypc_ctx *ctx, int vol, int lod, uint16_t *out_dev, void *stream);
+
+/* Copy a level's empty-space distance of the 4^3 sub-bricks under the current
+ * brush (computed if needed): out_dev receives nsb^3 uint8 values indexed like
+ * raypc_get_sub_bricks, the Chebyshev distance in sub-bricks from each
+ * sub-brick to the nearest active one, capped at 8 (0: active). Renders with
+ * skipping jump over the samples that stay inside the box of sub-bricks within
+ * distance - 1 (Section 2.2: the brush drives the empty-space skipping; the
+ * image is unchanged). */
+raypc_status raypc_get_skip_distance(raypc_ctx *ctx, int vol, int lod, uint8_t *out_dev, void *stream);
 
 #ifdef __cplusplus
 }

@@ -50,7 +50,8 @@ namespace {
 
 void free_level(Level& L) {
     void* ptrs[] = {L.cells, L.pairs, L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.cls, L.tf_active, L.tf_sactive};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.cls, L.tf_active, L.tf_sactive,
+                    L.sdist, L.sdist_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -58,17 +59,33 @@ void free_level(Level& L) {
 
 void free_bricks(Level& L) {
     void* ptrs[] = {L.bmin, L.bmax, L.active, L.skippable, L.list, L.n_active, L.pass_count,
-                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.tf_active, L.tf_sactive};
+                    L.sbmin, L.sbmax, L.sactive, L.slist, L.scount, L.tf_active, L.tf_sactive,
+                    L.sdist, L.sdist_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     L.bmin = L.bmax = L.sbmin = L.sbmax = nullptr;
     L.active = L.skippable = L.list = L.n_active = L.sactive = L.slist = L.scount = nullptr;
     L.tf_active = L.tf_sactive = nullptr;
+    L.sdist = L.sdist_tmp = nullptr;
+    L.sdist_of = nullptr;
     L.pass_count = nullptr;
     L.bricks = L.classified = L.cls_valid = false;
 }
 
+void free_staging(Volume* V) {
+    if (V->staging) cudaFree(V->staging);
+    if (V->ev_copied) cudaEventDestroy(V->ev_copied);
+    if (V->ev_consumed) cudaEventDestroy(V->ev_consumed);
+    if (V->copy_stream) cudaStreamDestroy(V->copy_stream);
+    V->staging = nullptr;
+    V->staging_bytes = 0;
+    V->ev_copied = V->ev_consumed = nullptr;
+    V->copy_stream = nullptr;
+    V->consumed_pending = false;
+}
+
 void free_volume(raypc_ctx* ctx, Volume* V) {
+    free_staging(V);
     for (auto& L : V->lv) free_level(L);
     if (V->tf) cudaFree(V->tf);
     if (V->tf_prefix) cudaFree(V->tf_prefix);
@@ -115,6 +132,7 @@ raypc_status classify_all(Volume* V, cudaStream_t s) {
     for (int l = 0; l < V->nlev; ++l) {
         V->lv[l].classified = true;
         V->lv[l].cls_valid = false;          // cell classes follow the brush; computed on demand
+        V->lv[l].sdist_of = nullptr;         // so does the empty-space distance
     }
     return RAYPC_OK;
 }
@@ -153,15 +171,61 @@ raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
     return RAYPC_OK;
 }
 
+// Staging of a host source for raypc_update_volume: the volume's own buffer and copy stream
+// (created on first use, charged to the budget). The copy waits only for the previous ingest to
+// have read the buffer, so the next time step's copy overlaps whatever still runs on the
+// caller's stream; the caller's stream waits for the copy. Returns false when the buffer cannot
+// be had (budget), and the caller falls back to a stream-ordered temporary.
+bool stage_host_source(raypc_ctx* ctx, Volume* V, const void* src, size_t bytes, cudaStream_t s,
+                       const void** dsrc, raypc_status* st) {
+    *st = RAYPC_OK;
+    if (V->staging_bytes != bytes) {
+        if (V->staging) {
+            cudaStreamSynchronize(V->copy_stream);
+            if (V->consumed_pending) cudaEventSynchronize(V->ev_consumed);
+            cudaFree(V->staging);
+            V->bytes -= V->staging_bytes;
+            ctx->used -= V->staging_bytes < ctx->used ? V->staging_bytes : ctx->used;
+            V->staging = nullptr;
+            V->staging_bytes = 0;
+            V->consumed_pending = false;
+        }
+        if (ctx->alloc(&V->staging, bytes, &V->bytes) != RAYPC_OK) {
+            cudaGetLastError();
+            return false;
+        }
+        V->staging_bytes = bytes;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!V->copy_stream) e = cudaStreamCreateWithFlags(&V->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !V->ev_copied) e = cudaEventCreateWithFlags(&V->ev_copied, cudaEventDisableTiming);
+    if (e == cudaSuccess && !V->ev_consumed) e = cudaEventCreateWithFlags(&V->ev_consumed, cudaEventDisableTiming);
+    if (e == cudaSuccess && V->consumed_pending) e = cudaStreamWaitEvent(V->copy_stream, V->ev_consumed, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V->staging, src, bytes, cudaMemcpyHostToDevice, V->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(V->ev_copied, V->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, V->ev_copied, 0);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(e, "host to device copy");
+        return true;
+    }
+    *dsrc = V->staging;
+    return true;
+}
+
 raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_device, int src_dtype,
-                    cudaStream_t s) {
-    (void)ctx;
+                    cudaStream_t s, bool own_staging = false) {
     Level& L = V->lv[0];
     const size_t nvox = (size_t)L.n * L.n * L.n;
     const void* dsrc = src;
     void* staging = nullptr;
     cudaError_t e;
-    if (!src_is_device) {
+    bool staged = false;
+    if (!src_is_device && own_staging) {
+        raypc_status st;
+        staged = stage_host_source(ctx, V, src, nvox * V->nvars * elem_size(src_dtype), s, &dsrc, &st);
+        if (st != RAYPC_OK) return st;
+    }
+    if (!src_is_device && !staged) {
         size_t src_bytes = nvox * V->nvars * elem_size(src_dtype);
         e = cudaMallocAsync(&staging, src_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
@@ -172,6 +236,10 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
     e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, L.sbmin,
                       L.sbmax, s);
     if (staging) cudaFreeAsync(staging, s);
+    if (staged && e == cudaSuccess) {
+        e = cudaEventRecord(V->ev_consumed, s);       // the staging buffer is free once this ingest ran
+        V->consumed_pending = e == cudaSuccess;
+    }
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     L.bricks = true;               // level-0 brick min/max come out of the ingest pass
     for (auto& l : V->lv) l.classified = l.cls_valid = false;
@@ -437,7 +505,7 @@ raypc_status raypc_update_volume(raypc_ctx* ctx, int vol, const void* src, int s
     Volume* V = nullptr;
     raypc_status st = get_volume(ctx, vol, &V);
     if (st) return st;
-    if ((st = ingest(ctx, V, src, src_is_device, src_dtype, (cudaStream_t)stream))) return st;
+    if ((st = ingest(ctx, V, src, src_is_device, src_dtype, (cudaStream_t)stream, true))) return st;
     V->stale = true;
     for (int l = 1; l <= RAYPC_MAX_LOD; ++l) V->lv[l].bricks = false;
     return RAYPC_OK;
@@ -584,6 +652,26 @@ raypc_status raypc_set_tf(raypc_ctx* ctx, int vol, const float* rgbs, int color_
 
 // With tf_skip, the render reads the activity bits ANDed with the TF visibility of
 // the level's bricks and sub-bricks (computed for this render on its stream).
+// Empty-space distance of the sub-bricks under the activity bits the render reads (the
+// brush's, or the TF-visible ones with tf_skip), for renders with skipping.
+static raypc_status ensure_distance(raypc_ctx* ctx, Volume* V, Level& L, RenderArgs& a, bool recompute,
+                                    cudaStream_t s) {
+    if (!a.skip) return RAYPC_OK;
+    if (!L.sdist) {
+        const size_t bytes = L.nsbricks();
+        raypc_status st = ctx->alloc((void**)&L.sdist, bytes, &V->bytes);
+        if (st == RAYPC_OK) st = ctx->alloc((void**)&L.sdist_tmp, bytes, &V->bytes);
+        if (st) return st;
+        L.sdist_of = nullptr;
+    }
+    if (recompute || L.sdist_of != a.lv.sactive) {
+        CK(launch_subbrick_distance(a.lv.sactive, L.nsb, L.sdist, L.sdist_tmp, s), "empty-space distance");
+        L.sdist_of = a.lv.sactive;
+    }
+    a.lv.sdist = L.sdist;
+    return RAYPC_OK;
+}
+
 static raypc_status apply_tf_skip(Volume* V, Level& L, const raypc_render_opts* opts, RenderArgs& a, cudaStream_t s) {
     if (!opts || !opts->tf_skip) return RAYPC_OK;
     TfVisArgs t{};
@@ -626,6 +714,7 @@ raypc_status raypc_render(raypc_ctx* ctx, int vol, int lod, const raypc_camera* 
     if ((st = ensure_cell_classes(ctx, V, *L, (cudaStream_t)stream))) return st;
     a.cls = L->cls;
     if ((st = apply_tf_skip(V, *L, opts, a, (cudaStream_t)stream))) return st;
+    if ((st = ensure_distance(ctx, V, *L, a, opts && opts->tf_skip, (cudaStream_t)stream))) return st;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }
@@ -655,6 +744,7 @@ raypc_status raypc_render_progressive(raypc_ctx* ctx, int vol, int lod, const ra
     a.accum = reinterpret_cast<float4*>(accum_rgba_dev);
     a.accum_w = 1.0f / (float)((double)pass + 1.0);
     if ((st = apply_tf_skip(V, *L, opts, a, (cudaStream_t)stream))) return st;
+    if ((st = ensure_distance(ctx, V, *L, a, opts && opts->tf_skip, (cudaStream_t)stream))) return st;
     CK(launch_render(a, V->dtype, (cudaStream_t)stream), "render kernel");
     return RAYPC_OK;
 }
@@ -974,6 +1064,26 @@ raypc_status raypc_get_cell_classes(raypc_ctx* ctx, int vol, int lod, uint16_t* 
     if ((st = ensure_cell_classes(ctx, V, *L, s))) return st;
     CK(cudaMemcpyAsync(out_dev, L->cls, (size_t)L->n * L->n * L->n * sizeof(uint16_t), cudaMemcpyDeviceToDevice, s),
        "copy cell classes");
+    return RAYPC_OK;
+}
+
+raypc_status raypc_get_skip_distance(raypc_ctx* ctx, int vol, int lod, uint8_t* out_dev, void* stream) {
+    if (!ctx || !out_dev) return fail(RAYPC_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceGuard g(ctx->device);
+    Volume* V = nullptr;
+    raypc_status st = get_volume(ctx, vol, &V);
+    if (st) return st;
+    Level* L = nullptr;
+    if ((st = get_level(V, lod, &L))) return st;
+    if (V->stale) return fail(RAYPC_ERR_INVALID_ARG, "volume updated: raypc_build_bricks must run first");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_classified(V, *L, s))) return st;
+    RenderArgs a{};
+    a.skip = 1;
+    a.lv.sactive = L->sactive;
+    if ((st = ensure_distance(ctx, V, *L, a, false, s))) return st;
+    CK(cudaMemcpyAsync(out_dev, L->sdist, L->nsbricks(), cudaMemcpyDeviceToDevice, s), "copy skip distance");
     return RAYPC_OK;
 }
 

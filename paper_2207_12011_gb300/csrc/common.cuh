@@ -178,7 +178,12 @@ struct LevelArgs {
     const float* bmax;
     const uint32_t* active;    // bitmask, ceil(nb^3/32) words
     const uint32_t* sactive;   // sub-brick bitmask, ceil(nsb^3/32) words
+    const uint8_t* sdist;      // optional: empty-space distance of the sub-bricks under sactive (see
+                               // launch_subbrick_distance); renders with skipping jump by it
 };
+
+// Cap of the sub-brick empty-space distance (sub-bricks).
+constexpr int kDistCap = 8;
 
 // Implicit position axes (x, y, z, radius) usable in brushes and as PC axes;
 // PC axis id kPosAxisBase + a names position axis a.
@@ -607,6 +612,12 @@ struct TfVisArgs {
     uint32_t* out_sactive;
 };
 cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream);
+
+// Empty-space distance of the nsb^3 sub-bricks under the activity bits sactive:
+// Chebyshev distance in sub-bricks to the nearest active sub-brick, capped at
+// kDistCap, 0 for active ones (volume_kernels.cu). tmp: nsb^3 bytes of scratch.
+cudaError_t launch_subbrick_distance(const uint32_t* sactive, int nsb, uint8_t* dist, uint8_t* tmp,
+                                     cudaStream_t stream);
 
 // PC line subsample (pcsub_kernels.cu).
 constexpr int kSubMaxSegments = 8192;   // warp-owned row segments of the ordered compaction

@@ -1,6 +1,7 @@
 // Host-side exact helpers of the C-ABI runtime (plain C++, no CUDA): the
-// squared-radius thresholds that turn a radius brush into a |p|^2 range, and
-// the number of in-shell cells of a level.
+// squared-radius thresholds that turn a radius brush into a |p|^2 range, the
+// number of in-shell cells of a level, and the binary16 bounds that decide a
+// brush test of FP16 values exactly.
 #pragma once
 
 #include <algorithm>
@@ -62,6 +63,47 @@ inline unsigned long long count_in_shell(int n, int64_t s_in, int64_t s_out) {
             total += row > 0 ? (unsigned long long)row : 0ull;
         }
     return total;
+}
+
+// Value of an IEEE binary16 bit pattern as a float (exact: every binary16
+// value is a float).
+inline float half_bits_value(uint16_t h) {
+    const int e = (h >> 10) & 31, m = h & 1023;
+    float v;
+    if (e == 0) v = std::ldexp((float)m, -24);                 // zero or subnormal
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = std::ldexp((float)(m + 1024), e - 25);
+    return (h >> 15) ? -v : v;
+}
+
+// Binary16 bounds that decide comparisons against a float bound b exactly for
+// every binary16 value h: h >= b iff h >= half_ceil_bits(b), the smallest
+// binary16 value >= b, and h <= b iff h <= half_floor_bits(b), the largest <= b
+// (both may be an infinity; NaN h fails either way). Found by bisection over
+// the non-NaN binary16 patterns in increasing order: -inf .. -0 (0xFC00 down to
+// 0x8000), then +0 .. +inf (0x0000 up to 0x7C00). b must not be NaN.
+inline uint16_t half_of_order(uint32_t i) {
+    return i <= 0x7C00u ? (uint16_t)(0xFC00u - i) : (uint16_t)(i - 0x7C01u);
+}
+
+inline uint16_t half_ceil_bits(float b) {
+    uint32_t l = 0u, h = 2u * 0x7C01u - 1u;                  // order indices of -inf .. +inf
+    if (!(half_bits_value(half_of_order(h)) >= b)) return 0x7C00u;
+    while (l < h) {
+        const uint32_t m = l + (h - l) / 2;
+        if (half_bits_value(half_of_order(m)) >= b) h = m; else l = m + 1;
+    }
+    return half_of_order(l);
+}
+
+inline uint16_t half_floor_bits(float b) {
+    uint32_t l = 0u, h = 2u * 0x7C01u - 1u;
+    if (!(half_bits_value(half_of_order(l)) <= b)) return 0xFC00u;
+    while (l < h) {
+        const uint32_t m = l + (h - l + 1) / 2;
+        if (half_bits_value(half_of_order(m)) <= b) l = m; else h = m - 1;
+    }
+    return half_of_order(l);
 }
 
 }  // namespace raypc

@@ -16,16 +16,15 @@
 // memory) and composited front to back with early ray termination.
 //
 // The samples inside the inner core are jumped over analytically (exactly: see
-// the march). Empty-space skipping: when a sample falls in an inactive sub-brick, the ray
-// jumps over the rest of its box -- the whole 8^3 brick when that is inactive
-// too, else the 4^3 sub-brick. The last sample still inside the box is
-// estimated from the box's exit plane and then recomputed with the exact
-// per-sample arithmetic; the jump is taken only if that sample is in the box.
-// Along a ray every step from k to the cell index on one axis (t_k, position,
-// grid coordinate, clamp, floor, min) is monotone in k, so two samples in the
-// box enclose only samples in the box: skipping changes no decision and needs
-// no neighbour condition. The lattice itself (t_k = t0 + (k + j) dt, j = 1/2
-// except in jittered progressive passes) is never shifted by a jump.
+// the march). Empty-space skipping: when the samples of all lanes running
+// together fall in inactive sub-bricks whose empty-space distance is D >= 2
+// (every sub-brick within D - 1 is inactive), the lanes skip together by their
+// smallest count of samples that cannot leave that box of sub-bricks: the lattice moves the cell index by at most g cells per sample
+// on any axis (g = dt * n/2 * max |d_a|), so the next floor((4 (D - 1) -
+// 1/16) / g) samples stay in the box (1/16 cell covers the FP32 rounding of t,
+// the position and the grid coordinate) and are rejected without being
+// computed. The lattice itself (t_k = t0 + (k + j) dt, j = 1/2 except in
+// jittered progressive passes) is never shifted by a skip.
 #include "common.cuh"
 
 namespace raypc {
@@ -134,7 +133,7 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             const float sq = __fsqrt_rn(disc);
             const float t0 = fmaxf(__fsub_rn(-b, sq), 0.0f);
             const float t1 = __fadd_rn(-b, sq);
-            const int n = A.lv.n, nb = A.lv.nb, nsb = A.lv.nsb;
+            const int n = A.lv.n, nsb = A.lv.nsb;
             const float hn = 0.5f * (float)n, off = hn - 0.5f;
             const float dt = A.dt;
             const size_t sy_ = (size_t)n, sz_ = (size_t)n * n, plane = sz_ * n;
@@ -147,8 +146,8 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             int n_lat = max(0, (int)floorf((t1 - t0) * inv_dt - jo));
             while (n_lat > 0 && !(__fmaf_rn(__fadd_rn((float)(n_lat - 1), jo), dt, t0) < t1)) --n_lat;
             while (__fmaf_rn(__fadd_rn((float)n_lat, jo), dt, t0) < t1) ++n_lat;
-            const float inv_hn = 1.0f / hn;
-            const float idx = 1.0f / dx, idy = 1.0f / dy, idz = 1.0f / dz;
+            // grid cells the lattice advances per sample along the fastest axis
+            const float inv_g = 1.0f / (dt * hn * fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
             // Inner core: the samples core_a..core_b lie inside r_in and fail the shell
             // test, so the march jumps over them. The range comes from the core chord of
             // a slightly smaller sphere and is then verified with the per-sample FP32
@@ -231,38 +230,29 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 iy = grid_index_rn(pyw, n, hn, off, uy);
                 iz = grid_index_rn(pzw, n, hn, off, uz);
                 const uint32_t sid = ((uint32_t)(iz >> 2) * nsb + (iy >> 2)) * nsb + (ix >> 2);
-                if (!bit_of(A.lv.sactive, sid)) {
-                    if (A.skip) {
-                        const uint32_t bid = ((uint32_t)(iz >> 3) * nb + (iy >> 3)) * nb + (ix >> 3);
-                        const int sh = bit_of(A.lv.active, bid) ? 2 : 3;
-                        const int bw = 1 << sh;
-                        const int lo[3] = {(ix >> sh) << sh, (iy >> sh) << sh, (iz >> sh) << sh};
-                        const float dd[3] = {dx, dy, dz}, oo[3] = {ox, oy, oz}, ii[3] = {idx, idy, idz};
-                        // estimated exit time from the box (lower index in [lo, lo + bw) per axis)
-                        float te = __int_as_float(0x7f800000);
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            if (dd[a] > 0.0f && lo[a] + bw <= n - 2)
-                                te = fminf(te, (fmaf((float)(lo[a] + bw) + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
-                            else if (dd[a] < 0.0f && lo[a] > 0)
-                                te = fminf(te, (fmaf((float)lo[a] + 0.5f, inv_hn, -1.0f) - oo[a]) * ii[a]);
-                        }
-                        const float kk = fminf((te - t0) * inv_dt - jo, 1.0e9f);
-                        const int kl = kk > (float)(k + 1) ? min((int)ceilf(kk) - 1, k_last - 1) : k;
-                        if (kl > k) {
-                            // the estimated last sample, recomputed exactly
-                            const float tl = __fmaf_rn(__fadd_rn((float)kl, jo), dt, t0);
-                            float gx, gy, gz;
-                            const int jx = grid_index_rn(__fmaf_rn(tl, dx, ox), n, hn, off, gx);
-                            const int jy = grid_index_rn(__fmaf_rn(tl, dy, oy), n, hn, off, gy);
-                            const int jz = grid_index_rn(__fmaf_rn(tl, dz, oz), n, hn, off, gz);
-                            if (((jx ^ ix) >> sh) == 0 && ((jy ^ iy) >> sh) == 0 && ((jz ^ iz) >> sh) == 0) {
-                                skipped += (unsigned)(kl - k);
-                                k = kl + 1;
-                                continue;
-                            }
-                        }
+                const bool active = bit_of(A.lv.sactive, sid);
+                if (A.skip && A.lv.sdist) {
+                    // every sub-brick within D - 1 of an inactive one is inactive, so the cell
+                    // index stays in that box -- at least 4 (D - 1) cells beyond this sub-brick
+                    // on every side -- while the lattice moves it by less than 4 (D - 1) cells
+                    // per axis: by at most g cells per sample, with 1/16 cell kept for the FP32
+                    // rounding of t, the position and the grid coordinate. The lanes that run
+                    // together skip together, by their smallest safe count, so they stay on
+                    // neighbouring samples.
+                    int m = 0;
+                    if (!active) {
+                        const int D = __ldg(A.lv.sdist + sid);
+                        if (D >= 2) m = (int)(((float)(4 * D - 4) - 0.0625f) * inv_g);
+                        if (k + m >= 65536) m = 0;
                     }
+                    m = __reduce_min_sync(__activemask(), m);
+                    if (m > 0) {
+                        skipped += (unsigned)m;
+                        k += m + 1;
+                        continue;
+                    }
+                }
+                if (!active) {
                     ++k;
                     continue;
                 }

@@ -60,6 +60,9 @@ struct Level {
     uint16_t* cls = nullptr;      // cell classes under the current brush (n^3), computed on demand
     uint32_t* tf_active = nullptr;   // activity AND TF visibility (renders with tf_skip)
     uint32_t* tf_sactive = nullptr;
+    uint8_t* sdist = nullptr;        // empty-space distance of the sub-bricks (renders with skipping)
+    uint8_t* sdist_tmp = nullptr;
+    const uint32_t* sdist_of = nullptr;   // activity bits the distance was computed from (null: stale)
     bool cls_valid = false;
     bool bricks = false;
     bool classified = false;
@@ -88,6 +91,13 @@ struct Volume {
     int color_var = 0;
     float tf_lo = 0.f, tf_hi = 1.f;
     size_t bytes = 0;
+    // host-source updates: a staging buffer of the source's size, filled on a copy stream of
+    // the volume's own; ev_consumed marks the last ingest that read it
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied = nullptr, ev_consumed = nullptr;
+    bool consumed_pending = false;
 };
 
 inline size_t elem_size(int dtype) { return dtype == RAYPC_F16 ? 2 : 4; }

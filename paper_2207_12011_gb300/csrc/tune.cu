@@ -159,6 +159,9 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         void* slist = nullptr;
         if (e == cudaSuccess) e = cudaMalloc(&slist, L->nsbricks() * sizeof(uint32_t) + 16);
         if (e == cudaSuccess) temps.push_back(slist);
+        void* dist = nullptr;                 // empty-space distance (renders with skipping), + scratch
+        if (e == cudaSuccess) e = cudaMalloc(&dist, 2 * L->nsbricks() + 16);
+        if (e == cudaSuccess) temps.push_back(dist);
         if (e != cudaSuccess) { st = cuda_fail(e, "tuning buffers"); break; }
         ClassifyArgs c{};
         c.nlev = 2;
@@ -199,6 +202,9 @@ raypc_status raypc_autotune(raypc_ctx* ctx, const raypc_view* views, int nviews,
         if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning cell classes"); break; }
         args[i].cls = cc.out;
         args[i].pass_count = c.lv[0].pass_count;
+        ce = launch_subbrick_distance(args[i].lv.sactive, L->nsb, (uint8_t*)dist, (uint8_t*)dist + L->nsbricks(), s);
+        if (ce != cudaSuccess) { st = cuda_fail(ce, "tuning empty-space distance"); break; }
+        args[i].lv.sdist = (const uint8_t*)dist;
     }
     if (st != RAYPC_OK) {
         free_temps();

@@ -559,6 +559,48 @@ __global__ void __launch_bounds__(256) k_tf_visibility(TfVisArgs A) {
 
 }  // namespace
 
+// Empty-space distance of the 4^3 sub-bricks: the Chebyshev distance, in
+// sub-bricks, to the nearest active one, capped at kDistCap (0: active). The L-inf
+// distance transform is separable: d(p) = min over qz of max(|dz|, min over qy of
+// max(|dy|, min over active qx of |dx|)), each 1D pass a window of +-kDistCap.
+// pass 0: x from the activity bits into a; 1: y from a into b; 2: z from b into a.
+__global__ void __launch_bounds__(256) k_subbrick_distance(const uint32_t* __restrict__ act, int nsb, int pass,
+                                                           const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
+    const size_t total = (size_t)nsb * nsb * nsb;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    const int x = (int)(id % nsb), y = (int)((id / nsb) % nsb), z = (int)(id / ((size_t)nsb * nsb));
+    int d = kDistCap;
+    if (pass == 0) {
+        for (int o = -kDistCap; o <= kDistCap; ++o) {
+            const int xx = x + o;
+            if (xx < 0 || xx >= nsb) continue;
+            const size_t q = id - x + xx;
+            if ((__ldg(act + (q >> 5)) >> (q & 31)) & 1u) d = min(d, abs(o));
+        }
+    } else {
+        const int c = pass == 1 ? y : z;
+        const size_t stride = pass == 1 ? (size_t)nsb : (size_t)nsb * nsb;
+        for (int o = -kDistCap; o <= kDistCap; ++o) {
+            const int cc = c + o;
+            if (cc < 0 || cc >= nsb) continue;
+            d = min(d, max(abs(o), (int)__ldg(in + (size_t)((long long)id + (long long)o * (long long)stride))));
+        }
+    }
+    out[id] = (uint8_t)d;
+}
+
+cudaError_t launch_subbrick_distance(const uint32_t* sactive, int nsb, uint8_t* dist, uint8_t* tmp,
+                                     cudaStream_t stream) {
+    const size_t total = (size_t)nsb * nsb * nsb;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    k_subbrick_distance<<<blocks, 256, 0, stream>>>(sactive, nsb, 0, nullptr, dist);
+    k_subbrick_distance<<<blocks, 256, 0, stream>>>(sactive, nsb, 1, dist, tmp);
+    k_subbrick_distance<<<blocks, 256, 0, stream>>>(sactive, nsb, 2, tmp, dist);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream) {
     const size_t nbr = (size_t)a.nb * a.nb * a.nb, nsub = (size_t)a.nsb * a.nsb * a.nsb;
     const size_t total = ((nbr + 31) & ~(size_t)31) + nsub;

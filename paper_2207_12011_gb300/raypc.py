@@ -121,6 +121,7 @@ _SIGS = {
     "raypc_get_bricks": [_P, _I, _I, _P, _P, _P],
     "raypc_get_skip_list": [_P, _I, _I, _P, _P, _P, _P, _P],
     "raypc_get_sub_bricks": [_P, _I, _I, _P, _P, _P, _P],
+    "raypc_get_skip_distance": [_P, _I, _I, _P, _P],
     "raypc_get_cell_classes": [_P, _I, _I, _P, _P],
     "raypc_batch_create": [_P, _I, ctypes.POINTER(_P)],
     "raypc_batch_destroy": [_P],
@@ -489,6 +490,16 @@ class Volume:
               ctypes.c_void_p(mx.data_ptr()), ctypes.c_void_p(act.data_ptr() if classify else None),
               _stream(stream))
         return mn, mx, act
+
+
+    def skip_distance(self, lod: int = 0, stream=None) -> torch.Tensor:
+        """Empty-space distance of the 4^3 sub-bricks under the current brush -> uint8 [nsb,nsb,nsb]."""
+        info = self.info(lod)
+        nsb = (info.n + 3) // 4
+        out = torch.empty((nsb, nsb, nsb), dtype=torch.uint8, device=torch.device("cuda", self.ctx.device))
+        _call("raypc_get_skip_distance", self.ctx.handle, self.id, int(lod), ctypes.c_void_p(out.data_ptr()),
+              _stream(stream))
+        return out
 
 
 def _noalloc_args(cells, axis_order, edges, lo, hi, out, cuda: bool = True):

@@ -67,6 +67,38 @@ def bits(rp, words, nbits):
 # ----------------------------------------------------------------------------
 # ingest, LOD, bricks, classification
 # ----------------------------------------------------------------------------
+def test_update_from_host_sources(ctx):
+    """raypc_update_volume from host sources copies through the volume's staging buffer on its
+    own copy stream; time steps updated back to back (pinned, then pageable, an FP16 source),
+    each followed by a rebuild and a render that the next copy overlaps, leave exactly the values
+    and images of a volume loaded from the device, and bricks equal to the oracle's."""
+    n = 40
+    steps = [synth.make_shell_volume(n, seed=31 + t) for t in range(3)]
+    brush = synth.make_brush(steps[0], "c2")
+    tf = synth.make_tf(steps[0], "v_r")
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    v = load(ctx, steps[0], "f16", n_lod=1, brush=brush, tf=tf)
+    srcs = [steps[1].pin_memory(), steps[2], steps[1].half().pin_memory(), steps[2].pin_memory()]
+    imgs = []
+    for src in srcs:
+        v.update(src)
+        v.build_bricks(n_lod=1)
+        v.set_brush(brush.lo, brush.hi, brush.active_mask)
+        img, _ = v.render(cam, 64, 48)
+        imgs.append(img)
+    torch.cuda.synchronize()
+    for src, img in zip(srcs, imgs):
+        ref = load(ctx, src.float().cuda(), "f16", n_lod=1, brush=brush, tf=tf)
+        rimg, _ = ref.render(cam, 64, 48)
+        assert torch.equal(img, rimg)
+        ref.free()
+    assert torch.equal(v.export().cpu(), synth.to_storage(steps[2], "f16"))
+    mn, mx = v.bricks()
+    omn, omx = oracle.brick_minmax(stored(steps[2], "f16"))
+    assert np.array_equal(mn.cpu().numpy(), omn) and np.array_equal(mx.cpu().numpy(), omx)
+    v.free()
+
+
 @pytest.mark.parametrize("store", ["f32", "f16"])
 @pytest.mark.parametrize("n,nvars", [(37, 6), (16, 3), (2, 1), (4, 2), (68, 2)])
 def test_ingest_roundtrip(ctx, store, n, nvars):
@@ -257,6 +289,74 @@ def test_skipping_never_changes_the_image(ctx):
         assert stats[True][0] == stats[False][0]                   # same marched lattice samples
         assert stats[True][0] == int(outs[True][1][..., 0].sum())
         assert stats[True][2] == int(outs[True][1][..., 1].sum())
+        v.free()
+
+
+def _chebyshev_distance_brute(active: np.ndarray, cap: int = 8) -> np.ndarray:
+    """Chebyshev distance (in sub-bricks) of every sub-brick to the nearest active one, capped:
+    grow the active set by one 3x3x3 dilation per step."""
+    d = np.full(active.shape, cap, np.uint8)
+    cur = active.astype(bool)
+    d[cur] = 0
+    for r in range(1, cap):
+        pad = np.pad(cur, 1)
+        grown = np.zeros_like(cur)
+        m = cur.shape[0]
+        for dz in range(3):
+            for dy in range(3):
+                for dx in range(3):
+                    grown |= pad[dz:dz + m, dy:dy + m, dx:dx + m]
+        cur = grown
+        d[(d == cap) & cur] = r
+    return d
+
+
+@pytest.mark.parametrize("n,store", [(128, "f32"), (60, "f16")])
+def test_skip_distance_and_skipping_keep_every_decision(ctx, rp, n, store):
+    """The empty-space distance equals a brute-force Chebyshev distance over the sub-brick
+    activity bits, and renders with the distance skip give the same pixels and per-pixel
+    counts as renders without it -- and as the oracle with ERT off -- for oblique and
+    axis-aligned rays, default, coarse and fine steps, TF-aware skipping and a jittered pass."""
+    vol = synth.make_shell_volume(n, seed=19)
+    tf = synth.make_tf(vol, "T_anom")
+    st_np = stored(vol, store)
+    nsb = (n + 3) // 4
+    cams = [synth.orbit_camera(40, 10, 2.9), synth.orbit_camera(0, 0, 2.7), synth.orbit_camera(90, 0, 3.1),
+            synth.orbit_camera(200, -55, 2.6)]
+    for bname in ("c1", "c2", "c3"):
+        brush = synth.make_brush(vol, bname)
+        v = load(ctx, vol, store, brush=brush, tf=tf)
+        _, _, act = v.sub_bricks()
+        active = bits(rp, act, nsb ** 3).reshape(nsb, nsb, nsb)
+        dist = v.skip_distance().cpu().numpy()
+        assert np.array_equal(dist, _chebyshev_distance_brute(active)), bname
+        skipped = 0
+        for ci, cam in enumerate(cams):
+            for step in (0.0, 2.0 / n, 1.0 / (8 * n)):
+                if step and ci % 2:
+                    continue
+                res = {}
+                for skip in (True, False):
+                    stt = torch.zeros(8, dtype=torch.int64, device="cuda")
+                    img, cnt = v.render(cam, 61, 47, skip=skip, counts=True, stats=stt, step=step, ert=False)
+                    res[skip] = (img, cnt, stt.cpu().numpy())
+                assert torch.equal(res[True][0], res[False][0]) and torch.equal(res[True][1], res[False][1])
+                assert res[True][2][0] == res[False][2][0]
+                skipped += int(res[True][2][3])
+                if step == 0.0 and ci < 2:
+                    ref, rc = oracle.render(st_np, R_IN, R_OUT, cam.as_array(), 61, 47, 1.0 / n, brush.lo, brush.hi,
+                                            brush.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=False)
+                    assert np.array_equal(res[True][1].cpu().numpy().astype(np.uint32), rc)
+                    assert np.abs(res[True][0].cpu().numpy() - ref).max() <= (1e-3 if store == "f32" else 4e-3)
+        # TF-aware skipping and a jittered progressive pass, with and without the distance skip
+        for skip in (True, False):
+            a, ca = v.render(cams[0], 61, 47, skip=skip, counts=True, tf_skip=True, ert=False)
+            b, cb = v.render_progressive(cams[0], 61, 47, 3, 2, None, skip=skip, counts=True, ert=False)
+            res[("tf", skip)] = (a, ca, b, cb)
+        for i in range(4):
+            assert torch.equal(res[("tf", True)][i], res[("tf", False)][i])
+        if n >= 128 and bname != "c2":
+            assert skipped > 0, bname                              # the distance skip was taken
         v.free()
 
 
@@ -552,6 +652,44 @@ def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
             assert np.array_equal(H, Ho), (bname, order, use)
             assert cells > 0 and all(int(H[p].sum()) == cells for p in range(H.shape[0]))
         v.free()
+
+
+def test_histogram_fp16_bounds_between_and_at_half_values(ctx):
+    """FP16 fields are tested two cells at a time against binary16 bounds (the smallest
+    half >= lo, the largest half <= hi); bounds at, just below and just above stored values,
+    beyond the binary16 range, and NaN / infinite cells must count exactly what the oracle's
+    FP32 comparison counts."""
+    n = 48
+    vol = synth.make_shell_volume(n, seed=23)
+    vol[0, 20, 20:30, 10:20] = float("nan")
+    vol[1, 30, 5:9, 20:40] = float("inf")
+    vol[2, 25, 10:12, :] = -float("inf")
+    vol[3, 10:14, 24, 30:34] = 7.0e4                       # beyond the binary16 range: +inf stored
+    st = stored(vol, "f16")
+    order = (0, 1, 2, 3, 4, 5)
+    edges = synth.make_edges(torch.from_numpy(np.nan_to_num(st, nan=0.0, posinf=0.0, neginf=0.0)), order, bins=128)
+    base = synth.make_brush(torch.from_numpy(np.nan_to_num(st, nan=0.0, posinf=0.0, neginf=0.0)), "c3")
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        lo, hi = base.lo.copy(), base.hi.copy()
+        for v in range(6):
+            if not (base.active_mask >> v) & 1:
+                continue
+            kind = (trial + v) % 4
+            if kind == 1:                                      # just above / below a stored value
+                lo[v] = np.nextafter(np.float32(lo[v]), np.float32(np.inf)) if np.isfinite(lo[v]) else lo[v]
+                hi[v] = np.nextafter(np.float32(hi[v]), np.float32(-np.inf)) if np.isfinite(hi[v]) else hi[v]
+            elif kind == 2:                                    # between two binary16 values
+                lo[v] = np.float32(lo[v] + rng.uniform(-1e-3, 1e-3)) if np.isfinite(lo[v]) else lo[v]
+                hi[v] = np.float32(hi[v] + rng.uniform(-1e-3, 1e-3)) if np.isfinite(hi[v]) else hi[v]
+            elif kind == 3:                                    # open above the binary16 range
+                hi[v] = np.float32(6.6e4) if trial % 2 else np.float32(np.inf)
+        v16 = load(ctx, vol, "f16", brush=synth.Brush(lo, hi, base.active_mask))
+        H = v16.pc_histogram(order, edges, use_brush=True).cpu().numpy().astype(np.uint32)
+        Ho, cells = oracle.histogram(st, R_IN, R_OUT, lo, hi, base.active_mask, order, edges, use_brush=True)
+        assert np.array_equal(H, Ho), trial
+        assert cells > 0
+        v16.free()
 
 
 @pytest.mark.parametrize("n,store,bname", [(48, "f32", "c2"), (33, "f16", "c1")])

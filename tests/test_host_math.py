@@ -1,5 +1,6 @@
 """Exact host helpers of the library (CPU): the squared-radius thresholds of the
-radius brush and the in-shell cell count of a level, against brute force."""
+radius brush, the in-shell cell count of a level and the binary16 brush bounds,
+against brute force."""
 from __future__ import annotations
 
 import os
@@ -15,6 +16,7 @@ PROGRAM = r"""
 #include <cstdio>
 #include <cmath>
 #include <random>
+#include <vector>
 #include "host_math.h"
 
 int main() {
@@ -62,6 +64,23 @@ int main() {
         }
     }
     printf("count %d\n", cbad);
+    // binary16 bounds: for every non-NaN half h, (h >= b) == (h >= ceil(b)) and (h <= b) == (h <= floor(b))
+    int hbad = 0;
+    std::vector<float> bounds = {0.0f, -0.0f, 1.0f, -1.0f, 65504.0f, 65520.0f, 70000.0f, -70000.0f, 1e-8f, -1e-8f,
+                                 5.96e-8f, 6.1e-5f, INFINITY, -INFINITY, 0.3333333f, 2049.0f, 2050.5f, 1e30f, -1e30f};
+    std::uniform_real_distribution<float> W(-3.0f, 3.0f);
+    for (int i = 0; i < 300; ++i) bounds.push_back(W(rng));
+    for (int i = 0; i < 60; ++i) bounds.push_back(raypc::half_bits_value((uint16_t)(rng() & 0x7BFF)) * ((i & 1) ? -1.0f : 1.0f));
+    for (float b : bounds) {
+        const float c = raypc::half_bits_value(raypc::half_ceil_bits(b)), f = raypc::half_bits_value(raypc::half_floor_bits(b));
+        for (uint32_t bits = 0; bits < 65536u; ++bits) {
+            const float h = raypc::half_bits_value((uint16_t)bits);
+            if (std::isnan(h)) continue;
+            if ((h >= b) != (h >= c)) ++hbad;
+            if ((h <= b) != (h <= f)) ++hbad;
+        }
+    }
+    printf("half %d\n", hbad);
     return 0;
 }
 """
@@ -76,4 +95,4 @@ def test_host_math_against_brute_force(tmp_path):
     if r.returncode != 0:
         pytest.fail(r.stderr)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    assert out == ["radius", "0", "count", "0"], out
+    assert out == ["radius", "0", "count", "0", "half", "0"], out
