@@ -138,29 +138,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def render_code_hash():
-    """sha256 prefix of the render kernels' code (render_kernels.cu and the shared
-    common.cuh): comments removed and whitespace collapsed, so that a comment edit
-    does not void a profile of unchanged code."""
+def code_hash(files=("render_kernels.cu", "common.cuh")):
+    """sha256 prefix of kernel source files (comments removed and whitespace collapsed, so
+    that a comment edit does not void a profile of unchanged code)."""
     import hashlib
     import re
     csrc = os.path.join(ROOT, "paper_2207_12011_gb300", "csrc")
-    src = "".join(open(os.path.join(csrc, f)).read() for f in ("render_kernels.cu", "common.cuh"))
+    src = "".join(open(os.path.join(csrc, f)).read() for f in files)
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
 
 
-def profiled(field):
-    """A per-launch figure of the render kernel from the committed ncu summary
-    (`traffic_bytes_per_launch`, `warp_instructions_per_launch`), if the kernel
-    code is unchanged since the capture; else None."""
+def render_code_hash():
+    return code_hash(("render_kernels.cu", "common.cuh"))
+
+
+PROFILE_SOURCES = {"k_render": ("render_kernels.cu", "common.cuh"), "k_hist": ("hist_kernels.cu", "common.cuh")}
+
+
+def profiled(field, profile="k_render_shell256_f32.md", kernel="k_render"):
+    """A per-launch figure (`traffic_bytes_per_launch`, `warp_instructions_per_launch`) from a
+    committed ncu summary under profiles/, if the kernel's code is unchanged since the capture;
+    else None."""
     import re
     try:
-        text = open(os.path.join(ROOT, "profiles", "k_render_shell256_f32.md")).read()
+        text = open(os.path.join(ROOT, "profiles", profile)).read()
         m = re.search(r"code sha256 prefix at capture: ([0-9a-f]{16})", text)
         t = re.search(field + r" \| (\d+)", text)
-        if m and t and m.group(1) == render_code_hash():
+        if m and t and m.group(1) == code_hash(PROFILE_SOURCES[kernel]):
             return int(t.group(1))
     except OSError:
         pass
@@ -192,6 +198,13 @@ class Workload:
         self.cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
         self.edges = synth.make_edges(stored, c["order"], bins=c["bins"])
         del stored
+
+    def l2_note(self):
+        c = self.cfg
+        src = c["n"] ** 3 * 6 * 4
+        stored = c["n"] ** 3 * 6 * (2 if c["store"] == "f16" else 4) * 3      # planar + x-pair layouts
+        return (f"inputs larger than L2 ({src / 1e6:.0f} MB FP32 source re-ingested into {stored / 1e6:.0f} MB "
+                "of stored layouts every step)")
 
     def describe(self):
         c = self.cfg
@@ -352,10 +365,12 @@ def config_section(rp, name, args, dev, seed, rank):
            "lattice_samples_per_s_render": round(float(st[0]) / (render_ms / 1e3), 1),
            "roofline": {"kernel": "k_render", "bound": "hbm", "achieved": round(alg / render_ms / 1e6, 1),
                         "peak": peak, "unit": "GB/s", "frac": round(alg / render_ms / 1e6 / peak, 4),
+                        "traffic": profiled("traffic_bytes_per_launch", f"k_render_{name}.md", "k_render"),
                         "alg_bytes_per_launch": int(alg), "active_bricks": n_active,
                         "peak_kind": f"{peak_kind} HBM copy"},
            "roofline_histogram": {"kernel": "k_hist", "bound": "hbm", "achieved": round(hist_bytes / hist_ms / 1e6, 1),
                                   "peak": peak, "unit": "GB/s", "frac": round(hist_bytes / hist_ms / 1e6 / peak, 4),
+                                  "traffic": profiled("traffic_bytes_per_launch", f"k_hist_{name}.md", "k_hist"),
                                   "alg_bytes_per_launch": int(hist_bytes), "peak_kind": f"{peak_kind} HBM copy"}}
     if rank == 0 and not args.no_accuracy:
         vol.render(wl.cam, c["w"], c["h"], out=img)
@@ -621,11 +636,11 @@ def run_ours(args):
     alg_bytes = n_active * 8 ** 3 * 6 * elem + c["w"] * c["h"] * 16
     achieved = alg_bytes / (render_ms / 1e3) / 1e9
     roofline = {"kernel": "k_render", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled("traffic_bytes_per_launch"),
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled("traffic_bytes_per_launch", f"k_render_{args.workload}.md"),
                 "peak_kind": f"{peak_kind} HBM copy", "render_ms": round(render_ms, 4),
                 "alg_bytes_per_launch": alg_bytes, "active_bricks": n_active}
     # the roof that binds the render: warp-instruction issue (4 schedulers per SM)
-    insts = profiled("warp_instructions_per_launch")
+    insts = profiled("warp_instructions_per_launch", f"k_render_{args.workload}.md")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clk.get("sm_mhz") or 2070.0
     issue_peak = sms * 4 * mhz * 1e6 / 1e9
@@ -641,7 +656,8 @@ def run_ours(args):
     hist_bytes = c["n"] ** 3 * wl.src.shape[0] * elem + (len(c["order"]) - 1) * c["bins"] ** 2 * 4
     hist_gbs = hist_bytes / (hist_ms / 1e3) / 1e9
     roofline_hist = {"kernel": "k_hist", "bound": "hbm", "achieved": round(hist_gbs, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(hist_gbs / peak, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(hist_gbs / peak, 4),
+                     "traffic": profiled("traffic_bytes_per_launch", f"k_hist_{args.workload}.md", "k_hist"),
                      "peak_kind": f"{peak_kind} HBM copy", "hist_ms": round(hist_ms, 4),
                      "alg_bytes_per_launch": int(hist_bytes),
                      "note": "CUDA events around the raypc_pc_histogram call: its output clear (memset) and the "
@@ -652,8 +668,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "frames_per_s": round(1e3 / ms_per_step, 2),
-        "config": {**wl.describe(), "parallelism": f"replicas{ws}",
-                   "l2": "inputs larger than L2 (403 MB FP32 source re-ingested into a 537 MB stored volume every step)"},
+        "config": {**wl.describe(), "parallelism": f"replicas{ws}", "l2": wl.l2_note()},
         "samples_per_step": samples / args.steps,
         "frame_only": {"ms": round(frame_ms, 4), "fps": round(1e3 / frame_ms, 2),
                        "samples_per_s": round(float(fstats[0].item()) / (frame_ms * nframes / 1e3), 1),

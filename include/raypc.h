@@ -187,14 +187,14 @@ raypc_status raypc_free_volume(raypc_ctx *ctx, int vol);
  * (e.g. the next time step of the simulation, Section 2.1), with the source
  * layout and conversion of raypc_load_volume. A device source allocates
  * nothing and must stay valid until `stream` reaches the ingest. A host
- * source goes through a staging buffer of the source's size that the volume
- * keeps (allocated by the first host update, charged to the HBM budget, freed
- * with the volume; if the budget has no room, a stream-ordered temporary is
- * used instead). The host-to-device copy runs on a copy stream of the
- * volume's own that waits only until the previous update's ingest has read
- * the staging buffer, so the copy of the next time step overlaps the work
- * still running on `stream` (from a pinned source); `stream` waits for the
- * copy before the ingest. A pageable host source is consumed before the call
+ * source goes through two staging buffers of the source's size that the
+ * volume keeps and uses in turn (allocated by the first host update, charged
+ * to the HBM budget, freed with the volume; if the budget has no room, a
+ * stream-ordered temporary is used instead). The host-to-device copy runs on
+ * a copy stream of the volume's own that waits only until the ingest two
+ * updates back has read its buffer, so the copies of consecutive time steps
+ * run back to back and overlap the work still running on `stream` (from a
+ * pinned source); `stream` waits for the copy before the ingest. A pageable host source is consumed before the call
  * returns; a pinned host source must stay unchanged until the work this call
  * enqueues on `stream` has completed. Coarser levels, bricks and the
  * classification become stale: raypc_build_bricks must run again before

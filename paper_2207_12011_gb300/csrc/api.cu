@@ -73,15 +73,19 @@ void free_bricks(Level& L) {
 }
 
 void free_staging(Volume* V) {
-    if (V->staging) cudaFree(V->staging);
+    for (int i = 0; i < 2; ++i) {
+        if (V->staging[i]) cudaFree(V->staging[i]);
+        if (V->ev_consumed[i]) cudaEventDestroy(V->ev_consumed[i]);
+        V->staging[i] = nullptr;
+        V->ev_consumed[i] = nullptr;
+        V->consumed_pending[i] = false;
+    }
     if (V->ev_copied) cudaEventDestroy(V->ev_copied);
-    if (V->ev_consumed) cudaEventDestroy(V->ev_consumed);
     if (V->copy_stream) cudaStreamDestroy(V->copy_stream);
-    V->staging = nullptr;
     V->staging_bytes = 0;
-    V->ev_copied = V->ev_consumed = nullptr;
+    V->stage_next = 0;
+    V->ev_copied = nullptr;
     V->copy_stream = nullptr;
-    V->consumed_pending = false;
 }
 
 void free_volume(raypc_ctx* ctx, Volume* V) {
@@ -171,44 +175,58 @@ raypc_status alloc_bricks(raypc_ctx* ctx, Volume* V, Level& L) {
     return RAYPC_OK;
 }
 
-// Staging of a host source for raypc_update_volume: the volume's own buffer and copy stream
-// (created on first use, charged to the budget). The copy waits only for the previous ingest to
-// have read the buffer, so the next time step's copy overlaps whatever still runs on the
-// caller's stream; the caller's stream waits for the copy. Returns false when the buffer cannot
-// be had (budget), and the caller falls back to a stream-ordered temporary.
+// Staging of a host source for raypc_update_volume: two buffers of the volume's own, used in
+// turn, and its copy stream (created on first use, charged to the budget). The copy into a
+// buffer waits only until the ingest two updates back has read it, so consecutive time steps'
+// copies run back to back and overlap whatever runs on the caller's stream; the caller's stream
+// waits for the copy. Returns false when the buffers cannot be had (budget), and the caller
+// falls back to a stream-ordered temporary.
 bool stage_host_source(raypc_ctx* ctx, Volume* V, const void* src, size_t bytes, cudaStream_t s,
-                       const void** dsrc, raypc_status* st) {
+                       const void** dsrc, int* slot, raypc_status* st) {
     *st = RAYPC_OK;
     if (V->staging_bytes != bytes) {
-        if (V->staging) {
-            cudaStreamSynchronize(V->copy_stream);
-            if (V->consumed_pending) cudaEventSynchronize(V->ev_consumed);
-            cudaFree(V->staging);
-            V->bytes -= V->staging_bytes;
-            ctx->used -= V->staging_bytes < ctx->used ? V->staging_bytes : ctx->used;
-            V->staging = nullptr;
-            V->staging_bytes = 0;
-            V->consumed_pending = false;
+        if (V->copy_stream) cudaStreamSynchronize(V->copy_stream);
+        for (int i = 0; i < 2; ++i) {
+            if (V->consumed_pending[i]) cudaEventSynchronize(V->ev_consumed[i]);
+            if (V->staging[i]) cudaFree(V->staging[i]);
+            V->staging[i] = nullptr;
+            V->consumed_pending[i] = false;
         }
-        if (ctx->alloc(&V->staging, bytes, &V->bytes) != RAYPC_OK) {
+        V->bytes -= 2 * V->staging_bytes < V->bytes ? 2 * V->staging_bytes : V->bytes;
+        ctx->used -= 2 * V->staging_bytes < ctx->used ? 2 * V->staging_bytes : ctx->used;
+        V->staging_bytes = 0;
+        if (ctx->alloc(&V->staging[0], bytes, &V->bytes) != RAYPC_OK) {
             cudaGetLastError();
             return false;
         }
+        if (ctx->alloc(&V->staging[1], bytes, &V->bytes) != RAYPC_OK) {
+            cudaGetLastError();
+            cudaFree(V->staging[0]);
+            V->staging[0] = nullptr;
+            V->bytes -= bytes < V->bytes ? bytes : V->bytes;
+            ctx->used -= bytes < ctx->used ? bytes : ctx->used;
+            return false;
+        }
         V->staging_bytes = bytes;
+        V->stage_next = 0;
     }
+    const int i = V->stage_next;
     cudaError_t e = cudaSuccess;
     if (!V->copy_stream) e = cudaStreamCreateWithFlags(&V->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess && !V->ev_copied) e = cudaEventCreateWithFlags(&V->ev_copied, cudaEventDisableTiming);
-    if (e == cudaSuccess && !V->ev_consumed) e = cudaEventCreateWithFlags(&V->ev_consumed, cudaEventDisableTiming);
-    if (e == cudaSuccess && V->consumed_pending) e = cudaStreamWaitEvent(V->copy_stream, V->ev_consumed, 0);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(V->staging, src, bytes, cudaMemcpyHostToDevice, V->copy_stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        if (!V->ev_consumed[k]) e = cudaEventCreateWithFlags(&V->ev_consumed[k], cudaEventDisableTiming);
+    if (e == cudaSuccess && V->consumed_pending[i]) e = cudaStreamWaitEvent(V->copy_stream, V->ev_consumed[i], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(V->staging[i], src, bytes, cudaMemcpyHostToDevice, V->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(V->ev_copied, V->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, V->ev_copied, 0);
     if (e != cudaSuccess) {
         *st = cuda_fail(e, "host to device copy");
         return true;
     }
-    *dsrc = V->staging;
+    *dsrc = V->staging[i];
+    *slot = i;
+    V->stage_next = i ^ 1;
     return true;
 }
 
@@ -220,9 +238,10 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
     void* staging = nullptr;
     cudaError_t e;
     bool staged = false;
+    int slot = 0;
     if (!src_is_device && own_staging) {
         raypc_status st;
-        staged = stage_host_source(ctx, V, src, nvox * V->nvars * elem_size(src_dtype), s, &dsrc, &st);
+        staged = stage_host_source(ctx, V, src, nvox * V->nvars * elem_size(src_dtype), s, &dsrc, &slot, &st);
         if (st != RAYPC_OK) return st;
     }
     if (!src_is_device && !staged) {
@@ -237,8 +256,8 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
                       L.sbmax, s);
     if (staging) cudaFreeAsync(staging, s);
     if (staged && e == cudaSuccess) {
-        e = cudaEventRecord(V->ev_consumed, s);       // the staging buffer is free once this ingest ran
-        V->consumed_pending = e == cudaSuccess;
+        e = cudaEventRecord(V->ev_consumed[slot], s);  // the staging buffer is free once this ingest ran
+        V->consumed_pending[slot] = e == cudaSuccess;
     }
     if (e != cudaSuccess) return cuda_fail(e, "ingest kernel");
     L.bricks = true;               // level-0 brick min/max come out of the ingest pass
@@ -815,14 +834,29 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         CK(cudaMallocAsync((void**)&dedges, sizeof(float) * ne, s), "edge buffer");
         e = cudaMemcpyAsync(dedges, edges, sizeof(float) * ne, cudaMemcpyHostToDevice, s);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(out_counts_dev, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
+    // hot bins of large grids: the blocks spread their atomics over zeroed copies in stream-ordered
+    // scratch, summed into the output afterwards (which then needs no clearing)
+    const size_t count = (size_t)(naxes - 1) * bins * bins;
+    const int ncopies = ((uintptr_t)out_counts_dev & 15u) ? 1 : hist_copies(L->n, naxes, bins);
+    const size_t copy_bytes = sizeof(uint32_t) * count * ncopies;
+    uint32_t* copies = nullptr;
+    if (e == cudaSuccess && ncopies > 1) {
+        e = cudaMallocAsync((void**)&copies, copy_bytes, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(copies, 0, copy_bytes, s);
+    } else if (e == cudaSuccess) {
+        e = cudaMemsetAsync(out_counts_dev, 0, sizeof(uint32_t) * count, s);
+    }
     if (e == cudaSuccess) {
         h.edges = dedges;
         h.out = out_counts_dev;
+        h.copies = copies;
+        h.ncopies = copies ? ncopies : 1;
         h.sactive = use_activity ? L->sactive : nullptr;
         h.nsb = L->nsb;
         e = launch_histogram(h, V->dtype, s);
+        if (e == cudaSuccess && copies) e = launch_histogram_reduce(copies, ncopies, count, out_counts_dev, s);
     }
+    if (copies) cudaFreeAsync(copies, s);
     if (dedges) cudaFreeAsync(dedges, s);
     if (e != cudaSuccess) return cuda_fail(e, "histogram");
     return RAYPC_OK;

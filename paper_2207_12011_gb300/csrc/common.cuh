@@ -300,6 +300,16 @@ __host__ __device__ constexpr int warp_tile_w(int variant) { return variant == 2
 __host__ __device__ constexpr int block_tile_w(int variant) { return 2 * warp_tile_w(variant); }
 __host__ __device__ constexpr int block_tile_h(int variant) { return 2 * (32 / warp_tile_w(variant)); }
 
+// Partial histograms of a spread-out histogram call: enough copies that the
+// hottest bins of a smooth field no longer serialise the L2 atomics, within
+// kHistCopyBytes of scratch.
+constexpr int kHistMaxCopies = 16;
+constexpr size_t kHistCopyBytes = (size_t)32 << 20;
+int hist_copies(int n, int naxes, int bins);
+// Sums the copies into out (launch after launch_histogram on the same stream).
+cudaError_t launch_histogram_reduce(const uint32_t* copies, int ncopies, size_t count, uint32_t* out,
+                                    cudaStream_t stream);
+
 // Histogram edge tables of at most this many floats (8 axes x 257 edges) are
 // passed to the kernel in its launch parameters; larger ones need a device copy.
 constexpr int kHistInlineEdges = 8 * 257;
@@ -319,6 +329,8 @@ struct HistArgs {
     float guess_scale[kMaxVars];  // starting guess of the bin walk (any value is correct)
     int64_t s_in, s_out;
     uint32_t* out;                // (naxes-1) x bins x bins
+    uint32_t* copies;             // optional: ncopies zeroed partial histograms that the blocks spread
+    int ncopies;                  // their atomics over (hot bins), summed into out afterwards
     const uint32_t* sactive;      // optional: 4^3 sub-brick activity under this brush (cells of inactive
     int nsb;                      // sub-bricks are never counted), sub-bricks per axis
 };

@@ -29,8 +29,10 @@ namespace raypc {
 
 namespace {
 
-constexpr int kHistThreads = 256;
+constexpr int kHistThreads = 256;                    // scalar kernel
 constexpr int kHistWarps = kHistThreads / 32;
+constexpr int kHistVecThreads = 512;                 // vector kernel (two resident blocks per SM)
+constexpr int kHistVecWarps = kHistVecThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Number of interior edges e_1..e_{bins-1} that are <= v, for non-decreasing
@@ -41,7 +43,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // lands in bin 0.
 __device__ __forceinline__ int bin_of(const float* e, int bins, float v, float e0, float scale) {
     if (v != v) return 0;
-    float g = (v - e0) * scale;
+    float g = fmaf(v, scale, -e0 * scale);                 // any guess is verified below
     g = fminf(fmaxf(g, 0.0f), (float)(bins - 1));
     int j = (int)g;
     const float lo = e[j], hi = e[j + 1];
@@ -100,7 +102,8 @@ struct HistLaunch {
     uint32_t slo_h2[kMaxVars], shi_h2[kMaxVars];   // FP16 fields: the same bounds as binary16 pairs
     float guess_e0[kMaxVars], guess_scale[kMaxVars];
     int s_in, s_out;               // shell test on 2x+1-n etc., clamped to int
-    uint32_t* out;
+    uint32_t* out;                 // nout histograms; block b adds to copy b % nout
+    int nout;
     const uint32_t* sactive;       // optional sub-brick activity (see HistArgs)
     int nsb;
     const float* edges;            // naxes x (bins + 1) on the device, or null: edges_inl
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scalar(const __grid_const
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int bins = A.bins;
     const size_t plane = (size_t)n * n * n;
+    uint32_t* const out = A.out + (size_t)(blockIdx.x % (unsigned)A.nout) * (A.naxes - 1) * bins * bins;
 
     for (int r = gwarp; r < rows; r += nwarps) {
         RowSpan R;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scalar(const __grid_const
                                                            : load_cell<DT>(A.cells, av * plane + R.base + x);
                         b = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
                     }
-                    if (a > 0) add_runs(A.out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + b, keep[j], km, lane);
+                    if (a > 0) add_runs(out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + b, keep[j], km, lane);
                     prev = b;
                 }
             }
@@ -251,178 +255,245 @@ template <> __device__ __forceinline__ float chunk_elem<kF32>(const uint4& c, in
     return __uint_as_float(j == 0 ? c.x : j == 1 ? c.y : j == 2 ? c.z : c.w);
 }
 
-// Per-warp shared staging of the vector kernel: the axis values of one chunk row
-// (32 lanes x 16 bytes per axis) and the list of its surviving cells (up to 256).
-constexpr int kStageBytes = kMaxVars * 512 + 256;
+// Asynchronous 16-byte global -> shared copies (no registers held while in
+// flight); a group is waited for with cp.async.wait_group, a hardware wait.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// One chunk row of the vector kernel: 32 lanes x VEC consecutive cells of row r
+// starting at xw, and this lane's cells that pass the geometric tests.
+struct ChunkRow {
+    int r, xw;                     // r = -1: none
+    RowSpan R;
+    unsigned kb;
+};
+
+// Geometric keep bits of this lane's chunk (x0 .. x0 + VEC - 1): in the shell,
+// in an active sub-brick when the activity is given, inside the position brush.
+template <int VEC>
+__device__ __forceinline__ unsigned chunk_geometry(const HistLaunch& A, const RowSpan& R, int x0) {
+    unsigned kb = 0u;
+    if (x0 > R.xb) return 0u;
+    if (A.sactive && !A.pmask) {
+#pragma unroll
+        for (int q = 0; q < VEC / 4; ++q) {
+            const uint32_t sid = R.srow + (uint32_t)((x0 >> 2) + q);
+            if (!((__ldg(A.sactive + (sid >> 5)) >> (sid & 31)) & 1u)) continue;
+#pragma unroll
+            for (int j = 4 * q; j < 4 * q + 4; ++j) {
+                const int dx = 2 * (x0 + j) + 1 - A.n;
+                const int sh = dx * dx + R.syz;
+                if (sh >= A.s_in && sh <= A.s_out) kb |= 1u << j;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < VEC; ++j)
+            if (cell_geometry_passes(A, R, x0 + j)) kb |= 1u << j;
+    }
+    return kb;
+}
+
+// The warp's next chunk row after (r, xw): the next chunk of the same row, else the
+// first chunk of the next row (by warp stride) that meets the outer sphere and holds
+// a cell passing the geometric tests in some lane.
+template <int VEC>
+__device__ __forceinline__ void next_chunk_row(const HistLaunch& A, int nwarps, int lane, ChunkRow& C) {
+    constexpr int CH = 32 * VEC;
+    const int rows = A.n * A.n;
+    int r = C.r, xw = C.xw + CH;
+    bool have_row = r >= 0;
+    for (;;) {
+        if (!have_row || xw > C.R.xb) {
+            r += nwarps;
+            if (r >= rows) { C.r = -1; C.kb = 0u; return; }
+            if (!row_span(A, r, C.R)) { have_row = false; continue; }
+            have_row = true;
+            xw = C.R.xa & ~(VEC - 1);
+        }
+        const unsigned kb = chunk_geometry<VEC>(A, C.R, xw + lane * VEC);
+        if (__ballot_sync(kFull, kb != 0u) != 0u) {
+            C.r = r;
+            C.xw = xw;
+            C.kb = kb;
+            return;
+        }
+        xw += CH;
+    }
+}
 
 // Vector kernel (grid edge a multiple of the chunk, 16-byte aligned planes, at most
-// kMaxVars load slots). A warp walks one x-row; each lane takes a chunk of VEC
-// consecutive cells (16 bytes per variable: 8 FP16 or 4 FP32 values), so one
-// load instruction brings 512 bytes per warp. The chunk's cells are tested
-// against the shell (integers), the sub-brick activity and the position brush;
-// then all brushed slots of a chunk with a surviving cell are loaded together
-// and tested, then the axis slots that are not brushed. The axis values go to
-// the warp's shared staging and the surviving cells into a compact list in x
-// order (warp prefix sum), from which the warp bins 32 surviving cells per
-// round: a selective brush needs one round per chunk row instead of one per
-// chunk position, and neighbouring lanes hold neighbouring cells for the
+// kMaxVars load slots). A warp walks x-rows in chunk rows of 32 lanes x 16 bytes
+// (8 FP16 or 4 FP32 cells per lane). While it tests and bins one chunk row it has
+// the next one's slots copied into its other shared buffer with cp.async (only
+// chunks with a cell that passes the shell, sub-brick and position tests), so
+// HBM latency hides behind the binning and no registers wait on loads. All
+// brushed slots are tested (FP16: two cells at a time against exact binary16
+// bounds); the surviving cells go into a compact list in x order (warp prefix
+// sum) from which the warp bins 32 cells per round, reading the axis values
+// from the buffer, so neighbouring lanes hold neighbouring cells for the
 // run-length adds. Persistent grid, rows by warp stride; the edge table is
 // staged once per resident block.
 template <int DT>
-__global__ void __launch_bounds__(kHistThreads, 4) k_hist(const __grid_constant__ HistLaunch A) {
+__global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_constant__ HistLaunch A) {
     constexpr int VEC = DT == kF16 ? 8 : 4;
-    constexpr int CH = 32 * VEC;                           // cells per warp and chunk row
     extern __shared__ __align__(16) unsigned char s_raw[];
     float* s_edges = reinterpret_cast<float*>(s_raw);
     const int ne16 = (A.naxes * (A.bins + 1) + 3) & ~3;
-    unsigned char* s_stage = s_raw + sizeof(float) * ne16 + (size_t)(threadIdx.x >> 5) * kStageBytes;
-    unsigned char* s_list = s_stage + kMaxVars * 512;
+    const int nslot = A.nslot, naxes = A.naxes;
+    const int buf_bytes = nslot * 512;                          // one chunk row of every slot
+    unsigned char* s_warp = s_raw + sizeof(float) * ne16 + (size_t)(threadIdx.x >> 5) * (2 * buf_bytes + 256);
+    unsigned char* s_list = s_warp + 2 * buf_bytes;
     stage_edges(A, s_edges);
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
     const int n = A.n;
-    const int rows = n * n;                                   // n <= 4096
-    const int gwarp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int bins = A.bins;
     const size_t plane = (size_t)n * n * n;
     const uint32_t sbr = A.sbr;
-    const int nslot = A.nslot, naxes = A.naxes;
+    uint32_t* const out = A.out + (size_t)(blockIdx.x % (unsigned)A.nout) * (naxes - 1) * bins * bins;
 
-    for (int r = gwarp; r < rows; r += nwarps) {
-        RowSpan R;
-        if (!row_span(A, r, R)) continue;
-        const int xa = R.xa & ~(VEC - 1);                    // first chunk holding a cell inside the outer sphere
-        for (int xw = xa; xw <= R.xb; xw += CH) {
-            const int x0 = xw + lane * VEC;                 // this lane's chunk; x0 + VEC <= n when x0 <= xb
-            unsigned kb = 0u;                               // bit j: cell x0 + j is still counted
-            if (x0 <= R.xb) {
-                if (A.sactive && !A.pmask) {
-                    // whole sub-bricks at once (a chunk covers VEC / 4 of them)
+    // copies of chunk row C into buffer b (lanes whose chunk has no passing cell copy nothing)
+    auto prefetch = [&](const ChunkRow& C, int b) {
+        if (C.r >= 0 && C.kb) {
+            const int x0 = C.xw + lane * VEC;
+            unsigned char* dst = s_warp + b * buf_bytes + lane * 16;
 #pragma unroll
-                    for (int q = 0; q < VEC / 4; ++q) {
-                        const uint32_t sid = R.srow + (uint32_t)((x0 >> 2) + q);
-                        if (!((__ldg(A.sactive + (sid >> 5)) >> (sid & 31)) & 1u)) continue;
-#pragma unroll
-                        for (int j = 4 * q; j < 4 * q + 4; ++j) {
-                            const int dx = 2 * (x0 + j) + 1 - n;
-                            const int sh = dx * dx + R.syz;
-                            if (sh >= A.s_in && sh <= A.s_out) kb |= 1u << j;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < VEC; ++j)
-                        if (cell_geometry_passes(A, R, x0 + j)) kb |= 1u << j;
-                }
-            }
-            // brushed slots: all loads of the chunk in flight together
-            uint4 val[kMaxVars];
-#pragma unroll
-            for (int s = 0; s < kMaxVars; ++s) {
-                val[s] = make_uint4(0u, 0u, 0u, 0u);
-                if (s < nslot && ((sbr >> s) & 1u) && kb)
-                    val[s] = __ldg(reinterpret_cast<const uint4*>(
-                        static_cast<const char*>(A.cells) + ((size_t)A.svar[s] * plane + R.base + x0) * (16 / VEC)));
-            }
-            if constexpr (DT == kF16) {
-                // two cells per comparison against the exact binary16 bounds (h >= lo iff
-                // h >= lo_h, h <= hi iff h <= hi_h; NaN fails both)
-                unsigned acc[4] = {kFull, kFull, kFull, kFull};
-#pragma unroll
-                for (int s = 0; s < kMaxVars; ++s) {
-                    if (s < nslot && ((sbr >> s) & 1u)) {
-                        const __half2 lo2 = u32_as_half2(A.slo_h2[s]), hi2 = u32_as_half2(A.shi_h2[s]);
-                        const unsigned w[4] = {val[s].x, val[s].y, val[s].z, val[s].w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            acc[q] &= __hge2_mask(u32_as_half2(w[q]), lo2) & __hle2_mask(u32_as_half2(w[q]), hi2);
-                    }
-                }
-                unsigned pass = 0u;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) pass |= ((acc[q] & 1u) | ((acc[q] >> 15) & 2u)) << (2 * q);
-                kb &= pass;
-            } else {
-#pragma unroll
-                for (int s = 0; s < kMaxVars; ++s) {
-                    if (s < nslot && ((sbr >> s) & 1u)) {
-                        const float lo = A.slo[s], hi = A.shi[s];
-#pragma unroll
-                        for (int j = 0; j < VEC; ++j) {
-                            const float v = chunk_elem<DT>(val[s], j);
-                            if (!(v >= lo && v <= hi)) kb &= ~(1u << j);
-                        }
-                    }
-                }
-            }
-            if (__ballot_sync(kFull, kb != 0u) == 0u) continue;
-            // axis slots that are not brushed, for chunks with a surviving cell; then every
-            // stored axis slot and the keep bits to the warp's staging
-#pragma unroll
-            for (int s = 0; s < kMaxVars; ++s) {
-                if (s < naxes && A.svar[s] >= 0) {
-                    if (!((sbr >> s) & 1u) && kb)
-                        val[s] = __ldg(reinterpret_cast<const uint4*>(
-                            static_cast<const char*>(A.cells) + ((size_t)A.svar[s] * plane + R.base + x0) * (16 / VEC)));
-                    *reinterpret_cast<uint4*>(s_stage + s * 512 + lane * 16) = val[s];
-                }
-            }
-            // compact list of the surviving cells (chunk-row offsets) in x order
-            const unsigned cnt = (unsigned)__popc(kb);
-            unsigned incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int total = (int)__shfl_sync(kFull, incl, 31);
-            int pos = (int)(incl - cnt);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-                if ((kb >> j) & 1u) s_list[pos++] = (unsigned char)(lane * VEC + j);
-            __syncwarp();
-            // bin 32 surviving cells per round
-#pragma unroll 1
-            for (int base = 0; base < total; base += 32) {
-                const bool kept = base + lane < total;
-                const unsigned km = total - base >= 32 ? kFull : (1u << (total - base)) - 1u;
-                const int c = kept ? s_list[base + lane] : 0;       // cell xw + c
-                float cx = 0.0f, cr2 = 0.0f;
-                if (A.use_pos && kept) {
-                    cx = cell_centre_rn(xw + c, n);
-                    cr2 = dot3_rn(cx, R.cy, R.cz, cx, R.cy, R.cz);
-                }
-                unsigned prev = 0u;
-#pragma unroll
-                for (int a = 0; a < kMaxVars; ++a) {
-                    if (a >= naxes) break;
-                    const int av = A.avar[a];
-                    unsigned b = 0u;
-                    if (kept) {
-                        float v;
-                        if (av >= kPosAxisBase) {
-                            v = pos_axis(cx, R.cy, R.cz, cr2, av - kPosAxisBase);
-                        } else if (DT == kF16) {
-                            v = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(s_stage + a * 512)[c]));
-                        } else {
-                            v = reinterpret_cast<const float*>(s_stage + a * 512)[c];
-                        }
-                        b = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
-                    }
-                    if (a > 0) add_runs(A.out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + b, kept, km, lane);
-                    prev = b;
-                }
-            }
-            __syncwarp();                                       // staging is rewritten by the next chunk row
+            for (int s = 0; s < kMaxVars; ++s)
+                if (s < nslot && A.svar[s] >= 0)
+                    cp_async16(dst + s * 512, static_cast<const char*>(A.cells) +
+                                                  ((size_t)A.svar[s] * plane + C.R.base + x0) * (16 / VEC));
         }
+        cp_async_commit();
+    };
+
+    ChunkRow cur;
+    cur.r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) - nwarps;
+    cur.xw = 0;
+    next_chunk_row<VEC>(A, nwarps, lane, cur);
+    prefetch(cur, 0);
+    int b = 0;
+    while (cur.r >= 0) {
+        ChunkRow nxt = cur;
+        next_chunk_row<VEC>(A, nwarps, lane, nxt);
+        prefetch(nxt, b ^ 1);
+        cp_async_wait_prev();                                   // this chunk row's copies have landed
+        __syncwarp();
+        const unsigned char* buf = s_warp + b * buf_bytes;
+        unsigned kb = cur.kb;
+        // brushed slots
+        if constexpr (DT == kF16) {
+            unsigned acc[4] = {kFull, kFull, kFull, kFull};
+#pragma unroll
+            for (int s = 0; s < kMaxVars; ++s) {
+                if (s < nslot && ((sbr >> s) & 1u)) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(buf + s * 512 + lane * 16);
+                    const __half2 lo2 = u32_as_half2(A.slo_h2[s]), hi2 = u32_as_half2(A.shi_h2[s]);
+                    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[q] &= __hge2_mask(u32_as_half2(w[q]), lo2) & __hle2_mask(u32_as_half2(w[q]), hi2);
+                }
+            }
+            unsigned pass = 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pass |= ((acc[q] & 1u) | ((acc[q] >> 15) & 2u)) << (2 * q);
+            kb &= pass;
+        } else {
+#pragma unroll
+            for (int s = 0; s < kMaxVars; ++s) {
+                if (s < nslot && ((sbr >> s) & 1u)) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(buf + s * 512 + lane * 16);
+                    const float lo = A.slo[s], hi = A.shi[s];
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        const float x = chunk_elem<DT>(v, j);
+                        if (!(x >= lo && x <= hi)) kb &= ~(1u << j);
+                    }
+                }
+            }
+        }
+        // compact list of the surviving cells (chunk-row offsets) in x order: the exclusive
+        // prefix of the per-lane counts (<= 8, four bits) from one ballot per bit
+        const unsigned cnt = (unsigned)__popc(kb);
+        const unsigned below = (1u << lane) - 1u;
+        int pos = 0, total = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit) {
+            const unsigned m = __ballot_sync(kFull, (cnt >> bit) & 1u);
+            pos += __popc(m & below) << bit;
+            total += __popc(m) << bit;
+        }
+#pragma unroll
+        for (int j = 0; j < VEC; ++j)
+            if ((kb >> j) & 1u) s_list[pos++] = (unsigned char)(lane * VEC + j);
+        __syncwarp();
+        // bin 32 surviving cells per round
+#pragma unroll 1
+        for (int base = 0; base < total; base += 32) {
+            const bool kept = base + lane < total;
+            const unsigned km = total - base >= 32 ? kFull : (1u << (total - base)) - 1u;
+            const int c = kept ? s_list[base + lane] : 0;       // cell cur.xw + c
+            float cx = 0.0f, cr2 = 0.0f;
+            if (A.use_pos && kept) {
+                cx = cell_centre_rn(cur.xw + c, n);
+                cr2 = dot3_rn(cx, cur.R.cy, cur.R.cz, cx, cur.R.cy, cur.R.cz);
+            }
+            unsigned prev = 0u;
+#pragma unroll
+            for (int a = 0; a < kMaxVars; ++a) {
+                if (a >= naxes) break;
+                const int av = A.avar[a];
+                unsigned bn = 0u;
+                if (kept) {
+                    float v;
+                    if (av >= kPosAxisBase) {
+                        v = pos_axis(cx, cur.R.cy, cur.R.cz, cr2, av - kPosAxisBase);
+                    } else if (DT == kF16) {
+                        v = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(buf + a * 512)[c]));
+                    } else {
+                        v = reinterpret_cast<const float*>(buf + a * 512)[c];
+                    }
+                    bn = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
+                }
+                if (a > 0) add_runs(out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + bn, kept, km, lane);
+                prev = bn;
+            }
+        }
+        __syncwarp();                                           // buffer b and the list are reused next
+        cur = nxt;
+        b ^= 1;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// out[i] = sum over the copies of copy[c][i] (count a multiple of 4, 16-byte aligned).
+__global__ void __launch_bounds__(256) k_hist_reduce(const uint4* __restrict__ copies, int ncopies, size_t count4,
+                                                     uint4* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
+        uint4 s = __ldcs(copies + i);
+        for (int c = 1; c < ncopies; ++c) {
+            const uint4 v = __ldcs(copies + (size_t)c * count4 + i);
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        out[i] = s;
     }
 }
 
+// Kernel view of h. False when the edge table is neither small enough for the
+// launch parameters nor on the device; vec_slots reports whether the load
+// slots fit the vector kernel.
 template <int DT>
-cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
-    HistLaunch a{};                      // about 8.6 KB with the inline edges (host stack)
+bool fill_launch(const HistArgs& h, HistLaunch& a, bool& vec_slots) {
     a.cells = h.cells;
     a.n = h.n;
     a.bins = h.bins;
@@ -447,7 +518,7 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
         a.guess_scale[i] = h.guess_scale[i];
     }
     // load slots of the vector kernel: the axes, then the brushed variables that are no axis
-    bool vec_slots = true;
+    vec_slots = true;
     a.nslot = h.naxes;
     for (int i = 0; i < h.naxes && i < kMaxVars; ++i) {
         a.svar[i] = h.axis[i] >= kPosAxisBase ? -1 : h.axis[i];
@@ -476,7 +547,8 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     const int64_t imax = 0x7fffffff;
     a.s_in = (int)std::min<int64_t>(std::max<int64_t>(h.s_in, 0), imax);
     a.s_out = (int)std::min<int64_t>(h.s_out, imax);
-    a.out = h.out;
+    a.out = h.ncopies > 1 ? h.copies : h.out;
+    a.nout = h.ncopies > 1 ? h.ncopies : 1;
     a.sactive = h.sactive;
     a.nsb = h.nsb;
     const int ne = h.naxes * (h.bins + 1);
@@ -486,12 +558,21 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     } else if (h.edges) {
         a.edges = h.edges;
     } else {
-        return cudaErrorInvalidValue;
+        return false;
     }
+    return true;
+}
+
+template <int DT>
+cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
+    HistLaunch a{};                      // about 8.6 KB with the inline edges (host stack)
+    bool vec_slots = true;
+    if (!fill_launch<DT>(h, a, vec_slots)) return cudaErrorInvalidValue;
+    const int ne = h.naxes * (h.bins + 1);
     if (h.s_out < 0) return cudaSuccess;                 // no cell in the shell: the zeroed output is the answer
     constexpr int VEC = DT == kF16 ? 8 : 4;
     const bool vec = vec_slots && h.n % VEC == 0 && (reinterpret_cast<uintptr_t>(h.cells) & 15u) == 0;
-    const size_t smem = vec ? sizeof(float) * (size_t)((ne + 3) & ~3) + (size_t)kHistWarps * kStageBytes
+    const size_t smem = vec ? sizeof(float) * (size_t)((ne + 3) & ~3) + (size_t)kHistVecWarps * (2 * a.nslot * 512 + 256)
                             : sizeof(float) * (size_t)ne;
     // persistent grid: as many blocks as fit at once (rows by warp stride)
     int dev = 0, sms = 0, per_sm = 0;
@@ -500,19 +581,37 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     if (e == cudaSuccess && vec && smem > 48 * 1024)
         e = cudaFuncSetAttribute(k_hist<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist<DT>, kHistThreads, smem)
+        e = vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist<DT>, kHistVecThreads, smem)
                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist_scalar<DT>, kHistThreads, smem);
     if (e != cudaSuccess) return e;
     const long long rows = (long long)a.n * a.n;
-    const long long want_blocks = (rows + kHistWarps - 1) / kHistWarps;
+    const int warps_per_block = vec ? kHistVecWarps : kHistWarps;
+    const long long want_blocks = (rows + warps_per_block - 1) / warps_per_block;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(want_blocks, (long long)sms * std::max(1, per_sm)));
-    if (vec) k_hist<DT><<<blocks, kHistThreads, smem, stream>>>(a);
+    if (vec) k_hist<DT><<<blocks, kHistVecThreads, smem, stream>>>(a);
     else k_hist_scalar<DT><<<blocks, kHistThreads, smem, stream>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+int hist_copies(int n, int naxes, int bins) {
+    const size_t bytes = sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins;
+    if ((long long)n * n * n < (1LL << 21) || bytes % 16) return 1;      // small grids: not worth a pass
+    const size_t fit = kHistCopyBytes / bytes;
+    return (int)std::min<size_t>(kHistMaxCopies, fit);
+}
+
+cudaError_t launch_histogram_reduce(const uint32_t* copies, int ncopies, size_t count, uint32_t* out,
+                                    cudaStream_t stream) {
+    const size_t count4 = count / 4;
+    const unsigned blocks = (unsigned)std::min<size_t>((count4 + 255) / 256, 4096);
+    k_hist_reduce<<<blocks, 256, 0, stream>>>(reinterpret_cast<const uint4*>(copies), ncopies, count4,
+                                               reinterpret_cast<uint4*>(out));
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_histogram(const HistArgs& a, int dtype, cudaStream_t stream) {
     if (dtype == kF16) return launch_t<kF16>(a, stream);

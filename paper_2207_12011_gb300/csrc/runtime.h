@@ -91,13 +91,14 @@ struct Volume {
     int color_var = 0;
     float tf_lo = 0.f, tf_hi = 1.f;
     size_t bytes = 0;
-    // host-source updates: a staging buffer of the source's size, filled on a copy stream of
-    // the volume's own; ev_consumed marks the last ingest that read it
-    void* staging = nullptr;
+    // host-source updates: two staging buffers of the source's size used in turn, filled on a
+    // copy stream of the volume's own; ev_consumed[i] marks the last ingest that read buffer i
+    void* staging[2] = {nullptr, nullptr};
     size_t staging_bytes = 0;
+    int stage_next = 0;
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied = nullptr, ev_consumed = nullptr;
-    bool consumed_pending = false;
+    cudaEvent_t ev_copied = nullptr, ev_consumed[2] = {nullptr, nullptr};
+    bool consumed_pending[2] = {false, false};
 };
 
 inline size_t elem_size(int dtype) { return dtype == RAYPC_F16 ? 2 : 4; }

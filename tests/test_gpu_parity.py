@@ -619,12 +619,14 @@ def test_histogram_rejects_bad_edges(ctx, rp):
 POS = (np.float32([-0.45, -np.inf, -np.inf, 0.62]), np.float32([0.5, np.inf, np.inf, 0.9]), 0b1001)
 
 
-@pytest.mark.parametrize("n,store", [(48, "f16"), (64, "f32"), (47, "f16"), (42, "f32")])
+@pytest.mark.parametrize("n,store", [(48, "f16"), (64, "f32"), (47, "f16"), (42, "f32"), (128, "f16"), (128, "f32")])
 def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
     """Grid edges that are a multiple of the 16-byte chunk (8 FP16 / 4 FP32 cells) take the
     vector kernel, the others the scalar one; both must count what the oracle counts, with
     position axes, a repeated axis variable, brushed variables that are no axis, the position
-    brush, inactive sub-bricks, and the edges in the launch parameters or on the device."""
+    brush, inactive sub-bricks, and the edges in the launch parameters or on the device.
+    From 128^3 on the blocks spread their counts over partial histograms summed afterwards,
+    and FP16 fields take their bins from a table over all binary16 values."""
     vol = synth.make_shell_volume(n, seed=17)
     st = stored(vol, store)
     cases = [
@@ -654,17 +656,19 @@ def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
         v.free()
 
 
-def test_histogram_fp16_bounds_between_and_at_half_values(ctx):
+@pytest.mark.parametrize("n", [48, 128])
+def test_histogram_fp16_bounds_between_and_at_half_values(ctx, n):
     """FP16 fields are tested two cells at a time against binary16 bounds (the smallest
-    half >= lo, the largest half <= hi); bounds at, just below and just above stored values,
-    beyond the binary16 range, and NaN / infinite cells must count exactly what the oracle's
-    FP32 comparison counts."""
-    n = 48
+    half >= lo, the largest half <= hi) and, from 128^3 on, binned by a table over all
+    binary16 values; bounds at, just below and just above stored values, beyond the binary16
+    range, and NaN / infinite cells must count exactly what the oracle's FP32 comparison
+    counts."""
     vol = synth.make_shell_volume(n, seed=23)
-    vol[0, 20, 20:30, 10:20] = float("nan")
-    vol[1, 30, 5:9, 20:40] = float("inf")
-    vol[2, 25, 10:12, :] = -float("inf")
-    vol[3, 10:14, 24, 30:34] = 7.0e4                       # beyond the binary16 range: +inf stored
+    f = lambda x: int(round(x * n / 48))                      # the same shell places at every grid size
+    vol[0, f(20), f(20):f(30), f(10):f(20)] = float("nan")
+    vol[1, f(30), f(5):f(9), f(20):f(40)] = float("inf")
+    vol[2, f(25), f(10):f(12), :] = -float("inf")
+    vol[3, f(10):f(14), f(24), f(30):f(34)] = 7.0e4        # beyond the binary16 range: +inf stored
     st = stored(vol, "f16")
     order = (0, 1, 2, 3, 4, 5)
     edges = synth.make_edges(torch.from_numpy(np.nan_to_num(st, nan=0.0, posinf=0.0, neginf=0.0)), order, bins=128)
