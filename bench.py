@@ -660,8 +660,9 @@ def run_ours(args):
                      "traffic": profiled("traffic_bytes_per_launch", f"k_hist_{args.workload}.md", "k_hist"),
                      "peak_kind": f"{peak_kind} HBM copy", "hist_ms": round(hist_ms, 4),
                      "alg_bytes_per_launch": int(hist_bytes),
-                     "note": "CUDA events around the raypc_pc_histogram call: its output clear (memset) and the "
-                             "kernel; the edges travel in the launch parameters"}
+                     "note": "CUDA events around the raypc_pc_histogram call: the clear of the output or of the "
+                             "partial histograms, the kernel and their reduction; the edges travel in the launch "
+                             "parameters"}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -681,8 +682,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(e2e_max_ms / e2e_steps, 3),
                 "how": "raypc_update_volume with the pinned host volume every step (C ABI host path: the "
-                       "library copies it on its own copy stream into the volume's staging buffer, overlapping "
-                       "the previous step's render and histograms); image + histograms read back per step",
+                       "library copies it on its own copy stream into one of the volume's two staging buffers, "
+                       "overlapping the previous step's render and histograms); image + histograms read back "
+                       "per step",
                 "copies_declared": True},
         "gpu_launches": int(launches),
         "autotune": {"chosen": tuned, "candidates": tuned_all},
