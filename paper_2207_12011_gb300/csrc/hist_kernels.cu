@@ -335,8 +335,10 @@ __device__ __forceinline__ void next_chunk_row(const HistLaunch& A, int nwarps, 
 // brushed slots are tested (FP16: two cells at a time against exact binary16
 // bounds); the surviving cells go into a compact list in x order (warp prefix
 // sum) from which the warp bins 32 cells per round, reading the axis values
-// from the buffer, so neighbouring lanes hold neighbouring cells for the
-// run-length adds. Persistent grid, rows by warp stride; the edge table is
+// from the buffer. Neighbouring lanes then hold neighbouring cells, whose bin
+// tuples mostly agree on a smooth field: a lane whose tuple differs from its
+// left neighbour's starts a run and adds the run's length to each
+// adjacent-axis pair (one atomic per pair and run). Persistent grid, rows by warp stride; the edge table is
 // staged once per resident block.
 template <int DT>
 __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_constant__ HistLaunch A) {
@@ -445,25 +447,45 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
                 cx = cell_centre_rn(cur.xw + c, n);
                 cr2 = dot3_rn(cx, cur.R.cy, cur.R.cz, cx, cur.R.cy, cur.R.cz);
             }
-            unsigned prev = 0u;
+            // the cell's bins, packed three per word (10 bits each, bins <= 1024)
+            unsigned bn[kMaxVars];
+            unsigned packed[3] = {0u, 0u, 0u};
 #pragma unroll
             for (int a = 0; a < kMaxVars; ++a) {
-                if (a >= naxes) break;
+                bn[a] = 0u;
+                if (a >= naxes || !kept) continue;
                 const int av = A.avar[a];
-                unsigned bn = 0u;
-                if (kept) {
-                    float v;
-                    if (av >= kPosAxisBase) {
-                        v = pos_axis(cx, cur.R.cy, cur.R.cz, cr2, av - kPosAxisBase);
-                    } else if (DT == kF16) {
-                        v = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(buf + a * 512)[c]));
-                    } else {
-                        v = reinterpret_cast<const float*>(buf + a * 512)[c];
-                    }
-                    bn = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
+                float v;
+                if (av >= kPosAxisBase) {
+                    v = pos_axis(cx, cur.R.cy, cur.R.cz, cr2, av - kPosAxisBase);
+                } else if (DT == kF16) {
+                    v = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(buf + a * 512)[c]));
+                } else {
+                    v = reinterpret_cast<const float*>(buf + a * 512)[c];
                 }
-                if (a > 0) add_runs(out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + bn, kept, km, lane);
-                prev = bn;
+                bn[a] = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
+                packed[a / 3] |= bn[a] << (10 * (a % 3));
+            }
+            // runs of equal bin tuples over consecutive listed cells: the lane that starts a run
+            // adds its length to each adjacent-axis pair
+            bool same = lane > 0;
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                if (3 * w >= naxes) break;
+                const unsigned left = __shfl_up_sync(kFull, packed[w], 1);   // every lane takes part
+                same = same && left == packed[w];
+            }
+            const bool head = kept && !same;
+            const unsigned hm = __ballot_sync(kFull, head);
+            if (head) {
+                const unsigned after = lane == 31 ? 0u : (kFull << (lane + 1));
+                const unsigned stop = (hm | ~km) & after;        // next run start or the end of the list
+                const unsigned len = (unsigned)((stop ? __ffs(stop) - 1 : 32) - lane);
+#pragma unroll
+                for (int a = 1; a < kMaxVars; ++a) {
+                    if (a >= naxes) break;
+                    atomicAdd(out + (size_t)(a - 1) * bins * bins + bn[a - 1] * (unsigned)bins + bn[a], len);
+                }
             }
         }
         __syncwarp();                                           // buffer b and the list are reused next
