@@ -2,21 +2,24 @@
 // Fig. 2): for every in-shell (and, optionally, in-brush) cell and every pair
 // of adjacent axes (a, a+1), H[a][bin_a][bin_{a+1}] += 1.
 //
-// HBM-bound scan. A warp walks one x-row of cells so the planar loads are
-// coalesced; rows whose cells all lie outside the shell are skipped without
-// touching memory. The vector kernel gives each lane a 16-byte chunk of a
-// row per variable (8 FP16 or 4 FP32 cells); the scalar kernel (ragged grid
-// edges, unaligned fields) one cell per lane. A cell's axis values that are
-// not brushed are loaded only after its brushed values pass. Position axes and
-// the position brush use the cell centre, coordinate RN((2i + 1 - n) / n).
-// With the volume's own brush the cells of inactive 4^3 sub-bricks are skipped
-// without loads: every vertex of such a sub-brick fails the brush (its values
-// lie between the sub-brick's min and max) or lies outside the shell (the
-// sub-brick's widened box, which holds the vertex centres, misses the shell).
-// The in-shell test is integer-exact. Bins come from a walk over the FP32 edges
-// held in shared memory (comparisons only, so exact). Increments are
-// aggregated per warp with __match_any_sync on the (bin_a, bin_{a+1}) key: one
-// atomicAdd per distinct key per warp and pair.
+// A scan over HBM plus the binning of the kept cells. A warp walks one x-row
+// of cells at a time so the planar loads are coalesced; rows whose cells all
+// lie outside the shell are skipped without touching memory. The vector kernel
+// streams 16-byte chunks of a row per variable (8 FP16 or 4 FP32 cells per
+// lane) through a cp.async double buffer in shared memory; the scalar kernel
+// (ragged grid edges, unaligned fields) takes one cell per lane. A cell's axis
+// values that are not brushed are loaded only after its brushed values pass.
+// Position axes and the position brush use the cell centre, coordinate
+// RN((2i + 1 - n) / n). With the volume's own brush the cells of inactive 4^3
+// sub-bricks are skipped without loads: every vertex of such a sub-brick fails
+// the brush (its values lie between the sub-brick's min and max) or lies
+// outside the shell (the sub-brick's widened box, which holds the vertex
+// centres, misses the shell). The in-shell test is integer-exact. Bins come
+// from the FP32 edges held in shared memory (comparisons only, so exact).
+// Increments are aggregated over runs of neighbouring cells that share their
+// bins (one atomicAdd per run), and on large grids spread over partial
+// histograms that a reduction sums, so the hot bins of a smooth field do not
+// serialise in L2.
 #include <math.h>
 #include <stdint.h>
 
