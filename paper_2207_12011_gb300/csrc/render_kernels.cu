@@ -16,14 +16,15 @@
 // memory) and composited front to back with early ray termination.
 //
 // The samples inside the inner core are jumped over analytically (exactly: see
-// the march). Empty-space skipping: when the samples of all lanes running
-// together fall in inactive sub-bricks whose empty-space distance is D >= 2
-// (every sub-brick within D - 1 is inactive), the lanes skip together by their
-// smallest count of samples that cannot leave that box of sub-bricks: the lattice moves the cell index by at most g cells per sample
-// on any axis (g = dt * n/2 * max |d_a|), so the next floor((4 (D - 1) -
-// 1/16) / g) samples stay in the box (1/16 cell covers the FP32 rounding of t,
-// the position and the grid coordinate) and are rejected without being
-// computed. The lattice itself (t_k = t0 + (k + j) dt, j = 1/2 except in
+// the march). Empty-space skipping: every sample reads its sub-brick's
+// empty-space distance D (the Chebyshev distance, in sub-bricks, to the nearest
+// active one; 0 for active ones). When the samples of all lanes running
+// together have D >= 2 (or >= 4, or 8), every lane's next floor((4 (D - 1) - 1/16) /
+// (dt n/2)) samples stay in its box of inactive sub-bricks -- the lattice moves
+// a cell index by at most dt n/2 cells per sample on any axis, and 1/16 cell
+// covers the FP32 rounding of t, the position and the grid coordinate -- so the
+// lanes skip that many samples together (one warp vote) and stay on
+// neighbouring samples. The lattice itself (t_k = t0 + (k + j) dt, j = 1/2 except in
 // jittered progressive passes) is never shifted by a skip.
 #include "common.cuh"
 
@@ -146,8 +147,12 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
             int n_lat = max(0, (int)floorf((t1 - t0) * inv_dt - jo));
             while (n_lat > 0 && !(__fmaf_rn(__fadd_rn((float)(n_lat - 1), jo), dt, t0) < t1)) --n_lat;
             while (__fmaf_rn(__fadd_rn((float)n_lat, jo), dt, t0) < t1) ++n_lat;
-            // grid cells the lattice advances per sample along the fastest axis
-            const float inv_g = 1.0f / (dt * hn * fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
+            // samples that stay in a box of inactive sub-bricks extending 4 (D - 1) cells beyond
+            // the current sub-brick (the lattice moves a cell index by at most dt n/2 cells per
+            // sample on any axis)
+            const int skip_near = (int)((4.0f - 0.0625f) / (dt * hn));                        // D >= 2
+            const int skip_mid = (int)((12.0f - 0.0625f) / (dt * hn));                        // D >= 4
+            const int skip_far = (int)((4.0f * (kDistCap - 1) - 0.0625f) / (dt * hn));         // D >= 8
             // Inner core: the samples core_a..core_b lie inside r_in and fail the shell
             // test, so the march jumps over them. The range comes from the core chord of
             // a slightly smaller sphere and is then verified with the per-sample FP32
@@ -230,27 +235,29 @@ __device__ __forceinline__ void march_pixel(const RenderArgs& A, const ViewShare
                 iy = grid_index_rn(pyw, n, hn, off, uy);
                 iz = grid_index_rn(pzw, n, hn, off, uz);
                 const uint32_t sid = ((uint32_t)(iz >> 2) * nsb + (iy >> 2)) * nsb + (ix >> 2);
-                const bool active = bit_of(A.lv.sactive, sid);
+                bool active;
                 if (A.skip && A.lv.sdist) {
-                    // every sub-brick within D - 1 of an inactive one is inactive, so the cell
-                    // index stays in that box -- at least 4 (D - 1) cells beyond this sub-brick
-                    // on every side -- while the lattice moves it by less than 4 (D - 1) cells
-                    // per axis: by at most g cells per sample, with 1/16 cell kept for the FP32
-                    // rounding of t, the position and the grid coordinate. The lanes that run
-                    // together skip together, by their smallest safe count, so they stay on
-                    // neighbouring samples.
-                    int m = 0;
-                    if (!active) {
-                        const int D = __ldg(A.lv.sdist + sid);
-                        if (D >= 2) m = (int)(((float)(4 * D - 4) - 0.0625f) * inv_g);
-                        if (k + m >= 65536) m = 0;
-                    }
-                    m = __reduce_min_sync(__activemask(), m);
-                    if (m > 0) {
+                    // the empty-space distance D (0: active): every sub-brick within D - 1 of
+                    // this one is inactive, so the cell index stays in that box -- at least
+                    // 4 (D - 1) cells beyond this sub-brick on every side -- while the lattice
+                    // moves it by less than 4 (D - 1) cells per axis, i.e. for the next
+                    // floor((4 (D - 1) - 1/16) / (dt n/2)) samples (dt n/2 bounds the cells
+                    // per sample on any axis; 1/16 cell covers the FP32 rounding of t, the
+                    // position and the grid coordinate). When all lanes running together
+                    // are at D >= 2 (>= 4, >= 8) they skip those samples together, so they
+                    // stay on neighbouring samples.
+                    const int D = __ldg(A.lv.sdist + sid);
+                    active = D == 0;
+                    const unsigned grp = __activemask();
+                    if (__all_sync(grp, D >= 2 && k + skip_far < 65536)) {
+                        const int m = !__all_sync(grp, D >= 4) ? skip_near
+                                    : (__all_sync(grp, D >= kDistCap) ? skip_far : skip_mid);
                         skipped += (unsigned)m;
                         k += m + 1;
                         continue;
                     }
+                } else {
+                    active = bit_of(A.lv.sactive, sid);
                 }
                 if (!active) {
                     ++k;
