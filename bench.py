@@ -302,7 +302,7 @@ def accuracy_report(wl, gpu_img, vol_np, src_np=None, count_row_stride=4):
     return out
 
 
-def config_section(rp, name, args, dev, seed, rank):
+def config_section(rp, name, args, dev, seed, rank, sm_mhz=2070.0):
     """One BASELINE configuration measured on its own: K whole-path steps (ingest, LOD, bricks,
     brush, render, histograms) with CUDA events around the render and the histograms, the
     resident-volume frame loop, the render and histogram rooflines, and (rank 0) the full-frame
@@ -372,6 +372,15 @@ def config_section(rp, name, args, dev, seed, rank):
                                   "peak": peak, "unit": "GB/s", "frac": round(hist_bytes / hist_ms / 1e6 / peak, 4),
                                   "traffic": profiled("traffic_bytes_per_launch", f"k_hist_{name}.md", "k_hist"),
                                   "alg_bytes_per_launch": int(hist_bytes), "peak_kind": f"{peak_kind} HBM copy"}}
+    insts = profiled("warp_instructions_per_launch", f"k_render_{name}.md")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    sec["roofline"]["binding"] = {
+        "bound": "issue", "unit": "G warp-instructions/s", "peak": round(issue_peak, 1),
+        "peak_kind": f"{sms} SMs x 4 schedulers x SM clock {sm_mhz:.0f} MHz",
+        "achieved": round(insts / (render_ms / 1e3) / 1e9, 1) if insts else None,
+        "frac": round(insts / (render_ms / 1e3) / 1e9 / issue_peak, 4) if insts else None,
+        "warp_instructions_per_launch": insts}
     if rank == 0 and not args.no_accuracy:
         vol.render(wl.cam, c["w"], c["h"], out=img)
         torch.cuda.synchronize()
@@ -709,7 +718,8 @@ def run_ours(args):
         line["configs"] = {}
         for name in configs:
             torch.cuda.empty_cache()
-            line["configs"][name] = config_section(rp, name, args, dev, synth.DEFAULT_SEED + rank, rank)
+            line["configs"][name] = config_section(rp, name, args, dev, synth.DEFAULT_SEED + rank, rank,
+                                                   clk.get("sm_mhz") or 2070.0)
     if not args.no_batched:
         torch.cuda.empty_cache()
         bt = run_batched(rp, dev, args, synth.DEFAULT_SEED + 1000 + rank)
