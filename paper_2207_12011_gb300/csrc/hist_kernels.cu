@@ -329,6 +329,43 @@ __device__ __forceinline__ void next_chunk_row(const HistLaunch& A, int nwarps, 
     }
 }
 
+// One binning round of the vector kernel: lane l holds a cell iff kept (the kept lanes
+// are a prefix, km their mask) with its axis values val[a]. Bins come from the FP32 edges in
+// shared memory; a lane whose bin tuple differs from its left neighbour's starts a run and
+// adds the run's length to each adjacent-axis pair (one atomic per pair and run).
+__device__ __forceinline__ void bin_round(const HistLaunch& A, const float* s_edges, uint32_t* out,
+                                          const float (&val)[kMaxVars], bool kept, unsigned km, int lane) {
+    const int naxes = A.naxes, bins = A.bins;
+    unsigned bn[kMaxVars];
+    unsigned packed[3] = {0u, 0u, 0u};                      // three bins per word, 10 bits each
+#pragma unroll
+    for (int a = 0; a < kMaxVars; ++a) {
+        bn[a] = 0u;
+        if (a >= naxes || !kept) continue;
+        bn[a] = (unsigned)bin_of(s_edges + a * (bins + 1), bins, val[a], A.guess_e0[a], A.guess_scale[a]);
+        packed[a / 3] |= bn[a] << (10 * (a % 3));
+    }
+    bool same = lane > 0;
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+        if (3 * w >= naxes) break;
+        const unsigned left = __shfl_up_sync(kFull, packed[w], 1);   // every lane takes part
+        same = same && left == packed[w];
+    }
+    const bool head = kept && !same;
+    const unsigned hm = __ballot_sync(kFull, head);
+    if (head) {
+        const unsigned after = lane == 31 ? 0u : (kFull << (lane + 1));
+        const unsigned stop = (hm | ~km) & after;            // next run start or the last kept lane
+        const unsigned len = (unsigned)((stop ? __ffs(stop) - 1 : 32) - lane);
+#pragma unroll
+        for (int a = 1; a < kMaxVars; ++a) {
+            if (a >= naxes) break;
+            atomicAdd(out + (size_t)(a - 1) * bins * bins + bn[a - 1] * (unsigned)bins + bn[a], len);
+        }
+    }
+}
+
 // Vector kernel (grid edge a multiple of the chunk, 16-byte aligned planes, at most
 // kMaxVars load slots). A warp walks x-rows in chunk rows of 32 lanes x 16 bytes
 // (8 FP16 or 4 FP32 cells per lane). While it tests and bins one chunk row it has
@@ -377,6 +414,10 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
         }
         cp_async_commit();
     };
+
+    const bool carry = DT == kF16 && !A.use_pos;
+    int q = 0;                                                  // carried cells, in lanes 0..q-1
+    unsigned cpk[kMaxVars / 2] = {0u, 0u, 0u, 0u};              // a carried cell's values, binary16 pairs
 
     ChunkRow cur;
     cur.r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) - nwarps;
@@ -439,61 +480,73 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
         for (int j = 0; j < VEC; ++j)
             if ((kb >> j) & 1u) s_list[pos++] = (unsigned char)(lane * VEC + j);
         __syncwarp();
-        // bin 32 surviving cells per round
+        // bin the surviving cells 32 per round. FP16 without position axes carries a remainder
+        // of fewer than 32 cells to the next chunk row (their values in the lanes' registers),
+        // so that sparse chunk rows still fill whole rounds
+        int consumed = 0;
 #pragma unroll 1
-        for (int base = 0; base < total; base += 32) {
-            const bool kept = base + lane < total;
-            const unsigned km = total - base >= 32 ? kFull : (1u << (total - base)) - 1u;
-            const int c = kept ? s_list[base + lane] : 0;       // cell cur.xw + c
-            float cx = 0.0f, cr2 = 0.0f;
-            if (A.use_pos && kept) {
-                cx = cell_centre_rn(cur.xw + c, n);
-                cr2 = dot3_rn(cx, cur.R.cy, cur.R.cz, cx, cur.R.cy, cur.R.cz);
-            }
-            // the cell's bins, packed three per word (10 bits each, bins <= 1024)
-            unsigned bn[kMaxVars];
-            unsigned packed[3] = {0u, 0u, 0u};
+        for (;;) {
+            const int avail = q + total - consumed;
+            if (avail == 0) break;
+            if (carry && avail < 32) {
+                if (lane >= q && lane < avail) {
+                    const int c = s_list[consumed + lane - q];
 #pragma unroll
-            for (int a = 0; a < kMaxVars; ++a) {
-                bn[a] = 0u;
-                if (a >= naxes || !kept) continue;
-                const int av = A.avar[a];
-                float v;
-                if (av >= kPosAxisBase) {
-                    v = pos_axis(cx, cur.R.cy, cur.R.cz, cr2, av - kPosAxisBase);
-                } else if (DT == kF16) {
-                    v = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(buf + a * 512)[c]));
-                } else {
-                    v = reinterpret_cast<const float*>(buf + a * 512)[c];
+                    for (int a = 0; a < kMaxVars; ++a) {
+                        if (a >= naxes) break;
+                        const unsigned hb = reinterpret_cast<const unsigned short*>(buf + a * 512)[c];
+                        cpk[a >> 1] = (cpk[a >> 1] & (0xffff0000u >> (16 * (a & 1)))) | (hb << (16 * (a & 1)));
+                    }
                 }
-                bn[a] = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
-                packed[a / 3] |= bn[a] << (10 * (a % 3));
+                q = avail;
+                break;
             }
-            // runs of equal bin tuples over consecutive listed cells: the lane that starts a run
-            // adds its length to each adjacent-axis pair
-            bool same = lane > 0;
+            const int take = min(32, avail);
+            const bool kept = lane < take;
+            const unsigned km = take == 32 ? kFull : (1u << take) - 1u;
+            float val[kMaxVars];
 #pragma unroll
-            for (int w = 0; w < 3; ++w) {
-                if (3 * w >= naxes) break;
-                const unsigned left = __shfl_up_sync(kFull, packed[w], 1);   // every lane takes part
-                same = same && left == packed[w];
-            }
-            const bool head = kept && !same;
-            const unsigned hm = __ballot_sync(kFull, head);
-            if (head) {
-                const unsigned after = lane == 31 ? 0u : (kFull << (lane + 1));
-                const unsigned stop = (hm | ~km) & after;        // next run start or the end of the list
-                const unsigned len = (unsigned)((stop ? __ffs(stop) - 1 : 32) - lane);
+            for (int a = 0; a < kMaxVars; ++a) val[a] = 0.0f;
+            if (kept && lane < q) {                             // a carried cell
 #pragma unroll
-                for (int a = 1; a < kMaxVars; ++a) {
+                for (int a = 0; a < kMaxVars; ++a)
+                    if (a < naxes)
+                        val[a] = __half2float(__ushort_as_half((unsigned short)(cpk[a >> 1] >> (16 * (a & 1)))));
+            } else if (kept) {
+                const int c = s_list[consumed + lane - q];       // cell cur.xw + c
+                float cx = 0.0f, cr2 = 0.0f;
+                if (A.use_pos) {
+                    cx = cell_centre_rn(cur.xw + c, n);
+                    cr2 = dot3_rn(cx, cur.R.cy, cur.R.cz, cx, cur.R.cy, cur.R.cz);
+                }
+#pragma unroll
+                for (int a = 0; a < kMaxVars; ++a) {
                     if (a >= naxes) break;
-                    atomicAdd(out + (size_t)(a - 1) * bins * bins + bn[a - 1] * (unsigned)bins + bn[a], len);
+                    const int av = A.avar[a];
+                    if (av >= kPosAxisBase)
+                        val[a] = pos_axis(cx, cur.R.cy, cur.R.cz, cr2, av - kPosAxisBase);
+                    else if (DT == kF16)
+                        val[a] = __half2float(__ushort_as_half(reinterpret_cast<const unsigned short*>(buf + a * 512)[c]));
+                    else
+                        val[a] = reinterpret_cast<const float*>(buf + a * 512)[c];
                 }
             }
+            bin_round(A, s_edges, out, val, kept, km, lane);
+            consumed += take - q;
+            q = 0;
         }
         __syncwarp();                                           // buffer b and the list are reused next
         cur = nxt;
         b ^= 1;
+    }
+    if (q > 0) {                                                // the last carried cells
+        const bool kept = lane < q;
+        float val[kMaxVars];
+#pragma unroll
+        for (int a = 0; a < kMaxVars; ++a)
+            val[a] = kept && a < naxes ? __half2float(__ushort_as_half((unsigned short)(cpk[a >> 1] >> (16 * (a & 1)))))
+                                       : 0.0f;
+        bin_round(A, s_edges, out, val, kept, (1u << q) - 1u, lane);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
