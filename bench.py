@@ -728,7 +728,8 @@ def run_ours(args):
         line["batched"] = bt
     if not args.no_served:
         torch.cuda.empty_cache()
-        line["served"] = run_served(rp, dev, args, synth.DEFAULT_SEED + 2000 + rank)
+        rate = ((line.get("batched") or {}).get("oracle_subset") or {}).get("oracle_samples_per_s")
+        line["served"] = run_served(rp, dev, args, synth.DEFAULT_SEED + 2000 + rank, rate)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ctx is not None:
@@ -765,6 +766,8 @@ def run_batched(rp, dev, args, seed):
     v32 = ctx.load_volume(src, store="f32")
     v32.build_bricks(n_lod=2)
     v32.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    check = not args.no_accuracy and dist_env()[1] == 0
+    vol_np = synth.to_storage(src, "f16").float().cpu().numpy() if check else None
     del src
     outs = [torch.empty((h, w, 4), dtype=torch.float32, device=dev) for _, w, h in views]
     stats = torch.zeros(rp.NSTATS, dtype=torch.int64, device=dev)
@@ -786,6 +789,32 @@ def run_batched(rp, dev, args, seed):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / reps
     batch_samples = float(stats[0].item()) / reps
+    # the oracle on a seeded subset (2 views, every 16th row): the batch's error there, and the
+    # oracle's rate on this workload, from which its time for the whole batch is extrapolated
+    oracle_check = None
+    if check:
+        import oracle
+        rng = np.random.default_rng(seed + 5)
+        picked = sorted(rng.choice(k, size=2, replace=False).tolist())
+        err, npix, osamples, osec = 0.0, 0, 0.0, 0.0
+        for i in picked:
+            (c, w, h), b = views[i], brushes[i]
+            pix = (np.arange(8, h, 16)[:, None] * w + np.arange(w)[None, :]).reshape(-1).astype(np.int64)
+            t0 = time.perf_counter()
+            ref, cnt = oracle.render(vol_np, synth.R_IN, synth.R_OUT, c.as_array(), w, h, 1.0 / n, b.lo, b.hi,
+                                     b.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi, ert=True, pixels=pix)
+            osec += time.perf_counter() - t0
+            osamples += float(cnt[:, 0].sum())
+            got = outs[i].cpu().numpy().reshape(-1, 4)[pix].astype(np.float64)
+            err = max(err, float(np.abs(got - ref).max()))
+            npix += len(pix)
+        rate = osamples / osec
+        oracle_check = {"views": picked, "pixels": npix, "max_abs_vs_oracle": err, "tol": 4e-3,
+                        "oracle_samples_per_s": round(rate, 1), "cores": oracle.num_threads(),
+                        "oracle_s_per_batch_extrapolated": round(batch_samples / rate, 2),
+                        "what": "FP64 oracle on every 16th row of 2 seeded views; the whole-batch oracle time is "
+                                "extrapolated from its rate (lattice samples / s) to the batch's lattice samples"}
+        del vol_np
     # algorithmic bytes of the batch: per view, its active bricks' values under its own brush
     # plus its image (the per-view classification inside the graph uses the same rule)
     alg_bytes = 0
@@ -833,6 +862,7 @@ def run_batched(rp, dev, args, seed):
                          "achieved": round(alg_bytes / batch_ms / 1e6, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(alg_bytes / batch_ms / 1e6 / peak, 4), "alg_bytes_per_batch": alg_bytes,
                          "peak_kind": f"{peak_kind} HBM copy"},
+            "oracle_subset": oracle_check,
             "speedup": round(plain_ms / batch_ms, 3),
             "speedup_vs_tuned_plain": round(tuned_ms / batch_ms, 3),
             "samples_per_batch": batch_samples}
@@ -876,7 +906,7 @@ def served_requests(nreq, seed, tables, rng):
     return reqs
 
 
-def run_served(rp, dev, args, seed):
+def run_served(rp, dev, args, seed, oracle_rate=None):
     n, nreq = args.serve_n, args.serve_requests
     rng = np.random.default_rng(seed)
     ctx = rp.Context(dev.index)
@@ -997,6 +1027,7 @@ def run_served(rp, dev, args, seed):
                 "plain_f32_fifo": {"p50_ms": ms(_pct(lp, 50)), "p99_ms": ms(_pct(lp, 99)),
                                    "coarse_p50_ms": ms(_pct(lpc, 50)), "coarse_p99_ms": ms(_pct(lpc, 99)),
                                    "samples_per_s": round(ps / pspan, 1), "span_s": round(pspan, 3)},
+                "samples": ss,
                 "p50_speedup": round(_pct(lp, 50) / _pct(ls, 50), 3) if ls and lp else None,
                 "p99_speedup": round(_pct(lp, 99) / _pct(ls, 99), 3) if ls and lp else None,
                 "throughput_ratio": round((ss / sspan) / (ps / pspan), 3) if ps > 0 and ss > 0 else None}
@@ -1013,6 +1044,11 @@ def run_served(rp, dev, args, seed):
                                 "per launch), coarse LOD-1 pass then full pass, per-view completion records")
     out["plain_f32_fifo"]["how"] = "one request at a time, per-frame launches, coarse LOD-1 pass then full pass"
     out["sweep"] = sweep
+    if oracle_rate:
+        out["oracle_s_extrapolated"] = {
+            "s": round(main["samples"] / oracle_rate, 2), "samples_per_s": oracle_rate,
+            "what": "the FP64 oracle's time for the stream's lattice samples, at its rate measured on the "
+                    "batched 512^3 FP16 subset (extrapolated)"}
     return out
 
 
