@@ -835,10 +835,11 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         e = cudaMemcpyAsync(dedges, edges, sizeof(float) * ne, cudaMemcpyHostToDevice, s);
     }
     // hot bins of large grids: the blocks spread their atomics over zeroed copies in stream-ordered
-    // scratch, summed into the output afterwards (which then needs no clearing)
+    // scratch, summed into the output afterwards (which then needs no clearing); the same
+    // scratch holds the row counter that balances the warps
     const size_t count = (size_t)(naxes - 1) * bins * bins;
     const int ncopies = ((uintptr_t)out_counts_dev & 15u) ? 1 : hist_copies(L->n, naxes, bins);
-    const size_t copy_bytes = sizeof(uint32_t) * count * ncopies;
+    const size_t copy_bytes = sizeof(uint32_t) * (count * ncopies + 4);
     uint32_t* copies = nullptr;
     if (e == cudaSuccess && ncopies > 1) {
         e = cudaMallocAsync((void**)&copies, copy_bytes, s);
@@ -851,6 +852,7 @@ raypc_status raypc_pc_histogram(raypc_ctx* ctx, int vol, int lod, const int* axi
         h.out = out_counts_dev;
         h.copies = copies;
         h.ncopies = copies ? ncopies : 1;
+        h.rowctr = copies ? copies + count * ncopies : nullptr;
         h.sactive = use_activity ? L->sactive : nullptr;
         h.nsb = L->nsb;
         e = launch_histogram(h, V->dtype, s);

@@ -331,6 +331,8 @@ struct HistArgs {
     uint32_t* out;                // (naxes-1) x bins x bins
     uint32_t* copies;             // optional: ncopies zeroed partial histograms that the blocks spread
     int ncopies;                  // their atomics over (hot bins), summed into out afterwards
+    uint32_t* rowctr;             // optional: a zeroed counter from which the warps take their rows
+                                  // (null: rows by warp stride)
     const uint32_t* sactive;      // optional: 4^3 sub-brick activity under this brush (cells of inactive
     int nsb;                      // sub-bricks are never counted), sub-bricks per axis
 };

@@ -39,18 +39,18 @@ constexpr int kHistVecWarps = kHistVecThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Number of interior edges e_1..e_{bins-1} that are <= v, for non-decreasing
-// edges: j from an affine guess is the answer iff (j == 0 or v >= e_j) and
-// (j == bins-1 or v < e_{j+1}) -- both edges are loaded at once; otherwise the
-// guess is walked to the answer with comparisons only (exact for any edges;
-// equally spaced edges rarely need a step). NaN compares false everywhere and
-// lands in bin 0.
-__device__ __forceinline__ int bin_of(const float* e, int bins, float v, float e0, float scale) {
-    if (v != v) return 0;
-    float g = fmaf(v, scale, -e0 * scale);                 // any guess is verified below
-    g = fminf(fmaxf(g, 0.0f), (float)(bins - 1));
-    int j = (int)g;
+// edges, from the staged table whose first and last entries are -inf and +inf
+// (stage_edges): j from an affine guess is the answer iff e[j] <= v < e[j+1]
+// (both loaded at once); otherwise the guess is walked to the answer with
+// comparisons of interior edges only (exact for any edges; equally spaced
+// edges rarely need a step). NaN compares false everywhere and lands in bin 0;
+// +inf fails only the last check of bin bins-1 and walks back to it.
+__device__ __forceinline__ int bin_of(const float* e, int bins, float v, float scale, float off) {
+    float g = fmaf(v, scale, off);                         // any guess is verified below
+    g = fminf(fmaxf(g, 0.0f), (float)(bins - 1));          // a NaN guess becomes 0
+    int j = __float_as_int(__fadd_rd(g, 0x1p23f)) - 0x4b000000;   // floor(g): 0 <= g < 2^23
     const float lo = e[j], hi = e[j + 1];
-    if ((j == 0 || v >= lo) && (j == bins - 1 || v < hi)) return j;
+    if ((v >= lo) & (v < hi)) return j;
     while (j > 0 && !(v >= e[j])) --j;
     while (j < bins - 1 && v >= e[j + 1]) ++j;
     return j;
@@ -103,7 +103,10 @@ struct HistLaunch {
     uint32_t sbr;                  // bit s: slot s is tested against the brush
     float slo[kMaxVars], shi[kMaxVars];
     uint32_t slo_h2[kMaxVars], shi_h2[kMaxVars];   // FP16 fields: the same bounds as binary16 pairs
-    float guess_e0[kMaxVars], guess_scale[kMaxVars];
+    float guess_scale[kMaxVars], guess_off[kMaxVars];   // bin guess fma(v, scale, off)
+    long long soff[kMaxVars];      // byte offset of each load slot's plane (vector kernel)
+    int rot;                       // row order: plane z is rotated in y by z * rot (mod n)
+    uint32_t* rowctr;              // zeroed row counter, or null: rows by warp stride
     int s_in, s_out;               // shell test on 2x+1-n etc., clamped to int
     uint32_t* out;                 // nout histograms; block b adds to copy b % nout
     int nout;
@@ -113,39 +116,79 @@ struct HistLaunch {
     float edges_inl[kInlineEdges];
 };
 
-// Copy the edge table into shared memory (all threads; the caller syncs).
+// Copy the edge table into shared memory (all threads; the caller syncs), with
+// each axis's outer edges e_0 and e_bins, which no count depends on, replaced by
+// -inf and +inf so that bin_of checks a guess with two comparisons.
 __device__ __forceinline__ void stage_edges(const HistLaunch& A, float* s_edges) {
     const int ne = A.naxes * (A.bins + 1);
-    if (A.edges)
-        for (int i = threadIdx.x; i < ne; i += blockDim.x) s_edges[i] = __ldg(A.edges + i);
-    else
-        for (int i = threadIdx.x; i < ne; i += blockDim.x) s_edges[i] = A.edges_inl[i];
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) {
+        const int k = i % (A.bins + 1);
+        s_edges[i] = k == 0 ? -INFINITY : k == A.bins ? INFINITY : A.edges ? __ldg(A.edges + i) : A.edges_inl[i];
+    }
 }
 
-// Row geometry shared by both kernels: the x range of row r (y, z) inside the
-// outer sphere, |2x + 1 - n| <= m; false when the whole row lies outside.
+// Row geometry shared by both kernels: the x range of the r-th row (y, z) inside the
+// outer sphere, |2x + 1 - n| <= m, and the range [ca, cb] of its cells inside the
+// inner sphere (empty when ca > cb); false when the whole row lies outside.
+// Rows are taken in z-planes whose y order is rotated by z * rot. With a row
+// counter the vector kernel's warps take the next untaken rows whenever they
+// finish (rot = 0): they finish together whatever the brush leaves in each row.
+// Without one they take rows by warp stride, and rot is a golden-ratio fraction
+// of n: a stride that is a multiple of n would otherwise give every warp one y
+// -- all its rows long chords through the shell or all short ones near the
+// outer sphere. The scalar kernel keeps the plain order (rot = 0).
 struct RowSpan {
-    int y, z, syz, xa, xb;
+    int y, z, syz, xa, xb, ca, cb;
     float cy, cz;
-    size_t base;                   // r * n
+    size_t base;                   // (z n + y) n
     uint32_t srow;                 // first sub-brick id of the row's sub-brick row
 };
 
 __device__ __forceinline__ bool row_span(const HistLaunch& A, int r, RowSpan& R) {
     const int n = A.n;
-    R.y = r % n;
     R.z = r / n;
+    R.y = r - R.z * n + (R.z * A.rot) % n;                  // z * rot < 2^24 for n <= 4096
+    if (R.y >= n) R.y -= n;
     const int dy = 2 * R.y + 1 - n, dz = 2 * R.z + 1 - n;
     R.syz = dy * dy + dz * dz;                              // < 2^31 for n <= 4096
     if (R.syz > A.s_out) return false;
     const int m = isqrt_floor(A.s_out - R.syz);
     R.xa = max(0, (n - m) / 2);
     R.xb = min(n - 1, (n - 1 + m) / 2);
+    R.ca = 1;
+    R.cb = 0;
+    const int din = A.s_in - R.syz;                         // cells with dx^2 < din fail the shell test
+    if (din > 0) {
+        const int mi = isqrt_floor(din - 1);                // |2x + 1 - n| <= mi
+        R.ca = max(0, (n - mi) / 2);
+        R.cb = min(n - 1, (n - 1 + mi) / 2);
+    }
     R.cy = A.use_pos ? cell_centre_rn(R.y, n) : 0.0f;
     R.cz = A.use_pos ? cell_centre_rn(R.z, n) : 0.0f;
-    R.base = (size_t)r * n;
+    R.base = ((size_t)R.z * n + R.y) * n;
     R.srow = ((uint32_t)(R.z >> 2) * A.nsb + (uint32_t)(R.y >> 2)) * A.nsb;
     return true;
+}
+
+// The warp's row after r (r = its warp index - nwarps: its first row). With a
+// row counter, warps take batches of kRowBatch neighbouring rows: warp w starts
+// with batch w, and every later batch is nwarps + the counter's next value,
+// taken one batch ahead in lane 0's rq (first_batch gives its initial value) so
+// that the atomic's latency hides behind a batch's work, and few enough atomics
+// meet at the one address. Without one, rows go by warp stride. Every lane calls
+// it; the result is the same in all of them.
+constexpr int kRowBatch = 2;
+
+__device__ __forceinline__ unsigned first_batch(const HistLaunch& A, int gwarp) {
+    return A.rowctr ? (unsigned)gwarp : 0u;
+}
+
+__device__ __forceinline__ int take_row(const HistLaunch& A, int r, int rows, int nwarps, int lane, unsigned& rq) {
+    if (!A.rowctr) return r + nwarps;
+    if (r >= 0 && (r + 1) % kRowBatch != 0) return r + 1;
+    const int t = (int)__shfl_sync(kFull, rq, 0) * kRowBatch;
+    if (t < rows && lane == 0) rq = (unsigned)nwarps + atomicAdd(A.rowctr, 1u);
+    return t;
 }
 
 // Whether cell x of row R is counted before any brushed value is read: in the
@@ -173,7 +216,8 @@ __device__ __forceinline__ bool cell_geometry_passes(const HistLaunch& A, const 
 
 // Scalar kernel: any grid edge, any alignment, any number of axes. A warp walks
 // one x-row of cells (lanes over x, two cells per lane in flight); persistent
-// grid, rows by warp stride.
+// grid, rows by warp stride in their plain order (the launch gives it rot = 0 and
+// no row counter: either costs this latency-bound kernel registers and time).
 template <int DT>
 __global__ void __launch_bounds__(kHistThreads) k_hist_scalar(const __grid_constant__ HistLaunch A) {
     extern __shared__ float s_edges[];
@@ -236,7 +280,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scalar(const __grid_const
                     if (keep[j]) {
                         const float v = av >= kPosAxisBase ? pos_axis(cx, R.cy, R.cz, cr2, av - kPosAxisBase)
                                                            : load_cell<DT>(A.cells, av * plane + R.base + x);
-                        b = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_e0[a], A.guess_scale[a]);
+                        b = (unsigned)bin_of(s_edges + a * (bins + 1), bins, v, A.guess_scale[a], A.guess_off[a]);
                     }
                     if (a > 0) add_runs(out + (size_t)(a - 1) * bins * bins, prev * (unsigned)bins + b, keep[j], km, lane);
                     prev = b;
@@ -273,30 +317,44 @@ struct ChunkRow {
     int r, xw;                     // r = -1: none
     RowSpan R;
     unsigned kb;
+    unsigned rq;                   // with a row counter, lane 0: the row to take after this one
 };
 
-// Geometric keep bits of this lane's chunk (x0 .. x0 + VEC - 1): in the shell,
-// in an active sub-brick when the activity is given, inside the position brush.
+
+// Bits j of [0, VEC) with lo <= j <= hi.
+template <int VEC>
+__device__ __forceinline__ unsigned span_bits(int lo, int hi) {
+    const int l = max(lo, 0), h = min(hi, VEC - 1);
+    return l > h ? 0u : (2u << h) - (1u << l);
+}
+
+// Geometric keep bits of this lane's chunk (x0 .. x0 + VEC - 1; x0 and n multiples
+// of VEC): in the shell (the row's ranges), in an active sub-brick when the
+// activity is given, inside the position brush. A chunk with a cell in the shell
+// lies inside the row, so its sub-brick ids are valid.
 template <int VEC>
 __device__ __forceinline__ unsigned chunk_geometry(const HistLaunch& A, const RowSpan& R, int x0) {
-    unsigned kb = 0u;
-    if (x0 > R.xb) return 0u;
-    if (A.sactive && !A.pmask) {
+    unsigned kb = span_bits<VEC>(R.xa - x0, R.xb - x0) & ~span_bits<VEC>(R.ca - x0, R.cb - x0);
+    if (kb && A.sactive) {
+        // the chunk's VEC / 4 sub-bricks sit in one activity word unless the first is bit 31
+        const uint32_t sid = R.srow + (uint32_t)(x0 >> 2);
+        unsigned act = __ldg(A.sactive + (sid >> 5)) >> (sid & 31);
+        if (VEC > 4 && (sid & 31) > 32 - VEC / 4) act |= __ldg(A.sactive + (sid >> 5) + 1) << (32 - (sid & 31));
 #pragma unroll
-        for (int q = 0; q < VEC / 4; ++q) {
-            const uint32_t sid = R.srow + (uint32_t)((x0 >> 2) + q);
-            if (!((__ldg(A.sactive + (sid >> 5)) >> (sid & 31)) & 1u)) continue;
+        for (int q = 0; q < VEC / 4; ++q)
+            if (!((act >> q) & 1u)) kb &= ~(0xfu << (4 * q));
+    }
+    if (kb && A.pmask) {
+        BrushArgs pb;
 #pragma unroll
-            for (int j = 4 * q; j < 4 * q + 4; ++j) {
-                const int dx = 2 * (x0 + j) + 1 - A.n;
-                const int sh = dx * dx + R.syz;
-                if (sh >= A.s_in && sh <= A.s_out) kb |= 1u << j;
-            }
+        for (int a = 0; a < kNumPos; ++a) { pb.plo[a] = A.plo[a]; pb.phi[a] = A.phi[a]; }
+        pb.pmask = A.pmask;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const float cx = cell_centre_rn(x0 + j, A.n);
+            if (((kb >> j) & 1u) && !pos_pass(cx, R.cy, R.cz, dot3_rn(cx, R.cy, R.cz, cx, R.cy, R.cz), pb))
+                kb &= ~(1u << j);
         }
-    } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j)
-            if (cell_geometry_passes(A, R, x0 + j)) kb |= 1u << j;
     }
     return kb;
 }
@@ -312,7 +370,7 @@ __device__ __forceinline__ void next_chunk_row(const HistLaunch& A, int nwarps, 
     bool have_row = r >= 0;
     for (;;) {
         if (!have_row || xw > C.R.xb) {
-            r += nwarps;
+            r = take_row(A, r, rows, nwarps, lane, C.rq);
             if (r >= rows) { C.r = -1; C.kb = 0u; return; }
             if (!row_span(A, r, C.R)) { have_row = false; continue; }
             have_row = true;
@@ -342,7 +400,7 @@ __device__ __forceinline__ void bin_round(const HistLaunch& A, const float* s_ed
     for (int a = 0; a < kMaxVars; ++a) {
         bn[a] = 0u;
         if (a >= naxes || !kept) continue;
-        bn[a] = (unsigned)bin_of(s_edges + a * (bins + 1), bins, val[a], A.guess_e0[a], A.guess_scale[a]);
+        bn[a] = (unsigned)bin_of(s_edges + a * (bins + 1), bins, val[a], A.guess_scale[a], A.guess_off[a]);
         packed[a / 3] |= bn[a] << (10 * (a % 3));
     }
     bool same = lane > 0;
@@ -378,8 +436,9 @@ __device__ __forceinline__ void bin_round(const HistLaunch& A, const float* s_ed
 // from the buffer. Neighbouring lanes then hold neighbouring cells, whose bin
 // tuples mostly agree on a smooth field: a lane whose tuple differs from its
 // left neighbour's starts a run and adds the run's length to each
-// adjacent-axis pair (one atomic per pair and run). Persistent grid, rows by warp stride; the edge table is
-// staged once per resident block.
+// adjacent-axis pair (one atomic per pair and run). Persistent grid, rows from
+// the row counter or by warp stride; the edge table is staged once per resident
+// block.
 template <int DT>
 __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_constant__ HistLaunch A) {
     constexpr int VEC = DT == kF16 ? 8 : 4;
@@ -397,7 +456,6 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
     const int n = A.n;
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
     const int bins = A.bins;
-    const size_t plane = (size_t)n * n * n;
     const uint32_t sbr = A.sbr;
     uint32_t* const out = A.out + (size_t)(blockIdx.x % (unsigned)A.nout) * (naxes - 1) * bins * bins;
 
@@ -406,11 +464,10 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
         if (C.r >= 0 && C.kb) {
             const int x0 = C.xw + lane * VEC;
             unsigned char* dst = s_warp + b * buf_bytes + lane * 16;
+            const char* src = static_cast<const char*>(A.cells) + (C.R.base + x0) * (16 / VEC);
 #pragma unroll
             for (int s = 0; s < kMaxVars; ++s)
-                if (s < nslot && A.svar[s] >= 0)
-                    cp_async16(dst + s * 512, static_cast<const char*>(A.cells) +
-                                                  ((size_t)A.svar[s] * plane + C.R.base + x0) * (16 / VEC));
+                if (s < nslot && A.svar[s] >= 0) cp_async16(dst + s * 512, src + A.soff[s]);
         }
         cp_async_commit();
     };
@@ -422,6 +479,7 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
     ChunkRow cur;
     cur.r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) - nwarps;
     cur.xw = 0;
+    cur.rq = first_batch(A, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5));
     next_chunk_row<VEC>(A, nwarps, lane, cur);
     prefetch(cur, 0);
     int b = 0;
@@ -592,8 +650,8 @@ bool fill_launch(const HistArgs& h, HistLaunch& a, bool& vec_slots) {
     for (int i = 0; i < h.naxes && i < kMaxVars; ++i) {
         a.avar[i] = h.axis[i];
         if (h.axis[i] >= kPosAxisBase) a.use_pos = 1;
-        a.guess_e0[i] = h.guess_e0[i];
         a.guess_scale[i] = h.guess_scale[i];
+        a.guess_off[i] = -h.guess_e0[i] * h.guess_scale[i];
     }
     // load slots of the vector kernel: the axes, then the brushed variables that are no axis
     vec_slots = true;
@@ -616,6 +674,10 @@ bool fill_launch(const HistArgs& h, HistLaunch& a, bool& vec_slots) {
         a.slo[s] = a.blo[k];
         a.shi[s] = a.bhi[k];
     }
+    const long long plane_bytes = (long long)h.n * h.n * h.n * (DT == kF16 ? 2 : 4);
+    for (int s = 0; s < a.nslot && s < kMaxVars; ++s) a.soff[s] = a.svar[s] >= 0 ? a.svar[s] * plane_bytes : 0;
+    a.rowctr = h.rowctr;
+    a.rot = h.rowctr ? 0 : (int)(0.6180339887498949 * h.n);
     if (DT == kF16)
         for (int s = 0; s < a.nslot && s < kMaxVars; ++s) {
             const uint32_t lo = half_ceil_bits(a.slo[s]), hi = half_floor_bits(a.shi[s]);
@@ -652,7 +714,7 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     const bool vec = vec_slots && h.n % VEC == 0 && (reinterpret_cast<uintptr_t>(h.cells) & 15u) == 0;
     const size_t smem = vec ? sizeof(float) * (size_t)((ne + 3) & ~3) + (size_t)kHistVecWarps * (2 * a.nslot * 512 + 256)
                             : sizeof(float) * (size_t)ne;
-    // persistent grid: as many blocks as fit at once (rows by warp stride)
+    // persistent grid: as many blocks as fit at once
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -666,6 +728,10 @@ cudaError_t launch_t(const HistArgs& h, cudaStream_t stream) {
     const int warps_per_block = vec ? kHistVecWarps : kHistWarps;
     const long long want_blocks = (rows + warps_per_block - 1) / warps_per_block;
     const int blocks = (int)std::max<long long>(1, std::min<long long>(want_blocks, (long long)sms * std::max(1, per_sm)));
+    if (!vec) {
+        a.rot = 0;
+        a.rowctr = nullptr;
+    }
     if (vec) k_hist<DT><<<blocks, kHistVecThreads, smem, stream>>>(a);
     else k_hist_scalar<DT><<<blocks, kHistThreads, smem, stream>>>(a);
     count_launches(1);

@@ -131,7 +131,7 @@ struct Launch {
 
 size_t output_bytes(const raypc_request& r) {
     if (r.kind == RAYPC_REQ_HISTOGRAM)
-        return align_up(sizeof(uint32_t) * (size_t)(r.naxes - 1) * r.bins * r.bins) +
+        return align_up(sizeof(uint32_t) * ((size_t)(r.naxes - 1) * r.bins * r.bins + 1)) +
                align_up(sizeof(float) * (size_t)r.naxes * (r.bins + 1));
     size_t img = align_up(sizeof(float) * 4 * (size_t)r.w * r.h);
     return img * (r.coarse_lod >= 0 ? 2 : 1) + align_up(sizeof(unsigned long long) * kNStats);
@@ -211,7 +211,10 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     if (q->edges.size() > (size_t)kHistInlineEdges)
         e = cudaMemcpyAsync(q->d_edges, q->edges.data(), sizeof(float) * q->edges.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (size_t)(naxes - 1) * bins * bins, s);
+    // the counts and, after them, the row counter that balances the warps
+    const size_t count = (size_t)(naxes - 1) * bins * bins;
+    h.rowctr = q->hist + count;
+    if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (count + 1), s);
     if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
     if (e != cudaSuccess) return cuda_fail(e, "server histogram");
     return RAYPC_OK;
@@ -287,7 +290,7 @@ void turn(raypc_server* S) {
         char* p = m;
         if (q->r.kind == RAYPC_REQ_HISTOGRAM) {
             q->hist = reinterpret_cast<uint32_t*>(p);
-            p += align_up(sizeof(uint32_t) * (size_t)(q->r.naxes - 1) * q->r.bins * q->r.bins);
+            p += align_up(sizeof(uint32_t) * ((size_t)(q->r.naxes - 1) * q->r.bins * q->r.bins + 1));
             q->d_edges = reinterpret_cast<float*>(p);
         } else {
             const size_t img = align_up(sizeof(float) * 4 * (size_t)q->r.w * q->r.h);

@@ -625,8 +625,7 @@ def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
     vector kernel, the others the scalar one; both must count what the oracle counts, with
     position axes, a repeated axis variable, brushed variables that are no axis, the position
     brush, inactive sub-bricks, and the edges in the launch parameters or on the device.
-    From 128^3 on the blocks spread their counts over partial histograms summed afterwards,
-    and FP16 fields take their bins from a table over all binary16 values."""
+    From 128^3 on the blocks spread their counts over partial histograms summed afterwards."""
     vol = synth.make_shell_volume(n, seed=17)
     st = stored(vol, store)
     cases = [
@@ -656,13 +655,42 @@ def test_histogram_vector_and_scalar_paths_bit_exact(ctx, rp, n, store):
         v.free()
 
 
+@pytest.mark.parametrize("n,store", [(64, "f32"), (128, "f16"), (61, "f32")])
+def test_histogram_shell_radii_and_row_orders(ctx, rp, n, store):
+    """The vector kernel takes each row's in-shell cells as ranges (outer sphere minus
+    inner sphere) and its rows either from a row counter (the regular call from 128^3 on)
+    or by warp stride in a rotated order (smaller grids, the allocation-free entry point);
+    the scalar kernel (61^3) tests cell by cell. All must count what the oracle counts for
+    shells without a core, thin shells, an outer sphere inside the grid and one beyond its
+    corners (the shell is Section 2.1's mantle between the core and the surface)."""
+    vol = synth.make_shell_volume(n, seed=23)
+    st = stored(vol, store)
+    brush = synth.make_brush(vol, "c2")
+    order = (0, 1, 2, 3, 4, 5)
+    edges = synth.make_edges(torch.from_numpy(st), order, 128)
+    cells = synth.to_storage(vol, store).cuda().contiguous()
+    for r_in, r_out in [(0.0, 1.0), (0.9, 1.0), (0.3, 0.7), (0.547, 2.0)]:
+        v = ctx.load_volume(vol.cuda(), store=store, r_in=r_in, r_out=r_out)
+        v.build_bricks()
+        v.set_brush(brush.lo, brush.hi, brush.active_mask)
+        for use in (True, False):
+            Ho, cells_o = oracle.histogram(st, r_in, r_out, brush.lo, brush.hi, brush.active_mask, order, edges,
+                                           use_brush=use)
+            H = v.pc_histogram(order, edges, use_brush=use).cpu().numpy().astype(np.uint32)
+            assert np.array_equal(H, Ho), (r_in, r_out, use)
+            assert cells_o > 0 and int(H[0].sum()) == cells_o
+            Hn = rp.pc_histogram_noalloc(cells, order, edges, brush.lo, brush.hi, brush.active_mask, use,
+                                         r_in=r_in, r_out=r_out).cpu().numpy().astype(np.uint32)
+            assert np.array_equal(Hn, Ho), ("noalloc", r_in, r_out, use)
+        v.free()
+
+
 @pytest.mark.parametrize("n", [48, 128])
 def test_histogram_fp16_bounds_between_and_at_half_values(ctx, n):
     """FP16 fields are tested two cells at a time against binary16 bounds (the smallest
-    half >= lo, the largest half <= hi) and, from 128^3 on, binned by a table over all
-    binary16 values; bounds at, just below and just above stored values, beyond the binary16
-    range, and NaN / infinite cells must count exactly what the oracle's FP32 comparison
-    counts."""
+    half >= lo, the largest half <= hi); bounds at, just below and just above stored values,
+    beyond the binary16 range, and NaN / infinite cells must count exactly what the oracle's
+    FP32 comparison counts, on grids with and without partial histograms."""
     vol = synth.make_shell_volume(n, seed=23)
     f = lambda x: int(round(x * n / 48))                      # the same shell places at every grid size
     vol[0, f(20), f(20):f(30), f(10):f(20)] = float("nan")
