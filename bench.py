@@ -922,7 +922,7 @@ def run_batched(rp, dev, args, seed):
     return {"what": f"{k} views of {n}^3 x 6, image sizes uniform in {{256,512,1024,2048}}^2 "
                     f"({pixels / 1e6:.1f} MP), random orbit cameras, distinct jittered 6-variable brushes",
             "batched_f16": {"ms_per_batch": round(batch_ms, 3), "samples_per_s": round(batch_samples / (batch_ms / 1e3), 1),
-                            "views_per_s": round(k / (batch_ms / 1e3), 1), "launch": "1 CUDA graph (per-view classification + cell classes + persistent render)"},
+                            "views_per_s": round(k / (batch_ms / 1e3), 1), "launch": "1 CUDA graph (per-view classification, cell classes and empty-space distance + persistent render)"},
             "plain_f32_per_frame": {"ms_per_batch": round(plain_ms, 3),
                                     "samples_per_s": round(plain_samples / (plain_ms / 1e3), 1),
                                     "launch": f"{k} x (set_brush + render), default launch choices (8x4 tiles, skipping on)"},

@@ -177,7 +177,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     // a depth output in any view selects the depth instance of the kernel (8x4 tiles)
     bool depth = false;
     for (int i = 0; i < nviews; ++i) depth = depth || views[i].opts.depth_dev != nullptr;
-    unsigned long long cls = 0;
+    unsigned long long cls = 0, dist = 0;
     long long tiles = 0;
     raypc_status st;
     for (int i = 0; i < nviews; ++i) {
@@ -195,7 +195,10 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         finish_position_brush(bv.a);
         if (i == 0) variant = depth ? 1 : bv.a.variant;
         bv.a.variant = variant;
-        const size_t words = L->nwords(), need = words + L->nswords() + L->nsbricks();
+        // per view: brick and sub-brick activity bits, the list of active sub-bricks, and
+        // the sub-bricks' empty-space distance with its scratch (bytes)
+        const size_t nsub = L->nsbricks();
+        const size_t words = L->nwords(), need = words + L->nswords() + nsub + (2 * nsub + 3) / 4;
         if (b->bits_words[i] < need) {
             // growing a slot's masks: no batch may still be reading the old ones
             wait_idle(b);
@@ -210,6 +213,11 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
         bv.a.lv.active = b->bits[i];
         bv.a.lv.sactive = b->bits[i] + words;
         bv.slist = b->bits[i] + words + L->nswords();
+        uint8_t* dist_buf = reinterpret_cast<uint8_t*>(b->bits[i] + words + L->nswords() + nsub);
+        bv.a.lv.sdist = bv.a.skip ? dist_buf : nullptr;   // renders with skipping jump by the distance
+        bv.stmp = dist_buf + nsub;
+        bv.dist_begin = dist;
+        if (bv.a.skip) dist += (nsub + 31) & ~(size_t)31;
         bv.scount = b->d_tiles + b->max_views + i;
         const size_t cells = (size_t)L->n * L->n * L->n;
         if (b->cls_cells[i] < cells) {
@@ -245,6 +253,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     H->nviews = nviews;
     H->total_tiles = (int)tiles;
     H->cls_total = cls;
+    H->dist_total = dist;
     if (!b->exec[slot] || b->exec_key[slot] != dtype * 16 + variant + (depth ? 8 : 0))
         if ((st = capture(b, slot, dtype, variant, depth))) return st;
     CK(cudaGraphLaunch(b->exec[slot], (cudaStream_t)stream), "batch graph launch");
@@ -253,7 +262,7 @@ raypc_status raypc_render_batch(raypc_batch* b, const raypc_view* views, int nvi
     b->last_slot = slot;
     b->seq += 1;
     b->cur ^= 1;
-    count_launches(3);
+    count_launches(6);
     return RAYPC_OK;
 }
 

@@ -282,12 +282,16 @@ struct BatchView {
     unsigned seq;                  // launch sequence number written on completion
     unsigned* tile_done;           // device counter of finished tiles (zeroed per launch)
     ViewDone* done;                // device alias of the mapped host record (may be null)
+    uint8_t* stmp;                 // nsb^3 bytes of scratch for the view's empty-space distance
+    unsigned long long dist_begin; // first flat sub-brick index of the view's distance range (multiple
+                                   // of 32; the range is empty for views that render without skipping)
 };
 
 struct BatchHeader {
     int nviews;
     int total_tiles;
     unsigned long long cls_total;  // flat brick range over all views (multiple of 32)
+    unsigned long long dist_total; // flat sub-brick range of the distance passes over all views
 };
 
 // Render launch variants: a 128-thread block is 2 x 2 warps; each warp marches
@@ -632,6 +636,11 @@ cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream);
 // kDistCap, 0 for active ones (volume_kernels.cu). tmp: nsb^3 bytes of scratch.
 cudaError_t launch_subbrick_distance(const uint32_t* sactive, int nsb, uint8_t* dist, uint8_t* tmp,
                                      cudaStream_t stream);
+// The same for every view of a batch that renders with skipping, from the view's
+// own activity bits into its a.lv.sdist (with its stmp as scratch), after the
+// per-view classification; `blocks` of 256 threads walk the views' ranges.
+cudaError_t launch_subbrick_distance_views(const BatchHeader* hdr, const BatchView* views, unsigned blocks,
+                                           cudaStream_t stream);
 
 // PC line subsample (pcsub_kernels.cu).
 constexpr int kSubMaxSegments = 8192;   // warp-owned row segments of the ordered compaction

@@ -552,6 +552,7 @@ cudaError_t launch_render_batch(const BatchHeader* hdr, const BatchView* views, 
     if (dtype == kF16) k_cell_classes_views<kF16><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
     else k_cell_classes_views<kF32><<<cls_blocks, 32 * kCellWarps, 0, stream>>>(hdr, views);
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_subbrick_distance_views(hdr, views, cls_blocks, stream);
     if (e != cudaSuccess) return e;
     if (depth) {
         if (dtype == kF16) batch_kernels<kF16, 1, true>(hdr, views, tile_counter, blocks, stream);

@@ -564,11 +564,9 @@ __global__ void __launch_bounds__(256) k_tf_visibility(TfVisArgs A) {
 // distance transform is separable: d(p) = min over qz of max(|dz|, min over qy of
 // max(|dy|, min over active qx of |dx|)), each 1D pass a window of +-kDistCap.
 // pass 0: x from the activity bits into a; 1: y from a into b; 2: z from b into a.
-__global__ void __launch_bounds__(256) k_subbrick_distance(const uint32_t* __restrict__ act, int nsb, int pass,
-                                                           const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
-    const size_t total = (size_t)nsb * nsb * nsb;
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= total) return;
+// One sub-brick id < nsb^3 of one pass.
+__device__ __forceinline__ uint8_t subbrick_distance_at(const uint32_t* __restrict__ act, int nsb, int pass,
+                                                      const uint8_t* __restrict__ in, size_t id) {
     const int x = (int)(id % nsb), y = (int)((id / nsb) % nsb), z = (int)(id / ((size_t)nsb * nsb));
     int d = kDistCap;
     if (pass == 0) {
@@ -587,7 +585,42 @@ __global__ void __launch_bounds__(256) k_subbrick_distance(const uint32_t* __res
             d = min(d, max(abs(o), (int)__ldg(in + (size_t)((long long)id + (long long)o * (long long)stride))));
         }
     }
-    out[id] = (uint8_t)d;
+    return (uint8_t)d;
+}
+
+__global__ void __launch_bounds__(256) k_subbrick_distance(const uint32_t* __restrict__ act, int nsb, int pass,
+                                                           const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
+    const size_t total = (size_t)nsb * nsb * nsb;
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total) return;
+    out[id] = subbrick_distance_at(act, nsb, pass, in, id);
+}
+
+// Every view of a batch: the threads walk the views' concatenated distance ranges (a
+// warp's 32 consecutive flat indices always belong to one view); pass 0 writes the
+// view's distance buffer, 1 its scratch, 2 the distance buffer again.
+__global__ void __launch_bounds__(256) k_subbrick_distance_views(const BatchHeader* __restrict__ hdr,
+                                                                 const BatchView* __restrict__ views, int pass) {
+    const unsigned long long total = hdr->dist_total;
+    const int nviews = hdr->nviews;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const unsigned long long g0 = g - lane;
+        int lo = 0, hi = nviews - 1;                 // the last view whose range starts at or before g0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (views[mid].dist_begin <= g0) lo = mid; else hi = mid - 1;
+        }
+        const BatchView& V = views[lo];
+        const int nsb = V.a.lv.nsb;
+        const size_t id = (size_t)(g - V.dist_begin);
+        if (id >= (size_t)nsb * nsb * nsb) continue;   // the padding of the view's range
+        uint8_t* dist = const_cast<uint8_t*>(V.a.lv.sdist);
+        const uint8_t* in = pass == 1 ? dist : V.stmp;
+        uint8_t* out = pass == 1 ? V.stmp : dist;
+        out[id] = subbrick_distance_at(V.a.lv.sactive, nsb, pass, in, id);
+    }
 }
 
 cudaError_t launch_subbrick_distance(const uint32_t* sactive, int nsb, uint8_t* dist, uint8_t* tmp,
@@ -599,6 +632,16 @@ cudaError_t launch_subbrick_distance(const uint32_t* sactive, int nsb, uint8_t* 
     k_subbrick_distance<<<blocks, 256, 0, stream>>>(sactive, nsb, 2, tmp, dist);
     count_launches(3);
     return cudaGetLastError();
+}
+
+cudaError_t launch_subbrick_distance_views(const BatchHeader* hdr, const BatchView* views, unsigned blocks,
+                                           cudaStream_t stream) {
+    for (int pass = 0; pass < 3; ++pass) {
+        k_subbrick_distance_views<<<blocks, 256, 0, stream>>>(hdr, views, pass);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_tf_visibility(const TfVisArgs& a, cudaStream_t stream) {
