@@ -131,3 +131,37 @@ def test_autotune_records_a_choice_used_by_auto(rp, tmp_path, monkeypatch):
         expl, _ = v.render(cam, 64, 48, variant=best["variant"], skip=best["skip"])
         assert torch.equal(auto, expl)
         v.free()
+
+
+def test_batched_views_skip_by_their_own_distance(rp):
+    """The batch graph computes each skipping view's empty-space distance from the view's
+    own brush (Section 2.2: no structure rebuilt when the brush changes): skipped sample
+    counts equal the single-frame render's, and pixels and per-pixel counts stay those
+    of the render without skipping."""
+    with rp.Context(0) as ctx:
+        v, src = _volume(ctx, 128, "f16", 8)
+        st = synth.to_storage(src, "f16").float()
+        cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+        views, singles = [], []
+        for i, bname in enumerate(("c3", "c1", "c2")):
+            b = synth.make_brush(st, bname)
+            v.set_brush(b.lo, b.hi, b.active_mask)
+            s1 = torch.zeros(8, dtype=torch.int64, device="cuda")
+            img, cnt = v.render(cam, 160, 120, skip=True, counts=True, stats=s1)
+            img0, cnt0 = v.render(cam, 160, 120, skip=False, counts=True)
+            assert torch.equal(img, img0) and torch.equal(cnt, cnt0)
+            singles.append((img0, cnt0, s1))
+            views.append(dict(vol=v, cam=cam, w=160, h=120, lo=b.lo, hi=b.hi, mask=b.active_mask, counts=True,
+                              stats=torch.zeros(8, dtype=torch.int64, device="cuda"), skip=True))
+        with rp.Batch(ctx, 4) as batch:
+            plain = dict(views[0], skip=False, stats=torch.zeros(8, dtype=torch.int64, device="cuda"))
+            outs = batch.render(views + [plain])
+            torch.cuda.synchronize()
+        skipped = 0
+        for (img0, cnt0, s1), q, (img, cnt) in zip(singles, views, outs):
+            assert torch.equal(img, img0) and torch.equal(cnt, cnt0)
+            assert torch.equal(q["stats"], s1)
+            skipped += int(q["stats"][3])
+        assert skipped > 0
+        assert int(plain["stats"][3]) == 0 and torch.equal(outs[3][0], singles[0][0])
+        v.free()
