@@ -1204,7 +1204,7 @@ def main(argv=None):
     ap.add_argument("--serve-n", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=240)
     ap.add_argument("--serve-load", type=float, default=0.8, help="arrival rate / plain FP32 capacity")
-    ap.add_argument("--serve-sweep", default="0.3,0.6,0.9,1.2", help="further loads, comma-separated")
+    ap.add_argument("--serve-sweep", default="0.3,0.6,0.9,1.2,2.0", help="further loads, comma-separated")
     ap.add_argument("--serve-inflight", type=int, default=32)
     ap.add_argument("--serve-budget-mb", type=int, default=4096)
     ap.add_argument("--serve-streams", type=int, default=3)
