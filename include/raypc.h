@@ -364,11 +364,12 @@ typedef struct raypc_batch raypc_batch;
  * table, per-view classification bitmasks and sub-brick lists, per-view cell
  * classes, a tile counter and a CUDA graph of the batched launch (table
  * upload, per-view brick and sub-brick classification, per-view cell classes,
- * one persistent render kernel), captured on first use and replayed
- * afterwards. Allocates device and pinned host memory; the per-view buffers
- * are allocated for a view slot on its first use and grown for larger levels:
- * n^3 * 2 bytes of cell classes plus about n^3 / 16 bytes of masks and lists
- * per used slot (268 MB at 512^3), charged to the context's budget. */
+ * the empty-space distance of every view that renders with skipping, one
+ * persistent render kernel), captured on first use and replayed afterwards.
+ * Allocates device and pinned host memory; the per-view buffers are allocated
+ * for a view slot on its first use and grown for larger levels: n^3 * 2 bytes
+ * of cell classes plus about n^3 / 10 bytes of masks, lists and distances per
+ * used slot (281 MB at 512^3), charged to the context's budget. */
 raypc_status raypc_batch_create(raypc_ctx *ctx, int max_views, raypc_batch **out);
 raypc_status raypc_batch_destroy(raypc_batch *batch);
 
@@ -376,7 +377,9 @@ raypc_status raypc_batch_destroy(raypc_batch *batch);
  * results bit for bit as raypc_render of each view with its brush set). Every
  * view's volume must have bricks built (not stale after an update), a transfer
  * function, and the same storage dtype. The tile variant of the launch is view
- * 0's (after RAYPC_AUTO resolution); skipping is chosen per view. Work is split into 16x8-pixel tiles
+ * 0's (after RAYPC_AUTO resolution); skipping is chosen per view, and a view
+ * with skipping jumps by the empty-space distance of its own classification,
+ * as a single-frame render does. Work is split into 16x8-pixel tiles
  * pulled dynamically by persistent thread blocks, so large and small images
  * balance across the GPU. The call returns after enqueueing; it may wait for
  * the batch submitted two calls earlier on this batch object to finish (the
