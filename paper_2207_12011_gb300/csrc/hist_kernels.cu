@@ -524,16 +524,16 @@ __global__ void __launch_bounds__(kHistVecThreads, 2) k_hist(const __grid_consta
             }
         }
         // compact list of the surviving cells (chunk-row offsets) in x order: the exclusive
-        // prefix of the per-lane counts (<= 8, four bits) from one ballot per bit
+        // prefix of the per-lane counts from an inclusive shuffle scan
         const unsigned cnt = (unsigned)__popc(kb);
-        const unsigned below = (1u << lane) - 1u;
-        int pos = 0, total = 0;
+        unsigned inc = cnt;
 #pragma unroll
-        for (int bit = 0; bit < 4; ++bit) {
-            const unsigned m = __ballot_sync(kFull, (cnt >> bit) & 1u);
-            pos += __popc(m & below) << bit;
-            total += __popc(m) << bit;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned t = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += t;
         }
+        int pos = (int)(inc - cnt);
+        const int total = (int)__shfl_sync(kFull, inc, 31);
 #pragma unroll
         for (int j = 0; j < VEC; ++j)
             if ((kb >> j) & 1u) s_list[pos++] = (unsigned char)(lane * VEC + j);
