@@ -252,8 +252,17 @@ raypc_status ingest(raypc_ctx* ctx, Volume* V, const void* src, int src_is_devic
         if (e != cudaSuccess) { cudaFreeAsync(staging, s); return cuda_fail(e, "host to device copy"); }
         dsrc = staging;
     }
-    e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, L.sbmin,
-                      L.sbmax, s);
+    // when the next level is allocated (raypc_build_bricks built it before), its cells and
+    // x-pairs come out of the same pass over the source
+    Level& C = V->lv[1];
+    const bool next = C.cells && C.pairs && C.n * 2 == L.n && ingest_next_level_fits(dsrc, L.n);
+    if (next)
+        e = launch_ingest_next_level(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax,
+                                     L.sbmin, L.sbmax, C.cells, C.pairs, s);
+    else
+        e = launch_ingest(dsrc, src_dtype, L.cells, L.pairs, V->dtype, L.n, V->nvars, L.bmin, L.bmax, L.sbmin,
+                          L.sbmax, s);
+    C.fresh = next && e == cudaSuccess;
     if (staging) cudaFreeAsync(staging, s);
     if (staged && e == cudaSuccess) {
         e = cudaEventRecord(V->ev_consumed[slot], s);  // the staging buffer is free once this ingest ran
@@ -569,8 +578,13 @@ raypc_status raypc_build_bricks(raypc_ctx* ctx, int vol, int brick_dim, int n_lo
             if (st) return st;
         }
         if ((st = alloc_bricks(ctx, V, L))) return st;
-        CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, L.bmin, L.bmax, L.sbmin, L.sbmax, s),
-           "LOD kernel");
+        if (L.fresh)             // the ingest already wrote this level's cells: its bricks only
+            CK(launch_level_bricks(L.cells, V->dtype, L.n, V->nvars, L.bmin, L.bmax, L.sbmin, L.sbmax, s),
+               "level bricks kernel");
+        else
+            CK(launch_lod(P.cells, P.n, L.cells, L.pairs, V->dtype, V->nvars, L.bmin, L.bmax, L.sbmin, L.sbmax, s),
+               "LOD kernel");
+        L.fresh = false;
         L.bricks = true;
     }
     if (V->stale || 1 + n_lod > V->nlev) V->nlev = 1 + n_lod;   // stale coarser levels drop out

@@ -585,6 +585,17 @@ cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pai
                           cudaStream_t stream);
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,
                        float* bmin, float* bmax, float* sbmin, float* sbmax, cudaStream_t stream);
+// Ingest that also writes the next level's cells and x-pairs (edge n / 2, the same
+// 2x2x2 means as launch_lod, from the values it stores) in the same pass over the
+// source; that level's brick min/max then come from launch_level_bricks. Only when
+// ingest_next_level_fits(src, n): n a multiple of 16 from 128 up, a 16-byte aligned source.
+bool ingest_next_level_fits(const void* src, int n);
+cudaError_t launch_ingest_next_level(const void* src, int src_dtype, void* cells, void* pairs, int dtype, int n,
+                                     int nvars, float* bmin, float* bmax, float* sbmin, float* sbmax,
+                                     void* next_cells, void* next_pairs, cudaStream_t stream);
+// Brick and sub-brick min/max of a level from its own stored cells.
+cudaError_t launch_level_bricks(const void* cells, int dtype, int n, int nvars, float* bmin, float* bmax,
+                                float* sbmin, float* sbmax, cudaStream_t stream);
 cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream);
 cudaError_t launch_cell_classes(const CellClassArgs& a, int dtype, cudaStream_t stream);
 cudaError_t launch_render(const RenderArgs& a, int dtype, cudaStream_t stream);

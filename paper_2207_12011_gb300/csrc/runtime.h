@@ -66,6 +66,8 @@ struct Level {
     bool cls_valid = false;
     bool bricks = false;
     bool classified = false;
+    bool fresh = false;           // cells and pairs written by the last ingest of the finer level,
+                                  // brick min/max not yet (raypc_build_bricks computes them)
     size_t nbricks() const { return (size_t)nb * nb * nb; }
     size_t nwords() const { return (nbricks() + 31) / 32; }
     size_t nsbricks() const { return (size_t)nsb * nsb * nsb; }

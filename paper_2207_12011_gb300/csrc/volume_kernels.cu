@@ -18,7 +18,8 @@ template <> __device__ __forceinline__ float to_stored<kF32>(float v) { return v
 template <> __device__ __forceinline__ float to_stored<kF16>(float v) { return __half2float(__float2half_rn(v)); }
 
 struct RowsArgs {
-    const void* src;      // ingest: planar source (src_dtype); LOD: planar cells of the finer level
+    const void* src;      // ingest: planar source (src_dtype); LOD: planar cells of the finer level;
+                          // bricks only: planar cells of this level
     int src_dtype;        // ingest only
     int n_src;            // LOD: edge of the finer level
     void* cells;          // this level, planar
@@ -29,6 +30,8 @@ struct RowsArgs {
     float* bmax;
     float* sbmin;         // [nsb^3][nvars], sub-bricks of edge kSub
     float* sbmax;
+    void* ccells;         // ingest with the next level: its planar cells (edge n / 2) ...
+    void* cpairs;         // ... and x-pairs
 };
 
 __device__ __forceinline__ void fold(float& mn, float& mx, float a_mn, float a_mx) {
@@ -132,12 +135,15 @@ __device__ __forceinline__ void store_run(void* cells, void* pairs, size_t i, co
 //   MODE 0 (ingest): the converted source value (source element type SRC).
 //   MODE 1 (LOD):    FP32 mean of the 2x2x2 fine cells, fine indices clamped,
 //                    ((c000 + c100) + (c010 + c110)) + ((c001 + c101) + (c011 + c111)), x 1/8.
+//   MODE 2 (ingest and the next level): as MODE 0; the kernel also forms the next
+//                    level's means from the values it produced (n a multiple of 16).
+//   MODE 3 (bricks only): the level's own stored cells, for its brick min/max.
 // With VEC > 1 the caller guarantees n % VEC == 0 and, for LOD, an even fine edge.
 template <int DT, int MODE, int SRC, int VEC>
 __device__ __forceinline__ void produce_run(const RowsArgs& A, int X, int y, int z, int v, float* val) {
     const int n = A.n;
     const bool right = X + VEC < n;
-    if (MODE == 0) {
+    if (MODE != 1) {
         const size_t row = (((size_t)v * n + z) * n + y) * n;
         load_run<SRC, VEC>(A.src, row + X, val);
         load_run<SRC, 1>(A.src, row + (right ? X + VEC : X + VEC - 1), val + VEC);
@@ -199,11 +205,55 @@ __device__ __forceinline__ void produce_run(const RowsArgs& A, int X, int y, int
 constexpr int kRowCols = 64;                            // column threads per block (blockDim.x)
 constexpr int kRowSlices = kBrick + 1;                  // blockDim.y
 
+// The next level's two cells (2 t, 2 t + 1) of one row, from the per-slice sums in
+// shared memory, stored with their x-pairs at flat index i (even). The pair of cell
+// 2 t + 1 needs cell 2 t + 2: from the neighbouring thread, the cell itself at the
+// row's end, or -- at the end of a column chunk -- from the next chunk's first
+// thread, which writes that half (`whole` false: only the first half here).
+template <int DT>
+__device__ __forceinline__ void store_next_level(void* cells, void* pairs, size_t i, float v0, float v1, float r,
+                                                 bool whole) {
+    if (DT == kF32) {
+        float* c = reinterpret_cast<float*>(cells) + i;
+        float* p = reinterpret_cast<float*>(pairs) + 2 * i;
+        *reinterpret_cast<float2*>(c) = make_float2(v0, v1);
+        if (whole) {
+            *reinterpret_cast<float4*>(p) = make_float4(v0, v1, v1, r);
+        } else {
+            *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
+            p[2] = v1;
+        }
+    } else {
+        const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1), hr = __float2half_rn(r);   // exact
+        __half2 c01 = __halves2half2(h0, h1), c1r = __halves2half2(h1, hr);
+        *reinterpret_cast<__half2*>(reinterpret_cast<__half*>(cells) + i) = c01;
+        __half* p = reinterpret_cast<__half*>(pairs) + 2 * i;
+        if (whole) {
+            uint2 w;
+            w.x = *reinterpret_cast<unsigned*>(&c01);
+            w.y = *reinterpret_cast<unsigned*>(&c1r);
+            *reinterpret_cast<uint2*>(p) = w;
+        } else {
+            *reinterpret_cast<__half2*>(p) = c01;
+            p[2] = h1;
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void store_pair_second(void* pairs, size_t i, float v) {
+    if (DT == kF32) reinterpret_cast<float*>(pairs)[2 * i + 1] = v;
+    else reinterpret_cast<__half*>(pairs)[2 * i + 1] = __float2half_rn(v);
+}
+
 template <int DT, int MODE, int SRC, int VEC>
 __global__ void __launch_bounds__(kRowCols * kRowSlices, 2) k_rows(RowsArgs A) {
     constexpr int G = kSub / VEC;                       // lanes per sub-brick column
-    constexpr int kBatch = MODE == 0 ? 3 : 1;          // rows whose loads are issued together
+    constexpr int kBatch = MODE == 1 ? 1 : 3;          // rows whose loads are issued together
+    constexpr int kHalf = kBrick / 2;
     __shared__ float s_half[kRowSlices][4][kRowCols];  // per slice: min, max of y half 0, then of half 1
+    // MODE 2: per fine slice and coarse row, the sums over the row pair of the x-pair sums
+    __shared__ float s_next[MODE == 2 ? kBrick : 1][kHalf][2][kRowCols];
     const int n = A.n;
     const int nb = (n + kBrick - 1) / kBrick;
     const int nsb = (n + kSub - 1) / kSub;
@@ -217,6 +267,7 @@ __global__ void __launch_bounds__(kRowCols * kRowSlices, 2) k_rows(RowsArgs A) {
         const bool valid = t < ncol && z < n;
         const int X = t * VEC;
         float ymn[2] = {qnan, qnan}, ymx[2] = {qnan, qnan};
+        float even0 = 0.0f, even1 = 0.0f;                // MODE 2: x-pair sums of the even row
 #pragma unroll
         for (int dy0 = 0; dy0 <= kBrick; dy0 += kBatch) {
             float val[kBatch][VEC + 1];
@@ -235,8 +286,19 @@ __global__ void __launch_bounds__(kRowCols * kRowSlices, 2) k_rows(RowsArgs A) {
                 for (int q = 1; q <= VEC; ++q) fold(rmn, rmx, val[j][q], val[j][q]);
                 if (dy <= kSub) fold(ymn[0], ymx[0], rmn, rmx);
                 if (dy >= kSub) fold(ymn[1], ymx[1], rmn, rmx);
-                if (dy < kBrick && dz < kBrick)
+                if (MODE != 3 && dy < kBrick && dz < kBrick)
                     store_run<DT, VEC>(A.cells, A.pairs, (((size_t)v * n + z) * n + y) * n + X, val[j]);
+                if (MODE == 2 && dy < kBrick && dz < kBrick) {
+                    // the next level's mean, in its order: (c000 + c100) + (c010 + c110) per fine slice
+                    const float p0 = __fadd_rn(val[j][0], val[j][1]), p1 = __fadd_rn(val[j][2], val[j][3]);
+                    if ((dy & 1) == 0) {
+                        even0 = p0;
+                        even1 = p1;
+                    } else {
+                        s_next[MODE == 2 ? dz : 0][dy >> 1][0][tx] = __fadd_rn(even0, p0);
+                        s_next[MODE == 2 ? dz : 0][dy >> 1][1][tx] = __fadd_rn(even1, p1);
+                    }
+                }
             }
         }
         s_half[dz][0][tx] = ymn[0];
@@ -283,6 +345,24 @@ __global__ void __launch_bounds__(kRowCols * kRowSlices, 2) k_rows(RowsArgs A) {
                 const size_t b = ((size_t)bz * nb + by) * nb + bx;
                 A.bmin[b * A.nvars + v] = bmn;
                 A.bmax[b * A.nvars + v] = bmx;
+            }
+        }
+        if (MODE == 2 && dz < kHalf && t < ncol) {
+            // the next level's cells 2t, 2t+1 of its rows 4 by .. 4 by + 3 in slice 4 bz + dz:
+            // ((fine slice 2 dz) + (fine slice 2 dz + 1)) / 8
+            const int m = n >> 1;
+            const bool row_end = t + 1 >= ncol, chunk_end = tx + 1 >= (int)blockDim.x;
+            const int s0 = MODE == 2 ? 2 * dz : 0, s1 = MODE == 2 ? 2 * dz + 1 : 0;
+#pragma unroll
+            for (int k = 0; k < kHalf; ++k) {
+                const float v0 = to_stored<DT>(__fmul_rn(__fadd_rn(s_next[s0][k][0][tx], s_next[s1][k][0][tx]), 0.125f));
+                const float v1 = to_stored<DT>(__fmul_rn(__fadd_rn(s_next[s0][k][1][tx], s_next[s1][k][1][tx]), 0.125f));
+                float r = v1;                            // the row's last cell pairs with itself
+                if (!row_end && !chunk_end)
+                    r = to_stored<DT>(__fmul_rn(__fadd_rn(s_next[s0][k][0][tx + 1], s_next[s1][k][0][tx + 1]), 0.125f));
+                const size_t i = (((size_t)v * m + (size_t)(bz * kHalf + dz)) * m + (size_t)(by * kHalf + k)) * m + 2 * t;
+                store_next_level<DT>(A.ccells, A.cpairs, i, v0, v1, r, row_end || !chunk_end);
+                if (tx == 0 && t > 0) store_pair_second<DT>(A.cpairs, i - 1, v0);   // the previous chunk's last pair
             }
         }
         __syncthreads();                                 // s_half is rewritten by the next column chunk
@@ -416,9 +496,18 @@ cudaError_t launch_rows(const RowsArgs& a, int dtype, cudaStream_t stream) {
     // source (ingest) or an even fine edge (LOD; n % 4 == 0 makes it 8k) -- and
     // the level is wide enough to fill a warp with runs.
     bool vec = a.n % 4 == 0 && a.n >= 128;
-    if (MODE == 0) vec = vec && ((uintptr_t)a.src % 16 == 0);
-    else vec = vec && a.n_src == 2 * a.n;
-    if (MODE == 0) {
+    if (MODE == 1) vec = vec && a.n_src == 2 * a.n;
+    else vec = vec && ((uintptr_t)a.src % 16 == 0);
+    if (MODE == 2) {
+        // the fused next level needs 4-column runs and whole bricks of both levels
+        if (!vec || a.n % 16 != 0 || !a.ccells || !a.cpairs) return cudaErrorInvalidValue;
+        const bool s16 = a.src_dtype == kF16;
+        if (dtype == kF16) { if (s16) launch_rows_t<kF16, 2, kF16, 4>(a, grid, stream); else launch_rows_t<kF16, 2, kF32, 4>(a, grid, stream); }
+        else               { if (s16) launch_rows_t<kF32, 2, kF16, 4>(a, grid, stream); else launch_rows_t<kF32, 2, kF32, 4>(a, grid, stream); }
+    } else if (MODE == 3) {
+        if (dtype == kF16) { if (vec) launch_rows_t<kF16, 3, kF16, 4>(a, grid, stream); else launch_rows_t<kF16, 3, kF16, 1>(a, grid, stream); }
+        else               { if (vec) launch_rows_t<kF32, 3, kF32, 4>(a, grid, stream); else launch_rows_t<kF32, 3, kF32, 1>(a, grid, stream); }
+    } else if (MODE == 0) {
         const bool s16 = a.src_dtype == kF16;
         if (dtype == kF16) {
             if (vec) { if (s16) launch_rows_t<kF16, 0, kF16, 4>(a, grid, stream); else launch_rows_t<kF16, 0, kF32, 4>(a, grid, stream); }
@@ -452,6 +541,43 @@ cudaError_t launch_ingest(const void* src, int src_dtype, void* cells, void* pai
     a.sbmin = sbmin;
     a.sbmax = sbmax;
     return launch_rows<0>(a, dtype, stream);
+}
+
+bool ingest_next_level_fits(const void* src, int n) {
+    return n % 16 == 0 && n >= 128 && n <= kMaxRowsEdge && (uintptr_t)src % 16 == 0;
+}
+
+cudaError_t launch_ingest_next_level(const void* src, int src_dtype, void* cells, void* pairs, int dtype, int n,
+                                     int nvars, float* bmin, float* bmax, float* sbmin, float* sbmax,
+                                     void* next_cells, void* next_pairs, cudaStream_t stream) {
+    RowsArgs a{};
+    a.src = src;
+    a.src_dtype = src_dtype;
+    a.cells = cells;
+    a.pairs = pairs;
+    a.n = n;
+    a.nvars = nvars;
+    a.bmin = bmin;
+    a.bmax = bmax;
+    a.sbmin = sbmin;
+    a.sbmax = sbmax;
+    a.ccells = next_cells;
+    a.cpairs = next_pairs;
+    return launch_rows<2>(a, dtype, stream);
+}
+
+cudaError_t launch_level_bricks(const void* cells, int dtype, int n, int nvars, float* bmin, float* bmax,
+                                float* sbmin, float* sbmax, cudaStream_t stream) {
+    RowsArgs a{};
+    a.src = cells;
+    a.src_dtype = dtype;
+    a.n = n;
+    a.nvars = nvars;
+    a.bmin = bmin;
+    a.bmax = bmax;
+    a.sbmin = sbmin;
+    a.sbmax = sbmax;
+    return launch_rows<3>(a, dtype, stream);
 }
 
 cudaError_t launch_lod(const void* fine, int n_fine, void* cells, void* pairs, int dtype, int nvars,

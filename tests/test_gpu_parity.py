@@ -151,6 +151,49 @@ def test_lod_and_bricks_bit_exact(rp, ctx, store, n):
     v.free()
 
 
+@pytest.mark.parametrize("store,n,src16", [("f32", 128, False), ("f16", 272, False), ("f16", 128, True),
+                                           ("f32", 120, False)])
+def test_update_writes_the_next_level_bit_exact(rp, ctx, store, n, src16):
+    """Once the coarser levels exist, an update's ingest also writes level 1's cells and
+    x-pairs in the same pass over the source (grid edges that are multiples of 16 from 128
+    up; 120 takes the separate LOD pass) and raypc_build_bricks adds only its brick min/max:
+    every level and its bricks must still equal the oracle's 2x2x2 means (Section 2.1), for
+    rows that span one or two column chunks, FP32 and FP16 storage, FP32 and FP16 sources."""
+    first = synth.make_shell_volume(n, seed=31)
+    second = synth.make_shell_volume(n, seed=32)
+    v = load(ctx, first, store, n_lod=2)
+    src = second.half() if src16 else second
+    v.update(src.cuda())
+    v.build_bricks(n_lod=2)
+    levels = oracle_levels(stored(src.float(), store), 2, store)
+    for lod in range(3):
+        got = v.export(lod).float().cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), levels[lod].view(np.uint32)), lod
+        mn, mx = v.bricks(lod)
+        omn, omx = oracle.brick_minmax(levels[lod])
+        assert np.array_equal(mn.cpu().numpy(), omn) and np.array_equal(mx.cpu().numpy(), omx), lod
+        smn, smx, _ = v.sub_bricks(lod, classify=False)
+        omn4, omx4 = oracle.brick_minmax(levels[lod], 4)
+        assert np.array_equal(smn.cpu().numpy(), omn4) and np.array_equal(smx.cpu().numpy(), omx4), lod
+    # the x-pairs of level 1 (the render's layout) agree with its cells
+    tf = synth.make_tf(torch.from_numpy(levels[0]), "T_anom")
+    v.set_tf(tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi)
+    b = synth.make_brush(torch.from_numpy(levels[0]), "c2")
+    v.set_brush(b.lo, b.hi, b.active_mask)
+    cam = synth.orbit_camera(**synth.DEFAULT_CAMERA)
+    pix = np.stack(np.meshgrid(np.arange(0, 96, 5), np.arange(0, 64, 3)), -1).reshape(-1, 2)
+    img, cnt = v.render(cam, 96, 64, lod=1, counts=True)
+    flat = pix[:, 1] * 96 + pix[:, 0]
+    o_rgba, o_cnt = oracle.render(levels[1], R_IN, R_OUT, cam.as_array(), 96, 64, 1.0 / levels[1].shape[1],
+                                  b.lo, b.hi, b.active_mask, tf.rgbs, tf.color_var, tf.v_lo, tf.v_hi,
+                                  pixels=flat)
+    g = img.cpu().numpy().reshape(-1, 4)[flat]
+    gc = cnt.cpu().numpy().reshape(-1, 2)[flat]
+    assert np.array_equal(gc, o_cnt)
+    assert np.abs(g - o_rgba).max() <= TOL[store]
+    v.free()
+
+
 @pytest.mark.parametrize("brush_name", ["c1", "c2", "c3", "empty", "none"])
 def test_classification_bit_exact(rp, ctx, brush_name):
     n = 64
