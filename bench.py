@@ -353,7 +353,7 @@ def accuracy_report(wl, gpu_img, vol_np, src_np=None, count_row_stride=4):
 
 
 def config_section(rp, name, args, dev, seed, rank, sm_mhz=2070.0):
-    """One BASELINE configuration measured on its own: K whole-path steps (ingest, LOD, bricks,
+    """One benchmark configuration measured on its own: K whole-path steps (ingest, LOD, bricks,
     brush, render, histograms) with CUDA events around the render and the histograms, the
     resident-volume frame loop, the render and histogram rooflines, and (rank 0) the full-frame
     accuracy against the oracle."""
