@@ -151,6 +151,8 @@ struct raypc_server {
     std::vector<int> busy;              // launches in flight per stream
     std::vector<cudaStream_t> streams;
     std::vector<raypc_batch*> batches;
+    std::vector<void*> hscratch;        // per stream: histogram scratch (partial copies, sub-brick bits)
+    std::vector<size_t> hscratch_bytes;
     Pool pool;
     char* pool_mem = nullptr;
     uint64_t next_id = 1;
@@ -173,8 +175,14 @@ void finish(raypc_server* S, Req* q, int status) {
         }
 }
 
-// Histogram of one request on stream s (the request's brush, its own edges).
-raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
+// Histogram of one request on stream si (the request's brush, its own edges). Like
+// raypc_pc_histogram, a brushed request first classifies the level's sub-bricks
+// under its own brush, so the kernel skips the cells of inactive ones, and large
+// grids spread the counts over zeroed partial histograms that a reduction sums
+// into the output; both live in the stream's scratch, which the requests of one
+// stream use one after the other in stream order.
+raypc_status launch_hist(raypc_server* S, Req* q, int si) {
+    cudaStream_t s = S->streams[si];
     std::lock_guard<std::mutex> lk(S->ctx->mu);
     DeviceGuard g(S->ctx->device);
     Volume* V = nullptr;
@@ -211,11 +219,58 @@ raypc_status launch_hist(raypc_server* S, Req* q, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
     if (q->edges.size() > (size_t)kHistInlineEdges)
         e = cudaMemcpyAsync(q->d_edges, q->edges.data(), sizeof(float) * q->edges.size(), cudaMemcpyHostToDevice, s);
-    // the counts and, after them, the row counter that balances the warps
+    // scratch: the partial copies and their row counter (large grids), then the sub-brick bits
     const size_t count = (size_t)(naxes - 1) * bins * bins;
-    h.rowctr = q->hist + count;
-    if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (count + 1), s);
-    if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
+    const int ncopies = ((uintptr_t)q->hist & 15u) ? 1 : hist_copies(L->n, naxes, bins);
+    const size_t copy_bytes = ncopies > 1 ? (sizeof(uint32_t) * (count * ncopies + 4) + 255) / 256 * 256 : 0;
+    const bool activity = h.use_brush && L->sbmin;
+    const size_t need = copy_bytes + (activity ? sizeof(uint32_t) * L->nswords() : 0);
+    if (need > S->hscratch_bytes[si]) {
+        // the stream's earlier histograms may still read the old scratch
+        if (S->hscratch[si]) {
+            cudaStreamSynchronize(s);
+            cudaFree(S->hscratch[si]);
+            S->ctx->used -= S->hscratch_bytes[si] < S->ctx->used ? S->hscratch_bytes[si] : S->ctx->used;
+            S->hscratch[si] = nullptr;
+            S->hscratch_bytes[si] = 0;
+        }
+        size_t charged = 0;
+        if ((st = S->ctx->alloc(&S->hscratch[si], need, &charged))) return st;
+        S->hscratch_bytes[si] = need;
+    }
+    char* scratch = static_cast<char*>(S->hscratch[si]);
+    if (activity && e == cudaSuccess) {
+        ClassifyArgs c{};
+        c.nvars = V->nvars;
+        c.rin2 = V->r_in * V->r_in;
+        c.rout2 = V->r_out * V->r_out;
+        c.brush = b;
+        c.nlev = 1;
+        c.nbrick = 0;
+        c.lv[0].bmin = L->sbmin;
+        c.lv[0].bmax = L->sbmax;
+        c.lv[0].n = L->n;
+        c.lv[0].bs = kSub;
+        c.lv[0].active = reinterpret_cast<uint32_t*>(scratch + copy_bytes);
+        e = launch_classify(c, s);
+        h.sactive = c.lv[0].active;
+        h.nsb = L->nsb;
+    }
+    if (ncopies > 1) {
+        // the counts spread over zeroed partial copies, summed into the output afterwards
+        uint32_t* copies = reinterpret_cast<uint32_t*>(scratch);
+        h.copies = copies;
+        h.ncopies = ncopies;
+        h.rowctr = copies + count * ncopies;
+        if (e == cudaSuccess) e = cudaMemsetAsync(copies, 0, sizeof(uint32_t) * (count * ncopies + 4), s);
+        if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
+        if (e == cudaSuccess) e = launch_histogram_reduce(copies, ncopies, count, q->hist, s);
+    } else {
+        // the counts and, after them, the row counter that balances the warps
+        h.rowctr = q->hist + count;
+        if (e == cudaSuccess) e = cudaMemsetAsync(q->hist, 0, sizeof(uint32_t) * (count + 1), s);
+        if (e == cudaSuccess) e = launch_histogram(h, V->dtype, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "server histogram");
     return RAYPC_OK;
 }
@@ -333,7 +388,7 @@ void turn(raypc_server* S) {
         // histograms first (short), with their own completion event
         for (Req* q : hists) {
             q->full_launched = true;
-            raypc_status hs = launch_hist(S, q, st);
+            raypc_status hs = launch_hist(S, q, s);
             if (hs != RAYPC_OK) { finish(S, q, hs); continue; }
             L.items.push_back({q, kHist, -1});
         }
@@ -460,6 +515,8 @@ raypc_status raypc_server_create(raypc_ctx* ctx, const raypc_server_config* cfg,
             if (e != cudaSuccess) { st = cuda_fail(e, "server stream"); break; }
             S->streams.push_back(s);
             S->busy.push_back(0);
+            S->hscratch.push_back(nullptr);
+            S->hscratch_bytes.push_back(0);
         }
     }
     for (int i = 0; i < cfg->num_streams && st == RAYPC_OK; ++i) {
@@ -494,6 +551,11 @@ raypc_status raypc_server_destroy(raypc_server* S) {
             cudaStreamSynchronize(s);
             cudaStreamDestroy(s);
         }
+        for (size_t i = 0; i < S->hscratch.size(); ++i)
+            if (S->hscratch[i]) {
+                cudaFree(S->hscratch[i]);
+                S->ctx->used -= S->hscratch_bytes[i] < S->ctx->used ? S->hscratch_bytes[i] : S->ctx->used;
+            }
         if (S->pool_mem) {
             cudaFree(S->pool_mem);
             S->ctx->used -= S->cfg.output_budget_bytes < S->ctx->used ? S->cfg.output_budget_bytes : S->ctx->used;

@@ -636,6 +636,10 @@ cudaError_t launch_classify(ClassifyArgs& c, cudaStream_t stream) {
     k_classify<<<blocks_for(total, 256), 256, 0, stream>>>(c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (c.nbrick == 0) {             // sub-bricks only: no skippable bits, no brick list
+        count_launches(1);
+        return cudaSuccess;
+    }
     k_skippable<<<blocks_for(c.total_brick, 256), 256, 0, stream>>>(c);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
