@@ -407,7 +407,10 @@ raypc_status raypc_render_batch(raypc_batch *batch, const raypc_view *views, int
  * is. Per-request timestamps are recorded. A request's results are identical to rendering /
  * histogramming it alone. Besides the output pool, each stream's batch holds
  * per-view buffers (see raypc_batch_create) for the view slots its launches
- * have used, at most num_streams * max_batch_views slots. */
+ * have used, at most num_streams * max_batch_views slots, and each stream a
+ * histogram scratch for the largest histogram it has run (the sub-brick bits
+ * of a request's brush and, from 128^3 on, 16 partial copies of its counts:
+ * 21 MB for 5 x 256^2 bins), all charged to the context's budget. */
 
 #define RAYPC_REQ_RENDER 0
 #define RAYPC_REQ_HISTOGRAM 1
